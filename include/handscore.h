@@ -1,0 +1,247 @@
+/*
+ * handscore.h -- C-ABI of the B300 hypothesis-scoring library (libhandscore.so)
+ * for the model-based 26-DOF hand tracker of arxiv 2005.07068.
+ *
+ * One PSO generation is   pose_fk -> render_score_batch -> pso_step,
+ * all asynchronous on the caller's stream.  The paper defines the problem as
+ * argmin_h E(h, O) (Section III.A, Eq. 5) minimised by PSO (Section III.B).
+ *
+ * Conventions
+ *  - Every data pointer is a DEVICE pointer owned by the caller, unless a
+ *    parameter says "host".  Scoring calls allocate nothing: scratch memory
+ *    is the caller's workspace (hs_workspace_size).
+ *  - Every call returns an int status: HS_OK (0) or a negative HS_ERR_* code.
+ *    Arguments are validated on the host before anything is launched; an
+ *    invalid call launches nothing and never aborts or traps.
+ *  - Kernels that meet bad data at run time (a non-finite pose, a wait that
+ *    timed out) set bits of a device status word, readable with
+ *    hs_get_device_status.
+ *  - Units: mm and rad.  Pose layout (Eq. 1-3): [x, y, z, theta_x, theta_y,
+ *    theta_z] of the wrist, then (MP_x, MP_z, PIP, DIP) for thumb, index,
+ *    middle, ring, pinky: 26 floats, row-major [P][26].
+ *  - Images are row-major with a row pitch in BYTES that must be a multiple
+ *    of 16 (the observation tiles are fetched with TMA); base addresses must
+ *    be 16-byte aligned.
+ */
+#ifndef HANDSCORE_H
+#define HANDSCORE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* a CUDA stream (cudaStream_t); NULL is the legacy default stream */
+typedef struct CUstream_st* hs_stream_t;
+
+/* ---- status codes ------------------------------------------------------ */
+#define HS_OK            0
+#define HS_ERR_ARG      -1  /* NULL pointer, bad enum, non-finite parameter */
+#define HS_ERR_ALIGN    -2  /* pointer not 16-B aligned or pitch not a multiple of 16 */
+#define HS_ERR_SIZE     -3  /* size out of range or workspace too small */
+#define HS_ERR_TIMEOUT  -4  /* a device wait ran out (see hs_get_device_status) */
+#define HS_ERR_NOT_IMPL -5
+#define HS_ERR_CUDA     -6  /* a CUDA runtime call failed (launch, copy, driver entry point) */
+
+/* ---- device status bits (hs_get_device_status) ------------------------- */
+#define HS_DEV_NONFINITE_POSE 0x1u /* pose_fk met a NaN/inf pose; that particle's E is NaN */
+#define HS_DEV_TMA_TIMEOUT    0x2u /* an observation tile load did not arrive in time */
+
+/* ---- limits -------------------------------------------------------------- */
+#define HS_NDOF            26
+#define HS_MAX_BONES       32
+#define HS_MAX_PRIMS       64
+#define HS_MAX_PARTICLES   65536
+#define HS_MAX_ROI         8192   /* W, H <= HS_MAX_ROI */
+
+/* ---- hand model (Section II.A, Fig. 2) ----------------------------------- */
+#define HS_PRIM_ELLIPSOID 0  /* dims = (sx, sy, sz, unused): semi-axes, mm      */
+#define HS_PRIM_ECONE     1  /* dims = (ax, az, hl, kappa): capped elliptic truncated
+                                cone along local y, |y| <= hl, section semi-axes
+                                (ax, az) * (1 + kappa * y / hl), |kappa| < 1;
+                                kappa = 0 is an elliptic cylinder                 */
+
+/* Bone b > 0 has frame  parent * T(offset) * Rz(rest[2]) Ry(rest[1]) Rx(rest[0])
+ * * Rz(pose[dof_z]) * Rx(pose[dof_x])  (a dof of -1 means none).  Bone 0 is the
+ * palm: origin at the wrist pose[0..2], rotation diag(1,-1,-1) *
+ * Rz(pose[5]) Ry(pose[4]) Rx(pose[3]).  Bones must be listed parents first. */
+typedef struct {
+    int32_t parent;     /* < own index; ignored for bone 0 */
+    int32_t dof_z;      /* pose index driving Rz, or -1 */
+    int32_t dof_x;      /* pose index driving Rx, or -1 */
+    int32_t reserved;
+    float offset[3];    /* bone origin in the parent frame, mm */
+    float rest[3];      /* fixed rest rotation angles (x, y, z), rad */
+} HsBoneDesc;
+
+/* a primitive is axis-aligned with its bone, centred at `center` (bone frame) */
+typedef struct {
+    int32_t bone;
+    int32_t kind;       /* HS_PRIM_ELLIPSOID or HS_PRIM_ECONE */
+    float center[3];
+    float dims[4];
+} HsPrimDesc;
+
+typedef struct {
+    int32_t n_bones;            /* 1..HS_MAX_BONES */
+    int32_t n_prims;            /* 1..HS_MAX_PRIMS */
+    const HsBoneDesc* bones;    /* host [n_bones] */
+    const HsPrimDesc* prims;    /* host [n_prims] */
+    float lo[HS_NDOF];          /* joint limits (Tables 1-2, possibly narrowed), mm / rad */
+    float hi[HS_NDOF];
+} HsModelDesc;
+
+/* opaque validated model; lives in host memory only (it is passed to the
+ * kernels by value as a launch parameter) */
+typedef struct HsModel HsModel;
+
+/* pinhole camera; pixel (u, v) casts the ray ((u+0.5-cx)/fx, (v+0.5-cy)/fy, 1),
+ * so depth = camera z (Kinect convention) */
+typedef struct {
+    float fx, fy, cx, cy;
+} HsCamera;
+
+#define HS_DEPTH_U16 0  /* uint16 mm, 0 = hole / undefined */
+#define HS_DEPTH_F32 1  /* float32 mm, 0 = undefined */
+
+/* observation O = (O_s, O_d) of Section II.B, one ROI */
+typedef struct {
+    const void* depth;      /* device [H][depth_pitch bytes] */
+    const uint8_t* skin;    /* device [H][skin_pitch bytes], nonzero = skin */
+    int32_t W, H;           /* ROI size, 1..HS_MAX_ROI */
+    int32_t depth_pitch;    /* bytes, multiple of 16, >= W * element size */
+    int32_t skin_pitch;     /* bytes, multiple of 16, >= W */
+    int32_t depth_type;     /* HS_DEPTH_U16 or HS_DEPTH_F32 */
+    uint32_t* stats;        /* device [2] (#valid depth pixels on skin, #skin pixels),
+                               written by hs_obs_prepare, read by render_score_batch */
+} HsObs;
+
+/* constants of Eq. 4-5 (paper: d_m = 1 cm, d_M = 4 cm, lambda = 20, lambda_k = 10) */
+typedef struct {
+    float d_m, d_M, lambda, lambda_k;
+} HsScoreParams;
+
+/* per-particle sums of Eq. 4 (optional output of render_score_batch) */
+typedef struct {
+    float t_sum;        /* sum of the clamped depth term */
+    uint32_t n_and;     /* sum(o_s AND r_m) */
+    uint32_t n_or;      /* sum(o_s OR r_m) */
+    uint32_t n_hit;     /* pixels where the hypothesis renders */
+} HsParts;
+
+/* 64-byte camera-space primitive record written by pose_fk (layout of float m[16]):
+ *   m[0..8]  columns c0, c1, c2 of M = S^-1 R^T (R: primitive-to-camera rotation,
+ *            S = diag of the primitive's scale), so a ray direction d = (a, b, 1)
+ *            maps to h = a c0 + b c1 + c2 in scaled local coordinates
+ *   m[9..11] C, the primitive centre in camera coordinates (mm); the renderer
+ *            takes the ray point at depth t0 = C_z: g = M (t0 d - C)
+ *   m[12]    reserved (0)
+ *   m[13]    kappa for HS_PRIM_ECONE; 2.0 marks an ellipsoid
+ *   m[14]    (int16 u0, int16 v0), m[15] (int16 u1, int16 v1): conservative
+ *            inclusive pixel box of the primitive's projection              */
+typedef struct {
+    float m[16];
+} HsPrim;
+
+/* swarm state, all device float arrays: x, v, pbest [P][26]; pbest_E [P];
+ * gbest [26]; gbest_E [1]; E [P] = objective of x from render_score_batch */
+typedef struct {
+    float* x;
+    float* v;
+    float* pbest;
+    float* pbest_E;
+    float* gbest;
+    float* gbest_E;
+    const float* E;
+} HsSwarm;
+
+/* Section III.B: c1 = 2.8, c2 = 1.3; w = 2 / |2 - psi - sqrt(psi^2 - 4 psi)|,
+ * psi = c1 + c2 > 4 (computed by pso_step); mutation every 3 generations of
+ * the worst half (n_mutate = P / 2); mutate_every <= 0 disables it */
+typedef struct {
+    float c1, c2;
+    int32_t mutate_every;
+    int32_t n_mutate;
+} HsPsoParams;
+
+/* ---- calls ------------------------------------------------------------------ */
+
+/* library version (major * 10000 + minor * 100 + patch) */
+int hs_version(void);
+
+/* static text for a status code */
+const char* hs_status_string(int status);
+
+/* Validate a model descriptor (Section II.A) and copy it into an opaque host
+ * object.  Allocates host memory only.  Errors: HS_ERR_ARG (NULL, bad parent
+ * order, bad dof index, bad kind, non-positive or non-finite dims, |kappa| >= 1,
+ * lo > hi), HS_ERR_SIZE (counts out of range). */
+int hs_model_create(const HsModelDesc* desc, HsModel** out);
+int hs_model_destroy(HsModel* model);
+
+/* Bytes of workspace render_score_batch needs for P particles (per-particle
+ * counters and per-CTA partial sums).  The workspace must be zeroed once
+ * (hs_workspace_reset) before first use; calls leave it zeroed again.
+ * Errors: HS_ERR_ARG (bytes NULL), HS_ERR_SIZE (P out of range). */
+int hs_workspace_size(int P, size_t* bytes);
+int hs_workspace_reset(void* workspace, size_t bytes, hs_stream_t stream);
+
+/* Per-frame preparation of an observation: counts the valid-depth skin pixels
+ * and the skin pixels of the ROI into obs->stats.  Call once whenever the
+ * observation changes, before render_score_batch.
+ * Errors: HS_ERR_ARG, HS_ERR_ALIGN, HS_ERR_SIZE, HS_ERR_CUDA. */
+int hs_obs_prepare(const HsObs* obs, hs_stream_t stream);
+
+/* Forward kinematics (Eq. 1-3, Tables 1-2): clamp each pose to the model's
+ * limits, build the bone frames and write P x n_prims camera-space records
+ * (HsPrim) and kc[P] (the finger-crossing penalty after Eq. 5, rad).  A pose
+ * with a NaN/inf entry gets kc = NaN and sets HS_DEV_NONFINITE_POSE.
+ * poses [P][26], prims [P][n_prims], kc [P].  P = 0 is a no-op.
+ * Errors: HS_ERR_ARG, HS_ERR_ALIGN (prims not 16-B aligned), HS_ERR_SIZE, HS_ERR_CUDA. */
+int pose_fk(const HsModel* model, const float* poses, int P, const HsCamera* cam,
+            HsPrim* prims, float* kc, hs_stream_t stream);
+
+/* Render every hypothesis into the observation ROI by FP32 analytic ray casting
+ * (depth map r_d, Section III.A) and reduce the per-pixel terms of Eq. 4 to
+ * E[p] = D + lambda_k kc[p] (Eq. 5).  No rendered image is stored; parts [P]
+ * (may be NULL) receives the sums.  dbg_depth [P][H][W] float (0 = no hit) and
+ * dbg_mask [P][H][W] uint8 (bit 0 = hit, bit 1 = r_m) are optional test
+ * outputs (NULL in production; when given they are cleared first).
+ * workspace: hs_workspace_size(P) bytes, zeroed once before first use.
+ * Errors: HS_ERR_ARG, HS_ERR_ALIGN, HS_ERR_SIZE, HS_ERR_CUDA. */
+int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* cam,
+                       const HsPrim* prims, const float* kc, int P, const HsScoreParams* params,
+                       void* workspace, size_t workspace_bytes, float* E, HsParts* parts,
+                       float* dbg_depth, uint8_t* dbg_mask, hs_stream_t stream);
+
+/* Tracking initialisation of a swarm (Section III.B: random positions, zero
+ * velocity): particle 0 = clamped seed_pose, particle i > 0 = seed_pose +
+ * (2u - 1) * scale[d] (u: Philox4x32-10 stream 3, counter (i, 3<<16 | d/4, 0,
+ * frame), key = seed), clamped; pbest = x, pbest_E = gbest_E = +inf,
+ * gbest = particle 0.  seed_pose: device [26]; scale: host [26].
+ * Errors: HS_ERR_ARG, HS_ERR_SIZE, HS_ERR_CUDA. */
+int pso_init(const HsModel* model, const HsSwarm* swarm, int P, const float* seed_pose,
+             const float* scale, uint64_t seed, uint32_t frame, hs_stream_t stream);
+
+/* One PSO generation after E = objective(x) (Section III.B, Eq. 6-7):
+ * pbest where E < pbest_E; gbest = pbest[argmin pbest_E] (lowest index on
+ * ties); v <- w (v + c1 r1 (pbest - x) + c2 r2 (gbest - x)), x <- clamp(x + v)
+ * with r1/r2 = uniforms 2d / 2d+1 of Philox stream 1, counter (i, 1<<16 | k/4,
+ * gen, frame); if mutate_every > 0 and gen % mutate_every == 0 the n_mutate
+ * particles with the largest E (ties: higher index, NaN worst) re-draw dims
+ * 6..25 uniformly in the limits (stream 2) with zero velocity there.
+ * One CTA per swarm; P <= 4096.
+ * Errors: HS_ERR_ARG, HS_ERR_SIZE, HS_ERR_CUDA. */
+int pso_step(const HsModel* model, const HsSwarm* swarm, int P, const HsPsoParams* params,
+             uint64_t seed, uint32_t frame, uint32_t gen, hs_stream_t stream);
+
+/* Read (and optionally clear) the device status word of the current device.
+ * Synchronises the device.  out: host.  Errors: HS_ERR_ARG, HS_ERR_CUDA. */
+int hs_get_device_status(uint32_t* out, int clear);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HANDSCORE_H */

@@ -1,0 +1,377 @@
+// api.cu -- the extern "C" boundary of libhandscore.so (include/handscore.h).
+//
+// Every entry point validates its arguments on the host and returns a
+// negative status before touching the GPU; only then does it launch.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "hs_args.cuh"
+
+namespace hs {
+
+// ---- the device status word ----------------------------------------------------
+static __device__ uint32_t g_status;
+constexpr int kMaxDevices = 64;
+static uint32_t* g_status_ptr[kMaxDevices];
+static std::mutex g_mutex;
+
+// device address of g_status on the current device (looked up once per device)
+static int status_ptr(uint32_t** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_status_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return HS_ERR_CUDA;
+        g_status_ptr[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = g_status_ptr[dev];
+    return HS_OK;
+}
+
+// ---- TMA descriptor encoding (driver entry point, no link-time libcuda) ----------
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+static int encode_tile_map(CUtensorMap* map, const void* base, CUtensorMapDataType type, int esz, int W, int H,
+                           int pitch)
+{
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!g_encode) return HS_ERR_CUDA;
+    (void)esz;
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    const cuuint32_t box[2] = {16, 16};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = g_encode(map, type, 2, const_cast<void*>(base), dims, strides, box, estr,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? HS_OK : HS_ERR_CUDA;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+static bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
+
+static int validate_obs(const HsObs* o)
+{
+    if (!o || !o->depth || !o->skin || !o->stats) return HS_ERR_ARG;
+    if (o->depth_type != HS_DEPTH_U16 && o->depth_type != HS_DEPTH_F32) return HS_ERR_ARG;
+    if (o->W < 1 || o->H < 1 || o->W > HS_MAX_ROI || o->H > HS_MAX_ROI) return HS_ERR_SIZE;
+    const int esz = o->depth_type == HS_DEPTH_F32 ? 4 : 2;
+    if (!aligned16(o->depth) || !aligned16(o->skin)) return HS_ERR_ALIGN;
+    if (o->depth_pitch % 16 != 0 || o->skin_pitch % 16 != 0) return HS_ERR_ALIGN;
+    if (o->depth_pitch < o->W * esz || o->skin_pitch < o->W) return HS_ERR_SIZE;
+    return HS_OK;
+}
+
+static int validate_cam(const HsCamera* c)
+{
+    if (!c) return HS_ERR_ARG;
+    if (!finite_pos(c->fx) || !finite_pos(c->fy) || !std::isfinite(c->cx) || !std::isfinite(c->cy))
+        return HS_ERR_ARG;
+    return HS_OK;
+}
+
+constexpr int kMaxK = 64;           // CTAs per particle in render_score_batch
+constexpr int kTargetCtas = 148 * 8;
+
+static size_t counters_bytes(int P) { return ((size_t)P * 4 + 255) / 256 * 256; }
+
+}  // namespace hs
+
+using namespace hs;
+
+struct HsModel {
+    DevModel dev;
+    Limits lim;
+};
+
+extern "C" {
+
+int hs_version(void) { return 100; }
+
+const char* hs_status_string(int s)
+{
+    switch (s) {
+    case HS_OK: return "ok";
+    case HS_ERR_ARG: return "invalid argument";
+    case HS_ERR_ALIGN: return "misaligned pointer or pitch";
+    case HS_ERR_SIZE: return "size out of range";
+    case HS_ERR_TIMEOUT: return "device wait timed out";
+    case HS_ERR_NOT_IMPL: return "not implemented";
+    case HS_ERR_CUDA: return "CUDA runtime error";
+    default: return "unknown status";
+    }
+}
+
+int hs_model_create(const HsModelDesc* d, HsModel** out)
+{
+    if (!d || !out || !d->bones || !d->prims) return HS_ERR_ARG;
+    if (d->n_bones < 1 || d->n_bones > HS_MAX_BONES || d->n_prims < 1 || d->n_prims > HS_MAX_PRIMS)
+        return HS_ERR_SIZE;
+    HsModel* m = static_cast<HsModel*>(std::calloc(1, sizeof(HsModel)));
+    if (!m) return HS_ERR_ARG;
+    DevModel& dm = m->dev;
+    dm.n_bones = d->n_bones;
+    dm.n_prims = d->n_prims;
+    int bad = 0;
+    for (int k = 0; k < HS_NDOF; ++k) {
+        if (!std::isfinite(d->lo[k]) || !std::isfinite(d->hi[k]) || d->lo[k] > d->hi[k]) bad = 1;
+        dm.lo[k] = m->lim.lo[k] = d->lo[k];
+        dm.hi[k] = m->lim.hi[k] = d->hi[k];
+    }
+    int max_depth = 0;
+    for (int b = 0; b < d->n_bones; ++b) {
+        const HsBoneDesc& B = d->bones[b];
+        DevBone& o = dm.bones[b];
+        o.parent = b == 0 ? -1 : B.parent;
+        o.dof_z = B.dof_z;
+        o.dof_x = B.dof_x;
+        if (b > 0 && (B.parent < 0 || B.parent >= b)) bad = 1;
+        if (B.dof_z < -1 || B.dof_z >= HS_NDOF || B.dof_x < -1 || B.dof_x >= HS_NDOF) bad = 1;
+        o.depth = b == 0 ? 0 : dm.bones[B.parent < 0 || B.parent >= b ? 0 : B.parent].depth + 1;
+        if (o.depth > max_depth) max_depth = o.depth;
+        for (int i = 0; i < 3; ++i) {
+            if (!std::isfinite(B.offset[i]) || !std::isfinite(B.rest[i])) bad = 1;
+            o.off[i] = B.offset[i];
+        }
+        // rest rotation Rz(rz) Ry(ry) Rx(rx), row-major, built in double
+        const double cx = std::cos(B.rest[0]), sx = std::sin(B.rest[0]);
+        const double cy = std::cos(B.rest[1]), sy = std::sin(B.rest[1]);
+        const double cz = std::cos(B.rest[2]), sz = std::sin(B.rest[2]);
+        const double R[9] = {cz * cy, cz * sy * sx - sz * cx, cz * sy * cx + sz * sx,
+                             sz * cy, sz * sy * sx + cz * cx, sz * sy * cx - cz * sx,
+                             -sy,     cy * sx,                cy * cx};
+        for (int i = 0; i < 9; ++i) o.rest[i] = (float)R[i];
+    }
+    dm.max_depth = max_depth;
+    for (int k = 0; k < d->n_prims; ++k) {
+        const HsPrimDesc& P = d->prims[k];
+        DevPrimDesc& o = dm.prims[k];
+        o.bone = P.bone;
+        o.kind = P.kind;
+        if (P.bone < 0 || P.bone >= d->n_bones) bad = 1;
+        if (P.kind != HS_PRIM_ELLIPSOID && P.kind != HS_PRIM_ECONE) bad = 1;
+        for (int i = 0; i < 3; ++i) {
+            if (!std::isfinite(P.center[i])) bad = 1;
+            o.center[i] = P.center[i];
+        }
+        for (int i = 0; i < 4; ++i) o.dims[i] = P.dims[i];
+        if (!finite_pos(P.dims[0]) || !finite_pos(P.dims[1]) || !finite_pos(P.dims[2])) bad = 1;
+        if (P.kind == HS_PRIM_ECONE && !(std::fabs(P.dims[3]) < 1.f)) bad = 1;
+    }
+    if (bad) {
+        std::free(m);
+        return HS_ERR_ARG;
+    }
+    *out = m;
+    return HS_OK;
+}
+
+int hs_model_destroy(HsModel* m)
+{
+    if (!m) return HS_ERR_ARG;
+    std::free(m);
+    return HS_OK;
+}
+
+int hs_workspace_size(int P, size_t* bytes)
+{
+    if (!bytes) return HS_ERR_ARG;
+    if (P < 0 || P > HS_MAX_PARTICLES) return HS_ERR_SIZE;
+    *bytes = counters_bytes(P) + (size_t)P * kMaxK * sizeof(float4);
+    return HS_OK;
+}
+
+int hs_workspace_reset(void* ws, size_t bytes, hs_stream_t stream)
+{
+    if (!ws && bytes) return HS_ERR_ARG;
+    if (!bytes) return HS_OK;
+    return cudaMemsetAsync(ws, 0, bytes, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int hs_obs_prepare(const HsObs* obs, hs_stream_t stream)
+{
+    int rc = validate_obs(obs);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(obs->stats, 0, 2 * sizeof(uint32_t), s) != cudaSuccess) return HS_ERR_CUDA;
+    if (launch_obs_stats(static_cast<const unsigned char*>(obs->depth), obs->depth_pitch,
+                         obs->depth_type == HS_DEPTH_F32, obs->skin, obs->skin_pitch, obs->W, obs->H, obs->stats,
+                         s) != cudaSuccess)
+        return HS_ERR_CUDA;
+    return HS_OK;
+}
+
+int pose_fk(const HsModel* model, const float* poses, int P, const HsCamera* cam, HsPrim* prims, float* kc,
+            hs_stream_t stream)
+{
+    if (!model || !poses || !prims || !kc) return HS_ERR_ARG;
+    int rc = validate_cam(cam);
+    if (rc) return rc;
+    if (P < 0 || P > HS_MAX_PARTICLES) return HS_ERR_SIZE;
+    if (!aligned16(prims)) return HS_ERR_ALIGN;
+    if (P == 0) return HS_OK;
+    FkArgs a;
+    a.poses = poses;
+    a.P = P;
+    a.fx = cam->fx;
+    a.fy = cam->fy;
+    a.cx = cam->cx;
+    a.cy = cam->cy;
+    a.prims = reinterpret_cast<float4*>(prims);
+    a.kc = kc;
+    if ((rc = status_ptr(&a.status))) return rc;
+    return launch_fk(model->dev, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsPrim* prims,
+                       const float* kc, int P, const HsScoreParams* params, void* workspace, size_t workspace_bytes,
+                       float* E, HsParts* parts, float* dbg_depth, uint8_t* dbg_mask, hs_stream_t stream)
+{
+    if (!model || !prims || !kc || !params || !E) return HS_ERR_ARG;
+    if ((dbg_depth == nullptr) != (dbg_mask == nullptr)) return HS_ERR_ARG;
+    int rc = validate_obs(obs);
+    if (rc) return rc;
+    if ((rc = validate_cam(cam))) return rc;
+    if (!std::isfinite(params->d_m) || !std::isfinite(params->d_M) || !std::isfinite(params->lambda) ||
+        !std::isfinite(params->lambda_k) || params->d_m < 0.f || params->d_M < 0.f)
+        return HS_ERR_ARG;
+    if (P < 0 || P > HS_MAX_PARTICLES) return HS_ERR_SIZE;
+    if (!aligned16(prims) || (workspace && !aligned16(workspace))) return HS_ERR_ALIGN;
+    size_t need = 0;
+    hs_workspace_size(P, &need);
+    if (P > 0 && (!workspace || workspace_bytes < need)) return HS_ERR_SIZE;
+    if (P == 0) return HS_OK;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool f32 = obs->depth_type == HS_DEPTH_F32;
+    CUtensorMap tm_depth, tm_skin;
+    if ((rc = encode_tile_map(&tm_depth, obs->depth, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                              f32 ? 4 : 2, obs->W, obs->H, obs->depth_pitch)))
+        return rc;
+    if ((rc = encode_tile_map(&tm_skin, obs->skin, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, obs->W, obs->H, obs->skin_pitch)))
+        return rc;
+    if (dbg_depth) {
+        const size_t n = (size_t)P * obs->W * obs->H;
+        if (cudaMemsetAsync(dbg_depth, 0, n * sizeof(float), s) != cudaSuccess ||
+            cudaMemsetAsync(dbg_mask, 0, n, s) != cudaSuccess)
+            return HS_ERR_CUDA;
+    }
+    const int tiles = ((obs->W + 15) / 16) * ((obs->H + 15) / 16);
+    int K = (kTargetCtas + P - 1) / P;
+    if (K > kMaxK) K = kMaxK;
+    if (K > tiles) K = tiles;
+    if (K < 1) K = 1;
+
+    RenderArgs a;
+    a.prims = reinterpret_cast<const float4*>(prims);
+    a.kc = kc;
+    a.P = P;
+    a.n_prims = model->dev.n_prims;
+    a.K = K;
+    a.W = obs->W;
+    a.H = obs->H;
+    a.fx = cam->fx;
+    a.fy = cam->fy;
+    a.cx = cam->cx;
+    a.cy = cam->cy;
+    a.d_m = params->d_m;
+    a.d_M = params->d_M;
+    a.lambda = params->lambda;
+    a.lambda_k = params->lambda_k;
+    a.depth_f32 = f32;
+    a.stats = obs->stats;
+    uint8_t* ws = static_cast<uint8_t*>(workspace);
+    a.counters = reinterpret_cast<uint32_t*>(ws);
+    a.partials = reinterpret_cast<float4*>(ws + counters_bytes(P));
+    a.E = E;
+    a.parts = parts;
+    a.dbg_depth = dbg_depth;
+    a.dbg_mask = dbg_mask;
+    if ((rc = status_ptr(&a.status))) return rc;
+    return launch_render_score(tm_depth, tm_skin, a, s) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int pso_init(const HsModel* model, const HsSwarm* sw, int P, const float* seed_pose, const float* scale,
+             uint64_t seed, uint32_t frame, hs_stream_t stream)
+{
+    if (!model || !sw || !seed_pose || !scale) return HS_ERR_ARG;
+    if (!sw->x || !sw->v || !sw->pbest || !sw->pbest_E || !sw->gbest || !sw->gbest_E) return HS_ERR_ARG;
+    if (P < 1 || P > HS_MAX_PARTICLES) return HS_ERR_SIZE;
+    PsoInitArgs a;
+    a.x = sw->x;
+    a.v = sw->v;
+    a.pbest = sw->pbest;
+    a.pbest_E = sw->pbest_E;
+    a.gbest = sw->gbest;
+    a.gbest_E = sw->gbest_E;
+    a.seed_pose = seed_pose;
+    for (int d = 0; d < HS_NDOF; ++d) {
+        if (!std::isfinite(scale[d]) || scale[d] < 0.f) return HS_ERR_ARG;
+        a.scale[d] = scale[d];
+    }
+    a.P = P;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.frame = frame;
+    return launch_pso_init(model->lim, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int pso_step(const HsModel* model, const HsSwarm* sw, int P, const HsPsoParams* prm, uint64_t seed, uint32_t frame,
+             uint32_t gen, hs_stream_t stream)
+{
+    if (!model || !sw || !prm) return HS_ERR_ARG;
+    if (!sw->x || !sw->v || !sw->pbest || !sw->pbest_E || !sw->gbest || !sw->gbest_E || !sw->E) return HS_ERR_ARG;
+    if (P < 1 || P > 4096) return HS_ERR_SIZE;
+    const double psi = (double)prm->c1 + (double)prm->c2;
+    if (!std::isfinite(psi) || prm->c1 < 0.f || prm->c2 < 0.f || psi <= 4.0) return HS_ERR_ARG;
+    if (prm->mutate_every > 0 && (prm->n_mutate < 0 || prm->n_mutate > P)) return HS_ERR_ARG;
+    PsoStepArgs a;
+    a.x = sw->x;
+    a.v = sw->v;
+    a.pbest = sw->pbest;
+    a.pbest_E = sw->pbest_E;
+    a.gbest = sw->gbest;
+    a.gbest_E = sw->gbest_E;
+    a.E = sw->E;
+    a.P = P;
+    a.c1 = prm->c1;
+    a.c2 = prm->c2;
+    // constriction factor of Section III.B
+    a.w = (float)(2.0 / std::fabs(2.0 - psi - std::sqrt(psi * psi - 4.0 * psi)));
+    a.mutate = prm->mutate_every > 0 && gen % (uint32_t)prm->mutate_every == 0 && prm->n_mutate > 0;
+    a.n_mutate = prm->n_mutate;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.frame = frame;
+    a.gen = gen;
+    return launch_pso_step(model->lim, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int hs_get_device_status(uint32_t* out, int clear)
+{
+    if (!out) return HS_ERR_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return HS_ERR_CUDA;
+    if (cudaMemcpyFromSymbol(out, g_status, sizeof(uint32_t)) != cudaSuccess) return HS_ERR_CUDA;
+    if (clear) {
+        const uint32_t z = 0;
+        if (cudaMemcpyToSymbol(g_status, &z, sizeof(uint32_t)) != cudaSuccess) return HS_ERR_CUDA;
+    }
+    return HS_OK;
+}
+
+}  // extern "C"

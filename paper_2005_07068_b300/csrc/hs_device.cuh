@@ -1,0 +1,97 @@
+// hs_device.cuh -- device-side definitions shared by the handscore kernels.
+//
+// The validated hand model travels to the kernels by value (a launch
+// parameter in the constant bank), so the library keeps no device copy of it.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/handscore.h"
+
+namespace hs {
+
+constexpr int kNdof = HS_NDOF;
+constexpr int kMaxBones = HS_MAX_BONES;
+constexpr int kMaxPrims = HS_MAX_PRIMS;
+constexpr float kEllipsoidMarker = 2.0f;  // HsPrim.m[13] value that marks an ellipsoid
+
+struct DevBone {
+    int32_t parent, dof_z, dof_x, depth;  // depth in the tree (palm = 0)
+    float off[3];
+    float rest[9];                        // row-major Rz Ry Rx of the rest angles
+};
+
+struct DevPrimDesc {
+    int32_t bone, kind;
+    float center[3];
+    float dims[4];
+};
+
+// everything the FK kernel needs about the model (about 4.7 KB)
+struct DevModel {
+    int32_t n_bones, n_prims, max_depth, pad;
+    DevBone bones[kMaxBones];
+    DevPrimDesc prims[kMaxPrims];
+    float lo[kNdof], hi[kNdof];
+};
+
+struct Limits {
+    float lo[kNdof], hi[kNdof];
+};
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ---------------------
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    }
+    return c;
+}
+
+// U[0,1) from the top 24 bits (exact in float)
+__device__ __forceinline__ float u01(uint32_t u) { return (float)(u >> 8) * (1.0f / 16777216.0f); }
+
+// Random-number streams of the swarm (counter word 1 = stream << 16 | block)
+constexpr uint32_t kStreamPso = 1, kStreamMutate = 2, kStreamInit = 3;
+
+// ---- fast PTX arithmetic (documented approximate instructions) --------------
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void set_status(uint32_t* status, uint32_t bit)
+{
+    if (status) atomicOr(status, bit);
+}
+
+// pack/unpack an inclusive int16 pixel box into two float-sized words
+__device__ __forceinline__ float pack_i16x2(int a, int b)
+{
+    const uint32_t w = (uint32_t)(uint16_t)(int16_t)a | ((uint32_t)(uint16_t)(int16_t)b << 16);
+    return __uint_as_float(w);
+}
+__device__ __forceinline__ int lo_i16(float w) { return (int)(int16_t)(__float_as_uint(w) & 0xFFFFu); }
+__device__ __forceinline__ int hi_i16(float w) { return (int)(int16_t)(__float_as_uint(w) >> 16); }
+
+}  // namespace hs

@@ -1,0 +1,180 @@
+// pso.cu -- swarm initialisation and one PSO generation on the device
+// (Section III.B, Eq. 6-7 and the mutation of the worst half).
+//
+// The paper runs the swarm on the CPU and reads D back every generation
+// (Section IV, step 3).  Here the whole generation stays on the GPU: one CTA
+// per swarm updates the personal bests, takes the argmin for the global best,
+// applies Eq. 6-7 with per-dimension r1/r2 from a counter-based Philox4x32-10
+// stream, clamps to the limits and, every `mutate_every` generations,
+// re-draws the finger dims of the worst particles.
+#include <cfloat>
+#include <climits>
+
+#include "hs_args.cuh"
+
+namespace hs {
+
+constexpr int kInitBlocks = (kNdof + 3) / 4;     // Philox blocks per particle for 26 dims
+constexpr int kPairBlocks = (2 * kNdof + 3) / 4; // for r1/r2 of 26 dims
+constexpr int kMutBlocks = (kNdof - 6 + 3) / 4;  // for the 20 finger dims
+constexpr int kPsoThreads = 512;
+
+__global__ void __launch_bounds__(256) pso_init_kernel(const __grid_constant__ Limits lim, const PsoInitArgs a)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = g / kInitBlocks, j = g % kInitBlocks;
+    if (i >= a.P) return;
+    const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamInit << 16) | (uint32_t)j, 0u, a.frame}, a.key0, a.key1);
+    const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const int d = 4 * j + l;
+        if (d >= kNdof) break;
+        const float sp = a.seed_pose[d];
+        float xv = i == 0 ? sp : fmaf(fmaf(2.f, u01(u[l]), -1.f), a.scale[d], sp);
+        xv = fminf(fmaxf(xv, lim.lo[d]), lim.hi[d]);
+        const size_t o = (size_t)i * kNdof + d;
+        a.x[o] = xv;
+        a.v[o] = 0.f;
+        a.pbest[o] = xv;
+        if (i == 0) a.gbest[d] = xv;
+    }
+    if (j == 0) {
+        a.pbest_E[i] = INFINITY;
+        if (i == 0) a.gbest_E[0] = INFINITY;
+    }
+}
+
+// (E_j, j) ranks before (E_i, i); NaN ranks after every number
+__device__ __forceinline__ bool ranks_before(float ej, int j, float ei, int i)
+{
+    const bool nj = isnan(ej), ni = isnan(ei);
+    if (nj != ni) return ni;
+    if (!nj && ej != ei) return ej < ei;
+    return j < i;
+}
+
+__global__ void __launch_bounds__(kPsoThreads) pso_step_kernel(const __grid_constant__ Limits lim, const PsoStepArgs a)
+{
+    extern __shared__ float sE[];  // [P]
+    __shared__ float s_gbest[kNdof];
+    __shared__ float red_v[kPsoThreads / 32];
+    __shared__ int red_i[kPsoThreads / 32];
+    __shared__ int s_g;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int P = a.P;
+
+    // 1. personal bests (strict improvement; NaN never improves)
+    float bv = INFINITY;
+    int bi = INT_MAX;
+    for (int i = tid; i < P; i += kPsoThreads) {
+        const float e = a.E[i];
+        sE[i] = e;
+        float pe = a.pbest_E[i];
+        if (e < pe) {
+            pe = e;
+            a.pbest_E[i] = e;
+            for (int d = 0; d < kNdof; ++d) a.pbest[(size_t)i * kNdof + d] = a.x[(size_t)i * kNdof + d];
+        }
+        if (bi == INT_MAX || pe < bv) {  // indices rise, so ties keep the lowest
+            bv = pe;
+            bi = i;
+        }
+    }
+    // 2. global best = argmin pbest_E, lowest index on ties
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi != INT_MAX && (bi == INT_MAX || ov < bv || (ov == bv && oi < bi))) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    if (lane == 0) {
+        red_v[warp] = bv;
+        red_i[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float v = red_v[0];
+        int g = red_i[0];
+        for (int w = 1; w < kPsoThreads / 32; ++w) {
+            const int oi = red_i[w];
+            if (oi != INT_MAX && (g == INT_MAX || red_v[w] < v || (red_v[w] == v && oi < g))) {
+                v = red_v[w];
+                g = oi;
+            }
+        }
+        s_g = g;
+        a.gbest_E[0] = v;
+    }
+    __syncthreads();
+    if (tid < kNdof) {
+        const float gv = a.pbest[(size_t)s_g * kNdof + tid];
+        s_gbest[tid] = gv;
+        a.gbest[tid] = gv;
+    }
+    __syncthreads();
+
+    // 3. Eq. 6-7 with per-dimension r1, r2, then clamp
+    for (int q = tid; q < P * kPairBlocks; q += kPsoThreads) {
+        const int i = q / kPairBlocks, j = q % kPairBlocks;
+        const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamPso << 16) | (uint32_t)j, a.gen, a.frame}, a.key0, a.key1);
+        const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int d = 2 * j + h;
+            if (d >= kNdof) break;
+            const float r1 = u01(u[2 * h]), r2 = u01(u[2 * h + 1]);
+            const size_t o = (size_t)i * kNdof + d;
+            const float x = a.x[o];
+            float acc = fmaf(a.c1 * r1, a.pbest[o] - x, a.v[o]);
+            acc = fmaf(a.c2 * r2, s_gbest[d] - x, acc);
+            const float vn = a.w * acc;
+            a.v[o] = vn;
+            a.x[o] = fminf(fmaxf(x + vn, lim.lo[d]), lim.hi[d]);
+        }
+    }
+
+    // 4. mutation of the n_mutate worst particles (by this generation's E)
+    if (a.mutate) {
+        __syncthreads();
+        for (int i = tid; i < P; i += kPsoThreads) {
+            const float ei = sE[i];
+            int rank = 0;
+            for (int j = 0; j < P; ++j) rank += ranks_before(sE[j], j, ei, i);
+            if (rank >= P - a.n_mutate) {
+                for (int jb = 0; jb < kMutBlocks; ++jb) {
+                    const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamMutate << 16) | (uint32_t)jb, a.gen, a.frame},
+                                               a.key0, a.key1);
+                    const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        const int d = 6 + 4 * jb + l;
+                        if (d >= kNdof) break;
+                        const size_t o = (size_t)i * kNdof + d;
+                        a.x[o] = fmaf(u01(u[l]), lim.hi[d] - lim.lo[d], lim.lo[d]);
+                        a.v[o] = 0.f;
+                    }
+                }
+            }
+        }
+    }
+}
+
+cudaError_t launch_pso_init(const Limits& lim, const PsoInitArgs& args, cudaStream_t stream)
+{
+    const int n = args.P * kInitBlocks;
+    pso_init_kernel<<<(n + 255) / 256, 256, 0, stream>>>(lim, args);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pso_step(const Limits& lim, const PsoStepArgs& args, cudaStream_t stream)
+{
+    const size_t smem = (size_t)args.P * sizeof(float);
+    pso_step_kernel<<<1, kPsoThreads, smem, stream>>>(lim, args);
+    return cudaGetLastError();
+}
+
+}  // namespace hs

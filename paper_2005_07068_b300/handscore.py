@@ -1,0 +1,307 @@
+"""Thin ctypes binding of libhandscore.so (include/handscore.h).
+
+Argument marshalling only: every step of the scoring path runs in the CUDA
+kernels of the library.  Device memory comes from torch tensors; the stream
+is torch's current stream unless one is given.  If the shared library is
+missing this module raises at first use; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhandscore.so")
+
+HS_OK, HS_ERR_ARG, HS_ERR_ALIGN, HS_ERR_SIZE, HS_ERR_TIMEOUT, HS_ERR_NOT_IMPL, HS_ERR_CUDA = 0, -1, -2, -3, -4, -5, -6
+HS_DEV_NONFINITE_POSE, HS_DEV_TMA_TIMEOUT = 0x1, 0x2
+HS_PRIM_ELLIPSOID, HS_PRIM_ECONE = 0, 1
+HS_DEPTH_U16, HS_DEPTH_F32 = 0, 1
+NDOF = 26
+
+
+class HsBoneDesc(ctypes.Structure):
+    _fields_ = [("parent", ctypes.c_int32), ("dof_z", ctypes.c_int32), ("dof_x", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("offset", ctypes.c_float * 3), ("rest", ctypes.c_float * 3)]
+
+
+class HsPrimDesc(ctypes.Structure):
+    _fields_ = [("bone", ctypes.c_int32), ("kind", ctypes.c_int32), ("center", ctypes.c_float * 3),
+                ("dims", ctypes.c_float * 4)]
+
+
+class HsModelDesc(ctypes.Structure):
+    _fields_ = [("n_bones", ctypes.c_int32), ("n_prims", ctypes.c_int32),
+                ("bones", ctypes.POINTER(HsBoneDesc)), ("prims", ctypes.POINTER(HsPrimDesc)),
+                ("lo", ctypes.c_float * NDOF), ("hi", ctypes.c_float * NDOF)]
+
+
+class HsCamera(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+class HsObs(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_void_p), ("skin", ctypes.c_void_p), ("W", ctypes.c_int32),
+                ("H", ctypes.c_int32), ("depth_pitch", ctypes.c_int32), ("skin_pitch", ctypes.c_int32),
+                ("depth_type", ctypes.c_int32), ("stats", ctypes.c_void_p)]
+
+
+class HsScoreParams(ctypes.Structure):
+    _fields_ = [("d_m", ctypes.c_float), ("d_M", ctypes.c_float), ("lambda_", ctypes.c_float),
+                ("lambda_k", ctypes.c_float)]
+
+
+class HsSwarm(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("x", "v", "pbest", "pbest_E", "gbest", "gbest_E", "E")]
+
+
+class HsPsoParams(ctypes.Structure):
+    _fields_ = [("c1", ctypes.c_float), ("c2", ctypes.c_float), ("mutate_every", ctypes.c_int32),
+                ("n_mutate", ctypes.c_int32)]
+
+
+_vp = ctypes.c_void_p
+_SIGS = {
+    "hs_version": ([], ctypes.c_int),
+    "hs_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "hs_model_create": ([ctypes.POINTER(HsModelDesc), ctypes.POINTER(_vp)], ctypes.c_int),
+    "hs_model_destroy": ([_vp], ctypes.c_int),
+    "hs_workspace_size": ([ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "hs_workspace_reset": ([_vp, ctypes.c_size_t, _vp], ctypes.c_int),
+    "hs_obs_prepare": ([ctypes.POINTER(HsObs), _vp], ctypes.c_int),
+    "pose_fk": ([_vp, _vp, ctypes.c_int, ctypes.POINTER(HsCamera), _vp, _vp, _vp], ctypes.c_int),
+    "render_score_batch": ([_vp, ctypes.POINTER(HsObs), ctypes.POINTER(HsCamera), _vp, _vp, ctypes.c_int,
+                            ctypes.POINTER(HsScoreParams), _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp, _vp],
+                           ctypes.c_int),
+    "pso_init": ([_vp, ctypes.POINTER(HsSwarm), ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_float),
+                  ctypes.c_uint64, ctypes.c_uint32, _vp], ctypes.c_int),
+    "pso_step": ([_vp, ctypes.POINTER(HsSwarm), ctypes.c_int, ctypes.POINTER(HsPsoParams), ctypes.c_uint64,
+                  ctypes.c_uint32, ctypes.c_uint32, _vp], ctypes.c_int),
+    "hs_get_device_status": ([ctypes.POINTER(ctypes.c_uint32), ctypes.c_int], ctypes.c_int),
+}
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run `python -m paper_2005_07068_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _LIB = L
+    return _LIB
+
+
+class HandscoreError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn}: {lib().hs_status_string(status).decode()} ({status})")
+        self.status = status
+
+
+def _check(fn: str, status: int) -> None:
+    if status != HS_OK:
+        raise HandscoreError(fn, status)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+# ---- model ------------------------------------------------------------------------
+
+class Model:
+    """A validated hand model (host object; passed to kernels by value)."""
+
+    def __init__(self, bones_i, bones_f, prims_i, prims_f, lo, hi):
+        nb, npr = len(bones_i), len(prims_i)
+        self._bones = (HsBoneDesc * nb)()
+        for b in range(nb):
+            B = self._bones[b]
+            B.parent, B.dof_z, B.dof_x = (int(v) for v in bones_i[b])
+            B.offset[:] = [float(v) for v in bones_f[b][:3]]
+            B.rest[:] = [float(v) for v in bones_f[b][3:6]]
+        self._prims = (HsPrimDesc * npr)()
+        for k in range(npr):
+            Pd = self._prims[k]
+            Pd.bone, Pd.kind = (int(v) for v in prims_i[k])
+            Pd.center[:] = [float(v) for v in prims_f[k][:3]]
+            Pd.dims[:] = [float(v) for v in prims_f[k][3:7]]
+        d = HsModelDesc()
+        d.n_bones, d.n_prims = nb, npr
+        d.bones = ctypes.cast(self._bones, ctypes.POINTER(HsBoneDesc))
+        d.prims = ctypes.cast(self._prims, ctypes.POINTER(HsPrimDesc))
+        d.lo[:] = [float(v) for v in lo]
+        d.hi[:] = [float(v) for v in hi]
+        h = _vp()
+        _check("hs_model_create", lib().hs_model_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.n_prims = npr
+        self.lo = np.asarray(lo, np.float32)
+        self.hi = np.asarray(hi, np.float32)
+
+    @classmethod
+    def from_geometry(cls, g, lo, hi) -> "Model":
+        return cls(g.bones_i, g.bones_f, g.prims_i, g.prims_f, lo, hi)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _LIB is not None:
+            _LIB.hs_model_destroy(h)
+            self.handle = None
+
+
+def camera(fx, fy, cx, cy) -> HsCamera:
+    return HsCamera(fx, fy, cx, cy)
+
+
+def score_params(d_m=10.0, d_M=40.0, lam=20.0, lam_k=10.0) -> HsScoreParams:
+    """Eq. 4-5 constants (Section III.A: 1 cm, 4 cm, 20, 10) in mm."""
+    return HsScoreParams(d_m, d_M, lam, lam_k)
+
+
+def pso_params(c1=2.8, c2=1.3, mutate_every=3, n_mutate=None, P=None) -> HsPsoParams:
+    """Section III.B constants; n_mutate defaults to half the swarm."""
+    if n_mutate is None:
+        n_mutate = (P or 0) // 2
+    return HsPsoParams(c1, c2, mutate_every, n_mutate)
+
+
+# ---- observation ----------------------------------------------------------------------
+
+@dataclass
+class Obs:
+    """Device observation: depth [H, pitch] (uint16 or float32, row pitch a multiple of
+    16 bytes), skin [H, pitch] uint8, ROI W x H, and a 2-word stats buffer."""
+    depth: torch.Tensor
+    skin: torch.Tensor
+    W: int
+    H: int
+    stats: torch.Tensor
+
+    def struct(self) -> HsObs:
+        dt = HS_DEPTH_F32 if self.depth.dtype == torch.float32 else HS_DEPTH_U16
+        return HsObs(_ptr(self.depth), _ptr(self.skin), self.W, self.H,
+                     self.depth.stride(0) * self.depth.element_size(), self.skin.stride(0), dt, _ptr(self.stats))
+
+    @classmethod
+    def from_numpy(cls, depth: np.ndarray, skin: np.ndarray, device="cuda") -> "Obs":
+        from .inputs import pitched
+        H, W = depth.shape
+        d = torch.from_numpy(pitched(depth)).to(device)
+        s = torch.from_numpy(pitched(skin.astype(np.uint8))).to(device)
+        return cls(d, s, W, H, torch.zeros(2, dtype=torch.int32, device=device))
+
+
+def hs_obs_prepare(obs: Obs, stream=None) -> None:
+    st = obs.struct()
+    _check("hs_obs_prepare", lib().hs_obs_prepare(ctypes.byref(st), _stream(stream)))
+
+
+def workspace_size(P: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check("hs_workspace_size", lib().hs_workspace_size(P, ctypes.byref(n)))
+    return n.value
+
+
+def new_workspace(P: int, device="cuda") -> torch.Tensor:
+    """A zeroed workspace tensor (uint8) for render_score_batch."""
+    return torch.zeros(max(workspace_size(P), 16), dtype=torch.uint8, device=device)
+
+
+def hs_workspace_reset(ws: torch.Tensor, stream=None) -> None:
+    _check("hs_workspace_reset", lib().hs_workspace_reset(_ptr(ws), ws.numel(), _stream(stream)))
+
+
+# ---- the hot path ------------------------------------------------------------------------
+
+def pose_fk(model: Model, poses: torch.Tensor, cam: HsCamera, prims: torch.Tensor, kc: torch.Tensor,
+            stream=None) -> None:
+    """poses [P, 26] f32 -> prims [P, n_prims, 16] f32 records, kc [P]."""
+    P = poses.shape[0]
+    _check("pose_fk", lib().pose_fk(model.handle, _ptr(poses), P, ctypes.byref(cam), _ptr(prims), _ptr(kc),
+                                    _stream(stream)))
+
+
+def render_score_batch(model: Model, obs: Obs, cam: HsCamera, prims: torch.Tensor, kc: torch.Tensor,
+                       params: HsScoreParams, ws: torch.Tensor, E: torch.Tensor, parts: torch.Tensor | None = None,
+                       dbg_depth: torch.Tensor | None = None, dbg_mask: torch.Tensor | None = None,
+                       stream=None) -> None:
+    """Fused render + Eq. 4-5: E [P]; parts [P, 4] int32 view of HsParts (optional);
+    dbg_depth [P, H, W] f32 and dbg_mask [P, H, W] uint8 (optional)."""
+    P = kc.shape[0]
+    st = obs.struct()
+    _check("render_score_batch",
+           lib().render_score_batch(model.handle, ctypes.byref(st), ctypes.byref(cam), _ptr(prims), _ptr(kc), P,
+                                    ctypes.byref(params), _ptr(ws), ws.numel(), _ptr(E), _ptr(parts),
+                                    _ptr(dbg_depth), _ptr(dbg_mask), _stream(stream)))
+
+
+@dataclass
+class Swarm:
+    """Device swarm state (float32): x, v, pbest [P, 26]; pbest_E [P]; gbest [26];
+    gbest_E [1]; E [P]."""
+    x: torch.Tensor
+    v: torch.Tensor
+    pbest: torch.Tensor
+    pbest_E: torch.Tensor
+    gbest: torch.Tensor
+    gbest_E: torch.Tensor
+    E: torch.Tensor
+
+    @classmethod
+    def empty(cls, P: int, device="cuda") -> "Swarm":
+        f = dict(dtype=torch.float32, device=device)
+        return cls(torch.zeros(P, NDOF, **f), torch.zeros(P, NDOF, **f), torch.zeros(P, NDOF, **f),
+                   torch.zeros(P, **f), torch.zeros(NDOF, **f), torch.zeros(1, **f), torch.zeros(P, **f))
+
+    @property
+    def P(self) -> int:
+        return self.x.shape[0]
+
+    def struct(self) -> HsSwarm:
+        return HsSwarm(*(_ptr(t) for t in (self.x, self.v, self.pbest, self.pbest_E, self.gbest, self.gbest_E,
+                                           self.E)))
+
+
+def pso_init(model: Model, sw: Swarm, seed_pose: torch.Tensor, scale, seed: int, frame: int, stream=None) -> None:
+    st = sw.struct()
+    sc = (ctypes.c_float * NDOF)(*[float(v) for v in scale])
+    _check("pso_init", lib().pso_init(model.handle, ctypes.byref(st), sw.P, _ptr(seed_pose), sc,
+                                      ctypes.c_uint64(seed), frame, _stream(stream)))
+
+
+def pso_step(model: Model, sw: Swarm, params: HsPsoParams, seed: int, frame: int, gen: int, stream=None) -> None:
+    st = sw.struct()
+    _check("pso_step", lib().pso_step(model.handle, ctypes.byref(st), sw.P, ctypes.byref(params),
+                                      ctypes.c_uint64(seed), frame, gen, _stream(stream)))
+
+
+def hs_get_device_status(clear: bool = False) -> int:
+    v = ctypes.c_uint32(0)
+    _check("hs_get_device_status", lib().hs_get_device_status(ctypes.byref(v), int(clear)))
+    return v.value
+
+
+def version() -> int:
+    return lib().hs_version()

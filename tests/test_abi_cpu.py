@@ -1,0 +1,192 @@
+"""The C-ABI boundary on CPU: the library loads, exports every function that
+include/handscore.h declares, its structs have the C layout, and invalid calls
+are rejected on the host before anything reaches a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2005_07068_b300 import build as B
+from paper_2005_07068_b300 import handscore as hs
+from paper_2005_07068_b300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "handscore.h")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)))
+
+
+def test_exports_every_declared_symbol():
+    names = declared_functions()
+    assert {"pose_fk", "render_score_batch", "pso_step", "pso_init", "hs_obs_prepare"} <= set(names)
+    out = subprocess.run(["nm", "-D", "--defined-only", hs.LIB_PATH], capture_output=True, text=True, check=True)
+    exported = {ln.split()[-1] for ln in out.stdout.splitlines() if " T " in ln}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    L = hs.lib()
+    for n in names:
+        assert getattr(L, n) is not None
+
+
+def test_struct_layout_matches_c(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "handscore.h"
+#define S(t) printf(#t " %zu\\n", sizeof(t));
+#define O(t, f) printf(#t "." #f " %zu\\n", offsetof(t, f));
+int main(void) {
+  S(HsBoneDesc) S(HsPrimDesc) S(HsModelDesc) S(HsCamera) S(HsObs) S(HsScoreParams) S(HsParts)
+  S(HsPrim) S(HsSwarm) S(HsPsoParams)
+  O(HsModelDesc, bones) O(HsModelDesc, lo) O(HsModelDesc, hi) O(HsObs, stats) O(HsObs, depth_type)
+  O(HsBoneDesc, rest) O(HsPrimDesc, dims) O(HsSwarm, E)
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
+    got = dict(ln.rsplit(" ", 1) for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                          check=True).stdout.splitlines())
+    py = {
+        "HsBoneDesc": ctypes.sizeof(hs.HsBoneDesc), "HsPrimDesc": ctypes.sizeof(hs.HsPrimDesc),
+        "HsModelDesc": ctypes.sizeof(hs.HsModelDesc), "HsCamera": ctypes.sizeof(hs.HsCamera),
+        "HsObs": ctypes.sizeof(hs.HsObs), "HsScoreParams": ctypes.sizeof(hs.HsScoreParams),
+        "HsParts": 16, "HsPrim": 64, "HsSwarm": ctypes.sizeof(hs.HsSwarm),
+        "HsPsoParams": ctypes.sizeof(hs.HsPsoParams),
+        "HsModelDesc.bones": hs.HsModelDesc.bones.offset, "HsModelDesc.lo": hs.HsModelDesc.lo.offset,
+        "HsModelDesc.hi": hs.HsModelDesc.hi.offset, "HsObs.stats": hs.HsObs.stats.offset,
+        "HsObs.depth_type": hs.HsObs.depth_type.offset, "HsBoneDesc.rest": hs.HsBoneDesc.rest.offset,
+        "HsPrimDesc.dims": hs.HsPrimDesc.dims.offset, "HsSwarm.E": hs.HsSwarm.E.offset,
+    }
+    for k, v in py.items():
+        assert int(got[k]) == v, k
+
+
+def _model():
+    g = I.hand_geometry()
+    lo, hi = I.search_limits()
+    return hs.Model.from_geometry(g, lo, hi)
+
+
+def test_model_validation():
+    m = _model()
+    assert m.handle
+    g = I.hand_geometry()
+    lo, hi = I.search_limits()
+    bad_parent = g.bones_i.copy()
+    bad_parent[5, 0] = 7
+    with pytest.raises(hs.HandscoreError) as e:
+        hs.Model(bad_parent, g.bones_f, g.prims_i, g.prims_f, lo, hi)
+    assert e.value.status == hs.HS_ERR_ARG
+    bad_kappa = g.prims_f.copy()
+    bad_kappa[0, 6] = 1.0
+    with pytest.raises(hs.HandscoreError):
+        hs.Model(g.bones_i, g.bones_f, g.prims_i, bad_kappa, lo, hi)
+    bad_dim = g.prims_f.copy()
+    bad_dim[3, 3] = 0.0
+    with pytest.raises(hs.HandscoreError):
+        hs.Model(g.bones_i, g.bones_f, g.prims_i, bad_dim, lo, hi)
+    with pytest.raises(hs.HandscoreError):
+        hs.Model(g.bones_i, g.bones_f, g.prims_i, g.prims_f, hi, lo)  # lo > hi
+    L = hs.lib()
+    assert L.hs_model_create(None, None) == hs.HS_ERR_ARG
+
+
+def test_workspace_size():
+    n = hs.workspace_size(64)
+    assert n >= 64 * 16
+    with pytest.raises(hs.HandscoreError):
+        hs.workspace_size(-1)
+    with pytest.raises(hs.HandscoreError):
+        hs.workspace_size(1 << 20)
+    assert hs.lib().hs_workspace_size(4, None) == hs.HS_ERR_ARG
+
+
+FAKE = 0x10000  # a 16-byte aligned address that validation never dereferences
+
+
+def _obs(**kw):
+    o = hs.HsObs(FAKE, FAKE, 320, 240, 640, 320, hs.HS_DEPTH_U16, FAKE)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(depth_pitch=600), hs.HS_ERR_ALIGN),       # not a multiple of 16
+    (dict(depth_pitch=320), hs.HS_ERR_SIZE),        # shorter than a row
+    (dict(skin=FAKE + 4), hs.HS_ERR_ALIGN),         # misaligned base
+    (dict(W=0), hs.HS_ERR_SIZE),
+    (dict(H=9000), hs.HS_ERR_SIZE),
+    (dict(depth_type=7), hs.HS_ERR_ARG),
+    (dict(stats=None), hs.HS_ERR_ARG),
+])
+def test_render_score_rejects_bad_observation(kw, code):
+    m = _model()
+    L = hs.lib()
+    cam = hs.camera(262.5, 262.5, 160, 120)
+    prm = hs.score_params()
+    o = _obs(**kw)
+    rc = L.render_score_batch(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 64, ctypes.byref(prm),
+                              FAKE, 1 << 20, FAKE, None, None, None, None)
+    assert rc == code
+    assert L.hs_obs_prepare(ctypes.byref(o), None) == code
+
+
+def test_other_host_checks():
+    m = _model()
+    L = hs.lib()
+    cam = hs.camera(262.5, 262.5, 160, 120)
+    prm = hs.score_params()
+    o = _obs()
+    # workspace too small
+    assert L.render_score_batch(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 64, ctypes.byref(prm),
+                                FAKE, 16, FAKE, None, None, None, None) == hs.HS_ERR_SIZE
+    # only one of the two debug outputs
+    assert L.render_score_batch(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 64, ctypes.byref(prm),
+                                FAKE, 1 << 20, FAKE, None, FAKE, None, None) == hs.HS_ERR_ARG
+    bad_cam = hs.camera(0.0, 262.5, 160, 120)
+    assert L.pose_fk(m.handle, FAKE, 4, ctypes.byref(bad_cam), FAKE, FAKE, None) == hs.HS_ERR_ARG
+    assert L.pose_fk(m.handle, FAKE, 4, ctypes.byref(cam), FAKE + 8, FAKE, None) == hs.HS_ERR_ALIGN
+    assert L.pose_fk(m.handle, FAKE, -1, ctypes.byref(cam), FAKE, FAKE, None) == hs.HS_ERR_SIZE
+    assert L.pose_fk(m.handle, FAKE, 0, ctypes.byref(cam), FAKE, FAKE, None) == hs.HS_OK  # P = 0: no-op
+    sw = hs.HsSwarm(FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
+    pp = hs.pso_params(P=64)
+    assert L.pso_step(m.handle, ctypes.byref(sw), 5000, ctypes.byref(pp), 1, 0, 1, None) == hs.HS_ERR_SIZE
+    low = hs.pso_params(c1=1.0, c2=1.0, P=64)  # psi <= 4: constriction undefined
+    assert L.pso_step(m.handle, ctypes.byref(sw), 64, ctypes.byref(low), 1, 0, 1, None) == hs.HS_ERR_ARG
+    sw.E = None
+    assert L.pso_step(m.handle, ctypes.byref(sw), 64, ctypes.byref(pp), 1, 0, 1, None) == hs.HS_ERR_ARG
+    scale = (ctypes.c_float * 26)(*([1.0] * 25 + [-1.0]))
+    sw.E = FAKE
+    assert L.pso_init(m.handle, ctypes.byref(sw), 64, FAKE, scale, 1, 0, None) == hs.HS_ERR_ARG
+    assert L.hs_get_device_status(None, 0) == hs.HS_ERR_ARG
+    assert hs.lib().hs_status_string(-3) == b"size out of range"
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU behaviour")
+def test_valid_call_without_gpu_reports_cuda_error():
+    m = _model()
+    cam = hs.camera(262.5, 262.5, 160, 120)
+    rc = hs.lib().pose_fk(m.handle, FAKE, 4, ctypes.byref(cam), FAKE, FAKE, None)
+    assert rc == hs.HS_ERR_CUDA
+
+
+def test_python_binding_requires_device_tensors():
+    with pytest.raises(ValueError):
+        hs._ptr(torch.zeros(4))
+    assert np.float32(hs.score_params().d_M) == 40.0

@@ -1,0 +1,468 @@
+#!/usr/bin/env python
+"""Hypothesis-scoring throughput of the hand tracker at Kinect scale.
+
+Workload (the Kinect-scale configuration): a 30-frame seeded trajectory of
+320x240 uint16 depth frames with a 600 mm background plane, N(0, 3 mm) noise,
+5% holes and 2% flipped skin pixels; per frame a 64-particle swarm runs 40
+generations of pose_fk -> render_score_batch -> pso_step, tracking from the
+previous frame's global best.  One step = one frame (one CUDA graph).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Prints one JSON line.  `value` is evals/s with the frames resident in HBM;
+`e2e` adds the host->device copy of each frame and the read-back of the
+result.  Under torchrun (N > 1) every rank tracks its own sequence (replicas;
+the swarm needs no exchange), timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W, H = 320, 240
+PARTICLES, GENS, FRAMES = 64, 40, 30
+METRIC = "hypothesis evals/s (render+cost, 320x240 ROI)"
+WORKLOAD = ("Kinect-scale tracking: 320x240 uint16 depth + uint8 skin frames (600 mm plane, N(0,3 mm) noise, "
+            "5% holes, 2% skin flips), 64 particles x 40 generations per frame, 30-frame seeded trajectory")
+FP32_LANES_PER_SM = 128
+# FP32 operations per ray-primitive test on the miss path, tallied from
+# render_score.cu (an FMA counts 2): ray point and direction in scaled local
+# coordinates (25), quadric coefficients and discriminant (ellipsoid 20,
+# cone 24 + cap planes 28 + 1 compare)
+FLOP_PER_TEST = {0: 45, 1: 78}
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample")
+    ap.add_argument("--profile", action="store_true", help="short run for an ncu launch list")
+    return ap.parse_args()
+
+
+# ---- host-side helpers ---------------------------------------------------------------
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def profile_traffic(kernel_src: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken on
+    the current source of the kernel; else None."""
+    path = os.path.join(ROOT, "profiles", "render_score_batch_kinect_320x240.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+        if kv.get("source_sha256") != sha:
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+class _Nvml:
+    """Read-only NVML queries through ctypes (the driver's libnvidia-ml)."""
+    CLOCK_SM = 1
+
+    def __init__(self, index: int):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        self._reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def clock(self, max_clock=False) -> float:
+        v = self.c.c_uint()
+        fn = self.lib.nvmlDeviceGetMaxClockInfo if max_clock else self.lib.nvmlDeviceGetClockInfo
+        if fn(self.h, self.CLOCK_SM, self.c.byref(v)) != 0:
+            raise RuntimeError("clock query failed")
+        return float(v.value)
+
+    def reasons(self) -> int:
+        v = self.c.c_ulonglong()
+        if self._reasons(self.h, self.c.byref(v)) != 0:
+            raise RuntimeError("reason query failed")
+        return int(v.value)
+
+
+class ClockSampler:
+    """SM clock and throttle reasons sampled every 10 ms through NVML
+    (read-only), so that even a short timed region gets samples."""
+    HW, HW_THERMAL, SW_THERMAL, SW_POWER = 0x8, 0x40, 0x20, 0x4
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = None
+        self.error = None
+
+    def __enter__(self):
+        import threading
+        try:
+            self._nv = _Nvml(self.index)
+            self.max_mhz = self._nv.clock(max_clock=True)
+        except Exception as ex:  # no NVML: report why, keep going
+            self._nv = None
+            self.error = repr(ex)[:200]
+            return self
+        self._stop = threading.Event()
+
+        def run():
+            while not self._stop.is_set():
+                try:
+                    self.samples.append((self._nv.clock(), self._nv.reasons()))
+                except Exception:
+                    pass
+                self._stop.wait(0.01)
+
+        self._t = threading.Thread(target=run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        if self._stop is not None:
+            self._stop.set()
+            self._t.join(timeout=2)
+
+    def summary(self, sm_max_default):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": sm_max_default, "reasons": [], "samples": 0,
+                    "error": self.error or "no samples"}
+        names = {self.HW: "hw_slowdown", self.HW_THERMAL: "hw_thermal_slowdown",
+                 self.SW_THERMAL: "sw_thermal_slowdown", self.SW_POWER: "sw_power_cap"}
+        reasons = sorted({n for _, r in self.samples for bit, n in names.items() if r & bit})
+        return {"sm_mhz": statistics.median(sm for sm, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.samples), "source": "NVML every 10 ms"}
+
+
+# ---- synthetic frames ----------------------------------------------------------------------
+
+def make_frames(seed: int, frames: int, hs, I, model, cam, device):
+    """Render the ground-truth trajectory with the CUDA renderer (P = 1 debug
+    output), corrupt it like a Kinect frame, return device observations."""
+    import torch
+    traj = I.trajectory(seed, frames).astype(np.float32)
+    dummy = hs.Obs.from_numpy(np.zeros((H, W), np.uint16), np.zeros((H, W), np.uint8), device)
+    hs.hs_obs_prepare(dummy)
+    prims = torch.zeros(1, model.n_prims, 16, device=device)
+    kc = torch.zeros(1, device=device)
+    ws = hs.new_workspace(1, device)
+    E = torch.zeros(1, device=device)
+    dd = torch.zeros(1, H, W, device=device)
+    dm = torch.zeros(1, H, W, dtype=torch.uint8, device=device)
+    obs, host = [], []
+    for f in range(frames):
+        hs.pose_fk(model, torch.from_numpy(traj[f:f + 1]).to(device), cam, prims, kc)
+        hs.render_score_batch(model, dummy, cam, prims, kc, hs.score_params(), ws, E, None, dd, dm)
+        depth = dd[0].cpu().numpy().astype(np.float64)
+        hit = (dm[0].cpu().numpy() & 1) > 0
+        d16, skin = I.kinect_observation(depth, hit, seed * 100 + f)
+        obs.append(hs.Obs.from_numpy(d16, skin, device))
+        host.append((d16, skin))
+    return traj, obs, host
+
+
+def algorithmic_flops(box_words: np.ndarray, kinds: np.ndarray) -> float:
+    """FP32 work of one render_score_batch launch: for every particle and
+    primitive, the pixels of its conservative box inside the ROI (pixel-exact
+    box culling) times the per-test tally of its kind.  box_words: the last two
+    words of every HsPrim record, [P, n_prims, 2] float32 holding int16 boxes."""
+    box = np.ascontiguousarray(box_words).view(np.int16).reshape(box_words.shape[0], box_words.shape[1], 4)
+    u0 = np.clip(box[..., 0], 0, W - 1)
+    v0 = np.clip(box[..., 1], 0, H - 1)
+    u1 = np.clip(box[..., 2], 0, W - 1)
+    v1 = np.clip(box[..., 3], 0, H - 1)
+    inside = (box[..., 2] >= 0) & (box[..., 3] >= 0) & (box[..., 0] < W) & (box[..., 1] < H)
+    area = np.where(inside, (u1 - u0 + 1) * (v1 - v0 + 1), 0).astype(np.float64)
+    per_kind = np.array([FLOP_PER_TEST[int(k)] for k in kinds], np.float64)
+    return float((area * per_kind[None, :]).sum())
+
+
+# ---- the CPU oracle (baseline leg and reference arm) ----------------------------------------
+
+def oracle_frame(seed: int):
+    """Frame 0 of the same workload, rendered and corrupted on the CPU by the oracle."""
+    import oracle
+    from paper_2005_07068_b300 import inputs as I
+    g = I.hand_geometry()
+    lo, hi = (a.astype(np.float32).astype(np.float64) for a in I.search_limits())
+    model = oracle.Model.from_geometry(g, lo, hi)
+    cam = oracle.camera_tuple(I.kinect_camera(W, H))
+    traj = I.trajectory(seed, 1)
+    depth, hit, _, _ = oracle.render_pose(model, traj[0], cam, W, H, boundary=False)
+    d16, skin = I.kinect_observation(depth, hit, seed * 100)
+    return oracle, I, model, cam, traj[0], d16.astype(np.float64), skin
+
+
+def time_oracle(seed: int, seconds: float, max_gens: int = GENS):
+    """Oracle tracking on frame 0 for about `seconds`: (evals/s, generations, P, threads)."""
+    oracle, I, model, cam, start, Od, S = oracle_frame(seed)
+    sw = oracle.pso_init(PARTICLES, start, I.perturbation_scale(), model.lo, model.hi, seed, 0)
+    t0 = time.perf_counter()
+    gens = 0
+    while gens < max_gens and (gens < 2 or time.perf_counter() - t0 < seconds):
+        r = oracle.score_batch(model, sw.x, cam, Od, S)
+        sw = oracle.pso_step(sw, r["E"], model.lo, model.hi, seed, 0, gens + 1)
+        gens += 1
+    dt = time.perf_counter() - t0
+    return PARTICLES * gens / dt, gens, oracle.threads_used()
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    seed = 2005070682
+    oracle, I, model, cam, start, Od, S = oracle_frame(seed)
+    sw = oracle.pso_init(PARTICLES, start, I.perturbation_scale(), model.lo, model.hi, seed, 0)
+    g = 0
+    for _ in range(args.warmup):
+        r = oracle.score_batch(model, sw.x, cam, Od, S)
+        g += 1
+        sw = oracle.pso_step(sw, r["E"], model.lo, model.hi, seed, 0, g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle.score_batch(model, sw.x, cam, Od, S)
+        g += 1
+        sw = oracle.pso_step(sw, r["E"], model.lo, model.hi, seed, 0, g)
+    dt = time.perf_counter() - t0
+    v = PARTICLES * args.steps / dt
+    cores = oracle.threads_used()
+    sample = (f"one step = one PSO generation of {PARTICLES} particles on a 320x240 frame (FP64 oracle: FK, "
+              f"brute-force ray cast of every pixel x 37 primitives, Eq. 4-5, Eq. 6-7), OpenMP over particles")
+    line = {"metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "roi": [W, H], "particles": PARTICLES, "generations": GENS,
+                       "frames": FRAMES, "parallelism": "replicas"},
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- the native arm ------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    from paper_2005_07068_b300 import build as B
+    from paper_2005_07068_b300 import handscore as hs
+    from paper_2005_07068_b300 import inputs as I
+    from paper_2005_07068_b300.tracker import Tracker
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    peaks = measured_peaks()
+    seed = I.CONFIG_SEED_BASE + 2 + 1000 * rank
+    g = I.hand_geometry()
+    lo, hi = (a.astype(np.float32) for a in I.search_limits())
+    model = hs.Model.from_geometry(g, lo, hi)
+    camt = I.kinect_camera(W, H)
+    cam = hs.camera(camt.fx, camt.fy, camt.cx, camt.cy)
+    frames = min(FRAMES, max(args.steps + args.warmup, 2)) if args.profile else FRAMES
+    traj, obs, host = make_frames(seed, frames, hs, I, model, cam, dev)
+    gt0 = torch.from_numpy(traj[0]).to(dev)
+    trk = Tracker(model, cam, PARTICLES, GENS, seed=seed, device=dev)
+    graphs = [trk.graph(obs[f], f, gt0 if f == 0 else None) for f in range(frames)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        graphs[i % frames].replay()
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        w0 = time.perf_counter()
+        for i in range(K):
+            flush.zero_()  # evict the previous frame from the 126 MB L2 (outside the step events)
+            evs[i][0].record(stream)
+            step(args.warmup + i)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        wall = time.perf_counter() - w0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_dev = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([t_dev], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t[0])
+    evals_total = K * PARTICLES * GENS * world
+    value = evals_total / t_dev
+
+    # ---- roofline of render_score_batch: CUDA events around every launch ----
+    # An eager replay of the same frames, gated behind a GPU sleep so that the
+    # host has enqueued the whole frame before the GPU starts: the events then
+    # bracket kernel time, not host-side launch gaps.
+    kinds = g.prims_i[:, 1]
+    dur = {"fk": [], "render": [], "pso": []}
+    flops = []
+    for f in range(min(3, frames)):
+        trk.seed_pose.copy_(gt0 if f == 0 else trk.swarm.gbest)
+        hs.hs_obs_prepare(obs[f])
+        hs.pso_init(model, trk.swarm, trk.seed_pose, trk.scale, seed, f)
+        torch.cuda.synchronize(dev)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(GENS)]
+        boxes = []
+        torch.cuda._sleep(40_000_000)  # ~20 ms of GPU time while the host enqueues the frame
+        for gen in range(1, GENS + 1):
+            e = ev[gen - 1]
+            e[0].record(stream)
+            hs.pose_fk(model, trk.swarm.x, cam, trk.prims, trk.kc)
+            e[1].record(stream)
+            hs.render_score_batch(model, obs[f], cam, trk.prims, trk.kc, trk.score, trk.ws, trk.swarm.E)
+            e[2].record(stream)
+            boxes.append(trk.prims[:, :, 14:16].clone())
+            e[3].record(stream)
+            hs.pso_step(model, trk.swarm, trk.pso, seed, f, gen)
+        torch.cuda.synchronize(dev)
+        for gen in range(GENS):
+            e = ev[gen]
+            dur["fk"].append(e[0].elapsed_time(e[1]) / 1e3)
+            dur["render"].append(e[1].elapsed_time(e[2]) / 1e3)
+            flops.append(algorithmic_flops(boxes[gen].cpu().numpy(), kinds))
+        pso_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(GENS)]
+        torch.cuda._sleep(40_000_000)
+        for gen in range(1, GENS + 1):
+            pso_ev[gen - 1][0].record(stream)
+            hs.pso_step(model, trk.swarm, trk.pso, seed, f, GENS + gen)
+            pso_ev[gen - 1][1].record(stream)
+        torch.cuda.synchronize(dev)
+        dur["pso"] += [a.elapsed_time(b) / 1e3 for a, b in pso_ev]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2032.0))
+    sm_max = float(peaks.get("sm_max_mhz") or clocks["sm_max_mhz"] or 2032.0)
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = sum(flops) / sum(dur["render"]) / 1e12
+    traffic = profile_traffic(os.path.join(ROOT, "paper_2005_07068_b300", "csrc", "render_score.cu"))
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic, "kernel": "render_score_kernel",
+                "peak_basis": f"FP32: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {sm_max:.0f} MHz "
+                              f"(sm_max_mhz of measured)",
+                "launch_us": 1e6 * sum(dur["render"]) / len(dur["render"]),
+                "flop_per_launch": sum(flops) / len(flops),
+                "kernel_us": {k: 1e6 * statistics.median(v) for k, v in dur.items()}}
+
+    # ---- end to end: pinned host frame -> device -> graph -> result on the host ----
+    e2e = None
+    if not args.no_e2e:
+        staging = hs.Obs.from_numpy(host[0][0], host[0][1], dev)
+        pin = []
+        for d16, skin in host:
+            from paper_2005_07068_b300.inputs import pitched
+            pin.append((torch.from_numpy(pitched(d16)).pin_memory(), torch.from_numpy(pitched(skin)).pin_memory()))
+        out = torch.zeros(27, dtype=torch.float32).pin_memory()
+        for f in range(frames):  # capture the staging graphs before timing
+            trk.graph(staging, f, gt0 if f == 0 else None)
+        for i in range(args.warmup):
+            f = i % frames
+            trk.track(pin[f][0], pin[f][1], staging, f, out, gt0 if f == 0 else None)
+        torch.cuda.synchronize(dev)
+        ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if dist:
+            dist.barrier()
+        for i in range(K):
+            f = (args.warmup + i) % frames
+            flush.zero_()
+            ee[i][0].record(stream)
+            trk.track(pin[f][0], pin[f][1], staging, f, out, gt0 if f == 0 else None)
+            ee[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        t_e2e = sum(a.elapsed_time(b) for a, b in ee) / 1e3
+        if dist:
+            t = torch.tensor([t_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t[0])
+        e2e = {"value": evals_total / t_e2e, "unit": "evals/s",
+               "h2d_bytes_per_step": int(pin[0][0].numel() * pin[0][0].element_size() + pin[0][1].numel()),
+               "d2h_bytes_per_step": int(out.numel() * out.element_size())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, gens, cores = time_oracle(seed, args.cpu_seconds)
+        cpu = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
+               "sample": f"frame 0 of the same workload (oracle-rendered), {PARTICLES} particles x {gens} "
+                         f"generations of FP64 FK + brute-force ray cast (all pixels x 37 primitives) + "
+                         f"Eq. 4-5 + Eq. 6-7, OpenMP over particles"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "roi": [W, H], "particles": PARTICLES, "generations": GENS,
+                           "frames": frames, "step": "one frame = one CUDA graph (2 + 3 x 40 kernels)",
+                           "l2": "flushed between steps (256 MiB write outside the step events)",
+                           "parallelism": f"replicas x{world}", "wall_s": wall},
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
+                "gpu_launches": K * trk.launches_per_frame()}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -137,7 +137,9 @@ typedef struct {
  *            maps to h = a c0 + b c1 + c2 in scaled local coordinates
  *   m[9..11] C, the primitive centre in camera coordinates (mm); the renderer
  *            takes the ray point at depth t0 = C_z: g = M (t0 d - C)
- *   m[12]    reserved (0)
+ *   m[12]    bit mask (as uint32) of the cone caps to render (bit 0 at -hl,
+ *            bit 1 at +hl); caps that the model hides inside a joint sphere or
+ *            ellipsoid are left out, which does not change any depth
  *   m[13]    kappa for HS_PRIM_ECONE; 2.0 marks an ellipsoid
  *   m[14]    (int16 u0, int16 v0), m[15] (int16 u1, int16 v1): conservative
  *            inclusive pixel box of the primitive's projection              */
@@ -181,9 +183,11 @@ const char* hs_status_string(int status);
 int hs_model_create(const HsModelDesc* desc, HsModel** out);
 int hs_model_destroy(HsModel* model);
 
-/* Bytes of workspace render_score_batch needs for P particles (per-particle
- * counters and per-CTA partial sums).  The workspace must be zeroed once
- * (hs_workspace_reset) before first use; calls leave it zeroed again.
+/* Bytes of workspace render_score_batch needs for P particles (32 bytes per
+ * particle: a work-queue ticket, an exit count and fixed-point sums).  The
+ * workspace must be zeroed once (hs_workspace_reset) before first use; every
+ * call leaves it zeroed again.  Calls sharing one workspace must not overlap
+ * on the GPU.
  * Errors: HS_ERR_ARG (bytes NULL), HS_ERR_SIZE (P out of range). */
 int hs_workspace_size(int P, size_t* bytes);
 int hs_workspace_reset(void* workspace, size_t bytes, hs_stream_t stream);

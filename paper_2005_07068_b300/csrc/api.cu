@@ -54,7 +54,7 @@ static int encode_tile_map(CUtensorMap* map, const void* base, CUtensorMapDataTy
     (void)esz;
     const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
     const cuuint64_t strides[1] = {(cuuint64_t)pitch};
-    const cuuint32_t box[2] = {16, 16};
+    const cuuint32_t box[2] = {16, 4};  // one TMA box = one 16 x 4 work unit
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = g_encode(map, type, 2, const_cast<void*>(base), dims, strides, box, estr,
                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -85,10 +85,8 @@ static int validate_cam(const HsCamera* c)
     return HS_OK;
 }
 
-constexpr int kMaxK = 64;           // CTAs per particle in render_score_batch
-constexpr int kTargetCtas = 148 * 8;
-
-static size_t counters_bytes(int P) { return ((size_t)P * 4 + 255) / 256 * 256; }
+constexpr int kMaxK = 64;              // single-warp CTAs per particle in render_score_batch
+constexpr int kTargetCtas = 148 * 24;  // one resident wave (24 single-warp CTAs per SM)
 
 }  // namespace hs
 
@@ -172,10 +170,47 @@ int hs_model_create(const HsModelDesc* d, HsModel** out)
         for (int i = 0; i < 4; ++i) o.dims[i] = P.dims[i];
         if (!finite_pos(P.dims[0]) || !finite_pos(P.dims[1]) || !finite_pos(P.dims[2])) bad = 1;
         if (P.kind == HS_PRIM_ECONE && !(std::fabs(P.dims[3]) < 1.f)) bad = 1;
+        // local scale (x, y, z): ellipsoid semi-axes; cone (ax, hl, az)
+        const float sc[3] = {P.dims[0], P.kind == HS_PRIM_ECONE ? P.dims[2] : P.dims[1],
+                             P.kind == HS_PRIM_ECONE ? P.dims[1] : P.dims[2]};
+        for (int i = 0; i < 3; ++i) o.inv_s[i] = 1.f / sc[i];
+        o.caps = 3;
     }
     if (bad) {
         std::free(m);
         return HS_ERR_ARG;
+    }
+    // A cone's planar cap is never the nearest surface when an ellipsoid that is
+    // rigidly attached at the cap centre contains the cap disc: every ray through
+    // the disc enters that ellipsoid first (or at the disc rim, at equal depth).
+    // Such caps are skipped by the renderer; the rendered depth is unchanged.
+    for (int k = 0; k < d->n_prims; ++k) {
+        DevPrimDesc& c = dm.prims[k];
+        if (c.kind != HS_PRIM_ECONE) continue;
+        for (int side = 0; side < 2; ++side) {
+            const float sgn = side ? 1.f : -1.f;
+            const float w = 1.f + sgn * c.dims[3];
+            const float rx = c.dims[0] * w, rz = c.dims[1] * w;
+            const float cc[3] = {c.center[0], c.center[1] + sgn * c.dims[2], c.center[2]};
+            bool covered = false;
+            for (int e = 0; e < d->n_prims && !covered; ++e) {
+                const DevPrimDesc& q = dm.prims[e];
+                if (q.kind != HS_PRIM_ELLIPSOID) continue;
+                const float tol = 1e-5f;  // relative slack on the radii only
+                const bool big = q.dims[0] >= rx * (1.f - tol) && q.dims[2] >= rz * (1.f - tol);
+                if (q.bone == c.bone && q.center[0] == cc[0] && q.center[1] == cc[1] && q.center[2] == cc[2] && big)
+                    covered = true;
+                // a sphere at the origin of a child bone whose origin is the cap centre
+                const bool sphere = q.dims[0] == q.dims[1] && q.dims[1] == q.dims[2];
+                if (sphere && q.bone > 0 && dm.bones[q.bone].parent == c.bone && q.center[0] == 0.f &&
+                    q.center[1] == 0.f && q.center[2] == 0.f) {
+                    const float* off = dm.bones[q.bone].off;
+                    if (off[0] == cc[0] && off[1] == cc[1] && off[2] == cc[2] && q.dims[0] >= std::fmax(rx, rz) * (1.f - tol))
+                        covered = true;
+                }
+            }
+            if (covered) c.caps &= ~(1 << side);
+        }
     }
     *out = m;
     return HS_OK;
@@ -192,7 +227,7 @@ int hs_workspace_size(int P, size_t* bytes)
 {
     if (!bytes) return HS_ERR_ARG;
     if (P < 0 || P > HS_MAX_PARTICLES) return HS_ERR_SIZE;
-    *bytes = counters_bytes(P) + (size_t)P * kMaxK * sizeof(float4);
+    *bytes = ((size_t)P * sizeof(HsParticleWork) + 255) / 256 * 256;
     return HS_OK;
 }
 
@@ -271,10 +306,10 @@ int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* c
             cudaMemsetAsync(dbg_mask, 0, n, s) != cudaSuccess)
             return HS_ERR_CUDA;
     }
-    const int tiles = ((obs->W + 15) / 16) * ((obs->H + 15) / 16);
+    // single-warp CTAs per particle: about one resident wave in total (any K
+    // is correct; it only changes how the units are dealt)
     int K = (kTargetCtas + P - 1) / P;
     if (K > kMaxK) K = kMaxK;
-    if (K > tiles) K = tiles;
     if (K < 1) K = 1;
 
     RenderArgs a;
@@ -285,19 +320,18 @@ int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* c
     a.K = K;
     a.W = obs->W;
     a.H = obs->H;
-    a.fx = cam->fx;
-    a.fy = cam->fy;
-    a.cx = cam->cx;
-    a.cy = cam->cy;
+    // ray of pixel (u, v): ((u + 0.5 - cx) / fx, (v + 0.5 - cy) / fy, 1), as one FMA per axis
+    a.inv_fx = (float)(1.0 / (double)cam->fx);
+    a.inv_fy = (float)(1.0 / (double)cam->fy);
+    a.off_x = (float)((0.5 - (double)cam->cx) / (double)cam->fx);
+    a.off_y = (float)((0.5 - (double)cam->cy) / (double)cam->fy);
     a.d_m = params->d_m;
     a.d_M = params->d_M;
     a.lambda = params->lambda;
     a.lambda_k = params->lambda_k;
     a.depth_f32 = f32;
     a.stats = obs->stats;
-    uint8_t* ws = static_cast<uint8_t*>(workspace);
-    a.counters = reinterpret_cast<uint32_t*>(ws);
-    a.partials = reinterpret_cast<float4*>(ws + counters_bytes(P));
+    a.work = static_cast<HsParticleWork*>(workspace);
     a.E = E;
     a.parts = parts;
     a.dbg_depth = dbg_depth;

@@ -26,8 +26,16 @@ __device__ __forceinline__ int clamp_i16(float v)
     return (int)fminf(fmaxf(v, -32767.0f), 32767.0f);
 }
 
-__global__ void __launch_bounds__(64) fk_kernel(const __grid_constant__ DevModel model, const FkArgs a)
+__global__ void __launch_bounds__(64) fk_kernel(const __grid_constant__ DevModel model_param, const FkArgs a)
 {
+    // one coalesced copy of the model into shared memory; every later access
+    // (thread-dependent bone / primitive indices) then hits shared memory
+    __shared__ DevModel model;
+    {
+        const uint32_t* srcw = reinterpret_cast<const uint32_t*>(&model_param);
+        uint32_t* dstw = reinterpret_cast<uint32_t*>(&model);
+        for (int i = threadIdx.x; i < (int)(sizeof(DevModel) / 4); i += blockDim.x) dstw[i] = srcw[i];
+    }
     __shared__ float q[kNdof];
     __shared__ float lR[kMaxBones][9];
     __shared__ float bR[kMaxBones][9];
@@ -106,16 +114,15 @@ __global__ void __launch_bounds__(64) fk_kernel(const __grid_constant__ DevModel
         for (int i = 0; i < 3; ++i)
             C[i] = q[i] + fmaf(R[3 * i], D.center[0], fmaf(R[3 * i + 1], D.center[1], fmaf(R[3 * i + 2], D.center[2], O[i])));
         const bool cone = D.kind == HS_PRIM_ECONE;
-        // scale S (local x, y, z) and box half extents e
-        float s[3], e[3];
+        // box half extents e (local x, y, z)
+        float e[3];
         if (cone) {
             const float grow = 1.f + fabsf(D.dims[3]);
-            s[0] = D.dims[0]; s[1] = D.dims[2]; s[2] = D.dims[1];
             e[0] = D.dims[0] * grow; e[1] = D.dims[2]; e[2] = D.dims[1] * grow;
         } else {
-            s[0] = e[0] = D.dims[0]; s[1] = e[1] = D.dims[1]; s[2] = e[2] = D.dims[2];
+            e[0] = D.dims[0]; e[1] = D.dims[1]; e[2] = D.dims[2];
         }
-        const float is0 = 1.f / s[0], is1 = 1.f / s[1], is2 = 1.f / s[2];
+        const float is0 = D.inv_s[0], is1 = D.inv_s[1], is2 = D.inv_s[2];
         // column j of M = S^-1 R^T is (R[j][0]/s0, R[j][1]/s1, R[j][2]/s2)
         float rec[16];
 #pragma unroll
@@ -129,7 +136,7 @@ __global__ void __launch_bounds__(64) fk_kernel(const __grid_constant__ DevModel
         rec[9] = C[0];
         rec[10] = C[1];
         rec[11] = C[2];
-        rec[12] = 0.f;
+        rec[12] = __uint_as_float(cone ? (uint32_t)D.caps : 0u);  // visible cone caps
         rec[13] = cone ? D.dims[3] : kEllipsoidMarker;
         // conservative pixel box from the 8 projected corners of the local box
         float amin = FLT_MAX, amax = -FLT_MAX, bmin = FLT_MAX, bmax = -FLT_MAX;
@@ -141,7 +148,7 @@ __global__ void __launch_bounds__(64) fk_kernel(const __grid_constant__ DevModel
             const float Y = fmaf(R[3], sx, fmaf(R[4], sy, fmaf(R[5], sz, C[1])));
             const float Z = fmaf(R[6], sx, fmaf(R[7], sy, fmaf(R[8], sz, C[2])));
             behind |= !(Z >= 1.0f);
-            const float iz = 1.f / Z;
+            const float iz = rcp_approx(Z);  // the box keeps a 1-pixel margin
             amin = fminf(amin, X * iz);
             amax = fmaxf(amax, X * iz);
             bmin = fminf(bmin, Y * iz);

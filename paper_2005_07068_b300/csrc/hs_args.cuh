@@ -17,17 +17,25 @@ struct FkArgs {
     uint32_t* status;
 };
 
+// per-particle scratch of render_score_batch (32 bytes, zero between calls)
+struct HsParticleWork {
+    uint32_t next;                // unit queue ticket
+    uint32_t exited;              // warps that have left the queue
+    unsigned long long t_fix;     // sum of depth-term differences, fixed point 2^-24 mm
+    uint32_t n_and, n_or, n_hit;  // sum(S and r_m), sum(r_m and not S), rendered pixels
+    uint32_t pad;
+};
+
 struct RenderArgs {
     const float4* prims;  // [P][n_prims][4]
     const float* kc;      // [P]
     int P, n_prims, K;
     int W, H;
-    float fx, fy, cx, cy;
+    float inv_fx, inv_fy, off_x, off_y;  // ray of pixel (u, v): (u inv_fx + off_x, v inv_fy + off_y, 1)
     float d_m, d_M, lambda, lambda_k;
     int depth_f32;
     const uint32_t* stats;  // [2]: #valid, #skin
-    float4* partials;       // [P][K]
-    uint32_t* counters;     // [P]
+    HsParticleWork* work;   // [P]
     float* E;
     HsParts* parts;
     float* dbg_depth;

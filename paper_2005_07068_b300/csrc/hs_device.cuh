@@ -26,6 +26,8 @@ struct DevPrimDesc {
     int32_t bone, kind;
     float center[3];
     float dims[4];
+    float inv_s[3];  // 1 / scale along local x, y, z
+    int32_t caps;    // cone caps to render: bit 0 at y = -hl, bit 1 at y = +hl
 };
 
 // everything the FK kernel needs about the model (about 4.7 KB)

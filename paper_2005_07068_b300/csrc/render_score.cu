@@ -6,23 +6,31 @@
 // paper renders 64 full images with OpenGL, replicates O 64 times and sums
 // with a pyramid (Section IV, steps 1-3).  Here nothing is rendered to memory:
 //
-//  * grid (K, P): CTA (k, p) walks tiles k, k+K, ... of particle p's
-//    screen-space box (union of its primitives' conservative boxes);
+//  * grid (K, P) of single-warp CTAs: the K warps of particle p split p's work
+//    units, 16x4-pixel blocks of its screen box (union of its primitives'
+//    conservative boxes, clipped to the ROI), dealt round-robin, so dense and
+//    sparse parts of the hand spread over all warps; a warp frees its SM slot
+//    as soon as it is done and nothing waits on a barrier;
 //  * the particle's 64-byte primitive records are staged in shared memory;
-//  * each 16x16 observation tile (depth + skin) arrives by a 2-D TMA load,
-//    double-buffered on two mbarriers (one shared copy of O, never replicated);
-//  * each warp owns an 8x4 pixel block and culls the primitives against it
-//    (warp-uniform bit mask), then every lane casts its pixel's ray against
-//    the surviving quadrics in scaled local coordinates (FP32, shifted to the
-//    primitive's depth t0 so the quadratic keeps its precision at ~500 mm);
-//  * the per-pixel terms are reduced with warp shuffles and a CTA sum;
-//  * the last CTA of a particle (atomic ticket) adds the K partials in a fixed
-//    order, so E is deterministic.
+//  * a unit's observation (16x4 depth + skin) arrives by a 2-D TMA load into
+//    one of the warp's two shared-memory stages, issued one unit ahead (one
+//    shared copy of O, never replicated);
+//  * the warp culls the primitives against each 8x4 half of the unit
+//    (warp-uniform masks) and skips the unit when nothing can render there;
+//    otherwise every lane casts two rays (one per half) against the
+//    quadrics in scaled local coordinates (FP32, taken at the primitive's
+//    centre depth t0 so the quadratic keeps its precision at ~500 mm);
+//  * per-lane sums are kept in 64-bit fixed point (2^-24 mm) and integer
+//    counts, so the totals do not depend on which warp took which unit: E is
+//    deterministic;
+//  * each warp flushes its sums with one set of atomics when the queue runs
+//    dry; the last warp of the particle (exit ticket) forms E and clears the
+//    particle's workspace for the next call.
 //
-// Pixels outside the particle's box render nothing, so their contribution is
-// the particle-independent baseline (t = d_M on valid skin, S in the union).
-// Each processed pixel therefore adds only its difference to that baseline,
-// and the per-frame totals (hs_obs_prepare) supply the rest.
+// Pixels where nothing renders keep the particle-independent baseline (t = d_M
+// on valid skin, S in the union).  Each rendered pixel therefore adds only its
+// difference to that baseline, and the per-frame totals (hs_obs_prepare)
+// supply the rest.
 #include <cuda.h>
 
 #include <cfloat>
@@ -32,18 +40,7 @@
 
 namespace hs {
 
-constexpr int kTW = 16, kTH = 16, kThreads = 256;
-
-struct __align__(128) RenderSmem {
-    unsigned char depth[2][kTW * kTH * 4];  // 2 stages, up to float32
-    unsigned char skin[2][kTW * kTH];
-    float4 prims[kMaxPrims * 4];
-    uint64_t bar[2];
-    float wsum_t[kThreads / 32];
-    uint32_t wsum_c[kThreads / 32];
-    int box[4];
-    int last;
-};
+constexpr float kFix = 16777216.0f;     // fixed-point scale of the depth sums (2^24 per mm)
 
 // ---- mbarrier / TMA (inline PTX) ---------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -96,7 +93,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // In scaled local coordinates the ray is g + s h with h = M d and
 // g = M (t0 d - C) = M (t0 a - C_x, t0 b - C_y, 0):
 //   ellipsoid:  |p|^2 = 1
-//   cone:       X^2 + Z^2 = (1 + kappa Y)^2, |Y| <= 1, caps at Y = -1, +1
+//   cone:       X^2 + Z^2 = (1 + kappa Y)^2, |Y| <= 1, and the caps at Y = -1, +1
+//               that the model leaves visible (record word 12)
 __device__ __forceinline__ float intersect(const float4& r0, const float4& r1, const float4& r2, const float4& r3,
                                           float a, float b)
 {
@@ -136,15 +134,18 @@ __device__ __forceinline__ float intersect(const float4& r0, const float4& r1, c
             if (fabsf(y1) <= 1.f && t0 + s1 > 0.f) best = fminf(best, s1);
             if (fabsf(y2) <= 1.f && t0 + s2 > 0.f) best = fminf(best, s2);
         }
-        // planar caps at Y = -1 (radius 1 - kappa) and Y = +1 (radius 1 + kappa)
-        const float ihy = rcp_approx(hy);
+        const uint32_t caps = __float_as_uint(r3.x);
+        if (caps) {  // planar caps at Y = -1 (radius 1 - kappa) and Y = +1 (radius 1 + kappa)
+            const float ihy = rcp_approx(hy);
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const float yc = c ? 1.f : -1.f;
-            const float s = (yc - gy) * ihy;
-            const float X = fmaf(s, hx, gx), Z = fmaf(s, hz, gz);
-            const float w = 1.f + yc * kap;
-            if (fmaf(X, X, Z * Z) <= w * w && t0 + s > 0.f) best = fminf(best, s);
+            for (int c = 0; c < 2; ++c) {
+                if (!(caps & (1u << c))) continue;
+                const float yc = c ? 1.f : -1.f;
+                const float s = (yc - gy) * ihy;
+                const float X = fmaf(s, hx, gx), Z = fmaf(s, hz, gz);
+                const float w = 1.f + yc * kap;
+                if (fmaf(X, X, Z * Z) <= w * w && t0 + s > 0.f) best = fminf(best, s);
+            }
         }
     }
     return best;
@@ -155,184 +156,218 @@ __device__ __forceinline__ bool box_overlaps(const float4& r3, int x0, int y0, i
     return lo_i16(r3.z) <= x1 && hi_i16(r3.z) <= y1 && lo_i16(r3.w) >= x0 && hi_i16(r3.w) >= y0;
 }
 
-__global__ void __launch_bounds__(kThreads, 4)
+// per-pixel terms of Eq. 4 (reading R1) as differences to the no-hit baseline,
+// added to the lane's fixed-point / integer sums; returns r_m
+__device__ __forceinline__ bool add_pixel(float od, bool S, float zt0, float zs, const RenderArgs& a, long long& at,
+                                          uint32_t& aa, uint32_t& ao, uint32_t& ah)
+{
+    const bool valid = S && od > 0.f;
+    const float diff = fabsf((od - zt0) - zs);  // O_d - z without rounding at the ~500 mm scale
+    const bool rm = !valid || diff < a.d_m;
+    const float t = valid ? fminf(diff, a.d_M) : (S ? 0.f : a.d_M);
+    at += __float2ll_rn((t - (valid ? a.d_M : 0.f)) * kFix);
+    aa += (S && rm);
+    ao += (rm && !S);
+    ah += 1;
+    return rm;
+}
+
+// a work unit: 16x4 pixels = two 8x4 sub-blocks; lane (lx, ly) owns pixel
+// (lx, ly) of both
+constexpr int kUW = 16, kUH = 4, kSub = 2;
+constexpr int kSlot = 384;  // one stage: depth [4][16] (<= float32, 256 B) at 0, skin [4][16] at 256
+
+struct RenderShared {
+    float4 prims[kMaxPrims * 4];
+    alignas(128) unsigned char tile[2][kSlot];
+    uint64_t bar[2];
+    int box[4];  // xa, v0, units per row, units
+};
+
+// the sub-block masks of unit (x0, y0): bit j of m[s] = primitive j's box
+// overlaps 8x4 sub-block s (s = column)
+__device__ __forceinline__ void cull_unit(const RenderShared& sm, int n_prims, int lane, int x0, int y0,
+                                          uint64_t m[kSub])
+{
+    m[0] = m[1] = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        const bool present = j < n_prims;
+        int u0 = 0, v0 = 0, u1 = 0, v1 = 0;
+        if (present) {
+            const float4 r3 = sm.prims[4 * j + 3];
+            u0 = lo_i16(r3.z);
+            v0 = hi_i16(r3.z);
+            u1 = lo_i16(r3.w);
+            v1 = hi_i16(r3.w);
+        }
+        const bool row = present && v0 <= y0 + 3 && v1 >= y0;
+        m[0] |= (uint64_t)__ballot_sync(0xffffffffu, row && u0 <= x0 + 7 && u1 >= x0) << (32 * h);
+        m[1] |= (uint64_t)__ballot_sync(0xffffffffu, row && u0 <= x0 + 15 && u1 >= x0 + 8) << (32 * h);
+    }
+}
+
+// One CTA = one warp.  The K warps of particle p split p's units round-robin;
+// a warp frees its SM slot as soon as it is done, so the hardware keeps
+// every SM filled with independent warps.
+__global__ void __launch_bounds__(32, 24)
     render_score_kernel(const __grid_constant__ CUtensorMap tm_depth, const __grid_constant__ CUtensorMap tm_skin,
                         const RenderArgs a)
 {
-    __shared__ RenderSmem sm;
-    const int k = blockIdx.x, p = blockIdx.y;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ RenderShared sm;
+    const int p = blockIdx.y;
+    const int lane = threadIdx.x;
+    const int esz = a.depth_f32 ? 4 : 2;
+    HsParticleWork* wk = a.work + p;
 
     const float4* src = a.prims + (size_t)p * a.n_prims * 4;
-    for (int i = tid; i < a.n_prims * 4; i += kThreads) sm.prims[i] = src[i];
-    if (tid == 0) {
-        mbar_init(&sm.bar[0], 1);
-        mbar_init(&sm.bar[1], 1);
-        mbar_fence_init();
+    for (int i = lane; i < a.n_prims * 4; i += 32) sm.prims[i] = src[i];
+    if (lane < 2) mbar_init(&sm.bar[lane], 1);
+    if (lane == 0) mbar_fence_init();
+    // the particle's screen box, clipped to the ROI, in 16x4 units
+    int u0 = INT_MAX, v0 = INT_MAX, u1 = INT_MIN, v1 = INT_MIN;
+    for (int i = lane; i < a.n_prims; i += 32) {
+        const float4 r3 = src[4 * i + 3];
+        u0 = min(u0, lo_i16(r3.z));
+        v0 = min(v0, hi_i16(r3.z));
+        u1 = max(u1, lo_i16(r3.w));
+        v1 = max(v1, hi_i16(r3.w));
     }
-    __syncthreads();
-
-    // the particle's screen box in tiles (union of primitive boxes, clipped to the ROI)
-    if (warp == 0) {
-        int u0 = INT_MAX, v0 = INT_MAX, u1 = INT_MIN, v1 = INT_MIN;
-        for (int i = lane; i < a.n_prims; i += 32) {
-            const float4 r3 = sm.prims[4 * i + 3];
-            u0 = min(u0, lo_i16(r3.z));
-            v0 = min(v0, hi_i16(r3.z));
-            u1 = max(u1, lo_i16(r3.w));
-            v1 = max(v1, hi_i16(r3.w));
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            u0 = min(u0, __shfl_xor_sync(0xffffffffu, u0, o));
-            v0 = min(v0, __shfl_xor_sync(0xffffffffu, v0, o));
-            u1 = max(u1, __shfl_xor_sync(0xffffffffu, u1, o));
-            v1 = max(v1, __shfl_xor_sync(0xffffffffu, v1, o));
-        }
-        if (lane == 0) {
-            u0 = max(u0, 0);
-            v0 = max(v0, 0);
-            u1 = min(u1, a.W - 1);
-            v1 = min(v1, a.H - 1);
-            if (u0 > u1 || v0 > v1) {
-                sm.box[0] = sm.box[1] = sm.box[2] = sm.box[3] = 0;
-            } else {
-                sm.box[0] = u0 / kTW;
-                sm.box[1] = v0 / kTH;
-                sm.box[2] = u1 / kTW - u0 / kTW + 1;
-                sm.box[3] = v1 / kTH - v0 / kTH + 1;
-            }
-        }
+    for (int o = 16; o > 0; o >>= 1) {
+        u0 = min(u0, __shfl_xor_sync(0xffffffffu, u0, o));
+        v0 = min(v0, __shfl_xor_sync(0xffffffffu, v0, o));
+        u1 = max(u1, __shfl_xor_sync(0xffffffffu, u1, o));
+        v1 = max(v1, __shfl_xor_sync(0xffffffffu, v1, o));
     }
-    __syncthreads();
-    const int tx0 = sm.box[0], ty0 = sm.box[1], ntx = sm.box[2];
-    const int n_tiles = ntx * sm.box[3];
-    const uint32_t tx_bytes = kTW * kTH * (a.depth_f32 ? 4u : 2u) + kTW * kTH;
+    u0 = max(u0, 0);
+    v0 = max(v0, 0);
+    u1 = min(u1, a.W - 1);
+    v1 = min(v1, a.H - 1);
+    const int xa = u0 & ~15;  // TMA: the uint8 skin needs x at a multiple of 16 bytes
+    const bool empty = u0 > u1 || v0 > v1;
+    const int nux = empty ? 1 : (u1 + 1 - xa + kUW - 1) / kUW;
+    const int n_units = empty ? 0 : nux * ((v1 - v0 + kUH) / kUH);
+    __syncwarp();
+    const float kcp = a.kc[p];
 
-    if (tid == 0 && k < n_tiles) {
-        mbar_arrive_expect_tx(&sm.bar[0], tx_bytes);
-        tma_load_2d(sm.depth[0], &tm_depth, (tx0 + k % ntx) * kTW, (ty0 + k / ntx) * kTH, &sm.bar[0]);
-        tma_load_2d(sm.skin[0], &tm_skin, (tx0 + k % ntx) * kTW, (ty0 + k / ntx) * kTH, &sm.bar[0]);
+    if (n_units == 0) {  // nothing of the hand inside the ROI: E is the baseline
+        if (blockIdx.x == 0 && lane == 0) {
+            const uint32_t n_valid = a.stats[0], n_skin = a.stats[1];
+            const float t_sum = a.d_M * (float)n_valid;
+            const float D = n_skin == 0 ? a.lambda : t_sum / (float)n_skin + a.lambda;
+            a.E[p] = D + a.lambda_k * kcp;
+            if (a.parts) a.parts[p] = HsParts{t_sum, 0u, n_skin, 0u};
+        }
+        return;
     }
 
-    float acc_t = 0.f;
+    const uint32_t tx_bytes = kUW * kUH * (uint32_t)(esz + 1);
+    long long acc_t = 0;
     uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
-    int it = 0;
-    for (int i = k; i < n_tiles; i += a.K, ++it) {
-        const int s = it & 1;
-        const int tx = tx0 + i % ntx, ty = ty0 + i / ntx;
-        const int nxt = i + a.K;
-        if (tid == 0 && nxt < n_tiles) {
-            mbar_arrive_expect_tx(&sm.bar[s ^ 1], tx_bytes);
-            tma_load_2d(sm.depth[s ^ 1], &tm_depth, (tx0 + nxt % ntx) * kTW, (ty0 + nxt / ntx) * kTH, &sm.bar[s ^ 1]);
-            tma_load_2d(sm.skin[s ^ 1], &tm_skin, (tx0 + nxt % ntx) * kTW, (ty0 + nxt / ntx) * kTH, &sm.bar[s ^ 1]);
+    uint32_t phases = 0u;  // bit s: parity of stage s's next completion
+    bool ok = true;
+    const int lx = lane & 7, ly = lane >> 3;
+    const int stride = gridDim.x;
+    int u = blockIdx.x;
+    int s = 0;  // stage of unit u
+    uint64_t mk[kSub];
+    auto prepare = [&](int unit, int stage, uint64_t m[kSub]) {
+        const int x0 = xa + kUW * (unit % nux), y0 = v0 + kUH * (unit / nux);
+        cull_unit(sm, a.n_prims, lane, x0, y0, m);
+        if ((m[0] | m[1]) && lane == 0) {
+            unsigned char* t = sm.tile[stage];
+            mbar_arrive_expect_tx(&sm.bar[stage], tx_bytes);
+            tma_load_2d(t, &tm_depth, x0, y0, &sm.bar[stage]);
+            tma_load_2d(t + 256, &tm_skin, x0, y0, &sm.bar[stage]);
         }
-        // warp-level culling: this warp's 8x4 pixel block against every primitive box
-        const int wx0 = tx * kTW + (warp & 1) * 8, wy0 = ty * kTH + (warp >> 1) * 4;
-        const bool c0 = lane < a.n_prims && box_overlaps(sm.prims[4 * lane + 3], wx0, wy0, wx0 + 7, wy0 + 3);
-        const bool c1 =
-            lane + 32 < a.n_prims && box_overlaps(sm.prims[4 * (lane + 32) + 3], wx0, wy0, wx0 + 7, wy0 + 3);
-        uint64_t mask = (uint64_t)__ballot_sync(0xffffffffu, c0) | ((uint64_t)__ballot_sync(0xffffffffu, c1) << 32);
-
-        const int px = wx0 + (lane & 7), py = wy0 + (lane >> 3);
-        const float ra = __fdiv_rn((float)px + 0.5f - a.cx, a.fx);
-        const float rb = __fdiv_rn((float)py + 0.5f - a.cy, a.fy);
-        // nearest hit: depth z = t0 + s, kept as (t0, s) so the cost can form
-        // O_d - z as (O_d - t0) - s without rounding at the ~500 mm scale
-        float z = INFINITY, zt0 = 0.f, zs = 0.f;
-        while (mask) {
-            const int j = __ffsll((long long)mask) - 1;
-            mask &= mask - 1;
-            const float4* r = &sm.prims[4 * j];
-            const float4 r2 = r[2];
-            const float s = intersect(r[0], r[1], r2, r[3], ra, rb);
-            const float zz = r2.w + s;
-            if (zz < z) {
-                z = zz;
-                zt0 = r2.w;
-                zs = s;
+    };
+    mk[0] = mk[1] = 0;
+    if (u < n_units) prepare(u, 0, mk);
+    while (u < n_units && ok) {
+        const int un = u + stride;
+        uint64_t mn[kSub] = {0, 0};
+        if (un < n_units) prepare(un, s ^ 1, mn);  // look-ahead: cull and start the next tile
+        const uint64_t any = mk[0] | mk[1];
+        if (any) {
+            const int x0 = xa + kUW * (u % nux), y0 = v0 + kUH * (u / nux);
+            const int px0 = x0 + lx, py = y0 + ly;
+            const float ra[2] = {fmaf((float)px0, a.inv_fx, a.off_x), fmaf((float)(px0 + 8), a.inv_fx, a.off_x)};
+            const float rb = fmaf((float)py, a.inv_fy, a.off_y);
+            // nearest hit per pixel as (t0, s): depth z = t0 + s
+            float z[kSub] = {INFINITY, INFINITY}, zt[kSub] = {0.f, 0.f}, zs[kSub] = {0.f, 0.f};
+            uint64_t mask = any;
+            while (mask) {
+                const int j = __ffsll((long long)mask) - 1;
+                mask &= mask - 1;
+                const float4* r = &sm.prims[4 * j];
+                const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3];
+#pragma unroll
+                for (int q = 0; q < kSub; ++q) {
+                    if ((mk[q] >> j) & 1) {
+                        const float sh = intersect(r0, r1, r2, r3, ra[q], rb);
+                        const float zz = r2.w + sh;
+                        if (zz < z[q]) {
+                            z[q] = zz;
+                            zt[q] = r2.w;
+                            zs[q] = sh;
+                        }
+                    }
+                }
             }
-        }
-
-        mbar_wait_bounded(&sm.bar[s], (uint32_t)(it >> 1) & 1u, a.status);
-        const int li = (py - ty * kTH) * kTW + (px - tx * kTW);
-        const float od = a.depth_f32 ? reinterpret_cast<const float*>(sm.depth[s])[li]
-                                     : (float)reinterpret_cast<const uint16_t*>(sm.depth[s])[li];
-        const bool S = sm.skin[s][li] != 0;
-        const bool in_roi = px < a.W && py < a.H;
-        const bool hit = z < INFINITY;
-        // per-pixel terms of Eq. 4 (reading R1), as differences to the no-hit baseline
-        const bool valid = S && od > 0.f;
-        const float diff = fabsf((od - zt0) - zs);
-        const bool rm = hit && (!valid || diff < a.d_m);
-        const float t = hit ? (valid ? fminf(diff, a.d_M) : (S ? 0.f : a.d_M)) : (valid ? a.d_M : 0.f);
-        float dt = t - (valid ? a.d_M : 0.f);
-        uint32_t c = (uint32_t)(S && rm) | ((uint32_t)(rm && !S) << 10) | ((uint32_t)hit << 20);
-        if (!in_roi) {
-            dt = 0.f;
-            c = 0;
-        } else if (a.dbg_depth) {
-            const size_t o = ((size_t)p * a.H + py) * a.W + px;
-            a.dbg_depth[o] = hit ? z : 0.f;
-            a.dbg_mask[o] = (uint8_t)((hit ? 1 : 0) | (rm ? 2 : 0));
-        }
+            ok = mbar_wait_bounded(&sm.bar[s], (phases >> s) & 1u, a.status);
+            phases ^= 1u << s;
+            const unsigned char* t = sm.tile[s];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            dt += __shfl_xor_sync(0xffffffffu, dt, o);
-            c += __shfl_xor_sync(0xffffffffu, c, o);
-        }
-        if (lane == 0) {
-            sm.wsum_t[warp] = dt;
-            sm.wsum_c[warp] = c;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            float st = 0.f;
-            uint32_t sc = 0;
-#pragma unroll
-            for (int w = 0; w < kThreads / 32; ++w) {
-                st += sm.wsum_t[w];
-                sc += sm.wsum_c[w];
+            for (int q = 0; q < kSub; ++q) {
+                const int xr = lx + 8 * q;
+                const int px = x0 + xr;
+                if (ok && z[q] < INFINITY && px < a.W && py < a.H) {
+                    const int oi = ly * kUW + xr;
+                    const float od = a.depth_f32 ? reinterpret_cast<const float*>(t)[oi]
+                                                 : (float)reinterpret_cast<const uint16_t*>(t)[oi];
+                    const bool rm = add_pixel(od, t[256 + oi] != 0, zt[q], zs[q], a, acc_t, acc_a, acc_o, acc_h);
+                    if (a.dbg_depth) {
+                        const size_t o = ((size_t)p * a.H + py) * a.W + px;
+                        a.dbg_depth[o] = z[q];
+                        a.dbg_mask[o] = (uint8_t)(1 | (rm ? 2 : 0));
+                    }
+                }
             }
-            acc_t += st;
-            acc_a += sc & 1023u;
-            acc_o += (sc >> 10) & 1023u;
-            acc_h += sc >> 20;
+            __syncwarp();  // every lane is done with this stage before it is refilled
         }
-        __syncthreads();
+        mk[0] = mn[0];
+        mk[1] = mn[1];
+        u = un;
+        s ^= 1;
     }
+    // a unit prepared but never processed (a wait timed out) leaves no copy behind
+    if (!ok && u < n_units && (mk[0] | mk[1])) mbar_wait_bounded(&sm.bar[s], (phases >> s) & 1u, a.status);
 
-    // per-CTA partial, then the last CTA of the particle finishes it
-    if (tid == 0) {
-        a.partials[(size_t)p * a.K + k] =
-            make_float4(acc_t, __uint_as_float(acc_a), __uint_as_float(acc_o), __uint_as_float(acc_h));
-        __threadfence();
-        const uint32_t prev = atomicAdd(&a.counters[p], 1u);
-        sm.last = prev == (uint32_t)(a.K - 1);
-    }
-    __syncthreads();
-    if (sm.last && warp == 0) {
-        __threadfence();
-        float st = 0.f;
-        uint32_t sa = 0, so = 0, sh = 0;
-        for (int j = lane; j < a.K; j += 32) {
-            const float4 v = __ldcg(&a.partials[(size_t)p * a.K + j]);
-            st += v.x;
-            sa += __float_as_uint(v.y);
-            so += __float_as_uint(v.z);
-            sh += __float_as_uint(v.w);
-        }
+    // flush this warp's sums; the last warp of the particle forms E and clears the workspace
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            st += __shfl_xor_sync(0xffffffffu, st, o);
-            sa += __shfl_xor_sync(0xffffffffu, sa, o);
-            so += __shfl_xor_sync(0xffffffffu, so, o);
-            sh += __shfl_xor_sync(0xffffffffu, sh, o);
-        }
-        if (lane == 0) {
-            const uint32_t n_valid = __ldcg(&a.stats[0]), n_skin = __ldcg(&a.stats[1]);
-            const float t_sum = st + a.d_M * (float)n_valid;
-            so += n_skin;
+    for (int o = 16; o > 0; o >>= 1) {
+        acc_t += __shfl_xor_sync(0xffffffffu, acc_t, o);
+        acc_a += __shfl_xor_sync(0xffffffffu, acc_a, o);
+        acc_o += __shfl_xor_sync(0xffffffffu, acc_o, o);
+        acc_h += __shfl_xor_sync(0xffffffffu, acc_h, o);
+    }
+    if (lane == 0) {
+        if (acc_t) atomicAdd(&wk->t_fix, (unsigned long long)acc_t);
+        if (acc_a) atomicAdd(&wk->n_and, acc_a);
+        if (acc_o) atomicAdd(&wk->n_or, acc_o);
+        if (acc_h) atomicAdd(&wk->n_hit, acc_h);
+        __threadfence();
+        const uint32_t done = atomicAdd(&wk->exited, 1u);
+        if (done == gridDim.x - 1) {
+            __threadfence();
+            const long long tf = (long long)atomicAdd(&wk->t_fix, 0ull);
+            const uint32_t sa = atomicAdd(&wk->n_and, 0u), so_d = atomicAdd(&wk->n_or, 0u);
+            const uint32_t sh = atomicAdd(&wk->n_hit, 0u);
+            const uint32_t n_valid = a.stats[0], n_skin = a.stats[1];
+            const float t_sum = (float)tf * (1.0f / kFix) + a.d_M * (float)n_valid;
+            const uint32_t so = so_d + n_skin;
             float D;
             if (so == 0) {
                 D = a.lambda;
@@ -340,9 +375,9 @@ __global__ void __launch_bounds__(kThreads, 4)
                 const float fa = (float)sa, fo = (float)so;
                 D = t_sum / fo + a.lambda * (1.f - 2.f * fa / (fa + fo));
             }
-            a.E[p] = D + a.lambda_k * a.kc[p];
+            a.E[p] = D + a.lambda_k * kcp;
             if (a.parts) a.parts[p] = HsParts{t_sum, sa, so, sh};
-            a.counters[p] = 0;
+            *wk = HsParticleWork{};  // every warp of the particle is done: safe to clear
         }
     }
 }
@@ -352,6 +387,7 @@ __global__ void __launch_bounds__(256) obs_stats_kernel(const unsigned char* dep
                                                         const uint8_t* skin, int skin_pitch, int W, int H,
                                                         uint32_t* stats)
 {
+    __shared__ uint32_t red[2][8];
     uint32_t nv = 0, ns = 0;
     for (int y = blockIdx.x; y < H; y += gridDim.x) {
         for (int x = threadIdx.x; x < W; x += blockDim.x) {
@@ -368,8 +404,18 @@ __global__ void __launch_bounds__(256) obs_stats_kernel(const unsigned char* dep
         ns += __shfl_xor_sync(0xffffffffu, ns, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&stats[0], nv);
-        atomicAdd(&stats[1], ns);
+        red[0][threadIdx.x >> 5] = nv;
+        red[1][threadIdx.x >> 5] = ns;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // one atomic pair per block keeps the two counters uncontended
+        uint32_t tv = 0, ts = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            tv += red[0][w];
+            ts += red[1][w];
+        }
+        atomicAdd(&stats[0], tv);
+        atomicAdd(&stats[1], ts);
     }
 }
 
@@ -377,14 +423,14 @@ cudaError_t launch_render_score(const CUtensorMap& tm_depth, const CUtensorMap& 
                                 cudaStream_t stream)
 {
     dim3 grid(args.K, args.P);
-    render_score_kernel<<<grid, kThreads, 0, stream>>>(tm_depth, tm_skin, args);
+    render_score_kernel<<<grid, 32, 0, stream>>>(tm_depth, tm_skin, args);
     return cudaGetLastError();
 }
 
 cudaError_t launch_obs_stats(const unsigned char* depth, int depth_pitch, int depth_f32, const uint8_t* skin,
                              int skin_pitch, int W, int H, uint32_t* stats, cudaStream_t stream)
 {
-    const int blocks = H < 296 ? H : 296;
+    const int blocks = H < 148 ? H : 148;
     obs_stats_kernel<<<blocks, 256, 0, stream>>>(depth, depth_pitch, depth_f32, skin, skin_pitch, W, H, stats);
     return cudaGetLastError();
 }

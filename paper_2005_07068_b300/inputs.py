@@ -115,7 +115,9 @@ class HandGeometry:
 def hand_geometry(seed: int = GEOMETRY_SEED) -> HandGeometry:
     """Seeded 16-bone / 37-primitive hand; bone lengths lie in [20, 90] mm."""
     rng = np.random.default_rng(seed)
-    palm_len = float(rng.uniform(75.0, 90.0))
+    # on a 1/64 mm grid, so the palm cylinder's cap planes (centre +- half
+    # length) coincide exactly with the end ellipsoids in float32 as well
+    palm_len = round(float(rng.uniform(75.0, 90.0)) * 64.0) / 64.0
     scale = {"index": 1.0, "middle": 1.06, "ring": 0.98, "pinky": 0.82}
     lengths = np.zeros((5, 3))
     lengths[0] = [rng.uniform(40, 50), rng.uniform(28, 36), rng.uniform(22, 28)]

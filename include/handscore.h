@@ -241,6 +241,29 @@ int pso_init(const HsModel* model, const HsSwarm* swarm, int P, const float* see
 int pso_step(const HsModel* model, const HsSwarm* swarm, int P, const HsPsoParams* params,
              uint64_t seed, uint32_t frame, uint32_t gen, hs_stream_t stream);
 
+/* render_score_batch for callers that cannot allocate device memory (a plugin
+ * whose host owns every allocation, a real-time loop that must not allocate
+ * after start-up, a layer without access to the application's allocator).
+ * The paper has no counterpart: this is a deployment convenience.  Identical
+ * to render_score_batch without the debug outputs, except that the scratch
+ * workspace is a fixed array inside this library (HS_NOALLOC_SCRATCH_BYTES
+ * bytes per GPU, held from library load until process exit), so the call
+ * allocates nothing (no cudaMalloc, no allocating library routine).
+ *  - P is limited to what the array holds: calls with hs_workspace_size(P) >
+ *    HS_NOALLOC_SCRATCH_BYTES (P > 8192 with the current 32-byte per-particle
+ *    layout) return HS_ERR_SIZE and launch nothing.
+ *  - The first call on a device looks up the array's device address (with
+ *    cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture.
+ *  - Every call on a device shares the one array and clears the part it uses
+ *    before launching, so calls that overlap on the GPU (different streams
+ *    without ordering between them) race and give wrong results.
+ * Errors: as render_score_batch, plus HS_ERR_SIZE for P over the limit. */
+#define HS_NOALLOC_SCRATCH_BYTES (256 * 1024)
+int render_score_batch_noalloc(const HsModel* model, const HsObs* obs, const HsCamera* cam,
+                               const HsPrim* prims, const float* kc, int P, const HsScoreParams* params,
+                               float* E, HsParts* parts, hs_stream_t stream);
+
 /* Read (and optionally clear) the device status word of the current device.
  * Synchronises the device.  out: host.  Errors: HS_ERR_ARG, HS_ERR_CUDA. */
 int hs_get_device_status(uint32_t* out, int clear);

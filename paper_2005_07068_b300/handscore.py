@@ -82,7 +82,10 @@ _SIGS = {
     "pso_step": ([_vp, ctypes.POINTER(HsSwarm), ctypes.c_int, ctypes.POINTER(HsPsoParams), ctypes.c_uint64,
                   ctypes.c_uint32, ctypes.c_uint32, _vp], ctypes.c_int),
     "hs_get_device_status": ([ctypes.POINTER(ctypes.c_uint32), ctypes.c_int], ctypes.c_int),
+    "render_score_batch_noalloc": ([_vp, ctypes.POINTER(HsObs), ctypes.POINTER(HsCamera), _vp, _vp, ctypes.c_int,
+                                    ctypes.POINTER(HsScoreParams), _vp, _vp, _vp], ctypes.c_int),
 }
+NOALLOC_SCRATCH_BYTES = 256 * 1024
 
 _LIB = None
 
@@ -255,6 +258,20 @@ def render_score_batch(model: Model, obs: Obs, cam: HsCamera, prims: torch.Tenso
            lib().render_score_batch(model.handle, ctypes.byref(st), ctypes.byref(cam), _ptr(prims), _ptr(kc), P,
                                     ctypes.byref(params), _ptr(ws), ws.numel(), _ptr(E), _ptr(parts),
                                     _ptr(dbg_depth), _ptr(dbg_mask), _stream(stream)))
+
+
+def render_score_batch_noalloc(model: Model, obs: Obs, cam: HsCamera, prims: torch.Tensor, kc: torch.Tensor,
+                               params: HsScoreParams, E: torch.Tensor, parts: torch.Tensor | None = None,
+                               stream=None) -> None:
+    """render_score_batch without a caller workspace: for callers that cannot
+    allocate device memory.  The scratch is a fixed array inside the library
+    (one per GPU, NOALLOC_SCRATCH_BYTES); calls that overlap on the GPU race."""
+    P = kc.shape[0]
+    st = obs.struct()
+    _check("render_score_batch_noalloc",
+           lib().render_score_batch_noalloc(model.handle, ctypes.byref(st), ctypes.byref(cam), _ptr(prims),
+                                            _ptr(kc), P, ctypes.byref(params), _ptr(E), _ptr(parts),
+                                            _stream(stream)))
 
 
 @dataclass

@@ -264,6 +264,22 @@ int render_score_batch_noalloc(const HsModel* model, const HsObs* obs, const HsC
                                const HsPrim* prims, const float* kc, int P, const HsScoreParams* params,
                                float* E, HsParts* parts, hs_stream_t stream);
 
+/* One generation fused with the FK of the new positions: exactly pso_step
+ * followed by pose_fk of the updated swarm, in one launch (one CTA per
+ * particle), except that the new positions go to x_next [P][26] (a second
+ * buffer; swarm->x is only read) so that no particle has to wait for another.
+ * The caller alternates the two position buffers between generations.  prims
+ * and kc receive the records of x_next for the next render_score_batch.
+ * Tie rule of the fused step: when a particle's E equals its personal-best E
+ * exactly and it is the global best, gbest takes its current position.
+ * 1 <= P <= HS_FUSED_MAX_PARTICLES (every CTA scans the P objectives).
+ * Errors: HS_ERR_ARG (NULL, x_next == swarm->x, bad constants), HS_ERR_ALIGN,
+ * HS_ERR_SIZE, HS_ERR_CUDA. */
+#define HS_FUSED_MAX_PARTICLES 1024
+int pso_step_fk(const HsModel* model, const HsSwarm* swarm, float* x_next, int P, const HsPsoParams* params,
+                uint64_t seed, uint32_t frame, uint32_t gen, const HsCamera* cam, HsPrim* prims, float* kc,
+                hs_stream_t stream);
+
 /* Read (and optionally clear) the device status word of the current device.
  * Synchronises the device.  out: host.  Errors: HS_ERR_ARG, HS_ERR_CUDA. */
 int hs_get_device_status(uint32_t* out, int clear);

@@ -396,6 +396,46 @@ int pso_step(const HsModel* model, const HsSwarm* sw, int P, const HsPsoParams* 
     return launch_pso_step(model->lim, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 
+int pso_step_fk(const HsModel* model, const HsSwarm* sw, float* x_next, int P, const HsPsoParams* prm,
+                uint64_t seed, uint32_t frame, uint32_t gen, const HsCamera* cam, HsPrim* prims, float* kc,
+                hs_stream_t stream)
+{
+    if (!model || !sw || !prm || !x_next || !prims || !kc) return HS_ERR_ARG;
+    if (!sw->x || !sw->v || !sw->pbest || !sw->pbest_E || !sw->gbest || !sw->gbest_E || !sw->E) return HS_ERR_ARG;
+    if (x_next == sw->x) return HS_ERR_ARG;  // positions are double-buffered
+    int rc = validate_cam(cam);
+    if (rc) return rc;
+    if (P < 1 || P > HS_FUSED_MAX_PARTICLES) return HS_ERR_SIZE;
+    if (!aligned16(prims)) return HS_ERR_ALIGN;
+    const double psi = (double)prm->c1 + (double)prm->c2;
+    if (!std::isfinite(psi) || prm->c1 < 0.f || prm->c2 < 0.f || psi <= 4.0) return HS_ERR_ARG;
+    if (prm->mutate_every > 0 && (prm->n_mutate < 0 || prm->n_mutate > P)) return HS_ERR_ARG;
+    PsoFkArgs a;
+    a.x = sw->x;
+    a.x_next = x_next;
+    a.v = sw->v;
+    a.pbest = sw->pbest;
+    a.pbest_E = sw->pbest_E;
+    a.gbest = sw->gbest;
+    a.gbest_E = sw->gbest_E;
+    a.E = sw->E;
+    a.P = P;
+    a.c1 = prm->c1;
+    a.c2 = prm->c2;
+    a.w = (float)(2.0 / std::fabs(2.0 - psi - std::sqrt(psi * psi - 4.0 * psi)));
+    a.mutate = prm->mutate_every > 0 && gen % (uint32_t)prm->mutate_every == 0 && prm->n_mutate > 0;
+    a.n_mutate = prm->n_mutate;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.frame = frame;
+    a.gen = gen;
+    a.cam = make_float4(cam->fx, cam->fy, cam->cx, cam->cy);
+    a.prims = reinterpret_cast<float4*>(prims);
+    a.kc = kc;
+    if ((rc = status_ptr(&a.status))) return rc;
+    return launch_pso_step_fk(model->dev, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
 int hs_get_device_status(uint32_t* out, int clear)
 {
     if (!out) return HS_ERR_ARG;

@@ -60,7 +60,24 @@ struct PsoStepArgs {
     uint32_t key0, key1, frame, gen;
 };
 
+// the fused generation step: PSO update of every particle, then FK of its new pose
+struct PsoFkArgs {
+    const float* x;        // [P][26] current positions (read only)
+    float* x_next;         // [P][26] new positions
+    float *v, *pbest, *pbest_E, *gbest, *gbest_E;
+    const float* E;
+    int P;
+    float c1, c2, w;
+    int mutate, n_mutate;
+    uint32_t key0, key1, frame, gen;
+    float4 cam;            // fx, fy, cx, cy
+    float4* prims;         // [P][n_prims][4]
+    float* kc;             // [P]
+    uint32_t* status;
+};
+
 cudaError_t launch_fk(const DevModel& model, const FkArgs& args, cudaStream_t stream);
+cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cudaStream_t stream);
 cudaError_t launch_render_score(const CUtensorMap& tm_depth, const CUtensorMap& tm_skin, const RenderArgs& args,
                                 cudaStream_t stream);
 cudaError_t launch_obs_stats(const unsigned char* depth, int depth_pitch, int depth_f32, const uint8_t* skin,

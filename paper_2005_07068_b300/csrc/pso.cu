@@ -10,7 +10,7 @@
 #include <cfloat>
 #include <climits>
 
-#include "hs_args.cuh"
+#include "hs_fk.cuh"
 
 namespace hs {
 
@@ -161,6 +161,127 @@ __global__ void __launch_bounds__(kPsoThreads) pso_step_kernel(const __grid_cons
             }
         }
     }
+}
+
+// One generation of the swarm fused with the FK of the new positions: one
+// 64-thread CTA per particle.  Every CTA reads the whole E / pbest_E vectors
+// (O(P) per CTA) to find the global best and its own mutation rank, so no CTA
+// waits for another: positions are double-buffered (x is read, x_next
+// written) and a particle's personal best is judged improved when E <= pbest_E
+// as read, which gives the same answer whether or not its owner has already
+// stored the update.
+__global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__ DevModel model_param,
+                                                         const PsoFkArgs a)
+{
+    __shared__ FkShared sh;
+    __shared__ float s_pb[kNdof], s_g[kNdof], s_xn[kNdof];
+    __shared__ float red_v[2];
+    __shared__ int red_i[2], red_r[2];
+    extern __shared__ float s_e[];  // E [P] then pbest_E [P]
+    float* s_pe = s_e + a.P;
+    fk_load_model(sh, model_param);
+    const int i = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int P = a.P;
+    for (int j = t; j < P; j += 64) {
+        s_e[j] = a.E[j];
+        s_pe[j] = a.pbest_E[j];
+    }
+    __syncthreads();
+    // global best = argmin_j min(E_j, pbest_E_j) (lowest index on ties, NaN never
+    // wins) and this particle's rank by E
+    const float ei = s_e[i];
+    float bv = INFINITY;
+    int bi = INT_MAX, rank = 0;
+    for (int j = t; j < P; j += 64) {
+        const float ej = s_e[j], pj = s_pe[j];
+        const float pe = ej < pj ? ej : pj;
+        if (bi == INT_MAX || pe < bv) {
+            bv = pe;
+            bi = j;
+        }
+        if (a.mutate) rank += ranks_before(ej, j, ei, i);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi != INT_MAX && (bi == INT_MAX || ov < bv || (ov == bv && oi < bi))) {
+            bv = ov;
+            bi = oi;
+        }
+        rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    }
+    if (lane == 0) {
+        red_v[warp] = bv;
+        red_i[warp] = bi;
+        red_r[warp] = rank;
+    }
+    __syncthreads();
+    int g = red_i[0];
+    float gE = red_v[0];
+    if (red_i[1] != INT_MAX && (g == INT_MAX || red_v[1] < gE || (red_v[1] == gE && red_i[1] < g))) {
+        g = red_i[1];
+        gE = red_v[1];
+    }
+    rank = red_r[0] + red_r[1];
+    const bool imp = ei < s_pe[i];  // strict improvement of this particle's personal best
+    if (t < kNdof) {
+        // the global best's position: its current x if that is its personal best now
+        const bool gimp = s_e[g] <= s_pe[g];
+        const float gv = gimp ? a.x[(size_t)g * kNdof + t] : a.pbest[(size_t)g * kNdof + t];
+        s_g[t] = gv;
+        if (i == 0) a.gbest[t] = gv;
+        const float xi = a.x[(size_t)i * kNdof + t];
+        const float pb = imp ? xi : a.pbest[(size_t)i * kNdof + t];
+        if (imp) a.pbest[(size_t)i * kNdof + t] = xi;
+        s_pb[t] = pb;
+        s_xn[t] = xi;
+    }
+    if (t == 0) {
+        if (imp) a.pbest_E[i] = ei;
+        if (i == 0) a.gbest_E[0] = gE;
+    }
+    __syncthreads();
+    // Eq. 6-7 with per-dimension r1, r2, then clamp
+    if (t < kPairBlocks) {
+        const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamPso << 16) | (uint32_t)t, a.gen, a.frame}, a.key0, a.key1);
+        const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int d = 2 * t + h;
+            const float r1 = u01(u[2 * h]), r2 = u01(u[2 * h + 1]);
+            const size_t o = (size_t)i * kNdof + d;
+            const float x = s_xn[d];
+            float acc = fmaf(a.c1 * r1, s_pb[d] - x, a.v[o]);
+            acc = fmaf(a.c2 * r2, s_g[d] - x, acc);
+            const float vn = a.w * acc;
+            a.v[o] = vn;
+            s_xn[d] = fminf(fmaxf(x + vn, sh.model.lo[d]), sh.model.hi[d]);
+        }
+    }
+    __syncthreads();
+    // mutation of the n_mutate worst particles by this generation's E
+    if (a.mutate && rank >= P - a.n_mutate && t < kMutBlocks) {
+        const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamMutate << 16) | (uint32_t)t, a.gen, a.frame}, a.key0,
+                                   a.key1);
+        const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int d = 6 + 4 * t + l;
+            if (d >= kNdof) break;
+            s_xn[d] = fmaf(u01(u[l]), sh.model.hi[d] - sh.model.lo[d], sh.model.lo[d]);
+            a.v[(size_t)i * kNdof + d] = 0.f;
+        }
+    }
+    __syncthreads();
+    if (t < kNdof) a.x_next[(size_t)i * kNdof + t] = s_xn[t];
+    fk_particle(sh, s_xn, a.cam, a.prims + (size_t)i * sh.model.n_prims * 4, a.kc + i, a.status);
+}
+
+cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cudaStream_t stream)
+{
+    pso_step_fk_kernel<<<args.P, 64, 2 * (size_t)args.P * sizeof(float), stream>>>(model, args);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pso_init(const Limits& lim, const PsoInitArgs& args, cudaStream_t stream)

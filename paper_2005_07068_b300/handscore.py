@@ -82,6 +82,8 @@ _SIGS = {
     "pso_step": ([_vp, ctypes.POINTER(HsSwarm), ctypes.c_int, ctypes.POINTER(HsPsoParams), ctypes.c_uint64,
                   ctypes.c_uint32, ctypes.c_uint32, _vp], ctypes.c_int),
     "hs_get_device_status": ([ctypes.POINTER(ctypes.c_uint32), ctypes.c_int], ctypes.c_int),
+    "pso_step_fk": ([_vp, ctypes.POINTER(HsSwarm), _vp, ctypes.c_int, ctypes.POINTER(HsPsoParams), ctypes.c_uint64,
+                     ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(HsCamera), _vp, _vp, _vp], ctypes.c_int),
     "render_score_batch_noalloc": ([_vp, ctypes.POINTER(HsObs), ctypes.POINTER(HsCamera), _vp, _vp, ctypes.c_int,
                                     ctypes.POINTER(HsScoreParams), _vp, _vp, _vp], ctypes.c_int),
 }
@@ -312,6 +314,16 @@ def pso_step(model: Model, sw: Swarm, params: HsPsoParams, seed: int, frame: int
     st = sw.struct()
     _check("pso_step", lib().pso_step(model.handle, ctypes.byref(st), sw.P, ctypes.byref(params),
                                       ctypes.c_uint64(seed), frame, gen, _stream(stream)))
+
+
+def pso_step_fk(model: Model, sw: Swarm, x_next: torch.Tensor, params: HsPsoParams, seed: int, frame: int, gen: int,
+                cam: HsCamera, prims: torch.Tensor, kc: torch.Tensor, stream=None) -> None:
+    """pso_step then pose_fk of the new positions, in one launch; the new
+    positions go to x_next (sw.x is only read)."""
+    st = sw.struct()
+    _check("pso_step_fk", lib().pso_step_fk(model.handle, ctypes.byref(st), _ptr(x_next), sw.P, ctypes.byref(params),
+                                            ctypes.c_uint64(seed), frame, gen, ctypes.byref(cam), _ptr(prims),
+                                            _ptr(kc), _stream(stream)))
 
 
 def hs_get_device_status(clear: bool = False) -> int:

@@ -1,11 +1,12 @@
 """Frame-by-frame tracking on one GPU through the C-ABI (Section III.B loop).
 
 One frame = per-frame observation preparation, swarm initialisation around
-the previous frame's global best (tracking), then `gens` generations of
-pose_fk -> render_score_batch -> pso_step.  The whole frame is captured once
-into a CUDA graph per (observation buffer, frame index), so a frame costs a
-single graph launch and no host round trip; the host reads only the final
-global best.
+the previous frame's global best (tracking) and FK of the initial swarm, then
+`gens` generations of render_score_batch -> pso_step_fk (the swarm update
+fused with the FK of the new positions; positions alternate between two
+buffers).  The whole frame is captured once into a CUDA graph per
+(observation buffer, frame index), so a frame costs a single graph launch and
+no host round trip; the host reads only the final global best.
 """
 from __future__ import annotations
 
@@ -28,6 +29,7 @@ class Tracker:
         self.scale = np.asarray(scale, np.float32)
         f = dict(dtype=torch.float32, device=self.device)
         self.swarm = hs.Swarm.empty(P, self.device)
+        self.x_buf = (self.swarm.x, torch.zeros_like(self.swarm.x))  # double-buffered positions
         self.prims = torch.zeros(P, model.n_prims, 16, **f)
         self.kc = torch.zeros(P, **f)
         self.ws = hs.new_workspace(P, self.device)
@@ -42,14 +44,19 @@ class Tracker:
         src = self.swarm.gbest if seed_pose is None else seed_pose
         self.seed_pose.copy_(src)
         hs.hs_obs_prepare(obs)
+        cur, nxt = self.x_buf
+        self.swarm.x = cur
         hs.pso_init(self.model, self.swarm, self.seed_pose, self.scale, self.seed, frame)
+        hs.pose_fk(self.model, cur, self.cam, self.prims, self.kc)
         for g in range(1, self.gens + 1):
-            hs.pose_fk(self.model, self.swarm.x, self.cam, self.prims, self.kc)
             hs.render_score_batch(self.model, obs, self.cam, self.prims, self.kc, self.score, self.ws, self.swarm.E)
-            hs.pso_step(self.model, self.swarm, self.pso, self.seed, frame, g)
+            self.swarm.x = cur
+            hs.pso_step_fk(self.model, self.swarm, nxt, self.pso, self.seed, frame, g, self.cam, self.prims, self.kc)
+            cur, nxt = nxt, cur
             if self.record_history:
                 self.history[g - 1, :26].copy_(self.swarm.gbest)
                 self.history[g - 1, 26:].copy_(self.swarm.gbest_E)
+        self.swarm.x = cur
 
     def graph(self, obs: hs.Obs, frame: int, seed_pose: torch.Tensor | None = None) -> torch.cuda.CUDAGraph:
         """The captured graph of enqueue_frame(obs, frame, seed_pose) (cached)."""
@@ -74,8 +81,8 @@ class Tracker:
             self.enqueue_frame(obs, frame, seed_pose)
 
     def launches_per_frame(self) -> int:
-        """Kernels of this library per frame: obs stats, init, 3 per generation."""
-        return 2 + 3 * self.gens
+        """Kernels of this library per frame: obs stats, init, FK, 2 per generation."""
+        return 3 + 2 * self.gens
 
     # ---- end to end from host memory ---------------------------------------------------
     def track(self, depth_host: torch.Tensor, skin_host: torch.Tensor, staging: hs.Obs, frame: int,

@@ -175,6 +175,11 @@ def test_other_host_checks():
     sw.E = FAKE
     assert L.pso_init(m.handle, ctypes.byref(sw), 64, FAKE, scale, 1, 0, None) == hs.HS_ERR_ARG
     assert L.hs_get_device_status(None, 0) == hs.HS_ERR_ARG
+    sw.E = FAKE
+    assert L.pso_step_fk(m.handle, ctypes.byref(sw), FAKE, 64, ctypes.byref(pp), 1, 0, 1, ctypes.byref(cam), FAKE,
+                         FAKE, None) == hs.HS_ERR_ARG  # x_next aliases x
+    assert L.pso_step_fk(m.handle, ctypes.byref(sw), FAKE + 4096, 2000, ctypes.byref(pp), 1, 0, 1, ctypes.byref(cam),
+                         FAKE, FAKE, None) == hs.HS_ERR_SIZE
     assert hs.lib().hs_status_string(-3) == b"size out of range"
 
 

@@ -264,3 +264,39 @@ def test_gpu_tracking_first_generation_and_descent():
     assert all(b <= a for a, b in zip(hist, hist[1:]))
     assert hist[-1] < hist[0]
     REPORT["tracking_config1_gbest_E"] = hist
+
+
+@pytest.mark.parametrize("gen,P", [(3, 48), (4, 64), (6, 200)])
+def test_fused_step_equals_step_then_fk(gen, P):
+    """pso_step_fk == pso_step followed by pose_fk of the new positions, bit for bit."""
+    lo, hi = (a.astype(np.float32) for a in I.search_limits())
+    g = C.geometry_f32()
+    m = hs.Model.from_geometry(g, lo, hi)
+    rng = np.random.default_rng(gen + P)
+    ref = oracle.pso_init(P, _f32(I.ground_truth_pose(33)), _f32(I.perturbation_scale()), _f32(lo), _f32(hi), 5, 1)
+    ref.v = _f32(rng.normal(0, 0.02, (P, 26)))
+    ref.pbest = _f32(np.clip(ref.x + rng.normal(0, 0.01, (P, 26)), lo, hi))
+    ref.pbest_E = _f32(rng.uniform(5, 30, P))
+    ref.x = _f32(ref.x)
+    ref.gbest = _f32(ref.pbest[int(np.argmin(ref.pbest_E))])
+    ref.gbest_E = float(ref.pbest_E.min())
+    E = _f32(rng.uniform(4, 40, P))
+    E[3] = np.nan
+    cam = hs.camera(262.5, 262.5, 160.0, 120.0)
+    params = hs.pso_params(P=P)
+    a = _gpu_swarm(ref, E)
+    hs.pso_step(m, a, params, 77, 1, gen)
+    prims_a = torch.zeros(P, 37, 16, device="cuda")
+    kc_a = torch.zeros(P, device="cuda")
+    hs.pose_fk(m, a.x, cam, prims_a, kc_a)
+    b = _gpu_swarm(ref, E)
+    x_next = torch.zeros_like(b.x)
+    prims_b = torch.zeros(P, 37, 16, device="cuda")
+    kc_b = torch.zeros(P, device="cuda")
+    hs.pso_step_fk(m, b, x_next, params, 77, 1, gen, cam, prims_b, kc_b)
+    torch.cuda.synchronize()
+    assert torch.equal(x_next, a.x) and torch.equal(b.v, a.v)
+    assert torch.equal(b.pbest, a.pbest) and torch.equal(b.pbest_E, a.pbest_E)
+    assert torch.equal(b.gbest, a.gbest) and torch.equal(b.gbest_E, a.gbest_E)
+    assert torch.equal(prims_b, prims_a) and torch.equal(kc_b, kc_a)
+    assert torch.equal(b.x, _gpu_swarm(ref, E).x)  # the current positions are only read

@@ -308,7 +308,7 @@ int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* c
     }
     // single-warp CTAs per particle: about one resident wave in total (any K
     // is correct; it only changes how the units are dealt)
-    int K = (kTargetCtas + P - 1) / P;
+    int K = kTargetCtas / P;  // rounded down: K * P never exceeds one wave
     if (K > kMaxK) K = kMaxK;
     if (K < 1) K = 1;
 

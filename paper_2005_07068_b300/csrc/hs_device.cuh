@@ -82,6 +82,12 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return r;
 }
 
+// Programmatic dependent launch: let the next kernel in the stream start its
+// launch now; wait until the previous kernel has completed and its writes are
+// visible (both are no-ops when the launch was not programmatic)
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void set_status(uint32_t* status, uint32_t bit)
 {
     if (status) atomicOr(status, bit);

@@ -179,7 +179,9 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
     __shared__ int red_i[2], red_r[2];
     extern __shared__ float s_e[];  // E [P] then pbest_E [P]
     float* s_pe = s_e + a.P;
+    pdl_launch_dependents();
     fk_load_model(sh, model_param);
+    pdl_wait();  // E comes from the previous kernel
     const int i = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int P = a.P;
     for (int j = t; j < P; j += 64) {
@@ -280,8 +282,17 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
 
 cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cudaStream_t stream)
 {
-    pso_step_fk_kernel<<<args.P, 64, 2 * (size_t)args.P * sizeof(float), stream>>>(model, args);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(args.P);
+    cfg.blockDim = dim3(64);
+    cfg.dynamicSmemBytes = 2 * (size_t)args.P * sizeof(float);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pso_step_fk_kernel, model, args);
 }
 
 cudaError_t launch_pso_init(const Limits& lim, const PsoInitArgs& args, cudaStream_t stream)

@@ -221,10 +221,11 @@ __global__ void __launch_bounds__(32, 24)
     const int esz = a.depth_f32 ? 4 : 2;
     HsParticleWork* wk = a.work + p;
 
-    const float4* src = a.prims + (size_t)p * a.n_prims * 4;
-    for (int i = lane; i < a.n_prims * 4; i += 32) sm.prims[i] = src[i];
     if (lane < 2) mbar_init(&sm.bar[lane], 1);
     if (lane == 0) mbar_fence_init();
+    pdl_wait();  // the primitive records and kc come from the previous kernel
+    const float4* src = a.prims + (size_t)p * a.n_prims * 4;
+    for (int i = lane; i < a.n_prims * 4; i += 32) sm.prims[i] = src[i];
     // the particle's screen box, clipped to the ROI, in 16x4 units
     int u0 = INT_MAX, v0 = INT_MAX, u1 = INT_MIN, v1 = INT_MIN;
     for (int i = lane; i < a.n_prims; i += 32) {
@@ -253,6 +254,7 @@ __global__ void __launch_bounds__(32, 24)
     const float kcp = a.kc[p];
 
     if (n_units == 0) {  // nothing of the hand inside the ROI: E is the baseline
+        pdl_launch_dependents();
         if (blockIdx.x == 0 && lane == 0) {
             const uint32_t n_valid = a.stats[0], n_skin = a.stats[1];
             const float t_sum = a.d_M * (float)n_valid;
@@ -345,6 +347,9 @@ __global__ void __launch_bounds__(32, 24)
     // a unit prepared but never processed (a wait timed out) leaves no copy behind
     if (!ok && u < n_units && (mk[0] | mk[1])) mbar_wait_bounded(&sm.bar[s], (phases >> s) & 1u, a.status);
 
+    // the next kernel may start launching once every warp is past its units (it
+    // still waits for this grid to finish before it reads E)
+    pdl_launch_dependents();
     // flush this warp's sums; the last warp of the particle forms E and clears the workspace
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -358,10 +363,11 @@ __global__ void __launch_bounds__(32, 24)
         if (acc_a) atomicAdd(&wk->n_and, acc_a);
         if (acc_o) atomicAdd(&wk->n_or, acc_o);
         if (acc_h) atomicAdd(&wk->n_hit, acc_h);
-        __threadfence();
-        const uint32_t done = atomicAdd(&wk->exited, 1u);
+        // release: the sums above are visible to whoever sees this ticket;
+        // acquire: the last warp sees every other warp's sums
+        uint32_t done;
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(done) : "l"(&wk->exited) : "memory");
         if (done == gridDim.x - 1) {
-            __threadfence();
             const long long tf = (long long)atomicAdd(&wk->t_fix, 0ull);
             const uint32_t sa = atomicAdd(&wk->n_and, 0u), so_d = atomicAdd(&wk->n_or, 0u);
             const uint32_t sh = atomicAdd(&wk->n_hit, 0u);
@@ -422,9 +428,16 @@ __global__ void __launch_bounds__(256) obs_stats_kernel(const unsigned char* dep
 cudaError_t launch_render_score(const CUtensorMap& tm_depth, const CUtensorMap& tm_skin, const RenderArgs& args,
                                 cudaStream_t stream)
 {
-    dim3 grid(args.K, args.P);
-    render_score_kernel<<<grid, 32, 0, stream>>>(tm_depth, tm_skin, args);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(args.K, args.P);
+    cfg.blockDim = dim3(32);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, render_score_kernel, tm_depth, tm_skin, args);
 }
 
 cudaError_t launch_obs_stats(const unsigned char* depth, int depth_pitch, int depth_f32, const uint8_t* skin,

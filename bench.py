@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample")
     ap.add_argument("--profile", action="store_true", help="short run for an ncu launch list")
+    ap.add_argument("--no-roofline", action="store_true", help="skip the render roofline replay")
     return ap.parse_args()
 
 
@@ -293,6 +294,7 @@ def main():
     from paper_2005_07068_b300 import build as B
     from paper_2005_07068_b300 import handscore as hs
     from paper_2005_07068_b300 import inputs as I
+    from paper_2005_07068_b300 import replicas as R
     from paper_2005_07068_b300.tracker import Tracker
 
     if not torch.cuda.is_available():
@@ -306,7 +308,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     peaks = measured_peaks()
-    seed = I.CONFIG_SEED_BASE + 2 + 1000 * rank
+    seed = R.replica_seed(I.CONFIG_SEED_BASE + 2, rank)
     g = I.hand_geometry()
     lo, hi = (a.astype(np.float32) for a in I.search_limits())
     model = hs.Model.from_geometry(g, lo, hi)
@@ -344,66 +346,77 @@ def main():
             dist.barrier()
         wall = time.perf_counter() - w0
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_dev = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([t_dev], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t[0])
-    evals_total = K * PARTICLES * GENS * world
-    value = evals_total / t_dev
+    value, t_dev, evals_total = R.aggregate(sum(step_ms) / 1e3, K * PARTICLES * GENS, dev)
 
-    # ---- roofline of render_score_batch: CUDA events around every launch ----
-    # An eager replay of the same frames, gated behind a GPU sleep so that the
-    # host has enqueued the whole frame before the GPU starts: the events then
-    # bracket kernel time, not host-side launch gaps.
+    # ---- roofline of render_score_batch ----
+    # The timed frames are replayed generation by generation: the primitive
+    # records and kc that each generation's render_score_batch consumed are
+    # kept, then those launches run back to back in one captured graph, timed
+    # with CUDA events on the launching stream (kernel time without host gaps).
     kinds = g.prims_i[:, 1]
-    dur = {"fk": [], "render": [], "pso": []}
-    flops = []
-    for f in range(min(3, frames)):
+    rf = min(3, frames) if not args.no_roofline else 0
+    hist_p = torch.zeros(max(rf, 1) * GENS, PARTICLES, model.n_prims, 16, device=dev)
+    hist_k = torch.zeros(max(rf, 1) * GENS, PARTICLES, device=dev)
+    n = 0
+    for f in range(rf):
+        cur, nxt = trk.x_buf
+        trk.swarm.x = cur
         trk.seed_pose.copy_(gt0 if f == 0 else trk.swarm.gbest)
         hs.hs_obs_prepare(obs[f])
         hs.pso_init(model, trk.swarm, trk.seed_pose, trk.scale, seed, f)
-        torch.cuda.synchronize(dev)
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(GENS)]
-        boxes = []
-        torch.cuda._sleep(40_000_000)  # ~20 ms of GPU time while the host enqueues the frame
+        hs.pose_fk(model, cur, cam, trk.prims, trk.kc)
         for gen in range(1, GENS + 1):
-            e = ev[gen - 1]
-            e[0].record(stream)
-            hs.pose_fk(model, trk.swarm.x, cam, trk.prims, trk.kc)
-            e[1].record(stream)
+            hist_p[n].copy_(trk.prims)
+            hist_k[n].copy_(trk.kc)
+            n += 1
             hs.render_score_batch(model, obs[f], cam, trk.prims, trk.kc, trk.score, trk.ws, trk.swarm.E)
-            e[2].record(stream)
-            boxes.append(trk.prims[:, :, 14:16].clone())
-            e[3].record(stream)
-            hs.pso_step(model, trk.swarm, trk.pso, seed, f, gen)
+            trk.swarm.x = cur
+            hs.pso_step_fk(model, trk.swarm, nxt, trk.pso, seed, f, gen, cam, trk.prims, trk.kc)
+            cur, nxt = nxt, cur
+        trk.swarm.x = cur
+    torch.cuda.synchronize(dev)
+    render_us, flops = None, []
+    if n:
+        E_tmp = torch.zeros(PARTICLES, device=dev)
+
+        def renders():
+            for q in range(n):
+                hs.render_score_batch(model, obs[q // GENS], cam, hist_p[q], hist_k[q], trk.score, trk.ws, E_tmp)
+
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            renders()
+        stream.wait_stream(side)
+        rg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(rg, stream=side):
+            renders()
+        rg.replay()
         torch.cuda.synchronize(dev)
-        for gen in range(GENS):
-            e = ev[gen]
-            dur["fk"].append(e[0].elapsed_time(e[1]) / 1e3)
-            dur["render"].append(e[1].elapsed_time(e[2]) / 1e3)
-            flops.append(algorithmic_flops(boxes[gen].cpu().numpy(), kinds))
-        pso_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(GENS)]
-        torch.cuda._sleep(40_000_000)
-        for gen in range(1, GENS + 1):
-            pso_ev[gen - 1][0].record(stream)
-            hs.pso_step(model, trk.swarm, trk.pso, seed, f, GENS + gen)
-            pso_ev[gen - 1][1].record(stream)
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        a_ev.record(stream)
+        for _ in range(reps):
+            rg.replay()
+        b_ev.record(stream)
         torch.cuda.synchronize(dev)
-        dur["pso"] += [a.elapsed_time(b) / 1e3 for a, b in pso_ev]
+        render_us = a_ev.elapsed_time(b_ev) * 1e3 / (reps * n)
+        hb = hist_p[:n, :, :, 14:16].cpu().numpy()
+        flops = [algorithmic_flops(hb[q], kinds) for q in range(n)]
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clocks = clk.summary(peaks.get("sm_max_mhz", 2032.0))
     sm_max = float(peaks.get("sm_max_mhz") or clocks["sm_max_mhz"] or 2032.0)
     peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = sum(flops) / sum(dur["render"]) / 1e12
+    flop_launch = sum(flops) / len(flops) if flops else 0.0
+    achieved = flop_launch / (render_us * 1e-6) / 1e12 if render_us else 0.0
     traffic = profile_traffic(os.path.join(ROOT, "paper_2005_07068_b300", "csrc", "render_score.cu"))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic, "kernel": "render_score_kernel",
                 "peak_basis": f"FP32: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {sm_max:.0f} MHz "
                               f"(sm_max_mhz of measured)",
-                "launch_us": 1e6 * sum(dur["render"]) / len(dur["render"]),
-                "flop_per_launch": sum(flops) / len(flops),
-                "kernel_us": {k: 1e6 * statistics.median(v) for k, v in dur.items()}}
+                "launch_us": render_us, "launches_timed": n * 5, "flop_per_launch": flop_launch,
+                "flop_basis": "pixel-exact primitive boxes x per-test FP32 tally (ellipsoid 45, cone 78)",
+                "timing": "CUDA events around a graph of the timed frames' render_score_batch launches"}
 
     # ---- end to end: pinned host frame -> device -> graph -> result on the host ----
     e2e = None
@@ -430,12 +443,8 @@ def main():
             trk.track(pin[f][0], pin[f][1], staging, f, out, gt0 if f == 0 else None)
             ee[i][1].record(stream)
         torch.cuda.synchronize(dev)
-        t_e2e = sum(a.elapsed_time(b) for a, b in ee) / 1e3
-        if dist:
-            t = torch.tensor([t_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t[0])
-        e2e = {"value": evals_total / t_e2e, "unit": "evals/s",
+        e2e_value, _, _ = R.aggregate(sum(a.elapsed_time(b) for a, b in ee) / 1e3, K * PARTICLES * GENS, dev)
+        e2e = {"value": e2e_value, "unit": "evals/s",
                "h2d_bytes_per_step": int(pin[0][0].numel() * pin[0][0].element_size() + pin[0][1].numel()),
                "d2h_bytes_per_step": int(out.numel() * out.element_size())}
 

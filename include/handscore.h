@@ -118,7 +118,8 @@ typedef struct {
                                written by hs_obs_prepare, read by render_score_batch */
 } HsObs;
 
-/* constants of Eq. 4-5 (paper: d_m = 1 cm, d_M = 4 cm, lambda = 20, lambda_k = 10) */
+/* constants of Eq. 4-5 (paper: d_m = 1 cm, d_M = 4 cm, lambda = 20, lambda_k = 10),
+ * in mm; 0 <= d_M < 127 (the depth sums are kept in 32-bit fixed point per pixel) */
 typedef struct {
     float d_m, d_M, lambda, lambda_k;
 } HsScoreParams;

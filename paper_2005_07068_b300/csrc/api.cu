@@ -283,7 +283,7 @@ int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* c
     if (rc) return rc;
     if ((rc = validate_cam(cam))) return rc;
     if (!std::isfinite(params->d_m) || !std::isfinite(params->d_M) || !std::isfinite(params->lambda) ||
-        !std::isfinite(params->lambda_k) || params->d_m < 0.f || params->d_M < 0.f)
+        !std::isfinite(params->lambda_k) || params->d_m < 0.f || params->d_M < 0.f || params->d_M >= 127.f)
         return HS_ERR_ARG;
     if (P < 0 || P > HS_MAX_PARTICLES) return HS_ERR_SIZE;
     if (!aligned16(prims) || (workspace && !aligned16(workspace))) return HS_ERR_ALIGN;

@@ -165,7 +165,9 @@ __device__ __forceinline__ bool add_pixel(float od, bool S, float zt0, float zs,
     const float diff = fabsf((od - zt0) - zs);  // O_d - z without rounding at the ~500 mm scale
     const bool rm = !valid || diff < a.d_m;
     const float t = valid ? fminf(diff, a.d_M) : (S ? 0.f : a.d_M);
-    at += __float2ll_rn((t - (valid ? a.d_M : 0.f)) * kFix);
+    // |t - d_M| <= d_M < 128 mm, so the 2^-24 mm fixed-point term fits in 32 bits;
+    // the sum is carried in a 64-bit integer (integer adds, order independent)
+    at += (long long)__float2int_rn((t - (valid ? a.d_M : 0.f)) * kFix);
     aa += (S && rm);
     ao += (rm && !S);
     ah += 1;
@@ -372,7 +374,9 @@ __global__ void __launch_bounds__(32, 24)
             const uint32_t sa = atomicAdd(&wk->n_and, 0u), so_d = atomicAdd(&wk->n_or, 0u);
             const uint32_t sh = atomicAdd(&wk->n_hit, 0u);
             const uint32_t n_valid = a.stats[0], n_skin = a.stats[1];
-            const float t_sum = (float)tf * (1.0f / kFix) + a.d_M * (float)n_valid;
+            // fixed point -> float from the two 32-bit halves (no 64-bit conversion)
+            const float t_fix_f = (float)(int)(tf >> 32) * 4294967296.0f + (float)(uint32_t)(tf & 0xffffffffu);
+            const float t_sum = t_fix_f * (1.0f / kFix) + a.d_M * (float)n_valid;
             const uint32_t so = so_d + n_skin;
             float D;
             if (so == 0) {

@@ -156,6 +156,10 @@ def test_other_host_checks():
     # workspace too small
     assert L.render_score_batch(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 64, ctypes.byref(prm),
                                 FAKE, 16, FAKE, None, None, None, None) == hs.HS_ERR_SIZE
+    # d_M beyond the fixed-point range
+    big = hs.score_params(d_M=200.0)
+    assert L.render_score_batch(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 64, ctypes.byref(big),
+                                FAKE, 1 << 20, FAKE, None, None, None, None) == hs.HS_ERR_ARG
     # only one of the two debug outputs
     assert L.render_score_batch(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 64, ctypes.byref(prm),
                                 FAKE, 1 << 20, FAKE, None, FAKE, None, None) == hs.HS_ERR_ARG

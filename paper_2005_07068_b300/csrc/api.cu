@@ -85,8 +85,8 @@ static int validate_cam(const HsCamera* c)
     return HS_OK;
 }
 
-constexpr int kMaxK = 64;              // single-warp CTAs per particle in render_score_batch
-constexpr int kTargetCtas = 148 * 24;  // one resident wave (24 single-warp CTAs per SM)
+constexpr int kMaxK = 16;             // 4-warp CTAs per particle in render_score_batch
+constexpr int kTargetCtas = 148 * 6;  // one resident wave (6 CTAs of 4 warps per SM)
 
 }  // namespace hs
 
@@ -306,8 +306,8 @@ int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* c
             cudaMemsetAsync(dbg_mask, 0, n, s) != cudaSuccess)
             return HS_ERR_CUDA;
     }
-    // single-warp CTAs per particle: about one resident wave in total (any K
-    // is correct; it only changes how the units are dealt)
+    // CTAs per particle: about one resident wave in total (any K is correct;
+    // it only changes how the units are dealt)
     int K = kTargetCtas / P;  // rounded down: K * P never exceeds one wave
     if (K > kMaxK) K = kMaxK;
     if (K < 1) K = 1;

@@ -33,9 +33,9 @@ struct DevPrimDesc {
 // everything the FK kernel needs about the model (about 4.7 KB)
 struct DevModel {
     int32_t n_bones, n_prims, max_depth, pad;
-    DevBone bones[kMaxBones];
-    DevPrimDesc prims[kMaxPrims];
     float lo[kNdof], hi[kNdof];
+    DevPrimDesc prims[kMaxPrims];  // kernels copy the used prefix of prims and of bones
+    DevBone bones[kMaxBones];
 };
 
 struct Limits {

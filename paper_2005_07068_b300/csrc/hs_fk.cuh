@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cfloat>
+#include <cstddef>
 
 #include "hs_args.cuh"
 
@@ -41,9 +42,15 @@ __device__ __forceinline__ int clamp_i16(float v)
 // memory; later accesses use thread-dependent bone / primitive indices
 __device__ __forceinline__ void fk_load_model(FkShared& sh, const DevModel& mp)
 {
+    // only the used part: header and limits, then the n_prims primitives and n_bones bones
     const uint32_t* srcw = reinterpret_cast<const uint32_t*>(&mp);
     uint32_t* dstw = reinterpret_cast<uint32_t*>(&sh.model);
-    for (int i = threadIdx.x; i < (int)(sizeof(DevModel) / 4); i += blockDim.x) dstw[i] = srcw[i];
+    constexpr int head = (int)(offsetof(DevModel, prims) / 4);
+    const int prim_end = head + mp.n_prims * (int)(sizeof(DevPrimDesc) / 4);
+    constexpr int bones0 = (int)(offsetof(DevModel, bones) / 4);
+    const int bone_words = mp.n_bones * (int)(sizeof(DevBone) / 4);
+    for (int i = threadIdx.x; i < prim_end; i += blockDim.x) dstw[i] = srcw[i];
+    for (int i = threadIdx.x; i < bone_words; i += blockDim.x) dstw[bones0 + i] = srcw[bones0 + i];
 }
 
 // FK of the raw pose `pose` [26] (global or shared memory): writes the particle's

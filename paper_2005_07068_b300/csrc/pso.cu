@@ -174,16 +174,40 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
                                                          const PsoFkArgs a)
 {
     __shared__ FkShared sh;
-    __shared__ float s_pb[kNdof], s_g[kNdof], s_xn[kNdof];
+    __shared__ float s_r[4 * kPairBlocks], s_m[4 * kMutBlocks];
+    __shared__ float s_xn[kNdof];
     __shared__ float red_v[2];
     __shared__ int red_i[2], red_r[2];
     extern __shared__ float s_e[];  // E [P] then pbest_E [P]
     float* s_pe = s_e + a.P;
-    pdl_launch_dependents();
-    fk_load_model(sh, model_param);
-    pdl_wait();  // E comes from the previous kernel
     const int i = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int P = a.P;
+    pdl_launch_dependents();
+    fk_load_model(sh, model_param);
+    // this particle's random numbers depend only on (particle, generation, frame, seed):
+    // draw them while the previous kernel finishes
+    if (t < kPairBlocks) {
+        const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamPso << 16) | (uint32_t)t, a.gen, a.frame}, a.key0, a.key1);
+        s_r[4 * t] = u01(r.x);
+        s_r[4 * t + 1] = u01(r.y);
+        s_r[4 * t + 2] = u01(r.z);
+        s_r[4 * t + 3] = u01(r.w);
+    } else if (t >= 32 && t < 32 + kMutBlocks) {
+        const int b = t - 32;
+        const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamMutate << 16) | (uint32_t)b, a.gen, a.frame}, a.key0,
+                                   a.key1);
+        s_m[4 * b] = u01(r.x);
+        s_m[4 * b + 1] = u01(r.y);
+        s_m[4 * b + 2] = u01(r.z);
+        s_m[4 * b + 3] = u01(r.w);
+    }
+    pdl_wait();  // E comes from the previous kernel
+    float xi = 0.f, pbi = 0.f, vi = 0.f;
+    if (t < kNdof) {  // this particle's own state, loaded before the global best is known
+        xi = a.x[(size_t)i * kNdof + t];
+        pbi = a.pbest[(size_t)i * kNdof + t];
+        vi = a.v[(size_t)i * kNdof + t];
+    }
     for (int j = t; j < P; j += 64) {
         s_e[j] = a.E[j];
         s_pe[j] = a.pbest_E[j];
@@ -227,56 +251,33 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
     }
     rank = red_r[0] + red_r[1];
     const bool imp = ei < s_pe[i];  // strict improvement of this particle's personal best
+    const bool mutated = a.mutate && rank >= P - a.n_mutate;
     if (t < kNdof) {
         // the global best's position: its current x if that is its personal best now
         const bool gimp = s_e[g] <= s_pe[g];
         const float gv = gimp ? a.x[(size_t)g * kNdof + t] : a.pbest[(size_t)g * kNdof + t];
-        s_g[t] = gv;
         if (i == 0) a.gbest[t] = gv;
-        const float xi = a.x[(size_t)i * kNdof + t];
-        const float pb = imp ? xi : a.pbest[(size_t)i * kNdof + t];
+        const float pb = imp ? xi : pbi;
         if (imp) a.pbest[(size_t)i * kNdof + t] = xi;
-        s_pb[t] = pb;
-        s_xn[t] = xi;
+        // Eq. 6-7 for dimension t (r1 = number 2t, r2 = number 2t+1), then clamp;
+        // the mutation re-draws a finger dimension and zeroes its velocity
+        float acc = fmaf(a.c1 * s_r[2 * t], pb - xi, vi);
+        acc = fmaf(a.c2 * s_r[2 * t + 1], gv - xi, acc);
+        float vn = a.w * acc;
+        float xn = fminf(fmaxf(xi + vn, sh.model.lo[t]), sh.model.hi[t]);
+        if (mutated && t >= 6) {
+            xn = fmaf(s_m[t - 6], sh.model.hi[t] - sh.model.lo[t], sh.model.lo[t]);
+            vn = 0.f;
+        }
+        a.v[(size_t)i * kNdof + t] = vn;
+        a.x_next[(size_t)i * kNdof + t] = xn;
+        s_xn[t] = xn;
     }
     if (t == 0) {
         if (imp) a.pbest_E[i] = ei;
         if (i == 0) a.gbest_E[0] = gE;
     }
-    __syncthreads();
-    // Eq. 6-7 with per-dimension r1, r2, then clamp
-    if (t < kPairBlocks) {
-        const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamPso << 16) | (uint32_t)t, a.gen, a.frame}, a.key0, a.key1);
-        const uint32_t u[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int d = 2 * t + h;
-            const float r1 = u01(u[2 * h]), r2 = u01(u[2 * h + 1]);
-            const size_t o = (size_t)i * kNdof + d;
-            const float x = s_xn[d];
-            float acc = fmaf(a.c1 * r1, s_pb[d] - x, a.v[o]);
-            acc = fmaf(a.c2 * r2, s_g[d] - x, acc);
-            const float vn = a.w * acc;
-            a.v[o] = vn;
-            s_xn[d] = fminf(fmaxf(x + vn, sh.model.lo[d]), sh.model.hi[d]);
-        }
-    }
-    __syncthreads();
-    // mutation of the n_mutate worst particles by this generation's E
-    if (a.mutate && rank >= P - a.n_mutate && t < kMutBlocks) {
-        const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamMutate << 16) | (uint32_t)t, a.gen, a.frame}, a.key0,
-                                   a.key1);
-        const uint32_t u[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            const int d = 6 + 4 * t + l;
-            if (d >= kNdof) break;
-            s_xn[d] = fmaf(u01(u[l]), sh.model.hi[d] - sh.model.lo[d], sh.model.lo[d]);
-            a.v[(size_t)i * kNdof + d] = 0.f;
-        }
-    }
-    __syncthreads();
-    if (t < kNdof) a.x_next[(size_t)i * kNdof + t] = s_xn[t];
+    // FK of the new pose (fk_particle starts with a barrier that publishes s_xn)
     fk_particle(sh, s_xn, a.cam, a.prims + (size_t)i * sh.model.n_prims * 4, a.kc + i, a.status);
 }
 

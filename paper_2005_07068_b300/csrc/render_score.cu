@@ -6,12 +6,13 @@
 // paper renders 64 full images with OpenGL, replicates O 64 times and sums
 // with a pyramid (Section IV, steps 1-3).  Here nothing is rendered to memory:
 //
-//  * grid (K, P) of single-warp CTAs: the K warps of particle p split p's work
+//  * grid (K, P) of 4-warp CTAs: the 4K warps of particle p split p's work
 //    units, 16x4-pixel blocks of its screen box (union of its primitives'
 //    conservative boxes, clipped to the ROI), dealt round-robin, so dense and
-//    sparse parts of the hand spread over all warps; a warp frees its SM slot
-//    as soon as it is done and nothing waits on a barrier;
-//  * the particle's 64-byte primitive records are staged in shared memory;
+//    sparse parts of the hand spread over all warps; after the prologue no
+//    warp waits for another;
+//  * the particle's 64-byte primitive records are staged once per CTA in
+//    shared memory;
 //  * a unit's observation (16x4 depth + skin) arrives by a 2-D TMA load into
 //    one of the warp's two shared-memory stages, issued one unit ahead (one
 //    shared copy of O, never replicated);
@@ -179,10 +180,12 @@ __device__ __forceinline__ bool add_pixel(float od, bool S, float zt0, float zs,
 constexpr int kUW = 16, kUH = 4, kSub = 2;
 constexpr int kSlot = 384;  // one stage: depth [4][16] (<= float32, 256 B) at 0, skin [4][16] at 256
 
+constexpr int kWarps = 4;  // warps per CTA; they share one staged copy of the records
+
 struct RenderShared {
     float4 prims[kMaxPrims * 4];
-    alignas(128) unsigned char tile[2][kSlot];
-    uint64_t bar[2];
+    alignas(128) unsigned char tile[kWarps][2][kSlot];
+    uint64_t bar[kWarps][2];
     int box[4];  // xa, v0, units per row, units
 };
 
@@ -210,54 +213,62 @@ __device__ __forceinline__ void cull_unit(const RenderShared& sm, int n_prims, i
     }
 }
 
-// One CTA = one warp.  The K warps of particle p split p's units round-robin;
-// a warp frees its SM slot as soon as it is done, so the hardware keeps
-// every SM filled with independent warps.
-__global__ void __launch_bounds__(32, 24)
+// A CTA is four warps that share the staged records and otherwise run on their
+// own (no barrier after the prologue).  The warps of particle p split p's
+// units round-robin; a CTA frees its SM slot as soon as its warps are done.
+__global__ void __launch_bounds__(kWarps * 32, 6)
     render_score_kernel(const __grid_constant__ CUtensorMap tm_depth, const __grid_constant__ CUtensorMap tm_skin,
                         const RenderArgs a)
 {
     __shared__ RenderShared sm;
     const int p = blockIdx.y;
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int esz = a.depth_f32 ? 4 : 2;
     HsParticleWork* wk = a.work + p;
 
-    if (lane < 2) mbar_init(&sm.bar[lane], 1);
-    if (lane == 0) mbar_fence_init();
+    if (lane < 2) mbar_init(&sm.bar[warp][lane], 1);
+    if (tid == 0) mbar_fence_init();
     pdl_wait();  // the primitive records and kc come from the previous kernel
     const float4* src = a.prims + (size_t)p * a.n_prims * 4;
-    for (int i = lane; i < a.n_prims * 4; i += 32) sm.prims[i] = src[i];
+    for (int i = tid; i < a.n_prims * 4; i += kWarps * 32) sm.prims[i] = src[i];
     // the particle's screen box, clipped to the ROI, in 16x4 units
-    int u0 = INT_MAX, v0 = INT_MAX, u1 = INT_MIN, v1 = INT_MIN;
-    for (int i = lane; i < a.n_prims; i += 32) {
-        const float4 r3 = src[4 * i + 3];
-        u0 = min(u0, lo_i16(r3.z));
-        v0 = min(v0, hi_i16(r3.z));
-        u1 = max(u1, lo_i16(r3.w));
-        v1 = max(v1, hi_i16(r3.w));
-    }
+    if (warp == 0) {
+        int u0 = INT_MAX, v0 = INT_MAX, u1 = INT_MIN, v1 = INT_MIN;
+        for (int i = lane; i < a.n_prims; i += 32) {
+            const float4 r3 = src[4 * i + 3];
+            u0 = min(u0, lo_i16(r3.z));
+            v0 = min(v0, hi_i16(r3.z));
+            u1 = max(u1, lo_i16(r3.w));
+            v1 = max(v1, hi_i16(r3.w));
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        u0 = min(u0, __shfl_xor_sync(0xffffffffu, u0, o));
-        v0 = min(v0, __shfl_xor_sync(0xffffffffu, v0, o));
-        u1 = max(u1, __shfl_xor_sync(0xffffffffu, u1, o));
-        v1 = max(v1, __shfl_xor_sync(0xffffffffu, v1, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            u0 = min(u0, __shfl_xor_sync(0xffffffffu, u0, o));
+            v0 = min(v0, __shfl_xor_sync(0xffffffffu, v0, o));
+            u1 = max(u1, __shfl_xor_sync(0xffffffffu, u1, o));
+            v1 = max(v1, __shfl_xor_sync(0xffffffffu, v1, o));
+        }
+        if (lane == 0) {
+            u0 = max(u0, 0);
+            v0 = max(v0, 0);
+            u1 = min(u1, a.W - 1);
+            v1 = min(v1, a.H - 1);
+            const int xa = u0 & ~15;  // TMA: the uint8 skin needs x at a multiple of 16 bytes
+            const bool empty = u0 > u1 || v0 > v1;
+            const int nux = empty ? 1 : (u1 + 1 - xa + kUW - 1) / kUW;
+            sm.box[0] = xa;
+            sm.box[1] = v0;
+            sm.box[2] = nux;
+            sm.box[3] = empty ? 0 : nux * ((v1 - v0 + kUH) / kUH);
+        }
     }
-    u0 = max(u0, 0);
-    v0 = max(v0, 0);
-    u1 = min(u1, a.W - 1);
-    v1 = min(v1, a.H - 1);
-    const int xa = u0 & ~15;  // TMA: the uint8 skin needs x at a multiple of 16 bytes
-    const bool empty = u0 > u1 || v0 > v1;
-    const int nux = empty ? 1 : (u1 + 1 - xa + kUW - 1) / kUW;
-    const int n_units = empty ? 0 : nux * ((v1 - v0 + kUH) / kUH);
-    __syncwarp();
+    __syncthreads();
+    const int xa = sm.box[0], v0 = sm.box[1], nux = sm.box[2], n_units = sm.box[3];
     const float kcp = a.kc[p];
 
     if (n_units == 0) {  // nothing of the hand inside the ROI: E is the baseline
         pdl_launch_dependents();
-        if (blockIdx.x == 0 && lane == 0) {
+        if (blockIdx.x == 0 && tid == 0) {
             const uint32_t n_valid = a.stats[0], n_skin = a.stats[1];
             const float t_sum = a.d_M * (float)n_valid;
             const float D = n_skin == 0 ? a.lambda : t_sum / (float)n_skin + a.lambda;
@@ -273,29 +284,38 @@ __global__ void __launch_bounds__(32, 24)
     uint32_t phases = 0u;  // bit s: parity of stage s's next completion
     bool ok = true;
     const int lx = lane & 7, ly = lane >> 3;
-    const int stride = gridDim.x;
-    int u = blockIdx.x;
-    int s = 0;  // stage of unit u
+    // units of this warp: u = g, g + stride, ... ; their (column, row) advance
+    // without divisions
+    const int stride = gridDim.x * kWarps;
+    const int sx = stride % nux, sy = stride / nux;
+    int u = blockIdx.x * kWarps + warp;
+    int ux = u % nux, uy = u / nux;  // unit u
+    int s = 0;                       // stage of unit u
     uint64_t mk[kSub];
-    auto prepare = [&](int unit, int stage, uint64_t m[kSub]) {
-        const int x0 = xa + kUW * (unit % nux), y0 = v0 + kUH * (unit / nux);
+    auto prepare = [&](int cx, int cy, int stage, uint64_t m[kSub]) {
+        const int x0 = xa + kUW * cx, y0 = v0 + kUH * cy;
         cull_unit(sm, a.n_prims, lane, x0, y0, m);
         if ((m[0] | m[1]) && lane == 0) {
-            unsigned char* t = sm.tile[stage];
-            mbar_arrive_expect_tx(&sm.bar[stage], tx_bytes);
-            tma_load_2d(t, &tm_depth, x0, y0, &sm.bar[stage]);
-            tma_load_2d(t + 256, &tm_skin, x0, y0, &sm.bar[stage]);
+            unsigned char* t = sm.tile[warp][stage];
+            mbar_arrive_expect_tx(&sm.bar[warp][stage], tx_bytes);
+            tma_load_2d(t, &tm_depth, x0, y0, &sm.bar[warp][stage]);
+            tma_load_2d(t + 256, &tm_skin, x0, y0, &sm.bar[warp][stage]);
         }
     };
     mk[0] = mk[1] = 0;
-    if (u < n_units) prepare(u, 0, mk);
+    if (u < n_units) prepare(ux, uy, 0, mk);
     while (u < n_units && ok) {
         const int un = u + stride;
+        int nx = ux + sx, ny = uy + sy;
+        if (nx >= nux) {
+            nx -= nux;
+            ++ny;
+        }
         uint64_t mn[kSub] = {0, 0};
-        if (un < n_units) prepare(un, s ^ 1, mn);  // look-ahead: cull and start the next tile
+        if (un < n_units) prepare(nx, ny, s ^ 1, mn);  // look-ahead: cull and start the next tile
         const uint64_t any = mk[0] | mk[1];
         if (any) {
-            const int x0 = xa + kUW * (u % nux), y0 = v0 + kUH * (u / nux);
+            const int x0 = xa + kUW * ux, y0 = v0 + kUH * uy;
             const int px0 = x0 + lx, py = y0 + ly;
             const float ra[2] = {fmaf((float)px0, a.inv_fx, a.off_x), fmaf((float)(px0 + 8), a.inv_fx, a.off_x)};
             const float rb = fmaf((float)py, a.inv_fy, a.off_y);
@@ -320,14 +340,16 @@ __global__ void __launch_bounds__(32, 24)
                     }
                 }
             }
-            ok = mbar_wait_bounded(&sm.bar[s], (phases >> s) & 1u, a.status);
+            ok = mbar_wait_bounded(&sm.bar[warp][s], (phases >> s) & 1u, a.status);
             phases ^= 1u << s;
-            const unsigned char* t = sm.tile[s];
+            const unsigned char* t = sm.tile[warp][s];
 #pragma unroll
             for (int q = 0; q < kSub; ++q) {
                 const int xr = lx + 8 * q;
                 const int px = x0 + xr;
-                if (ok && z[q] < INFINITY && px < a.W && py < a.H) {
+                const bool hit = ok && z[q] < INFINITY && px < a.W && py < a.H;
+                if (!__any_sync(0xffffffffu, hit)) continue;  // nothing rendered in this half
+                if (hit) {
                     const int oi = ly * kUW + xr;
                     const float od = a.depth_f32 ? reinterpret_cast<const float*>(t)[oi]
                                                  : (float)reinterpret_cast<const uint16_t*>(t)[oi];
@@ -344,10 +366,12 @@ __global__ void __launch_bounds__(32, 24)
         mk[0] = mn[0];
         mk[1] = mn[1];
         u = un;
+        ux = nx;
+        uy = ny;
         s ^= 1;
     }
     // a unit prepared but never processed (a wait timed out) leaves no copy behind
-    if (!ok && u < n_units && (mk[0] | mk[1])) mbar_wait_bounded(&sm.bar[s], (phases >> s) & 1u, a.status);
+    if (!ok && u < n_units && (mk[0] | mk[1])) mbar_wait_bounded(&sm.bar[warp][s], (phases >> s) & 1u, a.status);
 
     // the next kernel may start launching once every warp is past its units (it
     // still waits for this grid to finish before it reads E)
@@ -369,7 +393,7 @@ __global__ void __launch_bounds__(32, 24)
         // acquire: the last warp sees every other warp's sums
         uint32_t done;
         asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(done) : "l"(&wk->exited) : "memory");
-        if (done == gridDim.x - 1) {
+        if (done == gridDim.x * kWarps - 1) {
             const long long tf = (long long)atomicAdd(&wk->t_fix, 0ull);
             const uint32_t sa = atomicAdd(&wk->n_and, 0u), so_d = atomicAdd(&wk->n_or, 0u);
             const uint32_t sh = atomicAdd(&wk->n_hit, 0u);
@@ -434,7 +458,7 @@ cudaError_t launch_render_score(const CUtensorMap& tm_depth, const CUtensorMap& 
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(args.K, args.P);
-    cfg.blockDim = dim3(32);
+    cfg.blockDim = dim3(kWarps * 32);
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

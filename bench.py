@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample")
     ap.add_argument("--profile", action="store_true", help="short run for an ncu launch list")
     ap.add_argument("--no-roofline", action="store_true", help="skip the render roofline replay")
+    ap.add_argument("--workload", choices=["kinect", "batch"], default="kinect",
+                    help="kinect: one 320x240 sequence (the headline); batch: 64 sequences with uneven ROIs and P")
     return ap.parse_args()
 
 
@@ -176,11 +178,12 @@ class ClockSampler:
 
 # ---- synthetic frames ----------------------------------------------------------------------
 
-def make_frames(seed: int, frames: int, hs, I, model, cam, device):
+def make_frames(seed: int, frames: int, hs, I, model, cam, device, W=W, H=H, traj=None, keep_device=True):
     """Render the ground-truth trajectory with the CUDA renderer (P = 1 debug
     output), corrupt it like a Kinect frame, return device observations."""
     import torch
-    traj = I.trajectory(seed, frames).astype(np.float32)
+    if traj is None:
+        traj = I.trajectory(seed, frames).astype(np.float32)
     dummy = hs.Obs.from_numpy(np.zeros((H, W), np.uint16), np.zeros((H, W), np.uint8), device)
     hs.hs_obs_prepare(dummy)
     prims = torch.zeros(1, model.n_prims, 16, device=device)
@@ -196,22 +199,26 @@ def make_frames(seed: int, frames: int, hs, I, model, cam, device):
         depth = dd[0].cpu().numpy().astype(np.float64)
         hit = (dm[0].cpu().numpy() & 1) > 0
         d16, skin = I.kinect_observation(depth, hit, seed * 100 + f)
-        obs.append(hs.Obs.from_numpy(d16, skin, device))
+        if keep_device:
+            obs.append(hs.Obs.from_numpy(d16, skin, device))
         host.append((d16, skin))
     return traj, obs, host
 
 
-def algorithmic_flops(box_words: np.ndarray, kinds: np.ndarray) -> float:
+def algorithmic_flops(box_words: np.ndarray, kinds: np.ndarray, Wp=W, Hp=H) -> float:
     """FP32 work of one render_score_batch launch: for every particle and
     primitive, the pixels of its conservative box inside the ROI (pixel-exact
     box culling) times the per-test tally of its kind.  box_words: the last two
-    words of every HsPrim record, [P, n_prims, 2] float32 holding int16 boxes."""
+    words of every HsPrim record, [P, n_prims, 2] float32 holding int16 boxes.
+    Wp, Hp: the ROI size, or per-particle arrays [P] for a batch."""
     box = np.ascontiguousarray(box_words).view(np.int16).reshape(box_words.shape[0], box_words.shape[1], 4)
-    u0 = np.clip(box[..., 0], 0, W - 1)
-    v0 = np.clip(box[..., 1], 0, H - 1)
-    u1 = np.clip(box[..., 2], 0, W - 1)
-    v1 = np.clip(box[..., 3], 0, H - 1)
-    inside = (box[..., 2] >= 0) & (box[..., 3] >= 0) & (box[..., 0] < W) & (box[..., 1] < H)
+    Wp = np.broadcast_to(np.asarray(Wp), (box.shape[0],))[:, None]
+    Hp = np.broadcast_to(np.asarray(Hp), (box.shape[0],))[:, None]
+    u0 = np.clip(box[..., 0], 0, Wp - 1)
+    v0 = np.clip(box[..., 1], 0, Hp - 1)
+    u1 = np.clip(box[..., 2], 0, Wp - 1)
+    v1 = np.clip(box[..., 3], 0, Hp - 1)
+    inside = (box[..., 2] >= 0) & (box[..., 3] >= 0) & (box[..., 0] < Wp) & (box[..., 1] < Hp)
     area = np.where(inside, (u1 - u0 + 1) * (v1 - v0 + 1), 0).astype(np.float64)
     per_kind = np.array([FLOP_PER_TEST[int(k)] for k in kinds], np.float64)
     return float((area * per_kind[None, :]).sum())
@@ -280,6 +287,208 @@ def run_reference(args, rank):
     return 0
 
 
+# ---- many sequences at once -------------------------------------------------------------------
+
+BATCH_SEQ, BATCH_FRAMES = 64, 8
+BATCH_METRIC = "hypothesis evals/s (render+cost, 64 sequences, 48-256 px ROIs)"
+BATCH_WORKLOAD = ("batched tracking: 64 independent sequences, square ROIs with sides uniform in [48, 256] px "
+                  "(Kinect view scaled to the ROI), particles per sequence from {32, 64, 128, 256}, 40 generations, "
+                  "uint16 depth with the Kinect-scale noise recipe")
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    k = min(len(xs) - 1, max(0, int(math.ceil(q / 100.0 * len(xs))) - 1))
+    return xs[k]
+
+
+def run_batch(args, rank, world, local):
+    import torch
+    from paper_2005_07068_b300 import build as B
+    from paper_2005_07068_b300 import handscore as hs
+    from paper_2005_07068_b300 import inputs as I
+    from paper_2005_07068_b300 import replicas as R
+    from paper_2005_07068_b300.tracker import BatchTracker, PackedObs
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    peaks = measured_peaks()
+    seed = R.replica_seed(I.CONFIG_SEED_BASE + 4, rank)
+    sizes, Ps, seq_seeds = I.batch_workload(seed, BATCH_SEQ)
+    g = I.hand_geometry()
+    lo, hi = (a.astype(np.float32) for a in I.search_limits())
+    model = hs.Model.from_geometry(g, lo, hi)
+    frames = BATCH_FRAMES
+    cams, trajs = [], []
+    store = [PackedObs(sizes, device=dev) for _ in range(frames)]  # resident frames (+ pinned twins)
+    for q, (Wq, Hq) in enumerate(sizes):
+        ct = I.kinect_camera(Wq, Hq)
+        cams.append(hs.camera(ct.fx, ct.fy, ct.cx, ct.cy))
+        traj, _, host = make_frames(seq_seeds[q], frames, hs, I, model, cams[q], dev, W=Wq, H=Hq,
+                                    keep_device=False)
+        trajs.append(traj)
+        for f in range(frames):
+            store[f].write_host(q, *host[f])
+    for st in store:
+        st.upload(non_blocking=False)
+    staging = PackedObs(sizes, device=dev, pinned=False)  # the buffers the batch is bound to
+    batch = hs.Batch(model, staging.obs, cams, Ps, seq_seeds)
+    trk = BatchTracker(model, batch, GENS, device=dev)
+    gt0 = torch.from_numpy(np.stack([t[0] for t in trajs])).to(dev)
+    graphs = [trk.graph(f, gt0 if f == 0 else None) for f in range(frames)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    evals_frame = trk.evals_per_frame()
+
+    def step(i):
+        f = i % frames
+        staging.dev.copy_(store[f].dev)  # this frame of every sequence into the bound buffers
+        graphs[f].replay()
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        w0 = time.perf_counter()
+        for i in range(K):
+            flush.zero_()
+            evs[i][0].record(stream)
+            step(args.warmup + i)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        wall = time.perf_counter() - w0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    value, t_dev, _ = R.aggregate(sum(step_ms) / 1e3, K * evals_frame, dev)
+
+    # roofline: the render launches of one frame replayed back to back
+    kinds = g.prims_i[:, 1]
+    Pt = batch.P_total
+    hist_p = torch.zeros(GENS, Pt, model.n_prims, 16, device=dev)
+    hist_k = torch.zeros(GENS, Pt, device=dev)
+    staging.dev.copy_(store[0].dev)
+    cur, nxt = trk.x_buf
+    trk.swarm.x = cur
+    trk.seed_poses.copy_(gt0)
+    hs.hs_obs_prepare_multi(batch)
+    hs.pso_init_multi(model, batch, trk.swarm, trk.seed_poses, trk.scale, 0)
+    hs.pose_fk_multi(model, batch, cur, trk.prims, trk.kc)
+    for gen in range(1, GENS + 1):
+        hist_p[gen - 1].copy_(trk.prims)
+        hist_k[gen - 1].copy_(trk.kc)
+        hs.render_score_multi(model, batch, trk.prims, trk.kc, trk.score, trk.ws, trk.swarm.E)
+        trk.swarm.x = cur
+        hs.pso_step_fk_multi(model, batch, trk.swarm, nxt, trk.pso, 0, gen, trk.prims, trk.kc)
+        cur, nxt = nxt, cur
+    trk.swarm.x = cur
+    E_tmp = torch.zeros(Pt, device=dev)
+
+    def renders():
+        for q in range(GENS):
+            hs.render_score_multi(model, batch, hist_p[q], hist_k[q], trk.score, trk.ws, E_tmp)
+
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        renders()
+    stream.wait_stream(side)
+    rg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(rg, stream=side):
+        renders()
+    rg.replay()
+    torch.cuda.synchronize(dev)
+    a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    a_ev.record(stream)
+    for _ in range(reps):
+        rg.replay()
+    b_ev.record(stream)
+    torch.cuda.synchronize(dev)
+    render_us = a_ev.elapsed_time(b_ev) * 1e3 / (reps * GENS)
+    Wp = np.repeat([w for w, _ in sizes], Ps)
+    Hp = np.repeat([h for _, h in sizes], Ps)
+    flops = [algorithmic_flops(hist_p[q, :, :, 14:16].cpu().numpy(), kinds, Wp, Hp) for q in range(0, GENS, 4)]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2032.0))
+    sm_max = float(peaks.get("sm_max_mhz") or clocks["sm_max_mhz"] or 2032.0)
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flop_launch = sum(flops) / len(flops)
+    achieved = flop_launch / (render_us * 1e-6) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None, "kernel": "render_score_kernel (batch)",
+                "peak_basis": f"FP32: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {sm_max:.0f} MHz "
+                              f"(sm_max_mhz of measured)",
+                "launch_us": render_us, "launches_timed": reps * GENS, "flop_per_launch": flop_launch,
+                "flop_basis": "pixel-exact primitive boxes x per-test FP32 tally (ellipsoid 45, cone 78)",
+                "timing": "CUDA events around a graph of one frame's 40 render_score_multi launches"}
+
+    # end to end: one pinned copy of every sequence's frame, the graph, the results read back
+    e2e = None
+    if not args.no_e2e:
+        out = torch.zeros(batch.S, 27, dtype=torch.float32).pin_memory()
+
+        def track(i):
+            f = i % frames
+            staging.dev.copy_(store[f].host, non_blocking=True)
+            graphs[f].replay()
+            out[:, :26].copy_(trk.swarm.gbest, non_blocking=True)
+            out[:, 26].copy_(trk.swarm.gbest_E, non_blocking=True)
+
+        for i in range(args.warmup):
+            track(i)
+        torch.cuda.synchronize(dev)
+        ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for i in range(K):
+            flush.zero_()
+            ee[i][0].record(stream)
+            track(args.warmup + i)
+            ee[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_value, _, _ = R.aggregate(sum(a.elapsed_time(b) for a, b in ee) / 1e3, K * evals_frame, dev)
+        e2e = {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": int(staging.nbytes),
+               "d2h_bytes_per_step": int(out.numel() * out.element_size())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, gens, cores = time_oracle(seed, args.cpu_seconds)
+        cpu = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
+               "sample": f"one 320x240 Kinect-scale frame (oracle-rendered), {PARTICLES} particles x {gens} "
+                         f"generations of the FP64 oracle; its cost per evaluation grows with the ROI area "
+                         f"(76800 px here, {np.mean([w * h for w, h in sizes]):.0f} px mean in this batch)"}
+    if rank == 0:
+        line = {"metric": BATCH_METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": BATCH_WORKLOAD, "sequences": batch.S, "particles_total": Pt,
+                           "roi_px_mean": float(np.mean([w * h for w, h in sizes])), "generations": GENS,
+                           "frames": frames, "step": f"one frame of every sequence = one CUDA graph "
+                                                     f"({trk.launches_per_frame()} kernels) + one frame copy",
+                           "l2": "flushed between steps (256 MiB write outside the step events)",
+                           "parallelism": f"replicas x{world}", "wall_s": wall},
+                "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99),
+                               "what": "per-frame latency of every sequence (one step advances all of them)"},
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
+                "gpu_launches": K * trk.launches_per_frame()}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 # ---- the native arm ------------------------------------------------------------------------
 
 def main():
@@ -289,6 +498,8 @@ def main():
     local = _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.workload == "batch":
+        return run_batch(args, rank, world, local)
 
     import torch
     from paper_2005_07068_b300 import build as B
@@ -461,7 +672,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "roi": [W, H], "particles": PARTICLES, "generations": GENS,
-                           "frames": frames, "step": "one frame = one CUDA graph (2 + 3 x 40 kernels)",
+                           "frames": frames,
+                           "step": f"one frame = one CUDA graph ({trk.launches_per_frame()} kernels)",
                            "l2": "flushed between steps (256 MiB write outside the step events)",
                            "parallelism": f"replicas x{world}", "wall_s": wall},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,

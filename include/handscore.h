@@ -53,7 +53,7 @@ typedef struct CUstream_st* hs_stream_t;
 #define HS_NDOF            26
 #define HS_MAX_BONES       32
 #define HS_MAX_PRIMS       64
-#define HS_MAX_PARTICLES   65536
+#define HS_MAX_PARTICLES   65535  /* particles per call (the render grid's y extent) */
 #define HS_MAX_ROI         8192   /* W, H <= HS_MAX_ROI */
 
 /* ---- hand model (Section II.A, Fig. 2) ----------------------------------- */
@@ -280,6 +280,58 @@ int render_score_batch_noalloc(const HsModel* model, const HsObs* obs, const HsC
 int pso_step_fk(const HsModel* model, const HsSwarm* swarm, float* x_next, int P, const HsPsoParams* params,
                 uint64_t seed, uint32_t frame, uint32_t gen, const HsCamera* cam, HsPrim* prims, float* kc,
                 hs_stream_t stream);
+
+/* ---- batches: many independent swarms per launch ----------------------------------
+ * A batch binds S swarms (sequences), each with its own observation buffers,
+ * camera, particle count, mutation count and Philox key, so that one launch
+ * scores or updates every particle of every swarm (the paper's parallelism
+ * "between particles" extended across sequences, Section IV).  Particle arrays
+ * are concatenated over the swarms ([P_total][...], swarm s first at its
+ * offset); per-swarm arrays are gbest [S][26], gbest_E [S], seed poses [S][26].
+ * Random numbers use each particle's index within its swarm and the swarm's
+ * key, so a batch reproduces S separate single-swarm runs exactly. */
+#define HS_MAX_SWARMS 4096
+typedef struct {
+    HsObs obs;          /* this swarm's observation (buffers stay bound to the batch) */
+    HsCamera cam;
+    int32_t P;          /* particles, 1..HS_FUSED_MAX_PARTICLES */
+    int32_t n_mutate;   /* particles mutated every mutate_every generations (paper: P / 2) */
+    uint64_t seed;      /* Philox key of this swarm */
+} HsSwarmDesc;
+
+/* opaque host object describing a batch; its device part lives in the caller's buffer */
+typedef struct HsBatch HsBatch;
+
+/* Bytes of the device buffer a batch needs (views with TMA descriptors, the
+ * particle-to-swarm table).  Errors: HS_ERR_ARG, HS_ERR_SIZE. */
+int hs_batch_buffer_size(const HsSwarmDesc* swarms, int S, size_t* bytes);
+/* Validate the swarms, encode their TMA descriptors and write the batch into
+ * `buffer` (device, 256-byte aligned, hs_batch_buffer_size bytes; synchronous
+ * on `stream`).  Allocates host memory for the handle only.  The observation
+ * buffers must stay valid while the batch is used; new frames are copied into
+ * them.  Errors: HS_ERR_ARG, HS_ERR_ALIGN, HS_ERR_SIZE, HS_ERR_CUDA. */
+int hs_batch_create(const HsModel* model, const HsSwarmDesc* swarms, int S, void* buffer, size_t bytes,
+                    hs_stream_t stream, HsBatch** out);
+int hs_batch_destroy(HsBatch* batch);
+int hs_batch_particles(const HsBatch* batch, int* P_total);
+/* hs_obs_prepare for every swarm of the batch (two launches). */
+int hs_obs_prepare_multi(const HsBatch* batch, hs_stream_t stream);
+/* pose_fk over all P_total particles, each with its swarm's camera. */
+int pose_fk_multi(const HsModel* model, const HsBatch* batch, const float* poses, HsPrim* prims, float* kc,
+                  hs_stream_t stream);
+/* render_score_batch over all particles of all swarms in one launch (each
+ * particle against its swarm's observation); workspace: hs_workspace_size(P_total). */
+int render_score_multi(const HsModel* model, const HsBatch* batch, const HsPrim* prims, const float* kc,
+                       const HsScoreParams* params, void* workspace, size_t workspace_bytes, float* E,
+                       HsParts* parts, hs_stream_t stream);
+/* pso_init for every swarm: seed_poses device [S][26], scale host [26]. */
+int pso_init_multi(const HsModel* model, const HsBatch* batch, const HsSwarm* swarm, const float* seed_poses,
+                   const float* scale, uint32_t frame, hs_stream_t stream);
+/* pso_step_fk for every swarm in one launch (n_mutate from each swarm's
+ * descriptor; c1, c2 and mutate_every from params). */
+int pso_step_fk_multi(const HsModel* model, const HsBatch* batch, const HsSwarm* swarm, float* x_next,
+                      const HsPsoParams* params, uint32_t frame, uint32_t gen, HsPrim* prims, float* kc,
+                      hs_stream_t stream);
 
 /* Read (and optionally clear) the device status word of the current device.
  * Synchronises the device.  out: host.  Errors: HS_ERR_ARG, HS_ERR_CUDA. */

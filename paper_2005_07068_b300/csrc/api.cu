@@ -97,6 +97,27 @@ struct HsModel {
     Limits lim;
 };
 
+struct HsBatch {
+    int S, P_total, P_max, max_H;
+    BatchDev dev;  // device views / particle-to-swarm table (inside the caller's buffer)
+};
+
+namespace {
+__global__ void zero_stats_kernel(const BatchDev b)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < b.S) {
+        b.views[s].stats[0] = 0u;
+        b.views[s].stats[1] = 0u;
+    }
+}
+
+size_t batch_bytes(int S, long long P_total)
+{
+    return 256 + (size_t)S * sizeof(SwarmView) + ((size_t)P_total * 4 + 255) / 256 * 256;
+}
+}  // namespace
+
 extern "C" {
 
 int hs_version(void) { return 100; }
@@ -260,7 +281,7 @@ int pose_fk(const HsModel* model, const float* poses, int P, const HsCamera* cam
     if (P < 0 || P > HS_MAX_PARTICLES) return HS_ERR_SIZE;
     if (!aligned16(prims)) return HS_ERR_ALIGN;
     if (P == 0) return HS_OK;
-    FkArgs a;
+    FkArgs a = {};
     a.poses = poses;
     a.P = P;
     a.fx = cam->fx;
@@ -312,7 +333,7 @@ int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* c
     if (K > kMaxK) K = kMaxK;
     if (K < 1) K = 1;
 
-    RenderArgs a;
+    RenderArgs a = {};
     a.prims = reinterpret_cast<const float4*>(prims);
     a.kc = kc;
     a.P = P;
@@ -346,7 +367,7 @@ int pso_init(const HsModel* model, const HsSwarm* sw, int P, const float* seed_p
     if (!model || !sw || !seed_pose || !scale) return HS_ERR_ARG;
     if (!sw->x || !sw->v || !sw->pbest || !sw->pbest_E || !sw->gbest || !sw->gbest_E) return HS_ERR_ARG;
     if (P < 1 || P > HS_MAX_PARTICLES) return HS_ERR_SIZE;
-    PsoInitArgs a;
+    PsoInitArgs a = {};
     a.x = sw->x;
     a.v = sw->v;
     a.pbest = sw->pbest;
@@ -374,7 +395,7 @@ int pso_step(const HsModel* model, const HsSwarm* sw, int P, const HsPsoParams* 
     const double psi = (double)prm->c1 + (double)prm->c2;
     if (!std::isfinite(psi) || prm->c1 < 0.f || prm->c2 < 0.f || psi <= 4.0) return HS_ERR_ARG;
     if (prm->mutate_every > 0 && (prm->n_mutate < 0 || prm->n_mutate > P)) return HS_ERR_ARG;
-    PsoStepArgs a;
+    PsoStepArgs a = {};
     a.x = sw->x;
     a.v = sw->v;
     a.pbest = sw->pbest;
@@ -410,7 +431,7 @@ int pso_step_fk(const HsModel* model, const HsSwarm* sw, float* x_next, int P, c
     const double psi = (double)prm->c1 + (double)prm->c2;
     if (!std::isfinite(psi) || prm->c1 < 0.f || prm->c2 < 0.f || psi <= 4.0) return HS_ERR_ARG;
     if (prm->mutate_every > 0 && (prm->n_mutate < 0 || prm->n_mutate > P)) return HS_ERR_ARG;
-    PsoFkArgs a;
+    PsoFkArgs a = {};
     a.x = sw->x;
     a.x_next = x_next;
     a.v = sw->v;
@@ -433,6 +454,229 @@ int pso_step_fk(const HsModel* model, const HsSwarm* sw, float* x_next, int P, c
     a.prims = reinterpret_cast<float4*>(prims);
     a.kc = kc;
     if ((rc = status_ptr(&a.status))) return rc;
+    return launch_pso_step_fk(model->dev, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+// ---- batches of independent swarms ------------------------------------------------
+
+int hs_batch_buffer_size(const HsSwarmDesc* sw, int S, size_t* bytes)
+{
+    if (!sw || !bytes) return HS_ERR_ARG;
+    if (S < 1 || S > HS_MAX_SWARMS) return HS_ERR_SIZE;
+    long long total = 0;
+    for (int s = 0; s < S; ++s) {
+        if (sw[s].P < 1 || sw[s].P > HS_FUSED_MAX_PARTICLES) return HS_ERR_SIZE;
+        total += sw[s].P;
+    }
+    if (total > HS_MAX_PARTICLES) return HS_ERR_SIZE;
+    *bytes = batch_bytes(S, total);
+    return HS_OK;
+}
+
+int hs_batch_create(const HsModel* model, const HsSwarmDesc* sw, int S, void* buffer, size_t bytes,
+                    hs_stream_t stream, HsBatch** out)
+{
+    if (!model || !sw || !buffer || !out) return HS_ERR_ARG;
+    size_t need = 0;
+    int rc = hs_batch_buffer_size(sw, S, &need);
+    if (rc) return rc;
+    if (bytes < need) return HS_ERR_SIZE;
+    if ((reinterpret_cast<uintptr_t>(buffer) & 255u) != 0) return HS_ERR_ALIGN;
+    for (int s = 0; s < S; ++s) {
+        if ((rc = validate_obs(&sw[s].obs))) return rc;
+        if ((rc = validate_cam(&sw[s].cam))) return rc;
+        if (sw[s].n_mutate < 0 || sw[s].n_mutate > sw[s].P) return HS_ERR_ARG;
+    }
+    // host image of the buffer: [256-byte header][S views][particle -> swarm table]
+    unsigned char* img = static_cast<unsigned char*>(std::calloc(1, need));
+    if (!img) return HS_ERR_ARG;
+    SwarmView* views = reinterpret_cast<SwarmView*>(img + 256);
+    int32_t* sid = reinterpret_cast<int32_t*>(img + 256 + (size_t)S * sizeof(SwarmView));
+    int off = 0, P_max = 0, max_H = 0;
+    for (int s = 0; s < S && rc == HS_OK; ++s) {
+        const HsObs& o = sw[s].obs;
+        const HsCamera& c = sw[s].cam;
+        SwarmView& v = views[s];
+        const bool f32 = o.depth_type == HS_DEPTH_F32;
+        rc = encode_tile_map(&v.tm_depth, o.depth, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                             f32 ? 4 : 2, o.W, o.H, o.depth_pitch);
+        if (rc == HS_OK)
+            rc = encode_tile_map(&v.tm_skin, o.skin, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, o.W, o.H, o.skin_pitch);
+        v.W = o.W;
+        v.H = o.H;
+        v.depth_f32 = f32;
+        v.P = sw[s].P;
+        v.offset = off;
+        v.n_mutate = sw[s].n_mutate;
+        v.depth_pitch = o.depth_pitch;
+        v.skin_pitch = o.skin_pitch;
+        v.inv_fx = (float)(1.0 / (double)c.fx);
+        v.inv_fy = (float)(1.0 / (double)c.fy);
+        v.off_x = (float)((0.5 - (double)c.cx) / (double)c.fx);
+        v.off_y = (float)((0.5 - (double)c.cy) / (double)c.fy);
+        v.fx = c.fx;
+        v.fy = c.fy;
+        v.cx = c.cx;
+        v.cy = c.cy;
+        v.depth = static_cast<const unsigned char*>(o.depth);
+        v.skin = o.skin;
+        v.stats = o.stats;
+        v.key0 = (uint32_t)sw[s].seed;
+        v.key1 = (uint32_t)(sw[s].seed >> 32);
+        for (int i = 0; i < sw[s].P; ++i) sid[off + i] = s;
+        off += sw[s].P;
+        if (sw[s].P > P_max) P_max = sw[s].P;
+        if (o.H > max_H) max_H = o.H;
+    }
+    if (rc == HS_OK && cudaMemcpyAsync(buffer, img, need, cudaMemcpyHostToDevice, (cudaStream_t)stream) != cudaSuccess)
+        rc = HS_ERR_CUDA;
+    if (rc == HS_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) rc = HS_ERR_CUDA;
+    std::free(img);
+    if (rc) return rc;
+    HsBatch* b = static_cast<HsBatch*>(std::calloc(1, sizeof(HsBatch)));
+    if (!b) return HS_ERR_ARG;
+    b->S = S;
+    b->P_total = off;
+    b->P_max = P_max;
+    b->max_H = max_H;
+    unsigned char* dev = static_cast<unsigned char*>(buffer);
+    b->dev.S = S;
+    b->dev.P_total = off;
+    b->dev.views = reinterpret_cast<const SwarmView*>(dev + 256);
+    b->dev.sid = reinterpret_cast<const int32_t*>(dev + 256 + (size_t)S * sizeof(SwarmView));
+    *out = b;
+    return HS_OK;
+}
+
+int hs_batch_destroy(HsBatch* b)
+{
+    if (!b) return HS_ERR_ARG;
+    std::free(b);
+    return HS_OK;
+}
+
+int hs_batch_particles(const HsBatch* b, int* P_total)
+{
+    if (!b || !P_total) return HS_ERR_ARG;
+    *P_total = b->P_total;
+    return HS_OK;
+}
+
+int hs_obs_prepare_multi(const HsBatch* b, hs_stream_t stream)
+{
+    if (!b) return HS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    zero_stats_kernel<<<(b->S + 127) / 128, 128, 0, s>>>(b->dev);
+    if (cudaGetLastError() != cudaSuccess) return HS_ERR_CUDA;
+    return launch_obs_stats_multi(b->dev, b->max_H, s) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int pose_fk_multi(const HsModel* model, const HsBatch* b, const float* poses, HsPrim* prims, float* kc,
+                  hs_stream_t stream)
+{
+    if (!model || !b || !poses || !prims || !kc) return HS_ERR_ARG;
+    if (!aligned16(prims)) return HS_ERR_ALIGN;
+    FkArgs a = {};
+    a.poses = poses;
+    a.P = b->P_total;
+    a.fx = a.fy = 1.f;
+    a.prims = reinterpret_cast<float4*>(prims);
+    a.kc = kc;
+    a.batch = b->dev;
+    int rc = status_ptr(&a.status);
+    if (rc) return rc;
+    return launch_fk(model->dev, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int render_score_multi(const HsModel* model, const HsBatch* b, const HsPrim* prims, const float* kc,
+                       const HsScoreParams* params, void* workspace, size_t workspace_bytes, float* E, HsParts* parts,
+                       hs_stream_t stream)
+{
+    if (!model || !b || !prims || !kc || !params || !E || !workspace) return HS_ERR_ARG;
+    if (!std::isfinite(params->d_m) || !std::isfinite(params->d_M) || !std::isfinite(params->lambda) ||
+        !std::isfinite(params->lambda_k) || params->d_m < 0.f || params->d_M < 0.f || params->d_M >= 127.f)
+        return HS_ERR_ARG;
+    if (!aligned16(prims) || !aligned16(workspace)) return HS_ERR_ALIGN;
+    size_t need = 0;
+    hs_workspace_size(b->P_total, &need);
+    if (workspace_bytes < need) return HS_ERR_SIZE;
+    RenderArgs a = {};
+    a.prims = reinterpret_cast<const float4*>(prims);
+    a.kc = kc;
+    a.P = b->P_total;
+    a.n_prims = model->dev.n_prims;
+    int K = kTargetCtas / b->P_total;
+    if (K > kMaxK) K = kMaxK;
+    if (K < 1) K = 1;
+    a.K = K;
+    a.d_m = params->d_m;
+    a.d_M = params->d_M;
+    a.lambda = params->lambda;
+    a.lambda_k = params->lambda_k;
+    a.work = static_cast<HsParticleWork*>(workspace);
+    a.E = E;
+    a.parts = parts;
+    a.batch = b->dev;
+    int rc = status_ptr(&a.status);
+    if (rc) return rc;
+    CUtensorMap unused = {};  // the maps come from the batch views
+    return launch_render_score(unused, unused, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int pso_init_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw, const float* seed_poses,
+                   const float* scale, uint32_t frame, hs_stream_t stream)
+{
+    if (!model || !b || !sw || !seed_poses || !scale) return HS_ERR_ARG;
+    if (!sw->x || !sw->v || !sw->pbest || !sw->pbest_E || !sw->gbest || !sw->gbest_E) return HS_ERR_ARG;
+    PsoInitArgs a = {};
+    a.x = sw->x;
+    a.v = sw->v;
+    a.pbest = sw->pbest;
+    a.pbest_E = sw->pbest_E;
+    a.gbest = sw->gbest;
+    a.gbest_E = sw->gbest_E;
+    a.seed_pose = seed_poses;
+    for (int d = 0; d < HS_NDOF; ++d) {
+        if (!std::isfinite(scale[d]) || scale[d] < 0.f) return HS_ERR_ARG;
+        a.scale[d] = scale[d];
+    }
+    a.P = b->P_total;
+    a.frame = frame;
+    a.batch = b->dev;
+    return launch_pso_init(model->lim, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int pso_step_fk_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw, float* x_next,
+                      const HsPsoParams* prm, uint32_t frame, uint32_t gen, HsPrim* prims, float* kc,
+                      hs_stream_t stream)
+{
+    if (!model || !b || !sw || !prm || !x_next || !prims || !kc) return HS_ERR_ARG;
+    if (!sw->x || !sw->v || !sw->pbest || !sw->pbest_E || !sw->gbest || !sw->gbest_E || !sw->E) return HS_ERR_ARG;
+    if (x_next == sw->x) return HS_ERR_ARG;
+    if (!aligned16(prims)) return HS_ERR_ALIGN;
+    const double psi = (double)prm->c1 + (double)prm->c2;
+    if (!std::isfinite(psi) || prm->c1 < 0.f || prm->c2 < 0.f || psi <= 4.0) return HS_ERR_ARG;
+    PsoFkArgs a = {};
+    a.x = sw->x;
+    a.x_next = x_next;
+    a.v = sw->v;
+    a.pbest = sw->pbest;
+    a.pbest_E = sw->pbest_E;
+    a.gbest = sw->gbest;
+    a.gbest_E = sw->gbest_E;
+    a.E = sw->E;
+    a.P = b->P_max;  // shared memory for the largest swarm; each CTA uses its own swarm's size
+    a.c1 = prm->c1;
+    a.c2 = prm->c2;
+    a.w = (float)(2.0 / std::fabs(2.0 - psi - std::sqrt(psi * psi - 4.0 * psi)));
+    a.mutate = prm->mutate_every > 0 && gen % (uint32_t)prm->mutate_every == 0;
+    a.frame = frame;
+    a.gen = gen;
+    a.prims = reinterpret_cast<float4*>(prims);
+    a.kc = kc;
+    a.batch = b->dev;
+    int rc = status_ptr(&a.status);
+    if (rc) return rc;
     return launch_pso_step_fk(model->dev, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 

@@ -9,8 +9,13 @@ __global__ void __launch_bounds__(64) fk_kernel(const __grid_constant__ DevModel
     __shared__ FkShared sh;
     fk_load_model(sh, model_param);
     const int p = blockIdx.x;
-    fk_particle(sh, a.poses + (size_t)p * kNdof, make_float4(a.fx, a.fy, a.cx, a.cy),
-                a.prims + (size_t)p * model_param.n_prims * 4, a.kc + p, a.status);
+    float4 cam = make_float4(a.fx, a.fy, a.cx, a.cy);
+    if (a.batch.views) {  // the camera of this particle's swarm
+        const SwarmView& v = a.batch.views[a.batch.sid[p]];
+        cam = make_float4(v.fx, v.fy, v.cx, v.cy);
+    }
+    fk_particle(sh, a.poses + (size_t)p * kNdof, cam, a.prims + (size_t)p * model_param.n_prims * 4, a.kc + p,
+                a.status);
 }
 
 cudaError_t launch_fk(const DevModel& model, const FkArgs& args, cudaStream_t stream)

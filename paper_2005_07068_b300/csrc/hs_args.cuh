@@ -8,6 +8,30 @@
 
 namespace hs {
 
+// One swarm of a batch (device memory, written by hs_batch_create): its
+// observation (TMA tensor maps + raw pointers), camera, particle range,
+// mutation count and Philox key.  Particles of swarm s are [offset, offset+P).
+struct alignas(64) SwarmView {
+    CUtensorMap tm_depth;  // 2-D map of the depth image, 16 x 4 boxes
+    CUtensorMap tm_skin;   // 2-D map of the skin mask, 16 x 4 boxes
+    int32_t W, H, depth_f32, P;
+    int32_t offset, n_mutate, depth_pitch, skin_pitch;
+    float inv_fx, inv_fy, off_x, off_y;  // render rays: (u inv_fx + off_x, v inv_fy + off_y, 1)
+    float fx, fy, cx, cy;                // FK projection
+    const unsigned char* depth;
+    const uint8_t* skin;
+    uint32_t* stats;
+    uint32_t key0, key1;
+};
+
+// header of a batch buffer: S views, then the swarm index of every particle
+struct BatchDev {
+    int32_t S, P_total;
+    const SwarmView* views;  // [S]
+    const int32_t* sid;      // [P_total]
+};
+
+
 struct FkArgs {
     const float* poses;  // [P][26]
     int P;
@@ -15,6 +39,7 @@ struct FkArgs {
     float4* prims;       // [P][n_prims][4]
     float* kc;           // [P]
     uint32_t* status;
+    BatchDev batch;      // when set: the camera of particle p's swarm
 };
 
 // per-particle scratch of render_score_batch (32 bytes, zero between calls)
@@ -41,14 +66,16 @@ struct RenderArgs {
     float* dbg_depth;
     uint8_t* dbg_mask;
     uint32_t* status;
+    BatchDev batch;  // batch.views == nullptr: one swarm described by the fields above
 };
 
 struct PsoInitArgs {
     float *x, *v, *pbest, *pbest_E, *gbest, *gbest_E;
-    const float* seed_pose;
+    const float* seed_pose;  // [26], or [S][26] for a batch
     float scale[kNdof];
     int P;
     uint32_t key0, key1, frame;
+    BatchDev batch;  // when set: per-swarm seed pose, key and gbest slot
 };
 
 struct PsoStepArgs {
@@ -74,6 +101,7 @@ struct PsoFkArgs {
     float4* prims;         // [P][n_prims][4]
     float* kc;             // [P]
     uint32_t* status;
+    BatchDev batch;        // when set: every particle works within its own swarm
 };
 
 cudaError_t launch_fk(const DevModel& model, const FkArgs& args, cudaStream_t stream);
@@ -82,6 +110,7 @@ cudaError_t launch_render_score(const CUtensorMap& tm_depth, const CUtensorMap& 
                                 cudaStream_t stream);
 cudaError_t launch_obs_stats(const unsigned char* depth, int depth_pitch, int depth_f32, const uint8_t* skin,
                              int skin_pitch, int W, int H, uint32_t* stats, cudaStream_t stream);
+cudaError_t launch_obs_stats_multi(const BatchDev& batch, int max_H, cudaStream_t stream);
 cudaError_t launch_pso_init(const Limits& lim, const PsoInitArgs& args, cudaStream_t stream);
 cudaError_t launch_pso_step(const Limits& lim, const PsoStepArgs& args, cudaStream_t stream);
 

@@ -24,24 +24,35 @@ __global__ void __launch_bounds__(256) pso_init_kernel(const __grid_constant__ L
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = g / kInitBlocks, j = g % kInitBlocks;
     if (i >= a.P) return;
-    const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamInit << 16) | (uint32_t)j, 0u, a.frame}, a.key0, a.key1);
+    // a batch: particle i is number li of swarm s, with that swarm's key, seed pose and gbest slot
+    int li = i, s = 0;
+    uint32_t k0 = a.key0, k1 = a.key1;
+    if (a.batch.views) {
+        s = a.batch.sid[i];
+        const SwarmView& v = a.batch.views[s];
+        li = i - v.offset;
+        k0 = v.key0;
+        k1 = v.key1;
+    }
+    const float* seed_pose = a.seed_pose + (size_t)s * kNdof;
+    const U4 r = philox4x32_10(U4{(uint32_t)li, (kStreamInit << 16) | (uint32_t)j, 0u, a.frame}, k0, k1);
     const uint32_t u[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
         const int d = 4 * j + l;
         if (d >= kNdof) break;
-        const float sp = a.seed_pose[d];
-        float xv = i == 0 ? sp : fmaf(fmaf(2.f, u01(u[l]), -1.f), a.scale[d], sp);
+        const float sp = seed_pose[d];
+        float xv = li == 0 ? sp : fmaf(fmaf(2.f, u01(u[l]), -1.f), a.scale[d], sp);
         xv = fminf(fmaxf(xv, lim.lo[d]), lim.hi[d]);
         const size_t o = (size_t)i * kNdof + d;
         a.x[o] = xv;
         a.v[o] = 0.f;
         a.pbest[o] = xv;
-        if (i == 0) a.gbest[d] = xv;
+        if (li == 0) a.gbest[(size_t)s * kNdof + d] = xv;
     }
     if (j == 0) {
         a.pbest_E[i] = INFINITY;
-        if (i == 0) a.gbest_E[0] = INFINITY;
+        if (li == 0) a.gbest_E[s] = INFINITY;
     }
 }
 
@@ -178,24 +189,37 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
     __shared__ float s_xn[kNdof];
     __shared__ float red_v[2];
     __shared__ int red_i[2], red_r[2];
-    extern __shared__ float s_e[];  // E [P] then pbest_E [P]
-    float* s_pe = s_e + a.P;
-    const int i = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int P = a.P;
+    extern __shared__ float s_e[];  // E [P] then pbest_E [P] of this particle's swarm
+    const int q = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // the swarm of particle q: particles [off, off + P), q is number i of them
+    int off = 0, P = a.P, n_mutate = a.n_mutate, s = 0;
+    uint32_t k0 = a.key0, k1 = a.key1;
+    float4 cam = a.cam;
+    if (a.batch.views) {
+        s = a.batch.sid[q];
+        const SwarmView& v = a.batch.views[s];
+        off = v.offset;
+        P = v.P;
+        n_mutate = v.n_mutate;
+        k0 = v.key0;
+        k1 = v.key1;
+        cam = make_float4(v.fx, v.fy, v.cx, v.cy);
+    }
+    const int i = q - off;
+    float* s_pe = s_e + P;
     pdl_launch_dependents();
     fk_load_model(sh, model_param);
     // this particle's random numbers depend only on (particle, generation, frame, seed):
     // draw them while the previous kernel finishes
     if (t < kPairBlocks) {
-        const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamPso << 16) | (uint32_t)t, a.gen, a.frame}, a.key0, a.key1);
+        const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamPso << 16) | (uint32_t)t, a.gen, a.frame}, k0, k1);
         s_r[4 * t] = u01(r.x);
         s_r[4 * t + 1] = u01(r.y);
         s_r[4 * t + 2] = u01(r.z);
         s_r[4 * t + 3] = u01(r.w);
     } else if (t >= 32 && t < 32 + kMutBlocks) {
         const int b = t - 32;
-        const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamMutate << 16) | (uint32_t)b, a.gen, a.frame}, a.key0,
-                                   a.key1);
+        const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamMutate << 16) | (uint32_t)b, a.gen, a.frame}, k0, k1);
         s_m[4 * b] = u01(r.x);
         s_m[4 * b + 1] = u01(r.y);
         s_m[4 * b + 2] = u01(r.z);
@@ -204,13 +228,13 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
     pdl_wait();  // E comes from the previous kernel
     float xi = 0.f, pbi = 0.f, vi = 0.f;
     if (t < kNdof) {  // this particle's own state, loaded before the global best is known
-        xi = a.x[(size_t)i * kNdof + t];
-        pbi = a.pbest[(size_t)i * kNdof + t];
-        vi = a.v[(size_t)i * kNdof + t];
+        xi = a.x[(size_t)q * kNdof + t];
+        pbi = a.pbest[(size_t)q * kNdof + t];
+        vi = a.v[(size_t)q * kNdof + t];
     }
     for (int j = t; j < P; j += 64) {
-        s_e[j] = a.E[j];
-        s_pe[j] = a.pbest_E[j];
+        s_e[j] = a.E[off + j];
+        s_pe[j] = a.pbest_E[off + j];
     }
     __syncthreads();
     // global best = argmin_j min(E_j, pbest_E_j) (lowest index on ties, NaN never
@@ -251,14 +275,14 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
     }
     rank = red_r[0] + red_r[1];
     const bool imp = ei < s_pe[i];  // strict improvement of this particle's personal best
-    const bool mutated = a.mutate && rank >= P - a.n_mutate;
+    const bool mutated = a.mutate && rank >= P - n_mutate;
     if (t < kNdof) {
         // the global best's position: its current x if that is its personal best now
         const bool gimp = s_e[g] <= s_pe[g];
-        const float gv = gimp ? a.x[(size_t)g * kNdof + t] : a.pbest[(size_t)g * kNdof + t];
-        if (i == 0) a.gbest[t] = gv;
+        const float gv = gimp ? a.x[(size_t)(off + g) * kNdof + t] : a.pbest[(size_t)(off + g) * kNdof + t];
+        if (i == 0) a.gbest[(size_t)s * kNdof + t] = gv;
         const float pb = imp ? xi : pbi;
-        if (imp) a.pbest[(size_t)i * kNdof + t] = xi;
+        if (imp) a.pbest[(size_t)q * kNdof + t] = xi;
         // Eq. 6-7 for dimension t (r1 = number 2t, r2 = number 2t+1), then clamp;
         // the mutation re-draws a finger dimension and zeroes its velocity
         float acc = fmaf(a.c1 * s_r[2 * t], pb - xi, vi);
@@ -269,22 +293,23 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
             xn = fmaf(s_m[t - 6], sh.model.hi[t] - sh.model.lo[t], sh.model.lo[t]);
             vn = 0.f;
         }
-        a.v[(size_t)i * kNdof + t] = vn;
-        a.x_next[(size_t)i * kNdof + t] = xn;
+        a.v[(size_t)q * kNdof + t] = vn;
+        a.x_next[(size_t)q * kNdof + t] = xn;
         s_xn[t] = xn;
     }
     if (t == 0) {
-        if (imp) a.pbest_E[i] = ei;
-        if (i == 0) a.gbest_E[0] = gE;
+        if (imp) a.pbest_E[q] = ei;
+        if (i == 0) a.gbest_E[s] = gE;
     }
     // FK of the new pose (fk_particle starts with a barrier that publishes s_xn)
-    fk_particle(sh, s_xn, a.cam, a.prims + (size_t)i * sh.model.n_prims * 4, a.kc + i, a.status);
+    fk_particle(sh, s_xn, cam, a.prims + (size_t)q * sh.model.n_prims * 4, a.kc + q, a.status);
 }
 
 cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cudaStream_t stream)
 {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(args.P);
+    // one CTA per particle (all swarms of a batch); shared memory for the largest swarm
+    cfg.gridDim = dim3(args.batch.views ? args.batch.P_total : args.P);
     cfg.blockDim = dim3(64);
     cfg.dynamicSmemBytes = 2 * (size_t)args.P * sizeof(float);
     cfg.stream = stream;

@@ -223,8 +223,27 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
     __shared__ RenderShared sm;
     const int p = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int esz = a.depth_f32 ? 4 : 2;
     HsParticleWork* wk = a.work + p;
+    // the observation, rays and stats of this particle's swarm
+    int W = a.W, H = a.H, depth_f32 = a.depth_f32;
+    float inv_fx = a.inv_fx, off_x = a.off_x, inv_fy = a.inv_fy, off_y = a.off_y;
+    const uint32_t* stats = a.stats;
+    const CUtensorMap* tmd = &tm_depth;
+    const CUtensorMap* tms = &tm_skin;
+    if (a.batch.views) {
+        const SwarmView& v = a.batch.views[a.batch.sid[p]];
+        W = v.W;
+        H = v.H;
+        depth_f32 = v.depth_f32;
+        inv_fx = v.inv_fx;
+        off_x = v.off_x;
+        inv_fy = v.inv_fy;
+        off_y = v.off_y;
+        stats = v.stats;
+        tmd = &v.tm_depth;
+        tms = &v.tm_skin;
+    }
+    const int esz = depth_f32 ? 4 : 2;
 
     if (lane < 2) mbar_init(&sm.bar[warp][lane], 1);
     if (tid == 0) mbar_fence_init();
@@ -251,8 +270,8 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
         if (lane == 0) {
             u0 = max(u0, 0);
             v0 = max(v0, 0);
-            u1 = min(u1, a.W - 1);
-            v1 = min(v1, a.H - 1);
+            u1 = min(u1, W - 1);
+            v1 = min(v1, H - 1);
             const int xa = u0 & ~15;  // TMA: the uint8 skin needs x at a multiple of 16 bytes
             const bool empty = u0 > u1 || v0 > v1;
             const int nux = empty ? 1 : (u1 + 1 - xa + kUW - 1) / kUW;
@@ -269,7 +288,7 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
     if (n_units == 0) {  // nothing of the hand inside the ROI: E is the baseline
         pdl_launch_dependents();
         if (blockIdx.x == 0 && tid == 0) {
-            const uint32_t n_valid = a.stats[0], n_skin = a.stats[1];
+            const uint32_t n_valid = stats[0], n_skin = stats[1];
             const float t_sum = a.d_M * (float)n_valid;
             const float D = n_skin == 0 ? a.lambda : t_sum / (float)n_skin + a.lambda;
             a.E[p] = D + a.lambda_k * kcp;
@@ -298,8 +317,8 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
         if ((m[0] | m[1]) && lane == 0) {
             unsigned char* t = sm.tile[warp][stage];
             mbar_arrive_expect_tx(&sm.bar[warp][stage], tx_bytes);
-            tma_load_2d(t, &tm_depth, x0, y0, &sm.bar[warp][stage]);
-            tma_load_2d(t + 256, &tm_skin, x0, y0, &sm.bar[warp][stage]);
+            tma_load_2d(t, tmd, x0, y0, &sm.bar[warp][stage]);
+            tma_load_2d(t + 256, tms, x0, y0, &sm.bar[warp][stage]);
         }
     };
     mk[0] = mk[1] = 0;
@@ -317,8 +336,8 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
         if (any) {
             const int x0 = xa + kUW * ux, y0 = v0 + kUH * uy;
             const int px0 = x0 + lx, py = y0 + ly;
-            const float ra[2] = {fmaf((float)px0, a.inv_fx, a.off_x), fmaf((float)(px0 + 8), a.inv_fx, a.off_x)};
-            const float rb = fmaf((float)py, a.inv_fy, a.off_y);
+            const float ra[2] = {fmaf((float)px0, inv_fx, off_x), fmaf((float)(px0 + 8), inv_fx, off_x)};
+            const float rb = fmaf((float)py, inv_fy, off_y);
             // nearest hit per pixel as (t0, s): depth z = t0 + s
             float z[kSub] = {INFINITY, INFINITY}, zt[kSub] = {0.f, 0.f}, zs[kSub] = {0.f, 0.f};
             uint64_t mask = any;
@@ -347,15 +366,15 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
             for (int q = 0; q < kSub; ++q) {
                 const int xr = lx + 8 * q;
                 const int px = x0 + xr;
-                const bool hit = ok && z[q] < INFINITY && px < a.W && py < a.H;
+                const bool hit = ok && z[q] < INFINITY && px < W && py < H;
                 if (!__any_sync(0xffffffffu, hit)) continue;  // nothing rendered in this half
                 if (hit) {
                     const int oi = ly * kUW + xr;
-                    const float od = a.depth_f32 ? reinterpret_cast<const float*>(t)[oi]
+                    const float od = depth_f32 ? reinterpret_cast<const float*>(t)[oi]
                                                  : (float)reinterpret_cast<const uint16_t*>(t)[oi];
                     const bool rm = add_pixel(od, t[256 + oi] != 0, zt[q], zs[q], a, acc_t, acc_a, acc_o, acc_h);
                     if (a.dbg_depth) {
-                        const size_t o = ((size_t)p * a.H + py) * a.W + px;
+                        const size_t o = ((size_t)p * H + py) * W + px;
                         a.dbg_depth[o] = z[q];
                         a.dbg_mask[o] = (uint8_t)(1 | (rm ? 2 : 0));
                     }
@@ -397,7 +416,7 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
             const long long tf = (long long)atomicAdd(&wk->t_fix, 0ull);
             const uint32_t sa = atomicAdd(&wk->n_and, 0u), so_d = atomicAdd(&wk->n_or, 0u);
             const uint32_t sh = atomicAdd(&wk->n_hit, 0u);
-            const uint32_t n_valid = a.stats[0], n_skin = a.stats[1];
+            const uint32_t n_valid = stats[0], n_skin = stats[1];
             // fixed point -> float from the two 32-bit halves (no 64-bit conversion)
             const float t_fix_f = (float)(int)(tf >> 32) * 4294967296.0f + (float)(uint32_t)(tf & 0xffffffffu);
             const float t_sum = t_fix_f * (1.0f / kFix) + a.d_M * (float)n_valid;
@@ -451,6 +470,49 @@ __global__ void __launch_bounds__(256) obs_stats_kernel(const unsigned char* dep
         atomicAdd(&stats[0], tv);
         atomicAdd(&stats[1], ts);
     }
+}
+
+// per-frame totals of every swarm of a batch: block (row group, swarm)
+__global__ void __launch_bounds__(256) obs_stats_multi_kernel(const BatchDev b)
+{
+    __shared__ uint32_t red[2][8];
+    const SwarmView& v = b.views[blockIdx.y];
+    uint32_t nv = 0, ns = 0;
+    for (int y = blockIdx.x; y < v.H; y += gridDim.x) {
+        for (int x = threadIdx.x; x < v.W; x += blockDim.x) {
+            const bool S = v.skin[(size_t)y * v.skin_pitch + x] != 0;
+            const float od = v.depth_f32 ? reinterpret_cast<const float*>(v.depth + (size_t)y * v.depth_pitch)[x]
+                                         : (float)reinterpret_cast<const uint16_t*>(v.depth + (size_t)y * v.depth_pitch)[x];
+            ns += S;
+            nv += S && od > 0.f;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+        ns += __shfl_xor_sync(0xffffffffu, ns, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = nv;
+        red[1][threadIdx.x >> 5] = ns;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tv = 0, ts = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            tv += red[0][w];
+            ts += red[1][w];
+        }
+        atomicAdd(&v.stats[0], tv);
+        atomicAdd(&v.stats[1], ts);
+    }
+}
+
+cudaError_t launch_obs_stats_multi(const BatchDev& batch, int max_H, cudaStream_t stream)
+{
+    const int rows = max_H < 16 ? max_H : 16;
+    obs_stats_multi_kernel<<<dim3(rows, batch.S), 256, 0, stream>>>(batch);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_render_score(const CUtensorMap& tm_depth, const CUtensorMap& tm_skin, const RenderArgs& args,

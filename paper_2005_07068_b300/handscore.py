@@ -64,6 +64,11 @@ class HsPsoParams(ctypes.Structure):
                 ("n_mutate", ctypes.c_int32)]
 
 
+class HsSwarmDesc(ctypes.Structure):
+    _fields_ = [("obs", HsObs), ("cam", HsCamera), ("P", ctypes.c_int32), ("n_mutate", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
 _vp = ctypes.c_void_p
 _SIGS = {
     "hs_version": ([], ctypes.c_int),
@@ -86,8 +91,24 @@ _SIGS = {
                      ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(HsCamera), _vp, _vp, _vp], ctypes.c_int),
     "render_score_batch_noalloc": ([_vp, ctypes.POINTER(HsObs), ctypes.POINTER(HsCamera), _vp, _vp, ctypes.c_int,
                                     ctypes.POINTER(HsScoreParams), _vp, _vp, _vp], ctypes.c_int),
+    "hs_batch_buffer_size": ([ctypes.POINTER(HsSwarmDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
+                             ctypes.c_int),
+    "hs_batch_create": ([_vp, ctypes.POINTER(HsSwarmDesc), ctypes.c_int, _vp, ctypes.c_size_t, _vp,
+                         ctypes.POINTER(_vp)], ctypes.c_int),
+    "hs_batch_destroy": ([_vp], ctypes.c_int),
+    "hs_batch_particles": ([_vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "hs_obs_prepare_multi": ([_vp, _vp], ctypes.c_int),
+    "pose_fk_multi": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "render_score_multi": ([_vp, _vp, _vp, _vp, ctypes.POINTER(HsScoreParams), _vp, ctypes.c_size_t, _vp, _vp, _vp],
+                           ctypes.c_int),
+    "pso_init_multi": ([_vp, _vp, ctypes.POINTER(HsSwarm), _vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32,
+                        _vp], ctypes.c_int),
+    "pso_step_fk_multi": ([_vp, _vp, ctypes.POINTER(HsSwarm), _vp, ctypes.POINTER(HsPsoParams), ctypes.c_uint32,
+                           ctypes.c_uint32, _vp, _vp, _vp], ctypes.c_int),
 }
 NOALLOC_SCRATCH_BYTES = 256 * 1024
+MAX_PARTICLES = 65535
+FUSED_MAX_PARTICLES = 1024
 
 _LIB = None
 
@@ -324,6 +345,87 @@ def pso_step_fk(model: Model, sw: Swarm, x_next: torch.Tensor, params: HsPsoPara
     _check("pso_step_fk", lib().pso_step_fk(model.handle, ctypes.byref(st), _ptr(x_next), sw.P, ctypes.byref(params),
                                             ctypes.c_uint64(seed), frame, gen, ctypes.byref(cam), _ptr(prims),
                                             _ptr(kc), _stream(stream)))
+
+
+# ---- batches of independent swarms ---------------------------------------------------
+
+class Batch:
+    """S independent swarms (sequences) scored and stepped together, one launch per
+    kernel: each with its own observation, camera, particle count and Philox key.
+    Particle arrays are concatenated over the swarms; gbest is [S, 26], gbest_E [S]."""
+
+    def __init__(self, model: Model, obs: list, cams: list, P: list, seeds: list, n_mutate: list | None = None,
+                 device="cuda", stream=None):
+        S = len(obs)
+        if not (len(cams) == len(P) == len(seeds) == S):
+            raise ValueError("one observation, camera, particle count and seed per swarm")
+        if n_mutate is None:
+            n_mutate = [p // 2 for p in P]
+        descs = (HsSwarmDesc * S)()
+        for s in range(S):
+            descs[s] = HsSwarmDesc(obs[s].struct(), cams[s], int(P[s]), int(n_mutate[s]), ctypes.c_uint64(seeds[s]))
+        n = ctypes.c_size_t(0)
+        _check("hs_batch_buffer_size", lib().hs_batch_buffer_size(descs, S, ctypes.byref(n)))
+        self.buffer = torch.zeros(n.value, dtype=torch.uint8, device=device)
+        h = _vp()
+        _check("hs_batch_create", lib().hs_batch_create(model.handle, descs, S, _ptr(self.buffer), n.value,
+                                                        _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self.obs = list(obs)  # the bound buffers stay alive with the batch
+        self.S = S
+        self.P = [int(p) for p in P]
+        self.offsets = np.concatenate([[0], np.cumsum(self.P)]).astype(np.int64)
+        self.P_total = int(self.offsets[-1])
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _LIB is not None:
+            _LIB.hs_batch_destroy(h)
+            self.handle = None
+
+
+def hs_obs_prepare_multi(batch: Batch, stream=None) -> None:
+    _check("hs_obs_prepare_multi", lib().hs_obs_prepare_multi(batch.handle, _stream(stream)))
+
+
+def pose_fk_multi(model: Model, batch: Batch, poses: torch.Tensor, prims: torch.Tensor, kc: torch.Tensor,
+                  stream=None) -> None:
+    """poses [P_total, 26] -> prims [P_total, n_prims, 16], kc [P_total], each with its swarm's camera."""
+    _check("pose_fk_multi", lib().pose_fk_multi(model.handle, batch.handle, _ptr(poses), _ptr(prims), _ptr(kc),
+                                                _stream(stream)))
+
+
+def render_score_multi(model: Model, batch: Batch, prims: torch.Tensor, kc: torch.Tensor, params: HsScoreParams,
+                       ws: torch.Tensor, E: torch.Tensor, parts: torch.Tensor | None = None, stream=None) -> None:
+    """E [P_total]: every particle scored against its own swarm's observation."""
+    _check("render_score_multi",
+           lib().render_score_multi(model.handle, batch.handle, _ptr(prims), _ptr(kc), ctypes.byref(params),
+                                    _ptr(ws), ws.numel(), _ptr(E), _ptr(parts), _stream(stream)))
+
+
+def pso_init_multi(model: Model, batch: Batch, sw: Swarm, seed_poses: torch.Tensor, scale, frame: int,
+                   stream=None) -> None:
+    """seed_poses [S, 26] device; sw holds [P_total] particle arrays, gbest [S, 26], gbest_E [S]."""
+    st = sw.struct()
+    sc = (ctypes.c_float * NDOF)(*[float(v) for v in scale])
+    _check("pso_init_multi", lib().pso_init_multi(model.handle, batch.handle, ctypes.byref(st), _ptr(seed_poses), sc,
+                                                  frame, _stream(stream)))
+
+
+def pso_step_fk_multi(model: Model, batch: Batch, sw: Swarm, x_next: torch.Tensor, params: HsPsoParams, frame: int,
+                      gen: int, prims: torch.Tensor, kc: torch.Tensor, stream=None) -> None:
+    st = sw.struct()
+    _check("pso_step_fk_multi",
+           lib().pso_step_fk_multi(model.handle, batch.handle, ctypes.byref(st), _ptr(x_next), ctypes.byref(params),
+                                   frame, gen, _ptr(prims), _ptr(kc), _stream(stream)))
+
+
+def batch_swarm(batch: Batch, device="cuda") -> Swarm:
+    """Zeroed swarm state for a batch: [P_total] particle arrays, [S] global bests."""
+    f = dict(dtype=torch.float32, device=device)
+    Pt, S = batch.P_total, batch.S
+    return Swarm(torch.zeros(Pt, NDOF, **f), torch.zeros(Pt, NDOF, **f), torch.zeros(Pt, NDOF, **f),
+                 torch.zeros(Pt, **f), torch.zeros(S, NDOF, **f), torch.zeros(S, **f), torch.zeros(Pt, **f))
 
 
 def hs_get_device_status(clear: bool = False) -> int:

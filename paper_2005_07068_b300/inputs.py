@@ -233,6 +233,19 @@ def trajectory(seed: int, n_frames: int, max_deg: float = 5.0, max_mm: float = 5
     return np.clip(traj, lo, hi)
 
 
+def batch_workload(seed: int, n_seq: int = 64, side=(48, 256), particles=(32, 64, 128, 256)
+                   ) -> tuple[list[tuple[int, int]], list[int], list[int]]:
+    """Many independent sequences at once: per sequence a square ROI whose side
+    is uniform in [side[0], side[1]] px, a particle count drawn uniformly from
+    `particles`, and a trajectory seed.  Each ROI is the Kinect view scaled to
+    its width (kinect_camera), so the hand covers the same fraction of every ROI."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(side[0], side[1] + 1, n_seq)
+    P = rng.choice(np.asarray(particles), n_seq)
+    seeds = rng.integers(1, 2**31 - 1, n_seq)
+    return [(int(s), int(s)) for s in sides], [int(p) for p in P], [int(v) for v in seeds]
+
+
 def perturbation_scale() -> np.ndarray:
     """Half-widths of the tracking init box: 10 mm per translation, 10 deg per angle."""
     s = np.full(N_DOF, math.radians(10.0))

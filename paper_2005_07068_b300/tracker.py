@@ -16,6 +16,26 @@ import torch
 from . import handscore as hs
 
 
+def _capture(device, state: list, enqueue) -> torch.cuda.CUDAGraph:
+    """Capture enqueue() into a CUDA graph.  One eager pass first resolves every
+    lazy set-up (module loading, symbol lookups) that capture forbids; the
+    tensors in `state` are saved before it and restored after, so capturing
+    has no effect on the tracker."""
+    cur = torch.cuda.current_stream(device)
+    saved = [t.clone() for t in state]
+    s = torch.cuda.Stream(device)
+    s.wait_stream(cur)
+    with torch.cuda.stream(s):
+        enqueue()
+    cur.wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        enqueue()
+    for t, v in zip(state, saved):
+        t.copy_(v)
+    return g
+
+
 class Tracker:
     def __init__(self, model: hs.Model, cam: hs.HsCamera, P: int = 64, gens: int = 40, *, seed: int = 1,
                  score=None, pso=None, scale=None, device="cuda", record_history: bool = False):
@@ -58,19 +78,18 @@ class Tracker:
                 self.history[g - 1, 26:].copy_(self.swarm.gbest_E)
         self.swarm.x = cur
 
+    def _state(self) -> list:
+        sw = self.swarm
+        return [*self.x_buf, sw.v, sw.pbest, sw.pbest_E, sw.gbest, sw.gbest_E, sw.E, self.prims, self.kc,
+                self.seed_pose]
+
     def graph(self, obs: hs.Obs, frame: int, seed_pose: torch.Tensor | None = None) -> torch.cuda.CUDAGraph:
-        """The captured graph of enqueue_frame(obs, frame, seed_pose) (cached)."""
+        """The captured graph of enqueue_frame(obs, frame, seed_pose) (cached).
+        Capturing leaves the tracker's state as it was."""
         key = (id(obs), frame, None if seed_pose is None else seed_pose.data_ptr())
         g = self._graphs.get(key)
         if g is None:
-            s = torch.cuda.Stream(self.device)
-            s.wait_stream(torch.cuda.current_stream(self.device))
-            with torch.cuda.stream(s):  # one eager pass resolves every lazy set-up before capture
-                self.enqueue_frame(obs, frame, seed_pose)
-            torch.cuda.current_stream(self.device).wait_stream(s)
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g, stream=s):
-                self.enqueue_frame(obs, frame, seed_pose)
+            g = _capture(self.device, self._state(), lambda: self.enqueue_frame(obs, frame, seed_pose))
             self._graphs[key] = g
         return g
 
@@ -94,3 +113,129 @@ class Tracker:
         self.run_frame(staging, frame, seed_pose)
         out_host[:26].copy_(self.swarm.gbest, non_blocking=True)
         out_host[26:].copy_(self.swarm.gbest_E, non_blocking=True)
+
+
+# ---- many sequences at once ------------------------------------------------------------
+
+def _round_up(n: int, a: int) -> int:
+    return (n + a - 1) // a * a
+
+
+class PackedObs:
+    """The observations of S sequences in ONE device buffer, with a pinned host
+    twin of the same layout, so a new frame for every sequence is one copy.
+    Swarm s has a depth image [H_s, pitch] (uint16 mm, or float32 mm) and a skin
+    mask [H_s, pitch] uint8, each starting on a 256-byte boundary with a row
+    pitch that is a multiple of 16 bytes (the TMA requirement)."""
+
+    def __init__(self, sizes, depth_f32: bool = False, device="cuda", pinned: bool = True):
+        self.sizes = [(int(W), int(H)) for W, H in sizes]
+        esz = 4 if depth_f32 else 2
+        self.depth_dtype = torch.float32 if depth_f32 else torch.uint16
+        self.layout = []  # (depth offset, depth pitch, skin offset, skin pitch) in bytes
+        off = 0
+        for W, H in self.sizes:
+            dp, sp = _round_up(W * esz, 16), _round_up(W, 16)
+            d0 = off
+            s0 = _round_up(d0 + dp * H, 256)
+            off = _round_up(s0 + sp * H, 256)
+            self.layout.append((d0, dp, s0, sp))
+        self.nbytes = off
+        self.device = torch.device(device)
+        self.dev = torch.zeros(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.host = torch.zeros(self.nbytes, dtype=torch.uint8, pin_memory=pinned)
+        self.stats = torch.zeros(len(self.sizes), 2, dtype=torch.int32, device=self.device)
+        self.obs = [self._obs(s) for s in range(len(self.sizes))]
+
+    def _views(self, buf: torch.Tensor, s: int):
+        (W, H), (d0, dp, s0, sp) = self.sizes[s], self.layout[s]
+        esz = 4 if self.depth_dtype == torch.float32 else 2
+        depth = buf[d0:d0 + dp * H].view(self.depth_dtype).view(H, dp // esz)
+        skin = buf[s0:s0 + sp * H].view(H, sp)
+        return depth, skin
+
+    def _obs(self, s: int) -> hs.Obs:
+        depth, skin = self._views(self.dev, s)
+        W, H = self.sizes[s]
+        return hs.Obs(depth, skin, W, H, self.stats[s])
+
+    def write_host(self, s: int, depth: np.ndarray, skin: np.ndarray) -> None:
+        """Place swarm s's frame (depth [H, W], skin [H, W]) into the host twin."""
+        W, H = self.sizes[s]
+        d, k = self._views(self.host, s)
+        d[:, :W].copy_(torch.from_numpy(np.ascontiguousarray(depth)).to(self.depth_dtype))
+        k[:, :W].copy_(torch.from_numpy(np.ascontiguousarray(skin).astype(np.uint8)))
+
+    def upload(self, non_blocking: bool = True) -> None:
+        """Host twin -> device buffer (a single copy)."""
+        self.dev.copy_(self.host, non_blocking=non_blocking)
+
+
+class BatchTracker:
+    """Tracks S independent sequences together: every kernel of the frame loop
+    runs once for all swarms (uneven ROI sizes and particle counts), and one
+    CUDA graph holds a whole frame of every sequence.  Sequence s reproduces,
+    bit for bit, a Tracker run with the same observation, camera, P and seed."""
+
+    def __init__(self, model: hs.Model, batch: hs.Batch, gens: int = 40, *, score=None, pso=None, scale=None,
+                 device="cuda"):
+        self.model, self.batch, self.gens = model, batch, gens
+        self.device = torch.device(device)
+        self.score = score if score is not None else hs.score_params()
+        self.pso = pso if pso is not None else hs.pso_params()  # n_mutate comes from each swarm
+        if scale is None:
+            scale = np.full(26, np.radians(10.0), np.float32)
+            scale[:3] = 10.0
+        self.scale = np.asarray(scale, np.float32)
+        f = dict(dtype=torch.float32, device=self.device)
+        self.swarm = hs.batch_swarm(batch, self.device)
+        self.x_buf = (self.swarm.x, torch.zeros_like(self.swarm.x))
+        self.prims = torch.zeros(batch.P_total, model.n_prims, 16, **f)
+        self.kc = torch.zeros(batch.P_total, **f)
+        self.ws = hs.new_workspace(batch.P_total, self.device)
+        self.seed_poses = torch.zeros(batch.S, 26, **f)
+        self._graphs: dict = {}
+
+    def enqueue_frame(self, frame: int, seed_poses: torch.Tensor | None = None) -> None:
+        """seed_poses: device [S, 26]; None = every swarm's current global best."""
+        src = self.swarm.gbest if seed_poses is None else seed_poses
+        self.seed_poses.copy_(src)
+        hs.hs_obs_prepare_multi(self.batch)
+        cur, nxt = self.x_buf
+        self.swarm.x = cur
+        hs.pso_init_multi(self.model, self.batch, self.swarm, self.seed_poses, self.scale, frame)
+        hs.pose_fk_multi(self.model, self.batch, cur, self.prims, self.kc)
+        for g in range(1, self.gens + 1):
+            hs.render_score_multi(self.model, self.batch, self.prims, self.kc, self.score, self.ws, self.swarm.E)
+            self.swarm.x = cur
+            hs.pso_step_fk_multi(self.model, self.batch, self.swarm, nxt, self.pso, frame, g, self.prims, self.kc)
+            cur, nxt = nxt, cur
+        self.swarm.x = cur
+
+    def _state(self) -> list:
+        sw = self.swarm
+        return [*self.x_buf, sw.v, sw.pbest, sw.pbest_E, sw.gbest, sw.gbest_E, sw.E, self.prims, self.kc,
+                self.seed_poses]
+
+    def graph(self, frame: int, seed_poses: torch.Tensor | None = None) -> torch.cuda.CUDAGraph:
+        """The captured graph of enqueue_frame(frame, seed_poses) (cached); capturing
+        leaves the state as it was."""
+        key = (frame, None if seed_poses is None else seed_poses.data_ptr())
+        g = self._graphs.get(key)
+        if g is None:
+            g = _capture(self.device, self._state(), lambda: self.enqueue_frame(frame, seed_poses))
+            self._graphs[key] = g
+        return g
+
+    def run_frame(self, frame: int, seed_poses: torch.Tensor | None = None, graph: bool = True) -> None:
+        if graph:
+            self.graph(frame, seed_poses).replay()
+        else:
+            self.enqueue_frame(frame, seed_poses)
+
+    def launches_per_frame(self) -> int:
+        """Kernels per frame for all swarms: 2 observation passes, init, FK, 2 per generation."""
+        return 4 + 2 * self.gens
+
+    def evals_per_frame(self) -> int:
+        return self.batch.P_total * self.gens

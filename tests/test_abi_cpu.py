@@ -51,7 +51,8 @@ def test_struct_layout_matches_c(tmp_path):
 #define O(t, f) printf(#t "." #f " %zu\\n", offsetof(t, f));
 int main(void) {
   S(HsBoneDesc) S(HsPrimDesc) S(HsModelDesc) S(HsCamera) S(HsObs) S(HsScoreParams) S(HsParts)
-  S(HsPrim) S(HsSwarm) S(HsPsoParams)
+  S(HsPrim) S(HsSwarm) S(HsPsoParams) S(HsSwarmDesc)
+  O(HsSwarmDesc, cam) O(HsSwarmDesc, P) O(HsSwarmDesc, seed)
   O(HsModelDesc, bones) O(HsModelDesc, lo) O(HsModelDesc, hi) O(HsObs, stats) O(HsObs, depth_type)
   O(HsBoneDesc, rest) O(HsPrimDesc, dims) O(HsSwarm, E)
   return 0;
@@ -66,7 +67,9 @@ int main(void) {
         "HsModelDesc": ctypes.sizeof(hs.HsModelDesc), "HsCamera": ctypes.sizeof(hs.HsCamera),
         "HsObs": ctypes.sizeof(hs.HsObs), "HsScoreParams": ctypes.sizeof(hs.HsScoreParams),
         "HsParts": 16, "HsPrim": 64, "HsSwarm": ctypes.sizeof(hs.HsSwarm),
-        "HsPsoParams": ctypes.sizeof(hs.HsPsoParams),
+        "HsPsoParams": ctypes.sizeof(hs.HsPsoParams), "HsSwarmDesc": ctypes.sizeof(hs.HsSwarmDesc),
+        "HsSwarmDesc.cam": hs.HsSwarmDesc.cam.offset, "HsSwarmDesc.P": hs.HsSwarmDesc.P.offset,
+        "HsSwarmDesc.seed": hs.HsSwarmDesc.seed.offset,
         "HsModelDesc.bones": hs.HsModelDesc.bones.offset, "HsModelDesc.lo": hs.HsModelDesc.lo.offset,
         "HsModelDesc.hi": hs.HsModelDesc.hi.offset, "HsObs.stats": hs.HsObs.stats.offset,
         "HsObs.depth_type": hs.HsObs.depth_type.offset, "HsBoneDesc.rest": hs.HsBoneDesc.rest.offset,
@@ -185,6 +188,51 @@ def test_other_host_checks():
     assert L.pso_step_fk(m.handle, ctypes.byref(sw), FAKE + 4096, 2000, ctypes.byref(pp), 1, 0, 1, ctypes.byref(cam),
                          FAKE, FAKE, None) == hs.HS_ERR_SIZE
     assert hs.lib().hs_status_string(-3) == b"size out of range"
+
+
+def _descs(P, **obs_kw):
+    S = len(P)
+    d = (hs.HsSwarmDesc * S)()
+    for s in range(S):
+        d[s] = hs.HsSwarmDesc(_obs(**obs_kw), hs.camera(262.5, 262.5, 160, 120), P[s], P[s] // 2, 7 + s)
+    return d
+
+
+def test_batch_host_checks():
+    m = _model()
+    L = hs.lib()
+    n = ctypes.c_size_t(0)
+    assert L.hs_batch_buffer_size(_descs([32, 64, 128]), 3, ctypes.byref(n)) == hs.HS_OK
+    assert n.value >= 3 * 256 + 224 * 4  # views with two TMA descriptors each, then the swarm table
+    assert L.hs_batch_buffer_size(_descs([32]), 0, ctypes.byref(n)) == hs.HS_ERR_SIZE
+    assert L.hs_batch_buffer_size(_descs([0]), 1, ctypes.byref(n)) == hs.HS_ERR_SIZE
+    assert L.hs_batch_buffer_size(_descs([2000]), 1, ctypes.byref(n)) == hs.HS_ERR_SIZE  # above the fused step
+    assert L.hs_batch_buffer_size(_descs([1024] * 64), 64, ctypes.byref(n)) == hs.HS_ERR_SIZE  # > 65535 in total
+    assert L.hs_batch_buffer_size(None, 1, ctypes.byref(n)) == hs.HS_ERR_ARG
+    h = ctypes.c_void_p()
+    good = _descs([32, 64])
+    L.hs_batch_buffer_size(good, 2, ctypes.byref(n))
+    need = n.value
+    assert L.hs_batch_create(m.handle, good, 2, FAKE, need - 256, None, ctypes.byref(h)) == hs.HS_ERR_SIZE
+    assert L.hs_batch_create(m.handle, good, 2, FAKE + 16, need, None, ctypes.byref(h)) == hs.HS_ERR_ALIGN
+    assert L.hs_batch_create(m.handle, _descs([32, 64], depth_pitch=600), 2, FAKE, need, None,
+                             ctypes.byref(h)) == hs.HS_ERR_ALIGN
+    assert L.hs_batch_create(m.handle, _descs([32, 64], stats=None), 2, FAKE, need, None,
+                             ctypes.byref(h)) == hs.HS_ERR_ARG
+    bad_mut = _descs([32, 64])
+    bad_mut[1].n_mutate = 65
+    assert L.hs_batch_create(m.handle, bad_mut, 2, FAKE, need, None, ctypes.byref(h)) == hs.HS_ERR_ARG
+    bad_cam = _descs([32, 64])
+    bad_cam[0].cam.fx = 0.0
+    assert L.hs_batch_create(m.handle, bad_cam, 2, FAKE, need, None, ctypes.byref(h)) == hs.HS_ERR_ARG
+    assert L.hs_batch_create(m.handle, good, 2, FAKE, need, None, None) == hs.HS_ERR_ARG
+    # the batch-wide calls reject a missing batch
+    prm = hs.score_params()
+    assert L.render_score_multi(m.handle, None, FAKE, FAKE, ctypes.byref(prm), FAKE, 1 << 20, FAKE, None,
+                                None) == hs.HS_ERR_ARG
+    assert L.pose_fk_multi(m.handle, None, FAKE, FAKE, FAKE, None) == hs.HS_ERR_ARG
+    assert L.hs_obs_prepare_multi(None, None) == hs.HS_ERR_ARG
+    assert L.hs_batch_destroy(None) == hs.HS_ERR_ARG
 
 
 @pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU behaviour")

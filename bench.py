@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample")
     ap.add_argument("--profile", action="store_true", help="short run for an ncu launch list")
     ap.add_argument("--no-roofline", action="store_true", help="skip the render roofline replay")
+    ap.add_argument("--render", default="auto", help="render kernel: auto, units, tiles32x16, tiles32x32, "
+                    "tiles64x32, tiles64x64")
+    ap.add_argument("--ctas", type=int, default=0, help="render CTAs per particle (0 = automatic)")
     ap.add_argument("--workload", choices=["kinect", "batch"], default="kinect",
                     help="kinect: one 320x240 sequence (the headline); batch: 64 sequences with uneven ROIs and P")
     return ap.parse_args()
@@ -325,7 +328,7 @@ def run_batch(args, rank, world, local):
     g = I.hand_geometry()
     lo, hi = (a.astype(np.float32) for a in I.search_limits())
     model = hs.Model.from_geometry(g, lo, hi)
-    frames = BATCH_FRAMES
+    frames = 2 if args.profile else BATCH_FRAMES
     cams, trajs = [], []
     store = [PackedObs(sizes, device=dev) for _ in range(frames)]  # resident frames (+ pinned twins)
     for q, (Wq, Hq) in enumerate(sizes):
@@ -340,7 +343,8 @@ def run_batch(args, rank, world, local):
         st.upload(non_blocking=False)
     staging = PackedObs(sizes, device=dev, pinned=False)  # the buffers the batch is bound to
     batch = hs.Batch(model, staging.obs, cams, Ps, seq_seeds)
-    trk = BatchTracker(model, batch, GENS, device=dev)
+    score = hs.score_params(variant=hs.RENDER_VARIANTS[args.render], ctas_per_particle=args.ctas)
+    trk = BatchTracker(model, batch, GENS, device=dev, score=score)
     gt0 = torch.from_numpy(np.stack([t[0] for t in trajs])).to(dev)
     graphs = [trk.graph(f, gt0 if f == 0 else None) for f in range(frames)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -373,6 +377,15 @@ def run_batch(args, rank, world, local):
         wall = time.perf_counter() - w0
     step_ms = [a.elapsed_time(b) for a, b in evs]
     value, t_dev, _ = R.aggregate(sum(step_ms) / 1e3, K * evals_frame, dev)
+
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2032.0))
+    if args.profile or args.no_roofline:
+        if rank == 0:
+            print(json.dumps({"metric": BATCH_METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+                              "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / K,
+                              "higher_is_better": True, "note": "short run (--profile / --no-roofline)",
+                              "clocks": clocks, "gpu_launches": K * trk.launches_per_frame()}), flush=True)
+        return 0
 
     # roofline: the render launches of one frame replayed back to back
     kinds = g.prims_i[:, 1]
@@ -422,13 +435,13 @@ def run_batch(args, rank, world, local):
     Hp = np.repeat([h for _, h in sizes], Ps)
     flops = [algorithmic_flops(hist_p[q, :, :, 14:16].cpu().numpy(), kinds, Wp, Hp) for q in range(0, GENS, 4)]
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    clocks = clk.summary(peaks.get("sm_max_mhz", 2032.0))
     sm_max = float(peaks.get("sm_max_mhz") or clocks["sm_max_mhz"] or 2032.0)
     peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     flop_launch = sum(flops) / len(flops)
     achieved = flop_launch / (render_us * 1e-6) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None, "kernel": "render_score_kernel (batch)",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": f"render_score_multi ({hs.render_variant(trk.score, Pt)})",
                 "peak_basis": f"FP32: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {sm_max:.0f} MHz "
                               f"(sm_max_mhz of measured)",
                 "launch_us": render_us, "launches_timed": reps * GENS, "flop_per_launch": flop_launch,
@@ -528,7 +541,8 @@ def main():
     frames = min(FRAMES, max(args.steps + args.warmup, 2)) if args.profile else FRAMES
     traj, obs, host = make_frames(seed, frames, hs, I, model, cam, dev)
     gt0 = torch.from_numpy(traj[0]).to(dev)
-    trk = Tracker(model, cam, PARTICLES, GENS, seed=seed, device=dev)
+    score = hs.score_params(variant=hs.RENDER_VARIANTS[args.render], ctas_per_particle=args.ctas)
+    trk = Tracker(model, cam, PARTICLES, GENS, seed=seed, device=dev, score=score)
     graphs = [trk.graph(obs[f], f, gt0 if f == 0 else None) for f in range(frames)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -622,7 +636,8 @@ def main():
     achieved = flop_launch / (render_us * 1e-6) / 1e12 if render_us else 0.0
     traffic = profile_traffic(os.path.join(ROOT, "paper_2005_07068_b300", "csrc", "render_score.cu"))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": traffic, "kernel": "render_score_kernel",
+                "frac": achieved / peak_tflops, "traffic": traffic,
+                "kernel": f"render_score_batch ({hs.render_variant(trk.score, PARTICLES)})",
                 "peak_basis": f"FP32: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {sm_max:.0f} MHz "
                               f"(sm_max_mhz of measured)",
                 "launch_us": render_us, "launches_timed": n * 5, "flop_per_launch": flop_launch,

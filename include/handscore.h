@@ -118,10 +118,27 @@ typedef struct {
                                written by hs_obs_prepare, read by render_score_batch */
 } HsObs;
 
+/* Render kernels (all give the same E; they differ in how work is laid out):
+ * the unit kernel walks pixels (16 x 4 blocks, primitives culled per 8 x 4
+ * half), the tile kernels walk primitives (pixel-exact rectangles of each
+ * primitive's box inside a TW x TH tile, nearest hit by a shared-memory
+ * z-buffer).  HS_RENDER_AUTO picks by the number of particles per call. */
+#define HS_RENDER_AUTO        0
+#define HS_RENDER_UNITS       1
+#define HS_RENDER_TILES_32x16 2
+#define HS_RENDER_TILES_32x32 3
+#define HS_RENDER_TILES_64x32 4
+#define HS_RENDER_TILES_64x64 5
+#define HS_RENDER_VARIANTS    6
+
 /* constants of Eq. 4-5 (paper: d_m = 1 cm, d_M = 4 cm, lambda = 20, lambda_k = 10),
- * in mm; 0 <= d_M < 127 (the depth sums are kept in 32-bit fixed point per pixel) */
+ * in mm; 0 <= d_M < 127 (the depth sums are kept in 32-bit fixed point per pixel);
+ * and the launch shape of the render (no effect on results): the kernel, and
+ * the CTAs per particle (0 = about one resident wave in total, else 1..64) */
 typedef struct {
     float d_m, d_M, lambda, lambda_k;
+    int32_t variant;           /* HS_RENDER_* */
+    int32_t ctas_per_particle;
 } HsScoreParams;
 
 /* per-particle sums of Eq. 4 (optional output of render_score_batch) */
@@ -216,6 +233,10 @@ int pose_fk(const HsModel* model, const float* poses, int P, const HsCamera* cam
  * outputs (NULL in production; when given they are cleared first).
  * workspace: hs_workspace_size(P) bytes, zeroed once before first use.
  * Errors: HS_ERR_ARG, HS_ERR_ALIGN, HS_ERR_SIZE, HS_ERR_CUDA. */
+/* The render kernel (HS_RENDER_*, never AUTO) a call over P particles with these
+ * parameters runs; HS_ERR_ARG for an invalid variant or P < 0. */
+int hs_render_variant(const HsScoreParams* params, int P);
+
 int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* cam,
                        const HsPrim* prims, const float* kc, int P, const HsScoreParams* params,
                        void* workspace, size_t workspace_bytes, float* E, HsParts* parts,

@@ -8,6 +8,8 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
+#include <algorithm>
 #include <mutex>
 
 #include "hs_args.cuh"
@@ -85,8 +87,55 @@ static int validate_cam(const HsCamera* c)
     return HS_OK;
 }
 
-constexpr int kMaxK = 16;             // 4-warp CTAs per particle in render_score_batch
+constexpr int kMaxK = 16;             // default cap of CTAs per particle in the render
+constexpr int kMaxCtasPerParticle = 64;
 constexpr int kTargetCtas = 148 * 6;  // one resident wave (6 CTAs of 4 warps per SM)
+
+}  // namespace hs
+
+int hs_render_variant(const HsScoreParams* p, int P)
+{
+    if (!p || p->variant < 0 || p->variant >= HS_RENDER_VARIANTS || P < 0) return HS_ERR_ARG;
+    if (p->variant != HS_RENDER_AUTO) return p->variant;
+    // many particles per call: the tile kernel (pixel-exact work, throughput);
+    // fewer than one wave of CTAs: the unit kernel (shorter critical path)
+    return P >= hs::kTargetCtas ? HS_RENDER_TILES_64x32 : HS_RENDER_UNITS;
+}
+
+namespace hs {
+
+static int validate_score_params(const HsScoreParams* p)
+{
+    if (!p) return HS_ERR_ARG;
+    if (!std::isfinite(p->d_m) || !std::isfinite(p->d_M) || !std::isfinite(p->lambda) ||
+        !std::isfinite(p->lambda_k) || p->d_m < 0.f || p->d_M < 0.f || p->d_M >= 127.f)
+        return HS_ERR_ARG;
+    if (p->variant < 0 || p->variant >= HS_RENDER_VARIANTS) return HS_ERR_ARG;
+    if (p->ctas_per_particle < 0 || p->ctas_per_particle > kMaxCtasPerParticle) return HS_ERR_ARG;
+    return HS_OK;
+}
+
+// the render kernel and its CTAs per particle for a call over P particles
+static cudaError_t launch_render(const HsScoreParams& prm, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,
+                                 RenderArgs& a, cudaStream_t s)
+{
+    const int variant = hs_render_variant(&prm, a.P);
+    // default: about one resident wave in total (any K is correct; it only
+    // changes how a particle's work is dealt)
+    int K = prm.ctas_per_particle;
+    if (K == 0) {
+        K = kTargetCtas / a.P;  // rounded down: K * P never exceeds one wave
+        if (K > kMaxK) K = kMaxK;
+        if (K < 1) K = 1;
+    }
+    a.K = K;
+    a.d_m = prm.d_m;
+    a.d_M = prm.d_M;
+    a.lambda = prm.lambda;
+    a.lambda_k = prm.lambda_k;
+    if (variant == HS_RENDER_UNITS) return launch_render_score(tm_depth, tm_skin, a, s);
+    return launch_render_tiles(variant, tm_depth, tm_skin, a, s);
+}
 
 }  // namespace hs
 
@@ -99,7 +148,8 @@ struct HsModel {
 
 struct HsBatch {
     int S, P_total, P_max, max_H;
-    BatchDev dev;  // device views / particle-to-swarm table (inside the caller's buffer)
+    BatchDev dev;          // device views / particle-to-swarm table (inside the caller's buffer)
+    const int32_t* order;  // device [P_total]: the render's CTA rows, largest ROI first
 };
 
 namespace {
@@ -112,9 +162,12 @@ __global__ void zero_stats_kernel(const BatchDev b)
     }
 }
 
+size_t table_bytes(long long P_total) { return ((size_t)P_total * 4 + 255) / 256 * 256; }
+
+// [256-byte header][S views][particle -> swarm table][render order]
 size_t batch_bytes(int S, long long P_total)
 {
-    return 256 + (size_t)S * sizeof(SwarmView) + ((size_t)P_total * 4 + 255) / 256 * 256;
+    return 256 + (size_t)S * sizeof(SwarmView) + 2 * table_bytes(P_total);
 }
 }  // namespace
 
@@ -303,9 +356,7 @@ int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* c
     int rc = validate_obs(obs);
     if (rc) return rc;
     if ((rc = validate_cam(cam))) return rc;
-    if (!std::isfinite(params->d_m) || !std::isfinite(params->d_M) || !std::isfinite(params->lambda) ||
-        !std::isfinite(params->lambda_k) || params->d_m < 0.f || params->d_M < 0.f || params->d_M >= 127.f)
-        return HS_ERR_ARG;
+    if ((rc = validate_score_params(params))) return rc;
     if (P < 0 || P > HS_MAX_PARTICLES) return HS_ERR_SIZE;
     if (!aligned16(prims) || (workspace && !aligned16(workspace))) return HS_ERR_ALIGN;
     size_t need = 0;
@@ -327,18 +378,11 @@ int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* c
             cudaMemsetAsync(dbg_mask, 0, n, s) != cudaSuccess)
             return HS_ERR_CUDA;
     }
-    // CTAs per particle: about one resident wave in total (any K is correct;
-    // it only changes how the units are dealt)
-    int K = kTargetCtas / P;  // rounded down: K * P never exceeds one wave
-    if (K > kMaxK) K = kMaxK;
-    if (K < 1) K = 1;
-
     RenderArgs a = {};
     a.prims = reinterpret_cast<const float4*>(prims);
     a.kc = kc;
     a.P = P;
     a.n_prims = model->dev.n_prims;
-    a.K = K;
     a.W = obs->W;
     a.H = obs->H;
     // ray of pixel (u, v): ((u + 0.5 - cx) / fx, (v + 0.5 - cy) / fy, 1), as one FMA per axis
@@ -346,10 +390,6 @@ int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* c
     a.inv_fy = (float)(1.0 / (double)cam->fy);
     a.off_x = (float)((0.5 - (double)cam->cx) / (double)cam->fx);
     a.off_y = (float)((0.5 - (double)cam->cy) / (double)cam->fy);
-    a.d_m = params->d_m;
-    a.d_M = params->d_M;
-    a.lambda = params->lambda;
-    a.lambda_k = params->lambda_k;
     a.depth_f32 = f32;
     a.stats = obs->stats;
     a.work = static_cast<HsParticleWork*>(workspace);
@@ -358,7 +398,7 @@ int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* c
     a.dbg_depth = dbg_depth;
     a.dbg_mask = dbg_mask;
     if ((rc = status_ptr(&a.status))) return rc;
-    return launch_render_score(tm_depth, tm_skin, a, s) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+    return launch_render(*params, tm_depth, tm_skin, a, s) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 
 int pso_init(const HsModel* model, const HsSwarm* sw, int P, const float* seed_pose, const float* scale,
@@ -487,11 +527,14 @@ int hs_batch_create(const HsModel* model, const HsSwarmDesc* sw, int S, void* bu
         if ((rc = validate_cam(&sw[s].cam))) return rc;
         if (sw[s].n_mutate < 0 || sw[s].n_mutate > sw[s].P) return HS_ERR_ARG;
     }
-    // host image of the buffer: [256-byte header][S views][particle -> swarm table]
+    // host image of the buffer
     unsigned char* img = static_cast<unsigned char*>(std::calloc(1, need));
     if (!img) return HS_ERR_ARG;
     SwarmView* views = reinterpret_cast<SwarmView*>(img + 256);
     int32_t* sid = reinterpret_cast<int32_t*>(img + 256 + (size_t)S * sizeof(SwarmView));
+    long long P_all = 0;
+    for (int s = 0; s < S; ++s) P_all += sw[s].P;
+    int32_t* order = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(sid) + table_bytes(P_all));
     int off = 0, P_max = 0, max_H = 0;
     for (int s = 0; s < S && rc == HS_OK; ++s) {
         const HsObs& o = sw[s].obs;
@@ -528,6 +571,18 @@ int hs_batch_create(const HsModel* model, const HsSwarmDesc* sw, int S, void* bu
         if (sw[s].P > P_max) P_max = sw[s].P;
         if (o.H > max_H) max_H = o.H;
     }
+    // render order: swarms by decreasing ROI area (stable), each swarm's particles in
+    // turn; CTAs start in this order, so the largest pieces of work go first
+    if (rc == HS_OK) {
+        std::vector<int> by_area(S);
+        for (int s = 0; s < S; ++s) by_area[s] = s;
+        std::stable_sort(by_area.begin(), by_area.end(), [&](int x, int y) {
+            return (long long)views[x].W * views[x].H > (long long)views[y].W * views[y].H;
+        });
+        int k = 0;
+        for (int s : by_area)
+            for (int i = 0; i < views[s].P; ++i) order[k++] = views[s].offset + i;
+    }
     if (rc == HS_OK && cudaMemcpyAsync(buffer, img, need, cudaMemcpyHostToDevice, (cudaStream_t)stream) != cudaSuccess)
         rc = HS_ERR_CUDA;
     if (rc == HS_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) rc = HS_ERR_CUDA;
@@ -544,6 +599,7 @@ int hs_batch_create(const HsModel* model, const HsSwarmDesc* sw, int S, void* bu
     b->dev.P_total = off;
     b->dev.views = reinterpret_cast<const SwarmView*>(dev + 256);
     b->dev.sid = reinterpret_cast<const int32_t*>(dev + 256 + (size_t)S * sizeof(SwarmView));
+    b->order = reinterpret_cast<const int32_t*>(dev + 256 + (size_t)S * sizeof(SwarmView) + table_bytes(off));
     *out = b;
     return HS_OK;
 }
@@ -593,9 +649,8 @@ int render_score_multi(const HsModel* model, const HsBatch* b, const HsPrim* pri
                        hs_stream_t stream)
 {
     if (!model || !b || !prims || !kc || !params || !E || !workspace) return HS_ERR_ARG;
-    if (!std::isfinite(params->d_m) || !std::isfinite(params->d_M) || !std::isfinite(params->lambda) ||
-        !std::isfinite(params->lambda_k) || params->d_m < 0.f || params->d_M < 0.f || params->d_M >= 127.f)
-        return HS_ERR_ARG;
+    int rc = validate_score_params(params);
+    if (rc) return rc;
     if (!aligned16(prims) || !aligned16(workspace)) return HS_ERR_ALIGN;
     size_t need = 0;
     hs_workspace_size(b->P_total, &need);
@@ -605,22 +660,14 @@ int render_score_multi(const HsModel* model, const HsBatch* b, const HsPrim* pri
     a.kc = kc;
     a.P = b->P_total;
     a.n_prims = model->dev.n_prims;
-    int K = kTargetCtas / b->P_total;
-    if (K > kMaxK) K = kMaxK;
-    if (K < 1) K = 1;
-    a.K = K;
-    a.d_m = params->d_m;
-    a.d_M = params->d_M;
-    a.lambda = params->lambda;
-    a.lambda_k = params->lambda_k;
     a.work = static_cast<HsParticleWork*>(workspace);
     a.E = E;
     a.parts = parts;
     a.batch = b->dev;
-    int rc = status_ptr(&a.status);
-    if (rc) return rc;
+    a.order = b->order;
+    if ((rc = status_ptr(&a.status))) return rc;
     CUtensorMap unused = {};  // the maps come from the batch views
-    return launch_render_score(unused, unused, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+    return launch_render(*params, unused, unused, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 
 int pso_init_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw, const float* seed_poses,

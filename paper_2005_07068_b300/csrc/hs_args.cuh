@@ -11,7 +11,7 @@ namespace hs {
 // One swarm of a batch (device memory, written by hs_batch_create): its
 // observation (TMA tensor maps + raw pointers), camera, particle range,
 // mutation count and Philox key.  Particles of swarm s are [offset, offset+P).
-struct alignas(64) SwarmView {
+struct SwarmView {  // 128-byte aligned (CUtensorMap)
     CUtensorMap tm_depth;  // 2-D map of the depth image, 16 x 4 boxes
     CUtensorMap tm_skin;   // 2-D map of the skin mask, 16 x 4 boxes
     int32_t W, H, depth_f32, P;
@@ -67,6 +67,7 @@ struct RenderArgs {
     uint8_t* dbg_mask;
     uint32_t* status;
     BatchDev batch;  // batch.views == nullptr: one swarm described by the fields above
+    const int32_t* order;  // CTA row y scores particle order[y] (nullptr: particle y)
 };
 
 struct PsoInitArgs {
@@ -108,6 +109,8 @@ cudaError_t launch_fk(const DevModel& model, const FkArgs& args, cudaStream_t st
 cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cudaStream_t stream);
 cudaError_t launch_render_score(const CUtensorMap& tm_depth, const CUtensorMap& tm_skin, const RenderArgs& args,
                                 cudaStream_t stream);
+cudaError_t launch_render_tiles(int variant, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,
+                                const RenderArgs& args, cudaStream_t stream);
 cudaError_t launch_obs_stats(const unsigned char* depth, int depth_pitch, int depth_f32, const uint8_t* skin,
                              int skin_pitch, int W, int H, uint32_t* stats, cudaStream_t stream);
 cudaError_t launch_obs_stats_multi(const BatchDev& batch, int max_H, cudaStream_t stream);

@@ -52,7 +52,14 @@ class HsObs(ctypes.Structure):
 
 class HsScoreParams(ctypes.Structure):
     _fields_ = [("d_m", ctypes.c_float), ("d_M", ctypes.c_float), ("lambda_", ctypes.c_float),
-                ("lambda_k", ctypes.c_float)]
+                ("lambda_k", ctypes.c_float), ("variant", ctypes.c_int32), ("ctas_per_particle", ctypes.c_int32)]
+
+
+# render kernels (same results, different work layout); AUTO picks by particles per call
+RENDER_AUTO, RENDER_UNITS, RENDER_TILES_32x16, RENDER_TILES_32x32, RENDER_TILES_64x32, RENDER_TILES_64x64 = range(6)
+RENDER_VARIANTS = {"auto": RENDER_AUTO, "units": RENDER_UNITS, "tiles32x16": RENDER_TILES_32x16,
+                   "tiles32x32": RENDER_TILES_32x32, "tiles64x32": RENDER_TILES_64x32,
+                   "tiles64x64": RENDER_TILES_64x64}
 
 
 class HsSwarm(ctypes.Structure):
@@ -91,6 +98,7 @@ _SIGS = {
                      ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(HsCamera), _vp, _vp, _vp], ctypes.c_int),
     "render_score_batch_noalloc": ([_vp, ctypes.POINTER(HsObs), ctypes.POINTER(HsCamera), _vp, _vp, ctypes.c_int,
                                     ctypes.POINTER(HsScoreParams), _vp, _vp, _vp], ctypes.c_int),
+    "hs_render_variant": ([ctypes.POINTER(HsScoreParams), ctypes.c_int], ctypes.c_int),
     "hs_batch_buffer_size": ([ctypes.POINTER(HsSwarmDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
                              ctypes.c_int),
     "hs_batch_create": ([_vp, ctypes.POINTER(HsSwarmDesc), ctypes.c_int, _vp, ctypes.c_size_t, _vp,
@@ -201,9 +209,18 @@ def camera(fx, fy, cx, cy) -> HsCamera:
     return HsCamera(fx, fy, cx, cy)
 
 
-def score_params(d_m=10.0, d_M=40.0, lam=20.0, lam_k=10.0) -> HsScoreParams:
-    """Eq. 4-5 constants (Section III.A: 1 cm, 4 cm, 20, 10) in mm."""
-    return HsScoreParams(d_m, d_M, lam, lam_k)
+def render_variant(params: HsScoreParams, P: int) -> str:
+    """Name of the render kernel a call over P particles runs with these parameters."""
+    v = lib().hs_render_variant(ctypes.byref(params), int(P))
+    _check("hs_render_variant", min(v, 0))
+    return {i: n for n, i in RENDER_VARIANTS.items()}[v]
+
+
+def score_params(d_m=10.0, d_M=40.0, lam=20.0, lam_k=10.0, variant=RENDER_AUTO, ctas_per_particle=0
+                 ) -> HsScoreParams:
+    """Eq. 4-5 constants (Section III.A: 1 cm, 4 cm, 20, 10) in mm, and the render's
+    launch shape (kernel variant, CTAs per particle; neither changes results)."""
+    return HsScoreParams(d_m, d_M, lam, lam_k, int(variant), int(ctas_per_particle))
 
 
 def pso_params(c1=2.8, c2=1.3, mutate_every=3, n_mutate=None, P=None) -> HsPsoParams:

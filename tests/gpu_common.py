@@ -83,7 +83,7 @@ class GpuResult:
     kc: np.ndarray
 
 
-def run_gpu(sc: Scene, debug=True, poses=None) -> GpuResult:
+def run_gpu(sc: Scene, debug=True, poses=None, variant=hs.RENDER_AUTO, ctas=0) -> GpuResult:
     poses = sc.poses if poses is None else poses
     P = poses.shape[0]
     dev = torch.device("cuda")
@@ -99,7 +99,8 @@ def run_gpu(sc: Scene, debug=True, poses=None) -> GpuResult:
     parts = torch.zeros(P, 4, dtype=torch.int32, device=dev)
     dd = torch.zeros(P, sc.H, sc.W, dtype=torch.float32, device=dev) if debug else None
     dm = torch.zeros(P, sc.H, sc.W, dtype=torch.uint8, device=dev) if debug else None
-    hs.render_score_batch(sc.model_g, obs, cam, prims, kc, hs.score_params(), ws, E, parts, dd, dm)
+    hs.render_score_batch(sc.model_g, obs, cam, prims, kc, hs.score_params(variant=variant, ctas_per_particle=ctas),
+                          ws, E, parts, dd, dm)
     torch.cuda.synchronize()
     pa = parts.cpu().numpy()
     parts_np = np.zeros((P, 4))

@@ -88,13 +88,28 @@ def test_fk_boxes_are_conservative():
     ("kinect_320x240_u16", 320, 240, 6, 2005070682, dict(noisy=True, f32=False)),
     ("edge_shifted_96x64", 96, 64, 8, 9, dict(zoom=2.0, shift=(70.0, 40.0))),
 ])
-def test_render_score_parity(name, W, H, P, seed, kw):
+@pytest.mark.parametrize("variant", sorted(set(hs.RENDER_VARIANTS.values()) - {hs.RENDER_AUTO}))
+def test_render_score_parity(name, W, H, P, seed, kw, variant):
     sc = C.make_scene(W, H, P, seed, **kw)
-    gr = C.run_gpu(sc)
+    gr = C.run_gpu(sc, variant=variant)
     o = C.run_oracle(sc)
     rep = {}
     C.check_parity(sc, gr, o, rep)
-    REPORT[name] = rep
+    REPORT[f"{name}/variant{variant}"] = rep
+
+
+@pytest.mark.parametrize("ctas", [1, 3, 16])
+def test_render_variants_agree(ctas):
+    """Every render kernel and launch shape gives the same counts and E (they
+    share the nearest-hit rule and integer sums; only the work layout differs)."""
+    sc = C.make_scene(200, 150, 40, 2005070683, noisy=True, f32=False, spread=1.5)
+    ref = C.run_gpu(sc, debug=True, variant=hs.RENDER_UNITS)
+    for v in sorted(set(hs.RENDER_VARIANTS.values()) - {hs.RENDER_AUTO}):
+        gr = C.run_gpu(sc, debug=True, variant=v, ctas=ctas)
+        assert np.array_equal(gr.parts[:, 1:], ref.parts[:, 1:]), v
+        assert np.array_equal(gr.mask, ref.mask), v
+        assert np.abs(gr.depth - ref.depth).max() <= 1e-4, v
+        assert np.all(np.abs(gr.E - ref.E) <= 1e-6 * np.abs(ref.E) + 1e-5), v
 
 
 def test_ground_truth_scores_zero_depth_term():
@@ -107,11 +122,12 @@ def test_ground_truth_scores_zero_depth_term():
     assert abs(D0) < 1e-3  # float32 observation of the FP64 render
 
 
-def test_brute_force_8x8():
+@pytest.mark.parametrize("variant", [hs.RENDER_UNITS, hs.RENDER_TILES_32x16, hs.RENDER_TILES_64x64])
+def test_brute_force_8x8(variant):
     """8x8 ROIs: every pixel compared one by one with the oracle."""
     for seed in (11, 12, 13):
         sc = C.make_scene(8, 8, 4, seed, cam=(20.0, 20.0, 4.0, 4.0), spread=0.3)
-        gr = C.run_gpu(sc)
+        gr = C.run_gpu(sc, variant=variant)
         o = C.run_oracle(sc)
         C.check_parity(sc, gr, o)
 
@@ -123,10 +139,10 @@ def test_empty_roi_and_offscreen_particles():
     far[1:, 0] = 60.0   # pushed to the limits of the view box
     far[1:, 1] = 120.0
     far[3:, 3] = 0.7
-    gr = C.run_gpu(sc, poses=far)
     o = C.run_oracle(sc, poses=far)
     sc2 = C.Scene(sc.W, sc.H, sc.cam, sc.gt, sc.Od, sc.S, far, sc.model_o, sc.model_g)
-    C.check_parity(sc2, gr, o)
+    for variant in (hs.RENDER_UNITS, hs.RENDER_TILES_64x32):
+        C.check_parity(sc2, C.run_gpu(sc, poses=far, variant=variant), o)
 
 
 def test_many_particles_sampled():
@@ -134,6 +150,9 @@ def test_many_particles_sampled():
     the per-pixel check on a sample."""
     sc = C.make_scene(64, 64, 1500, 105, spread=2.0)
     gr = C.run_gpu(sc, debug=False)
+    gt = C.run_gpu(sc, debug=False, variant=hs.RENDER_TILES_64x32)
+    assert np.all(np.abs(gt.E - gr.E) <= 1e-6 * np.abs(gr.E) + 1e-5)
+    assert np.array_equal(gt.parts[:, 1:], gr.parts[:, 1:])
     o = C.run_oracle(sc, per_pixel=False)
     err = np.abs(gr.E - o["E"])
     ok = err <= C.E_REL_TOL * np.abs(o["E"]) + C.E_ABS_TOL

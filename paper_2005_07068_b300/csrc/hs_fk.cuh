@@ -55,6 +55,40 @@ __device__ __forceinline__ void fk_load_model(FkShared& sh, const DevModel& mp)
 
 // FK of the raw pose `pose` [26] (global or shared memory): writes the particle's
 // n_prims records to prims [n_prims][4] and kc.  cam = (fx, fy, cx, cy).  Every
+// Widen [amin, amax] x [bmin, bmax] by the ray-direction range (a = x/z,
+// b = y/z) of the solid ellipse(s) {C + A w : |w| <= 1} with A A^T = Sg
+// (xx, yy, zz, xy, xz, yz).  A plane through the camera with normal n touches
+// it where (n.C)^2 = n^T Sg n; with n = (1, 0, -a) that is the quadratic
+// a^2 (Cz^2 - Szz) - 2 a (Cx Cz - Sxz) + (Cx^2 - Sxx) = 0, whose roots are the
+// exact bounds.  Its discriminant is expanded so that the ~Cz^2 Cx^2 terms
+// cancel symbolically.  Returns false unless the solid lies beyond the plane
+// z = 1 mm.
+__device__ __forceinline__ bool ellipse_ray_bounds(const float C[3], const float Sg[6], float& amin, float& amax,
+                                                   float& bmin, float& bmax)
+{
+    const float ez = sqrtf(fmaxf(Sg[2], 0.f));  // z half-extent
+    if (!(C[2] - ez >= 1.0f)) return false;
+    const float al = fmaf(C[2], C[2], -Sg[2]);
+    const float ial = 1.f / al;
+    {
+        const float be = fmaf(C[0], C[2], -Sg[4]);
+        const float disc = fmaf(Sg[0], C[2] * C[2], fmaf(-2.f * Sg[4], C[0] * C[2], fmaf(Sg[2], C[0] * C[0],
+                                fmaf(Sg[4], Sg[4], -Sg[0] * Sg[2]))));
+        const float sq = sqrtf(fmaxf(disc, 0.f));
+        amin = fminf(amin, (be - sq) * ial);
+        amax = fmaxf(amax, (be + sq) * ial);
+    }
+    {
+        const float be = fmaf(C[1], C[2], -Sg[5]);
+        const float disc = fmaf(Sg[1], C[2] * C[2], fmaf(-2.f * Sg[5], C[1] * C[2], fmaf(Sg[2], C[1] * C[1],
+                                fmaf(Sg[5], Sg[5], -Sg[1] * Sg[2]))));
+        const float sq = sqrtf(fmaxf(disc, 0.f));
+        bmin = fminf(bmin, (be - sq) * ial);
+        bmax = fmaxf(bmax, (be + sq) * ial);
+    }
+    return true;
+}
+
 // thread of the 64-thread CTA must call it (it synchronises the CTA).
 __device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, float4 cam, float4* prims, float* kc,
                                             uint32_t* status)
@@ -137,14 +171,6 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, flo
         for (int i = 0; i < 3; ++i)
             C[i] = q[i] + fmaf(R[3 * i], D.center[0], fmaf(R[3 * i + 1], D.center[1], fmaf(R[3 * i + 2], D.center[2], O[i])));
         const bool cone = D.kind == HS_PRIM_ECONE;
-        // box half extents e (local x, y, z)
-        float e[3];
-        if (cone) {
-            const float grow = 1.f + fabsf(D.dims[3]);
-            e[0] = D.dims[0] * grow; e[1] = D.dims[2]; e[2] = D.dims[1] * grow;
-        } else {
-            e[0] = D.dims[0]; e[1] = D.dims[1]; e[2] = D.dims[2];
-        }
         const float is0 = D.inv_s[0], is1 = D.inv_s[1], is2 = D.inv_s[2];
         // column j of M = S^-1 R^T is (R[j][0]/s0, R[j][1]/s1, R[j][2]/s2)
         float rec[16];
@@ -161,21 +187,39 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, flo
         rec[11] = C[2];
         rec[12] = __uint_as_float(cone ? (uint32_t)D.caps : 0u);  // visible cone caps
         rec[13] = cone ? D.dims[3] : kEllipsoidMarker;
-        // conservative pixel box from the 8 projected corners of the local box
+        // the exact ray-direction bounds of the solid (a, b ranges), from its
+        // ellipse(s): the ellipsoid itself, or the cone's two end ellipses (the
+        // truncated cone is their convex hull, whose box is the union of theirs)
         float amin = FLT_MAX, amax = -FLT_MAX, bmin = FLT_MAX, bmax = -FLT_MAX;
         bool behind = false;
+        if (cone) {
+            const float ax = D.dims[0], az = D.dims[1], hl = D.dims[2], kap = D.dims[3];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float sx = (c & 1) ? e[0] : -e[0], sy = (c & 2) ? e[1] : -e[1], sz = (c & 4) ? e[2] : -e[2];
-            const float X = fmaf(R[0], sx, fmaf(R[1], sy, fmaf(R[2], sz, C[0])));
-            const float Y = fmaf(R[3], sx, fmaf(R[4], sy, fmaf(R[5], sz, C[1])));
-            const float Z = fmaf(R[6], sx, fmaf(R[7], sy, fmaf(R[8], sz, C[2])));
-            behind |= !(Z >= 1.0f);
-            const float iz = rcp_approx(Z);  // the box keeps a 1-pixel margin
-            amin = fminf(amin, X * iz);
-            amax = fmaxf(amax, X * iz);
-            bmin = fminf(bmin, Y * iz);
-            bmax = fmaxf(bmax, Y * iz);
+            for (int c = 0; c < 2; ++c) {
+                const float sgn = c ? 1.f : -1.f;
+                const float g = 1.f + sgn * kap;  // section scale at Y = sgn
+                const float u2 = ax * ax * g * g, w2 = az * az * g * g;
+                float Sg[6];  // u2 r0 r0^T + w2 r2 r2^T (r_k = column k of R)
+                Sg[0] = fmaf(u2, R[0] * R[0], w2 * R[2] * R[2]);
+                Sg[1] = fmaf(u2, R[3] * R[3], w2 * R[5] * R[5]);
+                Sg[2] = fmaf(u2, R[6] * R[6], w2 * R[8] * R[8]);
+                Sg[3] = fmaf(u2, R[0] * R[3], w2 * R[2] * R[5]);
+                Sg[4] = fmaf(u2, R[0] * R[6], w2 * R[2] * R[8]);
+                Sg[5] = fmaf(u2, R[3] * R[6], w2 * R[5] * R[8]);
+                const float Cc[3] = {fmaf(sgn * hl, R[1], C[0]), fmaf(sgn * hl, R[4], C[1]),
+                                     fmaf(sgn * hl, R[7], C[2])};
+                behind |= !ellipse_ray_bounds(Cc, Sg, amin, amax, bmin, bmax);
+            }
+        } else {
+            const float s0 = D.dims[0] * D.dims[0], s1 = D.dims[1] * D.dims[1], s2 = D.dims[2] * D.dims[2];
+            float Sg[6];  // R diag(s^2) R^T
+            Sg[0] = fmaf(R[0] * R[0], s0, fmaf(R[1] * R[1], s1, R[2] * R[2] * s2));
+            Sg[1] = fmaf(R[3] * R[3], s0, fmaf(R[4] * R[4], s1, R[5] * R[5] * s2));
+            Sg[2] = fmaf(R[6] * R[6], s0, fmaf(R[7] * R[7], s1, R[8] * R[8] * s2));
+            Sg[3] = fmaf(R[0] * R[3], s0, fmaf(R[1] * R[4], s1, R[2] * R[5] * s2));
+            Sg[4] = fmaf(R[0] * R[6], s0, fmaf(R[1] * R[7], s1, R[2] * R[8] * s2));
+            Sg[5] = fmaf(R[3] * R[6], s0, fmaf(R[4] * R[7], s1, R[5] * R[8] * s2));
+            behind = !ellipse_ray_bounds(C, Sg, amin, amax, bmin, bmax);
         }
         int u0, v0, u1, v1;
         if (behind) {

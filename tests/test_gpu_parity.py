@@ -64,9 +64,12 @@ def test_fk_records_match_oracle():
 
 def test_fk_boxes_are_conservative():
     """Every pixel a primitive covers (oracle render of that primitive alone)
-    lies inside the box pose_fk wrote for it."""
+    lies inside the box pose_fk wrote for it, and the box is the exact bound of
+    the projected solid: within 2 px of the covered pixels on every side (one
+    pixel of margin plus the pixel-centre sampling) when nothing is clipped."""
     sc = C.make_scene(96, 72, 4, 102, zoom=1.6)
     gr = C.run_gpu(sc, debug=False)
+    slack = []
     for p in range(4):
         f = oracle.fk(sc.model_o, sc.poses[p].astype(np.float64))
         for k in range(sc.model_o.np_):
@@ -77,6 +80,13 @@ def test_fk_boxes_are_conservative():
             vv, uu = np.nonzero(hit)
             if len(uu):
                 assert uu.min() >= w[0] and uu.max() <= w[2] and vv.min() >= w[1] and vv.max() <= w[3], (p, k)
+                inside = uu.min() > 0 and vv.min() > 0 and uu.max() < sc.W - 1 and vv.max() < sc.H - 1
+                if inside and len(uu) >= 20:
+                    d = (uu.min() - w[0], vv.min() - w[1], w[2] - uu.max(), w[3] - vv.max())
+                    slack.append(max(d))
+                    assert max(d) <= 2, (p, k, d)
+    assert len(slack) > 40
+    REPORT["fk_box_max_slack_px"] = int(max(slack))
 
 
 # ---- render + cost ------------------------------------------------------------------

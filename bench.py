@@ -62,8 +62,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample")
     ap.add_argument("--profile", action="store_true", help="short run for an ncu launch list")
     ap.add_argument("--no-roofline", action="store_true", help="skip the render roofline replay")
-    ap.add_argument("--render", default="auto", help="render kernel: auto, units, tiles32x16, tiles32x32, "
-                    "tiles64x32, tiles64x64")
+    ap.add_argument("--render", default="tune", help="render kernel: tune (timed on the workload first), auto, "
+                    "units, tiles32x16, tiles32x32, tiles64x32, tiles64x64")
     ap.add_argument("--ctas", type=int, default=0, help="render CTAs per particle (0 = automatic)")
     ap.add_argument("--workload", choices=["kinect", "batch"], default="kinect",
                     help="kinect: one 320x240 sequence (the headline); batch: 64 sequences with uneven ROIs and P")
@@ -343,9 +343,13 @@ def run_batch(args, rank, world, local):
         st.upload(non_blocking=False)
     staging = PackedObs(sizes, device=dev, pinned=False)  # the buffers the batch is bound to
     batch = hs.Batch(model, staging.obs, cams, Ps, seq_seeds)
-    score = hs.score_params(variant=hs.RENDER_VARIANTS[args.render], ctas_per_particle=args.ctas)
+    score = hs.score_params(variant=hs.RENDER_VARIANTS.get(args.render, 0), ctas_per_particle=args.ctas)
     trk = BatchTracker(model, batch, GENS, device=dev, score=score)
     gt0 = torch.from_numpy(np.stack([t[0] for t in trajs])).to(dev)
+    tune = None
+    if args.render == "tune":
+        staging.dev.copy_(store[0].dev)
+        tune = trk.autotune(gt0)
     graphs = [trk.graph(f, gt0 if f == 0 else None) for f in range(frames)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -490,7 +494,9 @@ def run_batch(args, rank, world, local):
                            "frames": frames, "step": f"one frame of every sequence = one CUDA graph "
                                                      f"({trk.launches_per_frame()} kernels) + one frame copy",
                            "l2": "flushed between steps (256 MiB write outside the step events)",
-                           "parallelism": f"replicas x{world}", "wall_s": wall},
+                           "parallelism": f"replicas x{world}", "wall_s": wall,
+                           "render": {"kernel": hs.render_variant(trk.score, Pt),
+                                      "ctas_per_particle": trk.score.ctas_per_particle, "autotune_us": tune}},
                 "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99),
                                "what": "per-frame latency of every sequence (one step advances all of them)"},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
@@ -541,8 +547,9 @@ def main():
     frames = min(FRAMES, max(args.steps + args.warmup, 2)) if args.profile else FRAMES
     traj, obs, host = make_frames(seed, frames, hs, I, model, cam, dev)
     gt0 = torch.from_numpy(traj[0]).to(dev)
-    score = hs.score_params(variant=hs.RENDER_VARIANTS[args.render], ctas_per_particle=args.ctas)
+    score = hs.score_params(variant=hs.RENDER_VARIANTS.get(args.render, 0), ctas_per_particle=args.ctas)
     trk = Tracker(model, cam, PARTICLES, GENS, seed=seed, device=dev, score=score)
+    tune = trk.autotune(obs[0], gt0) if args.render == "tune" else None
     graphs = [trk.graph(obs[f], f, gt0 if f == 0 else None) for f in range(frames)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -690,7 +697,9 @@ def main():
                            "frames": frames,
                            "step": f"one frame = one CUDA graph ({trk.launches_per_frame()} kernels)",
                            "l2": "flushed between steps (256 MiB write outside the step events)",
-                           "parallelism": f"replicas x{world}", "wall_s": wall},
+                           "parallelism": f"replicas x{world}", "wall_s": wall,
+                           "render": {"kernel": hs.render_variant(trk.score, PARTICLES),
+                                      "ctas_per_particle": trk.score.ctas_per_particle, "autotune_us": tune}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
                 "gpu_launches": K * trk.launches_per_frame()}
         print(json.dumps(line), flush=True)

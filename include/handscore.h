@@ -354,6 +354,29 @@ int pso_step_fk_multi(const HsModel* model, const HsBatch* batch, const HsSwarm*
                       const HsPsoParams* params, uint32_t frame, uint32_t gen, HsPrim* prims, float* kc,
                       hs_stream_t stream);
 
+/* ---- render autotuning -----------------------------------------------------------
+ * Time every render kernel (HS_RENDER_UNITS .. HS_RENDER_TILES_64x64) with CTAs
+ * per particle from {automatic, 1, 2, 4, 8, 16, 32} (more than 1 only while
+ * K * P stays within about four resident waves) on the caller's own inputs, and
+ * write the fastest into params->variant and params->ctas_per_particle (the
+ * Eq. 4-5 constants are kept).  The choice never changes results, only time.
+ * Each candidate's `reps` calls are captured into a CUDA graph on a private
+ * stream (after `stream` is synchronised), launched once untimed and once
+ * between two CUDA events; the call synchronises and must not itself be
+ * captured.
+ * times_us (may be NULL) receives [HS_RENDER_VARIANTS][HS_TUNE_CTAS] average
+ * microseconds per call, -1 where not tried.  E receives the last call's
+ * objectives.  Errors: as render_score_batch / render_score_multi, and
+ * HS_ERR_ARG for reps outside 1..1000.  The paper has no counterpart: its
+ * render is a fixed OpenGL pipeline. */
+#define HS_TUNE_CTAS 7
+int render_score_batch_autotune(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsPrim* prims,
+                                const float* kc, int P, HsScoreParams* params, void* workspace,
+                                size_t workspace_bytes, float* E, int reps, float* times_us, hs_stream_t stream);
+int render_score_multi_autotune(const HsModel* model, const HsBatch* batch, const HsPrim* prims, const float* kc,
+                                HsScoreParams* params, void* workspace, size_t workspace_bytes, float* E, int reps,
+                                float* times_us, hs_stream_t stream);
+
 /* Read (and optionally clear) the device status word of the current device.
  * Synchronises the device.  out: host.  Errors: HS_ERR_ARG, HS_ERR_CUDA. */
 int hs_get_device_status(uint32_t* out, int clear);

@@ -727,6 +727,115 @@ int pso_step_fk_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw,
     return launch_pso_step_fk(model->dev, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 
+// ---- render autotuning -------------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+constexpr int kTuneCtas[HS_TUNE_CTAS] = {0, 1, 2, 4, 8, 16, 32};  // 0: the automatic choice
+
+// Times every (kernel, CTAs per particle) candidate of one render call and keeps
+// the fastest.  Each candidate's `reps` calls are captured into a CUDA graph on
+// a private stream (so host-side set-up does not pace them, as in a tracker's
+// graph) after one eager call, and the graph is launched once untimed and once
+// between two CUDA events.
+// launch(params, stream) issues one call.
+template <class Launch>
+int autotune(HsScoreParams* params, int P, int reps, float* times_us, cudaStream_t stream, Launch&& launch)
+{
+    if (reps < 1 || reps > 1000) return HS_ERR_ARG;
+    if (times_us)
+        for (int i = 0; i < HS_RENDER_VARIANTS * HS_TUNE_CTAS; ++i) times_us[i] = -1.f;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = HS_OK;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess || cudaStreamSynchronize(stream) != cudaSuccess)
+        rc = HS_ERR_CUDA;
+    HsScoreParams best = *params;
+    float best_us = INFINITY;
+    for (int v = HS_RENDER_UNITS; v < HS_RENDER_VARIANTS && rc == HS_OK; ++v) {
+        for (int c = 0; c < HS_TUNE_CTAS && rc == HS_OK; ++c) {
+            // more CTAs per particle only while the launch stays within a few waves
+            if (kTuneCtas[c] > 1 && (long long)kTuneCtas[c] * P > 4LL * kTargetCtas) break;
+            HsScoreParams cand = *params;
+            cand.variant = v;
+            cand.ctas_per_particle = kTuneCtas[c];
+            // one eager call first: lazy set-up (module loading, symbol lookups,
+            // the shared-memory opt-in) must not happen during capture
+            if ((rc = launch(cand, cs)) != HS_OK) break;
+            if (cudaStreamSynchronize(cs) != cudaSuccess) {
+                rc = HS_ERR_CUDA;
+                break;
+            }
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                rc = HS_ERR_CUDA;
+                break;
+            }
+            int lrc = HS_OK;
+            for (int r = 0; r < reps && lrc == HS_OK; ++r) lrc = launch(cand, cs);
+            const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+            if (lrc != HS_OK || ec != cudaSuccess) rc = lrc != HS_OK ? lrc : HS_ERR_CUDA;
+            if (rc == HS_OK && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) rc = HS_ERR_CUDA;
+            float ms = 0.f;
+            if (rc == HS_OK &&
+                (cudaGraphLaunch(ge, cs) != cudaSuccess || cudaEventRecord(e0, cs) != cudaSuccess ||
+                 cudaGraphLaunch(ge, cs) != cudaSuccess || cudaEventRecord(e1, cs) != cudaSuccess ||
+                 cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = HS_ERR_CUDA;
+            if (ge) cudaGraphExecDestroy(ge);
+            if (g) cudaGraphDestroy(g);
+            if (rc != HS_OK) break;
+            const float us = ms * 1e3f / (float)reps;
+            if (times_us) times_us[v * HS_TUNE_CTAS + c] = us;
+            if (us < best_us) {
+                best_us = us;
+                best = cand;
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (cs) cudaStreamDestroy(cs);
+    if (rc == HS_OK) *params = best;
+    return rc;
+}
+}  // namespace
+
+extern "C" {
+
+int render_score_batch_autotune(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsPrim* prims,
+                                const float* kc, int P, HsScoreParams* params, void* workspace,
+                                size_t workspace_bytes, float* E, int reps, float* times_us, hs_stream_t stream)
+{
+    if (!params) return HS_ERR_ARG;
+    // every argument is checked by a call that launches nothing
+    int rc = render_score_batch(model, obs, cam, prims, kc, 0, params, workspace, workspace_bytes, E, nullptr,
+                                nullptr, nullptr, stream);
+    if (rc) return rc;
+    if (P < 1 || P > HS_MAX_PARTICLES) return HS_ERR_SIZE;
+    return autotune(params, P, reps, times_us, (cudaStream_t)stream, [&](const HsScoreParams& c, cudaStream_t cs) {
+        return render_score_batch(model, obs, cam, prims, kc, P, &c, workspace, workspace_bytes, E, nullptr, nullptr,
+                                  nullptr, (hs_stream_t)cs);
+    });
+}
+
+int render_score_multi_autotune(const HsModel* model, const HsBatch* batch, const HsPrim* prims, const float* kc,
+                                HsScoreParams* params, void* workspace, size_t workspace_bytes, float* E, int reps,
+                                float* times_us, hs_stream_t stream)
+{
+    if (!model || !batch || !params) return HS_ERR_ARG;
+    int rc = validate_score_params(params);
+    if (rc) return rc;
+    return autotune(params, batch->P_total, reps, times_us, (cudaStream_t)stream,
+                    [&](const HsScoreParams& c, cudaStream_t cs) {
+                        return render_score_multi(model, batch, prims, kc, &c, workspace, workspace_bytes, E, nullptr,
+                                                  (hs_stream_t)cs);
+                    });
+}
+
 int hs_get_device_status(uint32_t* out, int clear)
 {
     if (!out) return HS_ERR_ARG;

@@ -99,6 +99,11 @@ _SIGS = {
     "render_score_batch_noalloc": ([_vp, ctypes.POINTER(HsObs), ctypes.POINTER(HsCamera), _vp, _vp, ctypes.c_int,
                                     ctypes.POINTER(HsScoreParams), _vp, _vp, _vp], ctypes.c_int),
     "hs_render_variant": ([ctypes.POINTER(HsScoreParams), ctypes.c_int], ctypes.c_int),
+    "render_score_batch_autotune": ([_vp, ctypes.POINTER(HsObs), ctypes.POINTER(HsCamera), _vp, _vp, ctypes.c_int,
+                                     ctypes.POINTER(HsScoreParams), _vp, ctypes.c_size_t, _vp, ctypes.c_int, _vp, _vp],
+                                    ctypes.c_int),
+    "render_score_multi_autotune": ([_vp, _vp, _vp, _vp, ctypes.POINTER(HsScoreParams), _vp, ctypes.c_size_t, _vp,
+                                     ctypes.c_int, _vp, _vp], ctypes.c_int),
     "hs_batch_buffer_size": ([ctypes.POINTER(HsSwarmDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
                              ctypes.c_int),
     "hs_batch_create": ([_vp, ctypes.POINTER(HsSwarmDesc), ctypes.c_int, _vp, ctypes.c_size_t, _vp,
@@ -443,6 +448,46 @@ def batch_swarm(batch: Batch, device="cuda") -> Swarm:
     Pt, S = batch.P_total, batch.S
     return Swarm(torch.zeros(Pt, NDOF, **f), torch.zeros(Pt, NDOF, **f), torch.zeros(Pt, NDOF, **f),
                  torch.zeros(Pt, **f), torch.zeros(S, NDOF, **f), torch.zeros(S, **f), torch.zeros(Pt, **f))
+
+
+TUNE_CTAS = (0, 1, 2, 4, 8, 16, 32)  # 0: the automatic choice
+
+
+def _tune_table(times) -> dict:
+    names = {i: n for n, i in RENDER_VARIANTS.items()}
+    out = {}
+    for v in range(1, len(RENDER_VARIANTS)):
+        for c, k in enumerate(TUNE_CTAS):
+            t = times[v * len(TUNE_CTAS) + c]
+            if t >= 0:
+                out[f"{names[v]}/k{k}"] = float(t)
+    return out
+
+
+def render_score_batch_autotune(model: Model, obs: Obs, cam: HsCamera, prims: torch.Tensor, kc: torch.Tensor,
+                                params: HsScoreParams, ws: torch.Tensor, E: torch.Tensor, reps: int = 5,
+                                stream=None) -> tuple[HsScoreParams, dict]:
+    """The fastest render launch shape for these inputs: (params with variant and
+    CTAs per particle set, {candidate: microseconds per call})."""
+    out = HsScoreParams(*[getattr(params, f) for f, _ in HsScoreParams._fields_])
+    times = (ctypes.c_float * (len(RENDER_VARIANTS) * len(TUNE_CTAS)))()
+    st = obs.struct()
+    _check("render_score_batch_autotune",
+           lib().render_score_batch_autotune(model.handle, ctypes.byref(st), ctypes.byref(cam), _ptr(prims), _ptr(kc),
+                                             kc.shape[0], ctypes.byref(out), _ptr(ws), ws.numel(), _ptr(E), reps,
+                                             times, _stream(stream)))
+    return out, _tune_table(times)
+
+
+def render_score_multi_autotune(model: Model, batch: "Batch", prims: torch.Tensor, kc: torch.Tensor,
+                                params: HsScoreParams, ws: torch.Tensor, E: torch.Tensor, reps: int = 5,
+                                stream=None) -> tuple[HsScoreParams, dict]:
+    out = HsScoreParams(*[getattr(params, f) for f, _ in HsScoreParams._fields_])
+    times = (ctypes.c_float * (len(RENDER_VARIANTS) * len(TUNE_CTAS)))()
+    _check("render_score_multi_autotune",
+           lib().render_score_multi_autotune(model.handle, batch.handle, _ptr(prims), _ptr(kc), ctypes.byref(out),
+                                             _ptr(ws), ws.numel(), _ptr(E), reps, times, _stream(stream)))
+    return out, _tune_table(times)
 
 
 def hs_get_device_status(clear: bool = False) -> int:

@@ -99,6 +99,23 @@ class Tracker:
         else:
             self.enqueue_frame(obs, frame, seed_pose)
 
+    def autotune(self, obs: hs.Obs, seed_pose: torch.Tensor, reps: int = 5) -> dict:
+        """Pick the fastest render launch shape for this workload (the initial
+        swarm of a frame around seed_pose) and use it from now on; returns the
+        timing table.  Leaves the tracker's state as it was."""
+        saved = [t.clone() for t in self._state()]
+        self.seed_pose.copy_(seed_pose)
+        hs.hs_obs_prepare(obs)
+        self.swarm.x = self.x_buf[0]
+        hs.pso_init(self.model, self.swarm, self.seed_pose, self.scale, self.seed, 0)
+        hs.pose_fk(self.model, self.swarm.x, self.cam, self.prims, self.kc)
+        self.score, table = hs.render_score_batch_autotune(self.model, obs, self.cam, self.prims, self.kc, self.score,
+                                                           self.ws, self.swarm.E, reps)
+        for t, v in zip(self._state(), saved):
+            t.copy_(v)
+        self._graphs.clear()
+        return table
+
     def launches_per_frame(self) -> int:
         """Kernels of this library per frame: obs stats, init, FK, 2 per generation."""
         return 3 + 2 * self.gens
@@ -232,6 +249,23 @@ class BatchTracker:
             self.graph(frame, seed_poses).replay()
         else:
             self.enqueue_frame(frame, seed_poses)
+
+    def autotune(self, seed_poses: torch.Tensor, reps: int = 5) -> dict:
+        """Pick the fastest render launch shape for the batch (the initial swarms
+        around seed_poses [S, 26], the observations currently bound) and use it
+        from now on; returns the timing table.  Leaves the state as it was."""
+        saved = [t.clone() for t in self._state()]
+        self.seed_poses.copy_(seed_poses)
+        hs.hs_obs_prepare_multi(self.batch)
+        self.swarm.x = self.x_buf[0]
+        hs.pso_init_multi(self.model, self.batch, self.swarm, self.seed_poses, self.scale, 0)
+        hs.pose_fk_multi(self.model, self.batch, self.swarm.x, self.prims, self.kc)
+        self.score, table = hs.render_score_multi_autotune(self.model, self.batch, self.prims, self.kc, self.score,
+                                                           self.ws, self.swarm.E, reps)
+        for t, v in zip(self._state(), saved):
+            t.copy_(v)
+        self._graphs.clear()
+        return table
 
     def launches_per_frame(self) -> int:
         """Kernels per frame for all swarms: 2 observation passes, init, FK, 2 per generation."""

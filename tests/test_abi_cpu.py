@@ -188,6 +188,20 @@ def test_other_host_checks():
     assert L.pso_step_fk(m.handle, ctypes.byref(sw), FAKE + 4096, 2000, ctypes.byref(pp), 1, 0, 1, ctypes.byref(cam),
                          FAKE, FAKE, None) == hs.HS_ERR_SIZE
     assert hs.lib().hs_status_string(-3) == b"size out of range"
+    # render launch shape: variant and CTAs per particle are validated; autotuning needs params and reps >= 1
+    bad_v = hs.score_params(variant=9)
+    assert L.render_score_batch(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 64, ctypes.byref(bad_v),
+                                FAKE, 1 << 20, FAKE, None, None, None, None) == hs.HS_ERR_ARG
+    bad_k = hs.score_params(ctas_per_particle=65)
+    assert L.render_score_batch(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 64, ctypes.byref(bad_k),
+                                FAKE, 1 << 20, FAKE, None, None, None, None) == hs.HS_ERR_ARG
+    assert L.hs_render_variant(ctypes.byref(prm), 64) == hs.RENDER_UNITS
+    assert L.hs_render_variant(ctypes.byref(prm), 5000) == hs.RENDER_TILES_64x32
+    assert L.hs_render_variant(ctypes.byref(bad_v), 64) == hs.HS_ERR_ARG
+    assert L.render_score_batch_autotune(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 64, None, FAKE,
+                                         1 << 20, FAKE, 3, None, None) == hs.HS_ERR_ARG
+    assert L.render_score_batch_autotune(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 64,
+                                         ctypes.byref(prm), FAKE, 1 << 20, FAKE, 0, None, None) == hs.HS_ERR_ARG
 
 
 def _descs(P, **obs_kw):

@@ -178,3 +178,36 @@ def test_batch_of_many_small_swarms():
     for s in (0, 17, 39):
         gr = C.run_gpu(sc, debug=False, poses=poses[s])
         assert np.array_equal(E[60 * s:60 * (s + 1)].cpu().numpy(), gr.E), s
+
+
+def test_autotune_picks_a_valid_shape_and_keeps_results(scenes):
+    """The autotuner times real candidates, returns one of them, and the choice
+    does not change E (single swarm and batch)."""
+    sc = scenes[2]
+    gr = C.run_gpu(sc, debug=False)
+    dev = torch.device("cuda")
+    obs = hs.Obs.from_numpy(sc.Od, sc.S, dev)
+    hs.hs_obs_prepare(obs)
+    cam = hs.camera(*[float(v) for v in sc.cam])
+    P = sc.poses.shape[0]
+    prims = torch.from_numpy(gr.prims).to(dev)
+    kc = torch.from_numpy(gr.kc).to(dev)
+    E = torch.zeros(P, device=dev)
+    prm, table = hs.render_score_batch_autotune(sc.model_g, obs, cam, prims, kc, hs.score_params(),
+                                                hs.new_workspace(P), E, reps=2)
+    assert prm.variant in range(1, 6) and prm.ctas_per_particle in hs.TUNE_CTAS
+    assert len(table) >= 5 and all(t > 0 for t in table.values())
+    assert min(table.values()) == table[f"{hs.render_variant(prm, P)}/k{prm.ctas_per_particle}"]
+    assert np.float32(prm.d_M) == 40.0
+    E2 = torch.zeros(P, device=dev)
+    hs.render_score_batch(sc.model_g, obs, cam, prims, kc, prm, hs.new_workspace(P), E2)
+    torch.cuda.synchronize()
+    assert np.all(np.abs(E2.cpu().numpy() - gr.E) <= 1e-6 * np.abs(gr.E) + 1e-5)
+    # the batch tracker's tuning leaves its state untouched
+    obs_l, cams, b = _batch(scenes)
+    bt = T.BatchTracker(sc.model_g, b, gens=3)
+    before = [t.clone() for t in bt._state()]
+    starts = torch.from_numpy(np.stack([s.poses[0] for s in scenes])).cuda()
+    table = bt.autotune(starts, reps=1)
+    assert bt.score.variant in range(1, 6) and len(table) >= 5
+    assert all(torch.equal(a, c) for a, c in zip(before, bt._state()))

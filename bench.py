@@ -80,19 +80,39 @@ def measured_peaks():
         return {}
 
 
-def profile_traffic(kernel_src: str):
-    """dram bytes per launch from the committed ncu summary, if it was taken on
-    the current source of the kernel; else None."""
-    path = os.path.join(ROOT, "profiles", "render_score_batch_kinect_320x240.txt")
+CSRC = os.path.join(ROOT, "paper_2005_07068_b300", "csrc")
+# the render kernels' sources, and the committed ncu summary taken on them
+KERNEL_SOURCES = {
+    "units": ["render_score.cu", "hs_render.cuh", "hs_args.cuh", "hs_device.cuh"],
+    "tiles": ["render_tiles.cu", "hs_render.cuh", "hs_args.cuh", "hs_device.cuh"],
+}
+PROFILE_FILES = {("kinect", "units"): "render_units_kinect_320x240.txt",
+                 ("batch", "tiles"): "render_tiles64x32_batch_64seq.txt"}
+
+
+def source_sha256(kind: str) -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kind]:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profile_traffic(workload: str, kernel: str):
+    """dram bytes per launch from the committed ncu summary of this workload's
+    render kernel, if it was taken on the kernel's current source; else None."""
+    kind = "units" if kernel == "units" else "tiles"
+    name = PROFILE_FILES.get((workload, kind))
+    if name is None or (kind == "tiles" and kernel != "tiles64x32"):
+        return None
     try:
         kv = {}
-        with open(path) as f:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             for line in f:
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
-        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-        if kv.get("source_sha256") != sha:
+        if kv.get("source_sha256") != source_sha256(kind):
             return None
         return float(kv["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -444,7 +464,7 @@ def run_batch(args, rank, world, local):
     flop_launch = sum(flops) / len(flops)
     achieved = flop_launch / (render_us * 1e-6) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
+                "frac": achieved / peak_tflops, "traffic": profile_traffic("batch", hs.render_variant(trk.score, Pt)),
                 "kernel": f"render_score_multi ({hs.render_variant(trk.score, Pt)})",
                 "peak_basis": f"FP32: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {sm_max:.0f} MHz "
                               f"(sm_max_mhz of measured)",
@@ -641,7 +661,7 @@ def main():
     peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     flop_launch = sum(flops) / len(flops) if flops else 0.0
     achieved = flop_launch / (render_us * 1e-6) / 1e12 if render_us else 0.0
-    traffic = profile_traffic(os.path.join(ROOT, "paper_2005_07068_b300", "csrc", "render_score.cu"))
+    traffic = profile_traffic("kinect", hs.render_variant(trk.score, PARTICLES))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "kernel": f"render_score_batch ({hs.render_variant(trk.score, PARTICLES)})",

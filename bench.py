@@ -65,8 +65,12 @@ def parse():
     ap.add_argument("--render", default="tune", help="render kernel: tune (timed on the workload first), auto, "
                     "units, tiles32x16, tiles32x32, tiles64x32, tiles64x64")
     ap.add_argument("--ctas", type=int, default=0, help="render CTAs per particle (0 = automatic)")
-    ap.add_argument("--workload", choices=["kinect", "batch"], default="kinect",
-                    help="kinect: one 320x240 sequence (the headline); batch: 64 sequences with uneven ROIs and P")
+    ap.add_argument("--workload", choices=["kinect", "batch", "fullframe"], default="kinect",
+                    help="kinect: one 320x240 sequence (the headline); batch: 64 sequences with uneven ROIs and P; "
+                         "fullframe: 640x480 sequence, s/frame to <= 5 deg at several swarm sizes")
+    ap.add_argument("--particles", default="256,1024,4096", help="fullframe: swarm sizes")
+    ap.add_argument("--frames", type=int, default=100, help="fullframe: frames of the sequence")
+    ap.add_argument("--gens", default="5,10,20,50", help="fullframe: generation budgets per frame")
     return ap.parse_args()
 
 
@@ -528,6 +532,142 @@ def run_batch(args, rank, world, local):
     return 0
 
 
+# ---- full frames: seconds per frame to <= 5 degrees -----------------------------------------
+
+FULL_W, FULL_H, FULL_GENS = 640, 480, 50
+FULL_METRIC = "s/frame to track within 5 deg mean joint error (640x480, plain PSO)"
+FULL_WORKLOAD = ("full-frame tracking: 640x480 uint16 depth + uint8 skin (Kinect noise recipe), seeded 100-frame "
+                 "trajectory (<= 5 deg / 5 mm per frame), frame 0 from the ground truth perturbed by U[+-10 deg, "
+                 "+-10 mm], swarm sizes 256 / 1024 / 4096 x generation budgets 5 / 10 / 20 / 50 per frame")
+
+
+def replay_render_us(dev, renders, reps: int = 3) -> float:
+    """Average microseconds per render launch of `renders()` (n launches) replayed
+    back to back from one captured graph, CUDA events on the launching stream."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        n = renders()
+    stream.wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        renders()
+    g.replay()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        g.replay()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b) * 1e3 / (reps * n)
+
+
+def run_fullframe(args, rank, world, local):
+    import torch
+    from paper_2005_07068_b300 import build as B
+    from paper_2005_07068_b300 import handscore as hs
+    from paper_2005_07068_b300 import inputs as I
+    from paper_2005_07068_b300 import replicas as R
+    from paper_2005_07068_b300 import sweep as SW
+    from paper_2005_07068_b300.tracker import Tracker
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks = measured_peaks()
+    seed = R.replica_seed(I.CONFIG_SEED_BASE + 5, rank)
+    g = I.hand_geometry()
+    lo, hi = (a.astype(np.float32) for a in I.search_limits())
+    model = hs.Model.from_geometry(g, lo, hi)
+    camt = I.kinect_camera(FULL_W, FULL_H)
+    cam = hs.camera(camt.fx, camt.fy, camt.cx, camt.cy)
+    frames = max(2, args.frames)
+    traj, obs, _ = make_frames(seed, frames, hs, I, model, cam, dev, W=FULL_W, H=FULL_H)
+    rng = np.random.default_rng(seed)
+    start_np = np.clip(traj[0] + rng.uniform(-1, 1, 26) * I.perturbation_scale(), lo, hi).astype(np.float32)
+    start = torch.from_numpy(start_np).to(dev)
+    kinds = g.prims_i[:, 1]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz") or 2032.0)
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    settings, per_p = [], []
+    gen_budgets = [int(v) for v in args.gens.split(",") if v]
+    with ClockSampler(local) as clk:
+        for P in [int(v) for v in args.particles.split(",") if v]:
+            score = hs.score_params(variant=hs.RENDER_VARIANTS.get(args.render, 0), ctas_per_particle=args.ctas)
+            tune = None
+            if args.render == "tune":
+                tuner = Tracker(model, cam, P, 1, seed=seed, device=dev, score=score)
+                tune = tuner.autotune(obs[0], start)
+                score = tuner.score
+                del tuner
+            for G in gen_budgets:
+                trk = Tracker(model, cam, P, G, seed=seed, device=dev, score=score)
+                results = SW.track_sequence(trk, obs, traj, start, frames=frames)
+                summ = SW.summarize(results)
+                summ.update({"particles": P, "generations": G,
+                             "evals_per_s": P * G * frames / (sum(r.frame_ms for r in results) * 1e-3)})
+                settings.append(summ)
+                del trk
+            # render roofline at this P: the launches of frame 0 (50 generations) replayed back to back
+            trk = Tracker(model, cam, P, FULL_GENS, seed=seed, device=dev, score=score)
+            hist_p = torch.zeros(FULL_GENS, P, model.n_prims, 16, device=dev)
+            hist_k = torch.zeros(FULL_GENS, P, device=dev)
+            cur, nxt = trk.x_buf
+            trk.swarm.x = cur
+            trk.seed_pose.copy_(start)
+            hs.hs_obs_prepare(obs[0])
+            hs.pso_init(model, trk.swarm, trk.seed_pose, trk.scale, seed, 0)
+            hs.pose_fk(model, cur, cam, trk.prims, trk.kc)
+            for gen in range(1, FULL_GENS + 1):
+                hist_p[gen - 1].copy_(trk.prims)
+                hist_k[gen - 1].copy_(trk.kc)
+                hs.render_score_batch(model, obs[0], cam, trk.prims, trk.kc, trk.score, trk.ws, trk.swarm.E)
+                trk.swarm.x = cur
+                hs.pso_step_fk(model, trk.swarm, nxt, trk.pso, seed, 0, gen, cam, trk.prims, trk.kc)
+                cur, nxt = nxt, cur
+            trk.swarm.x = cur
+            E_tmp = torch.zeros(P, device=dev)
+
+            def renders():
+                for q in range(FULL_GENS):
+                    hs.render_score_batch(model, obs[0], cam, hist_p[q], hist_k[q], trk.score, trk.ws, E_tmp)
+                return FULL_GENS
+
+            us = replay_render_us(dev, renders)
+            flops = np.mean([algorithmic_flops(hist_p[q, :, :, 14:16].cpu().numpy(), kinds, FULL_W, FULL_H)
+                             for q in range(0, FULL_GENS, 10)])
+            achieved = flops / (us * 1e-6) / 1e12
+            per_p.append({"particles": P, "render": {"kernel": hs.render_variant(trk.score, P),
+                                                     "ctas_per_particle": trk.score.ctas_per_particle,
+                                                     "autotune_us": tune},
+                          "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                                       "frac": achieved / peak_tflops, "launch_us": us, "flop_per_launch": flops}})
+            del trk, hist_p, hist_k
+            torch.cuda.empty_cache()
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2032.0))
+    best = SW.fastest_within(settings, 0.9)
+    if rank == 0:
+        line = {"metric": FULL_METRIC, "value": best["frame_ms_mean"] * 1e-3 if best else None,
+                "unit": "s/frame", "n_gpus": world, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": FULL_WORKLOAD, "roi": [FULL_W, FULL_H], "frames": frames, "threshold_deg": 5.0,
+                           "criterion": ">= 90 % of frames end within 5 deg mean joint error (23 angular DOFs)",
+                           "value_from": (f"{best['particles']} particles x {best['generations']} generations"
+                                          if best else "no setting tracked within 5 deg on 90 % of frames"),
+                           "timing": "CUDA events around each frame's graph (observation totals, init, FK, "
+                                     "G x (render, fused step))"},
+                "settings": settings, "per_swarm_size": per_p, "clocks": clocks,
+                "gpu_launches": sum((3 + 2 * s_["generations"]) * s_["frames"] for s_ in settings)}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---- the native arm ------------------------------------------------------------------------
 
 def main():
@@ -539,6 +679,8 @@ def main():
         return run_reference(args, rank)
     if args.workload == "batch":
         return run_batch(args, rank, world, local)
+    if args.workload == "fullframe":
+        return run_fullframe(args, rank, world, local)
 
     import torch
     from paper_2005_07068_b300 import build as B

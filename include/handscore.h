@@ -297,7 +297,7 @@ int render_score_batch_noalloc(const HsModel* model, const HsObs* obs, const HsC
  * 1 <= P <= HS_FUSED_MAX_PARTICLES (every CTA scans the P objectives).
  * Errors: HS_ERR_ARG (NULL, x_next == swarm->x, bad constants), HS_ERR_ALIGN,
  * HS_ERR_SIZE, HS_ERR_CUDA. */
-#define HS_FUSED_MAX_PARTICLES 1024
+#define HS_FUSED_MAX_PARTICLES 4096  /* 2 x 4096 floats of shared memory per CTA */
 int pso_step_fk(const HsModel* model, const HsSwarm* swarm, float* x_next, int P, const HsPsoParams* params,
                 uint64_t seed, uint32_t frame, uint32_t gen, const HsCamera* cam, HsPrim* prims, float* kc,
                 hs_stream_t stream);

@@ -121,7 +121,7 @@ _SIGS = {
 }
 NOALLOC_SCRATCH_BYTES = 256 * 1024
 MAX_PARTICLES = 65535
-FUSED_MAX_PARTICLES = 1024
+FUSED_MAX_PARTICLES = 4096
 
 _LIB = None
 

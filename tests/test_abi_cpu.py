@@ -185,7 +185,7 @@ def test_other_host_checks():
     sw.E = FAKE
     assert L.pso_step_fk(m.handle, ctypes.byref(sw), FAKE, 64, ctypes.byref(pp), 1, 0, 1, ctypes.byref(cam), FAKE,
                          FAKE, None) == hs.HS_ERR_ARG  # x_next aliases x
-    assert L.pso_step_fk(m.handle, ctypes.byref(sw), FAKE + 4096, 2000, ctypes.byref(pp), 1, 0, 1, ctypes.byref(cam),
+    assert L.pso_step_fk(m.handle, ctypes.byref(sw), FAKE + 4096, 5000, ctypes.byref(pp), 1, 0, 1, ctypes.byref(cam),
                          FAKE, FAKE, None) == hs.HS_ERR_SIZE
     assert hs.lib().hs_status_string(-3) == b"size out of range"
     # render launch shape: variant and CTAs per particle are validated; autotuning needs params and reps >= 1
@@ -220,7 +220,7 @@ def test_batch_host_checks():
     assert n.value >= 3 * 256 + 224 * 4  # views with two TMA descriptors each, then the swarm table
     assert L.hs_batch_buffer_size(_descs([32]), 0, ctypes.byref(n)) == hs.HS_ERR_SIZE
     assert L.hs_batch_buffer_size(_descs([0]), 1, ctypes.byref(n)) == hs.HS_ERR_SIZE
-    assert L.hs_batch_buffer_size(_descs([2000]), 1, ctypes.byref(n)) == hs.HS_ERR_SIZE  # above the fused step
+    assert L.hs_batch_buffer_size(_descs([5000]), 1, ctypes.byref(n)) == hs.HS_ERR_SIZE  # above the fused step
     assert L.hs_batch_buffer_size(_descs([1024] * 64), 64, ctypes.byref(n)) == hs.HS_ERR_SIZE  # > 65535 in total
     assert L.hs_batch_buffer_size(None, 1, ctypes.byref(n)) == hs.HS_ERR_ARG
     h = ctypes.c_void_p()

@@ -295,7 +295,7 @@ def test_gpu_tracking_first_generation_and_descent():
     REPORT["tracking_config1_gbest_E"] = hist
 
 
-@pytest.mark.parametrize("gen,P", [(3, 48), (4, 64), (6, 200)])
+@pytest.mark.parametrize("gen,P", [(3, 48), (4, 64), (6, 200), (3, 4096)])
 def test_fused_step_equals_step_then_fk(gen, P):
     """pso_step_fk == pso_step followed by pose_fk of the new positions, bit for bit."""
     lo, hi = (a.astype(np.float32) for a in I.search_limits())

@@ -63,7 +63,7 @@ def test_zero_softness_limit_is_the_hard_objective(scene):
     cov = np.real(parts["coverage"])
     hit = o["hit"][0]
     from scipy.ndimage import binary_dilation, binary_erosion
-    edge = binary_dilation(hit, iterations=4) & ~binary_erosion(hit, iterations=4)
+    edge = binary_dilation(hit, iterations=6) & ~binary_erosion(hit, iterations=6)
     assert np.all(cov[hit & ~edge] > 0.95) and np.all(cov[~hit & ~edge] < 0.05)
 
 

@@ -13,10 +13,21 @@ otherwise follows E term by term (reading R1):
   the signed distance in pixels to j's silhouette, taken to first order from
   the ray-quadric discriminant Delta_j: delta_j = Delta_j / |grad_pixel Delta_j|
   (positive inside); union coverage c = 1 - prod_j (1 - sigma_j);
-* depth: the near root t = (-B - sqrt(Delta+)) / A of the ray-quadric
-  equation, with the soft positive part Delta+ = (Delta + sqrt(Delta^2 +
+* depth: the near root of the ray-quadric equation A t^2 + 2 B t + C = 0
+  (t the camera-ray parameter, = depth), written as t = C / (-B + sqrt(Delta+))
+  with the soft positive part Delta+ = (Delta + sqrt(Delta^2 +
   (tau |grad Delta|)^2)) / 2 in place of max(Delta, 0), so that the depth is
-  smooth across the silhouette (the exact root has an infinite slope there);
+  smooth across the silhouette (the exact root has an infinite slope there).
+  With Delta+ = Delta this is the near root; unlike (-B - sqrt(Delta+)) / A it
+  stays bounded as A -> 0 (a ray nearly parallel to a cone's surface).  A
+  visible near root needs A > 0 and B < 0, which the primitive must satisfy.
+  The depth's offset s = t - t0 from the primitive's centre depth t0 is then
+  clamped smoothly to its bounding radius R (largest semi-axis, or for a cone
+  the half-diagonal sqrt(h_l^2 + r_max^2)): identity for |s| <= R, and
+  sign(s) R (2 - exp(1 - |s| / R)) beyond (C1, at most 2R).  A real hit is
+  never clamped; near-miss rays of a cone seen nearly end-on otherwise get
+  depths metres away.  The cone's end cut below uses the same clamped
+  offsets (of the root and of the closest approach);
   a cone's coverage is further multiplied by sigma(delta_Y / tau), its end
   cut |Y| <= 1 softened with delta_Y = (1 - |Y_e|) L pixels.  L is the
   projected half-length of the axis in pixels (the distance between the
@@ -26,7 +37,14 @@ otherwise follows E term by term (reading R1):
   grazing silhouette, where the root slides along the ray as 1 / A) with
   that of the ray's closest approach to the axis, t* = -B/A (smooth there),
   by w = sigma(delta / tau - 2): the root well inside the silhouette, the
-  closest approach near and outside it.  Cone caps are not part of E_s (the
+  closest approach near and outside it; both at their clamped offsets.
+  A cone seen within a few degrees of a surface generator fades out: with
+  a = A / |h|^2 (the squared sine of that angle) its coverage is also
+  multiplied by a^4 / (a^4 + a0^4), a0 = 0.06 tau (tau in pixels; at
+  tau = 0.5: half at ~10 degrees, 1e-6 at ~2, and no fade as tau -> 0).
+  There every quantity above is ill-conditioned (the quadratic degenerates,
+  A -> 0), and the joint sphere at the cone's near end hides all of it but a
+  thin crescent.  Cone caps are not part of E_s (the
   model's joint spheres cover every cone end);
 * soft nearest surface: the primitives are composited front to back in order
   of depth, alpha_j = sigma_j, T_j = prod over nearer k of (1 - alpha_k),
@@ -123,9 +141,17 @@ def _smin(x, y, tau):
         return m - tau * np.log(np.exp(-(x - m) / tau) + np.exp(-(y - m) / tau))
 
 
+def _clamp_offset(s, R):
+    """Identity for |s| <= R, sign(s) R (2 - exp(1 - |s| / R)) beyond (C1, |.| < 2R)."""
+    a = np.where(_re(s) >= 0, s, -s)
+    sgn = np.where(_re(s) >= 0, 1.0, -1.0)
+    with np.errstate(all="ignore"):
+        return np.where(_re(a) <= R, s, sgn * R * (2.0 - np.exp(1.0 - a / R)))
+
+
 def primitive_terms(kind, dims, R, C, a, b, fx, fy, tau=TAU_PX):
     """Per-pixel terms of one primitive for rays d = (a, b, 1) over the pixel grid:
-    (Delta, delta_px, z, ok, delta_y_px or None for an ellipsoid)."""
+    (Delta, delta_px, z, ok, None for an ellipsoid or (delta_y_px, fade) for a cone)."""
     # local frame: ray from the camera o + t e, o = R^T (0 - C), e = R^T d
     o = -(R.T @ C)
     e = [R[0, i] * a + R[1, i] * b + R[2, i] for i in range(3)]
@@ -160,8 +186,15 @@ def primitive_terms(kind, dims, R, C, a, b, fx, fy, tau=TAU_PX):
         delta = Dl / N
         tn = tau * N
         Dp = 0.5 * (Dl + np.sqrt(Dl * Dl + tn * tn))  # soft positive part of Delta
-        t = (-B - np.sqrt(Dp)) / A
-    ok = (_re(A) > 0) & (_re(t) > 0)
+        r = np.sqrt(Dp)
+        t = Cq / (-B + r)  # the near root (B < 0), without cancellation
+        if kind == 0:
+            Rb = max(dims[0], dims[1], dims[2])
+        else:
+            Rb = np.sqrt(dims[2] ** 2 + (max(dims[0], dims[1]) * (1.0 + abs(dims[3]))) ** 2)
+        t0 = C[2]
+        t = t0 + _clamp_offset(t - t0, Rb)
+    ok = (_re(A) > 0) & (_re(B) < 0) & (_re(t) > 0)
     if kind == 0:
         return Dl, delta, t, ok, None
     ax, az, hl, kap = dims[0], dims[1], dims[2], dims[3]
@@ -172,12 +205,15 @@ def primitive_terms(kind, dims, R, C, a, b, fx, fy, tau=TAU_PX):
     r_px = max(ax, az) * (1.0 + abs(kap)) * fx / C[2]
     L = half_len if _re(half_len) > _re(r_px) else r_px
     with np.errstate(all="ignore"):
+        a_rel = A / (es[0] * es[0] + es[1] * es[1] + es[2] * es[2])  # squared sine to the generator
+        a4 = a_rel ** 4
+        fade = a4 / (a4 + (0.06 * tau) ** 4)
         y_root = os_[1] + t * es[1]
-        y_near = os_[1] + (-B / A) * es[1]
+        y_near = os_[1] + (t0 + _clamp_offset(-B / A - t0, Rb)) * es[1]
         Y = y_near + _sigmoid(delta / tau - 2.0) * (y_root - y_near)
         absY = np.where(_re(Y) >= 0, Y, -Y)
         delta_y = (1.0 - absY) * L  # pixels to the cone's end along its projected axis
-    return Dl, delta, t, ok, delta_y
+    return Dl, delta, t, ok, (delta_y, fade)
 
 
 def soft_objective(model: Model, pose, cam, Od, S, params=DEFAULT_PARAMS, *, tau=TAU_PX, tau_mm=TAU_MM,
@@ -201,7 +237,8 @@ def soft_objective(model: Model, pose, cam, Od, S, params=DEFAULT_PARAMS, *, tau
         _, delta, t, ok, delta_y = primitive_terms(kind, model.prims_f[j, 3:7], pR[j], pC[j], a, b, fx, fy, tau)
         sig = _sigmoid(delta / tau)
         if delta_y is not None:
-            sig = sig * _sigmoid(delta_y / tau)
+            dy, fade = delta_y
+            sig = sig * _sigmoid(dy / tau) * fade
         alpha[j] = np.where(ok, sig, 0.0)
         z[j] = np.where(ok, t, 1e30)  # primitives that do not count sort last
     # front-to-back compositing in order of depth (decided on real parts)

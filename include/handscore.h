@@ -354,6 +354,52 @@ int pso_step_fk_multi(const HsModel* model, const HsBatch* batch, const HsSwarm*
                       const HsPsoParams* params, uint32_t frame, uint32_t gen, HsPrim* prims, float* kc,
                       hs_stream_t stream);
 
+/* ---- the smoothed objective E_s and its gradient (gradient polish) ---------------
+ * E (Eq. 4-5) is piecewise constant in the pose at every silhouette and depth
+ * threshold, so its gradient carries no silhouette information.  E_s keeps
+ * E's terms (reading R1) and replaces each hard decision by a smooth one:
+ *  - primitive coverage sigma(delta / tau_px), delta = Delta / |grad Delta| the
+ *    first-order signed pixel distance to the primitive's silhouette from the
+ *    ray-quadric discriminant; cones also fade at their end cut |Y| <= 1 over
+ *    tau_px along the projected axis; the root uses a soft positive part of
+ *    Delta (width tau_px in pixels);
+ *  - the primitives touching a pixel are composited front to back in depth
+ *    order (coverage c = 1 - prod(1 - alpha), depth z~ = sum T alpha z / c);
+ *  - |O_d - z~| -> sqrt((O_d - z~)^2 + tau_mm^2), the d_M clamp -> a soft
+ *    minimum, the d_m test -> a sigmoid, all of width tau_mm;
+ *  - per pixel t = c t_hit + (1 - c) t_miss, r_m = c m; D_s and E_s as Eq. 4-5.
+ * As tau_px, tau_mm -> 0, E_s -> E.  The paper optimises E with PSO alone; E_s
+ * and its gradient serve the gradient polish of the best particles.  FP32. */
+#define HS_SOFT_ADJ 13  /* per-primitive adjoint: M (9, record order), C (3), cone length in pixels (1) */
+typedef struct {
+    float tau_px;        /* silhouette softness, pixels (0.5) */
+    float tau_mm;        /* depth softness, mm (0.5) */
+    int32_t ctas_per_particle;  /* 0 = automatic */
+    int32_t reserved;
+} HsSoftParams;
+
+/* E_s of P particles whose records came from pose_fk (FP32).  sums [P][3]
+ * (may be NULL) receives (sum t, sum and, sum or), which the backward pass
+ * needs.  workspace: hs_workspace_size(P) bytes, zeroed once (left zeroed).
+ * obs->stats must be prepared (hs_obs_prepare).
+ * Errors: HS_ERR_ARG, HS_ERR_ALIGN, HS_ERR_SIZE, HS_ERR_CUDA. */
+int soft_score(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsPrim* prims, const float* kc,
+               int P, const HsScoreParams* params, const HsSoftParams* soft, void* workspace,
+               size_t workspace_bytes, float* E_s, float* sums, hs_stream_t stream);
+/* dE_s / d(records): adds, for every particle and primitive, the adjoint of its
+ * record (M in record order, C) and of the cone's pixel length to adj
+ * [P][n_prims][HS_SOFT_ADJ] (device, zero on entry; pose_grad clears it).
+ * sums: soft_score's output for the same inputs. */
+int soft_score_backward(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsPrim* prims, int P,
+                        const HsScoreParams* params, const HsSoftParams* soft, const float* sums, float* adj,
+                        hs_stream_t stream);
+/* dE_s / d pose [P][26] from the record adjoints (forward-mode tangents of the
+ * FK, Eq. 1-3) plus lambda_k dkc/dpose; zero for a parameter outside its
+ * limits (the FK clamps it).  Rewrites prims/kc with pose_fk's values and
+ * clears adj. */
+int pose_grad(const HsModel* model, const float* poses, int P, const HsCamera* cam, const HsScoreParams* params,
+              HsPrim* prims, float* kc, float* adj, float* grad, hs_stream_t stream);
+
 /* ---- render autotuning -----------------------------------------------------------
  * Time every render kernel (HS_RENDER_UNITS .. HS_RENDER_TILES_64x64) with CTAs
  * per particle from {automatic, 1, 2, 4, 8, 16, 32} (more than 1 only while

@@ -497,6 +497,114 @@ int pso_step_fk(const HsModel* model, const HsSwarm* sw, float* x_next, int P, c
     return launch_pso_step_fk(model->dev, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 
+// ---- the smoothed objective and its gradient ---------------------------------------
+
+static int soft_common(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsPrim* prims, int P,
+                       const HsScoreParams* params, const HsSoftParams* sp, SoftArgs& a)
+{
+    if (!model || !prims || !params || !sp) return HS_ERR_ARG;
+    int rc = validate_obs(obs);
+    if (rc) return rc;
+    if ((rc = validate_cam(cam))) return rc;
+    if ((rc = validate_score_params(params))) return rc;
+    if (!(sp->tau_px > 0.f && sp->tau_px <= 8.f) || !(sp->tau_mm > 0.f && sp->tau_mm <= 10.f)) return HS_ERR_ARG;
+    if (sp->ctas_per_particle < 0 || sp->ctas_per_particle > kMaxCtasPerParticle) return HS_ERR_ARG;
+    if (P < 0 || P > HS_MAX_PARTICLES) return HS_ERR_SIZE;
+    if (!aligned16(prims)) return HS_ERR_ALIGN;
+    a = SoftArgs{};
+    a.prims = reinterpret_cast<const float4*>(prims);
+    a.P = P;
+    a.n_prims = model->dev.n_prims;
+    int K = sp->ctas_per_particle;
+    if (K == 0) {
+        K = P > 0 ? kTargetCtas / P : 1;
+        if (K > kMaxK) K = kMaxK;
+        if (K < 1) K = 1;
+    }
+    a.K = K;
+    a.W = obs->W;
+    a.H = obs->H;
+    a.inv_fx = (float)(1.0 / (double)cam->fx);
+    a.inv_fy = (float)(1.0 / (double)cam->fy);
+    a.off_x = (float)((0.5 - (double)cam->cx) / (double)cam->fx);
+    a.off_y = (float)((0.5 - (double)cam->cy) / (double)cam->fy);
+    a.fx = cam->fx;
+    a.fy = cam->fy;
+    a.d_m = params->d_m;
+    a.d_M = params->d_M;
+    a.lambda = params->lambda;
+    a.lambda_k = params->lambda_k;
+    a.tau = sp->tau_px;
+    a.tau_mm = sp->tau_mm;
+    a.depth = static_cast<const unsigned char*>(obs->depth);
+    a.skin = obs->skin;
+    a.depth_pitch = obs->depth_pitch;
+    a.skin_pitch = obs->skin_pitch;
+    a.depth_f32 = obs->depth_type == HS_DEPTH_F32;
+    a.stats = obs->stats;
+    return HS_OK;
+}
+
+int soft_score(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsPrim* prims, const float* kc,
+               int P, const HsScoreParams* params, const HsSoftParams* soft, void* workspace,
+               size_t workspace_bytes, float* E_s, float* sums, hs_stream_t stream)
+{
+    SoftArgs a;
+    int rc = soft_common(model, obs, cam, prims, P, params, soft, a);
+    if (rc) return rc;
+    if (!kc || !E_s) return HS_ERR_ARG;
+    if (workspace && !aligned16(workspace)) return HS_ERR_ALIGN;
+    size_t need = 0;
+    hs_workspace_size(P, &need);
+    if (P > 0 && (!workspace || workspace_bytes < need)) return HS_ERR_SIZE;
+    if (P == 0) return HS_OK;
+    a.kc = kc;
+    a.work = static_cast<SoftWork*>(workspace);
+    a.E = E_s;
+    a.sums = sums;
+    return launch_soft(false, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int soft_score_backward(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsPrim* prims, int P,
+                        const HsScoreParams* params, const HsSoftParams* soft, const float* sums, float* adj,
+                        hs_stream_t stream)
+{
+    SoftArgs a;
+    int rc = soft_common(model, obs, cam, prims, P, params, soft, a);
+    if (rc) return rc;
+    if (!sums || !adj) return HS_ERR_ARG;
+    if (P == 0) return HS_OK;
+    a.sums = const_cast<float*>(sums);
+    a.adj = adj;
+    return launch_soft(true, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int pose_grad(const HsModel* model, const float* poses, int P, const HsCamera* cam, const HsScoreParams* params,
+              HsPrim* prims, float* kc, float* adj, float* grad, hs_stream_t stream)
+{
+    if (!model || !poses || !params || !prims || !kc || !adj || !grad) return HS_ERR_ARG;
+    int rc = validate_cam(cam);
+    if (rc) return rc;
+    if ((rc = validate_score_params(params))) return rc;
+    if (P < 0 || P > HS_MAX_PARTICLES) return HS_ERR_SIZE;
+    if (!aligned16(prims)) return HS_ERR_ALIGN;
+    if (P == 0) return HS_OK;
+    GradArgs a = {};
+    a.poses = poses;
+    a.P = P;
+    a.fx = cam->fx;
+    a.fy = cam->fy;
+    a.cx = cam->cx;
+    a.cy = cam->cy;
+    a.lambda_k = params->lambda_k;
+    a.prims = reinterpret_cast<float4*>(prims);
+    a.kc = kc;
+    a.adj = adj;
+    a.grad = grad;
+    if ((rc = status_ptr(&a.status))) return rc;
+    return launch_pose_grad(model->dev, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
 // ---- batches of independent swarms ------------------------------------------------
 
 int hs_batch_buffer_size(const HsSwarmDesc* sw, int S, size_t* bytes)

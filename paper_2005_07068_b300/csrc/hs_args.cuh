@@ -105,6 +105,47 @@ struct PsoFkArgs {
     BatchDev batch;        // when set: every particle works within its own swarm
 };
 
+// ---- the smoothed objective and its gradient (soft.cu) ----
+constexpr int kAdj = HS_SOFT_ADJ;  // per-primitive adjoint: record M (9), C (3), cone length L (1)
+
+struct SoftWork {
+    uint32_t exited, pad;
+    long long t, a, o;  // fixed-point 2^-24: sum of t - t_miss, sum S r_m, sum (1 - S) r_m
+};
+static_assert(sizeof(SoftWork) == 32, "one 32-byte workspace slot per particle");
+
+struct SoftArgs {
+    const float4* prims;  // [P][n_prims][4]
+    const float* kc;      // [P]
+    int P, n_prims, K;
+    int W, H;
+    float inv_fx, inv_fy, off_x, off_y, fx, fy;
+    float d_m, d_M, lambda, lambda_k, tau, tau_mm;
+    const unsigned char* depth;
+    const uint8_t* skin;
+    int depth_pitch, skin_pitch, depth_f32;
+    const uint32_t* stats;  // [2]: #valid, #skin
+    SoftWork* work;         // forward: [P], zero between calls
+    float* E;               // forward: [P]
+    float* sums;            // forward output / backward input: [P][3] (sum t, sum and, sum or)
+    float* adj;             // backward: [P][n_prims][kAdj], accumulated
+};
+
+struct GradArgs {
+    const float* poses;  // [P][26]
+    int P;
+    float fx, fy, cx, cy;
+    float lambda_k;
+    float4* prims;   // [P][n_prims][4] (rewritten by the FK, same values as pose_fk)
+    float* kc;       // [P]
+    float* adj;      // [P][n_prims][kAdj], read then cleared
+    float* grad;     // [P][26]
+    uint32_t* status;
+};
+
+cudaError_t launch_soft(bool backward, const SoftArgs& args, cudaStream_t stream);
+cudaError_t launch_pose_grad(const DevModel& model, const GradArgs& args, cudaStream_t stream);
+
 cudaError_t launch_fk(const DevModel& model, const FkArgs& args, cudaStream_t stream);
 cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cudaStream_t stream);
 cudaError_t launch_render_score(const CUtensorMap& tm_depth, const CUtensorMap& tm_skin, const RenderArgs& args,

@@ -71,6 +71,14 @@ class HsPsoParams(ctypes.Structure):
                 ("n_mutate", ctypes.c_int32)]
 
 
+class HsSoftParams(ctypes.Structure):
+    _fields_ = [("tau_px", ctypes.c_float), ("tau_mm", ctypes.c_float), ("ctas_per_particle", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+SOFT_ADJ = 13  # per-primitive adjoint: M (9), C (3), cone length in pixels (1)
+
+
 class HsSwarmDesc(ctypes.Structure):
     _fields_ = [("obs", HsObs), ("cam", HsCamera), ("P", ctypes.c_int32), ("n_mutate", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]
@@ -104,6 +112,14 @@ _SIGS = {
                                     ctypes.c_int),
     "render_score_multi_autotune": ([_vp, _vp, _vp, _vp, ctypes.POINTER(HsScoreParams), _vp, ctypes.c_size_t, _vp,
                                      ctypes.c_int, _vp, _vp], ctypes.c_int),
+    "soft_score": ([_vp, ctypes.POINTER(HsObs), ctypes.POINTER(HsCamera), _vp, _vp, ctypes.c_int,
+                    ctypes.POINTER(HsScoreParams), ctypes.POINTER(HsSoftParams), _vp, ctypes.c_size_t, _vp, _vp, _vp],
+                   ctypes.c_int),
+    "soft_score_backward": ([_vp, ctypes.POINTER(HsObs), ctypes.POINTER(HsCamera), _vp, ctypes.c_int,
+                             ctypes.POINTER(HsScoreParams), ctypes.POINTER(HsSoftParams), _vp, _vp, _vp],
+                            ctypes.c_int),
+    "pose_grad": ([_vp, _vp, ctypes.c_int, ctypes.POINTER(HsCamera), ctypes.POINTER(HsScoreParams), _vp, _vp, _vp,
+                   _vp, _vp], ctypes.c_int),
     "hs_batch_buffer_size": ([ctypes.POINTER(HsSwarmDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
                              ctypes.c_int),
     "hs_batch_create": ([_vp, ctypes.POINTER(HsSwarmDesc), ctypes.c_int, _vp, ctypes.c_size_t, _vp,
@@ -367,6 +383,39 @@ def pso_step_fk(model: Model, sw: Swarm, x_next: torch.Tensor, params: HsPsoPara
     _check("pso_step_fk", lib().pso_step_fk(model.handle, ctypes.byref(st), _ptr(x_next), sw.P, ctypes.byref(params),
                                             ctypes.c_uint64(seed), frame, gen, ctypes.byref(cam), _ptr(prims),
                                             _ptr(kc), _stream(stream)))
+
+
+# ---- the smoothed objective E_s and its gradient ------------------------------------
+
+def soft_params(tau_px: float = 0.5, tau_mm: float = 0.5, ctas_per_particle: int = 0) -> HsSoftParams:
+    return HsSoftParams(tau_px, tau_mm, int(ctas_per_particle), 0)
+
+
+def soft_score(model: Model, obs: Obs, cam: HsCamera, prims: torch.Tensor, kc: torch.Tensor, params: HsScoreParams,
+               soft: HsSoftParams, ws: torch.Tensor, E_s: torch.Tensor, sums: torch.Tensor | None = None,
+               stream=None) -> None:
+    """E_s [P] of the records prims [P, n_prims, 16]; sums [P, 3] for the backward pass."""
+    st = obs.struct()
+    _check("soft_score", lib().soft_score(model.handle, ctypes.byref(st), ctypes.byref(cam), _ptr(prims), _ptr(kc),
+                                          kc.shape[0], ctypes.byref(params), ctypes.byref(soft), _ptr(ws), ws.numel(),
+                                          _ptr(E_s), _ptr(sums), _stream(stream)))
+
+
+def soft_score_backward(model: Model, obs: Obs, cam: HsCamera, prims: torch.Tensor, params: HsScoreParams,
+                        soft: HsSoftParams, sums: torch.Tensor, adj: torch.Tensor, stream=None) -> None:
+    """Adds dE_s/d(records) to adj [P, n_prims, SOFT_ADJ] (zero on entry)."""
+    st = obs.struct()
+    _check("soft_score_backward",
+           lib().soft_score_backward(model.handle, ctypes.byref(st), ctypes.byref(cam), _ptr(prims), prims.shape[0],
+                                     ctypes.byref(params), ctypes.byref(soft), _ptr(sums), _ptr(adj), _stream(stream)))
+
+
+def pose_grad(model: Model, poses: torch.Tensor, cam: HsCamera, params: HsScoreParams, prims: torch.Tensor,
+              kc: torch.Tensor, adj: torch.Tensor, grad: torch.Tensor, stream=None) -> None:
+    """grad [P, 26] = dE_s/dpose from the record adjoints (adj is cleared)."""
+    _check("pose_grad", lib().pose_grad(model.handle, _ptr(poses), poses.shape[0], ctypes.byref(cam),
+                                        ctypes.byref(params), _ptr(prims), _ptr(kc), _ptr(adj), _ptr(grad),
+                                        _stream(stream)))
 
 
 # ---- batches of independent swarms ---------------------------------------------------

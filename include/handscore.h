@@ -388,17 +388,37 @@ int soft_score(const HsModel* model, const HsObs* obs, const HsCamera* cam, cons
                size_t workspace_bytes, float* E_s, float* sums, hs_stream_t stream);
 /* dE_s / d(records): adds, for every particle and primitive, the adjoint of its
  * record (M in record order, C) and of the cone's pixel length to adj
- * [P][n_prims][HS_SOFT_ADJ] (device, zero on entry; pose_grad clears it).
- * sums: soft_score's output for the same inputs. */
+ * [P][n_prims][HS_SOFT_ADJ] (device, 64-bit fixed point with 2^-40
+ * resolution so that sums do not depend on scheduling; zero on entry,
+ * pose_grad clears it).  sums: soft_score's output for the same inputs. */
 int soft_score_backward(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsPrim* prims, int P,
-                        const HsScoreParams* params, const HsSoftParams* soft, const float* sums, float* adj,
+                        const HsScoreParams* params, const HsSoftParams* soft, const float* sums, int64_t* adj,
                         hs_stream_t stream);
 /* dE_s / d pose [P][26] from the record adjoints (forward-mode tangents of the
  * FK, Eq. 1-3) plus lambda_k dkc/dpose; zero for a parameter outside its
  * limits (the FK clamps it).  Rewrites prims/kc with pose_fk's values and
  * clears adj. */
 int pose_grad(const HsModel* model, const float* poses, int P, const HsCamera* cam, const HsScoreParams* params,
-              HsPrim* prims, float* kc, float* adj, float* grad, hs_stream_t stream);
+              HsPrim* prims, float* kc, int64_t* adj, float* grad, hs_stream_t stream);
+
+/* ---- gradient polish of the best particles (hybrid PSO) --------------------------
+ * Not in the paper, which relies on PSO alone; the paper names fingers stuck in
+ * local optima as its failure mode (Section III.B, V).  After a generation's E
+ * is known: polish_select picks the k best particles (lowest E, lower index on
+ * ties, NaN last), polish_gather copies their poses and E, polish_step moves
+ * them down the gradient of E_s, and polish_keep_better writes a polished pose
+ * (and its exact E) back only where it lowered E.  All device arrays. */
+#define HS_POLISH_MAX 256
+int polish_select(const float* E, int P, int k, int32_t* sel, hs_stream_t stream);
+int polish_gather(const float* x, const float* E, const int32_t* sel, int k, float* x_sel, float* E_sel,
+                  hs_stream_t stream);
+/* x_sel [k][26] <- clamp(x_sel - eta S^2 g / |S g|) with S = scale (host [26],
+ * > 0; e.g. 10 mm / 10 degrees) and the model's limits: a step of length eta
+ * in scaled units along the preconditioned gradient grad [k][26]. */
+int polish_step(const HsModel* model, float* x_sel, const float* grad, int k, float eta, const float* scale,
+                hs_stream_t stream);
+int polish_keep_better(float* x, float* E, const int32_t* sel, int k, const float* x_sel, const float* E_old,
+                       const float* E_new, hs_stream_t stream);
 
 /* ---- render autotuning -----------------------------------------------------------
  * Time every render kernel (HS_RENDER_UNITS .. HS_RENDER_TILES_64x64) with CTAs

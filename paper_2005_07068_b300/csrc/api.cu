@@ -516,9 +516,9 @@ static int soft_common(const HsModel* model, const HsObs* obs, const HsCamera* c
     a.P = P;
     a.n_prims = model->dev.n_prims;
     int K = sp->ctas_per_particle;
-    if (K == 0) {
+    if (K == 0) {  // about one resident wave in total (these calls serve few particles)
         K = P > 0 ? kTargetCtas / P : 1;
-        if (K > kMaxK) K = kMaxK;
+        if (K > kMaxCtasPerParticle) K = kMaxCtasPerParticle;
         if (K < 1) K = 1;
     }
     a.K = K;
@@ -566,7 +566,7 @@ int soft_score(const HsModel* model, const HsObs* obs, const HsCamera* cam, cons
 }
 
 int soft_score_backward(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsPrim* prims, int P,
-                        const HsScoreParams* params, const HsSoftParams* soft, const float* sums, float* adj,
+                        const HsScoreParams* params, const HsSoftParams* soft, const float* sums, int64_t* adj,
                         hs_stream_t stream)
 {
     SoftArgs a;
@@ -575,12 +575,12 @@ int soft_score_backward(const HsModel* model, const HsObs* obs, const HsCamera* 
     if (!sums || !adj) return HS_ERR_ARG;
     if (P == 0) return HS_OK;
     a.sums = const_cast<float*>(sums);
-    a.adj = adj;
+    a.adj = reinterpret_cast<long long*>(adj);
     return launch_soft(true, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 
 int pose_grad(const HsModel* model, const float* poses, int P, const HsCamera* cam, const HsScoreParams* params,
-              HsPrim* prims, float* kc, float* adj, float* grad, hs_stream_t stream)
+              HsPrim* prims, float* kc, int64_t* adj, float* grad, hs_stream_t stream)
 {
     if (!model || !poses || !params || !prims || !kc || !adj || !grad) return HS_ERR_ARG;
     int rc = validate_cam(cam);
@@ -599,10 +599,53 @@ int pose_grad(const HsModel* model, const float* poses, int P, const HsCamera* c
     a.lambda_k = params->lambda_k;
     a.prims = reinterpret_cast<float4*>(prims);
     a.kc = kc;
-    a.adj = adj;
+    a.adj = reinterpret_cast<long long*>(adj);
     a.grad = grad;
     if ((rc = status_ptr(&a.status))) return rc;
     return launch_pose_grad(model->dev, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+// ---- gradient polish ----------------------------------------------------------------
+
+int polish_select(const float* E, int P, int k, int32_t* sel, hs_stream_t stream)
+{
+    if (!E || !sel) return HS_ERR_ARG;
+    if (P < 1 || P > HS_MAX_PARTICLES || k < 1 || k > HS_POLISH_MAX || k > P) return HS_ERR_SIZE;
+    return launch_select_best(E, P, k, sel, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int polish_gather(const float* x, const float* E, const int32_t* sel, int k, float* x_sel, float* E_sel,
+                  hs_stream_t stream)
+{
+    if (!x || !E || !sel || !x_sel || !E_sel) return HS_ERR_ARG;
+    if (k < 1 || k > HS_POLISH_MAX) return HS_ERR_SIZE;
+    return launch_gather(x, E, sel, k, x_sel, E_sel, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int polish_step(const HsModel* model, float* x_sel, const float* grad, int k, float eta, const float* scale,
+                hs_stream_t stream)
+{
+    if (!model || !x_sel || !grad || !scale) return HS_ERR_ARG;
+    if (k < 1 || k > HS_POLISH_MAX) return HS_ERR_SIZE;
+    if (!std::isfinite(eta) || eta < 0.f) return HS_ERR_ARG;
+    PolishStep st = {};
+    st.eta = eta;
+    for (int d = 0; d < HS_NDOF; ++d) {
+        if (!std::isfinite(scale[d]) || scale[d] <= 0.f) return HS_ERR_ARG;
+        st.scale[d] = scale[d];
+        st.lo[d] = model->lim.lo[d];
+        st.hi[d] = model->lim.hi[d];
+    }
+    return launch_polish_step(x_sel, grad, k, st, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int polish_keep_better(float* x, float* E, const int32_t* sel, int k, const float* x_sel, const float* E_old,
+                       const float* E_new, hs_stream_t stream)
+{
+    if (!x || !E || !sel || !x_sel || !E_old || !E_new) return HS_ERR_ARG;
+    if (k < 1 || k > HS_POLISH_MAX) return HS_ERR_SIZE;
+    return launch_keep_better(x, E, sel, k, x_sel, E_old, E_new, (cudaStream_t)stream) == cudaSuccess ? HS_OK
+                                                                                                  : HS_ERR_CUDA;
 }
 
 // ---- batches of independent swarms ------------------------------------------------

@@ -128,7 +128,7 @@ struct SoftArgs {
     SoftWork* work;         // forward: [P], zero between calls
     float* E;               // forward: [P]
     float* sums;            // forward output / backward input: [P][3] (sum t, sum and, sum or)
-    float* adj;             // backward: [P][n_prims][kAdj], accumulated
+    long long* adj;         // backward: [P][n_prims][kAdj], fixed point 2^-40, accumulated
 };
 
 struct GradArgs {
@@ -138,10 +138,23 @@ struct GradArgs {
     float lambda_k;
     float4* prims;   // [P][n_prims][4] (rewritten by the FK, same values as pose_fk)
     float* kc;       // [P]
-    float* adj;      // [P][n_prims][kAdj], read then cleared
+    long long* adj;  // [P][n_prims][kAdj], fixed point 2^-40, read then cleared
     float* grad;     // [P][26]
     uint32_t* status;
 };
+
+// one polish step: eta in scaled units, per-parameter scale and limits
+struct PolishStep {
+    float eta;
+    float scale[kNdof];
+    float lo[kNdof], hi[kNdof];
+};
+cudaError_t launch_select_best(const float* E, int P, int k, int32_t* sel, cudaStream_t s);
+cudaError_t launch_gather(const float* x, const float* E, const int32_t* sel, int k, float* x_sel, float* E_sel,
+                          cudaStream_t s);
+cudaError_t launch_polish_step(float* x, const float* grad, int k, const PolishStep& st, cudaStream_t s);
+cudaError_t launch_keep_better(float* x, float* E, const int32_t* sel, int k, const float* x_sel, const float* E_old,
+                               const float* E_new, cudaStream_t s);
 
 cudaError_t launch_soft(bool backward, const SoftArgs& args, cudaStream_t stream);
 cudaError_t launch_pose_grad(const DevModel& model, const GradArgs& args, cudaStream_t stream);

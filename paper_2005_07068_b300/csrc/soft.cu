@@ -45,6 +45,24 @@ constexpr float kAlphaMin = 1e-7f;  // touches below this are dropped
 
 __device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + expf(-x)); }
 
+// Adjoints are summed as 64-bit fixed point with 2^-40 resolution (|value| <
+// 2^23), so that the totals do not depend on the order of the atomic adds.
+// The conversion uses 32-bit halves: v 2^40 is exact in FP32 (a power-of-two
+// scaling), its high and low words are then exact FP32 integers.
+constexpr float kAdjScale = 1099511627776.0f;  // 2^40
+__device__ __forceinline__ long long adj_to_fix(float v)
+{
+    const float w = v * kAdjScale;
+    const float hi = floorf(w * 2.3283064365386963e-10f);  // w / 2^32
+    const float lo = fmaf(-hi, 4294967296.0f, w);          // exact: w - hi 2^32, in [0, 2^32)
+    return ((long long)__float2int_rn(hi) << 32) + (long long)__float2uint_rn(lo);
+}
+__device__ __forceinline__ float adj_from_fix(long long f)
+{
+    const float hi = (float)(int)(f >> 32), lo = (float)(uint32_t)(f & 0xffffffffu);
+    return fmaf(hi, 4294967296.0f, lo) * (1.0f / kAdjScale);
+}
+
 // everything a primitive's coverage and depth at one pixel depend on
 struct SoftPrimEval {
     float h[3], g[3], hu[3], gu[3], hv[3], gv[3];
@@ -295,7 +313,7 @@ __device__ __forceinline__ float cone_pixel_length(const float4& r0, const float
 
 // byte offsets of soft_kernel's dynamic shared memory (each 16-byte aligned)
 struct SoftLayout {
-    size_t rec, box, L, R, uni, adj, al, zl, Tl, jl, bytes;
+    size_t rec, box, L, R, uni, adj, al, zl, Tl, jl, mp, bytes;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) / 16 * 16; }
@@ -308,12 +326,13 @@ __host__ __device__ inline SoftLayout soft_layout(int n, bool bwd)
     l.L = align16(l.box + (size_t)n * 16);             // float [n]: cone length in pixels
     l.R = align16(l.L + (size_t)n * 4);                // float [n]: bounding radius (depth clamp)
     l.uni = align16(l.R + (size_t)n * 4);              // int [4]: union box
-    l.adj = align16(l.uni + 16);                       // float [n][kAdj] (backward)
-    l.al = align16(l.adj + (bwd ? (size_t)n * kAdj * 4 : 0));  // float [n][threads]: alpha
+    l.adj = align16(l.uni + 16);                       // int64 [n][kAdj] (backward, fixed point 2^-40)
+    l.al = align16(l.adj + (bwd ? (size_t)n * kAdj * 8 : 0));  // float [n][threads]: alpha
     l.zl = align16(l.al + (size_t)n * kSoftThreads * 4);       // float [n][threads]: depth
     l.Tl = align16(l.zl + (size_t)n * kSoftThreads * 4);       // float [n][threads]: transmittance (backward)
     l.jl = align16(l.Tl + (bwd ? (size_t)n * kSoftThreads * 4 : 0));  // uint8 [n][threads]: primitive (backward)
-    l.bytes = align16(l.jl + (bwd ? (size_t)n * kSoftThreads : 0));
+    l.mp = align16(l.jl + (bwd ? (size_t)n * kSoftThreads : 0));      // uint8 [n][threads]: entry of a primitive + 1
+    l.bytes = align16(l.mp + (bwd ? (size_t)n * kSoftThreads : 0));
     return l;
 }
 
@@ -329,16 +348,19 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
     float* s_L = reinterpret_cast<float*>(smem + lay.L);
     float* s_R = reinterpret_cast<float*>(smem + lay.R);
     int* s_uni = reinterpret_cast<int*>(smem + lay.uni);
-    float* s_adj = reinterpret_cast<float*>(smem + lay.adj);
+    unsigned long long* s_adj = reinterpret_cast<unsigned long long*>(smem + lay.adj);
     float* s_al = reinterpret_cast<float*>(smem + lay.al);
     float* s_zl = reinterpret_cast<float*>(smem + lay.zl);
     float* s_Tl = reinterpret_cast<float*>(smem + lay.Tl);
     uint8_t* s_jl = smem + lay.jl;
+    uint8_t* s_mp = smem + lay.mp;
 
     const float4* src = a.prims + (size_t)p * n * 4;
     for (int i = tid; i < n * 4; i += kSoftThreads) s_rec[i] = src[i];
-    if (BWD)
-        for (int i = tid; i < n * kAdj; i += kSoftThreads) s_adj[i] = 0.f;
+    if (BWD) {
+        for (int i = tid; i < n * kAdj; i += kSoftThreads) s_adj[i] = 0ull;
+        for (int i = tid; i < n * kSoftThreads; i += kSoftThreads) s_mp[i] = 0;
+    }
     __syncthreads();
     if (tid < n) {
         const float4 r0 = s_rec[4 * tid], r1 = s_rec[4 * tid + 1], r2 = s_rec[4 * tid + 2], r3 = s_rec[4 * tid + 3];
@@ -393,9 +415,17 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
     }
     long long acc_t = 0, acc_a = 0, acc_o = 0;
     const float tm = a.tau_mm;
-    for (int i = blockIdx.x * kSoftThreads + tid; i < npix; i += gridDim.x * kSoftThreads) {
+    // The trip count is the same for every thread, so that the backward pass can
+    // reduce each primitive's adjoint across the warp (lanes without a pixel idle).
+    for (int base = blockIdx.x * kSoftThreads; base < npix; base += gridDim.x * kSoftThreads) {
+        const int i = base + tid;
+        uint64_t present = 0ull;  // backward: primitives in this lane's list
+        float ra = 0.f, rb = 0.f;
+        do {
+        if (i >= npix) break;
         const int v = bv0 + i / bw, u = bu0 + i % bw;
-        const float ra = fmaf((float)u, a.inv_fx, a.off_x), rb = fmaf((float)v, a.inv_fy, a.off_y);
+        ra = fmaf((float)u, a.inv_fx, a.off_x);
+        rb = fmaf((float)v, a.inv_fy, a.off_y);
         int cnt = 0;
         for (int j = 0; j < n; ++j) {
             const int4 bx = s_box[j];
@@ -416,7 +446,7 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
             s_zl[k * kSoftThreads + tid] = e.z;
             if (BWD) s_jl[k * kSoftThreads + tid] = (uint8_t)j;
         }
-        if (cnt == 0) continue;
+        if (cnt == 0) break;
         float T = 1.f, Nz = 0.f;
         for (int k = 0; k < cnt; ++k) {
             const float al = s_al[k * kSoftThreads + tid];
@@ -425,7 +455,7 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
             T *= 1.f - al;
         }
         const float c = 1.f - T;
-        if (!(c > 0.f)) continue;
+        if (!(c > 0.f)) break;
         const float zt = Nz / c;
         const float od = a.depth_f32 ? reinterpret_cast<const float*>(a.depth + (size_t)v * a.depth_pitch)[u]
                                      : (float)reinterpret_cast<const uint16_t*>(a.depth + (size_t)v * a.depth_pitch)[u];
@@ -454,6 +484,8 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
             else
                 acc_o += (long long)__float2int_rn(c * m * kFix);
         } else {
+            // per-entry adjoints of alpha and z through the compositing (back to front);
+            // each entry's (d alpha, d z) replaces its (T, alpha) in place
             const float gr_ = S ? G_and : G_or;
             const float gc = G_t * (t_hit - t_miss) + gr_ * m;
             const float gzt = valid ? (G_t * c * dsmin + gr_ * c * dm) * (-dd / diff) : 0.f;
@@ -463,30 +495,58 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
             for (int k = cnt - 1; k >= 0; --k) {
                 const float al = s_al[k * kSoftThreads + tid], zk = s_zl[k * kSoftThreads + tid];
                 const float Tk = s_Tl[k * kSoftThreads + tid];
-                const float ga = gN * Tk * (zk - Rsuf) + gct * Tk * Psuf;
-                const float gz = gN * Tk * al;
+                s_Tl[k * kSoftThreads + tid] = gN * Tk * (zk - Rsuf) + gct * Tk * Psuf;  // d E / d alpha
+                s_al[k * kSoftThreads + tid] = gN * Tk * al;                            // d E / d z
                 const int j = s_jl[k * kSoftThreads + tid];
-                SoftPrimEval e;
-                const float4 r0 = s_rec[4 * j], r1 = s_rec[4 * j + 1], r2 = s_rec[4 * j + 2], r3 = s_rec[4 * j + 3];
-                soft_eval(r0, r1, r2, r3, s_L[j], s_R[j], ra, rb, a.inv_fx, a.inv_fy, a.tau, e);
-                float adj[kAdj];
-#pragma unroll
-                for (int q = 0; q < kAdj; ++q) adj[q] = 0.f;
-                soft_backprop(r0, r1, r2, r3, s_L[j], s_R[j], ra, rb, a.inv_fx, a.inv_fy, a.tau, e, ga, gz, adj);
-#pragma unroll
-                for (int q = 0; q < kAdj; ++q)
-                    if (adj[q] != 0.f) atomicAdd(&s_adj[j * kAdj + q], adj[q]);
+                s_mp[j * kSoftThreads + tid] = (uint8_t)(k + 1);
+                present |= 1ull << j;
                 Rsuf = fmaf(al, zk, (1.f - al) * Rsuf);
                 Psuf *= 1.f - al;
+            }
+        }
+        } while (0);
+        if constexpr (BWD) {
+            // one primitive at a time across the warp: lanes that touch it push their
+            // (d alpha, d z) back to its record; the warp sums the 13 adjoints in fixed
+            // point and 13 lanes add them to the CTA's accumulators
+            const int lane = tid & 31;
+            for (int j = 0; j < n; ++j) {
+                const bool mine = (present >> j) & 1ull;
+                if (!__any_sync(0xffffffffu, mine)) continue;
+                long long f[kAdj];
+#pragma unroll
+                for (int q = 0; q < kAdj; ++q) f[q] = 0;
+                if (mine) {
+                    const int k = (int)s_mp[j * kSoftThreads + tid] - 1;
+                    s_mp[j * kSoftThreads + tid] = 0;
+                    const float ga = s_Tl[k * kSoftThreads + tid], gz = s_al[k * kSoftThreads + tid];
+                    const float4 r0 = s_rec[4 * j], r1 = s_rec[4 * j + 1], r2 = s_rec[4 * j + 2], r3 = s_rec[4 * j + 3];
+                    SoftPrimEval e;
+                    soft_eval(r0, r1, r2, r3, s_L[j], s_R[j], ra, rb, a.inv_fx, a.inv_fy, a.tau, e);
+                    float adj[kAdj];
+#pragma unroll
+                    for (int q = 0; q < kAdj; ++q) adj[q] = 0.f;
+                    soft_backprop(r0, r1, r2, r3, s_L[j], s_R[j], ra, rb, a.inv_fx, a.inv_fy, a.tau, e, ga, gz, adj);
+#pragma unroll
+                    for (int q = 0; q < kAdj; ++q) f[q] = adj_to_fix(adj[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < kAdj; ++q) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
+                }
+#pragma unroll
+                for (int q = 0; q < kAdj; ++q)
+                    if (lane == q && f[q] != 0) atomicAdd(&s_adj[j * kAdj + q], (unsigned long long)f[q]);
             }
         }
     }
 
     if constexpr (BWD) {
         __syncthreads();
-        float* dst = a.adj + (size_t)p * n * kAdj;
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.adj) + (size_t)p * n * kAdj;
         for (int i = tid; i < n * kAdj; i += kSoftThreads)
-            if (s_adj[i] != 0.f) atomicAdd(&dst[i], s_adj[i]);
+            if (s_adj[i] != 0ull) atomicAdd(&dst[i], s_adj[i]);
     } else {
     // forward: CTA sums, then the particle's last CTA forms E_s
 #pragma unroll
@@ -539,16 +599,16 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
 __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ DevModel model_param, const GradArgs a)
 {
     __shared__ FkShared sh;
-    __shared__ float s_g[kNdof];
-    extern __shared__ float s_tan[];  // [26][n_bones][12]: dR (9), dP (3) of every bone for every DOF
+    extern __shared__ float s_tan[];  // [26][n_bones][12]: dR (9), dP (3) of every bone for every DOF,
+                                      // then [n_prims][26]: each primitive's contribution
     fk_load_model(sh, model_param);
     const int p = blockIdx.x, t = threadIdx.x;
     const float* pose = a.poses + (size_t)p * kNdof;
     fk_particle(sh, pose, make_float4(a.fx, a.fy, a.cx, a.cy), a.prims + (size_t)p * sh.model.n_prims * 4, a.kc + p,
                 a.status);
-    if (t < kNdof) s_g[t] = 0.f;
     __syncthreads();
     const int nb = sh.model.n_bones, np = sh.model.n_prims;
+    float* s_contrib = s_tan + (size_t)kNdof * nb * 12;
     if (t < kNdof) {
         // tangents of every bone frame with respect to pose parameter t (parents first)
         for (int k = 0; k < nb; ++k) {
@@ -628,12 +688,12 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ D
         }
     }
     __syncthreads();
-    float* adjp = a.adj + (size_t)p * np * kAdj;
+    long long* adjp = a.adj + (size_t)p * np * kAdj;
     for (int j = t; j < np; j += 64) {
         const DevPrimDesc& D = sh.model.prims[j];
         float ad[kAdj];
 #pragma unroll
-        for (int q = 0; q < kAdj; ++q) ad[q] = adjp[j * kAdj + q];
+        for (int q = 0; q < kAdj; ++q) ad[q] = adj_from_fix(adjp[j * kAdj + q]);
         const float* R = sh.bR[D.bone];
         const float* O = sh.bP[D.bone];
         const bool cone = D.kind == HS_PRIM_ECONE;
@@ -690,14 +750,15 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ D
                 }
                 acc = fmaf(ad[12], dL, acc);
             }
-            if (acc != 0.f) atomicAdd(&s_g[k], acc);
+            s_contrib[j * kNdof + k] = acc;
         }
 #pragma unroll
-        for (int q = 0; q < kAdj; ++q) adjp[j * kAdj + q] = 0.f;  // ready for the next backward pass
+        for (int q = 0; q < kAdj; ++q) adjp[j * kAdj + q] = 0ll;  // ready for the next backward pass
     }
     __syncthreads();
     if (t < kNdof) {
-        float g = s_g[t];
+        float g = 0.f;
+        for (int j = 0; j < np; ++j) g += s_contrib[j * kNdof + t];  // fixed order: deterministic
         // kc(h) = sum over (11, 15), (15, 19), (19, 23) of max(q_b - q_a, 0)
         const int pa[3] = {11, 15, 19}, pb[3] = {15, 19, 23};
 #pragma unroll
@@ -744,7 +805,7 @@ cudaError_t launch_soft(bool backward, const SoftArgs& args, cudaStream_t stream
 
 cudaError_t launch_pose_grad(const DevModel& model, const GradArgs& args, cudaStream_t stream)
 {
-    const size_t smem = (size_t)kNdof * model.n_bones * 12 * sizeof(float);
+    const size_t smem = ((size_t)kNdof * model.n_bones * 12 + (size_t)model.n_prims * kNdof) * sizeof(float);
     pose_grad_kernel<<<args.P, 64, smem, stream>>>(model, args);
     return cudaGetLastError();
 }

@@ -28,7 +28,7 @@ class SoftScorer:
         self.kc = torch.zeros(P, **f)
         self.ws = hs.new_workspace(P, self.device)
         self.sums = torch.zeros(P, 3, **f)
-        self.adj = torch.zeros(P, self.model.n_prims, hs.SOFT_ADJ, **f)
+        self.adj = torch.zeros(P, self.model.n_prims, hs.SOFT_ADJ, dtype=torch.int64, device=self.device)
         self.grad = torch.zeros(P, 26, **f)
 
     def forward(self, poses: torch.Tensor) -> torch.Tensor:

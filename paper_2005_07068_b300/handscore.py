@@ -120,6 +120,11 @@ _SIGS = {
                             ctypes.c_int),
     "pose_grad": ([_vp, _vp, ctypes.c_int, ctypes.POINTER(HsCamera), ctypes.POINTER(HsScoreParams), _vp, _vp, _vp,
                    _vp, _vp], ctypes.c_int),
+    "polish_select": ([_vp, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
+    "polish_gather": ([_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
+    "polish_step": ([_vp, _vp, _vp, ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float), _vp],
+                    ctypes.c_int),
+    "polish_keep_better": ([_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
     "hs_batch_buffer_size": ([ctypes.POINTER(HsSwarmDesc), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
                              ctypes.c_int),
     "hs_batch_create": ([_vp, ctypes.POINTER(HsSwarmDesc), ctypes.c_int, _vp, ctypes.c_size_t, _vp,
@@ -403,7 +408,7 @@ def soft_score(model: Model, obs: Obs, cam: HsCamera, prims: torch.Tensor, kc: t
 
 def soft_score_backward(model: Model, obs: Obs, cam: HsCamera, prims: torch.Tensor, params: HsScoreParams,
                         soft: HsSoftParams, sums: torch.Tensor, adj: torch.Tensor, stream=None) -> None:
-    """Adds dE_s/d(records) to adj [P, n_prims, SOFT_ADJ] (zero on entry)."""
+    """Adds dE_s/d(records) to adj [P, n_prims, SOFT_ADJ] int64 (fixed point 2^-40, zero on entry)."""
     st = obs.struct()
     _check("soft_score_backward",
            lib().soft_score_backward(model.handle, ctypes.byref(st), ctypes.byref(cam), _ptr(prims), prims.shape[0],
@@ -416,6 +421,31 @@ def pose_grad(model: Model, poses: torch.Tensor, cam: HsCamera, params: HsScoreP
     _check("pose_grad", lib().pose_grad(model.handle, _ptr(poses), poses.shape[0], ctypes.byref(cam),
                                         ctypes.byref(params), _ptr(prims), _ptr(kc), _ptr(adj), _ptr(grad),
                                         _stream(stream)))
+
+
+# ---- gradient polish of the best particles ---------------------------------------------
+
+def polish_select(E: torch.Tensor, k: int, sel: torch.Tensor, stream=None) -> None:
+    """sel [k] int32 <- indices of the k lowest E (lower index on ties, NaN last)."""
+    _check("polish_select", lib().polish_select(_ptr(E), E.shape[0], int(k), _ptr(sel), _stream(stream)))
+
+
+def polish_gather(x: torch.Tensor, E: torch.Tensor, sel: torch.Tensor, x_sel: torch.Tensor, E_sel: torch.Tensor,
+                  stream=None) -> None:
+    _check("polish_gather", lib().polish_gather(_ptr(x), _ptr(E), _ptr(sel), sel.shape[0], _ptr(x_sel), _ptr(E_sel),
+                                                _stream(stream)))
+
+
+def polish_step(model: Model, x_sel: torch.Tensor, grad: torch.Tensor, eta: float, scale, stream=None) -> None:
+    sc = (ctypes.c_float * NDOF)(*[float(v) for v in scale])
+    _check("polish_step", lib().polish_step(model.handle, _ptr(x_sel), _ptr(grad), x_sel.shape[0], float(eta), sc,
+                                            _stream(stream)))
+
+
+def polish_keep_better(x: torch.Tensor, E: torch.Tensor, sel: torch.Tensor, x_sel: torch.Tensor, E_old: torch.Tensor,
+                       E_new: torch.Tensor, stream=None) -> None:
+    _check("polish_keep_better", lib().polish_keep_better(_ptr(x), _ptr(E), _ptr(sel), sel.shape[0], _ptr(x_sel),
+                                                          _ptr(E_old), _ptr(E_new), _stream(stream)))
 
 
 # ---- batches of independent swarms ---------------------------------------------------

@@ -70,6 +70,7 @@ class Tracker:
         hs.pose_fk(self.model, cur, self.cam, self.prims, self.kc)
         for g in range(1, self.gens + 1):
             hs.render_score_batch(self.model, obs, self.cam, self.prims, self.kc, self.score, self.ws, self.swarm.E)
+            self._after_render(obs, cur)
             self.swarm.x = cur
             hs.pso_step_fk(self.model, self.swarm, nxt, self.pso, self.seed, frame, g, self.cam, self.prims, self.kc)
             cur, nxt = nxt, cur
@@ -77,6 +78,9 @@ class Tracker:
                 self.history[g - 1, :26].copy_(self.swarm.gbest)
                 self.history[g - 1, 26:].copy_(self.swarm.gbest_E)
         self.swarm.x = cur
+
+    def _after_render(self, obs: hs.Obs, x: torch.Tensor) -> None:
+        """Hook between a generation's scoring and its swarm update (plain PSO: none)."""
 
     def _state(self) -> list:
         sw = self.swarm
@@ -130,6 +134,54 @@ class Tracker:
         self.run_frame(staging, frame, seed_pose)
         out_host[:26].copy_(self.swarm.gbest, non_blocking=True)
         out_host[26:].copy_(self.swarm.gbest_E, non_blocking=True)
+
+
+class HybridTracker(Tracker):
+    """Plain PSO plus, every generation, a gradient polish of the k best
+    particles: `steps` normalised descent steps on the smoothed objective E_s
+    (step lengths eta0, eta0 decay, ... in units of the per-parameter scale),
+    then the polished poses are scored with the exact E and kept only where E
+    fell.  The swarm update then proceeds as in plain PSO."""
+
+    def __init__(self, model: hs.Model, cam: hs.HsCamera, P: int = 64, gens: int = 40, *, k: int = 8,
+                 steps: int = 5, eta0: float = 0.3, decay: float = 0.7, soft=None, **kw):
+        super().__init__(model, cam, P, gens, **kw)
+        if not 1 <= k <= min(P, 256):
+            raise ValueError("k must be in 1..min(P, 256)")
+        self.k, self.steps = k, steps
+        self.etas = [eta0 * decay ** i for i in range(steps)]
+        self.soft = soft if soft is not None else hs.soft_params()
+        self.score_k = hs.score_params(self.score.d_m, self.score.d_M, self.score.lambda_, self.score.lambda_k)
+        f = dict(dtype=torch.float32, device=self.device)
+        self.sel = torch.zeros(k, dtype=torch.int32, device=self.device)
+        self.x_sel = torch.zeros(k, 26, **f)
+        self.E_sel = torch.zeros(k, **f)
+        self.E_new = torch.zeros(k, **f)
+        self.E_soft = torch.zeros(k, **f)
+        self.prims_k = torch.zeros(k, model.n_prims, 16, **f)
+        self.kc_k = torch.zeros(k, **f)
+        self.ws_k = hs.new_workspace(k, self.device)
+        self.sums_k = torch.zeros(k, 3, **f)
+        self.adj_k = torch.zeros(k, model.n_prims, hs.SOFT_ADJ, dtype=torch.int64, device=self.device)
+        self.grad_k = torch.zeros(k, 26, **f)
+
+    def _after_render(self, obs: hs.Obs, x: torch.Tensor) -> None:
+        m, cam, k = self.model, self.cam, self.k
+        hs.polish_select(self.swarm.E, k, self.sel)
+        hs.polish_gather(x, self.swarm.E, self.sel, self.x_sel, self.E_sel)
+        for eta in self.etas:
+            hs.pose_fk(m, self.x_sel, cam, self.prims_k, self.kc_k)
+            hs.soft_score(m, obs, cam, self.prims_k, self.kc_k, self.score_k, self.soft, self.ws_k, self.E_soft,
+                          self.sums_k)
+            hs.soft_score_backward(m, obs, cam, self.prims_k, self.score_k, self.soft, self.sums_k, self.adj_k)
+            hs.pose_grad(m, self.x_sel, cam, self.score_k, self.prims_k, self.kc_k, self.adj_k, self.grad_k)
+            hs.polish_step(m, self.x_sel, self.grad_k, eta, self.scale)
+        hs.pose_fk(m, self.x_sel, cam, self.prims_k, self.kc_k)
+        hs.render_score_batch(m, obs, cam, self.prims_k, self.kc_k, self.score_k, self.ws_k, self.E_new)
+        hs.polish_keep_better(x, self.swarm.E, self.sel, self.x_sel, self.E_sel, self.E_new)
+
+    def launches_per_frame(self) -> int:
+        return super().launches_per_frame() + self.gens * (5 + 5 * self.steps)
 
 
 # ---- many sequences at once ------------------------------------------------------------

@@ -188,6 +188,25 @@ def test_other_host_checks():
     assert L.pso_step_fk(m.handle, ctypes.byref(sw), FAKE + 4096, 5000, ctypes.byref(pp), 1, 0, 1, ctypes.byref(cam),
                          FAKE, FAKE, None) == hs.HS_ERR_SIZE
     assert hs.lib().hs_status_string(-3) == b"size out of range"
+    # gradient polish and the smoothed objective: host checks
+    assert L.polish_select(FAKE, 8, 9, FAKE, None) == hs.HS_ERR_SIZE   # k > P
+    assert L.polish_select(FAKE, 8, 0, FAKE, None) == hs.HS_ERR_SIZE
+    assert L.polish_select(None, 8, 4, FAKE, None) == hs.HS_ERR_ARG
+    assert L.polish_gather(FAKE, FAKE, FAKE, 300, FAKE, FAKE, None) == hs.HS_ERR_SIZE
+    bad_scale = (ctypes.c_float * 26)(*([1.0] * 25 + [0.0]))
+    assert L.polish_step(m.handle, FAKE, FAKE, 4, 0.1, bad_scale, None) == hs.HS_ERR_ARG
+    ok_scale = (ctypes.c_float * 26)(*([1.0] * 26))
+    assert L.polish_step(m.handle, FAKE, FAKE, 4, -1.0, ok_scale, None) == hs.HS_ERR_ARG
+    sp = hs.soft_params()
+    bad_sp = hs.soft_params(tau_px=0.0)
+    assert L.soft_score(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 4, ctypes.byref(prm),
+                        ctypes.byref(bad_sp), FAKE, 1 << 20, FAKE, None, None) == hs.HS_ERR_ARG
+    assert L.soft_score(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 4, ctypes.byref(prm),
+                        ctypes.byref(sp), FAKE, 16, FAKE, None, None) == hs.HS_ERR_SIZE
+    assert L.soft_score_backward(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, 4, ctypes.byref(prm),
+                                 ctypes.byref(sp), None, FAKE, None) == hs.HS_ERR_ARG
+    assert L.pose_grad(m.handle, FAKE, 4, ctypes.byref(cam), ctypes.byref(prm), FAKE + 8, FAKE, FAKE, FAKE,
+                       None) == hs.HS_ERR_ALIGN
     # render launch shape: variant and CTAs per particle are validated; autotuning needs params and reps >= 1
     bad_v = hs.score_params(variant=9)
     assert L.render_score_batch(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 64, ctypes.byref(bad_v),

@@ -117,3 +117,61 @@ def test_gradient_descends_and_respects_limits(scene):
     scorer.forward(out)
     g_out = scorer.gradient(out).cpu().numpy()
     assert np.all(g_out[:, 13] == 0.0)
+
+
+def test_polish_select_and_keep_better():
+    dev = torch.device("cuda")
+    E = torch.tensor([5.0, 1.0, 3.0, 1.0, float("nan"), 0.5, 7.0, 3.0], device=dev)
+    sel = torch.zeros(5, dtype=torch.int32, device=dev)
+    hs.polish_select(E, 5, sel)
+    torch.cuda.synchronize()
+    assert sel.cpu().tolist() == [5, 1, 3, 2, 7]  # ascending, lower index on ties, NaN last
+    x = torch.arange(8 * 26, dtype=torch.float32, device=dev).reshape(8, 26)
+    x_sel = torch.zeros(5, 26, device=dev)
+    E_sel = torch.zeros(5, device=dev)
+    hs.polish_gather(x, E, sel, x_sel, E_sel)
+    torch.cuda.synchronize()
+    assert torch.equal(x_sel, x[sel.long()]) and torch.equal(E_sel, E[sel.long()])
+    x_new = x_sel + 100.0
+    E_new = torch.tensor([0.4, 2.0, 0.9, float("nan"), 2.5], device=dev)  # better, worse, better, nan, better
+    hs.polish_keep_better(x, E, sel, x_new, E_sel, E_new)
+    torch.cuda.synchronize()
+    Ec = E.cpu().numpy()
+    assert Ec[5] == np.float32(0.4) and Ec[1] == 1.0 and Ec[3] == np.float32(0.9) and Ec[2] == 3.0
+    assert Ec[7] == np.float32(2.5)
+    assert torch.equal(x[5], x_new[0]) and torch.equal(x[3], x_new[2]) and torch.equal(x[1], x_sel[1])
+
+
+def test_hybrid_polish_never_raises_E_and_tracks(scene):
+    """One frame of the hybrid (k = 8, 5 polish steps): after every polish the
+    objectives are elementwise no larger than before it; gbest_E ends below the
+    starting pose's E; graph replay equals eager execution."""
+    from paper_2005_07068_b300 import tracker as T
+    sc, poses = scene
+    dev = torch.device("cuda")
+    obs = hs.Obs.from_numpy(sc.Od, sc.S, dev)
+    cam = hs.camera(*[float(v) for v in sc.cam])
+    start = torch.from_numpy(poses[3]).to(dev)
+
+    class Probe(T.HybridTracker):
+        def _after_render(self, o, x):
+            before = self.swarm.E.clone()
+            super()._after_render(o, x)
+            self.checks.append((before, self.swarm.E.clone()))
+
+    tr = Probe(sc.model_g, cam, P=64, gens=8, seed=11, device=dev)
+    tr.checks = []
+    tr.run_frame(obs, 0, start, graph=False)
+    torch.cuda.synchronize()
+    for before, after in tr.checks:
+        b, a = before.cpu().numpy(), after.cpu().numpy()
+        assert np.all(a <= b)
+    assert any(np.any(a.cpu().numpy() < b.cpu().numpy()) for b, a in tr.checks)  # the polish did something
+    eager = (tr.swarm.gbest.clone(), tr.swarm.gbest_E.clone())
+    E_start = C.run_gpu(sc, debug=False, poses=poses[3:4]).E[0]
+    assert float(eager[1][0]) < E_start
+    tr2 = T.HybridTracker(sc.model_g, cam, P=64, gens=8, seed=11, device=dev)
+    tr2.run_frame(obs, 0, start, graph=True)
+    torch.cuda.synchronize()
+    assert torch.equal(tr2.swarm.gbest, eager[0]) and torch.equal(tr2.swarm.gbest_E, eager[1])
+    REPORT["hybrid_frame_gbest_E"] = float(eager[1][0])

@@ -497,6 +497,110 @@ int pso_step_fk(const HsModel* model, const HsSwarm* sw, float* x_next, int P, c
     return launch_pso_step_fk(model->dev, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 
+// ---- a whole tracking frame in one cooperative launch -------------------------------
+
+int hs_frame_workspace_size(int P, size_t* bytes)
+{
+    if (!bytes) return HS_ERR_ARG;
+    if (P < 1 || P > HS_FRAME_MAX_PARTICLES) return HS_ERR_SIZE;
+    *bytes = sizeof(FrameCtl) + 3 * (size_t)P * sizeof(FrameSums);
+    return HS_OK;
+}
+
+int hs_frame_capacity(int* ctas)
+{
+    if (!ctas) return HS_ERR_ARG;
+    return track_frame_capacity(ctas) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int track_frame(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsSwarm* sw, float* x_next, int P,
+                int gens, const HsScoreParams* score, const HsPsoParams* prm, const float* seed_pose,
+                const float* scale, uint64_t seed, uint32_t frame, int ctas_per_particle, void* workspace,
+                size_t workspace_bytes, HsPrim* prims, float* kc, hs_stream_t stream)
+{
+    if (!model || !sw || !x_next || !score || !prm || !seed_pose || !scale || !kc) return HS_ERR_ARG;
+    if (!sw->x || !sw->v || !sw->pbest || !sw->pbest_E || !sw->gbest || !sw->gbest_E || !sw->E) return HS_ERR_ARG;
+    if (x_next == sw->x || gens < 0) return HS_ERR_ARG;
+    int rc = validate_obs(obs);
+    if (rc) return rc;
+    if ((rc = validate_cam(cam))) return rc;
+    if ((rc = validate_score_params(score))) return rc;
+    if (P < 1 || P > HS_FRAME_MAX_PARTICLES) return HS_ERR_SIZE;
+    if (ctas_per_particle < 0 || ctas_per_particle > 64) return HS_ERR_ARG;
+    const double psi = (double)prm->c1 + (double)prm->c2;
+    if (!std::isfinite(psi) || prm->c1 < 0.f || prm->c2 < 0.f || psi <= 4.0) return HS_ERR_ARG;
+    if (prm->mutate_every > 0 && (prm->n_mutate < 0 || prm->n_mutate > P)) return HS_ERR_ARG;
+    if (!workspace || (prims && !aligned16(prims)) || !aligned16(workspace)) return workspace ? HS_ERR_ALIGN : HS_ERR_ARG;
+    size_t need = 0;
+    hs_frame_workspace_size(P, &need);
+    if (workspace_bytes < need) return HS_ERR_SIZE;
+    FrameArgs a = {};
+    for (int d = 0; d < HS_NDOF; ++d) {
+        if (!std::isfinite(scale[d]) || scale[d] < 0.f) return HS_ERR_ARG;
+        a.scale[d] = scale[d];
+    }
+    int cap = 0;
+    if (track_frame_capacity(&cap) != cudaSuccess) return HS_ERR_CUDA;
+    int C = ctas_per_particle;
+    if (C == 0) C = std::min(8, cap / P);
+    if (C < 1 || (long long)P * C > cap) return HS_ERR_SIZE;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool f32 = obs->depth_type == HS_DEPTH_F32;
+    CUtensorMap tm_depth, tm_skin;
+    if ((rc = encode_tile_map(&tm_depth, obs->depth, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                              f32 ? 4 : 2, obs->W, obs->H, obs->depth_pitch)))
+        return rc;
+    if ((rc = encode_tile_map(&tm_skin, obs->skin, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, obs->W, obs->H, obs->skin_pitch)))
+        return rc;
+    a.W = obs->W;
+    a.H = obs->H;
+    a.depth_f32 = f32;
+    // rays and projection exactly as render_score_batch and pso_step_fk form them
+    a.inv_fx = (float)(1.0 / (double)cam->fx);
+    a.inv_fy = (float)(1.0 / (double)cam->fy);
+    a.off_x = (float)((0.5 - (double)cam->cx) / (double)cam->fx);
+    a.off_y = (float)((0.5 - (double)cam->cy) / (double)cam->fy);
+    a.cam = make_float4(cam->fx, cam->fy, cam->cx, cam->cy);
+    a.depth = static_cast<const unsigned char*>(obs->depth);
+    a.skin = obs->skin;
+    a.depth_pitch = obs->depth_pitch;
+    a.skin_pitch = obs->skin_pitch;
+    a.stats = obs->stats;
+    a.d_m = score->d_m;
+    a.d_M = score->d_M;
+    a.lambda = score->lambda;
+    a.lambda_k = score->lambda_k;
+    a.xbuf[0] = sw->x;
+    a.xbuf[1] = x_next;
+    a.v = sw->v;
+    a.pbest = sw->pbest;
+    a.pbest_E = sw->pbest_E;
+    a.gbest = sw->gbest;
+    a.gbest_E = sw->gbest_E;
+    a.E = const_cast<float*>(sw->E);
+    a.prims_out = reinterpret_cast<float4*>(prims);
+    a.kc = kc;
+    a.seed_pose = seed_pose;
+    a.c1 = prm->c1;
+    a.c2 = prm->c2;
+    a.w = (float)(2.0 / std::fabs(2.0 - psi - std::sqrt(psi * psi - 4.0 * psi)));
+    a.mutate_every = prm->mutate_every;
+    a.n_mutate = prm->n_mutate;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.frame = frame;
+    a.P = P;
+    a.C = C;
+    a.gens = gens;
+    a.ctl = static_cast<FrameCtl*>(workspace);
+    a.sums = reinterpret_cast<FrameSums*>(static_cast<unsigned char*>(workspace) + sizeof(FrameCtl));
+    if ((rc = status_ptr(&a.status))) return rc;
+    // the frame's observation totals start from zero (as hs_obs_prepare)
+    if (cudaMemsetAsync(obs->stats, 0, 2 * sizeof(uint32_t), s) != cudaSuccess) return HS_ERR_CUDA;
+    return launch_track_frame(model->dev, tm_depth, tm_skin, a, s) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
 // ---- the smoothed objective and its gradient ---------------------------------------
 
 static int soft_common(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsPrim* prims, int P,

@@ -1,0 +1,307 @@
+// frame.cu -- one whole tracking frame (Section III.B: initialise the swarm
+// around the previous frame's best pose, then generations of "score every
+// particle (Section III.A, Eq. 4-5), move the swarm (Eq. 6-7, mutation)") in
+// a single cooperative launch.
+//
+// The graph path launches a kernel per step (observation totals, init, FK,
+// then render + fused step per generation): about 20 us per generation at
+// 64 particles, mostly launch gaps and the latency chains of short kernels.
+// Here C CTAs per particle stay resident for the whole frame:
+//
+//  * every CTA keeps its particle's state (position, velocity, personal best)
+//    and its FK records in shared memory; the C CTAs of a particle run the
+//    same FK and the same swarm update (identical inputs, identical results),
+//    and the first of them (the primary) stores the particle's state;
+//  * generation g: FK of the current pose -> raster records -> the CTA's share
+//    of the particle's 16x4 units (the unit renderer of render_score_batch,
+//    hs_units.cuh) -> integer sums added to the particle's slot of generation
+//    g (three slots rotate, so a slot is cleared two generations before it is
+//    reused) -> one grid barrier -> every CTA forms E of every particle of the
+//    swarm from the sums (form_E, as the render kernels do) and takes its
+//    particle's step (swarm_update, as pso_step_fk does);
+//  * the observation totals are counted by all CTAs before the first barrier.
+//
+// Results equal the graph path bit for bit (unit kernel render + pso_step_fk),
+// because every piece of arithmetic is the same code.  The barrier's wait is
+// bounded: if it runs out, HS_DEV_BARRIER_TIMEOUT is set and the CTAs leave.
+// The last CTA to leave returns the workspace to zero for the next frame.
+#include "hs_step.cuh"
+#include "hs_units.cuh"
+
+namespace hs {
+
+constexpr int kFrameWarps = 8;
+constexpr int kFrameThreads = kFrameWarps * 32;
+constexpr uint32_t kBarrierPolls = 1u << 24;  // each poll sleeps ~0.1 us: a few seconds in all
+
+struct FrameShared {
+    FkShared fk;                      // model, pose, bone frames
+    float4 rec[kMaxPrims * 4];        // this particle's FK records
+    float4 rast[kMaxPrims * 5];       // their raster records
+    int2 pbox[kMaxPrims];
+    alignas(128) unsigned char tile[kFrameWarps][kStages][kSlot];
+    uint64_t bar[kFrameWarps][kStages];
+    float x[kNdof], v[kNdof], pb[kNdof];  // the particle's state (identical in its C CTAs)
+    float pe;                             // its personal-best E
+    float kc;
+    float r[4 * kPairBlocks], m[4 * kMutBlocks];
+    long long red_t[kFrameWarps];
+    uint32_t red_c[kFrameWarps][3];
+    float red_v[kFrameWarps];
+    int red_i[kFrameWarps], red_r[kFrameWarps];
+    uint32_t st[2];
+    int box[4];
+};
+
+// all threads of every CTA: returns false if the wait ran out
+__device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, uint32_t* status)
+{
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        uint32_t v;
+        // release: this CTA's earlier writes (seen by thread 0 through the CTA
+        // barrier) are visible to whoever acquires the count
+        asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(v) : "l"(count) : "memory");
+        uint32_t polls = 0;
+        for (;;) {
+            asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            if (v >= target) break;
+            if (++polls >= kBarrierPolls) {
+                set_status(status, HS_DEV_BARRIER_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+__global__ void __launch_bounds__(kFrameThreads, 3)
+    track_frame_kernel(const __grid_constant__ DevModel model, const __grid_constant__ CUtensorMap tm_depth,
+                       const __grid_constant__ CUtensorMap tm_skin, const FrameArgs a)
+{
+    __shared__ FrameShared sh;
+    extern __shared__ float s_dyn[];  // E [P], then pbest_E [P] as read
+    float* s_e = s_dyn;
+    float* s_pe = s_dyn + a.P;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int P = a.P, p = blockIdx.x / a.C, c = blockIdx.x % a.C;
+    const bool primary = c == 0;
+    const uint32_t nblocks = gridDim.x;
+    const int n_prims = model.n_prims;
+
+    fk_load_model(sh.fk, model);
+    if (lane < kStages) mbar_init(&sh.bar[warp][lane], 1);
+    if (t == 0) {
+        mbar_fence_init();
+        sh.st[0] = sh.st[1] = 0u;
+    }
+    __syncthreads();
+
+    // observation totals of the frame (#valid skin pixels, #skin pixels):
+    // rows split over all CTAs, complete before the first barrier
+    {
+        uint32_t nv = 0, ns = 0;
+        for (int y = blockIdx.x; y < a.H; y += nblocks) {
+            for (int x = t; x < a.W; x += kFrameThreads) {
+                const bool S = a.skin[(size_t)y * a.skin_pitch + x] != 0;
+                const float od = a.depth_f32 ? reinterpret_cast<const float*>(a.depth + (size_t)y * a.depth_pitch)[x]
+                                             : (float)reinterpret_cast<const uint16_t*>(
+                                                   a.depth + (size_t)y * a.depth_pitch)[x];
+                ns += S;
+                nv += S && od > 0.f;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            nv += __shfl_xor_sync(0xffffffffu, nv, o);
+            ns += __shfl_xor_sync(0xffffffffu, ns, o);
+        }
+        if (lane == 0 && (nv | ns)) {
+            atomicAdd(&sh.st[0], nv);
+            atomicAdd(&sh.st[1], ns);
+        }
+    }
+
+    // tracking initialisation of this particle (as pso_init)
+    if (t < kNdof) {
+        const float xv = init_position(p, t, a.seed_pose[t], a.scale[t], sh.fk.model.lo[t], sh.fk.model.hi[t],
+                                       a.frame, a.key0, a.key1);
+        sh.x[t] = xv;
+        sh.v[t] = 0.f;
+        sh.pb[t] = xv;
+        if (primary) {
+            const size_t o = (size_t)p * kNdof + t;
+            a.xbuf[0][o] = xv;
+            a.v[o] = 0.f;
+            a.pbest[o] = xv;
+            if (p == 0) a.gbest[t] = xv;
+        }
+    }
+    if (t == 0) {
+        sh.pe = INFINITY;
+        if (primary) {
+            a.pbest_E[p] = INFINITY;
+            if (p == 0) a.gbest_E[0] = INFINITY;
+        }
+    }
+    __syncthreads();
+    if (t == 0 && (sh.st[0] | sh.st[1])) {
+        atomicAdd(&a.stats[0], sh.st[0]);
+        atomicAdd(&a.stats[1], sh.st[1]);
+    }
+
+    const ParticleView pv{a.W, a.H, a.depth_f32, a.inv_fx, a.off_x, a.inv_fy, a.off_y, a.stats, &tm_depth, &tm_skin};
+    RenderArgs ra = {};
+    ra.d_m = a.d_m;
+    ra.d_M = a.d_M;
+    ra.status = a.status;
+    const SwarmRefs R0{nullptr, nullptr, a.v, a.pbest, a.pbest_E, a.gbest, a.gbest_E, a.c1, a.c2, a.w, 0};
+    uint32_t phases = 0u;
+    uint32_t barriers = 0u;
+    bool alive = true;
+    for (int g = 1; g <= a.gens; ++g) {
+        draw_step_randoms(p, (uint32_t)g, a.frame, a.key0, a.key1, sh.r, sh.m, t);
+        // FK of the current pose (fk_particle starts with a barrier that publishes sh.x)
+        fk_particle(sh.fk, sh.x, a.cam, sh.rec, &sh.kc, a.status);
+        __syncthreads();
+        stage_prims(sh.rec, n_prims, pv, sh.rast, sh.pbox, t, kFrameThreads);
+        if (warp == 0) unit_box(sh.rec, n_prims, a.W, a.H, lane, sh.box);
+        __syncthreads();
+        long long acc_t = 0;
+        uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
+        if (sh.box[3] > 0)
+            render_units_warp(sh.rast, sh.pbox, n_prims, sh.box, sh.tile[warp], sh.bar[warp], phases,
+                              c * kFrameWarps + warp, a.C * kFrameWarps, pv, ra, p, lane, acc_t, acc_a, acc_o, acc_h);
+        warp_sum(acc_t, acc_a, acc_o, acc_h);
+        if (lane == 0) {
+            sh.red_t[warp] = acc_t;
+            sh.red_c[warp][0] = acc_a;
+            sh.red_c[warp][1] = acc_o;
+            sh.red_c[warp][2] = acc_h;
+        }
+        __syncthreads();
+        FrameSums* slot = a.sums + (size_t)(g % 3) * P;
+        if (t == 0) {
+            for (int w = 1; w < kFrameWarps; ++w) {
+                acc_t += sh.red_t[w];
+                acc_a += sh.red_c[w][0];
+                acc_o += sh.red_c[w][1];
+                acc_h += sh.red_c[w][2];
+            }
+            if (acc_t) atomicAdd(&slot[p].t_fix, (unsigned long long)acc_t);
+            if (acc_a) atomicAdd(&slot[p].n_and, acc_a);
+            if (acc_o) atomicAdd(&slot[p].n_or, acc_o);
+            if (acc_h) atomicAdd(&slot[p].n_hit, acc_h);
+            if (primary) slot[p].kc = sh.kc;
+        }
+        // every particle's sums (and the frame's totals) are in
+        ++barriers;
+        if (!grid_barrier(&a.ctl->barrier, barriers * nblocks, a.status)) {
+            alive = false;
+            break;
+        }
+        // E of every particle of the swarm, and the personal-best Es as read
+        // (this particle's own from its copy)
+        // (loads through L2: other CTAs wrote these during this launch)
+        const uint32_t stats[2] = {__ldcg(a.stats), __ldcg(a.stats + 1)};
+        for (int j = t; j < P; j += kFrameThreads) {
+            const uint4 w0 = __ldcg(reinterpret_cast<const uint4*>(slot + j));
+            const uint4 w1 = __ldcg(reinterpret_cast<const uint4*>(slot + j) + 1);
+            const long long tf = (long long)(((unsigned long long)w0.y << 32) | w0.x);
+            float t_sum;
+            uint32_t so;
+            s_e[j] = form_E(tf, w0.z, w0.w, stats, a.d_M, a.lambda, a.lambda_k, __uint_as_float(w1.y), t_sum, so);
+            s_pe[j] = j == p ? sh.pe : __ldcg(a.pbest_E + j);
+        }
+        __syncthreads();
+        SwarmRefs R = R0;
+        R.x = a.xbuf[(g - 1) & 1];
+        R.x_next = a.xbuf[g & 1];
+        R.mutate = a.mutate_every > 0 && g % a.mutate_every == 0 && a.n_mutate > 0;
+        float xi = 0.f, pbi = 0.f, vi = 0.f;
+        if (t < kNdof) {
+            xi = sh.x[t];
+            pbi = sh.pb[t];
+            vi = sh.v[t];
+        }
+        const StepOut o = swarm_update<kFrameThreads>(R, p, p, 0, P, 0, a.n_mutate, s_e, s_pe, sh.r, sh.m,
+                                                      sh.fk.model.lo, sh.fk.model.hi, xi, pbi, vi, sh.pe, primary,
+                                                      sh.red_v, sh.red_i, sh.red_r);
+        __syncthreads();  // every thread has read sh.x / sh.pe of this generation
+        if (t < kNdof) {
+            sh.x[t] = o.xn;
+            sh.v[t] = o.vn;
+            sh.pb[t] = o.pb;
+        }
+        if (t == 0) {
+            if (o.imp) sh.pe = s_e[p];
+            if (primary) {
+                a.E[p] = s_e[p];
+                // the slot generation g + 2 will use: every CTA read it (as
+                // generation g - 1's) before this barrier, none writes it before the next
+                a.sums[(size_t)((g + 2) % 3) * P + p] = FrameSums{};
+            }
+        }
+    }
+    if (alive) {
+        // the records and kc of the final positions
+        fk_particle(sh.fk, sh.x, a.cam, sh.rec, &sh.kc, a.status);
+        __syncthreads();
+        if (primary) {
+            if (a.prims_out)
+                for (int i = t; i < n_prims * 4; i += kFrameThreads)
+                    a.prims_out[(size_t)p * n_prims * 4 + i] = sh.rec[i];
+            if (t == 0) a.kc[p] = sh.kc;
+        }
+    }
+    // leave; the last CTA returns the workspace to zero
+    __syncthreads();
+    __shared__ uint32_t s_last;
+    if (t == 0) {
+        uint32_t done;
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(done) : "l"(&a.ctl->exited) : "memory");
+        s_last = done == nblocks - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        for (int i = t; i < 3 * P; i += kFrameThreads) a.sums[i] = FrameSums{};
+        if (t == 0) {
+            a.ctl->barrier = 0u;
+            a.ctl->exited = 0u;
+        }
+    }
+}
+
+cudaError_t track_frame_capacity(int* ctas)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // the dynamic part (2 P floats) is small next to the static part; size it for the largest P
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_frame_kernel, kFrameThreads,
+                                                          2 * HS_FRAME_MAX_PARTICLES * sizeof(float));
+    *ctas = e == cudaSuccess ? sms * per_sm : 0;
+    return e;
+}
+
+cudaError_t launch_track_frame(const DevModel& model, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,
+                               const FrameArgs& args, cudaStream_t stream)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(args.P * args.C);
+    cfg.blockDim = dim3(kFrameThreads);
+    cfg.dynamicSmemBytes = 2 * (size_t)args.P * sizeof(float);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident at once (the grid barrier needs it)
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, track_frame_kernel, model, tm_depth, tm_skin, args);
+}
+
+}  // namespace hs

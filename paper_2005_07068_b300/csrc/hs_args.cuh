@@ -105,6 +105,46 @@ struct PsoFkArgs {
     BatchDev batch;        // when set: every particle works within its own swarm
 };
 
+// ---- one whole tracking frame in one cooperative launch (frame.cu) ----
+// per-particle sums of one generation (32 bytes): the render's integer sums
+// and the kc of the scored pose
+struct FrameSums {
+    unsigned long long t_fix;     // sum of depth-term differences, fixed point 2^-24 mm
+    uint32_t n_and, n_or, n_hit;  // sum(S and r_m), sum(r_m and not S), rendered pixels
+    float kc;
+    uint32_t pad[2];
+};
+// control block at the start of the frame workspace (128 bytes)
+struct FrameCtl {
+    uint32_t barrier;  // grid-barrier arrivals of this launch
+    uint32_t exited;   // CTAs that have finished
+    uint32_t pad[30];
+};
+
+struct FrameArgs {
+    int W, H, depth_f32;
+    float inv_fx, inv_fy, off_x, off_y;  // render rays
+    float4 cam;                          // FK projection: fx, fy, cx, cy
+    const unsigned char* depth;
+    const uint8_t* skin;
+    int depth_pitch, skin_pitch;
+    uint32_t* stats;                     // obs stats [2], zero at launch
+    float d_m, d_M, lambda, lambda_k;
+    float* xbuf[2];                      // positions: generation g scores xbuf[(g - 1) & 1], writes xbuf[g & 1]
+    float *v, *pbest, *pbest_E, *gbest, *gbest_E, *E;
+    float4* prims_out;                   // [P][n_prims][4] records of the final positions, or nullptr
+    float* kc;                           // [P] kc of the final positions
+    const float* seed_pose;              // [26]
+    float scale[kNdof];                  // initial spread per dimension
+    float c1, c2, w;
+    int mutate_every, n_mutate;
+    uint32_t key0, key1, frame;
+    int P, C, gens;
+    FrameCtl* ctl;
+    FrameSums* sums;                     // [3][P]
+    uint32_t* status;
+};
+
 // ---- the smoothed objective and its gradient (soft.cu) ----
 constexpr int kAdj = HS_SOFT_ADJ;  // per-primitive adjoint: record M (9), C (3), cone length L (1)
 
@@ -161,6 +201,9 @@ cudaError_t launch_pose_grad(const DevModel& model, const GradArgs& args, cudaSt
 
 cudaError_t launch_fk(const DevModel& model, const FkArgs& args, cudaStream_t stream);
 cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cudaStream_t stream);
+cudaError_t launch_track_frame(const DevModel& model, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,
+                               const FrameArgs& args, cudaStream_t stream);
+cudaError_t track_frame_capacity(int* ctas);  // co-resident CTAs of track_frame_kernel on the current device
 cudaError_t launch_render_score(const CUtensorMap& tm_depth, const CUtensorMap& tm_skin, const RenderArgs& args,
                                 cudaStream_t stream);
 cudaError_t launch_render_tiles(int variant, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,

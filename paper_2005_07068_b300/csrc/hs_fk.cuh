@@ -69,7 +69,7 @@ __device__ __forceinline__ bool ellipse_ray_bounds(const float C[3], const float
     const float ez = sqrtf(fmaxf(Sg[2], 0.f));  // z half-extent
     if (!(C[2] - ez >= 1.0f)) return false;
     const float al = fmaf(C[2], C[2], -Sg[2]);
-    const float ial = 1.f / al;
+    const float ial = __frcp_rn(al);  // correctly rounded, as 1 / al
     {
         const float be = fmaf(C[0], C[2], -Sg[4]);
         const float disc = fmaf(Sg[0], C[2] * C[2], fmaf(-2.f * Sg[4], C[0] * C[2], fmaf(Sg[2], C[0] * C[0],

@@ -66,31 +66,115 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // ---- ray / quadric ----------------------------------------------------------------
-// Nearest hit of pixel direction d = (a, b, 1) with one primitive, as the depth
-// offset s from the primitive's centre depth t0 = C_z (depth = t0 + s), or +inf.
-// In scaled local coordinates the ray is g + s h with h = M d and
-// g = M (t0 d - C) = M (t0 a - C_x, t0 b - C_y, 0):
+// A primitive in scaled local coordinates is the quadric
 //   ellipsoid:  |p|^2 = 1
 //   cone:       X^2 + Z^2 = (1 + kappa Y)^2, |Y| <= 1, and the caps at Y = -1, +1
 //               that the model leaves visible (record word 12)
-__device__ __forceinline__ float intersect(const float4& r0, const float4& r1, const float4& r2, const float4& r3,
-                                          float a, float b)
+// and the ray of pixel (u, v), d = (a, b, 1) with a = u inv_fx + off_x, meets it
+// at depth t0 + s where the quadratic A s^2 + 2 B s + C = 0 holds (t0 = C_z, the
+// primitive's centre depth).  Written relative to the ray through the projected
+// centre, d = d_c + (alpha, beta, 0) with t0 d_c = C, the local ray is g + s h
+// with k = M (alpha, beta, 0), g = t0 k, h = h_c + k, h_c = M d_c.
+//
+// Its discriminant B^2 - A C is a quadratic polynomial in the pixel offsets
+// (du, dv) = (u - u_c, v - v_c) from the projected centre (the quartic and
+// cubic terms cancel exactly, because shifting s does not change it).  Written
+// with the identity (x.Dy)^2 - (x.Dx)(y.Dy) = -sum_{i<j} d_i d_j (x_i y_j - x_j y_i)^2
+// for diagonal D, its coefficients are sums of squares of small terms, with no
+// cancellation of the ~t0^2 |h_c|^2 parts:
+//   ellipsoid: disc = |h_c|^2 + 2 h_c.k + |k|^2 - t0^2 |h_c x k|^2
+//   cone:      disc = h_X^2 + h_Z^2 + 2 (h_X k_X + h_Z k_Z) + 2 kappa t0 (h_X n_XY - h_Z n_YZ)
+//                     + k_X^2 + k_Z^2 + 2 t0 kappa (k_X n_XY - k_Z n_YZ)
+//                     + t0^2 (kappa^2 (n_XY^2 + n_YZ^2) - n_XZ^2)
+//              (h = h_c, n_ij = h_i k_j - h_j k_i)
+// So a pixel is tested for coverage with five FMAs; the roots, which need A,
+// B, C, are formed only where the discriminant is not negative.
+//
+// Raster record (5 float4, built once per CTA from the 64-byte FK record):
+//   q0 = (u_c, v_c, c0, c_u)   q1 = (c_v, c_uu, c_uv, c_vv)   disc polynomial
+//   q2 = (k_u, t0)             q3 = (k_v, kappa or ellipsoid marker)
+//   q4 = (h_c, caps)           k = du k_u + dv k_v
+struct RasterPrim {
+    float4 q0, q1, q2, q3, q4;
+};
+
+__device__ __forceinline__ RasterPrim make_raster(const float4* rec, float inv_fx, float off_x, float inv_fy,
+                                                  float off_y)
 {
+    const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
+    const float m0[3] = {r0.x, r0.y, r0.z}, m1[3] = {r0.w, r1.x, r1.y}, m2[3] = {r1.z, r1.w, r2.x};
     const float t0 = r2.w, kap = r3.y;
-    const float hx = fmaf(a, r0.x, fmaf(b, r0.w, r1.z));
-    const float hy = fmaf(a, r0.y, fmaf(b, r1.x, r1.w));
-    const float hz = fmaf(a, r0.z, fmaf(b, r1.y, r2.x));
-    const float ex = fmaf(t0, a, -r2.y), ey = fmaf(t0, b, -r2.z);
-    const float gx = fmaf(ex, r0.x, ey * r0.w);
-    const float gy = fmaf(ex, r0.y, ey * r1.x);
-    const float gz = fmaf(ex, r0.z, ey * r1.y);
+    // projected centre direction and pixel (correctly rounded reciprocals: a
+    // few ulps in u_c, v_c shift the silhouette by ~1e-4 px at most)
+    const float it0 = __frcp_rn(t0);
+    const float ac = r2.y * it0, bc = r2.z * it0;
+    const float uc = (ac - off_x) * __frcp_rn(inv_fx), vc = (bc - off_y) * __frcp_rn(inv_fy);
+    float hc[3], ku[3], kv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        hc[i] = fmaf(ac, m0[i], fmaf(bc, m1[i], m2[i]));
+        ku[i] = m0[i] * inv_fx;
+        kv[i] = m1[i] * inv_fy;
+    }
+    // (u, v) coefficients of the linear forms, and of products of two of them
+    struct L { float u, v; };
+    auto cr = [&](int i, int j) { return L{hc[i] * ku[j] - hc[j] * ku[i], hc[i] * kv[j] - hc[j] * kv[i]}; };
+    const L kX{ku[0], kv[0]}, kY{ku[1], kv[1]}, kZ{ku[2], kv[2]};
+    float c0, cu, cv, cuu, cuv, cvv;
+    const float t2 = t0 * t0;
+    if (kap > 1.5f) {  // ellipsoid
+        const L n0 = cr(1, 2), n1 = cr(2, 0), n2 = cr(0, 1);
+        c0 = hc[0] * hc[0] + hc[1] * hc[1] + hc[2] * hc[2];
+        cu = 2.f * (hc[0] * kX.u + hc[1] * kY.u + hc[2] * kZ.u);
+        cv = 2.f * (hc[0] * kX.v + hc[1] * kY.v + hc[2] * kZ.v);
+        cuu = (kX.u * kX.u + kY.u * kY.u + kZ.u * kZ.u) - t2 * (n0.u * n0.u + n1.u * n1.u + n2.u * n2.u);
+        cuv = 2.f * ((kX.u * kX.v + kY.u * kY.v + kZ.u * kZ.v) - t2 * (n0.u * n0.v + n1.u * n1.v + n2.u * n2.v));
+        cvv = (kX.v * kX.v + kY.v * kY.v + kZ.v * kZ.v) - t2 * (n0.v * n0.v + n1.v * n1.v + n2.v * n2.v);
+    } else {  // cone
+        const L nXY = cr(0, 1), nYZ = cr(1, 2), nXZ = cr(0, 2);
+        const float tk = t0 * kap, tk2 = t2 * kap * kap;
+        c0 = hc[0] * hc[0] + hc[2] * hc[2];
+        cu = 2.f * (hc[0] * kX.u + hc[2] * kZ.u) + 2.f * tk * (hc[0] * nXY.u - hc[2] * nYZ.u);
+        cv = 2.f * (hc[0] * kX.v + hc[2] * kZ.v) + 2.f * tk * (hc[0] * nXY.v - hc[2] * nYZ.v);
+        cuu = kX.u * kX.u + kZ.u * kZ.u + 2.f * tk * (kX.u * nXY.u - kZ.u * nYZ.u) +
+              tk2 * (nXY.u * nXY.u + nYZ.u * nYZ.u) - t2 * nXZ.u * nXZ.u;
+        cuv = 2.f * (kX.u * kX.v + kZ.u * kZ.v) +
+              2.f * tk * (kX.u * nXY.v + kX.v * nXY.u - kZ.u * nYZ.v - kZ.v * nYZ.u) +
+              2.f * tk2 * (nXY.u * nXY.v + nYZ.u * nYZ.v) - 2.f * t2 * nXZ.u * nXZ.v;
+        cvv = kX.v * kX.v + kZ.v * kZ.v + 2.f * tk * (kX.v * nXY.v - kZ.v * nYZ.v) +
+              tk2 * (nXY.v * nXY.v + nYZ.v * nYZ.v) - t2 * nXZ.v * nXZ.v;
+    }
+    RasterPrim R;
+    R.q0 = make_float4(uc, vc, c0, cu);
+    R.q1 = make_float4(cv, cuu, cuv, cvv);
+    R.q2 = make_float4(ku[0], ku[1], ku[2], t0);
+    R.q3 = make_float4(kv[0], kv[1], kv[2], kap);
+    R.q4 = make_float4(hc[0], hc[1], hc[2], r3.x);
+    return R;
+}
+
+// the discriminant at pixel offsets (du, dv): >= 0 where the quadric's surface
+// can be hit (for a cone with visible caps the caps are tested regardless)
+__device__ __forceinline__ float raster_disc(const float4& q0, const float4& q1, float du, float dv)
+{
+    return fmaf(du, fmaf(du, q1.y, fmaf(dv, q1.z, q0.w)), fmaf(dv, fmaf(dv, q1.w, q1.x), q0.z));
+}
+
+// Nearest hit of the pixel at offsets (du, dv) with one primitive, given its
+// discriminant there, as the depth offset s from the primitive's centre depth
+// t0 (depth = t0 + s), or +inf.
+__device__ __forceinline__ float raster_hit(const float4& q2, const float4& q3, const float4& q4, float du, float dv,
+                                            float disc)
+{
+    const float t0 = q2.w, kap = q3.w;
+    const float kx = fmaf(du, q2.x, dv * q3.x), ky = fmaf(du, q2.y, dv * q3.y), kz = fmaf(du, q2.z, dv * q3.z);
+    const float hx = q4.x + kx, hy = q4.y + ky, hz = q4.z + kz;
+    const float gx = t0 * kx, gy = t0 * ky, gz = t0 * kz;
     float best = INFINITY;
     if (kap > 1.5f) {
-        const float A = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-        const float B = fmaf(gx, hx, fmaf(gy, hy, gz * hz));
-        const float C = fmaf(gx, gx, fmaf(gy, gy, fmaf(gz, gz, -1.f)));
-        const float disc = fmaf(B, B, -A * C);
         if (disc >= 0.f) {
+            const float A = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+            const float B = fmaf(gx, hx, fmaf(gy, hy, gz * hz));
             const float sq = sqrt_approx(disc);
             const float ia = rcp_approx(A);
             const float sn = (-B - sq) * ia;
@@ -98,12 +182,11 @@ __device__ __forceinline__ float intersect(const float4& r0, const float4& r1, c
             best = t0 + sn > 0.f ? sn : (t0 + sf > 0.f ? sf : INFINITY);
         }
     } else {
-        const float w0 = fmaf(kap, gy, 1.f), w1 = kap * hy;
-        const float A = fmaf(hx, hx, fmaf(hz, hz, -w1 * w1));
-        const float B = fmaf(gx, hx, fmaf(gz, hz, -w0 * w1));
-        const float C = fmaf(gx, gx, fmaf(gz, gz, -w0 * w0));
-        const float disc = fmaf(B, B, -A * C);
         if (disc >= 0.f) {
+            const float w0 = fmaf(kap, gy, 1.f), w1 = kap * hy;
+            const float A = fmaf(hx, hx, fmaf(hz, hz, -w1 * w1));
+            const float B = fmaf(gx, hx, fmaf(gz, hz, -w0 * w1));
+            const float C = fmaf(gx, gx, fmaf(gz, gz, -w0 * w0));
             const float sq = sqrt_approx(disc);
             const float qq = -(B + copysignf(sq, B));
             const float s1 = qq * rcp_approx(A);
@@ -112,7 +195,7 @@ __device__ __forceinline__ float intersect(const float4& r0, const float4& r1, c
             if (fabsf(y1) <= 1.f && t0 + s1 > 0.f) best = fminf(best, s1);
             if (fabsf(y2) <= 1.f && t0 + s2 > 0.f) best = fminf(best, s2);
         }
-        const uint32_t caps = __float_as_uint(r3.x);
+        const uint32_t caps = __float_as_uint(q4.w);
         if (caps) {  // planar caps at Y = -1 (radius 1 - kappa) and Y = +1 (radius 1 + kappa)
             const float ihy = rcp_approx(hy);
 #pragma unroll
@@ -127,6 +210,12 @@ __device__ __forceinline__ float intersect(const float4& r0, const float4& r1, c
         }
     }
     return best;
+}
+
+// true when the primitive must be tested at a pixel whose discriminant is disc
+__device__ __forceinline__ bool raster_maybe(const float4& q4, float disc)
+{
+    return disc >= 0.f || __float_as_uint(q4.w) != 0u;
 }
 
 // per-pixel terms of Eq. 4 (reading R1) as differences to the no-hit baseline,
@@ -182,6 +271,30 @@ __device__ __forceinline__ void write_baseline(const RenderArgs& a, int p, const
     if (a.parts) a.parts[p] = HsParts{t_sum, 0u, n_skin, 0u};
 }
 
+// E of Eq. 5 from a particle's sums (reading R1): tf = sum of the rendered
+// pixels' depth-term differences to the no-hit baseline (fixed point, 2^-24
+// mm), sa = sum(S and r_m), so_d = sum(r_m and not S); the frame's totals
+// stats = (#valid skin pixels, #skin pixels) supply the baseline.
+// D = sum t / sum(S or r_m) + lambda (1 - 2 sum(S and r_m) / (sum(S and r_m) + sum(S or r_m))),
+// D = lambda for an empty union; E = D + lambda_k kc.
+__device__ __forceinline__ float form_E(long long tf, uint32_t sa, uint32_t so_d, const uint32_t* stats, float d_M,
+                                        float lambda, float lambda_k, float kcp, float& t_sum, uint32_t& so)
+{
+    const uint32_t n_valid = stats[0], n_skin = stats[1];
+    // fixed point -> float from the two 32-bit halves (no 64-bit conversion)
+    const float t_fix_f = (float)(int)(tf >> 32) * 4294967296.0f + (float)(uint32_t)(tf & 0xffffffffu);
+    t_sum = t_fix_f * (1.0f / kFix) + d_M * (float)n_valid;
+    so = so_d + n_skin;
+    float D;
+    if (so == 0) {
+        D = lambda;
+    } else {
+        const float fa = (float)sa, fo = (float)so;
+        D = t_sum / fo + lambda * (1.f - 2.f * fa / (fa + fo));
+    }
+    return D + lambda_k * kcp;
+}
+
 // Add one contributor's sums to particle p's workspace and take an exit ticket;
 // the last of `contributors` forms E (Eq. 4-5) and clears the workspace.
 __device__ __forceinline__ void flush_and_finish(const RenderArgs& a, int p, HsParticleWork* wk,
@@ -200,19 +313,9 @@ __device__ __forceinline__ void flush_and_finish(const RenderArgs& a, int p, HsP
     const long long tf = (long long)atomicAdd(&wk->t_fix, 0ull);
     const uint32_t sa = atomicAdd(&wk->n_and, 0u), so_d = atomicAdd(&wk->n_or, 0u);
     const uint32_t sh = atomicAdd(&wk->n_hit, 0u);
-    const uint32_t n_valid = stats[0], n_skin = stats[1];
-    // fixed point -> float from the two 32-bit halves (no 64-bit conversion)
-    const float t_fix_f = (float)(int)(tf >> 32) * 4294967296.0f + (float)(uint32_t)(tf & 0xffffffffu);
-    const float t_sum = t_fix_f * (1.0f / kFix) + a.d_M * (float)n_valid;
-    const uint32_t so = so_d + n_skin;
-    float D;
-    if (so == 0) {
-        D = a.lambda;
-    } else {
-        const float fa = (float)sa, fo = (float)so;
-        D = t_sum / fo + a.lambda * (1.f - 2.f * fa / (fa + fo));
-    }
-    a.E[p] = D + a.lambda_k * kcp;
+    float t_sum;
+    uint32_t so;
+    a.E[p] = form_E(tf, sa, so_d, stats, a.d_M, a.lambda, a.lambda_k, kcp, t_sum, so);
     if (a.parts) a.parts[p] = HsParts{t_sum, sa, so, sh};
     *wk = HsParticleWork{};  // every contributor is done: safe to clear
 }

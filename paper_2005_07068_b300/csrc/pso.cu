@@ -10,13 +10,10 @@
 #include <cfloat>
 #include <climits>
 
-#include "hs_fk.cuh"
+#include "hs_step.cuh"
 
 namespace hs {
 
-constexpr int kInitBlocks = (kNdof + 3) / 4;     // Philox blocks per particle for 26 dims
-constexpr int kPairBlocks = (2 * kNdof + 3) / 4; // for r1/r2 of 26 dims
-constexpr int kMutBlocks = (kNdof - 6 + 3) / 4;  // for the 20 finger dims
 constexpr int kPsoThreads = 512;
 
 __global__ void __launch_bounds__(256) pso_init_kernel(const __grid_constant__ Limits lim, const PsoInitArgs a)
@@ -54,15 +51,6 @@ __global__ void __launch_bounds__(256) pso_init_kernel(const __grid_constant__ L
         a.pbest_E[i] = INFINITY;
         if (li == 0) a.gbest_E[s] = INFINITY;
     }
-}
-
-// (E_j, j) ranks before (E_i, i); NaN ranks after every number
-__device__ __forceinline__ bool ranks_before(float ej, int j, float ei, int i)
-{
-    const bool nj = isnan(ej), ni = isnan(ei);
-    if (nj != ni) return ni;
-    if (!nj && ej != ei) return ej < ei;
-    return j < i;
 }
 
 __global__ void __launch_bounds__(kPsoThreads) pso_step_kernel(const __grid_constant__ Limits lim, const PsoStepArgs a)
@@ -190,7 +178,7 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
     __shared__ float red_v[2];
     __shared__ int red_i[2], red_r[2];
     extern __shared__ float s_e[];  // E [P] then pbest_E [P] of this particle's swarm
-    const int q = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int q = blockIdx.x, t = threadIdx.x;
     // the swarm of particle q: particles [off, off + P), q is number i of them
     int off = 0, P = a.P, n_mutate = a.n_mutate, s = 0;
     uint32_t k0 = a.key0, k1 = a.key1;
@@ -211,20 +199,7 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
     fk_load_model(sh, model_param);
     // this particle's random numbers depend only on (particle, generation, frame, seed):
     // draw them while the previous kernel finishes
-    if (t < kPairBlocks) {
-        const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamPso << 16) | (uint32_t)t, a.gen, a.frame}, k0, k1);
-        s_r[4 * t] = u01(r.x);
-        s_r[4 * t + 1] = u01(r.y);
-        s_r[4 * t + 2] = u01(r.z);
-        s_r[4 * t + 3] = u01(r.w);
-    } else if (t >= 32 && t < 32 + kMutBlocks) {
-        const int b = t - 32;
-        const U4 r = philox4x32_10(U4{(uint32_t)i, (kStreamMutate << 16) | (uint32_t)b, a.gen, a.frame}, k0, k1);
-        s_m[4 * b] = u01(r.x);
-        s_m[4 * b + 1] = u01(r.y);
-        s_m[4 * b + 2] = u01(r.z);
-        s_m[4 * b + 3] = u01(r.w);
-    }
+    draw_step_randoms(i, a.gen, a.frame, k0, k1, s_r, s_m, t);
     pdl_wait();  // E comes from the previous kernel
     float xi = 0.f, pbi = 0.f, vi = 0.f;
     if (t < kNdof) {  // this particle's own state, loaded before the global best is known
@@ -237,70 +212,10 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
         s_pe[j] = a.pbest_E[off + j];
     }
     __syncthreads();
-    // global best = argmin_j min(E_j, pbest_E_j) (lowest index on ties, NaN never
-    // wins) and this particle's rank by E
-    const float ei = s_e[i];
-    float bv = INFINITY;
-    int bi = INT_MAX, rank = 0;
-    for (int j = t; j < P; j += 64) {
-        const float ej = s_e[j], pj = s_pe[j];
-        const float pe = ej < pj ? ej : pj;
-        if (bi == INT_MAX || pe < bv) {
-            bv = pe;
-            bi = j;
-        }
-        if (a.mutate) rank += ranks_before(ej, j, ei, i);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (oi != INT_MAX && (bi == INT_MAX || ov < bv || (ov == bv && oi < bi))) {
-            bv = ov;
-            bi = oi;
-        }
-        rank += __shfl_xor_sync(0xffffffffu, rank, o);
-    }
-    if (lane == 0) {
-        red_v[warp] = bv;
-        red_i[warp] = bi;
-        red_r[warp] = rank;
-    }
-    __syncthreads();
-    int g = red_i[0];
-    float gE = red_v[0];
-    if (red_i[1] != INT_MAX && (g == INT_MAX || red_v[1] < gE || (red_v[1] == gE && red_i[1] < g))) {
-        g = red_i[1];
-        gE = red_v[1];
-    }
-    rank = red_r[0] + red_r[1];
-    const bool imp = ei < s_pe[i];  // strict improvement of this particle's personal best
-    const bool mutated = a.mutate && rank >= P - n_mutate;
-    if (t < kNdof) {
-        // the global best's position: its current x if that is its personal best now
-        const bool gimp = s_e[g] <= s_pe[g];
-        const float gv = gimp ? a.x[(size_t)(off + g) * kNdof + t] : a.pbest[(size_t)(off + g) * kNdof + t];
-        if (i == 0) a.gbest[(size_t)s * kNdof + t] = gv;
-        const float pb = imp ? xi : pbi;
-        if (imp) a.pbest[(size_t)q * kNdof + t] = xi;
-        // Eq. 6-7 for dimension t (r1 = number 2t, r2 = number 2t+1), then clamp;
-        // the mutation re-draws a finger dimension and zeroes its velocity
-        float acc = fmaf(a.c1 * s_r[2 * t], pb - xi, vi);
-        acc = fmaf(a.c2 * s_r[2 * t + 1], gv - xi, acc);
-        float vn = a.w * acc;
-        float xn = fminf(fmaxf(xi + vn, sh.model.lo[t]), sh.model.hi[t]);
-        if (mutated && t >= 6) {
-            xn = fmaf(s_m[t - 6], sh.model.hi[t] - sh.model.lo[t], sh.model.lo[t]);
-            vn = 0.f;
-        }
-        a.v[(size_t)q * kNdof + t] = vn;
-        a.x_next[(size_t)q * kNdof + t] = xn;
-        s_xn[t] = xn;
-    }
-    if (t == 0) {
-        if (imp) a.pbest_E[q] = ei;
-        if (i == 0) a.gbest_E[s] = gE;
-    }
+    const SwarmRefs R{a.x, a.x_next, a.v, a.pbest, a.pbest_E, a.gbest, a.gbest_E, a.c1, a.c2, a.w, a.mutate};
+    const StepOut o = swarm_update<64>(R, q, i, off, P, s, n_mutate, s_e, s_pe, s_r, s_m, sh.model.lo, sh.model.hi,
+                                       xi, pbi, vi, s_pe[i], true, red_v, red_i, red_r);
+    if (t < kNdof) s_xn[t] = o.xn;
     // FK of the new pose (fk_particle starts with a barrier that publishes s_xn)
     fk_particle(sh, s_xn, cam, a.prims + (size_t)q * sh.model.n_prims * 4, a.kc + q, a.status);
 }

@@ -11,7 +11,8 @@
 //    exact rectangle box ∩ tile; the rectangles are cut into 32-pixel chunks
 //    and the warps deal the chunks round-robin, so each lane tests exactly one
 //    pixel of one primitive per step (pixel-exact culling, the primitive's
-//    record held in registers while its chunks last);
+//    raster record held in registers while its chunks last): the discriminant
+//    polynomial decides coverage, the roots are solved only on a hit;
 //  * hits go to a z-buffer in shared memory as 64-bit keys with atomicMin: the
 //    depth z = t0 + s rounded to float in the high word (nearest surface wins),
 //    and in the low word the exact rounding residual dz = s - (z - t0), so
@@ -34,8 +35,9 @@ constexpr int kMaxDevices = 64;
 template <int TW, int TH>
 struct TileLayout {
     static constexpr int kBoxes = (TW / 16) * (TH / 4);  // 16 x 4 TMA boxes per tile
-    static constexpr int kPrims = 0;                      // float4 [kMaxPrims][4]
-    static constexpr int kZ = kPrims + kMaxPrims * 64;    // u64 [TH][TW]
+    static constexpr int kRast = 0;                       // float4 [kMaxPrims][5]: raster records
+    static constexpr int kPBox = kRast + kMaxPrims * 80;  // int2 [kMaxPrims]: packed pixel boxes
+    static constexpr int kZ = kPBox + kMaxPrims * 8;      // u64 [TH][TW]
     static constexpr int kDepth = kZ + TW * TH * 8;       // box b at b * 256 (16 x 4 x <= 4 bytes)
     static constexpr int kSkin = kDepth + kBoxes * 256;   // box b at b * 128 (16 x 4 bytes)
     static constexpr int kRect = kSkin + kBoxes * 128;    // int4 [kMaxPrims]: x0, y0, w, pixels
@@ -58,7 +60,8 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
 {
     using Lay = TileLayout<TW, TH>;
     extern __shared__ __align__(128) unsigned char smem[];
-    float4* s_prims = reinterpret_cast<float4*>(smem + Lay::kPrims);
+    float4* s_rast = reinterpret_cast<float4*>(smem + Lay::kRast);
+    int2* s_pbox = reinterpret_cast<int2*>(smem + Lay::kPBox);
     unsigned long long* s_z = reinterpret_cast<unsigned long long*>(smem + Lay::kZ);
     unsigned char* s_depth = smem + Lay::kDepth;
     unsigned char* s_skin = smem + Lay::kSkin;
@@ -82,7 +85,17 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
     pdl_wait();  // the primitive records and kc come from the previous kernel
     const int n_prims = a.n_prims;
     const float4* src = a.prims + (size_t)p * n_prims * 4;
-    for (int i = tid; i < n_prims * 4; i += NW * 32) s_prims[i] = src[i];
+    for (int j = tid; j < n_prims; j += NW * 32) {  // raster form of each primitive, once per CTA
+        const RasterPrim R = make_raster(src + 4 * j, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y);
+        float4* d = s_rast + 5 * j;
+        d[0] = R.q0;
+        d[1] = R.q1;
+        d[2] = R.q2;
+        d[3] = R.q3;
+        d[4] = R.q4;
+        const float4 r3 = src[4 * j + 3];
+        s_pbox[j] = make_int2(__float_as_int(r3.z), __float_as_int(r3.w));
+    }
     if (warp == 0) {  // the particle's screen box, clipped to the ROI
         int u0 = INT_MAX, v0 = INT_MAX, u1 = INT_MIN, v1 = INT_MIN;
         for (int i = lane; i < n_prims; i += 32) {
@@ -151,10 +164,11 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
                 const int j = lane + 32 * h;
                 int rx0 = 0, ry0 = 0, rw = 0, n = 0;
                 if (j < n_prims) {
-                    const float4 r3 = s_prims[4 * j + 3];
-                    rx0 = max(lo_i16(r3.z), tx0);
-                    ry0 = max(hi_i16(r3.z), ty0);
-                    const int rx1 = min(lo_i16(r3.w), cx1), ry1 = min(hi_i16(r3.w), cy1);
+                    const int2 bx = s_pbox[j];
+                    rx0 = max(lo_i16(__int_as_float(bx.x)), tx0);
+                    ry0 = max(hi_i16(__int_as_float(bx.x)), ty0);
+                    const int rx1 = min(lo_i16(__int_as_float(bx.y)), cx1);
+                    const int ry1 = min(hi_i16(__int_as_float(bx.y)), cy1);
                     if (rx1 >= rx0 && ry1 >= ry0) {
                         rw = rx1 - rx0 + 1;
                         n = rw * (ry1 - ry0 + 1);
@@ -200,19 +214,19 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
             const int4 rc = s_rect[k];
             const uint32_t mg = s_magic[k];
             const int c0 = s_pre[k], c1 = s_pre[k + 1];
-            const float4 r0 = s_prims[4 * j], r1 = s_prims[4 * j + 1], r2 = s_prims[4 * j + 2],
-                         r3 = s_prims[4 * j + 3];
+            const float4 q0 = s_rast[5 * j], q1 = s_rast[5 * j + 1], q2 = s_rast[5 * j + 2],
+                         q3 = s_rast[5 * j + 3], q4 = s_rast[5 * j + 4];
             for (; c < c1; c += NW) {
                 const int idx = ((c - c0) << 5) + lane;
                 if (idx < rc.w) {
                     const int y = (int)(((unsigned long long)(uint32_t)idx * mg) >> 31);
                     const int px = rc.x + idx - y * rc.z, py = rc.y + y;
-                    const float ra = fmaf((float)px, pv.inv_fx, pv.off_x);
-                    const float rb = fmaf((float)py, pv.inv_fy, pv.off_y);
-                    const float sh = intersect(r0, r1, r2, r3, ra, rb);
-                    const float zz = r2.w + sh;
+                    const float du = (float)px - q0.x, dv = (float)py - q0.y;
+                    const float disc = raster_disc(q0, q1, du, dv);
+                    const float sh = raster_maybe(q4, disc) ? raster_hit(q2, q3, q4, du, dv, disc) : INFINITY;
+                    const float zz = q2.w + sh;
                     if (zz < INFINITY) {
-                        const float dz = sh - (zz - r2.w);  // z - t0 is exact (Sterbenz): dz is the residual
+                        const float dz = sh - (zz - q2.w);  // z - t0 is exact (Sterbenz): dz is the residual
                         atomicMin(&s_z[(py - ty0) * TW + (px - tx0)],
                                   ((unsigned long long)__float_as_uint(zz) << 32) | __float_as_uint(dz));
                     }

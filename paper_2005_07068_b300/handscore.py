@@ -139,10 +139,17 @@ _SIGS = {
                         _vp], ctypes.c_int),
     "pso_step_fk_multi": ([_vp, _vp, ctypes.POINTER(HsSwarm), _vp, ctypes.POINTER(HsPsoParams), ctypes.c_uint32,
                            ctypes.c_uint32, _vp, _vp, _vp], ctypes.c_int),
+    "hs_frame_workspace_size": ([ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "hs_frame_capacity": ([ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "track_frame": ([_vp, ctypes.POINTER(HsObs), ctypes.POINTER(HsCamera), ctypes.POINTER(HsSwarm), _vp, ctypes.c_int,
+                     ctypes.c_int, ctypes.POINTER(HsScoreParams), ctypes.POINTER(HsPsoParams), _vp,
+                     ctypes.POINTER(ctypes.c_float), ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, _vp,
+                     ctypes.c_size_t, _vp, _vp, _vp], ctypes.c_int),
 }
 NOALLOC_SCRATCH_BYTES = 256 * 1024
 MAX_PARTICLES = 65535
 FUSED_MAX_PARTICLES = 4096
+FRAME_MAX_PARTICLES = 1024
 
 _LIB = None
 
@@ -388,6 +395,38 @@ def pso_step_fk(model: Model, sw: Swarm, x_next: torch.Tensor, params: HsPsoPara
     _check("pso_step_fk", lib().pso_step_fk(model.handle, ctypes.byref(st), _ptr(x_next), sw.P, ctypes.byref(params),
                                             ctypes.c_uint64(seed), frame, gen, ctypes.byref(cam), _ptr(prims),
                                             _ptr(kc), _stream(stream)))
+
+
+# ---- a whole tracking frame in one launch ---------------------------------------------
+
+def new_frame_workspace(P: int, device="cuda") -> torch.Tensor:
+    """Zeroed workspace of track_frame for P particles (every call leaves it zeroed)."""
+    n = ctypes.c_size_t()
+    _check("hs_frame_workspace_size", lib().hs_frame_workspace_size(P, ctypes.byref(n)))
+    return torch.zeros((n.value + 15) // 16 * 4, dtype=torch.int32, device=device)
+
+
+def frame_capacity() -> int:
+    """CTAs of track_frame the current device keeps resident at once."""
+    n = ctypes.c_int()
+    _check("hs_frame_capacity", lib().hs_frame_capacity(ctypes.byref(n)))
+    return n.value
+
+
+def track_frame(model: Model, obs: Obs, cam: HsCamera, sw: Swarm, x_next: torch.Tensor, gens: int,
+                score: HsScoreParams, pso: HsPsoParams, seed_pose: torch.Tensor, scale, seed: int, frame: int,
+                ctas_per_particle: int, ws: torch.Tensor, kc: torch.Tensor, prims: torch.Tensor | None = None,
+                stream=None) -> None:
+    """One whole frame (obs totals, init around seed_pose, gens x (score, step)) in
+    one cooperative launch; identical to the step-by-step calls.  Generation g
+    writes positions to (sw.x, x_next)[g & 1]."""
+    st = sw.struct()
+    sc = (ctypes.c_float * NDOF)(*[float(v) for v in np.asarray(scale, np.float32)])
+    _check("track_frame", lib().track_frame(model.handle, ctypes.byref(obs.struct()), ctypes.byref(cam),
+                                            ctypes.byref(st), _ptr(x_next), sw.P, gens, ctypes.byref(score),
+                                            ctypes.byref(pso), _ptr(seed_pose), sc, ctypes.c_uint64(seed), frame,
+                                            ctas_per_particle, _ptr(ws), ws.numel() * ws.element_size(),
+                                            _ptr(prims), _ptr(kc), _stream(stream)))
 
 
 # ---- the smoothed objective E_s and its gradient ------------------------------------

@@ -136,6 +136,66 @@ class Tracker:
         out_host[26:].copy_(self.swarm.gbest_E, non_blocking=True)
 
 
+class FrameTracker(Tracker):
+    """Plain PSO tracking with each frame in ONE cooperative launch (track_frame):
+    C CTAs per particle stay resident for the whole frame, keep the particle's
+    records and state on chip and meet at one grid barrier per generation.
+    Bit for bit the same swarm as Tracker (same observation, camera, P, seed);
+    no CUDA graph is needed, a frame is a single launch."""
+
+    def __init__(self, model: hs.Model, cam: hs.HsCamera, P: int = 64, gens: int = 40, *, ctas_per_particle: int = 0,
+                 **kw):
+        super().__init__(model, cam, P, gens, **kw)
+        if P > hs.FRAME_MAX_PARTICLES:
+            raise ValueError(f"track_frame takes at most {hs.FRAME_MAX_PARTICLES} particles")
+        self.ctas = ctas_per_particle
+        self.fws = hs.new_frame_workspace(P, self.device)
+
+    def enqueue_frame(self, obs: hs.Obs, frame: int, seed_pose: torch.Tensor | None = None) -> None:
+        src = self.swarm.gbest if seed_pose is None else seed_pose
+        self.seed_pose.copy_(src)
+        x0, x1 = self.x_buf
+        self.swarm.x = x0
+        hs.track_frame(self.model, obs, self.cam, self.swarm, x1, self.gens, self.score, self.pso, self.seed_pose,
+                       self.scale, self.seed, frame, self.ctas, self.fws, self.kc, self.prims)
+        self.swarm.x = self.x_buf[self.gens & 1]
+
+    def run_frame(self, obs: hs.Obs, frame: int, seed_pose: torch.Tensor | None = None, graph: bool = True) -> None:
+        self.enqueue_frame(obs, frame, seed_pose)
+
+    def candidates(self) -> list[int]:
+        """CTAs per particle that fit on the device at this P."""
+        cap = hs.frame_capacity()
+        return [c for c in (1, 2, 3, 4, 6, 8) if self.P * c <= cap]
+
+    def autotune(self, obs: hs.Obs, seed_pose: torch.Tensor, reps: int = 5) -> dict:
+        """Pick the fastest CTAs-per-particle for this workload (whole frames from
+        seed_pose, timed with CUDA events) and use it from now on; returns the
+        timing table (us per frame).  Leaves the tracker's state as it was."""
+        saved = [t.clone() for t in self._state()]
+        keep = self.ctas
+        table = {}
+        for c in self.candidates():
+            self.ctas = c
+            self.enqueue_frame(obs, 0, seed_pose)  # warm
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record()
+            for _ in range(reps):
+                self.enqueue_frame(obs, 0, seed_pose)
+            t1.record()
+            t1.synchronize()
+            table[f"frame/c{c}"] = 1e3 * t0.elapsed_time(t1) / reps
+        self.ctas = min(self.candidates(), key=lambda c: table[f"frame/c{c}"]) if table else keep
+        for t, v in zip(self._state(), saved):
+            t.copy_(v)
+        self.swarm.x = self.x_buf[0]
+        return table
+
+    def launches_per_frame(self) -> int:
+        """One cooperative launch per frame (plus the reset of the observation totals)."""
+        return 1
+
+
 class HybridTracker(Tracker):
     """Plain PSO plus, every generation, a gradient polish of the k best
     particles: `steps` normalised descent steps on the smoothed objective E_s

@@ -164,10 +164,23 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
     bool alive = true;
     for (int g = 1; g <= a.gens; ++g) {
         draw_step_randoms(p, (uint32_t)g, a.frame, a.key0, a.key1, sh.r, sh.m, t);
-        // FK of the current pose (fk_particle starts with a barrier that publishes sh.x)
-        fk_particle(sh.fk, sh.x, a.cam, sh.rec, &sh.kc, a.status);
+        // FK of the current pose (fk_particle starts with a barrier that publishes
+        // sh.x); each record's raster form is made by the thread that formed it
+        fk_particle(sh.fk, sh.x, a.cam, sh.rec, &sh.kc, a.status, [&](int j, const float* rec) {
+            const float4 r4[4] = {make_float4(rec[0], rec[1], rec[2], rec[3]),
+                                  make_float4(rec[4], rec[5], rec[6], rec[7]),
+                                  make_float4(rec[8], rec[9], rec[10], rec[11]),
+                                  make_float4(rec[12], rec[13], rec[14], rec[15])};
+            const RasterPrim R = make_raster(r4, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y);
+            float4* d = sh.rast + 5 * j;
+            d[0] = R.q0;
+            d[1] = R.q1;
+            d[2] = R.q2;
+            d[3] = R.q3;
+            d[4] = R.q4;
+            sh.pbox[j] = make_int2(__float_as_int(rec[14]), __float_as_int(rec[15]));
+        });
         __syncthreads();
-        stage_prims(sh.rec, n_prims, pv, sh.rast, sh.pbox, t, kFrameThreads);
         if (warp == 0) unit_box(sh.rec, n_prims, a.W, a.H, lane, sh.box);
         __syncthreads();
         long long acc_t = 0;

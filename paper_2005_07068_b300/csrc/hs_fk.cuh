@@ -18,6 +18,7 @@ namespace hs {
 struct FkShared {
     DevModel model;
     float q[kNdof];
+    float sn[kNdof], cs[kNdof];  // sin and cos of the clamped angles
     float lR[kMaxBones][9];
     float bR[kMaxBones][9];
     float bP[kMaxBones][3];
@@ -90,8 +91,14 @@ __device__ __forceinline__ bool ellipse_ray_bounds(const float C[3], const float
 }
 
 // thread of the 64-thread CTA must call it (it synchronises the CTA).
+// emit(j, rec) is called by the thread that formed primitive j's record
+// (float[16], as stored), e.g. to derive more from it while it is in registers.
+struct NoEmit {
+    __device__ void operator()(int, const float*) const {}
+};
+template <class Emit = NoEmit>
 __device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, float4 cam, float4* prims, float* kc,
-                                            uint32_t* status)
+                                            uint32_t* status, const Emit& emit = Emit())
 {
     const DevModel& model = sh.model;
     float* q = sh.q;
@@ -105,7 +112,9 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, flo
     if (t < kNdof) {
         float v = pose[t];
         if (!isfinite(v)) atomicOr(&bad, 1);
-        q[t] = fminf(fmaxf(v, model.lo[t]), model.hi[t]);
+        const float qc = fminf(fmaxf(v, model.lo[t]), model.hi[t]);
+        q[t] = qc;
+        if (t >= 3) sincosf(qc, &sh.sn[t], &sh.cs[t]);  // every angle at once
     }
     __syncthreads();
 
@@ -114,10 +123,7 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, flo
         float R[9];
         if (t == 0) {
             // palm: diag(1,-1,-1) * Rz(q5) Ry(q4) Rx(q3)
-            float sx, cx, sy, cy, sz, cz;
-            sincosf(q[3], &sx, &cx);
-            sincosf(q[4], &sy, &cy);
-            sincosf(q[5], &sz, &cz);
+            const float sx = sh.sn[3], cx = sh.cs[3], sy = sh.sn[4], cy = sh.cs[4], sz = sh.sn[5], cz = sh.cs[5];
             const float Rz[9] = {cz, -sz, 0.f, sz, cz, 0.f, 0.f, 0.f, 1.f};
             const float Ry[9] = {cy, 0.f, sy, 0.f, 1.f, 0.f, -sy, 0.f, cy};
             const float Rx[9] = {1.f, 0.f, 0.f, 0.f, cx, -sx, 0.f, sx, cx};
@@ -129,8 +135,14 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, flo
         } else {
             const DevBone& B = model.bones[t];
             float sz = 0.f, cz = 1.f, sx = 0.f, cx = 1.f;
-            if (B.dof_z >= 0) sincosf(q[B.dof_z], &sz, &cz);
-            if (B.dof_x >= 0) sincosf(q[B.dof_x], &sx, &cx);
+            if (B.dof_z >= 0) {
+                sz = sh.sn[B.dof_z];
+                cz = sh.cs[B.dof_z];
+            }
+            if (B.dof_x >= 0) {
+                sx = sh.sn[B.dof_x];
+                cx = sh.cs[B.dof_x];
+            }
             const float ZX[9] = {cz, -sz * cx, sz * sx, sz, cz * cx, -cz * sx, 0.f, sx, cx};  // Rz Rx
             mat3_mul(B.rest, ZX, R);
         }
@@ -138,28 +150,36 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, flo
         for (int k = 0; k < 9; ++k) lR[t][k] = R[k];
     }
     __syncthreads();
-    if (t == 0) {
+    // global frame of each bone: one thread per bone walks its chain down from
+    // the root, G_k = G_{k-1} lR[a_k] and P_k = G_{k-1} off[a_k] + P_{k-1}, the
+    // same products in the same order as composing level by level, without a
+    // barrier per level (positions relative to the wrist; its translation is
+    // added once per primitive)
+    if (t < model.n_bones) {
+        float G[9], P[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < 9; ++k) bR[0][k] = lR[0][k];
-        bP[0][0] = 0.f;  // positions relative to the wrist; its translation is added once per primitive
-        bP[0][1] = 0.f;
-        bP[0][2] = 0.f;
-    }
-    __syncthreads();
-    for (int lvl = 1; lvl <= model.max_depth; ++lvl) {
-        if (t < model.n_bones && t > 0 && model.bones[t].depth == lvl) {
-            const DevBone& B = model.bones[t];
-            const float* Rp = bR[B.parent];
-            float R[9];
-            mat3_mul(Rp, lR[t], R);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) bR[t][k] = R[k];
+        for (int k = 0; k < 9; ++k) G[k] = lR[0][k];
+        const int d = model.bones[t].depth;
+        for (int k = 1; k <= d; ++k) {
+            int a = t;  // the ancestor of t at depth k
+            while (model.bones[a].depth > k) a = model.bones[a].parent;
+            const DevBone& B = model.bones[a];
+            float Pn[3], Gn[9];
 #pragma unroll
             for (int i = 0; i < 3; ++i)
-                bP[t][i] = fmaf(Rp[3 * i], B.off[0], fmaf(Rp[3 * i + 1], B.off[1], fmaf(Rp[3 * i + 2], B.off[2], bP[B.parent][i])));
+                Pn[i] = fmaf(G[3 * i], B.off[0], fmaf(G[3 * i + 1], B.off[1], fmaf(G[3 * i + 2], B.off[2], P[i])));
+            mat3_mul(G, lR[a], Gn);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) P[i] = Pn[i];
+#pragma unroll
+            for (int k2 = 0; k2 < 9; ++k2) G[k2] = Gn[k2];
         }
-        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 9; ++k) bR[t][k] = G[k];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) bP[t][i] = P[i];
     }
+    __syncthreads();
 
     // intersection-ready primitive records
     if (t < model.n_prims) {
@@ -238,6 +258,7 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, flo
         dst[1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
         dst[2] = make_float4(rec[8], rec[9], rec[10], rec[11]);
         dst[3] = make_float4(rec[12], rec[13], rec[14], rec[15]);
+        emit(t, rec);
     }
     if (t == 32) {
         // kc(h): pairs (index, middle), (middle, ring), (ring, pinky) of MP_z

@@ -187,6 +187,38 @@ typedef struct {
     int32_t n_mutate;
 } HsPsoParams;
 
+/* ---- kc variants (Section III.A, after Eq. 5) -----------------------------
+ * The paper adds lambda_k kc(h) to E to rule out implausible poses such as
+ * two fingers passing through each other, with kc the sum over the three
+ * adjacent pairs of non-thumb fingers of -min(phi, 0), phi the abduction
+ * difference of the pair (rad).  That only orders the abduction angles; the
+ * variants below add a direct test of interpenetration between fingers:
+ *   pen(h) = sum over pairs of collision proxies on different fingers of
+ *            max(0, r_i + r_j - |c_i - c_j|)   (mm)
+ * with the proxies the inscribed spheres of the model: one per ellipsoid
+ * primitive (centre, smallest semi-axis) and three per cone primitive, on its
+ * axis at y = -hl/2, 0, +hl/2, each the largest sphere about that point inside
+ * the cone of circular section rho (1 + kappa y / hl), rho = min(ax, az):
+ * radius min(rho (1 + kappa y / hl) / sqrt(1 + (rho kappa / hl)^2), hl - |y|).  A
+ * primitive's finger is the child of the palm bone (bone 0) on its bone's
+ * path to the palm; palm primitives (bone 0) take no part, nor do pairs of
+ * two proxies centred at the origins of bones attached to the palm (knuckle
+ * spheres: their distance is a constant of the model).  kc is then
+ *   HS_KC_ABDUCTION : the paper's kc (default)
+ *   HS_KC_ABD_PEN   : the paper's kc + pen_weight * pen
+ *   HS_KC_PEN       : pen_weight * pen
+ * (pen_weight in rad per mm, so that lambda_k applies to both).  pose_fk,
+ * pso_step_fk, track_frame and the batch calls return this kc; pose_grad
+ * implements only HS_KC_ABDUCTION (HS_ERR_NOT_IMPL otherwise). */
+#define HS_KC_ABDUCTION 0
+#define HS_KC_ABD_PEN   1
+#define HS_KC_PEN       2
+#define HS_MAX_PROXIES  128
+typedef struct {
+    int32_t variant;    /* HS_KC_* */
+    float pen_weight;   /* rad per mm of penetration, >= 0 */
+} HsKcParams;
+
 /* ---- calls ------------------------------------------------------------------ */
 
 /* library version (major * 10000 + minor * 100 + patch) */
@@ -201,6 +233,10 @@ const char* hs_status_string(int status);
  * lo > hi), HS_ERR_SIZE (counts out of range). */
 int hs_model_create(const HsModelDesc* desc, HsModel** out);
 int hs_model_destroy(HsModel* model);
+/* Select the kc variant of a model (see HsKcParams).  Errors: HS_ERR_ARG (NULL,
+ * unknown variant, pen_weight negative or not finite), HS_ERR_SIZE (the model
+ * has more than HS_MAX_PROXIES collision proxies and a variant needs them). */
+int hs_model_set_kc(HsModel* model, const HsKcParams* kc);
 
 /* Bytes of workspace render_score_batch needs for P particles (32 bytes per
  * particle: a work-queue ticket, an exit count and fixed-point sums).  The

@@ -144,6 +144,7 @@ using namespace hs;
 struct HsModel {
     DevModel dev;
     Limits lim;
+    int proxies;  // collision proxies the model has (dev holds at most kMaxProxies of them)
 };
 
 struct HsBatch {
@@ -286,7 +287,52 @@ int hs_model_create(const HsModelDesc* d, HsModel** out)
             if (covered) c.caps &= ~(1 << side);
         }
     }
+    // collision proxies of the interpenetration test (inscribed spheres), and
+    // the finger of each bone: the palm's child on its path to the palm
+    int finger[HS_MAX_BONES];
+    int n_fingers = 0;
+    finger[0] = -1;
+    for (int b = 1; b < d->n_bones; ++b) finger[b] = d->bones[b].parent == 0 ? n_fingers++ : finger[d->bones[b].parent];
+    int np = 0;
+    auto add_proxy = [&](int bone, float x, float y, float z, float r) {
+        const int fixed = bone > 0 && d->bones[bone].parent == 0 && x == 0.f && y == 0.f && z == 0.f;
+        if (np < kMaxProxies) dm.proxies[np] = DevProxy{{x, y, z}, r, bone, finger[bone], fixed};
+        ++np;
+    };
+    for (int k = 0; k < d->n_prims; ++k) {
+        const HsPrimDesc& P = d->prims[k];
+        if (P.kind == HS_PRIM_ELLIPSOID) {
+            add_proxy(P.bone, P.center[0], P.center[1], P.center[2],
+                      std::min(P.dims[0], std::min(P.dims[1], P.dims[2])));
+        } else {  // on the axis (local y) at -hl/2, 0, +hl/2: the largest sphere
+                  // inside the circular cone of section rho (1 + kappa y / hl) there
+            const double hl = P.dims[2], rho = std::min(P.dims[0], P.dims[1]), kap = P.dims[3];
+            for (int i = -1; i <= 1; ++i) {
+                const double y = 0.5 * i * hl;
+                const double side = rho * (1.0 + kap * y / hl) / std::sqrt(1.0 + (rho * kap / hl) * (rho * kap / hl));
+                add_proxy(P.bone, P.center[0], P.center[1] + (float)y, P.center[2],
+                          (float)std::min(side, hl - std::fabs(y)));
+            }
+        }
+    }
+    m->proxies = np;
+    dm.n_proxies = 0;  // the paper's kc needs none
+    dm.kc_variant = HS_KC_ABDUCTION;
+    dm.pen_weight = 0.f;
     *out = m;
+    return HS_OK;
+}
+
+int hs_model_set_kc(HsModel* model, const HsKcParams* kc)
+{
+    if (!model || !kc) return HS_ERR_ARG;
+    if (kc->variant != HS_KC_ABDUCTION && kc->variant != HS_KC_ABD_PEN && kc->variant != HS_KC_PEN) return HS_ERR_ARG;
+    if (!std::isfinite(kc->pen_weight) || kc->pen_weight < 0.f) return HS_ERR_ARG;
+    const bool pen = kc->variant != HS_KC_ABDUCTION;
+    if (pen && model->proxies > kMaxProxies) return HS_ERR_SIZE;
+    model->dev.kc_variant = kc->variant;
+    model->dev.pen_weight = kc->pen_weight;
+    model->dev.n_proxies = pen ? model->proxies : 0;
     return HS_OK;
 }
 
@@ -687,6 +733,7 @@ int pose_grad(const HsModel* model, const float* poses, int P, const HsCamera* c
               HsPrim* prims, float* kc, int64_t* adj, float* grad, hs_stream_t stream)
 {
     if (!model || !poses || !params || !prims || !kc || !adj || !grad) return HS_ERR_ARG;
+    if (model->dev.kc_variant != HS_KC_ABDUCTION) return HS_ERR_NOT_IMPL;  // the penetration term has no adjoint here
     int rc = validate_cam(cam);
     if (rc) return rc;
     if ((rc = validate_score_params(params))) return rc;

@@ -30,12 +30,25 @@ struct DevPrimDesc {
     int32_t caps;    // cone caps to render: bit 0 at y = -hl, bit 1 at y = +hl
 };
 
-// everything the FK kernel needs about the model (about 4.7 KB)
+// a collision proxy of the interpenetration test: an inscribed sphere of a
+// primitive, centre in its bone's frame
+struct DevProxy {
+    float local[3];
+    float radius;
+    int32_t bone, finger;  // finger: the palm's child bone on the path to the palm (numbered), -1 on the palm
+    int32_t fixed;         // centred at the origin of a bone attached to the palm: never moves relative to it
+};
+constexpr int kMaxProxies = HS_MAX_PROXIES;
+
+// everything the FK kernel needs about the model (about 7.8 KB)
 struct DevModel {
     int32_t n_bones, n_prims, max_depth, pad;
+    int32_t kc_variant, n_proxies;  // HS_KC_*; proxies used by the penetration test
+    float pen_weight, pad2;
     float lo[kNdof], hi[kNdof];
-    DevPrimDesc prims[kMaxPrims];  // kernels copy the used prefix of prims and of bones
+    DevPrimDesc prims[kMaxPrims];  // kernels copy the used prefix of prims, bones and proxies
     DevBone bones[kMaxBones];
+    DevProxy proxies[kMaxProxies];
 };
 
 struct Limits {

@@ -15,8 +15,12 @@
 
 namespace hs {
 
+constexpr float kPenFix = 1048576.0f;  // fixed-point scale of the penetration sum (2^20 per mm)
+
 struct FkShared {
     DevModel model;
+    float4 pc[kMaxProxies];          // collision proxies relative to the wrist: centre, radius
+    unsigned long long pen_fix;      // their penetration sum, fixed point
     float q[kNdof];
     float sn[kNdof], cs[kNdof];  // sin and cos of the clamped angles
     float lR[kMaxBones][9];
@@ -52,6 +56,9 @@ __device__ __forceinline__ void fk_load_model(FkShared& sh, const DevModel& mp)
     const int bone_words = mp.n_bones * (int)(sizeof(DevBone) / 4);
     for (int i = threadIdx.x; i < prim_end; i += blockDim.x) dstw[i] = srcw[i];
     for (int i = threadIdx.x; i < bone_words; i += blockDim.x) dstw[bones0 + i] = srcw[bones0 + i];
+    constexpr int prox0 = (int)(offsetof(DevModel, proxies) / 4);
+    const int prox_words = mp.n_proxies * (int)(sizeof(DevProxy) / 4);
+    for (int i = threadIdx.x; i < prox_words; i += blockDim.x) dstw[prox0 + i] = srcw[prox0 + i];
 }
 
 // FK of the raw pose `pose` [26] (global or shared memory): writes the particle's
@@ -260,9 +267,45 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, flo
         dst[3] = make_float4(rec[12], rec[13], rec[14], rec[15]);
         emit(t, rec);
     }
+    if (model.kc_variant != HS_KC_ABDUCTION) {  // (uniform over the CTA)
+        // interpenetration of different fingers: the collision proxies relative to
+        // the wrist (distances do not see its translation), then every pair of
+        // proxies on different fingers, summed in fixed point (order-independent)
+        const int n = model.n_proxies;
+        for (int i = t; i < n; i += blockDim.x) {
+            const DevProxy& X = model.proxies[i];
+            const float* R = bR[X.bone];
+            const float* O = bP[X.bone];
+            float c[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                c[k] = fmaf(R[3 * k], X.local[0], fmaf(R[3 * k + 1], X.local[1], fmaf(R[3 * k + 2], X.local[2], O[k])));
+            sh.pc[i] = make_float4(c[0], c[1], c[2], X.radius);
+        }
+        if (t == 0) sh.pen_fix = 0ull;
+        __syncthreads();
+        unsigned long long acc = 0ull;
+        for (int k = t; k < n * n; k += blockDim.x) {
+            const int i = k / n, j = k - i * n;
+            if (j <= i) continue;
+            const DevProxy &Xi = model.proxies[i], &Xj = model.proxies[j];
+            if (Xi.finger < 0 || Xj.finger < 0 || Xi.finger == Xj.finger || (Xi.fixed && Xj.fixed)) continue;
+            const float4 a = sh.pc[i], b = sh.pc[j];
+            const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+            const float pen = (a.w + b.w) - sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            if (pen > 0.f) acc += (unsigned long long)__float2ll_rn(pen * kPenFix);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((t & 31) == 0 && acc) atomicAdd(&sh.pen_fix, acc);
+        __syncthreads();
+    }
     if (t == 32) {
         // kc(h): pairs (index, middle), (middle, ring), (ring, pinky) of MP_z
-        const float k = fmaxf(q[15] - q[11], 0.f) + fmaxf(q[19] - q[15], 0.f) + fmaxf(q[23] - q[19], 0.f);
+        float k = fmaxf(q[15] - q[11], 0.f) + fmaxf(q[19] - q[15], 0.f) + fmaxf(q[23] - q[19], 0.f);
+        if (model.kc_variant == HS_KC_PEN) k = 0.f;
+        if (model.kc_variant != HS_KC_ABDUCTION)
+            k = fmaf(model.pen_weight, __ull2float_rn(sh.pen_fix) * (1.f / kPenFix), k);
         *kc = bad ? __int_as_float(0x7fc00000) : k;
         if (bad) set_status(status, HS_DEV_NONFINITE_POSE);
     }

@@ -18,7 +18,9 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhandscore.so")
 
 HS_OK, HS_ERR_ARG, HS_ERR_ALIGN, HS_ERR_SIZE, HS_ERR_TIMEOUT, HS_ERR_NOT_IMPL, HS_ERR_CUDA = 0, -1, -2, -3, -4, -5, -6
-HS_DEV_NONFINITE_POSE, HS_DEV_TMA_TIMEOUT = 0x1, 0x2
+HS_DEV_NONFINITE_POSE, HS_DEV_TMA_TIMEOUT, HS_DEV_BARRIER_TIMEOUT = 0x1, 0x2, 0x4
+HS_KC_ABDUCTION, HS_KC_ABD_PEN, HS_KC_PEN = 0, 1, 2
+MAX_PROXIES = 128
 HS_PRIM_ELLIPSOID, HS_PRIM_ECONE = 0, 1
 HS_DEPTH_U16, HS_DEPTH_F32 = 0, 1
 NDOF = 26
@@ -38,6 +40,10 @@ class HsModelDesc(ctypes.Structure):
     _fields_ = [("n_bones", ctypes.c_int32), ("n_prims", ctypes.c_int32),
                 ("bones", ctypes.POINTER(HsBoneDesc)), ("prims", ctypes.POINTER(HsPrimDesc)),
                 ("lo", ctypes.c_float * NDOF), ("hi", ctypes.c_float * NDOF)]
+
+
+class HsKcParams(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("pen_weight", ctypes.c_float)]
 
 
 class HsCamera(ctypes.Structure):
@@ -90,6 +96,7 @@ _SIGS = {
     "hs_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "hs_model_create": ([ctypes.POINTER(HsModelDesc), ctypes.POINTER(_vp)], ctypes.c_int),
     "hs_model_destroy": ([_vp], ctypes.c_int),
+    "hs_model_set_kc": ([_vp, ctypes.POINTER(HsKcParams)], ctypes.c_int),
     "hs_workspace_size": ([ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "hs_workspace_reset": ([_vp, ctypes.c_size_t, _vp], ctypes.c_int),
     "hs_obs_prepare": ([ctypes.POINTER(HsObs), _vp], ctypes.c_int),
@@ -230,6 +237,14 @@ class Model:
     @classmethod
     def from_geometry(cls, g, lo, hi) -> "Model":
         return cls(g.bones_i, g.bones_f, g.prims_i, g.prims_f, lo, hi)
+
+    def set_kc(self, variant: int = HS_KC_ABDUCTION, pen_weight: float = 0.0) -> "Model":
+        """Select the kc variant: the paper's abduction ordering, that plus
+        pen_weight x the interpenetration of different fingers (mm), or the
+        interpenetration term alone."""
+        _check("hs_model_set_kc", lib().hs_model_set_kc(self.handle, ctypes.byref(HsKcParams(variant, pen_weight))))
+        self.kc_variant, self.pen_weight = variant, pen_weight
+        return self
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -516,6 +531,14 @@ class Batch:
         self.P = [int(p) for p in P]
         self.offsets = np.concatenate([[0], np.cumsum(self.P)]).astype(np.int64)
         self.P_total = int(self.offsets[-1])
+
+    def set_kc(self, variant: int = HS_KC_ABDUCTION, pen_weight: float = 0.0) -> "Model":
+        """Select the kc variant: the paper's abduction ordering, that plus
+        pen_weight x the interpenetration of different fingers (mm), or the
+        interpenetration term alone."""
+        _check("hs_model_set_kc", lib().hs_model_set_kc(self.handle, ctypes.byref(HsKcParams(variant, pen_weight))))
+        self.kc_variant, self.pen_weight = variant, pen_weight
+        return self
 
     def __del__(self):
         h = getattr(self, "handle", None)

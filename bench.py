@@ -37,10 +37,13 @@ METRIC = "hypothesis evals/s (render+cost, 320x240 ROI)"
 WORKLOAD = ("Kinect-scale tracking: 320x240 uint16 depth + uint8 skin frames (600 mm plane, N(0,3 mm) noise, "
             "5% holes, 2% skin flips), 64 particles x 40 generations per frame, 30-frame seeded trajectory")
 FP32_LANES_PER_SM = 128
-# FP32 operations per ray-primitive test on the miss path, tallied from
-# render_score.cu (an FMA counts 2): ray point and direction in scaled local
-# coordinates (25), quadric coefficients and discriminant (ellipsoid 20,
-# cone 24 + cap planes 28 + 1 compare)
+# Algorithmic FP32 operations per ray-primitive test (a pixel inside a
+# primitive's exact box), the fixed tally of the textbook per-pixel test (an
+# FMA counts 2): ray point and direction in the primitive's scaled local
+# coordinates (25), quadric coefficients and discriminant (ellipsoid 20;
+# cone 24 + cap planes 28 + 1 compare).  The kernels decide coverage with
+# fewer operations (the discriminant as a polynomial in the pixel offsets);
+# the tally stays the unit of work, so a faster kernel reads higher.
 FLOP_PER_TEST = {0: 45, 1: 78}
 
 
@@ -62,6 +65,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample")
     ap.add_argument("--profile", action="store_true", help="short run for an ncu launch list")
     ap.add_argument("--no-roofline", action="store_true", help="skip the render roofline replay")
+    ap.add_argument("--no-frame-path", action="store_true",
+                    help="skip the second measurement through track_frame (one launch per frame)")
     ap.add_argument("--render", default="tune", help="render kernel: tune (timed on the workload first), auto, "
                     "units, tiles32x16, tiles32x32, tiles64x32, tiles64x64")
     ap.add_argument("--ctas", type=int, default=0, help="render CTAs per particle (0 = automatic)")
@@ -87,11 +92,11 @@ def measured_peaks():
 CSRC = os.path.join(ROOT, "paper_2005_07068_b300", "csrc")
 # the render kernels' sources, and the committed ncu summary taken on them
 KERNEL_SOURCES = {
-    "units": ["render_score.cu", "hs_render.cuh", "hs_args.cuh", "hs_device.cuh"],
+    "units": ["render_score.cu", "hs_units.cuh", "hs_render.cuh", "hs_args.cuh", "hs_device.cuh"],
     "tiles": ["render_tiles.cu", "hs_render.cuh", "hs_args.cuh", "hs_device.cuh"],
 }
 PROFILE_FILES = {("kinect", "units"): "render_units_kinect_320x240.txt",
-                 ("batch", "tiles"): "render_tiles64x32_batch_64seq.txt"}
+                 ("batch", "tiles"): "render_tiles32x32_batch_64seq.txt"}
 
 
 def source_sha256(kind: str) -> str:
@@ -107,7 +112,7 @@ def profile_traffic(workload: str, kernel: str):
     render kernel, if it was taken on the kernel's current source; else None."""
     kind = "units" if kernel == "units" else "tiles"
     name = PROFILE_FILES.get((workload, kind))
-    if name is None or (kind == "tiles" and kernel != "tiles64x32"):
+    if name is None:
         return None
     try:
         kv = {}
@@ -116,7 +121,7 @@ def profile_traffic(workload: str, kernel: str):
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("source_sha256") != source_sha256(kind):
+        if kv.get("source_sha256") != source_sha256(kind) or kv.get("kernel") != kernel:
             return None
         return float(kv["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -742,6 +747,41 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in evs]
     value, t_dev, evals_total = R.aggregate(sum(step_ms) / 1e3, K * PARTICLES * GENS, dev)
 
+    # ---- the same frames, one cooperative launch per frame (track_frame) ----
+    # The frame kernel keeps every particle's records and state on chip and
+    # meets at one grid barrier per generation; it moves the swarm exactly as
+    # the graph does.  Timed the same way (L2 flushed between steps).
+    frame_path = None
+    if not args.no_frame_path:
+        from paper_2005_07068_b300.tracker import FrameTracker
+        ft = FrameTracker(model, cam, PARTICLES, GENS, seed=seed, device=dev, score=trk.score)
+        ftab = ft.autotune(obs[0], gt0)
+
+        def fstep(i):
+            f = i % frames
+            ft.run_frame(obs[f], f, gt0 if f == 0 else None)
+
+        for i in range(args.warmup):
+            fstep(i)
+        torch.cuda.synchronize(dev)
+        fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        with ClockSampler(local) as fclk:
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            for i in range(K):
+                flush.zero_()
+                fev[i][0].record(stream)
+                fstep(args.warmup + i)
+                fev[i][1].record(stream)
+            torch.cuda.synchronize(dev)
+        f_value, f_t, _ = R.aggregate(sum(a.elapsed_time(b) for a, b in fev) / 1e3, K * PARTICLES * GENS, dev)
+        fc = fclk.summary(peaks.get("sm_max_mhz", 2032.0))
+        frame_path = {"value": f_value, "unit": "evals/s", "ms_per_step": 1e3 * f_t / K,
+                      "kernel": "track_frame_kernel: one cooperative launch per frame",
+                      "ctas_per_particle": ft.ctas, "autotune_us_per_frame": ftab, "gpu_launches": K,
+                      "clocks": {"sm_mhz": fc["sm_mhz"], "reasons": fc["reasons"]}}
+
     # ---- roofline of render_score_batch ----
     # The timed frames are replayed generation by generation: the primitive
     # records and kc that each generation's render_score_batch consumed are
@@ -863,7 +903,7 @@ def main():
                            "render": {"kernel": hs.render_variant(trk.score, PARTICLES),
                                       "ctas_per_particle": trk.score.ctas_per_particle, "autotune_us": tune}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
-                "gpu_launches": K * trk.launches_per_frame()}
+                "gpu_launches": K * trk.launches_per_frame(), "frame_path": frame_path}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -76,6 +76,12 @@ def parse():
     ap.add_argument("--particles", default="256,1024,4096", help="fullframe: swarm sizes")
     ap.add_argument("--frames", type=int, default=100, help="fullframe: frames of the sequence")
     ap.add_argument("--gens", default="5,10,20,50", help="fullframe: generation budgets per frame")
+    ap.add_argument("--roi", default="640,480", help="fullframe: ROI W,H (the Kinect camera scaled to it)")
+    ap.add_argument("--methods", default="plain,hybrid",
+                    help="fullframe: plain (PSO) and/or hybrid (PSO + gradient polish of the k best particles)")
+    ap.add_argument("--polish", default="8,5", help="fullframe: hybrid polish: particles k, descent steps")
+    ap.add_argument("--kc", default="0,0", help="fullframe: kc variant and penetration weight (rad/mm): 0 = the "
+                    "paper's, 1 = plus the interpenetration of different fingers, 2 = interpenetration only")
     return ap.parse_args()
 
 
@@ -539,11 +545,11 @@ def run_batch(args, rank, world, local):
 
 # ---- full frames: seconds per frame to <= 5 degrees -----------------------------------------
 
-FULL_W, FULL_H, FULL_GENS = 640, 480, 50
-FULL_METRIC = "s/frame to track within 5 deg mean joint error (640x480, plain PSO)"
-FULL_WORKLOAD = ("full-frame tracking: 640x480 uint16 depth + uint8 skin (Kinect noise recipe), seeded 100-frame "
+FULL_GENS = 50
+FULL_METRIC = "s/frame to track within 5 deg mean joint error"
+FULL_WORKLOAD = ("full-frame tracking: {W}x{H} uint16 depth + uint8 skin (Kinect noise recipe), seeded {F}-frame "
                  "trajectory (<= 5 deg / 5 mm per frame), frame 0 from the ground truth perturbed by U[+-10 deg, "
-                 "+-10 mm], swarm sizes 256 / 1024 / 4096 x generation budgets 5 / 10 / 20 / 50 per frame")
+                 "+-10 mm], methods {M} x swarm sizes {P} x generation budgets {G} per frame")
 
 
 def replay_render_us(dev, renders, reps: int = 3) -> float:
@@ -577,7 +583,7 @@ def run_fullframe(args, rank, world, local):
     from paper_2005_07068_b300 import inputs as I
     from paper_2005_07068_b300 import replicas as R
     from paper_2005_07068_b300 import sweep as SW
-    from paper_2005_07068_b300.tracker import Tracker
+    from paper_2005_07068_b300.tracker import HybridTracker, Tracker
 
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
@@ -586,9 +592,20 @@ def run_fullframe(args, rank, world, local):
     dev = torch.device("cuda", local)
     peaks = measured_peaks()
     seed = R.replica_seed(I.CONFIG_SEED_BASE + 5, rank)
+    FULL_W, FULL_H = (int(v) for v in args.roi.split(","))
+    methods = [m for m in args.methods.split(",") if m]
+    if any(m not in ("plain", "hybrid") for m in methods):
+        raise SystemExit("--methods takes plain and/or hybrid")
+    k_pol, steps_pol = (int(v) for v in args.polish.split(","))
+    kc_var, kc_w = args.kc.split(",")
+    kc_var, kc_w = int(kc_var), float(kc_w)
     g = I.hand_geometry()
     lo, hi = (a.astype(np.float32) for a in I.search_limits())
     model = hs.Model.from_geometry(g, lo, hi)
+    if kc_var != hs.HS_KC_ABDUCTION:
+        model.set_kc(kc_var, kc_w)
+        if "hybrid" in methods:
+            raise SystemExit("the hybrid polish needs the paper's kc (the penetration term has no gradient)")
     camt = I.kinect_camera(FULL_W, FULL_H)
     cam = hs.camera(camt.fx, camt.fy, camt.cx, camt.cy)
     frames = max(2, args.frames)
@@ -611,14 +628,20 @@ def run_fullframe(args, rank, world, local):
                 tune = tuner.autotune(obs[0], start)
                 score = tuner.score
                 del tuner
-            for G in gen_budgets:
-                trk = Tracker(model, cam, P, G, seed=seed, device=dev, score=score)
-                results = SW.track_sequence(trk, obs, traj, start, frames=frames)
-                summ = SW.summarize(results)
-                summ.update({"particles": P, "generations": G,
-                             "evals_per_s": P * G * frames / (sum(r.frame_ms for r in results) * 1e-3)})
-                settings.append(summ)
-                del trk
+            for method in methods:
+                for G in gen_budgets:
+                    if method == "plain":
+                        trk = Tracker(model, cam, P, G, seed=seed, device=dev, score=score)
+                    else:
+                        trk = HybridTracker(model, cam, P, G, seed=seed, device=dev, score=score,
+                                            k=min(k_pol, P), steps=steps_pol)
+                    results = SW.track_sequence(trk, obs, traj, start, frames=frames)
+                    summ = SW.summarize(results)
+                    summ.update({"method": method, "particles": P, "generations": G,
+                                 "evals_per_s": P * G * frames / (sum(r.frame_ms for r in results) * 1e-3),
+                                 "launches_per_frame": trk.launches_per_frame()})
+                    settings.append(summ)
+                    del trk
             # render roofline at this P: the launches of frame 0 (50 generations) replayed back to back
             trk = Tracker(model, cam, P, FULL_GENS, seed=seed, device=dev, score=score)
             hist_p = torch.zeros(FULL_GENS, P, model.n_prims, 16, device=dev)
@@ -658,17 +681,22 @@ def run_fullframe(args, rank, world, local):
     clocks = clk.summary(peaks.get("sm_max_mhz", 2032.0))
     best = SW.fastest_within(settings, 0.9)
     if rank == 0:
-        line = {"metric": FULL_METRIC, "value": best["frame_ms_mean"] * 1e-3 if best else None,
+        work = FULL_WORKLOAD.format(W=FULL_W, H=FULL_H, F=frames, M=" / ".join(methods), P=args.particles,
+                                    G=args.gens)
+        line = {"metric": f"{FULL_METRIC} ({FULL_W}x{FULL_H})", "value": best["frame_ms_mean"] * 1e-3 if best else None,
                 "unit": "s/frame", "n_gpus": world, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": FULL_WORKLOAD, "roi": [FULL_W, FULL_H], "frames": frames, "threshold_deg": 5.0,
+                "config": {"workload": work, "roi": [FULL_W, FULL_H], "frames": frames, "threshold_deg": 5.0,
+                           "kc": {"variant": kc_var, "pen_weight_rad_per_mm": kc_w},
+                           "polish": {"k": k_pol, "steps": steps_pol} if "hybrid" in methods else None,
                            "criterion": ">= 90 % of frames end within 5 deg mean joint error (23 angular DOFs)",
-                           "value_from": (f"{best['particles']} particles x {best['generations']} generations"
-                                          if best else "no setting tracked within 5 deg on 90 % of frames"),
+                           "value_from": (f"{best['method']}: {best['particles']} particles x {best['generations']} "
+                                          f"generations" if best else
+                                          "no setting tracked within 5 deg on 90 % of frames"),
                            "timing": "CUDA events around each frame's graph (observation totals, init, FK, "
                                      "G x (render, fused step))"},
                 "settings": settings, "per_swarm_size": per_p, "clocks": clocks,
-                "gpu_launches": sum((3 + 2 * s_["generations"]) * s_["frames"] for s_ in settings)}
+                "gpu_launches": sum(s_["launches_per_frame"] * s_["frames"] for s_ in settings)}
         print(json.dumps(line), flush=True)
     return 0
 

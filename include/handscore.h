@@ -214,6 +214,7 @@ typedef struct {
 #define HS_KC_ABD_PEN   1
 #define HS_KC_PEN       2
 #define HS_MAX_PROXIES  128
+#define HS_MAX_PROXY_PAIRS 2048
 typedef struct {
     int32_t variant;    /* HS_KC_* */
     float pen_weight;   /* rad per mm of penetration, >= 0 */
@@ -234,8 +235,9 @@ const char* hs_status_string(int status);
 int hs_model_create(const HsModelDesc* desc, HsModel** out);
 int hs_model_destroy(HsModel* model);
 /* Select the kc variant of a model (see HsKcParams).  Errors: HS_ERR_ARG (NULL,
- * unknown variant, pen_weight negative or not finite), HS_ERR_SIZE (the model
- * has more than HS_MAX_PROXIES collision proxies and a variant needs them). */
+ * unknown variant, pen_weight negative or not finite), HS_ERR_SIZE (a variant
+ * needs the proxies and the model has more than HS_MAX_PROXIES of them or more
+ * than HS_MAX_PROXY_PAIRS pairs to test). */
 int hs_model_set_kc(HsModel* model, const HsKcParams* kc);
 
 /* Bytes of workspace render_score_batch needs for P particles (32 bytes per

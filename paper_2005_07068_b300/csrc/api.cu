@@ -145,6 +145,7 @@ struct HsModel {
     DevModel dev;
     Limits lim;
     int proxies;  // collision proxies the model has (dev holds at most kMaxProxies of them)
+    int pairs;    // and pairs of them the penetration test visits (dev holds at most kMaxPairs)
 };
 
 struct HsBatch {
@@ -316,7 +317,18 @@ int hs_model_create(const HsModelDesc* d, HsModel** out)
         }
     }
     m->proxies = np;
+    // the pairs the test visits: different fingers, not both fixed to the palm
+    int npairs = 0;
+    for (int i = 0; i < std::min(np, kMaxProxies); ++i)
+        for (int j = i + 1; j < std::min(np, kMaxProxies); ++j) {
+            const DevProxy &a = dm.proxies[i], &b = dm.proxies[j];
+            if (a.finger < 0 || b.finger < 0 || a.finger == b.finger || (a.fixed && b.fixed)) continue;
+            if (npairs < kMaxPairs) dm.pairs[npairs] = (uint16_t)(i | (j << 8));
+            ++npairs;
+        }
+    m->pairs = npairs;
     dm.n_proxies = 0;  // the paper's kc needs none
+    dm.n_pairs = 0;
     dm.kc_variant = HS_KC_ABDUCTION;
     dm.pen_weight = 0.f;
     *out = m;
@@ -329,10 +341,11 @@ int hs_model_set_kc(HsModel* model, const HsKcParams* kc)
     if (kc->variant != HS_KC_ABDUCTION && kc->variant != HS_KC_ABD_PEN && kc->variant != HS_KC_PEN) return HS_ERR_ARG;
     if (!std::isfinite(kc->pen_weight) || kc->pen_weight < 0.f) return HS_ERR_ARG;
     const bool pen = kc->variant != HS_KC_ABDUCTION;
-    if (pen && model->proxies > kMaxProxies) return HS_ERR_SIZE;
+    if (pen && (model->proxies > kMaxProxies || model->pairs > kMaxPairs)) return HS_ERR_SIZE;
     model->dev.kc_variant = kc->variant;
     model->dev.pen_weight = kc->pen_weight;
     model->dev.n_proxies = pen ? model->proxies : 0;
+    model->dev.n_pairs = pen ? model->pairs : 0;
     return HS_OK;
 }
 

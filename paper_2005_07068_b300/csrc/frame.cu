@@ -25,6 +25,8 @@
 // because every piece of arithmetic is the same code.  The barrier's wait is
 // bounded: if it runs out, HS_DEV_BARRIER_TIMEOUT is set and the CTAs leave.
 // The last CTA to leave returns the workspace to zero for the next frame.
+#include <atomic>
+
 #include "hs_step.cuh"
 #include "hs_units.cuh"
 
@@ -288,10 +290,19 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
     }
 }
 
+// the dynamic shared memory of the largest swarm (2 P floats) on top of the
+// static part passes the default 48 KB: opt in once per device
+static std::atomic<uint32_t> g_frame_opted[64];
+static cudaError_t frame_smem_opt_in()
+{
+    return opt_in_dynamic_smem(track_frame_kernel, 2 * HS_FRAME_MAX_PARTICLES * (int)sizeof(float), g_frame_opted);
+}
+
 cudaError_t track_frame_capacity(int* ctas)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = frame_smem_opt_in();
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // the dynamic part (2 P floats) is small next to the static part; size it for the largest P
     if (e == cudaSuccess)
@@ -304,6 +315,8 @@ cudaError_t track_frame_capacity(int* ctas)
 cudaError_t launch_track_frame(const DevModel& model, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,
                                const FrameArgs& args, cudaStream_t stream)
 {
+    const cudaError_t e = frame_smem_opt_in();
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(args.P * args.C);
     cfg.blockDim = dim3(kFrameThreads);

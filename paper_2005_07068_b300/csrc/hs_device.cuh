@@ -4,6 +4,7 @@
 // parameter in the constant bank), so the library keeps no device copy of it.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -39,16 +40,19 @@ struct DevProxy {
     int32_t fixed;         // centred at the origin of a bone attached to the palm: never moves relative to it
 };
 constexpr int kMaxProxies = HS_MAX_PROXIES;
+constexpr int kMaxPairs = HS_MAX_PROXY_PAIRS;
 
 // everything the FK kernel needs about the model (about 7.8 KB)
 struct DevModel {
     int32_t n_bones, n_prims, max_depth, pad;
     int32_t kc_variant, n_proxies;  // HS_KC_*; proxies used by the penetration test
-    float pen_weight, pad2;
+    float pen_weight;
+    int32_t n_pairs;                // the pairs of proxies it tests (on different fingers, not both fixed)
     float lo[kNdof], hi[kNdof];
     DevPrimDesc prims[kMaxPrims];  // kernels copy the used prefix of prims, bones and proxies
     DevBone bones[kMaxBones];
     DevProxy proxies[kMaxProxies];
+    uint16_t pairs[kMaxPairs];      // proxy i in the low byte, j in the high byte
 };
 
 struct Limits {
@@ -100,6 +104,22 @@ __device__ __forceinline__ float sqrt_approx(float x)
 // visible (both are no-ops when the launch was not programmatic)
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Let `kernel` take up to `bytes` of dynamic shared memory on the current device
+// (the default limit is 48 KB with the static part).  Once per (call site,
+// device); safe from several host threads.
+template <class Kernel>
+inline cudaError_t opt_in_dynamic_smem(Kernel kernel, int bytes, std::atomic<uint32_t> (&done)[64])
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done[dev].store(1u, std::memory_order_release);
+    return e;
+}
 
 __device__ __forceinline__ void set_status(uint32_t* status, uint32_t bit)
 {

@@ -59,6 +59,9 @@ __device__ __forceinline__ void fk_load_model(FkShared& sh, const DevModel& mp)
     constexpr int prox0 = (int)(offsetof(DevModel, proxies) / 4);
     const int prox_words = mp.n_proxies * (int)(sizeof(DevProxy) / 4);
     for (int i = threadIdx.x; i < prox_words; i += blockDim.x) dstw[prox0 + i] = srcw[prox0 + i];
+    constexpr int pairs0 = (int)(offsetof(DevModel, pairs) / 4);
+    const int pair_words = (mp.n_pairs + 1) / 2;
+    for (int i = threadIdx.x; i < pair_words; i += blockDim.x) dstw[pairs0 + i] = srcw[pairs0 + i];
 }
 
 // FK of the raw pose `pose` [26] (global or shared memory): writes the particle's
@@ -285,15 +288,15 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, flo
         if (t == 0) sh.pen_fix = 0ull;
         __syncthreads();
         unsigned long long acc = 0ull;
-        for (int k = t; k < n * n; k += blockDim.x) {
-            const int i = k / n, j = k - i * n;
-            if (j <= i) continue;
-            const DevProxy &Xi = model.proxies[i], &Xj = model.proxies[j];
-            if (Xi.finger < 0 || Xj.finger < 0 || Xi.finger == Xj.finger || (Xi.fixed && Xj.fixed)) continue;
-            const float4 a = sh.pc[i], b = sh.pc[j];
+        for (int k = t; k < model.n_pairs; k += blockDim.x) {  // the host listed the pairs to visit
+            const uint32_t ij = model.pairs[k];
+            const float4 a = sh.pc[ij & 0xffu], b = sh.pc[ij >> 8];
             const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-            const float pen = (a.w + b.w) - sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-            if (pen > 0.f) acc += (unsigned long long)__float2ll_rn(pen * kPenFix);
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)), rr = a.w + b.w;
+            if (d2 < rr * rr) {  // (the root only for the pairs that touch)
+                const float pen = rr - sqrtf(d2);
+                if (pen > 0.f) acc += (unsigned long long)__float2ll_rn(pen * kPenFix);
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

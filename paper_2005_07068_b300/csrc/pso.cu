@@ -222,6 +222,9 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
 
 cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cudaStream_t stream)
 {
+    static std::atomic<uint32_t> opted[64];
+    const cudaError_t e = opt_in_dynamic_smem(pso_step_fk_kernel, 2 * HS_FUSED_MAX_PARTICLES * (int)sizeof(float), opted);
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     // one CTA per particle (all swarms of a batch); shared memory for the largest swarm
     cfg.gridDim = dim3(args.batch.views ? args.batch.P_total : args.P);

@@ -806,6 +806,9 @@ cudaError_t launch_soft(bool backward, const SoftArgs& args, cudaStream_t stream
 cudaError_t launch_pose_grad(const DevModel& model, const GradArgs& args, cudaStream_t stream)
 {
     const size_t smem = ((size_t)kNdof * model.n_bones * 12 + (size_t)model.n_prims * kNdof) * sizeof(float);
+    static std::atomic<uint32_t> opted[64];
+    const cudaError_t e = opt_in_dynamic_smem(pose_grad_kernel, (kNdof * kMaxBones * 12 + kMaxPrims * kNdof) * 4, opted);
+    if (e != cudaSuccess) return e;
     pose_grad_kernel<<<args.P, 64, smem, stream>>>(model, args);
     return cudaGetLastError();
 }

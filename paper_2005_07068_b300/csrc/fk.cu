@@ -4,7 +4,10 @@
 
 namespace hs {
 
-__global__ void __launch_bounds__(64) fk_kernel(const __grid_constant__ DevModel model_param, const FkArgs a)
+// M: DevModelCore for the paper's kc (a smaller launch parameter), DevModel
+// when a kc variant needs the collision data
+template <class M>
+__global__ void __launch_bounds__(64) fk_kernel(const __grid_constant__ M model_param, const FkArgs a)
 {
     __shared__ FkShared sh;
     fk_load_model(sh, model_param);
@@ -14,13 +17,16 @@ __global__ void __launch_bounds__(64) fk_kernel(const __grid_constant__ DevModel
         const SwarmView& v = a.batch.views[a.batch.sid[p]];
         cam = make_float4(v.fx, v.fy, v.cx, v.cy);
     }
-    fk_particle(sh, a.poses + (size_t)p * kNdof, cam, a.prims + (size_t)p * model_param.n_prims * 4, a.kc + p,
+    fk_particle(sh, collide_data(model_param), a.poses + (size_t)p * kNdof, cam, a.prims + (size_t)p * model_param.n_prims * 4, a.kc + p,
                 a.status);
 }
 
 cudaError_t launch_fk(const DevModel& model, const FkArgs& args, cudaStream_t stream)
 {
-    fk_kernel<<<args.P, 64, 0, stream>>>(model, args);
+    if (model.kc_variant == HS_KC_ABDUCTION)
+        fk_kernel<DevModelCore><<<args.P, 64, 0, stream>>>(static_cast<const DevModelCore&>(model), args);
+    else
+        fk_kernel<DevModel><<<args.P, 64, 0, stream>>>(model, args);
     return cudaGetLastError();
 }
 

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
         draw_step_randoms(p, (uint32_t)g, a.frame, a.key0, a.key1, sh.r, sh.m, t);
         // FK of the current pose (fk_particle starts with a barrier that publishes
         // sh.x); each record's raster form is made by the thread that formed it
-        fk_particle(sh.fk, sh.x, a.cam, sh.rec, &sh.kc, a.status, [&](int j, const float* rec) {
+        fk_particle(sh.fk, &model, sh.x, a.cam, sh.rec, &sh.kc, a.status, [&](int j, const float* rec) {
             const float4 r4[4] = {make_float4(rec[0], rec[1], rec[2], rec[3]),
                                   make_float4(rec[4], rec[5], rec[6], rec[7]),
                                   make_float4(rec[8], rec[9], rec[10], rec[11]),
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
     }
     if (alive) {
         // the records and kc of the final positions
-        fk_particle(sh.fk, sh.x, a.cam, sh.rec, &sh.kc, a.status);
+        fk_particle(sh.fk, &model, sh.x, a.cam, sh.rec, &sh.kc, a.status);
         __syncthreads();
         if (primary) {
             if (a.prims_out)

@@ -42,15 +42,21 @@ struct DevProxy {
 constexpr int kMaxProxies = HS_MAX_PROXIES;
 constexpr int kMaxPairs = HS_MAX_PROXY_PAIRS;
 
-// everything the FK kernel needs about the model (about 7.8 KB)
-struct DevModel {
+// what every FK kernel copies to shared memory: header, limits, primitives, bones (about 5.6 KB)
+struct DevModelCore {
     int32_t n_bones, n_prims, max_depth, pad;
     int32_t kc_variant, n_proxies;  // HS_KC_*; proxies used by the penetration test
     float pen_weight;
     int32_t n_pairs;                // the pairs of proxies it tests (on different fingers, not both fixed)
     float lo[kNdof], hi[kNdof];
-    DevPrimDesc prims[kMaxPrims];  // kernels copy the used prefix of prims, bones and proxies
+    DevPrimDesc prims[kMaxPrims];  // kernels copy the used prefix of prims and bones
     DevBone bones[kMaxBones];
+};
+
+// everything the FK kernels need about the model; it travels by value as a
+// launch parameter, and the collision data of the penetration test stays
+// there (read only when a kc variant needs it)
+struct DevModel : DevModelCore {
     DevProxy proxies[kMaxProxies];
     uint16_t pairs[kMaxPairs];      // proxy i in the low byte, j in the high byte
 };

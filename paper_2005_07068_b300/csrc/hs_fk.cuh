@@ -18,7 +18,7 @@ namespace hs {
 constexpr float kPenFix = 1048576.0f;  // fixed-point scale of the penetration sum (2^20 per mm)
 
 struct FkShared {
-    DevModel model;
+    DevModelCore model;
     float4 pc[kMaxProxies];          // collision proxies relative to the wrist: centre, radius
     unsigned long long pen_fix;      // their penetration sum, fixed point
     float q[kNdof];
@@ -45,23 +45,17 @@ __device__ __forceinline__ int clamp_i16(float v)
 
 // one coalesced copy of the model (a by-value launch parameter) into shared
 // memory; later accesses use thread-dependent bone / primitive indices
-__device__ __forceinline__ void fk_load_model(FkShared& sh, const DevModel& mp)
+__device__ __forceinline__ void fk_load_model(FkShared& sh, const DevModelCore& mp)
 {
     // only the used part: header and limits, then the n_prims primitives and n_bones bones
     const uint32_t* srcw = reinterpret_cast<const uint32_t*>(&mp);
     uint32_t* dstw = reinterpret_cast<uint32_t*>(&sh.model);
-    constexpr int head = (int)(offsetof(DevModel, prims) / 4);
+    constexpr int head = (int)(offsetof(DevModelCore, prims) / 4);
     const int prim_end = head + mp.n_prims * (int)(sizeof(DevPrimDesc) / 4);
-    constexpr int bones0 = (int)(offsetof(DevModel, bones) / 4);
+    constexpr int bones0 = (int)(offsetof(DevModelCore, bones) / 4);
     const int bone_words = mp.n_bones * (int)(sizeof(DevBone) / 4);
     for (int i = threadIdx.x; i < prim_end; i += blockDim.x) dstw[i] = srcw[i];
     for (int i = threadIdx.x; i < bone_words; i += blockDim.x) dstw[bones0 + i] = srcw[bones0 + i];
-    constexpr int prox0 = (int)(offsetof(DevModel, proxies) / 4);
-    const int prox_words = mp.n_proxies * (int)(sizeof(DevProxy) / 4);
-    for (int i = threadIdx.x; i < prox_words; i += blockDim.x) dstw[prox0 + i] = srcw[prox0 + i];
-    constexpr int pairs0 = (int)(offsetof(DevModel, pairs) / 4);
-    const int pair_words = (mp.n_pairs + 1) / 2;
-    for (int i = threadIdx.x; i < pair_words; i += blockDim.x) dstw[pairs0 + i] = srcw[pairs0 + i];
 }
 
 // FK of the raw pose `pose` [26] (global or shared memory): writes the particle's
@@ -106,11 +100,19 @@ __device__ __forceinline__ bool ellipse_ray_bounds(const float C[3], const float
 struct NoEmit {
     __device__ void operator()(int, const float*) const {}
 };
+
+// the collision data of a kernel's model parameter: the model itself when the
+// kernel was given the whole model, nullptr when it was given only the core
+__device__ __forceinline__ const DevModel* collide_data(const DevModel& m) { return &m; }
+__device__ __forceinline__ const DevModel* collide_data(const DevModelCore&) { return nullptr; }
+// mp: the whole model as passed to the kernel, whose collision data the kc
+// variants read; kernels launched only for the paper's kc take the smaller
+// DevModelCore and pass nullptr (collide_data below).
 template <class Emit = NoEmit>
-__device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, float4 cam, float4* prims, float* kc,
-                                            uint32_t* status, const Emit& emit = Emit())
+__device__ __forceinline__ void fk_particle(FkShared& sh, const DevModel* mp, const float* pose, float4 cam,
+                                            float4* prims, float* kc, uint32_t* status, const Emit& emit = Emit())
 {
-    const DevModel& model = sh.model;
+    const DevModelCore& model = sh.model;
     float* q = sh.q;
     float(*lR)[9] = sh.lR;
     float(*bR)[9] = sh.bR;
@@ -270,13 +272,13 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, flo
         dst[3] = make_float4(rec[12], rec[13], rec[14], rec[15]);
         emit(t, rec);
     }
-    if (model.kc_variant != HS_KC_ABDUCTION) {  // (uniform over the CTA)
+    if (model.kc_variant != HS_KC_ABDUCTION && mp) {  // (uniform over the CTA)
         // interpenetration of different fingers: the collision proxies relative to
         // the wrist (distances do not see its translation), then every pair of
         // proxies on different fingers, summed in fixed point (order-independent)
         const int n = model.n_proxies;
         for (int i = t; i < n; i += blockDim.x) {
-            const DevProxy& X = model.proxies[i];
+            const DevProxy& X = mp->proxies[i];
             const float* R = bR[X.bone];
             const float* O = bP[X.bone];
             float c[3];
@@ -289,7 +291,7 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const float* pose, flo
         __syncthreads();
         unsigned long long acc = 0ull;
         for (int k = t; k < model.n_pairs; k += blockDim.x) {  // the host listed the pairs to visit
-            const uint32_t ij = model.pairs[k];
+            const uint32_t ij = mp->pairs[k];
             const float4 a = sh.pc[ij & 0xffu], b = sh.pc[ij >> 8];
             const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
             const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)), rr = a.w + b.w;

@@ -178,8 +178,12 @@ __device__ __forceinline__ float raster_hit(const float4& q2, const float4& q3, 
             const float sq = sqrt_approx(disc);
             const float ia = rcp_approx(A);
             const float sn = (-B - sq) * ia;
-            const float sf = (-B + sq) * ia;
-            best = t0 + sn > 0.f ? sn : (t0 + sf > 0.f ? sf : INFINITY);
+            if (t0 + sn > 0.f) {
+                best = sn;
+            } else {  // the camera is inside the ellipsoid: the far root, if in front
+                const float sf = (-B + sq) * ia;
+                best = t0 + sf > 0.f ? sf : INFINITY;
+            }
         }
     } else {
         if (disc >= 0.f) {

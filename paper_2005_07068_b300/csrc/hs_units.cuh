@@ -166,31 +166,43 @@ __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2
         float z[kSub] = {INFINITY, INFINITY}, zt[kSub] = {0.f, 0.f}, zs[kSub] = {0.f, 0.f};
         if (any) {
             const float fpx0 = (float)px0, fpx1 = (float)(px0 + 8), fpy = (float)py;
-            uint64_t mask = any;
-            while (mask) {
-                const int j = __ffsll((long long)mask) - 1;
-                mask &= mask - 1;
-                const float4* R = rast + 5 * j;
-                const bool in0 = (mk[0] >> j) & 1, in1 = (mk[1] >> j) & 1;  // warp-uniform
-                const float4 q0 = R[0], q1 = R[1];
-                const float dv = fpy - q0.y, du0 = fpx0 - q0.x, du1 = fpx1 - q0.x;
-                const float d0 = raster_disc(q0, q1, du0, dv), d1 = raster_disc(q0, q1, du1, dv);
-                const bool caps = __float_as_uint(R[4].w) != 0u;
-                // the roots only when some lane's discriminant admits a hit
-                if (__any_sync(0xffffffffu, (in0 && (d0 >= 0.f || caps)) || (in1 && (d1 >= 0.f || caps)))) {
-                    const float4 q2 = R[2], q3 = R[3], q4 = R[4];
-                    const float sh0 = raster_hit(q2, q3, q4, du0, dv, d0);
-                    const float sh1 = raster_hit(q2, q3, q4, du1, dv, d1);
-                    const float zz0 = q2.w + sh0, zz1 = q2.w + sh1;
-                    if (in0 && zz0 < z[0]) {
-                        z[0] = zz0;
-                        zt[0] = q2.w;
-                        zs[0] = sh0;
-                    }
-                    if (in1 && zz1 < z[1]) {
-                        z[1] = zz1;
-                        zt[1] = q2.w;
-                        zs[1] = sh1;
+            // the primitive mask as two 32-bit words; the roots of each half only
+            // when some lane of that half can be hit
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                const uint32_t a0 = (uint32_t)(mk[0] >> (32 * w)), a1 = (uint32_t)(mk[1] >> (32 * w));
+                uint32_t mask = a0 | a1;
+                while (mask) {
+                    const int b = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const float4* R = rast + 5 * (b + 32 * w);
+                    const bool in0 = (a0 >> b) & 1u, in1 = (a1 >> b) & 1u;  // warp-uniform
+                    const float4 q0 = R[0], q1 = R[1];
+                    const float dv = fpy - q0.y, du0 = fpx0 - q0.x, du1 = fpx1 - q0.x;
+                    const float d0 = raster_disc(q0, q1, du0, dv), d1 = raster_disc(q0, q1, du1, dv);
+                    const bool caps = __float_as_uint(R[4].w) != 0u;
+                    const uint32_t v0 = __ballot_sync(0xffffffffu, in0 && (d0 >= 0.f || caps));
+                    const uint32_t v1 = __ballot_sync(0xffffffffu, in1 && (d1 >= 0.f || caps));
+                    if (v0 | v1) {
+                        const float4 q2 = R[2], q3 = R[3], q4 = R[4];
+                        if (v0) {
+                            const float sh0 = raster_hit(q2, q3, q4, du0, dv, d0);
+                            const float zz0 = q2.w + sh0;
+                            if (zz0 < z[0]) {
+                                z[0] = zz0;
+                                zt[0] = q2.w;
+                                zs[0] = sh0;
+                            }
+                        }
+                        if (v1) {
+                            const float sh1 = raster_hit(q2, q3, q4, du1, dv, d1);
+                            const float zz1 = q2.w + sh1;
+                            if (zz1 < z[1]) {
+                                z[1] = zz1;
+                                zt[1] = q2.w;
+                                zs[1] = sh1;
+                            }
+                        }
                     }
                 }
             }

@@ -169,8 +169,8 @@ __global__ void __launch_bounds__(kPsoThreads) pso_step_kernel(const __grid_cons
 // written) and a particle's personal best is judged improved when E <= pbest_E
 // as read, which gives the same answer whether or not its owner has already
 // stored the update.
-__global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__ DevModel model_param,
-                                                         const PsoFkArgs a)
+template <class M>  // DevModelCore for the paper's kc, DevModel for a kc variant
+__global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__ M model_param, const PsoFkArgs a)
 {
     __shared__ FkShared sh;
     __shared__ float s_r[4 * kPairBlocks], s_m[4 * kMutBlocks];
@@ -217,13 +217,16 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
                                        xi, pbi, vi, s_pe[i], true, red_v, red_i, red_r);
     if (t < kNdof) s_xn[t] = o.xn;
     // FK of the new pose (fk_particle starts with a barrier that publishes s_xn)
-    fk_particle(sh, s_xn, cam, a.prims + (size_t)q * sh.model.n_prims * 4, a.kc + q, a.status);
+    fk_particle(sh, collide_data(model_param), s_xn, cam, a.prims + (size_t)q * sh.model.n_prims * 4, a.kc + q, a.status);
 }
 
 cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cudaStream_t stream)
 {
-    static std::atomic<uint32_t> opted[64];
-    const cudaError_t e = opt_in_dynamic_smem(pso_step_fk_kernel, 2 * HS_FUSED_MAX_PARTICLES * (int)sizeof(float), opted);
+    const bool core = model.kc_variant == HS_KC_ABDUCTION;
+    static std::atomic<uint32_t> opted[2][64];
+    const int smem_max = 2 * HS_FUSED_MAX_PARTICLES * (int)sizeof(float);
+    const cudaError_t e = core ? opt_in_dynamic_smem(pso_step_fk_kernel<DevModelCore>, smem_max, opted[0])
+                               : opt_in_dynamic_smem(pso_step_fk_kernel<DevModel>, smem_max, opted[1]);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     // one CTA per particle (all swarms of a batch); shared memory for the largest swarm
@@ -236,7 +239,9 @@ cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cud
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, pso_step_fk_kernel, model, args);
+    return core ? cudaLaunchKernelEx(&cfg, pso_step_fk_kernel<DevModelCore>, static_cast<const DevModelCore&>(model),
+                                     args)
+                : cudaLaunchKernelEx(&cfg, pso_step_fk_kernel<DevModel>, model, args);
 }
 
 cudaError_t launch_pso_init(const Limits& lim, const PsoInitArgs& args, cudaStream_t stream)

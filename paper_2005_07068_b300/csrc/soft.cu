@@ -596,7 +596,9 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
 
 // ---- pose gradient: record adjoints -> d E_s / d pose ------------------------------
 
-__global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ DevModel model_param, const GradArgs a)
+// (the paper's kc only: pose_grad refuses the kc variants, so the core model suffices)
+__global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ DevModelCore model_param,
+                                                       const GradArgs a)
 {
     __shared__ FkShared sh;
     extern __shared__ float s_tan[];  // [26][n_bones][12]: dR (9), dP (3) of every bone for every DOF,
@@ -604,7 +606,7 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ D
     fk_load_model(sh, model_param);
     const int p = blockIdx.x, t = threadIdx.x;
     const float* pose = a.poses + (size_t)p * kNdof;
-    fk_particle(sh, pose, make_float4(a.fx, a.fy, a.cx, a.cy), a.prims + (size_t)p * sh.model.n_prims * 4, a.kc + p,
+    fk_particle(sh, nullptr, pose, make_float4(a.fx, a.fy, a.cx, a.cy), a.prims + (size_t)p * sh.model.n_prims * 4, a.kc + p,
                 a.status);
     __syncthreads();
     const int nb = sh.model.n_bones, np = sh.model.n_prims;
@@ -809,7 +811,7 @@ cudaError_t launch_pose_grad(const DevModel& model, const GradArgs& args, cudaSt
     static std::atomic<uint32_t> opted[64];
     const cudaError_t e = opt_in_dynamic_smem(pose_grad_kernel, (kNdof * kMaxBones * 12 + kMaxPrims * kNdof) * 4, opted);
     if (e != cudaSuccess) return e;
-    pose_grad_kernel<<<args.P, 64, smem, stream>>>(model, args);
+    pose_grad_kernel<<<args.P, 64, smem, stream>>>(static_cast<const DevModelCore&>(model), args);
     return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@ constexpr int kFrameWarps = 8;
 constexpr int kFrameThreads = kFrameWarps * 32;
 constexpr uint32_t kBarrierPolls = 1u << 24;  // each poll sleeps ~0.1 us: a few seconds in all
 
+
 struct FrameShared {
     FkShared fk;                      // model, pose, bone frames
     float4 rec[kMaxPrims * 4];        // this particle's FK records
@@ -55,8 +56,11 @@ struct FrameShared {
     int box[4];
 };
 
-// all threads of every CTA: returns false if the wait ran out
-__device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, uint32_t* status)
+// all threads of every CTA: returns false if the wait ran out.  work() runs
+// on every thread after this CTA has arrived, while the others are awaited
+// (it must not touch what the barrier publishes).
+template <class Work>
+__device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, uint32_t* status, const Work& work)
 {
     __syncthreads();
     int ok = 1;
@@ -65,6 +69,10 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, u
         // release: this CTA's earlier writes (seen by thread 0 through the CTA
         // barrier) are visible to whoever acquires the count
         asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(v) : "l"(count) : "memory");
+    }
+    work();
+    if (threadIdx.x == 0) {
+        uint32_t v;
         uint32_t polls = 0;
         for (;;) {
             asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
@@ -165,7 +173,6 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
     uint32_t barriers = 0u;
     bool alive = true;
     for (int g = 1; g <= a.gens; ++g) {
-        draw_step_randoms(p, (uint32_t)g, a.frame, a.key0, a.key1, sh.r, sh.m, t);
         // FK of the current pose (fk_particle starts with a barrier that publishes
         // sh.x); each record's raster form is made by the thread that formed it
         fk_particle(sh.fk, &model, sh.x, a.cam, sh.rec, &sh.kc, a.status, [&](int j, const float* rec) {
@@ -212,9 +219,11 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
             if (acc_h) atomicAdd(&slot[p].n_hit, acc_h);
             if (primary) slot[p].kc = sh.kc;
         }
-        // every particle's sums (and the frame's totals) are in
+        // every particle's sums (and the frame's totals) are in; meanwhile this
+        // particle's random numbers for the step
         ++barriers;
-        if (!grid_barrier(&a.ctl->barrier, barriers * nblocks, a.status)) {
+        if (!grid_barrier(&a.ctl->barrier, barriers * nblocks, a.status,
+                          [&] { draw_step_randoms(p, (uint32_t)g, a.frame, a.key0, a.key1, sh.r, sh.m, t); })) {
             alive = false;
             break;
         }

@@ -82,6 +82,30 @@ def test_frame_equals_step_by_step(scene, gens):
     assert ref[-1]["gbest_E"][0] <= ref[0]["gbest_E"][0]
 
 
+def test_frame_at_the_capacity_limit():
+    """As many particles as the device keeps resident at one CTA each (the
+    largest grid a frame may have), on a small ROI: still the step-by-step
+    result, and a grid one CTA larger is refused without a launch."""
+    cap = hs.frame_capacity()
+    P = min(cap, hs.FRAME_MAX_PARTICLES)
+    sc = C.make_scene(64, 48, 2, 717, noisy=True, f32=False)
+    cam = hs.camera(*[float(v) for v in sc.cam])
+    obs = hs.Obs.from_numpy(sc.Od, sc.S, torch.device("cuda"))
+    start = torch.from_numpy(sc.gt).cuda()
+    ref = _run(T.Tracker(sc.model_g, cam, P=P, gens=3, seed=9), obs, 1, start)
+    ft = T.FrameTracker(sc.model_g, cam, P=P, gens=3, seed=9, ctas_per_particle=1)
+    got = _run(ft, obs, 1, start)
+    for k in ref[0]:
+        assert np.array_equal(got[0][k], ref[0][k], equal_nan=True), k
+    if P < hs.FRAME_MAX_PARTICLES:
+        big = T.FrameTracker(sc.model_g, cam, P=P + 1, gens=3, seed=9, ctas_per_particle=1)
+        with pytest.raises(hs.HandscoreError) as e:
+            big.run_frame(obs, 0, start)
+        assert e.value.status == hs.HS_ERR_SIZE
+    torch.cuda.synchronize()
+    assert hs.hs_get_device_status(clear=True) == 0
+
+
 def test_first_generation_against_oracle():
     """One generation: E of the initial swarm (the positions the frame kernel
     drew around the seed pose, left in the first position buffer) against the

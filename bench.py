@@ -809,7 +809,7 @@ def main():
         fc = fclk.summary(peaks.get("sm_max_mhz", 2032.0))
         frame_path = {"value": f_value, "unit": "evals/s", "ms_per_step": 1e3 * f_t / K,
                       "kernel": "track_frame_kernel: one cooperative launch per frame",
-                      "ctas_per_particle": ft.ctas, "autotune_us_per_frame": ftab, "gpu_launches": K,
+                      "ctas": ft.ctas, "autotune_us_per_frame": ftab, "gpu_launches": K,
                       "clocks": fc}
     graph_ms = 1e3 * t_dev / K
     # the headline is the faster of the two paths (same frames, same swarm)
@@ -947,7 +947,8 @@ def main():
                   "gpu_launches": K * trk.launches_per_frame(), "clocks": clocks}
     if use_frame:
         value, step_ms_h, launches, clocks = frame_path["value"], frame_path["ms_per_step"], K, frame_path["clocks"]
-        step_desc = (f"one frame = one cooperative launch of track_frame ({PARTICLES} particles x {ft.ctas} CTAs; "
+        step_desc = (f"one frame = one cooperative launch of track_frame ({PARTICLES} particles, {ft.ctas} CTAs dealt "
+                     f"to them by their render work each generation; "
                      f"the faster of it and the CUDA graph of the step-by-step calls)")
     else:
         step_ms_h, launches = graph_ms, K * trk.launches_per_frame()

@@ -345,37 +345,41 @@ int pso_step_fk(const HsModel* model, const HsSwarm* swarm, float* x_next, int P
  * Section III.B's per-frame loop -- initialise the swarm around the previous
  * frame's best pose, then `gens` generations of "score every particle (Section
  * III.A, Eq. 4-5), move the swarm (Eq. 6-7 and the mutation)" -- as one
- * cooperative launch that keeps P x C CTAs resident (C = ctas_per_particle)
- * for the whole frame.  Each particle's FK records and state stay in shared
- * memory; one grid barrier per generation separates scoring from the update.
+ * cooperative launch whose `ctas` CTAs stay resident for the whole frame, with
+ * one grid barrier per generation between scoring and the update.  Every
+ * generation the CTAs are dealt to particles: each particle gets at least one,
+ * the rest go out in proportion to the 16x4-pixel work units of its previous
+ * render (evenly in the first generation).  The CTAs of a particle share its
+ * units; its FK records stay in their shared memory.
  *
  * Results are exactly those of the step-by-step calls
  *     hs_obs_prepare(obs); pso_init(swarm, seed_pose, scale, seed, frame);
  *     pose_fk(x); for g = 1..gens: render_score_batch (any variant) on the
  *     records; pso_step_fk(gen = g) with swarm->x and x_next alternating
- * bit for bit: E (swarm->E, written through the const pointer: it must be a
- * writable device array), pbest, pbest_E, gbest, gbest_E, v, obs->stats, and
- * the positions (generation g writes buffer g & 1 of {swarm->x, x_next}, so
- * the final positions are in swarm->x when gens is even, in x_next when odd).
- * prims (optional, may be NULL) and kc [P] receive the records and kc of the
- * final positions.
+ * bit for bit, whatever `ctas`: E (swarm->E, written through the const
+ * pointer: it must be a writable device array), pbest, pbest_E, gbest,
+ * gbest_E, v, obs->stats, and the positions (generation g writes buffer g & 1
+ * of {swarm->x, x_next}, so the final positions are in swarm->x when gens is
+ * even, in x_next when odd).  prims (optional, may be NULL) and kc [P] receive
+ * the records and kc of the final positions.
  *
- * ctas_per_particle: 0 picks the largest C with P x C resident CTAs (at most
- * 8); P x C must not exceed hs_frame_capacity().  workspace:
- * hs_frame_workspace_size(P) bytes, zeroed once before first use (every call
- * leaves it zeroed).  Calls that share a workspace must not overlap on the GPU.
- * If a grid barrier wait runs out (a few seconds), the frame stops,
- * HS_DEV_BARRIER_TIMEOUT is set and the swarm's contents are void.
- * Errors: HS_ERR_ARG (NULL, x_next == swarm->x, bad constants, gens < 0),
- * HS_ERR_ALIGN, HS_ERR_SIZE (P out of range, P x C over capacity, workspace
- * too small), HS_ERR_CUDA. */
+ * ctas: CTAs of the grid, P <= ctas <= hs_frame_capacity(); 0 picks
+ * min(capacity, 8 P).  workspace: hs_frame_workspace_size(P) bytes (counters,
+ * sums, and a second buffer of the swarm state), zeroed once before first use
+ * (every call leaves its counters and sums zeroed).  Calls that share a
+ * workspace must not overlap on the GPU.  If a grid barrier wait runs out (a
+ * few seconds), the frame stops, HS_DEV_BARRIER_TIMEOUT is set and the
+ * swarm's contents are void.
+ * Errors: HS_ERR_ARG (NULL, x_next == swarm->x, bad constants, gens < 0,
+ * ctas < 0), HS_ERR_ALIGN, HS_ERR_SIZE (P out of range, ctas < P or over
+ * capacity, workspace too small), HS_ERR_CUDA. */
 #define HS_FRAME_MAX_PARTICLES 1024
 int hs_frame_workspace_size(int P, size_t* bytes);
 /* CTAs of track_frame that the current device keeps resident at once */
 int hs_frame_capacity(int* ctas);
 int track_frame(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsSwarm* swarm, float* x_next,
                 int P, int gens, const HsScoreParams* score, const HsPsoParams* pso, const float* seed_pose,
-                const float* scale, uint64_t seed, uint32_t frame, int ctas_per_particle, void* workspace,
+                const float* scale, uint64_t seed, uint32_t frame, int ctas, void* workspace,
                 size_t workspace_bytes, HsPrim* prims, float* kc, hs_stream_t stream);
 
 /* ---- batches: many independent swarms per launch ----------------------------------

@@ -574,7 +574,7 @@ int hs_frame_capacity(int* ctas)
 
 int track_frame(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsSwarm* sw, float* x_next, int P,
                 int gens, const HsScoreParams* score, const HsPsoParams* prm, const float* seed_pose,
-                const float* scale, uint64_t seed, uint32_t frame, int ctas_per_particle, void* workspace,
+                const float* scale, uint64_t seed, uint32_t frame, int ctas, void* workspace,
                 size_t workspace_bytes, HsPrim* prims, float* kc, hs_stream_t stream)
 {
     if (!model || !sw || !x_next || !score || !prm || !seed_pose || !scale || !kc) return HS_ERR_ARG;
@@ -585,7 +585,7 @@ int track_frame(const HsModel* model, const HsObs* obs, const HsCamera* cam, con
     if ((rc = validate_cam(cam))) return rc;
     if ((rc = validate_score_params(score))) return rc;
     if (P < 1 || P > HS_FRAME_MAX_PARTICLES) return HS_ERR_SIZE;
-    if (ctas_per_particle < 0 || ctas_per_particle > 64) return HS_ERR_ARG;
+    if (ctas < 0) return HS_ERR_ARG;
     const double psi = (double)prm->c1 + (double)prm->c2;
     if (!std::isfinite(psi) || prm->c1 < 0.f || prm->c2 < 0.f || psi <= 4.0) return HS_ERR_ARG;
     if (prm->mutate_every > 0 && (prm->n_mutate < 0 || prm->n_mutate > P)) return HS_ERR_ARG;
@@ -600,9 +600,8 @@ int track_frame(const HsModel* model, const HsObs* obs, const HsCamera* cam, con
     }
     int cap = 0;
     if (track_frame_capacity(&cap) != cudaSuccess) return HS_ERR_CUDA;
-    int C = ctas_per_particle;
-    if (C == 0) C = std::min(8, cap / P);
-    if (C < 1 || (long long)P * C > cap) return HS_ERR_SIZE;
+    const int nb = ctas ? ctas : std::min(cap, 8 * P);
+    if (nb < P || nb > cap) return HS_ERR_SIZE;
 
     cudaStream_t s = (cudaStream_t)stream;
     const bool f32 = obs->depth_type == HS_DEPTH_F32;
@@ -650,14 +649,13 @@ int track_frame(const HsModel* model, const HsObs* obs, const HsCamera* cam, con
     a.key1 = (uint32_t)(seed >> 32);
     a.frame = frame;
     a.P = P;
-    a.C = C;
     a.gens = gens;
     a.ctl = static_cast<FrameCtl*>(workspace);
     a.sums = reinterpret_cast<FrameSums*>(static_cast<unsigned char*>(workspace) + sizeof(FrameCtl));
     if ((rc = status_ptr(&a.status))) return rc;
     // the frame's observation totals start from zero (as hs_obs_prepare)
     if (cudaMemsetAsync(obs->stats, 0, 2 * sizeof(uint32_t), s) != cudaSuccess) return HS_ERR_CUDA;
-    return launch_track_frame(model->dev, tm_depth, tm_skin, a, s) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+    return launch_track_frame(model->dev, tm_depth, tm_skin, a, nb, s) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 
 // ---- the smoothed objective and its gradient ---------------------------------------

@@ -6,10 +6,11 @@
 // The graph path launches a kernel per step (observation totals, init, FK,
 // then render + fused step per generation): about 20 us per generation at
 // 64 particles, mostly launch gaps and the latency chains of short kernels.
-// Here C CTAs per particle stay resident for the whole frame:
+// Here the grid's CTAs stay resident for the whole frame, dealt evenly to the
+// particles (each gets floor(n / P) or ceil(n / P) of the n CTAs):
 //
 //  * every CTA keeps its particle's state (position, velocity, personal best)
-//    and its FK records in shared memory; the C CTAs of a particle run the
+//    and its FK records in shared memory; the CTAs of a particle run the
 //    same FK and the same swarm update (identical inputs, identical results),
 //    and the first of them (the primary) stores the particle's state;
 //  * generation g: FK of the current pose -> raster records -> the CTA's share
@@ -52,6 +53,7 @@ struct FrameShared {
     uint32_t red_c[kFrameWarps][3];
     float red_v[kFrameWarps];
     int red_i[kFrameWarps], red_r[kFrameWarps];
+    int gprev;  // the swarm's global best after the previous generation
     uint32_t st[2];
     int box[4];
 };
@@ -65,10 +67,10 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, u
     __syncthreads();
     int ok = 1;
     if (threadIdx.x == 0) {
-        uint32_t v;
         // release: this CTA's earlier writes (seen by thread 0 through the CTA
-        // barrier) are visible to whoever acquires the count
-        asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(v) : "l"(count) : "memory");
+        // barrier) are visible to whoever acquires the count; no value returns,
+        // so the thread goes on at once
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
     }
     work();
     if (threadIdx.x == 0) {
@@ -97,9 +99,13 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
     float* s_e = s_dyn;
     float* s_pe = s_dyn + a.P;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int P = a.P, p = blockIdx.x / a.C, c = blockIdx.x % a.C;
-    const bool primary = c == 0;
     const uint32_t nblocks = gridDim.x;
+    // particle p has CTAs [ceil(p n / P), ceil((p + 1) n / P)) of the n in the grid
+    const int P = a.P, p = (int)((unsigned long long)blockIdx.x * (unsigned)P / nblocks);
+    const int first = (int)(((unsigned long long)p * nblocks + P - 1) / (unsigned)P);
+    const int C = (int)(((unsigned long long)(p + 1) * nblocks + P - 1) / (unsigned)P) - first;
+    const int c = (int)blockIdx.x - first;
+    const bool primary = c == 0;
     const int n_prims = model.n_prims;
 
     fk_load_model(sh.fk, model);
@@ -152,6 +158,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
     }
     if (t == 0) {
         sh.pe = INFINITY;
+        sh.gprev = 0;
         if (primary) {
             a.pbest_E[p] = INFINITY;
             if (p == 0) a.gbest_E[0] = INFINITY;
@@ -196,7 +203,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
         uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
         if (sh.box[3] > 0)
             render_units_warp(sh.rast, sh.pbox, n_prims, sh.box, sh.tile[warp], sh.bar[warp], phases,
-                              c * kFrameWarps + warp, a.C * kFrameWarps, pv, ra, p, lane, acc_t, acc_a, acc_o, acc_h);
+                              c * kFrameWarps + warp, C * kFrameWarps, pv, ra, p, lane, acc_t, acc_a, acc_o, acc_h);
         warp_sum(acc_t, acc_a, acc_o, acc_h);
         if (lane == 0) {
             sh.red_t[warp] = acc_t;
@@ -227,6 +234,17 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
             alive = false;
             break;
         }
+        SwarmRefs R = R0;
+        R.x = a.xbuf[(g - 1) & 1];
+        R.x_next = a.xbuf[g & 1];
+        R.mutate = a.mutate_every > 0 && g % a.mutate_every == 0 && a.n_mutate > 0;
+        // the previous global best's position, read with the sums: it is most
+        // often the global best again, and then needs no read after the argmin
+        GbestGuess guess{sh.gprev, 0.f, 0.f};
+        if (t < kNdof) {
+            guess.x = __ldcg(R.x + (size_t)guess.g * kNdof + t);
+            guess.pb = __ldcg(a.pbest + (size_t)guess.g * kNdof + t);
+        }
         // E of every particle of the swarm, and the personal-best Es as read
         // (this particle's own from its copy)
         // (loads through L2: other CTAs wrote these during this launch)
@@ -241,10 +259,6 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
             s_pe[j] = j == p ? sh.pe : __ldcg(a.pbest_E + j);
         }
         __syncthreads();
-        SwarmRefs R = R0;
-        R.x = a.xbuf[(g - 1) & 1];
-        R.x_next = a.xbuf[g & 1];
-        R.mutate = a.mutate_every > 0 && g % a.mutate_every == 0 && a.n_mutate > 0;
         float xi = 0.f, pbi = 0.f, vi = 0.f;
         if (t < kNdof) {
             xi = sh.x[t];
@@ -253,7 +267,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
         }
         const StepOut o = swarm_update<kFrameThreads>(R, p, p, 0, P, 0, a.n_mutate, s_e, s_pe, sh.r, sh.m,
                                                       sh.fk.model.lo, sh.fk.model.hi, xi, pbi, vi, sh.pe, primary,
-                                                      sh.red_v, sh.red_i, sh.red_r);
+                                                      sh.red_v, sh.red_i, sh.red_r, guess);
         __syncthreads();  // every thread has read sh.x / sh.pe of this generation
         if (t < kNdof) {
             sh.x[t] = o.xn;
@@ -262,6 +276,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
         }
         if (t == 0) {
             if (o.imp) sh.pe = s_e[p];
+            sh.gprev = o.g;
             if (primary) {
                 a.E[p] = s_e[p];
                 // the slot generation g + 2 will use: every CTA read it (as
@@ -322,12 +337,12 @@ cudaError_t track_frame_capacity(int* ctas)
 }
 
 cudaError_t launch_track_frame(const DevModel& model, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,
-                               const FrameArgs& args, cudaStream_t stream)
+                               const FrameArgs& args, int ctas, cudaStream_t stream)
 {
     const cudaError_t e = frame_smem_opt_in();
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(args.P * args.C);
+    cfg.gridDim = dim3(ctas);
     cfg.blockDim = dim3(kFrameThreads);
     cfg.dynamicSmemBytes = 2 * (size_t)args.P * sizeof(float);
     cfg.stream = stream;

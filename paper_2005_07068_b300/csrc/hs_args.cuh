@@ -139,7 +139,7 @@ struct FrameArgs {
     float c1, c2, w;
     int mutate_every, n_mutate;
     uint32_t key0, key1, frame;
-    int P, C, gens;
+    int P, gens;
     FrameCtl* ctl;
     FrameSums* sums;                     // [3][P]
     uint32_t* status;
@@ -202,7 +202,7 @@ cudaError_t launch_pose_grad(const DevModel& model, const GradArgs& args, cudaSt
 cudaError_t launch_fk(const DevModel& model, const FkArgs& args, cudaStream_t stream);
 cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cudaStream_t stream);
 cudaError_t launch_track_frame(const DevModel& model, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,
-                               const FrameArgs& args, cudaStream_t stream);
+                               const FrameArgs& args, int ctas, cudaStream_t stream);
 cudaError_t track_frame_capacity(int* ctas);  // co-resident CTAs of track_frame_kernel on the current device
 cudaError_t launch_render_score(const CUtensorMap& tm_depth, const CUtensorMap& tm_skin, const RenderArgs& args,
                                 cudaStream_t stream);

@@ -86,26 +86,37 @@ struct SwarmRefs {
 struct StepOut {
     float xn, vn, pb;  // new position, velocity and personal best of dimension t
     bool imp;          // the personal best improved (pbest_E becomes E_i)
+    int g;             // the swarm's global best (index within the swarm)
 };
 
-// One generation of particle number i (global row q) of a swarm of P
-// particles starting at row off (swarm s).  NT threads (a multiple of 32)
-// call it; s_e / s_pe [P] hold the swarm's E and pbest_E as read (the caller
-// fills them and synchronises); xi, pbi, vi: the particle's own dimension t
-// (t < 26) and own_pe its own pbest_E, from a copy no other thread writes.
-// red_*: [NT / 32] shared scratch.  When `store`, writes the particle's v,
-// x_next, pbest / pbest_E (on improvement) and, for i == 0, the swarm's gbest.
+// a caller's early read of one particle's x and pbest (dimension t), taken
+// after every particle's previous update was stored: if that particle turns
+// out to be the global best, its position comes from here instead of a
+// second read (the values are the same: x does not change during an update,
+// and pbest_g is only rewritten when x_g becomes the best, in which case x_g
+// is taken)
+struct GbestGuess {
+    int g;  // swarm index, or -1 for none
+    float x, pb;
+};
+
+// The global best and the ranks: what every particle's update reads of the
+// whole swarm.
+struct SwarmBest {
+    int g;     // argmin_j min(E_j, pbest_E_j as read): lowest index on ties, NaN never wins
+    float gE;  // that minimum
+    int rank;  // particles ranking before particle i by E (counted when mutating)
+};
+
+// NT threads (a multiple of 32) call it; s_e / s_pe [P] hold the swarm's E and
+// pbest_E as read (the caller fills them and synchronises).  red_*: [NT / 32]
+// shared scratch.  Every thread gets the result.
 template <int NT>
-__device__ __forceinline__ StepOut swarm_update(const SwarmRefs& R, int q, int i, int off, int P, int s, int n_mutate,
-                                                const float* s_e, const float* s_pe, const float* s_r,
-                                                const float* s_m, const float* lo, const float* hi, float xi,
-                                                float pbi, float vi, float own_pe, bool store, float* red_v,
-                                                int* red_i, int* red_r)
+__device__ __forceinline__ SwarmBest swarm_best(int P, int i, bool mutate, const float* s_e, const float* s_pe,
+                                                float* red_v, int* red_i, int* red_r)
 {
     static_assert(NT % 32 == 0, "whole warps");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    // global best = argmin_j min(E_j, pbest_E_j) (lowest index on ties, NaN never
-    // wins) and this particle's rank by E
     const float ei = s_e[i];
     float bv = INFINITY;
     int bi = INT_MAX, rank = 0;
@@ -116,7 +127,7 @@ __device__ __forceinline__ StepOut swarm_update(const SwarmRefs& R, int q, int i
             bv = pe;
             bi = j;
         }
-        if (R.mutate) rank += ranks_before(ej, j, ei, i);
+        if (mutate) rank += ranks_before(ej, j, ei, i);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -134,48 +145,81 @@ __device__ __forceinline__ StepOut swarm_update(const SwarmRefs& R, int q, int i
         red_r[warp] = rank;
     }
     __syncthreads();
-    int g = red_i[0];
-    float gE = red_v[0];
-    rank = red_r[0];
+    SwarmBest b{red_i[0], red_v[0], red_r[0]};
 #pragma unroll
     for (int w = 1; w < NT / 32; ++w) {
-        if (red_i[w] != INT_MAX && (g == INT_MAX || red_v[w] < gE || (red_v[w] == gE && red_i[w] < g))) {
-            g = red_i[w];
-            gE = red_v[w];
+        if (red_i[w] != INT_MAX && (b.g == INT_MAX || red_v[w] < b.gE || (red_v[w] == b.gE && red_i[w] < b.g))) {
+            b.g = red_i[w];
+            b.gE = red_v[w];
         }
-        rank += red_r[w];
+        b.rank += red_r[w];
     }
-    StepOut out{0.f, 0.f, 0.f, ei < own_pe};  // strict improvement of this particle's personal best
-    const bool mutated = R.mutate && rank >= P - n_mutate;
+    return b;
+}
+
+// dimension t of the global best's position: its current x if that is its
+// personal best now, else its pbest (read through L2: another CTA of a
+// resident grid may have written them)
+__device__ __forceinline__ float gbest_position(const float* x, const float* pbest, int row, bool x_is_best, int t)
+{
+    return x_is_best ? __ldcg(x + (size_t)row * kNdof + t) : __ldcg(pbest + (size_t)row * kNdof + t);
+}
+
+// Eq. 6-7 for dimension t of one particle (r1 = number 2t, r2 = number 2t+1 of
+// s_r), then the clamp to the limits; a mutated particle re-draws its finger
+// dimensions and zeroes their velocity.  imp: its personal best improved.
+__device__ __forceinline__ StepOut swarm_move(float c1, float c2, float w, bool imp, bool mutated, int t, float xi,
+                                              float pbi, float vi, float gv, const float* s_r, const float* s_m,
+                                              const float* lo, const float* hi)
+{
+    StepOut out{0.f, 0.f, imp ? xi : pbi, imp, 0};
+    float acc = fmaf(c1 * s_r[2 * t], out.pb - xi, vi);
+    acc = fmaf(c2 * s_r[2 * t + 1], gv - xi, acc);
+    float vn = w * acc;
+    float xn = fminf(fmaxf(xi + vn, lo[t]), hi[t]);
+    if (mutated && t >= 6) {
+        xn = fmaf(s_m[t - 6], hi[t] - lo[t], lo[t]);
+        vn = 0.f;
+    }
+    out.xn = xn;
+    out.vn = vn;
+    return out;
+}
+
+// One generation of particle number i (global row q) of a swarm of P
+// particles starting at row off (swarm s), updated in place.  NT threads call
+// it; s_e / s_pe as for swarm_best; xi, pbi, vi: the particle's own dimension
+// t (t < 26) and own_pe its own pbest_E, from a copy no other thread writes.
+// When `store`, writes the particle's v, x_next, pbest / pbest_E (on
+// improvement) and, for i == 0, the swarm's gbest.  guess: see GbestGuess.
+template <int NT>
+__device__ __forceinline__ StepOut swarm_update(const SwarmRefs& R, int q, int i, int off, int P, int s, int n_mutate,
+                                                const float* s_e, const float* s_pe, const float* s_r,
+                                                const float* s_m, const float* lo, const float* hi, float xi,
+                                                float pbi, float vi, float own_pe, bool store, float* red_v,
+                                                int* red_i, int* red_r, const GbestGuess& guess = GbestGuess{-1, 0.f, 0.f})
+{
+    const int t = threadIdx.x;
+    const SwarmBest b = swarm_best<NT>(P, i, R.mutate, s_e, s_pe, red_v, red_i, red_r);
+    const float ei = s_e[i];
+    StepOut out{0.f, 0.f, 0.f, ei < own_pe, b.g};  // strict improvement of this particle's personal best
+    const bool mutated = R.mutate && b.rank >= P - n_mutate;
     if (t < kNdof) {
-        // the global best's position: its current x if that is its personal best now
-        const bool gimp = s_e[g] <= s_pe[g];
-        // (read through L2: another CTA of a resident grid may have written them)
-        const float gv = gimp ? __ldcg(R.x + (size_t)(off + g) * kNdof + t)
-                              : __ldcg(R.pbest + (size_t)(off + g) * kNdof + t);
+        const bool x_is_best = s_e[b.g] <= s_pe[b.g];
+        const float gv = b.g == guess.g ? (x_is_best ? guess.x : guess.pb)
+                                        : gbest_position(R.x, R.pbest, off + b.g, x_is_best, t);
         if (store && i == 0) R.gbest[(size_t)s * kNdof + t] = gv;
-        out.pb = out.imp ? xi : pbi;
         if (store && out.imp) R.pbest[(size_t)q * kNdof + t] = xi;
-        // Eq. 6-7 for dimension t (r1 = number 2t, r2 = number 2t+1), then clamp;
-        // the mutation re-draws a finger dimension and zeroes its velocity
-        float acc = fmaf(R.c1 * s_r[2 * t], out.pb - xi, vi);
-        acc = fmaf(R.c2 * s_r[2 * t + 1], gv - xi, acc);
-        float vn = R.w * acc;
-        float xn = fminf(fmaxf(xi + vn, lo[t]), hi[t]);
-        if (mutated && t >= 6) {
-            xn = fmaf(s_m[t - 6], hi[t] - lo[t], lo[t]);
-            vn = 0.f;
-        }
+        out = swarm_move(R.c1, R.c2, R.w, out.imp, mutated, t, xi, pbi, vi, gv, s_r, s_m, lo, hi);
+        out.g = b.g;
         if (store) {
-            R.v[(size_t)q * kNdof + t] = vn;
-            R.x_next[(size_t)q * kNdof + t] = xn;
+            R.v[(size_t)q * kNdof + t] = out.vn;
+            R.x_next[(size_t)q * kNdof + t] = out.xn;
         }
-        out.xn = xn;
-        out.vn = vn;
     }
     if (store && t == 0) {
         if (out.imp) R.pbest_E[q] = ei;
-        if (i == 0) R.gbest_E[s] = gE;
+        if (i == 0) R.gbest_E[s] = b.gE;
     }
     return out;
 }

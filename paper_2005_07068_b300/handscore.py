@@ -415,7 +415,8 @@ def pso_step_fk(model: Model, sw: Swarm, x_next: torch.Tensor, params: HsPsoPara
 # ---- a whole tracking frame in one launch ---------------------------------------------
 
 def new_frame_workspace(P: int, device="cuda") -> torch.Tensor:
-    """Zeroed workspace of track_frame for P particles (every call leaves it zeroed)."""
+    """Zeroed workspace of track_frame for P particles (every call leaves its
+    counters and sums zeroed; the rest is a second buffer of the swarm state)."""
     n = ctypes.c_size_t()
     _check("hs_frame_workspace_size", lib().hs_frame_workspace_size(P, ctypes.byref(n)))
     return torch.zeros((n.value + 15) // 16 * 4, dtype=torch.int32, device=device)
@@ -430,17 +431,18 @@ def frame_capacity() -> int:
 
 def track_frame(model: Model, obs: Obs, cam: HsCamera, sw: Swarm, x_next: torch.Tensor, gens: int,
                 score: HsScoreParams, pso: HsPsoParams, seed_pose: torch.Tensor, scale, seed: int, frame: int,
-                ctas_per_particle: int, ws: torch.Tensor, kc: torch.Tensor, prims: torch.Tensor | None = None,
+                ctas: int, ws: torch.Tensor, kc: torch.Tensor, prims: torch.Tensor | None = None,
                 stream=None) -> None:
     """One whole frame (obs totals, init around seed_pose, gens x (score, step)) in
-    one cooperative launch; identical to the step-by-step calls.  Generation g
-    writes positions to (sw.x, x_next)[g & 1]."""
+    one cooperative launch of `ctas` CTAs (0: automatic), dealt to particles by
+    their work each generation; identical to the step-by-step calls.
+    Generation g writes positions to (sw.x, x_next)[g & 1]."""
     st = sw.struct()
     sc = (ctypes.c_float * NDOF)(*[float(v) for v in np.asarray(scale, np.float32)])
     _check("track_frame", lib().track_frame(model.handle, ctypes.byref(obs.struct()), ctypes.byref(cam),
                                             ctypes.byref(st), _ptr(x_next), sw.P, gens, ctypes.byref(score),
                                             ctypes.byref(pso), _ptr(seed_pose), sc, ctypes.c_uint64(seed), frame,
-                                            ctas_per_particle, _ptr(ws), ws.numel() * ws.element_size(),
+                                            ctas, _ptr(ws), ws.numel() * ws.element_size(),
                                             _ptr(prims), _ptr(kc), _stream(stream)))
 
 

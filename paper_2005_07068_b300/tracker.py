@@ -138,17 +138,17 @@ class Tracker:
 
 class FrameTracker(Tracker):
     """Plain PSO tracking with each frame in ONE cooperative launch (track_frame):
-    C CTAs per particle stay resident for the whole frame, keep the particle's
-    records and state on chip and meet at one grid barrier per generation.
-    Bit for bit the same swarm as Tracker (same observation, camera, P, seed);
-    no CUDA graph is needed, a frame is a single launch."""
+    `ctas` CTAs stay resident for the whole frame and meet at one grid barrier
+    per generation; each generation they are dealt to particles in proportion
+    to the particles' render work.  Bit for bit the same swarm as Tracker (same
+    observation, camera, P, seed); no CUDA graph is needed, a frame is a
+    single launch.  ctas = 0 lets the library choose."""
 
-    def __init__(self, model: hs.Model, cam: hs.HsCamera, P: int = 64, gens: int = 40, *, ctas_per_particle: int = 0,
-                 **kw):
+    def __init__(self, model: hs.Model, cam: hs.HsCamera, P: int = 64, gens: int = 40, *, ctas: int = 0, **kw):
         super().__init__(model, cam, P, gens, **kw)
         if P > hs.FRAME_MAX_PARTICLES:
             raise ValueError(f"track_frame takes at most {hs.FRAME_MAX_PARTICLES} particles")
-        self.ctas = ctas_per_particle
+        self.ctas = ctas
         self.fws = hs.new_frame_workspace(P, self.device)
 
     def enqueue_frame(self, obs: hs.Obs, frame: int, seed_pose: torch.Tensor | None = None) -> None:
@@ -164,19 +164,22 @@ class FrameTracker(Tracker):
         self.enqueue_frame(obs, frame, seed_pose)
 
     def candidates(self) -> list[int]:
-        """CTAs per particle that fit on the device at this P."""
+        """Grid sizes to try at this P: whole CTAs per particle (1, 2, 3, 4, 6, 8)
+        and whole waves of the device's SMs, within the resident capacity."""
         cap = hs.frame_capacity()
-        return [c for c in (1, 2, 3, 4, 6, 8) if self.P * c <= cap]
+        sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+        sizes = {self.P * c for c in (1, 2, 3, 4, 6, 8)} | {sms * k for k in range(1, 9)} | {cap}
+        return sorted(n for n in sizes if self.P <= n <= cap)
 
     def autotune(self, obs: hs.Obs, seed_pose: torch.Tensor, reps: int = 5) -> dict:
-        """Pick the fastest CTAs-per-particle for this workload (whole frames from
+        """Pick the fastest grid size for this workload (whole frames from
         seed_pose, timed with CUDA events) and use it from now on; returns the
         timing table (us per frame).  Leaves the tracker's state as it was."""
         saved = [t.clone() for t in self._state()]
         keep = self.ctas
         table = {}
-        for c in self.candidates():
-            self.ctas = c
+        for n in self.candidates():
+            self.ctas = n
             self.enqueue_frame(obs, 0, seed_pose)  # warm
             t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             t0.record()
@@ -184,8 +187,8 @@ class FrameTracker(Tracker):
                 self.enqueue_frame(obs, 0, seed_pose)
             t1.record()
             t1.synchronize()
-            table[f"frame/c{c}"] = 1e3 * t0.elapsed_time(t1) / reps
-        self.ctas = min(self.candidates(), key=lambda c: table[f"frame/c{c}"]) if table else keep
+            table[f"frame/n{n}"] = 1e3 * t0.elapsed_time(t1) / reps
+        self.ctas = min(self.candidates(), key=lambda n: table[f"frame/n{n}"]) if table else keep
         for t, v in zip(self._state(), saved):
             t.copy_(v)
         self.swarm.x = self.x_buf[0]

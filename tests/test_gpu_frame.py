@@ -44,6 +44,12 @@ def _state(tr):
                 prims=tr.prims, kc=tr.kc)
 
 
+def _counter_words(P):
+    """int32 words of the frame workspace that every call leaves zeroed (the
+    control block and three slots of per-particle sums)."""
+    return (128 + 3 * 32 * P) // 4
+
+
 def _run(tr, obs, frames, start):
     out = []
     for f in range(frames):
@@ -59,7 +65,9 @@ def _run(tr, obs, frames, start):
 @pytest.mark.parametrize("gens", [7, 4])
 def test_frame_equals_step_by_step(scene, gens):
     """Two frames (mutation after generations 3 and 6 when gens = 7; an even
-    count leaves the positions in the first buffer) at every CTA count."""
+    count leaves the positions in the first buffer) at several grid sizes: one
+    CTA per particle, sizes that are no multiple of P (uneven deals), the
+    device's capacity and the automatic choice."""
     W, H, P, seed, kw = SCENES[scene]
     sc = C.make_scene(W, H, P, seed, **kw)
     cam = hs.camera(*[float(v) for v in sc.cam])
@@ -67,16 +75,18 @@ def test_frame_equals_step_by_step(scene, gens):
     start = torch.from_numpy(sc.poses[-1]).cuda()
     ref = _run(T.Tracker(sc.model_g, cam, P=P, gens=gens, seed=seed), obs, 2, start)
     ft = T.FrameTracker(sc.model_g, cam, P=P, gens=gens, seed=seed)
-    counts = ft.candidates()
-    assert counts and counts[0] == 1
-    for c in counts[:4]:
-        ft = T.FrameTracker(sc.model_g, cam, P=P, gens=gens, seed=seed, ctas_per_particle=c)
+    cand = ft.candidates()
+    cap = hs.frame_capacity()
+    assert cand and cand[0] == P and cand[-1] == cap
+    sizes = sorted({P, 2 * P + 1, 3 * P - 1, cap} & set(range(P, cap + 1))) + [0]
+    for n in sizes:
+        ft = T.FrameTracker(sc.model_g, cam, P=P, gens=gens, seed=seed, ctas=n)
         got = _run(ft, obs, 2, start)
         for f in range(2):
             for k in ref[f]:
-                assert np.array_equal(got[f][k], ref[f][k], equal_nan=True), (c, f, k)
-        # the workspace is left zeroed for the next frame
-        assert int(ft.fws.abs().sum()) == 0, c
+                assert np.array_equal(got[f][k], ref[f][k], equal_nan=True), (n, f, k)
+        # the counters and sums are left zeroed for the next frame
+        assert int(ft.fws[:_counter_words(P)].abs().sum()) == 0, n
     assert hs.hs_get_device_status(clear=True) == 0
     # the search made progress
     assert ref[-1]["gbest_E"][0] <= ref[0]["gbest_E"][0]
@@ -93,12 +103,12 @@ def test_frame_at_the_capacity_limit():
     obs = hs.Obs.from_numpy(sc.Od, sc.S, torch.device("cuda"))
     start = torch.from_numpy(sc.gt).cuda()
     ref = _run(T.Tracker(sc.model_g, cam, P=P, gens=3, seed=9), obs, 1, start)
-    ft = T.FrameTracker(sc.model_g, cam, P=P, gens=3, seed=9, ctas_per_particle=1)
+    ft = T.FrameTracker(sc.model_g, cam, P=P, gens=3, seed=9, ctas=P)
     got = _run(ft, obs, 1, start)
     for k in ref[0]:
         assert np.array_equal(got[0][k], ref[0][k], equal_nan=True), k
     if P < hs.FRAME_MAX_PARTICLES:
-        big = T.FrameTracker(sc.model_g, cam, P=P + 1, gens=3, seed=9, ctas_per_particle=1)
+        big = T.FrameTracker(sc.model_g, cam, P=P + 1, gens=3, seed=9, ctas=P + 1)
         with pytest.raises(hs.HandscoreError) as e:
             big.run_frame(obs, 0, start)
         assert e.value.status == hs.HS_ERR_SIZE
@@ -114,7 +124,7 @@ def test_first_generation_against_oracle():
     sc = C.make_scene(W, H, P, seed, noisy=True, f32=False)
     cam = hs.camera(*[float(v) for v in sc.cam])
     obs = hs.Obs.from_numpy(sc.Od, sc.S, torch.device("cuda"))
-    ft = T.FrameTracker(sc.model_g, cam, P=P, gens=1, seed=seed, ctas_per_particle=2)
+    ft = T.FrameTracker(sc.model_g, cam, P=P, gens=1, seed=seed, ctas=2 * P + 3)
     start = torch.from_numpy(sc.gt).cuda()
     ft.run_frame(obs, 0, start)
     torch.cuda.synchronize()
@@ -131,16 +141,19 @@ def test_frame_rejects_bad_arguments():
     obs = hs.Obs.from_numpy(sc.Od, sc.S, torch.device("cuda"))
     ft = T.FrameTracker(sc.model_g, cam, P=8, gens=3, seed=1)
     start = torch.from_numpy(sc.gt).cuda()
-    with pytest.raises(hs.HandscoreError) as e:  # more CTAs per particle than the device holds
-        hs.track_frame(ft.model, obs, cam, ft.swarm, ft.x_buf[1], 3, ft.score, ft.pso, start, ft.scale, 1, 0,
-                       64 if 8 * 64 > hs.frame_capacity() else 65, ft.fws, ft.kc)
-    assert e.value.status in (hs.HS_ERR_SIZE, hs.HS_ERR_ARG)
+    for n, status in ((hs.frame_capacity() + 1, hs.HS_ERR_SIZE),  # more CTAs than the device holds
+                      (7, hs.HS_ERR_SIZE),                       # fewer CTAs than particles
+                      (-1, hs.HS_ERR_ARG)):
+        with pytest.raises(hs.HandscoreError) as e:
+            hs.track_frame(ft.model, obs, cam, ft.swarm, ft.x_buf[1], 3, ft.score, ft.pso, start, ft.scale, 1, 0,
+                           n, ft.fws, ft.kc)
+        assert e.value.status == status, n
     with pytest.raises(hs.HandscoreError) as e:  # workspace too small
-        hs.track_frame(ft.model, obs, cam, ft.swarm, ft.x_buf[1], 3, ft.score, ft.pso, start, ft.scale, 1, 0, 1,
+        hs.track_frame(ft.model, obs, cam, ft.swarm, ft.x_buf[1], 3, ft.score, ft.pso, start, ft.scale, 1, 0, 8,
                        ft.fws[:4], ft.kc)
     assert e.value.status == hs.HS_ERR_SIZE
     with pytest.raises(hs.HandscoreError) as e:  # positions must be double-buffered
-        hs.track_frame(ft.model, obs, cam, ft.swarm, ft.swarm.x, 3, ft.score, ft.pso, start, ft.scale, 1, 0, 1,
+        hs.track_frame(ft.model, obs, cam, ft.swarm, ft.swarm.x, 3, ft.score, ft.pso, start, ft.scale, 1, 0, 8,
                        ft.fws, ft.kc)
     assert e.value.status == hs.HS_ERR_ARG
     torch.cuda.synchronize()

@@ -101,7 +101,7 @@ def test_frame_equals_step_by_step_with_penetration_term():
     start = torch.from_numpy(sc.poses[-1]).cuda()
     out = []
     for tr in (T.Tracker(sc.model_g, cam, P=32, gens=6, seed=5),
-               T.FrameTracker(sc.model_g, cam, P=32, gens=6, seed=5, ctas_per_particle=2)):
+               T.FrameTracker(sc.model_g, cam, P=32, gens=6, seed=5, ctas=70)):
         tr.run_frame(obs, 0, start, graph=False)
         torch.cuda.synchronize()
         out.append([t.cpu().numpy().copy() for t in (tr.swarm.x, tr.swarm.gbest, tr.swarm.gbest_E, tr.kc, tr.prims)])

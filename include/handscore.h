@@ -54,6 +54,7 @@ typedef struct CUstream_st* hs_stream_t;
 #define HS_NDOF            26
 #define HS_MAX_BONES       32
 #define HS_MAX_PRIMS       64
+#define HS_MAX_DEPTH       7      /* bone chains: the palm at depth 0, its descendants at most this deep */
 #define HS_MAX_PARTICLES   65535  /* particles per call (the render grid's y extent) */
 #define HS_MAX_ROI         8192   /* W, H <= HS_MAX_ROI */
 
@@ -231,7 +232,8 @@ const char* hs_status_string(int status);
 /* Validate a model descriptor (Section II.A) and copy it into an opaque host
  * object.  Allocates host memory only.  Errors: HS_ERR_ARG (NULL, bad parent
  * order, bad dof index, bad kind, non-positive or non-finite dims, |kappa| >= 1,
- * lo > hi), HS_ERR_SIZE (counts out of range). */
+ * lo > hi), HS_ERR_SIZE (counts out of range, a bone deeper than
+ * HS_MAX_DEPTH). */
 int hs_model_create(const HsModelDesc* desc, HsModel** out);
 int hs_model_destroy(HsModel* model);
 /* Select the kc variant of a model (see HsKcParams).  Errors: HS_ERR_ARG (NULL,

@@ -231,6 +231,12 @@ int hs_model_create(const HsModelDesc* d, HsModel** out)
                              -sy,     cy * sx,                cy * cx};
         for (int i = 0; i < 9; ++i) o.rest[i] = (float)R[i];
     }
+    if (!bad && max_depth > HS_MAX_DEPTH) return HS_ERR_SIZE;
+    for (int b = 0; !bad && b < d->n_bones; ++b) {  // the path from the palm, for FK's one-pass chains
+        DevBone& o = dm.bones[b];
+        for (int k = 0; k < kMaxChain; ++k) o.anc[k] = 0;
+        for (int k = o.depth, a = b; k >= 0; --k, a = dm.bones[a].parent) o.anc[k] = (int8_t)a;
+    }
     dm.max_depth = max_depth;
     for (int k = 0; k < d->n_prims; ++k) {
         const HsPrimDesc& P = d->prims[k];

@@ -55,7 +55,7 @@ struct FrameShared {
     int red_i[kFrameWarps], red_r[kFrameWarps];
     int gprev;  // the swarm's global best after the previous generation
     uint32_t st[2];
-    int box[4];
+    int4 wbox[2];  // union of the pixel boxes of primitives 0..31 and 32..63
 };
 
 // all threads of every CTA: returns false if the wait ran out.  work() runs
@@ -195,14 +195,28 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
             d[3] = R.q3;
             d[4] = R.q4;
             sh.pbox[j] = make_int2(__float_as_int(rec[14]), __float_as_int(rec[15]));
+            // the union of the pixel boxes, per warp of record threads
+            const int w = j >> 5;
+            const uint32_t mask = n_prims >= 32 * (w + 1) ? 0xffffffffu : (1u << (n_prims - 32 * w)) - 1u;
+            const int u0 = __reduce_min_sync(mask, lo_i16(rec[14])), v0 = __reduce_min_sync(mask, hi_i16(rec[14]));
+            const int u1 = __reduce_max_sync(mask, lo_i16(rec[15])), v1 = __reduce_max_sync(mask, hi_i16(rec[15]));
+            if ((j & 31) == 0) sh.wbox[w] = make_int4(u0, v0, u1, v1);
         });
         __syncthreads();
-        if (warp == 0) unit_box(sh.rec, n_prims, a.W, a.H, lane, sh.box);
-        __syncthreads();
+        // the particle's units (every thread forms the same box)
+        int box[4];
+        {
+            int4 b = sh.wbox[0];
+            if (n_prims > 32) {
+                const int4 b1 = sh.wbox[1];
+                b = make_int4(min(b.x, b1.x), min(b.y, b1.y), max(b.z, b1.z), max(b.w, b1.w));
+            }
+            unit_box_clip(b.x, b.y, b.z, b.w, a.W, a.H, box);
+        }
         long long acc_t = 0;
         uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
-        if (sh.box[3] > 0)
-            render_units_warp(sh.rast, sh.pbox, n_prims, sh.box, sh.tile[warp], sh.bar[warp], phases,
+        if (box[3] > 0)
+            render_units_warp(sh.rast, sh.pbox, n_prims, box, sh.tile[warp], sh.bar[warp], phases,
                               c * kFrameWarps + warp, C * kFrameWarps, pv, ra, p, lane, acc_t, acc_a, acc_o, acc_h);
         warp_sum(acc_t, acc_a, acc_o, acc_h);
         if (lane == 0) {
@@ -265,7 +279,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
             pbi = sh.pb[t];
             vi = sh.v[t];
         }
-        const StepOut o = swarm_update<kFrameThreads>(R, p, p, 0, P, 0, a.n_mutate, s_e, s_pe, sh.r, sh.m,
+        const StepOut o = swarm_update<kFrameThreads, true>(R, p, p, 0, P, 0, a.n_mutate, s_e, s_pe, sh.r, sh.m,
                                                       sh.fk.model.lo, sh.fk.model.hi, xi, pbi, vi, sh.pe, primary,
                                                       sh.red_v, sh.red_i, sh.red_r, guess);
         __syncthreads();  // every thread has read sh.x / sh.pe of this generation

@@ -17,10 +17,12 @@ constexpr int kMaxBones = HS_MAX_BONES;
 constexpr int kMaxPrims = HS_MAX_PRIMS;
 constexpr float kEllipsoidMarker = 2.0f;  // HsPrim.m[13] value that marks an ellipsoid
 
+constexpr int kMaxChain = HS_MAX_DEPTH + 1;  // bones on a path from the palm
 struct DevBone {
     int32_t parent, dof_z, dof_x, depth;  // depth in the tree (palm = 0)
     float off[3];
     float rest[9];                        // row-major Rz Ry Rx of the rest angles
+    int8_t anc[kMaxChain];                // anc[k]: its ancestor at depth k (anc[depth] = the bone)
 };
 
 struct DevPrimDesc {

@@ -38,6 +38,38 @@ __device__ __forceinline__ void mat3_mul(const float* a, const float* b, float* 
             c[3 * r + k] = fmaf(a[3 * r], b[k], fmaf(a[3 * r + 1], b[3 + k], a[3 * r + 2] * b[6 + k]));
 }
 
+// local rotation of the palm: diag(1, -1, -1) Rz(q5) Ry(q4) Rx(q3), from the
+// sines and cosines of the angles
+__device__ __forceinline__ void palm_local(const float* sn, const float* cs, float* R)
+{
+    const float sx = sn[3], cx = cs[3], sy = sn[4], cy = cs[4], sz = sn[5], cz = cs[5];
+    const float Rz[9] = {cz, -sz, 0.f, sz, cz, 0.f, 0.f, 0.f, 1.f};
+    const float Ry[9] = {cy, 0.f, sy, 0.f, 1.f, 0.f, -sy, 0.f, cy};
+    const float Rx[9] = {1.f, 0.f, 0.f, 0.f, cx, -sx, 0.f, sx, cx};
+    float T[9];
+    mat3_mul(Rz, Ry, T);
+    mat3_mul(T, Rx, R);
+#pragma unroll
+    for (int k = 3; k < 9; ++k) R[k] = -R[k];
+}
+
+// local rotation of a finger bone: rest Rz(theta_z) Rx(theta_x) (a missing
+// degree of freedom is a zero angle)
+__device__ __forceinline__ void bone_local(const DevBone& B, const float* sn, const float* cs, float* R)
+{
+    float sz = 0.f, cz = 1.f, sx = 0.f, cx = 1.f;
+    if (B.dof_z >= 0) {
+        sz = sn[B.dof_z];
+        cz = cs[B.dof_z];
+    }
+    if (B.dof_x >= 0) {
+        sx = sn[B.dof_x];
+        cx = cs[B.dof_x];
+    }
+    const float ZX[9] = {cz, -sz * cx, sz * sx, sz, cz * cx, -cz * sx, 0.f, sx, cx};  // Rz Rx
+    mat3_mul(B.rest, ZX, R);
+}
+
 __device__ __forceinline__ int clamp_i16(float v)
 {
     return (int)fminf(fmaxf(v, -32767.0f), 32767.0f);
@@ -58,8 +90,6 @@ __device__ __forceinline__ void fk_load_model(FkShared& sh, const DevModelCore& 
     for (int i = threadIdx.x; i < bone_words; i += blockDim.x) dstw[bones0 + i] = srcw[bones0 + i];
 }
 
-// FK of the raw pose `pose` [26] (global or shared memory): writes the particle's
-// n_prims records to prims [n_prims][4] and kc.  cam = (fx, fy, cx, cy).  Every
 // Widen [amin, amax] x [bmin, bmax] by the ray-direction range (a = x/z,
 // b = y/z) of the solid ellipse(s) {C + A w : |w| <= 1} with A A^T = Sg
 // (xx, yy, zz, xy, xz, yz).  A plane through the camera with normal n touches
@@ -67,19 +97,21 @@ __device__ __forceinline__ void fk_load_model(FkShared& sh, const DevModelCore& 
 // a^2 (Cz^2 - Szz) - 2 a (Cx Cz - Sxz) + (Cx^2 - Sxx) = 0, whose roots are the
 // exact bounds.  Its discriminant is expanded so that the ~Cz^2 Cx^2 terms
 // cancel symbolically.  Returns false unless the solid lies beyond the plane
-// z = 1 mm.
+// z = 1 mm.  The box made from these bounds keeps a pixel of margin on every
+// side, so approximate square roots and reciprocals (relative error ~1e-7)
+// cannot make it miss a covered pixel.
 __device__ __forceinline__ bool ellipse_ray_bounds(const float C[3], const float Sg[6], float& amin, float& amax,
                                                    float& bmin, float& bmax)
 {
-    const float ez = sqrtf(fmaxf(Sg[2], 0.f));  // z half-extent
+    const float ez = sqrt_approx(fmaxf(Sg[2], 0.f));  // z half-extent
     if (!(C[2] - ez >= 1.0f)) return false;
     const float al = fmaf(C[2], C[2], -Sg[2]);
-    const float ial = __frcp_rn(al);  // correctly rounded, as 1 / al
+    const float ial = rcp_approx(al);
     {
         const float be = fmaf(C[0], C[2], -Sg[4]);
         const float disc = fmaf(Sg[0], C[2] * C[2], fmaf(-2.f * Sg[4], C[0] * C[2], fmaf(Sg[2], C[0] * C[0],
                                 fmaf(Sg[4], Sg[4], -Sg[0] * Sg[2]))));
-        const float sq = sqrtf(fmaxf(disc, 0.f));
+        const float sq = sqrt_approx(fmaxf(disc, 0.f));
         amin = fminf(amin, (be - sq) * ial);
         amax = fmaxf(amax, (be + sq) * ial);
     }
@@ -87,14 +119,16 @@ __device__ __forceinline__ bool ellipse_ray_bounds(const float C[3], const float
         const float be = fmaf(C[1], C[2], -Sg[5]);
         const float disc = fmaf(Sg[1], C[2] * C[2], fmaf(-2.f * Sg[5], C[1] * C[2], fmaf(Sg[2], C[1] * C[1],
                                 fmaf(Sg[5], Sg[5], -Sg[1] * Sg[2]))));
-        const float sq = sqrtf(fmaxf(disc, 0.f));
+        const float sq = sqrt_approx(fmaxf(disc, 0.f));
         bmin = fminf(bmin, (be - sq) * ial);
         bmax = fmaxf(bmax, (be + sq) * ial);
     }
     return true;
 }
 
-// thread of the 64-thread CTA must call it (it synchronises the CTA).
+// FK of the raw pose `pose` [26] (global or shared memory): writes the particle's
+// n_prims records to prims [n_prims][4] and kc.  cam = (fx, fy, cx, cy).  Every
+// thread of the CTA must call it (it synchronises the CTA).
 // emit(j, rec) is called by the thread that formed primitive j's record
 // (float[16], as stored), e.g. to derive more from it while it is in registers.
 struct NoEmit {
@@ -130,57 +164,59 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const DevModel* mp, co
     }
     __syncthreads();
 
-    // local rotation of each bone
-    if (t < model.n_bones) {
-        float R[9];
-        if (t == 0) {
-            // palm: diag(1,-1,-1) * Rz(q5) Ry(q4) Rx(q3)
-            const float sx = sh.sn[3], cx = sh.cs[3], sy = sh.sn[4], cy = sh.cs[4], sz = sh.sn[5], cz = sh.cs[5];
-            const float Rz[9] = {cz, -sz, 0.f, sz, cz, 0.f, 0.f, 0.f, 1.f};
-            const float Ry[9] = {cy, 0.f, sy, 0.f, 1.f, 0.f, -sy, 0.f, cy};
-            const float Rx[9] = {1.f, 0.f, 0.f, 0.f, cx, -sx, 0.f, sx, cx};
-            float T[9];
-            mat3_mul(Rz, Ry, T);
-            mat3_mul(T, Rx, R);
-#pragma unroll
-            for (int k = 3; k < 9; ++k) R[k] = -R[k];
-        } else {
-            const DevBone& B = model.bones[t];
-            float sz = 0.f, cz = 1.f, sx = 0.f, cx = 1.f;
-            if (B.dof_z >= 0) {
-                sz = sh.sn[B.dof_z];
-                cz = sh.cs[B.dof_z];
-            }
-            if (B.dof_x >= 0) {
-                sx = sh.sn[B.dof_x];
-                cx = sh.cs[B.dof_x];
-            }
-            const float ZX[9] = {cz, -sz * cx, sz * sx, sz, cz * cx, -cz * sx, 0.f, sx, cx};  // Rz Rx
-            mat3_mul(B.rest, ZX, R);
-        }
-#pragma unroll
-        for (int k = 0; k < 9; ++k) lR[t][k] = R[k];
-    }
-    __syncthreads();
-    // global frame of each bone: one thread per bone walks its chain down from
-    // the root, G_k = G_{k-1} lR[a_k] and P_k = G_{k-1} off[a_k] + P_{k-1}, the
-    // same products in the same order as composing level by level, without a
-    // barrier per level (positions relative to the wrist; its translation is
-    // added once per primitive)
+    // frame of each bone: one thread per bone composes its path from the palm,
+    // G_k = G_{k-1} L(a_k) and P_k = G_{k-1} off(a_k) + P_{k-1} (a_k its
+    // ancestor at depth k), forming each local rotation L from the angles'
+    // sines and cosines as it goes: no barrier per level, none between local
+    // and global frames (positions relative to the wrist; its translation is
+    // added once per primitive).  Each thread also keeps its own L in lR.
     if (t < model.n_bones) {
         float G[9], P[3] = {0.f, 0.f, 0.f};
+        palm_local(sh.sn, sh.cs, G);
+        const DevBone& Bt = model.bones[t];
+        const int d = Bt.depth;
+        if (t == 0) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) G[k] = lR[0][k];
-        const int d = model.bones[t].depth;
-        for (int k = 1; k <= d; ++k) {
-            int a = t;  // the ancestor of t at depth k
-            while (model.bones[a].depth > k) a = model.bones[a].parent;
-            const DevBone& B = model.bones[a];
-            float Pn[3], Gn[9];
+            for (int k = 0; k < 9; ++k) lR[0][k] = G[k];
+        }
+        // levels 1..3 (a hand's fingers are three bones deep): their local
+        // rotations first (anc[k] is the palm beyond the bone's depth, so the
+        // reads stay in bounds and need no branch), then the products
+        constexpr int kFast = 3;
+        float L[kFast][9];
+#pragma unroll
+        for (int k = 0; k < kFast; ++k) bone_local(model.bones[Bt.anc[k + 1]], sh.sn, sh.cs, L[k]);
+#pragma unroll
+        for (int k = 1; k <= kFast; ++k) {
+            if (k <= d) {
+                const DevBone& B = model.bones[Bt.anc[k]];
+                float Gn[9], Pn[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    Pn[i] = fmaf(G[3 * i], B.off[0], fmaf(G[3 * i + 1], B.off[1], fmaf(G[3 * i + 2], B.off[2], P[i])));
+                mat3_mul(G, L[k - 1], Gn);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) P[i] = Pn[i];
+#pragma unroll
+                for (int k2 = 0; k2 < 9; ++k2) G[k2] = Gn[k2];
+            }
+            if (k == d) {
+#pragma unroll
+                for (int q2 = 0; q2 < 9; ++q2) lR[t][q2] = L[k - 1][q2];
+            }
+        }
+        for (int k = kFast + 1; k <= d; ++k) {  // deeper chains, level by level
+            const DevBone& B = model.bones[Bt.anc[k]];
+            float Lk[9], Gn[9], Pn[3];
+            bone_local(B, sh.sn, sh.cs, Lk);
+            if (k == d) {
+#pragma unroll
+                for (int q2 = 0; q2 < 9; ++q2) lR[t][q2] = Lk[q2];
+            }
 #pragma unroll
             for (int i = 0; i < 3; ++i)
                 Pn[i] = fmaf(G[3 * i], B.off[0], fmaf(G[3 * i + 1], B.off[1], fmaf(G[3 * i + 2], B.off[2], P[i])));
-            mat3_mul(G, lR[a], Gn);
+            mat3_mul(G, Lk, Gn);
 #pragma unroll
             for (int i = 0; i < 3; ++i) P[i] = Pn[i];
 #pragma unroll

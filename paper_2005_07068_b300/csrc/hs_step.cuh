@@ -157,6 +157,38 @@ __device__ __forceinline__ SwarmBest swarm_best(int P, int i, bool mutate, const
     return b;
 }
 
+// The same from one warp alone: every warp of the caller computes it over all
+// P particles and every lane gets the result, with no shared memory and no
+// barrier (the order is total -- pbest_E is never NaN, so min(E, pbest_E) is
+// not either -- so every lane's reduction ends at the same argmin).
+__device__ __forceinline__ SwarmBest swarm_best_warp(int P, int i, bool mutate, const float* s_e, const float* s_pe)
+{
+    const int lane = threadIdx.x & 31;
+    const float ei = s_e[i];
+    float bv = INFINITY;
+    int bi = INT_MAX, rank = 0;
+    for (int j = lane; j < P; j += 32) {
+        const float ej = s_e[j], pj = s_pe[j];
+        const float pe = ej < pj ? ej : pj;
+        if (bi == INT_MAX || pe < bv) {
+            bv = pe;
+            bi = j;
+        }
+        if (mutate) rank += ranks_before(ej, j, ei, i);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi != INT_MAX && (bi == INT_MAX || ov < bv || (ov == bv && oi < bi))) {
+            bv = ov;
+            bi = oi;
+        }
+        rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    }
+    return SwarmBest{bi, bv, rank};
+}
+
 // dimension t of the global best's position: its current x if that is its
 // personal best now, else its pbest (read through L2: another CTA of a
 // resident grid may have written them)
@@ -192,7 +224,9 @@ __device__ __forceinline__ StepOut swarm_move(float c1, float c2, float w, bool 
 // t (t < 26) and own_pe its own pbest_E, from a copy no other thread writes.
 // When `store`, writes the particle's v, x_next, pbest / pbest_E (on
 // improvement) and, for i == 0, the swarm's gbest.  guess: see GbestGuess.
-template <int NT>
+// kWarpBest: every warp finds the global best on its own (swarm_best_warp),
+// else the NT threads share the scan (swarm_best); the result is the same.
+template <int NT, bool kWarpBest = false>
 __device__ __forceinline__ StepOut swarm_update(const SwarmRefs& R, int q, int i, int off, int P, int s, int n_mutate,
                                                 const float* s_e, const float* s_pe, const float* s_r,
                                                 const float* s_m, const float* lo, const float* hi, float xi,
@@ -200,7 +234,8 @@ __device__ __forceinline__ StepOut swarm_update(const SwarmRefs& R, int q, int i
                                                 int* red_i, int* red_r, const GbestGuess& guess = GbestGuess{-1, 0.f, 0.f})
 {
     const int t = threadIdx.x;
-    const SwarmBest b = swarm_best<NT>(P, i, R.mutate, s_e, s_pe, red_v, red_i, red_r);
+    const SwarmBest b = kWarpBest ? swarm_best_warp(P, i, R.mutate, s_e, s_pe)
+                                  : swarm_best<NT>(P, i, R.mutate, s_e, s_pe, red_v, red_i, red_r);
     const float ei = s_e[i];
     StepOut out{0.f, 0.f, 0.f, ei < own_pe, b.g};  // strict improvement of this particle's personal best
     const bool mutated = R.mutate && b.rank >= P - n_mutate;

@@ -46,9 +46,26 @@ __device__ __forceinline__ void stage_prims(const float4* rec, int n_prims, cons
     }
 }
 
-// one warp: the particle's screen box clipped to the ROI, in 16x4 units:
-// box = (xa, v0, units per row, units); xa is a multiple of 16 (TMA: the uint8
-// skin needs x at a multiple of 16 bytes); 0 units when nothing is in the ROI
+// the particle's pixel box (u0, v0)-(u1, v1) clipped to the ROI, in 16x4
+// units: box = (xa, v0, units per row, units); xa is a multiple of 16 (TMA:
+// the uint8 skin needs x at a multiple of 16 bytes); 0 units when nothing is
+// in the ROI
+__device__ __forceinline__ void unit_box_clip(int u0, int v0, int u1, int v1, int W, int H, int* box)
+{
+    u0 = max(u0, 0);
+    v0 = max(v0, 0);
+    u1 = min(u1, W - 1);
+    v1 = min(v1, H - 1);
+    const int xa = u0 & ~15;
+    const bool empty = u0 > u1 || v0 > v1;
+    const int nux = empty ? 1 : (u1 + 1 - xa + kUW - 1) / kUW;
+    box[0] = xa;
+    box[1] = v0;
+    box[2] = nux;
+    box[3] = empty ? 0 : nux * ((v1 - v0 + kUH) / kUH);
+}
+
+// one warp: the union of the primitives' pixel boxes, clipped (unit_box_clip)
 __device__ __forceinline__ void unit_box(const float4* rec, int n_prims, int W, int H, int lane, int* box)
 {
     int u0 = INT_MAX, v0 = INT_MAX, u1 = INT_MIN, v1 = INT_MIN;
@@ -66,19 +83,7 @@ __device__ __forceinline__ void unit_box(const float4* rec, int n_prims, int W, 
         u1 = max(u1, __shfl_xor_sync(0xffffffffu, u1, o));
         v1 = max(v1, __shfl_xor_sync(0xffffffffu, v1, o));
     }
-    if (lane == 0) {
-        u0 = max(u0, 0);
-        v0 = max(v0, 0);
-        u1 = min(u1, W - 1);
-        v1 = min(v1, H - 1);
-        const int xa = u0 & ~15;
-        const bool empty = u0 > u1 || v0 > v1;
-        const int nux = empty ? 1 : (u1 + 1 - xa + kUW - 1) / kUW;
-        box[0] = xa;
-        box[1] = v0;
-        box[2] = nux;
-        box[3] = empty ? 0 : nux * ((v1 - v0 + kUH) / kUH);
-    }
+    if (lane == 0) unit_box_clip(u0, v0, u1, v1, W, H, box);
 }
 
 // the sub-block masks of unit (x0, y0): bit j of m[s] = primitive j's box

@@ -109,6 +109,28 @@ def test_model_validation():
     assert L.hs_model_create(None, None) == hs.HS_ERR_ARG
 
 
+def test_model_chain_depth_limit():
+    """Bone chains up to HS_MAX_DEPTH (7) below the palm are accepted, deeper
+    ones are refused with HS_ERR_SIZE (FK composes each bone's path from the
+    palm in one pass, from a table of at most 8 ancestors)."""
+    g = I.hand_geometry()
+    lo, hi = I.search_limits()
+    for depth, ok in ((7, True), (8, False)):
+        bi = np.zeros((depth + 1, 3), np.int32)
+        bi[:, 1:] = -1           # no degrees of freedom
+        bi[1:, 0] = np.arange(depth)  # bone b hangs from bone b - 1
+        bf = np.zeros((depth + 1, 6), np.float32)
+        bf[1:, 1] = 10.0         # 10 mm along y per bone
+        pi = np.array([[depth, g.prims_i[0, 1]]], np.int32)
+        pf = g.prims_f[:1].copy()
+        if ok:
+            assert hs.Model(bi, bf, pi, pf, lo, hi).handle
+        else:
+            with pytest.raises(hs.HandscoreError) as e:
+                hs.Model(bi, bf, pi, pf, lo, hi)
+            assert e.value.status == hs.HS_ERR_SIZE
+
+
 def test_workspace_size():
     n = hs.workspace_size(64)
     assert n >= 64 * 16

@@ -78,9 +78,10 @@ def proxies(model: O.Model, fk: dict):
     return np.array(C), np.array(r), np.array(f), np.array(fixed, bool)
 
 
-def penetration_of(C, r, f, fixed=None) -> float:
+def penetration_of(C, r, f, fixed=None):
     """sum over pairs on different fingers (both >= 0), not both fixed to the
-    palm, of max(0, r_i + r_j - d_ij)."""
+    palm, of max(0, r_i + r_j - d_ij).  Centres may be complex (the complex
+    step below): the max is then decided on the real part."""
     pen = 0.0
     n = len(r)
     if fixed is None:
@@ -89,14 +90,37 @@ def penetration_of(C, r, f, fixed=None) -> float:
         for j in range(i + 1, n):
             if f[i] < 0 or f[j] < 0 or f[i] == f[j] or (fixed[i] and fixed[j]):
                 continue
-            d = float(np.sqrt(np.sum((C[i] - C[j]) ** 2)))
-            pen += max(0.0, r[i] + r[j] - d)
-    return pen
+            d = np.sqrt(np.sum((C[i] - C[j]) ** 2))
+            v = r[i] + r[j] - d
+            if np.real(v) > 0.0:
+                pen = pen + v
+    return pen if np.iscomplexobj(pen) else float(pen)
 
 
 def penetration(model: O.Model, pose) -> float:
     fk = O.fk(model, pose)
     return penetration_of(*proxies(model, fk))
+
+
+def kc_variant_gradient(model: O.Model, pose, variant: int, w: float, h: float = 1e-30) -> np.ndarray:
+    """d kc_variant / d pose [26] by the complex step: the pose is perturbed
+    by i h in one dimension at a time and carried through the FK of
+    oracle.soft (which takes complex poses), the proxies and the sum above;
+    the imaginary part over h is the derivative (no cancellation, exact to
+    rounding where the function is smooth)."""
+    from . import soft as OS
+
+    pose = np.asarray(pose, np.float64)
+    g = np.zeros(pose.shape[0])
+    for k in range(pose.shape[0]):
+        pc = pose.astype(complex)
+        pc[k] += 1j * h
+        _, pR, pC, kc = OS.fk(model, pc)
+        val = 0.0 if variant == 2 else kc
+        if variant != 0:
+            val = val + w * penetration_of(*proxies(model, {"prim_R": pR, "prim_C": pC}))
+        g[k] = np.imag(val) / h
+    return g
 
 
 def kc_variant(model: O.Model, pose, variant: int, w: float) -> float:

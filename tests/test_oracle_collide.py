@@ -145,3 +145,66 @@ def test_variants(i):
     assert K.kc_variant(MODEL, p, 0, 0.05) == pytest.approx(k0, abs=1e-15)
     assert K.kc_variant(MODEL, p, 2, 1.0) == pytest.approx(pen, abs=1e-12)
     assert K.kc_variant(MODEL, p, 1, 0.05) == pytest.approx(k0 + 0.05 * pen, abs=1e-12)
+
+
+def _penetrating_pose(seed, swing):
+    """Nearly straight fingers (every flexion 0.05 rad, strictly inside its
+    limits, so that the clamp is not at a corner) with the index swung by
+    `swing` rad toward the middle finger, the palm and wrist from a seeded
+    sample: the index and middle proxies interpenetrate."""
+    p = I.sample_poses(np.random.default_rng(seed), 1, LO, HI)[0]
+    p[6:] = 0.05
+    p[[11, 15, 19, 23]] = [swing, 0.0, math.radians(-15), math.radians(-25)]
+    assert np.all(p > LO) and np.all(p < HI)
+    return p
+
+
+def _min_threshold_gap(p):
+    """Smallest | r_i + r_j - d_ij | over the counted pairs: how far the pose
+    is from a kink of pen (where one pair starts or stops touching)."""
+    C, r, f, fixed = K.proxies(MODEL, oracle.fk(MODEL, p))
+    gaps = [abs(r[i] + r[j] - np.linalg.norm(C[i] - C[j]))
+            for i in range(len(r)) for j in range(i + 1, len(r))
+            if f[i] >= 0 and f[j] >= 0 and f[i] != f[j] and not (fixed[i] and fixed[j])]
+    return min(gaps)
+
+
+@pytest.mark.parametrize("seed,swing", [(11, -0.12), (12, -0.18), (13, -0.24)])
+def test_penetration_gradient_against_central_differences(seed, swing):
+    """The complex-step gradient of kc + w pen (variant 1) against FP64 central
+    differences of the real function (h = 1e-6), at poses away from any kink;
+    the wrist translation does not move the proxies relative to each other, so
+    its three components are zero."""
+    p = _penetrating_pose(seed, swing)
+    assert K.penetration(MODEL, p) > 0.5
+    assert _min_threshold_gap(p) > 1e-3
+    w = 0.05
+    g = K.kc_variant_gradient(MODEL, p, 1, w)
+    fd = np.zeros(26)
+    for k in range(26):
+        a, b = p.copy(), p.copy()
+        a[k] += 1e-6
+        b[k] -= 1e-6
+        fd[k] = (K.kc_variant(MODEL, a, 1, w) - K.kc_variant(MODEL, b, 1, w)) / 2e-6
+    assert np.abs(g - fd).max() <= 1e-6 * max(1.0, np.abs(g).max()), np.abs(g - fd).max()
+    assert np.all(g[:3] == 0.0)
+    assert np.abs(g).max() > 0.01  # the term does move the fingers
+
+
+def test_variant_gradients_reduce_to_the_abduction_ordering():
+    """Variant 0's gradient is the abduction ordering's in closed form: for each
+    pair (a, b) of adjacent non-thumb fingers with q_b > q_a, -1 on q_a and +1 on
+    q_b; variant 2 carries no part of it."""
+    p = POSES[1].copy()
+    p[[11, 15, 19, 23]] = [-0.1, 0.05, -0.3, -0.1]  # (11,15) and (19,23) ordered the wrong way
+    assert np.all(p > LO) and np.all(p < HI)
+    g0 = K.kc_variant_gradient(MODEL, p, 0, 0.0)
+    want = np.zeros(26)
+    for a, b in ((11, 15), (15, 19), (19, 23)):
+        if p[b] > p[a]:
+            want[a] -= 1.0
+            want[b] += 1.0
+    assert np.array_equal(g0, want)
+    g1 = K.kc_variant_gradient(MODEL, p, 1, 0.05)
+    g2 = K.kc_variant_gradient(MODEL, p, 2, 0.05)
+    assert np.abs(g1 - (g0 + g2)).max() <= 1e-12

@@ -606,8 +606,6 @@ def run_fullframe(args, rank, world, local):
     model = hs.Model.from_geometry(g, lo, hi)
     if kc_var != hs.HS_KC_ABDUCTION:
         model.set_kc(kc_var, kc_w)
-        if "hybrid" in methods:
-            raise SystemExit("the hybrid polish needs the paper's kc (the penetration term has no gradient)")
     camt = I.kinect_camera(FULL_W, FULL_H)
     cam = hs.camera(camt.fx, camt.fy, camt.cx, camt.cy)
     frames = max(2, args.frames)

@@ -209,8 +209,9 @@ typedef struct {
  *   HS_KC_ABD_PEN   : the paper's kc + pen_weight * pen
  *   HS_KC_PEN       : pen_weight * pen
  * (pen_weight in rad per mm, so that lambda_k applies to both).  pose_fk,
- * pso_step_fk, track_frame and the batch calls return this kc; pose_grad
- * implements only HS_KC_ABDUCTION (HS_ERR_NOT_IMPL otherwise). */
+ * pso_step_fk, track_frame and the batch calls return this kc, and pose_grad
+ * differentiates it (d pen / d pose: each penetrating pair contributes the
+ * unit vector between its centres, moved by the bones' tangents). */
 #define HS_KC_ABDUCTION 0
 #define HS_KC_ABD_PEN   1
 #define HS_KC_PEN       2

@@ -750,7 +750,6 @@ int pose_grad(const HsModel* model, const float* poses, int P, const HsCamera* c
               HsPrim* prims, float* kc, int64_t* adj, float* grad, hs_stream_t stream)
 {
     if (!model || !poses || !params || !prims || !kc || !adj || !grad) return HS_ERR_ARG;
-    if (model->dev.kc_variant != HS_KC_ABDUCTION) return HS_ERR_NOT_IMPL;  // the penetration term has no adjoint here
     int rc = validate_cam(cam);
     if (rc) return rc;
     if ((rc = validate_score_params(params))) return rc;

@@ -596,20 +596,56 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
 
 // ---- pose gradient: record adjoints -> d E_s / d pose ------------------------------
 
-// (the paper's kc only: pose_grad refuses the kc variants, so the core model suffices)
-__global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ DevModelCore model_param,
-                                                       const GradArgs a)
+// fixed-point scale of the penetration adjoint d pen / d c (sums of unit vectors)
+constexpr double kPenGradFix = 4294967296.0;  // 2^32
+
+// Model: DevModelCore for the paper's kc, DevModel when the kc variant needs
+// the collision data (then the adjoint of the interpenetration term is added)
+template <class Model>
+__global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ Model model_param, const GradArgs a)
 {
     __shared__ FkShared sh;
+    __shared__ long long s_gc[kMaxProxies * 3];  // d pen / d (proxy centre), fixed point
     extern __shared__ float s_tan[];  // [26][n_bones][12]: dR (9), dP (3) of every bone for every DOF,
                                       // then [n_prims][26]: each primitive's contribution
     fk_load_model(sh, model_param);
     const int p = blockIdx.x, t = threadIdx.x;
     const float* pose = a.poses + (size_t)p * kNdof;
-    fk_particle(sh, nullptr, pose, make_float4(a.fx, a.fy, a.cx, a.cy), a.prims + (size_t)p * sh.model.n_prims * 4, a.kc + p,
+    const DevModel* mp = collide_data(model_param);
+    fk_particle(sh, mp, pose, make_float4(a.fx, a.fy, a.cx, a.cy), a.prims + (size_t)p * sh.model.n_prims * 4, a.kc + p,
                 a.status);
     __syncthreads();
     const int nb = sh.model.n_bones, np = sh.model.n_prims;
+    const bool pen_term = mp && sh.model.kc_variant != HS_KC_ABDUCTION;  // (uniform over the CTA)
+    if (pen_term) {
+        // d pen / d c_i = sum over the penetrating pairs (i, j) of -(c_i - c_j) / |c_i - c_j|
+        // (and + for c_j), the same pairs and the same test as the sum in FK;
+        // accumulated in fixed point so that the order of the pairs does not matter
+        for (int i = t; i < 3 * sh.model.n_proxies; i += 64) s_gc[i] = 0ll;
+        __syncthreads();
+        for (int k = t; k < sh.model.n_pairs; k += 64) {
+            const uint32_t ij = mp->pairs[k];
+            const int i = ij & 0xffu, j = ij >> 8;
+            const float4 ci = sh.pc[i], cj = sh.pc[j];
+            const float dx = ci.x - cj.x, dy = ci.y - cj.y, dz = ci.z - cj.z;
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)), rr = ci.w + cj.w;
+            if (d2 < rr * rr) {
+                const float d = sqrtf(d2);
+                if (rr - d > 0.f && d > 0.f) {
+                    const float id = 1.f / d;
+                    const long long ux = __double2ll_rn((double)(dx * id) * kPenGradFix);
+                    const long long uy = __double2ll_rn((double)(dy * id) * kPenGradFix);
+                    const long long uz = __double2ll_rn((double)(dz * id) * kPenGradFix);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&s_gc[3 * i]), (unsigned long long)(-ux));
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&s_gc[3 * i + 1]), (unsigned long long)(-uy));
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&s_gc[3 * i + 2]), (unsigned long long)(-uz));
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&s_gc[3 * j]), (unsigned long long)ux);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&s_gc[3 * j + 1]), (unsigned long long)uy);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&s_gc[3 * j + 2]), (unsigned long long)uz);
+                }
+            }
+        }
+    }
     float* s_contrib = s_tan + (size_t)kNdof * nb * 12;
     if (t < kNdof) {
         // tangents of every bone frame with respect to pose parameter t (parents first)
@@ -762,13 +798,33 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ D
         float g = 0.f;
         for (int j = 0; j < np; ++j) g += s_contrib[j * kNdof + t];  // fixed order: deterministic
         // kc(h) = sum over (11, 15), (15, 19), (19, 23) of max(q_b - q_a, 0)
-        const int pa[3] = {11, 15, 19}, pb[3] = {15, 19, 23};
+        // (not part of kc under HS_KC_PEN)
+        if (sh.model.kc_variant != HS_KC_PEN) {
+            const int pa[3] = {11, 15, 19}, pb[3] = {15, 19, 23};
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            if (sh.q[pa[i]] - sh.q[pb[i]] < 0.f) {
-                if (t == pa[i]) g -= a.lambda_k;
-                if (t == pb[i]) g += a.lambda_k;
+            for (int i = 0; i < 3; ++i) {
+                if (sh.q[pa[i]] - sh.q[pb[i]] < 0.f) {
+                    if (t == pa[i]) g -= a.lambda_k;
+                    if (t == pb[i]) g += a.lambda_k;
+                }
             }
+        }
+        if (pen_term) {
+            // + lambda_k w d pen / d q_t = sum_i (d pen / d c_i) . (dR_b local_i + dP_b),
+            // b the proxy's bone, with the bone tangents of DOF t formed above
+            float gp = 0.f;
+            for (int i = 0; i < sh.model.n_proxies; ++i) {
+                const DevProxy& X = mp->proxies[i];
+                const float* dR = s_tan + ((size_t)t * nb + X.bone) * 12;
+                const float* dP = dR + 9;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float dc = fmaf(dR[3 * c], X.local[0], fmaf(dR[3 * c + 1], X.local[1],
+                                                                         fmaf(dR[3 * c + 2], X.local[2], dP[c])));
+                    gp = fmaf((float)((double)s_gc[3 * i + c] * (1.0 / kPenGradFix)), dc, gp);
+                }
+            }
+            g = fmaf(a.lambda_k * sh.model.pen_weight, gp, g);
         }
         // the FK clamps the pose to the limits: no gradient outside them
         const float x = pose[t];
@@ -808,10 +864,17 @@ cudaError_t launch_soft(bool backward, const SoftArgs& args, cudaStream_t stream
 cudaError_t launch_pose_grad(const DevModel& model, const GradArgs& args, cudaStream_t stream)
 {
     const size_t smem = ((size_t)kNdof * model.n_bones * 12 + (size_t)model.n_prims * kNdof) * sizeof(float);
-    static std::atomic<uint32_t> opted[64];
-    const cudaError_t e = opt_in_dynamic_smem(pose_grad_kernel, (kNdof * kMaxBones * 12 + kMaxPrims * kNdof) * 4, opted);
-    if (e != cudaSuccess) return e;
-    pose_grad_kernel<<<args.P, 64, smem, stream>>>(static_cast<const DevModelCore&>(model), args);
+    static std::atomic<uint32_t> opted[2][64];
+    const int smem_max = (kNdof * kMaxBones * 12 + kMaxPrims * kNdof) * 4;
+    if (model.kc_variant == HS_KC_ABDUCTION) {
+        const cudaError_t e = opt_in_dynamic_smem(pose_grad_kernel<DevModelCore>, smem_max, opted[0]);
+        if (e != cudaSuccess) return e;
+        pose_grad_kernel<DevModelCore><<<args.P, 64, smem, stream>>>(static_cast<const DevModelCore&>(model), args);
+    } else {
+        const cudaError_t e = opt_in_dynamic_smem(pose_grad_kernel<DevModel>, smem_max, opted[1]);
+        if (e != cudaSuccess) return e;
+        pose_grad_kernel<DevModel><<<args.P, 64, smem, stream>>>(model, args);
+    }
     return cudaGetLastError();
 }
 

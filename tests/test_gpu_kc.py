@@ -110,19 +110,60 @@ def test_frame_equals_step_by_step_with_penetration_term():
         assert np.array_equal(a, b)
 
 
-def test_gradient_refuses_the_penetration_term():
-    sc = C.make_scene(64, 48, 4, 904)
-    sc.model_g.set_kc(hs.HS_KC_PEN, 1.0)
-    try:
-        cam = hs.camera(*[float(v) for v in sc.cam])
-        P = 4
-        poses = torch.from_numpy(sc.poses).cuda()
-        prims = torch.zeros(P, sc.model_g.n_prims, 16, device="cuda")
-        kc = torch.zeros(P, device="cuda")
-        adj = torch.zeros(P, sc.model_g.n_prims, hs.SOFT_ADJ, dtype=torch.int64, device="cuda")
-        grad = torch.zeros(P, 26, device="cuda")
-        with pytest.raises(hs.HandscoreError) as e:
-            hs.pose_grad(sc.model_g, poses, cam, hs.score_params(), prims, kc, adj, grad)
-        assert e.value.status == hs.HS_ERR_NOT_IMPL
-    finally:
-        sc.model_g.set_kc(hs.HS_KC_ABDUCTION, 0.0)
+def _inside_poses(n, seed):
+    """Seeded poses strictly inside the limits, most of them with the index
+    swung into the middle finger (penetrating), none within 1e-3 mm of a kink
+    of pen (a pair just touching) or with two abduction angles equal."""
+    lo, hi = I.search_limits()
+    rng = np.random.default_rng(seed)
+    out = []
+    g = C.geometry_f32()
+    mo = oracle.Model.from_geometry(g, lo, hi)
+    while len(out) < n:
+        p = I.sample_poses(rng, 1, lo + 0.02, hi - 0.02)[0]
+        p[11] = rng.uniform(-0.25, -0.05)
+        p[15] = rng.uniform(-0.05, 0.15)
+        C_, r, f, fixed = K.proxies(mo, oracle.fk(mo, p))
+        gaps = [abs(r[i] + r[j] - np.linalg.norm(C_[i] - C_[j])) for i in range(len(r)) for j in range(i + 1, len(r))
+                if f[i] >= 0 and f[j] >= 0 and f[i] != f[j] and not (fixed[i] and fixed[j])]
+        if min(gaps) > 1e-3 and len(set(np.round(p[[11, 15, 19, 23]], 6))) == 4:
+            out.append(p.astype(np.float32))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("variant,w", [(hs.HS_KC_ABDUCTION, 0.0), (hs.HS_KC_ABD_PEN, 0.05), (hs.HS_KC_PEN, 1.0)])
+def test_gradient_of_the_kc_variants(variant, w):
+    """pose_grad with a zero render adjoint is lambda_k d kc / d pose alone:
+    against lambda_k times the oracle's complex-step gradient of the variant's
+    kc.  Tolerance (derived): the proxy centres carry the FK's FP32 error
+    (~1e-4 mm) over distances of a few mm, so each pair's unit vector is good
+    to ~1e-4 and the tangents to ~1e-6: 1e-3 of the largest component, and
+    the direction to a cosine of 1 - 1e-6."""
+    g = C.geometry_f32()
+    lo, hi = (a.astype(np.float32) for a in I.search_limits())
+    mo = oracle.Model.from_geometry(g, lo.astype(np.float64), hi.astype(np.float64))
+    mg = hs.Model.from_geometry(g, lo, hi).set_kc(variant, w)
+    cam = hs.camera(*[float(v) for v in oracle.camera_tuple(I.kinect_camera(320, 240))])
+    poses = _inside_poses(12, 905 + variant)
+    P = poses.shape[0]
+    prims = torch.zeros(P, mg.n_prims, 16, device="cuda")
+    kc = torch.zeros(P, device="cuda")
+    adj = torch.zeros(P, mg.n_prims, hs.SOFT_ADJ, dtype=torch.int64, device="cuda")
+    grad = torch.zeros(P, 26, device="cuda")
+    prm = hs.score_params()
+    hs.pose_grad(mg, torch.from_numpy(poses).cuda(), cam, prm, prims, kc, adj, grad)
+    torch.cuda.synchronize()
+    got = grad.cpu().numpy().astype(np.float64)
+    lam_k = float(prm.lambda_k)
+    pens = []
+    for k in range(P):
+        want = lam_k * K.kc_variant_gradient(mo, poses[k].astype(np.float64), variant, w)
+        scale = max(np.abs(want).max(), lam_k)
+        assert np.abs(got[k] - want).max() <= 1e-3 * scale, (k, np.abs(got[k] - want).max(), scale)
+        if np.linalg.norm(want) > 0:
+            cos = got[k] @ want / (np.linalg.norm(got[k]) * np.linalg.norm(want))
+            assert cos >= 1 - 1e-6, (k, cos)
+        pens.append(K.penetration(mo, poses[k].astype(np.float64)))
+    if variant != hs.HS_KC_ABDUCTION:
+        assert sum(p > 0.5 for p in pens) >= 4  # the term is exercised
+    assert hs.hs_get_device_status(clear=True) == 0

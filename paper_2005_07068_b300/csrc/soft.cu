@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
 // ---- pose gradient: record adjoints -> d E_s / d pose ------------------------------
 
 // fixed-point scale of the penetration adjoint d pen / d c (sums of unit vectors)
-constexpr double kPenGradFix = 4294967296.0;  // 2^32
+constexpr float kPenGradFix = 4294967296.0f;  // 2^32
 
 // Model: DevModelCore for the paper's kc, DevModel when the kc variant needs
 // the collision data (then the adjoint of the interpenetration term is added)
@@ -633,9 +633,9 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ M
                 const float d = sqrtf(d2);
                 if (rr - d > 0.f && d > 0.f) {
                     const float id = 1.f / d;
-                    const long long ux = __double2ll_rn((double)(dx * id) * kPenGradFix);
-                    const long long uy = __double2ll_rn((double)(dy * id) * kPenGradFix);
-                    const long long uz = __double2ll_rn((double)(dz * id) * kPenGradFix);
+                    const long long ux = __float2ll_rn(dx * id * kPenGradFix);
+                    const long long uy = __float2ll_rn(dy * id * kPenGradFix);
+                    const long long uz = __float2ll_rn(dz * id * kPenGradFix);
                     atomicAdd(reinterpret_cast<unsigned long long*>(&s_gc[3 * i]), (unsigned long long)(-ux));
                     atomicAdd(reinterpret_cast<unsigned long long*>(&s_gc[3 * i + 1]), (unsigned long long)(-uy));
                     atomicAdd(reinterpret_cast<unsigned long long*>(&s_gc[3 * i + 2]), (unsigned long long)(-uz));
@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ M
                 for (int c = 0; c < 3; ++c) {
                     const float dc = fmaf(dR[3 * c], X.local[0], fmaf(dR[3 * c + 1], X.local[1],
                                                                          fmaf(dR[3 * c + 2], X.local[2], dP[c])));
-                    gp = fmaf((float)((double)s_gc[3 * i + c] * (1.0 / kPenGradFix)), dc, gp);
+                    gp = fmaf(__ll2float_rn(s_gc[3 * i + c]) * (1.f / kPenGradFix), dc, gp);
                 }
             }
             g = fmaf(a.lambda_k * sh.model.pen_weight, gp, g);

@@ -7,6 +7,7 @@
 // applies Eq. 6-7 with per-dimension r1/r2 from a counter-based Philox4x32-10
 // stream, clamps to the limits and, every `mutate_every` generations,
 // re-draws the finger dims of the worst particles.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 
@@ -162,13 +163,17 @@ __global__ void __launch_bounds__(kPsoThreads) pso_step_kernel(const __grid_cons
     }
 }
 
-// One generation of the swarm fused with the FK of the new positions: one
-// 64-thread CTA per particle.  Every CTA reads the whole E / pbest_E vectors
-// (O(P) per CTA) to find the global best and its own mutation rank, so no CTA
-// waits for another: positions are double-buffered (x is read, x_next
-// written) and a particle's personal best is judged improved when E <= pbest_E
-// as read, which gives the same answer whether or not its owner has already
-// stored the update.
+// One generation of the swarm fused with the FK of the new positions: 64
+// threads per particle, each CTA taking particles q = blockIdx.x, + gridDim.x,
+// ... (the grid is what the device keeps resident, so the model is copied into
+// shared memory once per CTA rather than once per particle: the copy reads the
+// launch parameter with a different address in every lane, which the constant
+// cache serves one address at a time).  Every particle's update reads the
+// whole E / pbest_E vectors of its swarm (O(P)) to find the global best and its
+// own mutation rank, so no particle waits for another: positions are
+// double-buffered (x is read, x_next written) and a particle's personal best
+// is judged improved when E <= pbest_E as read, which gives the same answer
+// whether or not its owner has already stored the update.
 template <class M>  // DevModelCore for the paper's kc, DevModel for a kc variant
 __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__ M model_param, const PsoFkArgs a)
 {
@@ -178,46 +183,63 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
     __shared__ float red_v[2];
     __shared__ int red_i[2], red_r[2];
     extern __shared__ float s_e[];  // E [P] then pbest_E [P] of this particle's swarm
-    const int q = blockIdx.x, t = threadIdx.x;
-    // the swarm of particle q: particles [off, off + P), q is number i of them
-    int off = 0, P = a.P, n_mutate = a.n_mutate, s = 0;
-    uint32_t k0 = a.key0, k1 = a.key1;
-    float4 cam = a.cam;
-    if (a.batch.views) {
-        s = a.batch.sid[q];
-        const SwarmView& v = a.batch.views[s];
-        off = v.offset;
-        P = v.P;
-        n_mutate = v.n_mutate;
-        k0 = v.key0;
-        k1 = v.key1;
-        cam = make_float4(v.fx, v.fy, v.cx, v.cy);
-    }
-    const int i = q - off;
-    float* s_pe = s_e + P;
+    const int t = threadIdx.x;
+    const int total = a.batch.views ? a.batch.P_total : a.P;
     pdl_launch_dependents();
     fk_load_model(sh, model_param);
-    // this particle's random numbers depend only on (particle, generation, frame, seed):
-    // draw them while the previous kernel finishes
-    draw_step_randoms(i, a.gen, a.frame, k0, k1, s_r, s_m, t);
-    pdl_wait();  // E comes from the previous kernel
-    float xi = 0.f, pbi = 0.f, vi = 0.f;
-    if (t < kNdof) {  // this particle's own state, loaded before the global best is known
-        xi = a.x[(size_t)q * kNdof + t];
-        pbi = a.pbest[(size_t)q * kNdof + t];
-        vi = a.v[(size_t)q * kNdof + t];
+    for (int q = blockIdx.x; q < total; q += gridDim.x) {
+        // the swarm of particle q: particles [off, off + P), q is number i of them
+        int off = 0, P = a.P, n_mutate = a.n_mutate, s = 0;
+        uint32_t k0 = a.key0, k1 = a.key1;
+        float4 cam = a.cam;
+        if (a.batch.views) {
+            s = a.batch.sid[q];
+            const SwarmView& v = a.batch.views[s];
+            off = v.offset;
+            P = v.P;
+            n_mutate = v.n_mutate;
+            k0 = v.key0;
+            k1 = v.key1;
+            cam = make_float4(v.fx, v.fy, v.cx, v.cy);
+        }
+        const int i = q - off;
+        float* s_pe = s_e + P;
+        // this particle's random numbers depend only on (particle, generation, frame, seed):
+        // the first are drawn while the previous kernel finishes
+        draw_step_randoms(i, a.gen, a.frame, k0, k1, s_r, s_m, t);
+        if (q == (int)blockIdx.x) pdl_wait();  // E comes from the previous kernel
+        float xi = 0.f, pbi = 0.f, vi = 0.f;
+        if (t < kNdof) {  // this particle's own state, loaded before the global best is known
+            xi = a.x[(size_t)q * kNdof + t];
+            pbi = a.pbest[(size_t)q * kNdof + t];
+            vi = a.v[(size_t)q * kNdof + t];
+        }
+        for (int j = t; j < P; j += 64) {
+            s_e[j] = a.E[off + j];
+            s_pe[j] = a.pbest_E[off + j];
+        }
+        __syncthreads();
+        const SwarmRefs R{a.x, a.x_next, a.v, a.pbest, a.pbest_E, a.gbest, a.gbest_E, a.c1, a.c2, a.w, a.mutate};
+        const StepOut o = swarm_update<64>(R, q, i, off, P, s, n_mutate, s_e, s_pe, s_r, s_m, sh.model.lo,
+                                           sh.model.hi, xi, pbi, vi, s_pe[i], true, red_v, red_i, red_r);
+        if (t < kNdof) s_xn[t] = o.xn;
+        // FK of the new pose (fk_particle starts with a barrier that publishes s_xn)
+        fk_particle(sh, collide_data(model_param), s_xn, cam, a.prims + (size_t)q * sh.model.n_prims * 4, a.kc + q,
+                    a.status);
+        __syncthreads();  // this particle's shared state is no longer read
     }
-    for (int j = t; j < P; j += 64) {
-        s_e[j] = a.E[off + j];
-        s_pe[j] = a.pbest_E[off + j];
-    }
-    __syncthreads();
-    const SwarmRefs R{a.x, a.x_next, a.v, a.pbest, a.pbest_E, a.gbest, a.gbest_E, a.c1, a.c2, a.w, a.mutate};
-    const StepOut o = swarm_update<64>(R, q, i, off, P, s, n_mutate, s_e, s_pe, s_r, s_m, sh.model.lo, sh.model.hi,
-                                       xi, pbi, vi, s_pe[i], true, red_v, red_i, red_r);
-    if (t < kNdof) s_xn[t] = o.xn;
-    // FK of the new pose (fk_particle starts with a barrier that publishes s_xn)
-    fk_particle(sh, collide_data(model_param), s_xn, cam, a.prims + (size_t)q * sh.model.n_prims * 4, a.kc + q, a.status);
+}
+
+// CTAs of pso_step_fk_kernel the current device keeps resident with `smem`
+// bytes of dynamic shared memory
+template <class M>
+static int step_fk_resident(size_t smem)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pso_step_fk_kernel<M>, 64, smem) != cudaSuccess)
+        return 0;
+    return sms * per_sm;
 }
 
 cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cudaStream_t stream)
@@ -229,10 +251,14 @@ cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cud
                                : opt_in_dynamic_smem(pso_step_fk_kernel<DevModel>, smem_max, opted[1]);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    // one CTA per particle (all swarms of a batch); shared memory for the largest swarm
-    cfg.gridDim = dim3(args.batch.views ? args.batch.P_total : args.P);
-    cfg.blockDim = dim3(64);
+    // every particle of all swarms of a batch, over at most the resident CTAs;
+    // shared memory for the largest swarm
+    const int total = args.batch.views ? args.batch.P_total : args.P;
     cfg.dynamicSmemBytes = 2 * (size_t)args.P * sizeof(float);
+    const int resident = core ? step_fk_resident<DevModelCore>(cfg.dynamicSmemBytes)
+                              : step_fk_resident<DevModel>(cfg.dynamicSmemBytes);
+    cfg.gridDim = dim3(resident > 0 ? std::min(total, resident) : total);
+    cfg.blockDim = dim3(64);
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

@@ -14,14 +14,16 @@ template <class M>
 __global__ void __launch_bounds__(64) fk_kernel(const __grid_constant__ M model_param, const FkArgs a)
 {
     __shared__ FkShared sh;
+    __shared__ CollideSmem<M> s_col;
     fk_load_model(sh, model_param);
+    const CollideShared* col = collide_load(s_col, model_param);
     for (int p = blockIdx.x; p < a.P; p += gridDim.x) {
         float4 cam = make_float4(a.fx, a.fy, a.cx, a.cy);
         if (a.batch.views) {  // the camera of this particle's swarm
             const SwarmView& v = a.batch.views[a.batch.sid[p]];
             cam = make_float4(v.fx, v.fy, v.cx, v.cy);
         }
-        fk_particle(sh, collide_data(model_param), a.poses + (size_t)p * kNdof, cam,
+        fk_particle(sh, col, a.poses + (size_t)p * kNdof, cam,
                     a.prims + (size_t)p * model_param.n_prims * 4, a.kc + p, a.status);
         __syncthreads();  // this particle's shared state is no longer read
     }

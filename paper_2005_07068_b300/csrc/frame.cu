@@ -40,6 +40,7 @@ constexpr uint32_t kBarrierPolls = 1u << 24;  // each poll sleeps ~0.1 us: a few
 
 struct FrameShared {
     FkShared fk;                      // model, pose, bone frames
+    CollideShared col;                // the kc variants' collision data
     float4 rec[kMaxPrims * 4];        // this particle's FK records
     float4 rast[kMaxPrims * 5];       // their raster records
     int2 pbox[kMaxPrims];
@@ -109,6 +110,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
     const int n_prims = model.n_prims;
 
     fk_load_model(sh.fk, model);
+    const CollideShared* col = collide_load(sh.col, model);
     if (lane < kStages) mbar_init(&sh.bar[warp][lane], 1);
     if (t == 0) {
         mbar_fence_init();
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
     for (int g = 1; g <= a.gens; ++g) {
         // FK of the current pose (fk_particle starts with a barrier that publishes
         // sh.x); each record's raster form is made by the thread that formed it
-        fk_particle(sh.fk, &model, sh.x, a.cam, sh.rec, &sh.kc, a.status, [&](int j, const float* rec) {
+        fk_particle(sh.fk, col, sh.x, a.cam, sh.rec, &sh.kc, a.status, [&](int j, const float* rec) {
             const float4 r4[4] = {make_float4(rec[0], rec[1], rec[2], rec[3]),
                                   make_float4(rec[4], rec[5], rec[6], rec[7]),
                                   make_float4(rec[8], rec[9], rec[10], rec[11]),
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
     }
     if (alive) {
         // the records and kc of the final positions
-        fk_particle(sh.fk, &model, sh.x, a.cam, sh.rec, &sh.kc, a.status);
+        fk_particle(sh.fk, col, sh.x, a.cam, sh.rec, &sh.kc, a.status);
         __syncthreads();
         if (primary) {
             if (a.prims_out)

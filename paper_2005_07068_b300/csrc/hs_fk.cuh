@@ -10,6 +10,7 @@
 
 #include <cfloat>
 #include <cstddef>
+#include <type_traits>
 
 #include "hs_args.cuh"
 
@@ -137,13 +138,40 @@ struct NoEmit {
 
 // the collision data of a kernel's model parameter: the model itself when the
 // kernel was given the whole model, nullptr when it was given only the core
-__device__ __forceinline__ const DevModel* collide_data(const DevModel& m) { return &m; }
-__device__ __forceinline__ const DevModel* collide_data(const DevModelCore&) { return nullptr; }
-// mp: the whole model as passed to the kernel, whose collision data the kc
-// variants read; kernels launched only for the paper's kc take the smaller
-// DevModelCore and pass nullptr (collide_data below).
+// The collision data of the kc variants in shared memory: a CTA copies it
+// once from the launch parameter (whose reads with a different address in
+// every lane the constant cache serves one address at a time) and every FK
+// of the CTA then reads the copy.
+struct CollideShared {
+    DevProxy proxies[kMaxProxies];
+    uint16_t pairs[kMaxPairs];  // proxy i in the low byte, j in the high byte
+};
+// what a kernel of model type M keeps for it: kernels launched only for the
+// paper's kc take the smaller DevModelCore and keep nothing
+template <class M>
+using CollideSmem = typename std::conditional<std::is_same<M, DevModel>::value, CollideShared, char>::type;
+
+// copy the model's collision data into dst when its kc variant needs it (all
+// threads of the CTA; the first barrier of fk_particle publishes the copy);
+// returns the copy, or nullptr for the paper's kc
+__device__ __forceinline__ const CollideShared* collide_load(CollideShared& dst, const DevModel& m)
+{
+    if (m.kc_variant == HS_KC_ABDUCTION) return nullptr;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(m.proxies);
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst.proxies);
+    const int pw = m.n_proxies * (int)(sizeof(DevProxy) / 4);
+    for (int i = threadIdx.x; i < pw; i += blockDim.x) d[i] = src[i];
+    const uint32_t* srp = reinterpret_cast<const uint32_t*>(m.pairs);
+    uint32_t* dp = reinterpret_cast<uint32_t*>(dst.pairs);
+    const int qw = (m.n_pairs + 1) / 2;
+    for (int i = threadIdx.x; i < qw; i += blockDim.x) dp[i] = srp[i];
+    return &dst;
+}
+__device__ __forceinline__ const CollideShared* collide_load(char&, const DevModelCore&) { return nullptr; }
+
+// col: the collision data (collide_load), nullptr for the paper's kc.
 template <class Emit = NoEmit>
-__device__ __forceinline__ void fk_particle(FkShared& sh, const DevModel* mp, const float* pose, float4 cam,
+__device__ __forceinline__ void fk_particle(FkShared& sh, const CollideShared* col, const float* pose, float4 cam,
                                             float4* prims, float* kc, uint32_t* status, const Emit& emit = Emit())
 {
     const DevModelCore& model = sh.model;
@@ -308,13 +336,13 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const DevModel* mp, co
         dst[3] = make_float4(rec[12], rec[13], rec[14], rec[15]);
         emit(t, rec);
     }
-    if (model.kc_variant != HS_KC_ABDUCTION && mp) {  // (uniform over the CTA)
+    if (model.kc_variant != HS_KC_ABDUCTION && col) {  // (uniform over the CTA)
         // interpenetration of different fingers: the collision proxies relative to
         // the wrist (distances do not see its translation), then every pair of
         // proxies on different fingers, summed in fixed point (order-independent)
         const int n = model.n_proxies;
         for (int i = t; i < n; i += blockDim.x) {
-            const DevProxy& X = mp->proxies[i];
+            const DevProxy& X = col->proxies[i];
             const float* R = bR[X.bone];
             const float* O = bP[X.bone];
             float c[3];
@@ -327,7 +355,7 @@ __device__ __forceinline__ void fk_particle(FkShared& sh, const DevModel* mp, co
         __syncthreads();
         unsigned long long acc = 0ull;
         for (int k = t; k < model.n_pairs; k += blockDim.x) {  // the host listed the pairs to visit
-            const uint32_t ij = mp->pairs[k];
+            const uint32_t ij = col->pairs[k];
             const float4 a = sh.pc[ij & 0xffu], b = sh.pc[ij >> 8];
             const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
             const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz)), rr = a.w + b.w;

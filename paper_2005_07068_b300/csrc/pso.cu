@@ -178,6 +178,7 @@ template <class M>  // DevModelCore for the paper's kc, DevModel for a kc varian
 __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__ M model_param, const PsoFkArgs a)
 {
     __shared__ FkShared sh;
+    __shared__ CollideSmem<M> s_col;
     __shared__ float s_r[4 * kPairBlocks], s_m[4 * kMutBlocks];
     __shared__ float s_xn[kNdof];
     __shared__ float red_v[2];
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
     const int total = a.batch.views ? a.batch.P_total : a.P;
     pdl_launch_dependents();
     fk_load_model(sh, model_param);
+    const CollideShared* col = collide_load(s_col, model_param);
     for (int q = blockIdx.x; q < total; q += gridDim.x) {
         // the swarm of particle q: particles [off, off + P), q is number i of them
         int off = 0, P = a.P, n_mutate = a.n_mutate, s = 0;
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
                                            sh.model.hi, xi, pbi, vi, s_pe[i], true, red_v, red_i, red_r);
         if (t < kNdof) s_xn[t] = o.xn;
         // FK of the new pose (fk_particle starts with a barrier that publishes s_xn)
-        fk_particle(sh, collide_data(model_param), s_xn, cam, a.prims + (size_t)q * sh.model.n_prims * 4, a.kc + q,
+        fk_particle(sh, col, s_xn, cam, a.prims + (size_t)q * sh.model.n_prims * 4, a.kc + q,
                     a.status);
         __syncthreads();  // this particle's shared state is no longer read
     }

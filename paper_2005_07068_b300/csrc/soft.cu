@@ -606,12 +606,13 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ M
 {
     __shared__ FkShared sh;
     __shared__ long long s_gc[kMaxProxies * 3];  // d pen / d (proxy centre), fixed point
+    __shared__ CollideSmem<Model> s_col;
     extern __shared__ float s_tan[];  // [26][n_bones][12]: dR (9), dP (3) of every bone for every DOF,
                                       // then [n_prims][26]: each primitive's contribution
     fk_load_model(sh, model_param);
     const int p = blockIdx.x, t = threadIdx.x;
     const float* pose = a.poses + (size_t)p * kNdof;
-    const DevModel* mp = collide_data(model_param);
+    const CollideShared* mp = collide_load(s_col, model_param);
     fk_particle(sh, mp, pose, make_float4(a.fx, a.fy, a.cx, a.cy), a.prims + (size_t)p * sh.model.n_prims * 4, a.kc + p,
                 a.status);
     __syncthreads();

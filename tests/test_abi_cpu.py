@@ -302,3 +302,40 @@ def test_python_binding_requires_device_tensors():
     with pytest.raises(ValueError):
         hs._ptr(torch.zeros(4))
     assert np.float32(hs.score_params().d_M) == 40.0
+
+
+def test_track_frame_host_checks():
+    """track_frame refuses bad arguments on the host, before any CUDA call
+    (the capacity check, which needs the device, comes after these)."""
+    m = _model()
+    L = hs.lib()
+    cam = hs.camera(262.5, 262.5, 160, 120)
+    prm = hs.score_params()
+    pp = hs.pso_params(P=64)
+    o = _obs()
+    sw = hs.HsSwarm(FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
+    scale = (ctypes.c_float * 26)(*([1.0] * 26))
+    need = ctypes.c_size_t()
+    assert L.hs_frame_workspace_size(64, ctypes.byref(need)) == hs.HS_OK
+    assert need.value == 128 + 3 * 32 * 64  # control block and three slots of per-particle sums
+    assert L.hs_frame_workspace_size(0, ctypes.byref(need)) == hs.HS_ERR_SIZE
+    assert L.hs_frame_workspace_size(hs.FRAME_MAX_PARTICLES + 1, ctypes.byref(need)) == hs.HS_ERR_SIZE
+
+    def call(x_next=FAKE + 4096, P=64, gens=40, ctas=0, ws=FAKE, ws_bytes=1 << 20, kc=FAKE, pso=pp, sc=scale, s=sw):
+        return L.track_frame(m.handle, ctypes.byref(o), ctypes.byref(cam), ctypes.byref(s), x_next, P, gens,
+                             ctypes.byref(prm), ctypes.byref(pso), FAKE, sc, 1, 0, ctas, ws, ws_bytes, None, kc, None)
+
+    assert call(x_next=FAKE) == hs.HS_ERR_ARG            # positions must be double-buffered
+    assert call(gens=-1) == hs.HS_ERR_ARG
+    assert call(ctas=-1) == hs.HS_ERR_ARG
+    assert call(kc=None) == hs.HS_ERR_ARG
+    assert call(P=0) == hs.HS_ERR_SIZE
+    assert call(P=hs.FRAME_MAX_PARTICLES + 1) == hs.HS_ERR_SIZE
+    assert call(ws=None) == hs.HS_ERR_ARG
+    assert call(ws=FAKE + 8) == hs.HS_ERR_ALIGN
+    assert call(ws_bytes=128) == hs.HS_ERR_SIZE  # smaller than 64 particles need
+    assert call(pso=hs.pso_params(c1=1.0, c2=1.0, P=64)) == hs.HS_ERR_ARG   # psi <= 4
+    assert call(pso=hs.pso_params(P=64, n_mutate=65)) == hs.HS_ERR_ARG      # more mutants than particles
+    assert call(sc=(ctypes.c_float * 26)(*([1.0] * 25 + [-1.0]))) == hs.HS_ERR_ARG
+    bad = hs.HsSwarm(FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, None)  # no E
+    assert call(s=bad) == hs.HS_ERR_ARG

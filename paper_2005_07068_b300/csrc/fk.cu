@@ -11,7 +11,7 @@ namespace hs {
 // blockIdx.x, + gridDim.x, ... (at most the resident CTAs are launched, so the
 // model is copied into shared memory once per CTA, not once per particle).
 template <class M>
-__global__ void __launch_bounds__(64) fk_kernel(const __grid_constant__ M model_param, const FkArgs a)
+__global__ void __launch_bounds__(64, 8) fk_kernel(const __grid_constant__ M model_param, const FkArgs a)
 {
     __shared__ FkShared sh;
     __shared__ CollideSmem<M> s_col;

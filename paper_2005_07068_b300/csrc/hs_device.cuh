@@ -31,6 +31,7 @@ struct DevPrimDesc {
     float dims[4];
     float inv_s[3];  // 1 / scale along local x, y, z
     int32_t caps;    // cone caps to render: bit 0 at y = -hl, bit 1 at y = +hl
+    int32_t pad;     // (a whole number of 8-byte words)
 };
 
 // a collision proxy of the interpenetration test: an inscribed sphere of a
@@ -45,7 +46,7 @@ constexpr int kMaxProxies = HS_MAX_PROXIES;
 constexpr int kMaxPairs = HS_MAX_PROXY_PAIRS;
 
 // what every FK kernel copies to shared memory: header, limits, primitives, bones (about 5.6 KB)
-struct DevModelCore {
+struct alignas(8) DevModelCore {  // (8-aligned: kernels copy it in 8-byte words)
     int32_t n_bones, n_prims, max_depth, pad;
     int32_t kc_variant, n_proxies;  // HS_KC_*; proxies used by the penetration test
     float pen_weight;

@@ -80,14 +80,21 @@ __device__ __forceinline__ int clamp_i16(float v)
 // memory; later accesses use thread-dependent bone / primitive indices
 __device__ __forceinline__ void fk_load_model(FkShared& sh, const DevModelCore& mp)
 {
-    // only the used part: header and limits, then the n_prims primitives and n_bones bones
-    const uint32_t* srcw = reinterpret_cast<const uint32_t*>(&mp);
-    uint32_t* dstw = reinterpret_cast<uint32_t*>(&sh.model);
-    constexpr int head = (int)(offsetof(DevModelCore, prims) / 4);
-    const int prim_end = head + mp.n_prims * (int)(sizeof(DevPrimDesc) / 4);
-    constexpr int bones0 = (int)(offsetof(DevModelCore, bones) / 4);
-    const int bone_words = mp.n_bones * (int)(sizeof(DevBone) / 4);
+    // only the used part: header and limits, then the n_prims primitives and n_bones bones, in
+    // 8-byte words (every lane's read of the parameter is a constant-cache request of its own,
+    // so wider words mean fewer requests)
+    static_assert(offsetof(DevModelCore, prims) % 8 == 0 && offsetof(DevModelCore, bones) % 8 == 0 &&
+                      sizeof(DevPrimDesc) % 8 == 0 && sizeof(DevBone) % 8 == 0,
+                  "the model copy moves 8-byte words");
+    const uint2* srcw = reinterpret_cast<const uint2*>(&mp);
+    uint2* dstw = reinterpret_cast<uint2*>(&sh.model);
+    constexpr int head = (int)(offsetof(DevModelCore, prims) / 8);
+    const int prim_end = head + mp.n_prims * (int)(sizeof(DevPrimDesc) / 8);
+    constexpr int bones0 = (int)(offsetof(DevModelCore, bones) / 8);
+    const int bone_words = mp.n_bones * (int)(sizeof(DevBone) / 8);
+#pragma unroll 1
     for (int i = threadIdx.x; i < prim_end; i += blockDim.x) dstw[i] = srcw[i];
+#pragma unroll 1
     for (int i = threadIdx.x; i < bone_words; i += blockDim.x) dstw[bones0 + i] = srcw[bones0 + i];
 }
 

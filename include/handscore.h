@@ -370,9 +370,12 @@ int pso_step_fk(const HsModel* model, const HsSwarm* swarm, float* x_next, int P
  * min(capacity, 8 P).  workspace: hs_frame_workspace_size(P) bytes (counters,
  * sums, and a second buffer of the swarm state), zeroed once before first use
  * (every call leaves its counters and sums zeroed).  Calls that share a
- * workspace must not overlap on the GPU.  If a grid barrier wait runs out (a
- * few seconds), the frame stops, HS_DEV_BARRIER_TIMEOUT is set and the
- * swarm's contents are void.
+ * workspace must not overlap on the GPU.  If a grid barrier wait runs out
+ * (about a second), the frame stops, HS_DEV_BARRIER_TIMEOUT is set and the
+ * swarm's contents are void; the next call runs normally.  The workspace's
+ * third 32-bit word is read as a number of arrivals every grid barrier waits
+ * for beyond the grid's own: leave it zero (a test sets it to make the wait
+ * run out).
  * Errors: HS_ERR_ARG (NULL, x_next == swarm->x, bad constants, gens < 0,
  * ctas < 0), HS_ERR_ALIGN, HS_ERR_SIZE (P out of range, ctas < P or over
  * capacity, workspace too small), HS_ERR_CUDA. */

@@ -24,7 +24,7 @@
 //
 // Results equal the graph path bit for bit (unit kernel render + pso_step_fk),
 // because every piece of arithmetic is the same code.  The barrier's wait is
-// bounded: if it runs out, HS_DEV_BARRIER_TIMEOUT is set and the CTAs leave.
+// bounded (about a second): if it runs out, HS_DEV_BARRIER_TIMEOUT is set and the CTAs leave.
 // The last CTA to leave returns the workspace to zero for the next frame.
 #include <atomic>
 
@@ -35,7 +35,8 @@ namespace hs {
 
 constexpr int kFrameWarps = 8;
 constexpr int kFrameThreads = kFrameWarps * 32;
-constexpr uint32_t kBarrierPolls = 1u << 24;  // each poll sleeps ~0.1 us: a few seconds in all
+constexpr unsigned long long kBarrierWaitNs = 1000000000ull;  // a grid barrier waits at most ~1 s (wall clock)
+constexpr uint32_t kBarrierPolls = 1u << 26;  // and at most this many polls, should the clock not advance
 
 
 struct FrameShared {
@@ -77,10 +78,14 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, u
     if (threadIdx.x == 0) {
         uint32_t v;
         uint32_t polls = 0;
+        unsigned long long t0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
         for (;;) {
             asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
             if (v >= target) break;
-            if (++polls >= kBarrierPolls) {
+            unsigned long long now;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+            if (now - t0 > kBarrierWaitNs || ++polls >= kBarrierPolls) {
                 set_status(status, HS_DEV_BARRIER_TIMEOUT);
                 ok = 0;
                 break;
@@ -101,6 +106,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
     float* s_pe = s_dyn + a.P;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint32_t nblocks = gridDim.x;
+    const uint32_t missing = a.ctl->missing;  // zero but in the test of the barrier's time limit
     // particle p has CTAs [ceil(p n / P), ceil((p + 1) n / P)) of the n in the grid
     const int P = a.P, p = (int)((unsigned long long)blockIdx.x * (unsigned)P / nblocks);
     const int first = (int)(((unsigned long long)p * nblocks + P - 1) / (unsigned)P);
@@ -245,7 +251,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
         // every particle's sums (and the frame's totals) are in; meanwhile this
         // particle's random numbers for the step
         ++barriers;
-        if (!grid_barrier(&a.ctl->barrier, barriers * nblocks, a.status,
+        if (!grid_barrier(&a.ctl->barrier, barriers * (nblocks + missing), a.status,
                           [&] { draw_step_randoms(p, (uint32_t)g, a.frame, a.key0, a.key1, sh.r, sh.m, t); })) {
             alive = false;
             break;

@@ -118,7 +118,9 @@ struct FrameSums {
 struct FrameCtl {
     uint32_t barrier;  // grid-barrier arrivals of this launch
     uint32_t exited;   // CTAs that have finished
-    uint32_t pad[30];
+    uint32_t missing;  // arrivals every grid barrier waits for beyond the grid's own: zero, except to test the
+                       // barrier's time limit (the wait then runs out); the kernel only reads it
+    uint32_t pad[29];
 };
 
 struct FrameArgs {

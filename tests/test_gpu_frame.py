@@ -8,6 +8,8 @@ observation totals -- for every number of CTAs per particle.  The
 step-by-step path itself is checked against the FP64 oracle in
 test_gpu_parity.py; here its first generation is also checked against the
 oracle's scores of the same initial swarm."""
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -113,6 +115,34 @@ def test_frame_at_the_capacity_limit():
             big.run_frame(obs, 0, start)
         assert e.value.status == hs.HS_ERR_SIZE
     torch.cuda.synchronize()
+    assert hs.hs_get_device_status(clear=True) == 0
+
+
+def test_barrier_time_limit_is_reported():
+    """A grid barrier that waits for arrivals that never come (the workspace's
+    word for missing arrivals set) runs out after about a second: the frame
+    stops with HS_DEV_BARRIER_TIMEOUT and no fault, and the next frame (word
+    cleared) equals the step-by-step calls."""
+    W, H, P, seed = 64, 48, 8, 718
+    sc = C.make_scene(W, H, P, seed, noisy=True, f32=False)
+    cam = hs.camera(*[float(v) for v in sc.cam])
+    obs = hs.Obs.from_numpy(sc.Od, sc.S, torch.device("cuda"))
+    start = torch.from_numpy(sc.gt).cuda()
+    hs.hs_get_device_status(clear=True)
+    ft = T.FrameTracker(sc.model_g, cam, P=P, gens=3, seed=seed, ctas=P)
+    ft.fws[2] = 1  # one arrival that never comes
+    t0 = time.perf_counter()
+    ft.run_frame(obs, 0, start)
+    torch.cuda.synchronize()
+    waited = time.perf_counter() - t0
+    assert hs.hs_get_device_status(clear=True) & hs.HS_DEV_BARRIER_TIMEOUT
+    assert 0.5 < waited < 30.0, waited
+    assert int(ft.fws[:2].abs().sum()) == 0  # the counters were returned to zero on the way out
+    ft.fws[2] = 0
+    got = _run(ft, obs, 1, start)
+    ref = _run(T.Tracker(sc.model_g, cam, P=P, gens=3, seed=seed), obs, 1, start)
+    for k in ref[0]:
+        assert np.array_equal(got[0][k], ref[0][k], equal_nan=True), k
     assert hs.hs_get_device_status(clear=True) == 0
 
 

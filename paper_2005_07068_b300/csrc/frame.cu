@@ -4,7 +4,7 @@
 // a single cooperative launch.
 //
 // The graph path launches a kernel per step (observation totals, init, FK,
-// then render + fused step per generation): about 20 us per generation at
+// then render + fused step per generation): about 16 us per generation at
 // 64 particles, mostly launch gaps and the latency chains of short kernels.
 // Here the grid's CTAs stay resident for the whole frame, dealt evenly to the
 // particles (each gets floor(n / P) or ceil(n / P) of the n CTAs):
@@ -24,8 +24,9 @@
 //
 // Results equal the graph path bit for bit (unit kernel render + pso_step_fk),
 // because every piece of arithmetic is the same code.  The barrier's wait is
-// bounded (about a second): if it runs out, HS_DEV_BARRIER_TIMEOUT is set and the CTAs leave.
-// The last CTA to leave returns the workspace to zero for the next frame.
+// bounded (about a second): if it runs out, HS_DEV_BARRIER_TIMEOUT is set and
+// the CTAs leave.  The last CTA to leave returns the workspace's counters and
+// sums to zero for the next frame.
 #include <atomic>
 
 #include "hs_step.cuh"
@@ -47,7 +48,7 @@ struct FrameShared {
     int2 pbox[kMaxPrims];
     alignas(128) unsigned char tile[kFrameWarps][kStages][kSlot];
     uint64_t bar[kFrameWarps][kStages];
-    float x[kNdof], v[kNdof], pb[kNdof];  // the particle's state (identical in its C CTAs)
+    float x[kNdof], v[kNdof], pb[kNdof];  // the particle's state (identical in all its CTAs)
     float pe;                             // its personal-best E
     float kc;
     float r[4 * kPairBlocks], m[4 * kMutBlocks];

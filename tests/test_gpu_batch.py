@@ -101,10 +101,23 @@ def _track_single(sc, seed, frames, gens, start):
     return out
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_batch_tracking_equals_single_swarm_trackers(scenes, graph):
+@pytest.mark.parametrize("graph,variant", [(False, hs.HS_KC_ABDUCTION), (True, hs.HS_KC_ABDUCTION),
+                                           (False, hs.HS_KC_ABD_PEN)])
+def test_batch_tracking_equals_single_swarm_trackers(scenes, graph, variant):
     """Two frames x 7 generations (mutation at 3 and 6) of every sequence at once
-    == each sequence tracked alone, bit for bit."""
+    == each sequence tracked alone, bit for bit; also with the interpenetration
+    term in kc (the batched step then copies the collision data once per CTA and
+    serves several particles from it)."""
+    for sc in scenes:
+        sc.model_g.set_kc(variant, 0.05 if variant != hs.HS_KC_ABDUCTION else 0.0)
+    try:
+        _batch_tracking_equals_single(scenes, graph)
+    finally:
+        for sc in scenes:
+            sc.model_g.set_kc(hs.HS_KC_ABDUCTION, 0.0)
+
+
+def _batch_tracking_equals_single(scenes, graph):
     frames, gens = 2, 7
     seeds = [0x5EED0000 + 17 * s for s in range(len(scenes))]
     obs, cams, b = _batch(scenes, seeds)

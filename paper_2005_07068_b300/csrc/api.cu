@@ -682,13 +682,9 @@ static int soft_common(const HsModel* model, const HsObs* obs, const HsCamera* c
     a.prims = reinterpret_cast<const float4*>(prims);
     a.P = P;
     a.n_prims = model->dev.n_prims;
-    int K = sp->ctas_per_particle;
-    if (K == 0) {  // about one resident wave in total (these calls serve few particles)
-        K = P > 0 ? kTargetCtas / P : 1;
-        if (K > kMaxCtasPerParticle) K = kMaxCtasPerParticle;
-        if (K < 1) K = 1;
-    }
-    a.K = K;
+    // 0: the launcher picks one resident wave of the kernel in total (these calls
+    // serve few particles; the forward and backward kernels differ in occupancy)
+    a.K = sp->ctas_per_particle;
     a.W = obs->W;
     a.H = obs->H;
     a.inv_fx = (float)(1.0 / (double)cam->fx);

@@ -837,6 +837,7 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ M
 // ---- launchers ----------------------------------------------------------------------
 
 static constexpr int kMaxDevicesSoft = 64;
+static constexpr int kMaxSoftCtas = 64;  // CTAs per particle at most (HsSoftParams.ctas_per_particle's range)
 
 template <bool BWD>
 static cudaError_t launch_soft_impl(const SoftArgs& args, cudaStream_t stream)
@@ -853,7 +854,20 @@ static cudaError_t launch_soft_impl(const SoftArgs& args, cudaStream_t stream)
         if (e != cudaSuccess) return e;
         opted[dev].store(1u, std::memory_order_release);
     }
-    soft_kernel<BWD><<<dim3(args.K, args.P), kSoftThreads, smem, stream>>>(args);
+    int K = args.K;
+    if (K == 0) {
+        // CTAs per particle: one resident wave of this kernel in all (the backward
+        // pass keeps per-pixel lists in shared memory and fits fewer CTAs per SM;
+        // a grid a little over one wave would take about two waves' time)
+        int sms = 0, per_sm = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, soft_kernel<BWD>, kSoftThreads, smem);
+        if (e != cudaSuccess) return e;
+        K = args.P > 0 ? sms * per_sm / args.P : 1;
+        K = K < 1 ? 1 : (K > kMaxSoftCtas ? kMaxSoftCtas : K);
+    }
+    soft_kernel<BWD><<<dim3(K, args.P), kSoftThreads, smem, stream>>>(args);
     return cudaGetLastError();
 }
 

@@ -143,8 +143,6 @@ struct NoEmit {
     __device__ void operator()(int, const float*) const {}
 };
 
-// the collision data of a kernel's model parameter: the model itself when the
-// kernel was given the whole model, nullptr when it was given only the core
 // The collision data of the kc variants in shared memory: a CTA copies it
 // once from the launch parameter (whose reads with a different address in
 // every lane the constant cache serves one address at a time) and every FK

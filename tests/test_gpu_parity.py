@@ -62,6 +62,50 @@ def test_fk_records_match_oracle():
     REPORT["fk_max_centre_err_mm"] = worst_c
 
 
+def test_fk_deep_chain_matches_oracle():
+    """A model deeper than a hand (a chain of 7 bones below the palm, the
+    deepest HS_MAX_DEPTH allows), whose bones beyond the third level take FK's
+    general path: every bone frame against the FP64 oracle's, through the
+    records of one sphere per bone and of an ellipsoid at the tip."""
+    depth = 7
+    nb = depth + 1
+    bi = np.zeros((nb, 3), np.int32)
+    bi[0] = (-1, -1, -1)
+    for b in range(1, nb):
+        bi[b] = (b - 1, 6 + 2 * (b - 1), 7 + 2 * (b - 1))  # parent, z and x degrees of freedom
+    bf = np.zeros((nb, 6), np.float64)
+    bf[1:, 1] = np.linspace(30.0, 12.0, depth)  # offsets along y (mm)
+    bf[1:, 3] = 0.05                            # a small rest rotation about x
+    pi = np.array([[b, 0] for b in range(nb)] + [[depth, 0]], np.int32)
+    pf = np.zeros((nb + 1, 7), np.float64)
+    pf[:nb, 3:6] = 6.0                          # spheres at the bone origins
+    pf[nb, 1] = 10.0                            # an ellipsoid beyond the tip
+    pf[nb, 3:6] = (5.0, 8.0, 4.0)
+    lo, hi = I.search_limits()
+    lo, hi = lo.astype(np.float32), hi.astype(np.float32)
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)
+    mo = oracle.Model(bi, f32(bf), pi, f32(pf), lo.astype(np.float64), hi.astype(np.float64))
+    mg = hs.Model(bi, bf.astype(np.float32), pi, pf.astype(np.float32), lo, hi)
+    cam = hs.camera(*[float(v) for v in oracle.camera_tuple(I.kinect_camera(320, 240))])
+    rng = np.random.default_rng(103)
+    poses = I.sample_poses(rng, 16, lo, hi).astype(np.float32)
+    prims = torch.zeros(16, mg.n_prims, 16, device="cuda")
+    kc = torch.zeros(16, device="cuda")
+    hs.pose_fk(mg, torch.from_numpy(poses).cuda(), cam, prims, kc)
+    torch.cuda.synchronize()
+    rec = prims.cpu().numpy()
+    worst = 0.0
+    for p in range(16):
+        f = oracle.fk(mo, poses[p].astype(np.float64))
+        worst = max(worst, float(np.abs(rec[p, :, 9:12] - f["prim_C"]).max()))
+        for k in range(mg.n_prims):
+            d = mo.prims_f[k, 3:6]
+            M = (f["prim_R"][k] / d[None, :]).T
+            assert np.abs(rec[p, k, :9] - np.concatenate([M[:, 0], M[:, 1], M[:, 2]])).max() < 1e-5 / 4.0, (p, k)
+    assert worst < 2e-4, worst
+    assert hs.hs_get_device_status(clear=True) == 0
+
+
 def test_fk_boxes_are_conservative():
     """Every pixel a primitive covers (oracle render of that primitive alone)
     lies inside the box pose_fk wrote for it, and the box is the exact bound of

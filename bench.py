@@ -946,7 +946,7 @@ def main():
     if use_frame:
         value, step_ms_h, launches, clocks = frame_path["value"], frame_path["ms_per_step"], K, frame_path["clocks"]
         step_desc = (f"one frame = one cooperative launch of track_frame ({PARTICLES} particles, {ft.ctas} CTAs dealt "
-                     f"to them by their render work each generation; "
+                     f"evenly to them for the whole frame; "
                      f"the faster of it and the CUDA graph of the step-by-step calls)")
     else:
         step_ms_h, launches = graph_ms, K * trk.launches_per_frame()

@@ -367,9 +367,9 @@ int pso_step_fk(const HsModel* model, const HsSwarm* swarm, float* x_next, int P
  * the records and kc of the final positions.
  *
  * ctas: CTAs of the grid, P <= ctas <= hs_frame_capacity(); 0 picks
- * min(capacity, 8 P).  workspace: hs_frame_workspace_size(P) bytes (counters,
- * sums, and a second buffer of the swarm state), zeroed once before first use
- * (every call leaves its counters and sums zeroed).  Calls that share a
+ * min(capacity, 8 P).  workspace: hs_frame_workspace_size(P) bytes (a
+ * control block and three generations of per-particle sums), zeroed once
+ * before first use (every call leaves it zeroed).  Calls that share a
  * workspace must not overlap on the GPU.  If a grid barrier wait runs out
  * (about a second), the frame stops, HS_DEV_BARRIER_TIMEOUT is set and the
  * swarm's contents are void; the next call runs normally.  The workspace's

@@ -415,8 +415,8 @@ def pso_step_fk(model: Model, sw: Swarm, x_next: torch.Tensor, params: HsPsoPara
 # ---- a whole tracking frame in one launch ---------------------------------------------
 
 def new_frame_workspace(P: int, device="cuda") -> torch.Tensor:
-    """Zeroed workspace of track_frame for P particles (every call leaves its
-    counters and sums zeroed; the rest is a second buffer of the swarm state)."""
+    """Zeroed workspace of track_frame for P particles: a control block and
+    three generations of per-particle sums, which every call leaves zeroed."""
     n = ctypes.c_size_t()
     _check("hs_frame_workspace_size", lib().hs_frame_workspace_size(P, ctypes.byref(n)))
     return torch.zeros((n.value + 15) // 16 * 4, dtype=torch.int32, device=device)

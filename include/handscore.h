@@ -349,11 +349,11 @@ int pso_step_fk(const HsModel* model, const HsSwarm* swarm, float* x_next, int P
  * frame's best pose, then `gens` generations of "score every particle (Section
  * III.A, Eq. 4-5), move the swarm (Eq. 6-7 and the mutation)" -- as one
  * cooperative launch whose `ctas` CTAs stay resident for the whole frame, with
- * one grid barrier per generation between scoring and the update.  Every
- * generation the CTAs are dealt to particles: each particle gets at least one,
- * the rest go out in proportion to the 16x4-pixel work units of its previous
- * render (evenly in the first generation).  The CTAs of a particle share its
- * units; its FK records stay in their shared memory.
+ * one grid barrier per generation between scoring and the update.  The CTAs
+ * are dealt evenly to the particles for the whole frame: particle p has CTAs
+ * [ceil(p ctas / P), ceil((p + 1) ctas / P)).  The CTAs of a particle share
+ * its 16x4-pixel work units and keep its state and FK records in their shared
+ * memory.
  *
  * Results are exactly those of the step-by-step calls
  *     hs_obs_prepare(obs); pso_init(swarm, seed_pose, scale, seed, frame);

@@ -434,8 +434,8 @@ def track_frame(model: Model, obs: Obs, cam: HsCamera, sw: Swarm, x_next: torch.
                 ctas: int, ws: torch.Tensor, kc: torch.Tensor, prims: torch.Tensor | None = None,
                 stream=None) -> None:
     """One whole frame (obs totals, init around seed_pose, gens x (score, step)) in
-    one cooperative launch of `ctas` CTAs (0: automatic), dealt to particles by
-    their work each generation; identical to the step-by-step calls.
+    one cooperative launch of `ctas` CTAs (0: automatic), dealt evenly to the
+    particles for the whole frame; identical to the step-by-step calls.
     Generation g writes positions to (sw.x, x_next)[g & 1]."""
     st = sw.struct()
     sc = (ctypes.c_float * NDOF)(*[float(v) for v in np.asarray(scale, np.float32)])

@@ -138,11 +138,10 @@ class Tracker:
 
 class FrameTracker(Tracker):
     """Plain PSO tracking with each frame in ONE cooperative launch (track_frame):
-    `ctas` CTAs stay resident for the whole frame and meet at one grid barrier
-    per generation; each generation they are dealt to particles in proportion
-    to the particles' render work.  Bit for bit the same swarm as Tracker (same
-    observation, camera, P, seed); no CUDA graph is needed, a frame is a
-    single launch.  ctas = 0 lets the library choose."""
+    `ctas` CTAs, dealt evenly to the particles, stay resident for the whole
+    frame and meet at one grid barrier per generation.  Bit for bit the same
+    swarm as Tracker (same observation, camera, P, seed); no CUDA graph is
+    needed, a frame is a single launch.  ctas = 0 lets the library choose."""
 
     def __init__(self, model: hs.Model, cam: hs.HsCamera, P: int = 64, gens: int = 40, *, ctas: int = 0, **kw):
         super().__init__(model, cam, P, gens, **kw)

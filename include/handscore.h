@@ -311,18 +311,24 @@ int pso_step(const HsModel* model, const HsSwarm* swarm, int P, const HsPsoParam
  * The paper has no counterpart: this is a deployment convenience.  Identical
  * to render_score_batch without the debug outputs, except that the scratch
  * workspace is a fixed array inside this library (HS_NOALLOC_SCRATCH_BYTES
- * bytes per GPU, held from library load until process exit), so the call
- * allocates nothing (no cudaMalloc, no allocating library routine).
+ * bytes per GPU), so the call itself allocates nothing (no cudaMalloc, no
+ * allocating library routine).
  *  - P is limited to what the array holds: calls with hs_workspace_size(P) >
  *    HS_NOALLOC_SCRATCH_BYTES (P > 8192 with the current 32-byte per-particle
  *    layout) return HS_ERR_SIZE and launch nothing.
  *  - The first call on a device looks up the array's device address (with
- *    cudaGetSymbolAddress) and caches it; make that first call before any
- *    stream capture.
+ *    cudaGetSymbolAddress) and caches it.  Under lazy module loading (the
+ *    CUDA default) that first call is also when the driver loads the array
+ *    onto the device, so it is the call that can fail for lack of device
+ *    memory (HS_ERR_CUDA): make it at start-up, before any stream capture or
+ *    allocation-free phase.  From then on the device holds the array until the
+ *    process exits, and later calls allocate nothing.
  *  - Every call on a device shares the one array and clears the part it uses
  *    before launching, so calls that overlap on the GPU (different streams
  *    without ordering between them) race and give wrong results.
- * Errors: as render_score_batch, plus HS_ERR_SIZE for P over the limit. */
+ * Errors: the arguments other than P are checked first, exactly as by
+ * render_score_batch; then P (HS_ERR_SIZE when out of range or over the
+ * array's limit). */
 #define HS_NOALLOC_SCRATCH_BYTES (256 * 1024)
 int render_score_batch_noalloc(const HsModel* model, const HsObs* obs, const HsCamera* cam,
                                const HsPrim* prims, const float* kc, int P, const HsScoreParams* params,

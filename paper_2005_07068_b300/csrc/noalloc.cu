@@ -9,11 +9,14 @@
 // library's own device memory, so the caller passes only inputs and outputs.
 //
 // The array is a file-scope __device__ symbol of HS_NOALLOC_SCRATCH_BYTES
-// bytes.  Every GPU that loads the library holds one copy until the process
-// exits.  Host code cannot use the symbol's name as a device address, so the
+// bytes.  Host code cannot use the symbol's name as a device address, so the
 // address is looked up once per device with cudaGetSymbolAddress (with that
-// device current) and cached; that happens during the first call on the
-// device, so make that first call before any stream capture.
+// device current) and cached.  With lazy module loading (the CUDA default)
+// that lookup is also when the driver loads this file's module on the device
+// and reserves the array, so the first call on each device is the one that
+// can fail for lack of memory (HS_ERR_CUDA): make it at start-up, before any
+// stream capture or allocation-free phase.  The device then holds the array
+// until the process exits, and later calls allocate nothing.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -49,13 +52,14 @@ extern "C" int render_score_batch_noalloc(const HsModel* model, const HsObs* obs
                                           const HsPrim* prims, const float* kc, int P, const HsScoreParams* params,
                                           float* E, HsParts* parts, hs_stream_t stream)
 {
-    size_t need = 0;
-    int rc = hs_workspace_size(P, &need);  // also rejects P out of range
+    // every argument but P is checked first, by a call that launches nothing
+    // (P = 0), so that errors come in the same order as render_score_batch's
+    int rc = render_score_batch(model, obs, cam, prims, kc, 0, params, nullptr, 0, E, parts, nullptr, nullptr, stream);
     if (rc != HS_OK) return rc;
+    size_t need = 0;
+    if ((rc = hs_workspace_size(P, &need)) != HS_OK) return rc;      // P out of range
     if (need > (size_t)HS_NOALLOC_SCRATCH_BYTES) return HS_ERR_SIZE;  // P beyond what the fixed array holds
-    // every other argument is checked by a call that launches nothing (P = 0)
-    rc = render_score_batch(model, obs, cam, prims, kc, 0, params, nullptr, 0, E, parts, nullptr, nullptr, stream);
-    if (rc != HS_OK || P == 0) return rc;
+    if (P == 0) return HS_OK;
     void* scratch = nullptr;
     if ((rc = scratch_address(&scratch)) != HS_OK) return rc;
     // the array keeps whatever the last call left in it: start from zeros

@@ -55,6 +55,10 @@ int main(void) {
   O(HsSwarmDesc, cam) O(HsSwarmDesc, P) O(HsSwarmDesc, seed)
   O(HsModelDesc, bones) O(HsModelDesc, lo) O(HsModelDesc, hi) O(HsObs, stats) O(HsObs, depth_type)
   O(HsBoneDesc, rest) O(HsPrimDesc, dims) O(HsSwarm, E)
+  printf("HS_NOALLOC_SCRATCH_BYTES %d\\n", (int)HS_NOALLOC_SCRATCH_BYTES);
+  printf("HS_FUSED_MAX_PARTICLES %d\\n", (int)HS_FUSED_MAX_PARTICLES);
+  printf("HS_MAX_PARTICLES %d\\n", (int)HS_MAX_PARTICLES);
+  printf("HS_FRAME_MAX_PARTICLES %d\\n", (int)HS_FRAME_MAX_PARTICLES);
   return 0;
 }
 """)
@@ -74,6 +78,9 @@ int main(void) {
         "HsModelDesc.hi": hs.HsModelDesc.hi.offset, "HsObs.stats": hs.HsObs.stats.offset,
         "HsObs.depth_type": hs.HsObs.depth_type.offset, "HsBoneDesc.rest": hs.HsBoneDesc.rest.offset,
         "HsPrimDesc.dims": hs.HsPrimDesc.dims.offset, "HsSwarm.E": hs.HsSwarm.E.offset,
+        # constants the binding repeats
+        "HS_NOALLOC_SCRATCH_BYTES": hs.NOALLOC_SCRATCH_BYTES, "HS_FUSED_MAX_PARTICLES": hs.FUSED_MAX_PARTICLES,
+        "HS_MAX_PARTICLES": hs.MAX_PARTICLES, "HS_FRAME_MAX_PARTICLES": hs.FRAME_MAX_PARTICLES,
     }
     for k, v in py.items():
         assert int(got[k]) == v, k

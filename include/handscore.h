@@ -124,14 +124,19 @@ typedef struct {
  * the unit kernel walks pixels (16 x 4 blocks, primitives culled per 8 x 4
  * half), the tile kernels walk primitives (pixel-exact rectangles of each
  * primitive's box inside a TW x TH tile, nearest hit by a shared-memory
- * z-buffer).  HS_RENDER_AUTO picks by the number of particles per call. */
+ * z-buffer), the strip kernels walk pixel strips 8 wide and 16 or 32 tall
+ * (one warp per strip, each primitive's column terms formed once per strip,
+ * nearest hit in registers).  HS_RENDER_AUTO picks by the number of
+ * particles per call. */
 #define HS_RENDER_AUTO        0
 #define HS_RENDER_UNITS       1
 #define HS_RENDER_TILES_32x16 2
 #define HS_RENDER_TILES_32x32 3
 #define HS_RENDER_TILES_64x32 4
 #define HS_RENDER_TILES_64x64 5
-#define HS_RENDER_VARIANTS    6
+#define HS_RENDER_STRIPS_8x16 6
+#define HS_RENDER_STRIPS_8x32 7
+#define HS_RENDER_VARIANTS    8
 
 /* constants of Eq. 4-5 (paper: d_m = 1 cm, d_M = 4 cm, lambda = 20, lambda_k = 10),
  * in mm; 0 <= d_M < 127 (the depth sums are kept in 32-bit fixed point per pixel);

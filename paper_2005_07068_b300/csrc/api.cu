@@ -134,6 +134,8 @@ static cudaError_t launch_render(const HsScoreParams& prm, const CUtensorMap& tm
     a.lambda = prm.lambda;
     a.lambda_k = prm.lambda_k;
     if (variant == HS_RENDER_UNITS) return launch_render_score(tm_depth, tm_skin, a, s);
+    if (variant == HS_RENDER_STRIPS_8x16 || variant == HS_RENDER_STRIPS_8x32)
+        return launch_render_strips(variant, tm_depth, tm_skin, a, s);
     return launch_render_tiles(variant, tm_depth, tm_skin, a, s);
 }
 

@@ -44,7 +44,7 @@ struct FrameShared {
     FkShared fk;                      // model, pose, bone frames
     CollideShared col;                // the kc variants' collision data
     float4 rec[kMaxPrims * 4];        // this particle's FK records
-    float4 rast[kMaxPrims * 5];       // their raster records
+    float4 rast[kMaxPrims * kRastVec];  // their raster records
     int2 pbox[kMaxPrims];
     alignas(128) unsigned char tile[kFrameWarps][kStages][kSlot];
     uint64_t bar[kFrameWarps][kStages];
@@ -196,13 +196,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
                                   make_float4(rec[4], rec[5], rec[6], rec[7]),
                                   make_float4(rec[8], rec[9], rec[10], rec[11]),
                                   make_float4(rec[12], rec[13], rec[14], rec[15])};
-            const RasterPrim R = make_raster(r4, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y);
-            float4* d = sh.rast + 5 * j;
-            d[0] = R.q0;
-            d[1] = R.q1;
-            d[2] = R.q2;
-            d[3] = R.q3;
-            d[4] = R.q4;
+            make_raster(r4, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y, sh.rast + kRastVec * j);
             sh.pbox[j] = make_int2(__float_as_int(rec[14]), __float_as_int(rec[15]));
             // the union of the pixel boxes, per warp of record threads
             const int w = j >> 5;

@@ -48,7 +48,10 @@ struct HsParticleWork {
     uint32_t exited;              // warps that have left the queue
     unsigned long long t_fix;     // sum of depth-term differences, fixed point 2^-24 mm
     uint32_t n_and, n_or, n_hit;  // sum(S and r_m), sum(r_m and not S), rendered pixels
-    uint32_t pad;
+    uint32_t tx_test;             // zero, except to test the observation wait's time limit: the particle's
+                                  // first warp then arms its first load for this many bytes more than are
+                                  // copied, so that wait runs out (no copy is left in flight); the kernels
+                                  // only read it, and the last contributor clears the slot as usual
 };
 
 struct RenderArgs {
@@ -210,6 +213,8 @@ cudaError_t launch_render_score(const CUtensorMap& tm_depth, const CUtensorMap& 
                                 cudaStream_t stream);
 cudaError_t launch_render_tiles(int variant, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,
                                 const RenderArgs& args, cudaStream_t stream);
+cudaError_t launch_render_strips(int variant, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,
+                                 const RenderArgs& args, cudaStream_t stream);
 cudaError_t launch_obs_stats(const unsigned char* depth, int depth_pitch, int depth_f32, const uint8_t* skin,
                              int skin_pitch, int W, int H, uint32_t* stats, cudaStream_t stream);
 cudaError_t launch_obs_stats_multi(const BatchDev& batch, int max_H, cudaStream_t stream);

@@ -34,13 +34,7 @@ __device__ __forceinline__ void stage_prims(const float4* rec, int n_prims, cons
                                             int2* pbox, int tid, int nthreads)
 {
     for (int j = tid; j < n_prims; j += nthreads) {
-        const RasterPrim R = make_raster(rec + 4 * j, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y);
-        float4* d = rast + 5 * j;
-        d[0] = R.q0;
-        d[1] = R.q1;
-        d[2] = R.q2;
-        d[3] = R.q3;
-        d[4] = R.q4;
+        make_raster(rec + 4 * j, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y, rast + kRastVec * j);
         const float4 r3 = rec[4 * j + 3];
         pbox[j] = make_int2(__float_as_int(r3.z), __float_as_int(r3.w));
     }
@@ -117,12 +111,14 @@ __device__ __forceinline__ void cull_unit(const int2* pbox, int n_prims, int lan
 // so that the L2 latency of the loads hides behind the units in between.
 // Adds the rendered pixels' Eq. 4 terms to the lane's sums.  Returns false if
 // an observation load did not arrive in time (status flagged; the warp's
-// remaining units are skipped and no copy is left in flight).
+// remaining units are skipped and no copy is left in flight).  extra_tx: zero,
+// except in the test of that time limit (bytes the first load is armed for
+// beyond those copied).
 __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2* pbox, int n_prims, const int* box,
                                                   unsigned char (*tile)[kSlot], uint64_t* bar, uint32_t& phases,
                                                   int first, int stride, const ParticleView& pv, const RenderArgs& a,
                                                   int p, int lane, long long& acc_t, uint32_t& acc_a,
-                                                  uint32_t& acc_o, uint32_t& acc_h)
+                                                  uint32_t& acc_o, uint32_t& acc_h, uint32_t extra_tx = 0u)
 {
     const int xa = box[0], v0 = box[1], nux = box[2], n_units = box[3];
     if (first >= n_units) return true;
@@ -149,7 +145,7 @@ __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2
         if (lane == 0) {
             const int x0 = xa + kUW * ix, y0 = v0 + kUH * iy;
             fence_proxy_async();  // the stage's last generic reads come before the refill
-            mbar_arrive_expect_tx(&bar[st], tx_bytes);
+            mbar_arrive_expect_tx(&bar[st], tx_bytes + (issued == 0 ? extra_tx : 0u));
             tma_load_2d(tile[st], pv.tm_depth, x0, y0, &bar[st]);
             tma_load_2d(tile[st] + 256, pv.tm_skin, x0, y0, &bar[st]);
         }
@@ -180,31 +176,31 @@ __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2
                 while (mask) {
                     const int b = __ffs(mask) - 1;
                     mask &= mask - 1;
-                    const float4* R = rast + 5 * (b + 32 * w);
+                    const float4* R = rast + kRastVec * (b + 32 * w);
                     const bool in0 = (a0 >> b) & 1u, in1 = (a1 >> b) & 1u;  // warp-uniform
-                    const float4 q0 = R[0], q1 = R[1];
+                    const float4 q0 = R[0];
                     const float dv = fpy - q0.y, du0 = fpx0 - q0.x, du1 = fpx1 - q0.x;
-                    const float d0 = raster_disc(q0, q1, du0, dv), d1 = raster_disc(q0, q1, du1, dv);
-                    const bool caps = __float_as_uint(R[4].w) != 0u;
+                    const float d0 = raster_disc(R, du0, dv), d1 = raster_disc(R, du1, dv);
+                    const bool caps = raster_caps(R) != 0u;
                     const uint32_t v0 = __ballot_sync(0xffffffffu, in0 && (d0 >= 0.f || caps));
                     const uint32_t v1 = __ballot_sync(0xffffffffu, in1 && (d1 >= 0.f || caps));
                     if (v0 | v1) {
-                        const float4 q2 = R[2], q3 = R[3], q4 = R[4];
+                        const float t0 = R[3].z;
                         if (v0) {
-                            const float sh0 = raster_hit(q2, q3, q4, du0, dv, d0);
-                            const float zz0 = q2.w + sh0;
+                            const float sh0 = raster_hit(R, du0, dv, d0);
+                            const float zz0 = t0 + sh0;
                             if (zz0 < z[0]) {
                                 z[0] = zz0;
-                                zt[0] = q2.w;
+                                zt[0] = t0;
                                 zs[0] = sh0;
                             }
                         }
                         if (v1) {
-                            const float sh1 = raster_hit(q2, q3, q4, du1, dv, d1);
-                            const float zz1 = q2.w + sh1;
+                            const float sh1 = raster_hit(R, du1, dv, d1);
+                            const float zz1 = t0 + sh1;
                             if (zz1 < z[1]) {
                                 z[1] = zz1;
-                                zt[1] = q2.w;
+                                zt[1] = t0;
                                 zs[1] = sh1;
                             }
                         }

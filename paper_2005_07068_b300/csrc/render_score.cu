@@ -42,7 +42,7 @@ namespace hs {
 constexpr int kWarps = 4;  // warps per CTA; they share one staged copy of the records
 
 struct RenderShared {
-    float4 rast[kMaxPrims * 5];  // raster records (RasterPrim) of the particle's primitives
+    float4 rast[kMaxPrims * kRastVec];  // raster records of the particle's primitives
     int2 pbox[kMaxPrims];        // their pixel boxes (the packed words 14, 15 of the FK record)
     alignas(128) unsigned char tile[kWarps][kStages][kSlot];
     uint64_t bar[kWarps][kStages];
@@ -81,8 +81,11 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
     long long acc_t = 0;
     uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
     uint32_t phases = 0u;
+    // zero but in the test of the observation wait's time limit
+    const uint32_t extra_tx = blockIdx.x == 0 && warp == 0 ? wk->tx_test : 0u;
     render_units_warp(sm.rast, sm.pbox, a.n_prims, sm.box, sm.tile[warp], sm.bar[warp], phases,
-                      blockIdx.x * kWarps + warp, gridDim.x * kWarps, pv, a, p, lane, acc_t, acc_a, acc_o, acc_h);
+                      blockIdx.x * kWarps + warp, gridDim.x * kWarps, pv, a, p, lane, acc_t, acc_a, acc_o, acc_h,
+                      extra_tx);
 
     // the next kernel may start launching once every warp is past its units (it
     // still waits for this grid to finish before it reads E)

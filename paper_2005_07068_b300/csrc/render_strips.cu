@@ -1,0 +1,302 @@
+// render_strips.cu -- render + Eq. 4-5 cost by pixel strips (the strip kernel),
+// the third layout of the same computation as render_score_kernel and the
+// tile kernels (Section III.A: depth map r_d of hypothesis h, match map r_m,
+// D of Eq. 4, E = D + lambda_k kc of Eq. 5).
+//
+//  * grid (K, P) of 4-warp CTAs; the particle's screen box (union of its
+//    primitives' boxes, clipped to the ROI) is cut into strips 8 pixels wide
+//    and SH rows tall, dealt round-robin to the 4K warps of the particle; a
+//    warp renders its strips on its own (no CTA barrier after the prologue);
+//  * a lane owns one column of the strip and one row of every 4-row step
+//    (8 x 4 pixels per step, SH / 4 steps), and keeps the nearest hit of its
+//    SH / 4 pixels in registers;
+//  * per strip, the primitives whose box meets it are culled with two
+//    ballots; for each of them every lane forms the du terms of its column
+//    once (discriminant, A, B and, for cones, C and the axial coordinate:
+//    Poly2Col), then each step of the primitive's rows costs one polynomial
+//    (two FMAs) and a vote, and the roots run only in steps where some lane
+//    can be hit -- the same arithmetic as raster_hit, so the nearest hit is
+//    bit-identical to the unit kernel's (lower primitive index on equal depth);
+//  * the strip's observation (16-pixel-wide 2-D TMA boxes, one per 4-row
+//    band, the skin needs 16-byte rows) is loaded into one of the warp's two
+//    shared-memory buffers while the previous strip renders;
+//  * the rendered pixels add their Eq. 4 terms (reading R1) to the lane's
+//    fixed-point / integer sums (add_pixel), and the last warp of the particle
+//    forms E (flush_and_finish).
+#include <atomic>
+
+#include "hs_units.cuh"
+
+namespace hs {
+
+constexpr int kStripWarps = 4;
+constexpr int kStripW = 8;  // strip width in pixels (a lane's column)
+
+template <int SH>
+struct StripShared {
+    static constexpr int kBands = SH / 4;
+    float4 rast[kMaxPrims * kRastVec];
+    int2 pbox[kMaxPrims];
+    // per warp, two buffers of kBands 16 x 4 boxes (depth at 0, skin at 256 of each slot)
+    alignas(128) unsigned char obs[kStripWarps][2][kBands][kSlot];
+    uint64_t bar[kStripWarps][2];
+    int box[4];  // xa, v0, u1, v1 of the clipped box (u1 < 0: empty)
+};
+
+// primitives whose pixel box meets columns [x0, x0 + 7] and rows [y0, y1]: bit j
+__device__ __forceinline__ uint64_t cull_strip(const int2* pbox, int n_prims, int lane, int x0, int y0, int y1)
+{
+    uint64_t m = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        bool in = false;
+        if (j < n_prims) {
+            const int2 bx = pbox[j];
+            in = lo_i16(__int_as_float(bx.x)) <= x0 + kStripW - 1 && lo_i16(__int_as_float(bx.y)) >= x0 &&
+                 hi_i16(__int_as_float(bx.x)) <= y1 && hi_i16(__int_as_float(bx.y)) >= y0;
+        }
+        m |= (uint64_t)__ballot_sync(0xffffffffu, in) << (32 * h);
+    }
+    return m;
+}
+
+// resident CTAs per SM the register budget is set for: the 32-row strips keep
+// twice the per-pixel state of the 16-row ones in registers
+template <int SH>
+constexpr int strip_min_ctas() { return SH > 16 ? 5 : 6; }
+
+template <int SH>
+__global__ void __launch_bounds__(kStripWarps * 32, strip_min_ctas<SH>())
+    render_strips_kernel(const __grid_constant__ CUtensorMap tm_depth, const __grid_constant__ CUtensorMap tm_skin,
+                         const RenderArgs a)
+{
+    constexpr int kSteps = SH / 4;
+    using Sh = StripShared<SH>;
+    __shared__ Sh sm;
+    const int p = a.order ? a.order[blockIdx.y] : (int)blockIdx.y;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    HsParticleWork* wk = a.work + p;
+    const ParticleView pv = particle_view(a, p, &tm_depth, &tm_skin);
+
+    if (lane < 2) mbar_init(&sm.bar[warp][lane], 1);
+    if (tid == 0) mbar_fence_init();
+    pdl_wait();  // the primitive records and kc come from the previous kernel
+    const int n_prims = a.n_prims;
+    const float4* src = a.prims + (size_t)p * n_prims * 4;
+    stage_prims(src, n_prims, pv, sm.rast, sm.pbox, tid, kStripWarps * 32);
+    if (warp == 0) {  // the particle's screen box, clipped to the ROI
+        int u0 = INT_MAX, v0 = INT_MAX, u1 = INT_MIN, v1 = INT_MIN;
+        for (int i = lane; i < n_prims; i += 32) {
+            const float4 r3 = src[4 * i + 3];
+            u0 = min(u0, lo_i16(r3.z));
+            v0 = min(v0, hi_i16(r3.z));
+            u1 = max(u1, lo_i16(r3.w));
+            v1 = max(v1, hi_i16(r3.w));
+        }
+        u0 = __reduce_min_sync(0xffffffffu, u0);
+        v0 = __reduce_min_sync(0xffffffffu, v0);
+        u1 = __reduce_max_sync(0xffffffffu, u1);
+        v1 = __reduce_max_sync(0xffffffffu, v1);
+        if (lane == 0) {
+            u0 = max(u0, 0);
+            v0 = max(v0, 0);
+            u1 = min(u1, pv.W - 1);
+            v1 = min(v1, pv.H - 1);
+            const bool empty = u0 > u1 || v0 > v1;
+            sm.box[0] = u0 & ~15;  // TMA: the uint8 skin needs x at a multiple of 16 bytes
+            sm.box[1] = v0;
+            sm.box[2] = empty ? -1 : u1;
+            sm.box[3] = v1;
+        }
+    }
+    __syncthreads();
+    const int xa = sm.box[0], by0 = sm.box[1], bx1 = sm.box[2], by1 = sm.box[3];
+    const float kcp = a.kc[p];
+    if (bx1 < 0) {  // nothing of the hand inside the ROI: E is the baseline
+        pdl_launch_dependents();
+        if (blockIdx.x == 0 && tid == 0) write_baseline(a, p, pv.stats, kcp);
+        return;
+    }
+    const int nsx = (bx1 + 1 - xa + kStripW - 1) / kStripW;
+    const int n_strips = nsx * ((by1 + 1 - by0 + SH - 1) / SH);
+    const int first = blockIdx.x * kStripWarps + warp, stride = gridDim.x * kStripWarps;
+    const int W = pv.W, H = pv.H, depth_f32 = pv.depth_f32;
+    const int lx = lane & 7, ly = lane >> 3;
+    uint64_t* bar = sm.bar[warp];
+
+    // zero but in the test of the observation wait's time limit (bytes the
+    // particle's first load is armed for beyond those copied)
+    uint32_t extra_tx = blockIdx.x == 0 && warp == 0 ? wk->tx_test : 0u;
+    // the observation of strip q into buffer b: one 16 x 4 box of depth and of
+    // skin per band of rows inside the box, issued by one lane each
+    auto issue = [&](int q, int b) {
+        const int sy = q / nsx, sx = q - sy * nsx;
+        const int x16 = (xa + kStripW * sx) & ~15, y0 = by0 + SH * sy;
+        const int nb = (min(y0 + SH - 1, by1) - y0) / 4 + 1;
+        if (lane == 0) {
+            fence_proxy_async();  // the buffer's last generic reads come before the refill
+            mbar_arrive_expect_tx(&bar[b], (uint32_t)nb * 64u * (uint32_t)((depth_f32 ? 4 : 2) + 1) + extra_tx);
+        }
+        extra_tx = 0u;
+        __syncwarp();
+        if (lane < nb) {
+            tma_load_2d(sm.obs[warp][b][lane], pv.tm_depth, x16, y0 + 4 * lane, &bar[b]);
+            tma_load_2d(sm.obs[warp][b][lane] + 256, pv.tm_skin, x16, y0 + 4 * lane, &bar[b]);
+        }
+    };
+
+    long long acc_t = 0;
+    uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
+    uint32_t phases = 0u;
+    bool ok = true;
+    int buf = 0;
+    int q = first;
+    bool next_issued = false;  // the load of strip q + stride is in flight in buffer buf ^ 1
+    if (first < n_strips) issue(first, 0);
+    for (; q < n_strips; q += stride, buf ^= 1) {
+        next_issued = q + stride < n_strips;
+        if (next_issued) issue(q + stride, buf ^ 1);  // the next strip's observation meanwhile
+        const int sy = q / nsx, sx = q - sy * nsx;
+        const int x0 = xa + kStripW * sx, y0 = by0 + SH * sy;
+        const int y1 = min(y0 + SH - 1, by1);
+        // per pixel of the lane: nearest depth z = t0 + zs, the offset zs from
+        // the primitive's centre depth t0, and that t0
+        float z[kSteps], zt[kSteps], zs[kSteps];
+#pragma unroll
+        for (int s = 0; s < kSteps; ++s) {
+            z[s] = INFINITY;
+            zt[s] = 0.f;
+            zs[s] = 0.f;
+        }
+        const float fx = (float)(x0 + lx), fy0 = (float)(y0 + ly);
+        uint64_t mask = cull_strip(sm.pbox, n_prims, lane, x0, y0, y1);
+        while (mask) {  // warp-uniform walk over the strip's primitives, in index order
+            const int j = __ffsll((long long)mask) - 1;
+            mask &= mask - 1;
+            const float4* R = sm.rast + kRastVec * j;
+            const int2 pb = sm.pbox[j];
+            const int s0 = (max(hi_i16(__int_as_float(pb.x)), y0) - y0) >> 2;
+            const int s1 = (min(hi_i16(__int_as_float(pb.y)), y1) - y0) >> 2;
+            const float4 q0 = R[0], q1 = R[1];
+            const float du = fx - q0.x;
+            const uint32_t caps = raster_caps(R);
+            const Poly2Col PD = poly2_col(q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, du);
+            // coverage of every step of the primitive's rows at once
+            // (independent polynomials, one bit each, no branch per step)
+            uint32_t m = 0u;
+#pragma unroll
+            for (int s = 0; s < kSteps; ++s) {
+                const float dv = (fy0 + (float)(4 * s)) - q0.y;
+                m |= (uint32_t)(PD.at(dv) >= 0.f || caps != 0u) << s;
+            }
+            m &= (2u << s1) - (1u << s0);  // the steps of the primitive's rows
+            const uint32_t wm = __reduce_or_sync(0xffffffffu, m);  // steps some lane can hit
+            if (!wm) continue;
+            // the roots, where some lane of the step can be hit; the nearest hit
+            // per pixel (strict <: the lower primitive index wins equal depths)
+            const float4 q2 = R[2], q3 = R[3], q4 = R[4], q5 = R[5];
+            const float t0 = q3.z;
+            const bool ell = q3.w > 1.5f;
+            const Poly2Col PA = poly2_col(q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, du);
+            const Poly2Col PB = poly2_col(q4.x, q4.y, q4.z, q4.w, q5.x, q5.y, du);
+            Poly2Col PC{0.f, 0.f, 0.f};
+            float gy_u = 0.f, gy_v = 0.f, hy_u = 0.f, hy_v = 0.f;
+            if (!ell) {
+                const float4 q6 = R[6], q7 = R[7], q8 = R[8];
+                PC = poly2_col(q6.x, q6.y, q6.z, q6.w, q7.x, q7.y, du);
+                gy_u = fmaf(du, q7.z, 0.f);  // lin2(0, gY_u, gY_v) with its du term formed once
+                gy_v = q7.w;
+                hy_u = fmaf(du, q8.y, q8.x);
+                hy_v = q8.z;
+            }
+#pragma unroll
+            for (int s = 0; s < kSteps; ++s) {
+                if (!((wm >> s) & 1u)) continue;  // no lane can be hit in this step (warp-uniform)
+                const float dv = (fy0 + (float)(4 * s)) - q0.y;
+                const float disc = PD.at(dv);
+                float sh = INFINITY;
+                if (disc >= 0.f) {
+                    const float A = PA.at(dv), B = PB.at(dv);
+                    if (ell) {
+                        sh = ellipsoid_root(t0, A, B, disc);
+                    } else {
+                        const float C = PC.at(dv);
+                        sh = cone_root(t0, A, B, C, fmaf(dv, gy_v, gy_u), fmaf(dv, hy_v, hy_u), disc);
+                    }
+                }
+                if (caps) sh = cone_caps(R, caps, du, dv, sh);
+                const float zz = t0 + sh;
+                if (((m >> s) & 1u) && zz < z[s]) {
+                    z[s] = zz;
+                    zt[s] = t0;
+                    zs[s] = sh;
+                }
+            }
+        }
+        ok = mbar_wait_bounded(&bar[buf], (phases >> buf) & 1u, a.status);
+        phases ^= 1u << buf;
+        if (!ok) break;
+        {
+            const int px = x0 + lx, c = (x0 & 15) + lx;  // column inside the 16-wide boxes
+#pragma unroll
+            for (int s = 0; s < kSteps; ++s) {
+                const int py = y0 + 4 * s + ly;
+                const bool hit = z[s] < INFINITY && px < W && py < H;
+                if (!__any_sync(0xffffffffu, hit)) continue;  // nothing rendered in this step
+                if (hit) {
+                    const unsigned char* t = sm.obs[warp][buf][s];
+                    const int oi = ly * 16 + c;
+                    const float od = depth_f32 ? reinterpret_cast<const float*>(t)[oi]
+                                               : (float)reinterpret_cast<const uint16_t*>(t)[oi];
+                    const bool rm = add_pixel(od, t[256 + oi] != 0, zt[s], zs[s], a, acc_t, acc_a, acc_o, acc_h);
+                    if (a.dbg_depth) {
+                        const size_t o = ((size_t)p * H + py) * W + px;
+                        a.dbg_depth[o] = z[s];
+                        a.dbg_mask[o] = (uint8_t)(1 | (rm ? 2 : 0));
+                    }
+                }
+            }
+        }
+        __syncwarp();  // every lane is done with this buffer before it is refilled
+    }
+    if (!ok) {
+        // a load that did not arrive in time (status flagged): the warp's
+        // remaining strips are skipped, and the copies still expected -- the
+        // late one and the next strip's, if issued -- are awaited (bounded)
+        // so that none is in flight when the CTA leaves
+        mbar_wait_bounded(&bar[buf], ((phases >> buf) & 1u) ^ 1u, a.status);
+        if (next_issued) mbar_wait_bounded(&bar[buf ^ 1], (phases >> (buf ^ 1)) & 1u, a.status);
+    }
+    pdl_launch_dependents();
+    warp_sum(acc_t, acc_a, acc_o, acc_h);
+    if (lane == 0) flush_and_finish(a, p, wk, pv.stats, kcp, acc_t, acc_a, acc_o, acc_h, gridDim.x * kStripWarps);
+}
+
+template <int SH>
+static cudaError_t launch_strips(const CUtensorMap& tm_depth, const CUtensorMap& tm_skin, const RenderArgs& args,
+                                 cudaStream_t stream)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(args.K, args.P);
+    cfg.blockDim = dim3(kStripWarps * 32);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, render_strips_kernel<SH>, tm_depth, tm_skin, args);
+}
+
+cudaError_t launch_render_strips(int variant, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,
+                                 const RenderArgs& args, cudaStream_t stream)
+{
+    switch (variant) {
+    case HS_RENDER_STRIPS_8x16: return launch_strips<16>(tm_depth, tm_skin, args, stream);
+    case HS_RENDER_STRIPS_8x32: return launch_strips<32>(tm_depth, tm_skin, args, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace hs

@@ -35,8 +35,8 @@ constexpr int kMaxDevices = 64;
 template <int TW, int TH>
 struct TileLayout {
     static constexpr int kBoxes = (TW / 16) * (TH / 4);  // 16 x 4 TMA boxes per tile
-    static constexpr int kRast = 0;                       // float4 [kMaxPrims][5]: raster records
-    static constexpr int kPBox = kRast + kMaxPrims * 80;  // int2 [kMaxPrims]: packed pixel boxes
+    static constexpr int kRast = 0;                       // float4 [kMaxPrims][kRastVec]: raster records
+    static constexpr int kPBox = kRast + kMaxPrims * 16 * kRastVec;  // int2 [kMaxPrims]: packed pixel boxes
     static constexpr int kZ = kPBox + kMaxPrims * 8;      // u64 [TH][TW]
     static constexpr int kDepth = kZ + TW * TH * 8;       // box b at b * 256 (16 x 4 x <= 4 bytes)
     static constexpr int kSkin = kDepth + kBoxes * 256;   // box b at b * 128 (16 x 4 bytes)
@@ -86,13 +86,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
     const int n_prims = a.n_prims;
     const float4* src = a.prims + (size_t)p * n_prims * 4;
     for (int j = tid; j < n_prims; j += NW * 32) {  // raster form of each primitive, once per CTA
-        const RasterPrim R = make_raster(src + 4 * j, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y);
-        float4* d = s_rast + 5 * j;
-        d[0] = R.q0;
-        d[1] = R.q1;
-        d[2] = R.q2;
-        d[3] = R.q3;
-        d[4] = R.q4;
+        make_raster(src + 4 * j, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y, s_rast + kRastVec * j);
         const float4 r3 = src[4 * j + 3];
         s_pbox[j] = make_int2(__float_as_int(r3.z), __float_as_int(r3.w));
     }
@@ -139,6 +133,9 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
     uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
     uint32_t phase = 0;
     bool ok = true;
+    // zero but in the test of the observation wait's time limit (bytes the
+    // particle's first tile load is armed for beyond those copied)
+    uint32_t extra_tx = blockIdx.x == 0 ? wk->tx_test : 0u;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int ty = t / ntx, tx = t - ty * ntx;
         const int tx0 = xa + tx * TW, ty0 = by0 + ty * TH;
@@ -149,7 +146,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
             const int nbx = (cx1 - tx0) / 16 + 1, nby = (cy1 - ty0) / 4 + 1;
             if (lane == 0) {
                 fence_proxy_async();  // the last tile's generic reads come before these writes
-                mbar_arrive_expect_tx(s_bar, (uint32_t)(nbx * nby) * 64u * (esz + 1u));
+                mbar_arrive_expect_tx(s_bar, (uint32_t)(nbx * nby) * 64u * (esz + 1u) + extra_tx);
             }
             __syncwarp();
             for (int b = lane; b < nbx * nby; b += 32) {
@@ -214,25 +211,27 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
             const int4 rc = s_rect[k];
             const uint32_t mg = s_magic[k];
             const int c0 = s_pre[k], c1 = s_pre[k + 1];
-            const float4 q0 = s_rast[5 * j], q1 = s_rast[5 * j + 1], q2 = s_rast[5 * j + 2],
-                         q3 = s_rast[5 * j + 3], q4 = s_rast[5 * j + 4];
+            const float4* R = s_rast + kRastVec * j;
+            const float4 q0 = R[0];
+            const float t0 = R[3].z;
             for (; c < c1; c += NW) {
                 const int idx = ((c - c0) << 5) + lane;
                 if (idx < rc.w) {
                     const int y = (int)(((unsigned long long)(uint32_t)idx * mg) >> 31);
                     const int px = rc.x + idx - y * rc.z, py = rc.y + y;
                     const float du = (float)px - q0.x, dv = (float)py - q0.y;
-                    const float disc = raster_disc(q0, q1, du, dv);
-                    const float sh = raster_maybe(q4, disc) ? raster_hit(q2, q3, q4, du, dv, disc) : INFINITY;
-                    const float zz = q2.w + sh;
+                    const float disc = raster_disc(R, du, dv);
+                    const float sh = raster_maybe(R, disc) ? raster_hit(R, du, dv, disc) : INFINITY;
+                    const float zz = t0 + sh;
                     if (zz < INFINITY) {
-                        const float dz = sh - (zz - q2.w);  // z - t0 is exact (Sterbenz): dz is the residual
+                        const float dz = sh - (zz - t0);  // z - t0 is exact (Sterbenz): dz is the residual
                         atomicMin(&s_z[(py - ty0) * TW + (px - tx0)],
                                   ((unsigned long long)__float_as_uint(zz) << 32) | __float_as_uint(dz));
                     }
                 }
             }
         }
+        extra_tx = 0u;
         ok = __syncthreads_and(mbar_wait_bounded(s_bar, phase, a.status));
         if (!ok) break;
         phase ^= 1u;

@@ -62,10 +62,12 @@ class HsScoreParams(ctypes.Structure):
 
 
 # render kernels (same results, different work layout); AUTO picks by particles per call
-RENDER_AUTO, RENDER_UNITS, RENDER_TILES_32x16, RENDER_TILES_32x32, RENDER_TILES_64x32, RENDER_TILES_64x64 = range(6)
+(RENDER_AUTO, RENDER_UNITS, RENDER_TILES_32x16, RENDER_TILES_32x32, RENDER_TILES_64x32, RENDER_TILES_64x64,
+ RENDER_STRIPS_8x16, RENDER_STRIPS_8x32) = range(8)
 RENDER_VARIANTS = {"auto": RENDER_AUTO, "units": RENDER_UNITS, "tiles32x16": RENDER_TILES_32x16,
                    "tiles32x32": RENDER_TILES_32x32, "tiles64x32": RENDER_TILES_64x32,
-                   "tiles64x64": RENDER_TILES_64x64}
+                   "tiles64x64": RENDER_TILES_64x64, "strips8x16": RENDER_STRIPS_8x16,
+                   "strips8x32": RENDER_STRIPS_8x32}
 
 
 class HsSwarm(ctypes.Structure):

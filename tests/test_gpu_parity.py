@@ -164,6 +164,12 @@ def test_render_variants_agree(ctas):
         assert np.array_equal(gr.mask, ref.mask), v
         assert np.abs(gr.depth - ref.depth).max() <= 1e-4, v
         assert np.all(np.abs(gr.E - ref.E) <= 1e-6 * np.abs(ref.E) + 1e-5), v
+        if v in (hs.RENDER_STRIPS_8x16, hs.RENDER_STRIPS_8x32):
+            # the strip kernels run the unit kernel's arithmetic with the column
+            # terms formed once: the same nearest hit and sums, bit for bit
+            assert np.array_equal(gr.depth.view(np.uint32), ref.depth.view(np.uint32)), v
+            assert np.array_equal(gr.E.view(np.uint32), ref.E.view(np.uint32)), v
+            assert np.array_equal(gr.parts, ref.parts), v
 
 
 def test_ground_truth_scores_zero_depth_term():
@@ -176,7 +182,8 @@ def test_ground_truth_scores_zero_depth_term():
     assert abs(D0) < 1e-3  # float32 observation of the FP64 render
 
 
-@pytest.mark.parametrize("variant", [hs.RENDER_UNITS, hs.RENDER_TILES_32x16, hs.RENDER_TILES_64x64])
+@pytest.mark.parametrize("variant", [hs.RENDER_UNITS, hs.RENDER_TILES_32x16, hs.RENDER_TILES_64x64,
+                                     hs.RENDER_STRIPS_8x16])
 def test_brute_force_8x8(variant):
     """8x8 ROIs: every pixel compared one by one with the oracle."""
     for seed in (11, 12, 13):
@@ -200,8 +207,11 @@ def test_empty_roi_and_offscreen_particles():
 
 
 def test_many_particles_sampled():
-    """P = 1500 at 64x64 (grid of one CTA per particle): E of every particle, and
-    the per-pixel check on a sample."""
+    """P = 1500 at 64x64 (grid of one CTA per particle): E of every particle
+    against the oracle; every particle outside the E tolerance, and a random
+    sample of 24 more, go through the whole per-pixel protocol (boundary-only
+    flips, and E against the oracle cost recomputed from the GPU's own pixel
+    decisions)."""
     sc = C.make_scene(64, 64, 1500, 105, spread=2.0)
     gr = C.run_gpu(sc, debug=False)
     gt = C.run_gpu(sc, debug=False, variant=hs.RENDER_TILES_64x32)
@@ -210,13 +220,17 @@ def test_many_particles_sampled():
     o = C.run_oracle(sc, per_pixel=False)
     err = np.abs(gr.E - o["E"])
     ok = err <= C.E_REL_TOL * np.abs(o["E"]) + C.E_ABS_TOL
-    # a particle may carry a boundary flip (checked per pixel on the sample below)
     assert np.median(err / np.abs(o["E"])) < 1e-6
-    assert ok.mean() > 0.99
     REPORT["P1500_frac_within_tol"] = float(ok.mean())
-    idx = np.random.default_rng(0).choice(1500, 24, replace=False)
-    sub = C.Scene(sc.W, sc.H, sc.cam, sc.gt, sc.Od, sc.S, sc.poses[idx], sc.model_o, sc.model_g)
-    C.check_parity(sub, C.run_gpu(sub), C.run_oracle(sub))
+    out = np.flatnonzero(~ok)
+    REPORT["P1500_rechecked_per_pixel"] = int(out.size)
+    idx = np.union1d(out, np.random.default_rng(0).choice(1500, 24, replace=False))
+    for chunk in np.array_split(idx, max(1, idx.size // 32)):
+        sub = C.Scene(sc.W, sc.H, sc.cam, sc.gt, sc.Od, sc.S, sc.poses[chunk], sc.model_o, sc.model_g)
+        flipped = C.check_parity(sub, C.run_gpu(sub), C.run_oracle(sub))
+        # a particle outside the direct tolerance is explained by a boundary flip
+        # (check_parity has then passed its conditional E check)
+        assert np.all(flipped[np.isin(chunk, out)])
 
 
 def test_deterministic_repeat():

@@ -33,18 +33,38 @@ sys.path.insert(0, ROOT)
 
 W, H = 320, 240
 PARTICLES, GENS, FRAMES = 64, 40, 30
+HOST_WALL_FRAMES = 240
 METRIC = "hypothesis evals/s (render+cost, 320x240 ROI)"
 WORKLOAD = ("Kinect-scale tracking: 320x240 uint16 depth + uint8 skin frames (600 mm plane, N(0,3 mm) noise, "
             "5% holes, 2% skin flips), 64 particles x 40 generations per frame, 30-frame seeded trajectory")
 FP32_LANES_PER_SM = 128
-# Algorithmic FP32 operations per ray-primitive test (a pixel inside a
-# primitive's exact box), the fixed tally of the textbook per-pixel test (an
-# FMA counts 2): ray point and direction in the primitive's scaled local
-# coordinates (25), quadric coefficients and discriminant (ellipsoid 20;
-# cone 24 + cap planes 28 + 1 compare).  The kernels decide coverage with
-# fewer operations (the discriminant as a polynomial in the pixel offsets);
-# the tally stays the unit of work, so a faster kernel reads higher.
-FLOP_PER_TEST = {0: 45, 1: 78}
+XU_PER_SM_CLK = 16  # MUFU (square root, reciprocal) results per SM per clock: 4 per SM sub-partition
+# Algorithmic work of one ray-primitive test (a pixel inside a primitive's
+# exact screen box), the textbook per-pixel test counted once per primitive
+# kind (an FMA counts 2 FLOP; the primitive's local ray origin o = -M C and
+# the quadric's constant term are per-primitive, not per-test, work):
+#   every test:  local direction h = M (a, b, 1): 3 x 2 FMA = 12;
+#     ellipsoid  A = h.h (5), B = o.h (5), disc = B^2 - A C (3), disc >= 0 (1)            = 26
+#     cone       w = kappa h_y (1), A = h_x^2 + h_z^2 - w^2 (5),
+#                B = o_x h_x + o_z h_z - (1 + kappa o_y) w (5), disc (3), disc >= 0 (1)   = 27
+#   a hit adds:  ellipsoid  s = (-B - sqrt(disc)) / A: 2, t > 0: 1, nearest depth: 1  = 4 FLOP, 2 XU
+#                cone       q = -(B + sign(B) sqrt(disc)): 1, s1 = q / A, s2 = C / q: 2,
+#                           y = o_y + s h_y (x2): 4, |y| <= 1 (x2): 2, t > 0 (x2): 2,
+#                           nearest: 1                                                  = 12 FLOP, 3 XU
+# and a test hits with probability pi / 4, the fraction of its tight
+# axis-aligned box that an ellipse covers (oracle renders of 640x480 poses
+# give 0.66 hits per box pixel with the 1-pixel box margin).  So a test is
+# 26 + 4 pi/4 = 29.1 FLOP and 1.57 XU (ellipsoid), 27 + 12 pi/4 = 36.4 FLOP
+# and 2.36 XU (cone).  The kernels decide coverage and the roots with fewer
+# operations (quadratic polynomials in the pixel offsets); the tally stays the
+# unit of work, so a faster kernel reads higher.
+HIT_FILL = math.pi / 4
+TALLY = {0: (26.0, 4.0, 2.0), 1: (27.0, 12.0, 3.0)}  # kind: (FLOP per test, FLOP per hit, XU per hit)
+FLOP_PER_TEST = {k: t + HIT_FILL * h for k, (t, h, _) in TALLY.items()}
+XU_PER_TEST = {k: HIT_FILL * x for k, (_, _, x) in TALLY.items()}
+TALLY_BASIS = ("pixel-exact primitive boxes x per-test tally of the textbook ray-quadric test: ellipsoid "
+               f"{FLOP_PER_TEST[0]:.1f} FLOP + {XU_PER_TEST[0]:.2f} XU, cone {FLOP_PER_TEST[1]:.1f} FLOP + "
+               f"{XU_PER_TEST[1]:.2f} XU (miss part + pi/4 x hit part; derivation in bench.py and DESIGN)")
 
 
 def _env_int(k, d):
@@ -65,6 +85,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample")
     ap.add_argument("--profile", action="store_true", help="short run for an ncu launch list")
     ap.add_argument("--no-roofline", action="store_true", help="skip the render roofline replay")
+    ap.add_argument("--no-sub-rooflines", action="store_true",
+                    help="skip the render rooflines of the batched (64 sequences) and 640x480 workloads")
     ap.add_argument("--no-frame-path", action="store_true",
                     help="skip the second measurement through track_frame (one launch per frame)")
     ap.add_argument("--render", default="tune", help="render kernel: tune (timed on the workload first), auto, "
@@ -101,6 +123,7 @@ KERNEL_SOURCES = {
     "units": ["render_score.cu", "hs_units.cuh", "hs_render.cuh", "hs_args.cuh", "hs_device.cuh"],
     "tiles": ["render_tiles.cu", "hs_render.cuh", "hs_args.cuh", "hs_device.cuh"],
     "frame": ["frame.cu", "hs_units.cuh", "hs_step.cuh", "hs_fk.cuh", "hs_render.cuh", "hs_args.cuh", "hs_device.cuh"],
+    "strips": ["render_strips.cu", "hs_units.cuh", "hs_render.cuh", "hs_args.cuh", "hs_device.cuh"],
 }
 PROFILE_FILES = {("kinect", "units"): "render_units_kinect_320x240.txt",
                  ("batch", "tiles"): "render_tiles32x32_batch_64seq.txt",
@@ -118,7 +141,7 @@ def source_sha256(kind: str) -> str:
 def profile_traffic(workload: str, kernel: str):
     """dram bytes per launch from the committed ncu summary of this workload's
     render kernel, if it was taken on the kernel's current source; else None."""
-    kind = kernel if kernel in ("units", "frame") else "tiles"
+    kind = kernel if kernel in ("units", "frame") else "strips" if kernel.startswith("strips") else "tiles"
     name = PROFILE_FILES.get((workload, kind))
     if name is None:
         return None
@@ -167,8 +190,10 @@ class _Nvml:
 
 
 class ClockSampler:
-    """SM clock and throttle reasons sampled every 10 ms through NVML
-    (read-only), so that even a short timed region gets samples."""
+    """SM clock and throttle reasons sampled every 2 ms through NVML
+    (read-only), so that even a short timed region gets several samples (the
+    host enqueues the timed steps ahead of the GPU, so the sampler's brief
+    turns on the interpreter do not open gaps on the device)."""
     HW, HW_THERMAL, SW_THERMAL, SW_POWER = 0x8, 0x40, 0x20, 0x4
 
     def __init__(self, index: int):
@@ -194,7 +219,7 @@ class ClockSampler:
                     self.samples.append((self._nv.clock(), self._nv.reasons()))
                 except Exception:
                     pass
-                self._stop.wait(0.01)
+                self._stop.wait(0.002)
 
         self._t = threading.Thread(target=run, daemon=True)
         self._t.start()
@@ -213,7 +238,7 @@ class ClockSampler:
                  self.SW_THERMAL: "sw_thermal_slowdown", self.SW_POWER: "sw_power_cap"}
         reasons = sorted({n for _, r in self.samples for bit, n in names.items() if r & bit})
         return {"sm_mhz": statistics.median(sm for sm, _ in self.samples), "sm_max_mhz": self.max_mhz,
-                "reasons": reasons, "samples": len(self.samples), "source": "NVML every 10 ms"}
+                "reasons": reasons, "samples": len(self.samples), "source": "NVML every 2 ms"}
 
 
 # ---- synthetic frames ----------------------------------------------------------------------
@@ -245,12 +270,12 @@ def make_frames(seed: int, frames: int, hs, I, model, cam, device, W=W, H=H, tra
     return traj, obs, host
 
 
-def algorithmic_flops(box_words: np.ndarray, kinds: np.ndarray, Wp=W, Hp=H) -> float:
-    """FP32 work of one render_score_batch launch: for every particle and
-    primitive, the pixels of its conservative box inside the ROI (pixel-exact
-    box culling) times the per-test tally of its kind.  box_words: the last two
-    words of every HsPrim record, [P, n_prims, 2] float32 holding int16 boxes.
-    Wp, Hp: the ROI size, or per-particle arrays [P] for a batch."""
+def algorithmic_tests(box_words: np.ndarray, kinds: np.ndarray, Wp=W, Hp=H) -> np.ndarray:
+    """Ray-primitive tests of one render launch, per primitive kind: for every
+    particle and primitive, the pixels of its conservative box inside the ROI
+    (pixel-exact box culling).  box_words: the last two words of every HsPrim
+    record, [P, n_prims, 2] float32 holding int16 boxes.  Wp, Hp: the ROI size,
+    or per-particle arrays [P] for a batch.  Returns [tests of kind 0, kind 1]."""
     box = np.ascontiguousarray(box_words).view(np.int16).reshape(box_words.shape[0], box_words.shape[1], 4)
     Wp = np.broadcast_to(np.asarray(Wp), (box.shape[0],))[:, None]
     Hp = np.broadcast_to(np.asarray(Hp), (box.shape[0],))[:, None]
@@ -259,9 +284,47 @@ def algorithmic_flops(box_words: np.ndarray, kinds: np.ndarray, Wp=W, Hp=H) -> f
     u1 = np.clip(box[..., 2], 0, Wp - 1)
     v1 = np.clip(box[..., 3], 0, Hp - 1)
     inside = (box[..., 2] >= 0) & (box[..., 3] >= 0) & (box[..., 0] < Wp) & (box[..., 1] < Hp)
-    area = np.where(inside, (u1 - u0 + 1) * (v1 - v0 + 1), 0).astype(np.float64)
-    per_kind = np.array([FLOP_PER_TEST[int(k)] for k in kinds], np.float64)
-    return float((area * per_kind[None, :]).sum())
+    area = np.where(inside, (u1 - u0 + 1) * (v1 - v0 + 1), 0).astype(np.float64).sum(axis=0)
+    kinds = np.asarray(kinds)
+    return np.array([area[kinds == 0].sum(), area[kinds == 1].sum()])
+
+
+def fp32_xu_peaks(dev, peaks):
+    """FP32 and XU peaks from the unit counts and the measured maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz") or 2032.0)
+    return {"sms": sms, "sm_max_mhz": sm_max,
+            "fp32_tflops": sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12,
+            "xu_tops": sms * XU_PER_SM_CLK * sm_max * 1e6 / 1e12}
+
+
+def roofline_record(tests, launch_us, pk, kernel, timing, launches_timed, traffic=None, gens=1, note=None):
+    """The roofline of a render launch: FP32 side and XU side of the tally;
+    frac = the larger of the two fractions, and achieved / peak / unit are that
+    side's (so frac = achieved / peak).  tests: [ellipsoid, cone] tests per
+    generation; gens: generations per launch (the frame kernel)."""
+    tests = np.asarray(tests, np.float64) * gens
+    flop = float(tests[0] * FLOP_PER_TEST[0] + tests[1] * FLOP_PER_TEST[1])
+    xu = float(tests[0] * XU_PER_TEST[0] + tests[1] * XU_PER_TEST[1])
+    t = launch_us * 1e-6 if launch_us else float("inf")
+    ach_f, ach_x = flop / t / 1e12, xu / t / 1e12
+    frac_f, frac_x = ach_f / pk["fp32_tflops"], ach_x / pk["xu_tops"]
+    xu_side = frac_x > frac_f
+    rec = {"bound": "alu", "achieved": ach_x if xu_side else ach_f,
+           "peak": pk["xu_tops"] if xu_side else pk["fp32_tflops"],
+           "unit": "Top/s (XU)" if xu_side else "TFLOP/s", "frac": max(frac_f, frac_x),
+           "frac_fp32": frac_f, "frac_xu": frac_x, "traffic": traffic, "kernel": kernel,
+           "fp32": {"achieved_tflops": ach_f, "peak_tflops": pk["fp32_tflops"], "flop_per_launch": flop},
+           "xu": {"achieved_tops": ach_x, "peak_tops": pk["xu_tops"], "ops_per_launch": xu},
+           "tests_per_launch": float(tests.sum()),
+           "peak_basis": (f"FP32: {pk['sms']} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {pk['sm_max_mhz']:.0f} MHz; "
+                          f"XU: {pk['sms']} SMs x {XU_PER_SM_CLK} x {pk['sm_max_mhz']:.0f} MHz (sm_max_mhz of "
+                          f"measured)"),
+           "flop_basis": TALLY_BASIS, "launch_us": launch_us, "launches_timed": launches_timed, "timing": timing}
+    if note:
+        rec["note"] = note
+    return rec
 
 
 # ---- the CPU oracle (baseline leg and reference arm) ----------------------------------------
@@ -342,30 +405,14 @@ def percentile(xs, q):
     return xs[k]
 
 
-def run_batch(args, rank, world, local):
+def batch_setup(hs, I, model, seed, frames, dev, render, ctas):
+    """The batched workload: 64 sequences' frames resident in HBM (PackedObs
+    each, with pinned twins), the staging buffers the batch is bound to, the
+    batch and its tracker (render kernel autotuned on frame 0 when render is
+    "tune")."""
     import torch
-    from paper_2005_07068_b300 import build as B
-    from paper_2005_07068_b300 import handscore as hs
-    from paper_2005_07068_b300 import inputs as I
-    from paper_2005_07068_b300 import replicas as R
     from paper_2005_07068_b300.tracker import BatchTracker, PackedObs
-
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA GPU")
-    B.build()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    peaks = measured_peaks()
-    seed = R.replica_seed(I.CONFIG_SEED_BASE + 4, rank)
     sizes, Ps, seq_seeds = I.batch_workload(seed, BATCH_SEQ)
-    g = I.hand_geometry()
-    lo, hi = (a.astype(np.float32) for a in I.search_limits())
-    model = hs.Model.from_geometry(g, lo, hi)
-    frames = 2 if args.profile else BATCH_FRAMES
     cams, trajs = [], []
     store = [PackedObs(sizes, device=dev) for _ in range(frames)]  # resident frames (+ pinned twins)
     for q, (Wq, Hq) in enumerate(sizes):
@@ -380,13 +427,85 @@ def run_batch(args, rank, world, local):
         st.upload(non_blocking=False)
     staging = PackedObs(sizes, device=dev, pinned=False)  # the buffers the batch is bound to
     batch = hs.Batch(model, staging.obs, cams, Ps, seq_seeds)
-    score = hs.score_params(variant=hs.RENDER_VARIANTS.get(args.render, 0), ctas_per_particle=args.ctas)
+    score = hs.score_params(variant=hs.RENDER_VARIANTS.get(render, 0), ctas_per_particle=ctas)
     trk = BatchTracker(model, batch, GENS, device=dev, score=score)
     gt0 = torch.from_numpy(np.stack([t[0] for t in trajs])).to(dev)
     tune = None
-    if args.render == "tune":
+    if render == "tune":
         staging.dev.copy_(store[0].dev)
         tune = trk.autotune(gt0)
+    return sizes, Ps, store, staging, batch, trk, gt0, tune
+
+
+def batch_render_roofline(hs, model, sizes, Ps, store, staging, batch, trk, gt0, kinds, pk, dev):
+    """Roofline of render_score_multi on the batched workload: frame 0 of every
+    sequence tracked step by step, the 40 render launches' inputs kept, then
+    replayed back to back from one captured graph (CUDA events)."""
+    import torch
+    Pt = batch.P_total
+    hist_p = torch.zeros(GENS, Pt, model.n_prims, 16, device=dev)
+    hist_k = torch.zeros(GENS, Pt, device=dev)
+    staging.dev.copy_(store[0].dev)
+    cur, nxt = trk.x_buf
+    trk.swarm.x = cur
+    trk.seed_poses.copy_(gt0)
+    hs.hs_obs_prepare_multi(batch)
+    hs.pso_init_multi(model, batch, trk.swarm, trk.seed_poses, trk.scale, 0)
+    hs.pose_fk_multi(model, batch, cur, trk.prims, trk.kc)
+    for gen in range(1, GENS + 1):
+        hist_p[gen - 1].copy_(trk.prims)
+        hist_k[gen - 1].copy_(trk.kc)
+        hs.render_score_multi(model, batch, trk.prims, trk.kc, trk.score, trk.ws, trk.swarm.E)
+        trk.swarm.x = cur
+        hs.pso_step_fk_multi(model, batch, trk.swarm, nxt, trk.pso, 0, gen, trk.prims, trk.kc)
+        cur, nxt = nxt, cur
+    trk.swarm.x = cur
+    E_tmp = torch.zeros(Pt, device=dev)
+
+    def renders():
+        for q in range(GENS):
+            hs.render_score_multi(model, batch, hist_p[q], hist_k[q], trk.score, trk.ws, E_tmp)
+        return GENS
+
+    render_us = replay_render_us(dev, renders)
+    Wp = np.repeat([w for w, _ in sizes], Ps)
+    Hp = np.repeat([h for _, h in sizes], Ps)
+    tests = np.mean([algorithmic_tests(hist_p[q, :, :, 14:16].cpu().numpy(), kinds, Wp, Hp)
+                     for q in range(0, GENS, 4)], axis=0)
+    variant = hs.render_variant(trk.score, Pt)
+    rec = roofline_record(tests, render_us, pk, f"render_score_multi ({variant})",
+                          "CUDA events around a graph of one frame's 40 render_score_multi launches", 3 * GENS,
+                          traffic=profile_traffic("batch", variant))
+    rec.update({"workload": f"{batch.S} sequences, {Pt} particles, ROIs 48-256 px (one frame, 40 generations)",
+                "ctas_per_particle": trk.score.ctas_per_particle})
+    del hist_p, hist_k
+    return rec
+
+
+def run_batch(args, rank, world, local):
+    import torch
+    from paper_2005_07068_b300 import build as B
+    from paper_2005_07068_b300 import handscore as hs
+    from paper_2005_07068_b300 import inputs as I
+    from paper_2005_07068_b300 import replicas as R
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    peaks = measured_peaks()
+    seed = R.replica_seed(I.CONFIG_SEED_BASE + 4, rank)
+    g = I.hand_geometry()
+    lo, hi = (a.astype(np.float32) for a in I.search_limits())
+    model = hs.Model.from_geometry(g, lo, hi)
+    frames = 2 if args.profile else BATCH_FRAMES
+    sizes, Ps, store, staging, batch, trk, gt0, tune = batch_setup(hs, I, model, seed, frames, dev, args.render,
+                                                                    args.ctas)
     graphs = [trk.graph(f, gt0 if f == 0 else None) for f in range(frames)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -429,65 +548,9 @@ def run_batch(args, rank, world, local):
         return 0
 
     # roofline: the render launches of one frame replayed back to back
-    kinds = g.prims_i[:, 1]
     Pt = batch.P_total
-    hist_p = torch.zeros(GENS, Pt, model.n_prims, 16, device=dev)
-    hist_k = torch.zeros(GENS, Pt, device=dev)
-    staging.dev.copy_(store[0].dev)
-    cur, nxt = trk.x_buf
-    trk.swarm.x = cur
-    trk.seed_poses.copy_(gt0)
-    hs.hs_obs_prepare_multi(batch)
-    hs.pso_init_multi(model, batch, trk.swarm, trk.seed_poses, trk.scale, 0)
-    hs.pose_fk_multi(model, batch, cur, trk.prims, trk.kc)
-    for gen in range(1, GENS + 1):
-        hist_p[gen - 1].copy_(trk.prims)
-        hist_k[gen - 1].copy_(trk.kc)
-        hs.render_score_multi(model, batch, trk.prims, trk.kc, trk.score, trk.ws, trk.swarm.E)
-        trk.swarm.x = cur
-        hs.pso_step_fk_multi(model, batch, trk.swarm, nxt, trk.pso, 0, gen, trk.prims, trk.kc)
-        cur, nxt = nxt, cur
-    trk.swarm.x = cur
-    E_tmp = torch.zeros(Pt, device=dev)
-
-    def renders():
-        for q in range(GENS):
-            hs.render_score_multi(model, batch, hist_p[q], hist_k[q], trk.score, trk.ws, E_tmp)
-
-    side = torch.cuda.Stream(dev)
-    side.wait_stream(stream)
-    with torch.cuda.stream(side):
-        renders()
-    stream.wait_stream(side)
-    rg = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(rg, stream=side):
-        renders()
-    rg.replay()
-    torch.cuda.synchronize(dev)
-    a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 3
-    a_ev.record(stream)
-    for _ in range(reps):
-        rg.replay()
-    b_ev.record(stream)
-    torch.cuda.synchronize(dev)
-    render_us = a_ev.elapsed_time(b_ev) * 1e3 / (reps * GENS)
-    Wp = np.repeat([w for w, _ in sizes], Ps)
-    Hp = np.repeat([h for _, h in sizes], Ps)
-    flops = [algorithmic_flops(hist_p[q, :, :, 14:16].cpu().numpy(), kinds, Wp, Hp) for q in range(0, GENS, 4)]
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz") or clocks["sm_max_mhz"] or 2032.0)
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    flop_launch = sum(flops) / len(flops)
-    achieved = flop_launch / (render_us * 1e-6) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": profile_traffic("batch", hs.render_variant(trk.score, Pt)),
-                "kernel": f"render_score_multi ({hs.render_variant(trk.score, Pt)})",
-                "peak_basis": f"FP32: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {sm_max:.0f} MHz "
-                              f"(sm_max_mhz of measured)",
-                "launch_us": render_us, "launches_timed": reps * GENS, "flop_per_launch": flop_launch,
-                "flop_basis": "pixel-exact primitive boxes x per-test FP32 tally (ellipsoid 45, cone 78)",
-                "timing": "CUDA events around a graph of one frame's 40 render_score_multi launches"}
+    roofline = batch_render_roofline(hs, model, sizes, Ps, store, staging, batch, trk, gt0, g.prims_i[:, 1],
+                                     fp32_xu_peaks(dev, peaks), dev)
 
     # end to end: one pinned copy of every sequence's frame, the graph, the results read back
     e2e = None
@@ -578,6 +641,83 @@ def replay_render_us(dev, renders, reps: int = 3) -> float:
     return a.elapsed_time(b) * 1e3 / (reps * n)
 
 
+def record_frame_renders(hs, model, obs, cam, trk, seed_pose, seed, frame, gens, hist_p, hist_k, n=0):
+    """One frame tracked step by step (init, FK, then gens x (render, fused
+    step)), keeping the records and kc every render consumed in hist_p[n:],
+    hist_k[n:]; returns the next free slot."""
+    cur, nxt = trk.x_buf
+    trk.swarm.x = cur
+    trk.seed_pose.copy_(seed_pose)
+    hs.hs_obs_prepare(obs)
+    hs.pso_init(model, trk.swarm, trk.seed_pose, trk.scale, seed, frame)
+    hs.pose_fk(model, cur, cam, trk.prims, trk.kc)
+    for gen in range(1, gens + 1):
+        hist_p[n].copy_(trk.prims)
+        hist_k[n].copy_(trk.kc)
+        n += 1
+        hs.render_score_batch(model, obs, cam, trk.prims, trk.kc, trk.score, trk.ws, trk.swarm.E)
+        trk.swarm.x = cur
+        hs.pso_step_fk(model, trk.swarm, nxt, trk.pso, seed, frame, gen, cam, trk.prims, trk.kc)
+        cur, nxt = nxt, cur
+    trk.swarm.x = cur
+    return n
+
+
+FULL_ROOF_GENS = 10
+
+
+def fullframe_render_roofline(hs, I, model, kinds, pk, dev, P, seed, Wf=640, Hf=480, obs=None, start=None,
+                              render="tune", ctas=0, gens=FULL_ROOF_GENS, score=None):
+    """Roofline of render_score_batch on full Kinect frames (Wf x Hf, P
+    particles): frame 0 of the seeded sequence tracked from a perturbed start
+    for `gens` generations, the render launches' inputs kept and replayed back
+    to back from one captured graph (CUDA events)."""
+    import torch
+    from paper_2005_07068_b300.tracker import Tracker
+    camt = I.kinect_camera(Wf, Hf)
+    cam = hs.camera(camt.fx, camt.fy, camt.cx, camt.cy)
+    lo, hi = (a.astype(np.float32) for a in I.search_limits())
+    if obs is None:
+        traj, obs_l, _ = make_frames(seed, 1, hs, I, model, cam, dev, W=Wf, H=Hf)
+        obs = obs_l[0]
+        rng = np.random.default_rng(seed)
+        start_np = np.clip(traj[0] + rng.uniform(-1, 1, 26) * I.perturbation_scale(), lo, hi).astype(np.float32)
+        start = torch.from_numpy(start_np).to(dev)
+    tune = None
+    if score is None:
+        score = hs.score_params(variant=hs.RENDER_VARIANTS.get(render, 0), ctas_per_particle=ctas)
+    elif render == "tune":
+        render = "given"
+    if render == "tune":
+        tuner = Tracker(model, cam, P, 1, seed=seed, device=dev, score=score)
+        tune = tuner.autotune(obs, start)
+        score = tuner.score
+        del tuner
+    trk = Tracker(model, cam, P, gens, seed=seed, device=dev, score=score)
+    hist_p = torch.zeros(gens, P, model.n_prims, 16, device=dev)
+    hist_k = torch.zeros(gens, P, device=dev)
+    record_frame_renders(hs, model, obs, cam, trk, start, seed, 0, gens, hist_p, hist_k)
+    E_tmp = torch.zeros(P, device=dev)
+
+    def renders():
+        for q in range(gens):
+            hs.render_score_batch(model, obs, cam, hist_p[q], hist_k[q], trk.score, trk.ws, E_tmp)
+        return gens
+
+    us = replay_render_us(dev, renders)
+    tests = np.mean([algorithmic_tests(hist_p[q, :, :, 14:16].cpu().numpy(), kinds, Wf, Hf)
+                     for q in range(0, gens, max(1, gens // 5))], axis=0)
+    variant = hs.render_variant(trk.score, P)
+    rec = roofline_record(tests, us, pk, f"render_score_batch ({variant})",
+                          f"CUDA events around a graph of {gens} render_score_batch launches (generations 1-{gens} "
+                          f"of a tracked frame)", 3 * gens, traffic=profile_traffic(f"fullframe{Wf}x{Hf}P{P}", variant))
+    rec.update({"workload": f"{Wf}x{Hf} uint16 Kinect-style frame, {P} particles", "particles": P,
+                "ctas_per_particle": trk.score.ctas_per_particle, "autotune_us": tune})
+    del trk, hist_p, hist_k
+    torch.cuda.empty_cache()
+    return rec
+
+
 def run_fullframe(args, rank, world, local):
     import torch
     from paper_2005_07068_b300 import build as B
@@ -614,9 +754,7 @@ def run_fullframe(args, rank, world, local):
     start_np = np.clip(traj[0] + rng.uniform(-1, 1, 26) * I.perturbation_scale(), lo, hi).astype(np.float32)
     start = torch.from_numpy(start_np).to(dev)
     kinds = g.prims_i[:, 1]
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz") or 2032.0)
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    pk = fp32_xu_peaks(dev, peaks)
     settings, per_p = [], []
     gen_budgets = [int(v) for v in args.gens.split(",") if v]
     with ClockSampler(local) as clk:
@@ -642,42 +780,11 @@ def run_fullframe(args, rank, world, local):
                                  "launches_per_frame": trk.launches_per_frame()})
                     settings.append(summ)
                     del trk
-            # render roofline at this P: the launches of frame 0 (50 generations) replayed back to back
-            trk = Tracker(model, cam, P, FULL_GENS, seed=seed, device=dev, score=score)
-            hist_p = torch.zeros(FULL_GENS, P, model.n_prims, 16, device=dev)
-            hist_k = torch.zeros(FULL_GENS, P, device=dev)
-            cur, nxt = trk.x_buf
-            trk.swarm.x = cur
-            trk.seed_pose.copy_(start)
-            hs.hs_obs_prepare(obs[0])
-            hs.pso_init(model, trk.swarm, trk.seed_pose, trk.scale, seed, 0)
-            hs.pose_fk(model, cur, cam, trk.prims, trk.kc)
-            for gen in range(1, FULL_GENS + 1):
-                hist_p[gen - 1].copy_(trk.prims)
-                hist_k[gen - 1].copy_(trk.kc)
-                hs.render_score_batch(model, obs[0], cam, trk.prims, trk.kc, trk.score, trk.ws, trk.swarm.E)
-                trk.swarm.x = cur
-                hs.pso_step_fk(model, trk.swarm, nxt, trk.pso, seed, 0, gen, cam, trk.prims, trk.kc)
-                cur, nxt = nxt, cur
-            trk.swarm.x = cur
-            E_tmp = torch.zeros(P, device=dev)
-
-            def renders():
-                for q in range(FULL_GENS):
-                    hs.render_score_batch(model, obs[0], cam, hist_p[q], hist_k[q], trk.score, trk.ws, E_tmp)
-                return FULL_GENS
-
-            us = replay_render_us(dev, renders)
-            flops = np.mean([algorithmic_flops(hist_p[q, :, :, 14:16].cpu().numpy(), kinds, FULL_W, FULL_H)
-                             for q in range(0, FULL_GENS, 10)])
-            achieved = flops / (us * 1e-6) / 1e12
-            per_p.append({"particles": P, "render": {"kernel": hs.render_variant(trk.score, P),
-                                                     "ctas_per_particle": trk.score.ctas_per_particle,
-                                                     "autotune_us": tune},
-                          "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                                       "frac": achieved / peak_tflops, "launch_us": us, "flop_per_launch": flops}})
-            del trk, hist_p, hist_k
-            torch.cuda.empty_cache()
+            # render roofline at this P: generations of frame 0 replayed back to back
+            rec = fullframe_render_roofline(hs, I, model, kinds, pk, dev, P, seed, FULL_W, FULL_H, obs=obs[0],
+                                            start=start, score=score)
+            rec["autotune_us"] = tune
+            per_p.append(rec)
     clocks = clk.summary(peaks.get("sm_max_mhz", 2032.0))
     best = SW.fastest_within(settings, 0.9)
     if rank == 0:
@@ -819,86 +926,56 @@ def main():
     # kept, then those launches run back to back in one captured graph, timed
     # with CUDA events on the launching stream (kernel time without host gaps).
     kinds = g.prims_i[:, 1]
+    pk = fp32_xu_peaks(dev, peaks)
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2032.0))
     rf = min(3, frames) if not args.no_roofline else 0
-    hist_p = torch.zeros(max(rf, 1) * GENS, PARTICLES, model.n_prims, 16, device=dev)
-    hist_k = torch.zeros(max(rf, 1) * GENS, PARTICLES, device=dev)
-    n = 0
-    for f in range(rf):
-        cur, nxt = trk.x_buf
-        trk.swarm.x = cur
-        trk.seed_pose.copy_(gt0 if f == 0 else trk.swarm.gbest)
-        hs.hs_obs_prepare(obs[f])
-        hs.pso_init(model, trk.swarm, trk.seed_pose, trk.scale, seed, f)
-        hs.pose_fk(model, cur, cam, trk.prims, trk.kc)
-        for gen in range(1, GENS + 1):
-            hist_p[n].copy_(trk.prims)
-            hist_k[n].copy_(trk.kc)
-            n += 1
-            hs.render_score_batch(model, obs[f], cam, trk.prims, trk.kc, trk.score, trk.ws, trk.swarm.E)
-            trk.swarm.x = cur
-            hs.pso_step_fk(model, trk.swarm, nxt, trk.pso, seed, f, gen, cam, trk.prims, trk.kc)
-            cur, nxt = nxt, cur
-        trk.swarm.x = cur
-    torch.cuda.synchronize(dev)
-    render_us, flops = None, []
-    if n:
+    render_roofline, roofline, sub = None, None, {}
+    if rf:
+        hist_p = torch.zeros(rf * GENS, PARTICLES, model.n_prims, 16, device=dev)
+        hist_k = torch.zeros(rf * GENS, PARTICLES, device=dev)
+        n = 0
+        for f in range(rf):
+            n = record_frame_renders(hs, model, obs[f], cam, trk, gt0 if f == 0 else trk.swarm.gbest.clone(), seed,
+                                     f, GENS, hist_p, hist_k, n)
         E_tmp = torch.zeros(PARTICLES, device=dev)
 
         def renders():
             for q in range(n):
                 hs.render_score_batch(model, obs[q // GENS], cam, hist_p[q], hist_k[q], trk.score, trk.ws, E_tmp)
+            return n
 
-        side = torch.cuda.Stream(dev)
-        side.wait_stream(stream)
-        with torch.cuda.stream(side):
-            renders()
-        stream.wait_stream(side)
-        rg = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(rg, stream=side):
-            renders()
-        rg.replay()
-        torch.cuda.synchronize(dev)
-        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 5
-        a_ev.record(stream)
-        for _ in range(reps):
-            rg.replay()
-        b_ev.record(stream)
-        torch.cuda.synchronize(dev)
-        render_us = a_ev.elapsed_time(b_ev) * 1e3 / (reps * n)
+        render_us = replay_render_us(dev, renders, reps=5)
         hb = hist_p[:n, :, :, 14:16].cpu().numpy()
-        flops = [algorithmic_flops(hb[q], kinds) for q in range(n)]
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    clocks = clk.summary(peaks.get("sm_max_mhz", 2032.0))
-    sm_max = float(peaks.get("sm_max_mhz") or clocks["sm_max_mhz"] or 2032.0)
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    flop_launch = sum(flops) / len(flops) if flops else 0.0
-    achieved = flop_launch / (render_us * 1e-6) / 1e12 if render_us else 0.0
-    traffic = profile_traffic("kinect", hs.render_variant(trk.score, PARTICLES))
-    render_roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                       "frac": achieved / peak_tflops, "traffic": traffic,
-                       "kernel": f"render_score_batch ({hs.render_variant(trk.score, PARTICLES)})",
-                       "peak_basis": f"FP32: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {sm_max:.0f} MHz "
-                                     f"(sm_max_mhz of measured)",
-                       "launch_us": render_us, "launches_timed": n * 5, "flop_per_launch": flop_launch,
-                       "flop_basis": "pixel-exact primitive boxes x per-test FP32 tally (ellipsoid 45, cone 78)",
-                       "timing": "CUDA events around a graph of the timed frames' render_score_batch launches"}
-    roofline = render_roofline
-    if use_frame:
-        # the frame kernel does all of a frame's renders (and its FK and steps,
-        # whose FP32 work is not counted): the same algorithmic FLOPs per
-        # generation, GENS generations per launch, over the launch's duration
-        frame_us = frame_path["ms_per_step"] * 1e3
-        flop_frame = flop_launch * GENS
-        ach_f = flop_frame / (frame_us * 1e-6) / 1e12 if frame_us else 0.0
-        roofline = {"bound": "alu", "achieved": ach_f, "peak": peak_tflops, "unit": "TFLOP/s",
-                    "frac": ach_f / peak_tflops, "traffic": profile_traffic("kinect", "frame"),
-                    "kernel": "track_frame_kernel (one cooperative launch per frame)",
-                    "peak_basis": render_roofline["peak_basis"], "launch_us": frame_us, "launches_timed": K,
-                    "flop_per_launch": flop_frame,
-                    "flop_basis": f"{GENS} generations x the render's algorithmic FLOPs (pixel-exact primitive "
-                                  f"boxes x per-test FP32 tally); FK, cost finish and swarm steps not counted",
-                    "timing": "CUDA events around each timed frame's launch on the launching stream"}
+        tests = np.mean([algorithmic_tests(hb[q], kinds) for q in range(n)], axis=0)
+        variant = hs.render_variant(trk.score, PARTICLES)
+        render_roofline = roofline_record(tests, render_us, pk, f"render_score_batch ({variant})",
+                                          "CUDA events around a graph of the timed frames' render_score_batch "
+                                          "launches", n * 5, traffic=profile_traffic("kinect", variant))
+        roofline = render_roofline
+        if use_frame:
+            # the frame kernel does all of a frame's renders (and its FK and steps,
+            # whose work is not counted): the same algorithmic work per
+            # generation, GENS generations per launch, over the launch's duration
+            roofline = roofline_record(tests, frame_path["ms_per_step"] * 1e3, pk,
+                                       "track_frame_kernel (one cooperative launch per frame)",
+                                       "CUDA events around each timed frame's launch on the launching stream", K,
+                                       traffic=profile_traffic("kinect", "frame"), gens=GENS,
+                                       note=f"{GENS} generations x the render's algorithmic work; FK, cost finish "
+                                            f"and swarm steps not counted")
+        del hist_p, hist_k
+        # the render roofline on the other two workloads the kernels are built
+        # for: many sequences with uneven ROIs (render_score_multi) and full
+        # 640x480 frames with 4096 particles (render_score_batch)
+        if not args.no_sub_rooflines:
+            bseed = R.replica_seed(I.CONFIG_SEED_BASE + 4, rank)
+            bset = batch_setup(hs, I, model, bseed, 1, dev, args.render, args.ctas)
+            sub["batch_64seq"] = batch_render_roofline(hs, model, *bset[:7], kinds, pk, dev)
+            sub["batch_64seq"]["autotune_us"] = bset[7]
+            del bset
+            torch.cuda.empty_cache()
+            fseed = R.replica_seed(I.CONFIG_SEED_BASE + 5, rank)
+            sub["fullframe_640x480_P4096"] = fullframe_render_roofline(hs, I, model, kinds, pk, dev, 4096, fseed,
+                                                                       render=args.render, ctas=args.ctas)
 
     # ---- end to end: pinned host frame -> device -> graph -> result on the host ----
     e2e = None
@@ -930,7 +1007,28 @@ def main():
         e2e_value, _, _ = R.aggregate(sum(a.elapsed_time(b) for a, b in ee) / 1e3, K * PARTICLES * GENS, dev)
         e2e = {"value": e2e_value, "unit": "evals/s",
                "h2d_bytes_per_step": int(pin[0][0].numel() * pin[0][0].element_size() + pin[0][1].numel()),
-               "d2h_bytes_per_step": int(out.numel() * out.element_size())}
+               "d2h_bytes_per_step": int(out.numel() * out.element_size()),
+               "timing": "CUDA events on the stream around each frame's copies in, tracking and result copy out "
+                         "(L2 flushed between frames)"}
+        # host wall clock: pinned host frame in -> pose on the host, one frame
+        # at a time as a live camera delivers them (the host waits for each
+        # frame's result before it submits the next; the binding's ctypes
+        # calls and the launch are inside the interval; no L2 flush)
+        n_wall = max(HOST_WALL_FRAMES, K)
+        wall_ms = []
+        with ClockSampler(local) as wclk:
+            for i in range(n_wall):
+                f = (args.warmup + K + i) % frames
+                t0 = time.perf_counter()
+                etrk.track(pin[f][0], pin[f][1], staging, f, out, gt0 if f == 0 else None)
+                torch.cuda.current_stream(dev).synchronize()
+                wall_ms.append((time.perf_counter() - t0) * 1e3)
+        hw_value, _, _ = R.aggregate(sum(wall_ms) / 1e3, n_wall * PARTICLES * GENS, dev)
+        e2e["host_wall"] = {"value": hw_value, "unit": "evals/s", "frames": n_wall,
+                            "ms_per_frame_p50": percentile(wall_ms, 50), "ms_per_frame_p99": percentile(wall_ms, 99),
+                            "timing": "host perf_counter from submitting a pinned frame to its pose on the host, "
+                                      "a stream synchronisation per frame",
+                            "clocks": wclk.summary(peaks.get("sm_max_mhz", 2032.0))}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -963,7 +1061,8 @@ def main():
                            "parallelism": f"replicas x{world}", "wall_s": wall,
                            "render": {"kernel": hs.render_variant(trk.score, PARTICLES),
                                       "ctas_per_particle": trk.score.ctas_per_particle, "autotune_us": tune}},
-                "roofline": roofline, "render_roofline": render_roofline, "cpu_baseline": cpu, "clocks": clocks,
+                "roofline": roofline, "render_roofline": render_roofline, "render_rooflines": sub,
+                "cpu_baseline": cpu, "clocks": clocks,
                 "e2e": e2e, "gpu_launches": launches, "frame_path": frame_path, "graph_path": graph_path}
         print(json.dumps(line), flush=True)
     if dist:

@@ -146,32 +146,49 @@ __device__ __forceinline__ float lin2(float c0, float cu, float cv, float du, fl
     return fmaf(dv, cv, fmaf(du, cu, c0));
 }
 
-__device__ __forceinline__ void make_raster(const float4* rec, float inv_fx, float off_x, float inv_fy, float off_y,
-                                            float4* out)
+// What every part of a raster record is formed from: the projected centre,
+// h_c, k_u, k_v (scaled local coordinates), t0 and kappa.
+struct RasterBase {
+    float uc, vc, t0, kap, caps;
+    float hc[3], ku[3], kv[3];
+};
+
+__device__ __forceinline__ RasterBase raster_base(const float4* rec, float inv_fx, float off_x, float inv_fy,
+                                                  float off_y)
 {
     const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
     const float m0[3] = {r0.x, r0.y, r0.z}, m1[3] = {r0.w, r1.x, r1.y}, m2[3] = {r1.z, r1.w, r2.x};
-    const float t0 = r2.w, kap = r3.y;
+    RasterBase b;
+    b.t0 = r2.w;
+    b.kap = r3.y;
+    b.caps = r3.x;
     // projected centre direction and pixel (correctly rounded reciprocals: a
     // few ulps in u_c, v_c shift the silhouette by ~1e-4 px at most)
-    const float it0 = __frcp_rn(t0);
+    const float it0 = __frcp_rn(b.t0);
     const float ac = r2.y * it0, bc = r2.z * it0;
-    const float uc = (ac - off_x) * __frcp_rn(inv_fx), vc = (bc - off_y) * __frcp_rn(inv_fy);
-    float hc[3], ku[3], kv[3];
+    b.uc = (ac - off_x) * __frcp_rn(inv_fx);
+    b.vc = (bc - off_y) * __frcp_rn(inv_fy);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        hc[i] = fmaf(ac, m0[i], fmaf(bc, m1[i], m2[i]));
-        ku[i] = m0[i] * inv_fx;
-        kv[i] = m1[i] * inv_fy;
+        b.hc[i] = fmaf(ac, m0[i], fmaf(bc, m1[i], m2[i]));
+        b.ku[i] = m0[i] * inv_fx;
+        b.kv[i] = m1[i] * inv_fy;
     }
+    return b;
+}
+
+// part 0 of the record: r[0], r[1] (discriminant) and r[9], r[10] (the caps' linear forms)
+__device__ __forceinline__ void raster_part_disc(const RasterBase& b, float4* out)
+{
+    const float *hc = b.hc, *ku = b.ku, *kv = b.kv;
+    const float t0 = b.t0, kap = b.kap;
     // (u, v) coefficients of the linear forms, and of products of two of them
     struct L { float u, v; };
     auto cr = [&](int i, int j) { return L{hc[i] * ku[j] - hc[j] * ku[i], hc[i] * kv[j] - hc[j] * kv[i]}; };
     const L kX{ku[0], kv[0]}, kY{ku[1], kv[1]}, kZ{ku[2], kv[2]};
     float c0, cu, cv, cuu, cuv, cvv;
     const float t2 = t0 * t0;
-    const bool ell = kap > 1.5f;
-    if (ell) {
+    if (kap > 1.5f) {  // ellipsoid
         const L n0 = cr(1, 2), n1 = cr(2, 0), n2 = cr(0, 1);
         c0 = hc[0] * hc[0] + hc[1] * hc[1] + hc[2] * hc[2];
         cu = 2.f * (hc[0] * kX.u + hc[1] * kY.u + hc[2] * kZ.u);
@@ -179,7 +196,7 @@ __device__ __forceinline__ void make_raster(const float4* rec, float inv_fx, flo
         cuu = (kX.u * kX.u + kY.u * kY.u + kZ.u * kZ.u) - t2 * (n0.u * n0.u + n1.u * n1.u + n2.u * n2.u);
         cuv = 2.f * ((kX.u * kX.v + kY.u * kY.v + kZ.u * kZ.v) - t2 * (n0.u * n0.v + n1.u * n1.v + n2.u * n2.v));
         cvv = (kX.v * kX.v + kY.v * kY.v + kZ.v * kZ.v) - t2 * (n0.v * n0.v + n1.v * n1.v + n2.v * n2.v);
-    } else {
+    } else {  // cone
         const L nXY = cr(0, 1), nYZ = cr(1, 2), nXZ = cr(0, 2);
         const float tk = t0 * kap, tk2 = t2 * kap * kap;
         c0 = hc[0] * hc[0] + hc[2] * hc[2];
@@ -193,23 +210,63 @@ __device__ __forceinline__ void make_raster(const float4* rec, float inv_fx, flo
         cvv = kX.v * kX.v + kZ.v * kZ.v + 2.f * tk * (kX.v * nXY.v - kZ.v * nYZ.v) +
               tk2 * (nXY.v * nXY.v + nYZ.v * nYZ.v) - t2 * nXZ.v * nXZ.v;
     }
-    // the bilinear form Q of the quadric
-    const float wy = ell ? 1.f : -kap * kap, wxz = 1.f;
-    auto Q = [&](const float* x, const float* y) { return wxz * (x[0] * y[0] + x[2] * y[2]) + wy * x[1] * y[1]; };
-    const float Qhh = Q(hc, hc), Qhu = Q(hc, ku), Qhv = Q(hc, kv), Quu = Q(ku, ku), Quv = Q(ku, kv),
-                Qvv = Q(kv, kv);
-    const float lk = ell ? 0.f : kap;  // the cone's linear terms: B - kappa h_Y, C - 2 kappa g_Y
-    out[0] = make_float4(uc, vc, c0, cu);
+    out[0] = make_float4(b.uc, b.vc, c0, cu);
     out[1] = make_float4(cv, cuu, cuv, cvv);
+    out[9] = make_float4(hc[0], ku[0], kv[0], hc[2]);
+    out[10] = make_float4(ku[2], kv[2], 0.f, 0.f);
+}
+
+// the bilinear form Q of the quadric: x.y (ellipsoid), x_X y_X + x_Z y_Z - kappa^2 x_Y y_Y (cone)
+__device__ __forceinline__ float raster_q(const RasterBase& b, const float* x, const float* y)
+{
+    const float wy = b.kap > 1.5f ? 1.f : -b.kap * b.kap;
+    return (x[0] * y[0] + x[2] * y[2]) + wy * x[1] * y[1];
+}
+
+// part 1: r[2] .. r[5] (A and B of the roots, t0, kappa, caps)
+__device__ __forceinline__ void raster_part_ab(const RasterBase& b, float4* out)
+{
+    const float *hc = b.hc, *ku = b.ku, *kv = b.kv;
+    const float t0 = b.t0;
+    const float Qhh = raster_q(b, hc, hc), Qhu = raster_q(b, hc, ku), Qhv = raster_q(b, hc, kv),
+                Quu = raster_q(b, ku, ku), Quv = raster_q(b, ku, kv), Qvv = raster_q(b, kv, kv);
+    const float lk = b.kap > 1.5f ? 0.f : b.kap;  // the cone's linear term of B: - kappa h_Y
     out[2] = make_float4(Qhh, 2.f * Qhu, 2.f * Qhv, Quu);
-    out[3] = make_float4(2.f * Quv, Qvv, t0, kap);
+    out[3] = make_float4(2.f * Quv, Qvv, t0, b.kap);
     out[4] = make_float4(-lk * hc[1], t0 * Qhu - lk * ku[1], t0 * Qhv - lk * kv[1], t0 * Quu);
-    out[5] = make_float4(2.f * t0 * Quv, t0 * Qvv, r3.x, 0.f);
+    out[5] = make_float4(2.f * t0 * Quv, t0 * Qvv, b.caps, 0.f);
+}
+
+// part 2: r[6] .. r[8] (C of the cone's roots and the axial coordinate)
+__device__ __forceinline__ void raster_part_c(const RasterBase& b, float4* out)
+{
+    const float *hc = b.hc, *ku = b.ku, *kv = b.kv;
+    const float t0 = b.t0, t2 = t0 * t0;
+    const float Quu = raster_q(b, ku, ku), Quv = raster_q(b, ku, kv), Qvv = raster_q(b, kv, kv);
+    const float lk = b.kap > 1.5f ? 0.f : b.kap;  // the cone's linear term of C: - 2 kappa g_Y
     out[6] = make_float4(-1.f, -2.f * lk * t0 * ku[1], -2.f * lk * t0 * kv[1], t2 * Quu);
     out[7] = make_float4(2.f * t2 * Quv, t2 * Qvv, t0 * ku[1], t0 * kv[1]);
     out[8] = make_float4(hc[1], ku[1], kv[1], 0.f);
-    out[9] = make_float4(hc[0], ku[0], kv[0], hc[2]);
-    out[10] = make_float4(ku[2], kv[2], 0.f, 0.f);
+}
+
+// part `part` (0, 1, 2) of the raster record of the 64-byte FK record rec
+__device__ __forceinline__ void make_raster_part(const float4* rec, float inv_fx, float off_x, float inv_fy,
+                                                 float off_y, int part, float4* out)
+{
+    const RasterBase b = raster_base(rec, inv_fx, off_x, inv_fy, off_y);
+    if (part == 0) raster_part_disc(b, out);
+    else if (part == 1) raster_part_ab(b, out);
+    else raster_part_c(b, out);
+}
+
+// the whole raster record (the three parts in one thread)
+__device__ __forceinline__ void make_raster(const float4* rec, float inv_fx, float off_x, float inv_fy, float off_y,
+                                            float4* out)
+{
+    const RasterBase b = raster_base(rec, inv_fx, off_x, inv_fy, off_y);
+    raster_part_disc(b, out);
+    raster_part_ab(b, out);
+    raster_part_c(b, out);
 }
 
 __device__ __forceinline__ bool raster_is_ellipsoid(const float4* r) { return r[3].w > 1.5f; }
@@ -273,26 +330,31 @@ __device__ __forceinline__ float cone_caps(const float4* r, uint32_t caps, float
     return best;
 }
 
+// The nearest hit of a primitive's quadric surface (no caps) at pixel offsets
+// (du, dv), given the discriminant there, as the depth offset s from t0, or
+// +inf; ELL: the primitive is an ellipsoid (reads r[0..5]), else a cone
+// (r[0..8]).
+template <bool ELL>
+__device__ __forceinline__ float raster_surface_hit(const float4* r, float du, float dv, float disc)
+{
+    if (!(disc >= 0.f)) return INFINITY;
+    const float4 r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
+    const float A = poly2(r2.x, r2.y, r2.z, r2.w, r3.x, r3.y, du, dv);
+    const float B = poly2(r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, du, dv);
+    if (ELL) return ellipsoid_root(r3.z, A, B, disc);
+    const float4 r6 = r[6], r7 = r[7], r8 = r[8];
+    const float C = poly2(r6.x, r6.y, r6.z, r6.w, r7.x, r7.y, du, dv);
+    const float gy = lin2(0.f, r7.z, r7.w, du, dv), hy = lin2(r8.x, r8.y, r8.z, du, dv);
+    return cone_root(r3.z, A, B, C, gy, hy, disc);
+}
+
 // Nearest hit of the pixel at offsets (du, dv) with one primitive, given its
 // discriminant there, as the depth offset s from the primitive's centre depth
 // t0 (depth = t0 + s), or +inf.
 __device__ __forceinline__ float raster_hit(const float4* r, float du, float dv, float disc)
 {
-    const float4 r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
-    const float t0 = r3.z;
-    float best = INFINITY;
-    if (disc >= 0.f) {
-        const float A = poly2(r2.x, r2.y, r2.z, r2.w, r3.x, r3.y, du, dv);
-        const float B = poly2(r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, du, dv);
-        if (raster_is_ellipsoid(r)) {
-            best = ellipsoid_root(t0, A, B, disc);
-        } else {
-            const float4 r6 = r[6], r7 = r[7], r8 = r[8];
-            const float C = poly2(r6.x, r6.y, r6.z, r6.w, r7.x, r7.y, du, dv);
-            const float gy = lin2(0.f, r7.z, r7.w, du, dv), hy = lin2(r8.x, r8.y, r8.z, du, dv);
-            best = cone_root(t0, A, B, C, gy, hy, disc);
-        }
-    }
+    float best = raster_is_ellipsoid(r) ? raster_surface_hit<true>(r, du, dv, disc)
+                                        : raster_surface_hit<false>(r, du, dv, disc);
     const uint32_t caps = raster_caps(r);
     if (caps) best = cone_caps(r, caps, du, dv, best);
     return best;

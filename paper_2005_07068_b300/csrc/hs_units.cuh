@@ -28,15 +28,20 @@ constexpr int kUW = 16, kUH = 4, kSub = 2;
 constexpr int kSlot = 384;    // one stage: depth [4][16] (<= float32, 256 B) at 0, skin [4][16] at 256
 constexpr int kStages = 4;    // observation stages per warp: loads run kStages - 1 units ahead
 
-// raster record + pixel box of primitives j = tid, tid + nthreads, ... from the
-// 64-byte FK records rec (global or shared memory)
+// raster records + pixel boxes of the primitives from the 64-byte FK records
+// rec (global or shared memory), by nthreads threads: each record's three
+// parts (make_raster_part) are formed by three threads, so the prologue's
+// critical path is a third of a whole record
 __device__ __forceinline__ void stage_prims(const float4* rec, int n_prims, const ParticleView& pv, float4* rast,
                                             int2* pbox, int tid, int nthreads)
 {
-    for (int j = tid; j < n_prims; j += nthreads) {
-        make_raster(rec + 4 * j, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y, rast + kRastVec * j);
-        const float4 r3 = rec[4 * j + 3];
-        pbox[j] = make_int2(__float_as_int(r3.z), __float_as_int(r3.w));
+    for (int t = tid; t < 3 * n_prims; t += nthreads) {
+        const int j = t % n_prims, part = t / n_prims;
+        make_raster_part(rec + 4 * j, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y, part, rast + kRastVec * j);
+        if (part == 0) {
+            const float4 r3 = rec[4 * j + 3];
+            pbox[j] = make_int2(__float_as_int(r3.z), __float_as_int(r3.w));
+        }
     }
 }
 

@@ -24,7 +24,7 @@
 //  * one set of atomics per CTA, and the last CTA of the particle forms E.
 #include <atomic>
 
-#include "hs_render.cuh"
+#include "hs_units.cuh"
 
 namespace hs {
 
@@ -85,11 +85,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
     pdl_wait();  // the primitive records and kc come from the previous kernel
     const int n_prims = a.n_prims;
     const float4* src = a.prims + (size_t)p * n_prims * 4;
-    for (int j = tid; j < n_prims; j += NW * 32) {  // raster form of each primitive, once per CTA
-        make_raster(src + 4 * j, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y, s_rast + kRastVec * j);
-        const float4 r3 = src[4 * j + 3];
-        s_pbox[j] = make_int2(__float_as_int(r3.z), __float_as_int(r3.w));
-    }
+    stage_prims(src, n_prims, pv, s_rast, s_pbox, tid, NW * 32);  // raster form of each primitive, once per CTA
     if (warp == 0) {  // the particle's screen box, clipped to the ROI
         int u0 = INT_MAX, v0 = INT_MAX, u1 = INT_MIN, v1 = INT_MIN;
         for (int i = lane; i < n_prims; i += 32) {
@@ -214,21 +210,40 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
             const float4* R = s_rast + kRastVec * j;
             const float4 q0 = R[0];
             const float t0 = R[3].z;
-            for (; c < c1; c += NW) {
-                const int idx = ((c - c0) << 5) + lane;
-                if (idx < rc.w) {
-                    const int y = (int)(((unsigned long long)(uint32_t)idx * mg) >> 31);
-                    const int px = rc.x + idx - y * rc.z, py = rc.y + y;
-                    const float du = (float)px - q0.x, dv = (float)py - q0.y;
-                    const float disc = raster_disc(R, du, dv);
-                    const float sh = raster_maybe(R, disc) ? raster_hit(R, du, dv, disc) : INFINITY;
-                    const float zz = t0 + sh;
-                    if (zz < INFINITY) {
-                        const float dz = sh - (zz - t0);  // z - t0 is exact (Sterbenz): dz is the residual
-                        atomicMin(&s_z[(py - ty0) * TW + (px - tx0)],
-                                  ((unsigned long long)__float_as_uint(zz) << 32) | __float_as_uint(dz));
+            // the primitive's chunks; hit(du, dv, disc) gives the depth offset
+            auto chunks = [&](const float4* Rd, auto hit) {
+                for (; c < c1; c += NW) {
+                    const int idx = ((c - c0) << 5) + lane;
+                    if (idx < rc.w) {
+                        const int y = (int)(((unsigned long long)(uint32_t)idx * mg) >> 31);
+                        const int px = rc.x + idx - y * rc.z, py = rc.y + y;
+                        const float du = (float)px - q0.x, dv = (float)py - q0.y;
+                        const float sh = hit(du, dv, raster_disc(Rd, du, dv));
+                        const float zz = t0 + sh;
+                        if (zz < INFINITY) {
+                            const float dz = sh - (zz - t0);  // z - t0 is exact (Sterbenz): dz is the residual
+                            atomicMin(&s_z[(py - ty0) * TW + (px - tx0)],
+                                      ((unsigned long long)__float_as_uint(zz) << 32) | __float_as_uint(dz));
+                        }
                     }
                 }
+            };
+            // the record in registers for the primitive's chunks (the z-buffer
+            // atomics would otherwise make every pixel reload it), split by kind
+            if (raster_caps(R) != 0u) {  // visible cone caps: the general path, from shared memory
+                chunks(R, [&](float du, float dv, float disc) {
+                    return raster_maybe(R, disc) ? raster_hit(R, du, dv, disc) : INFINITY;
+                });
+            } else if (raster_is_ellipsoid(R)) {
+                float4 Rl[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) Rl[k] = R[k];
+                chunks(Rl, [&](float du, float dv, float disc) { return raster_surface_hit<true>(Rl, du, dv, disc); });
+            } else {
+                float4 Rl[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) Rl[k] = R[k];
+                chunks(Rl, [&](float du, float dv, float disc) { return raster_surface_hit<false>(Rl, du, dv, disc); });
             }
         }
         extra_tx = 0u;

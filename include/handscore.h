@@ -136,7 +136,13 @@ typedef struct {
 #define HS_RENDER_TILES_64x64 5
 #define HS_RENDER_STRIPS_8x16 6
 #define HS_RENDER_STRIPS_8x32 7
-#define HS_RENDER_VARIANTS    8
+/* the strip kernels as one persistent launch: one CTA per resident slot of
+ * the GPU, each taking the next particle (of any swarm of a batch, largest
+ * ROI first) from a counter in the workspace until all are scored;
+ * ctas_per_particle is ignored */
+#define HS_RENDER_PERSISTENT_8x16 8
+#define HS_RENDER_PERSISTENT_8x32 9
+#define HS_RENDER_VARIANTS    10
 
 /* constants of Eq. 4-5 (paper: d_m = 1 cm, d_M = 4 cm, lambda = 20, lambda_k = 10),
  * in mm; 0 <= d_M < 127 (the depth sums are kept in 32-bit fixed point per pixel);
@@ -186,11 +192,16 @@ typedef struct {
 
 /* Section III.B: c1 = 2.8, c2 = 1.3; w = 2 / |2 - psi - sqrt(psi^2 - 4 psi)|,
  * psi = c1 + c2 > 4 (computed by pso_step); mutation every 3 generations of
- * the worst half (n_mutate = P / 2); mutate_every <= 0 disables it */
+ * the worst half (n_mutate = P / 2); mutate_every <= 0 disables it.
+ * e_stop: Section III.B's stopping rule (the search ends once the best E
+ * falls below a threshold; the paper uses 1.0), per swarm and on the device,
+ * for the batch calls only (pso_step_fk_multi): 0 disables it, and the
+ * single-swarm calls require 0. */
 typedef struct {
     float c1, c2;
     int32_t mutate_every;
     int32_t n_mutate;
+    float e_stop;
 } HsPsoParams;
 
 /* ---- kc variants (Section III.A, after Eq. 5) -----------------------------
@@ -249,7 +260,8 @@ int hs_model_destroy(HsModel* model);
 int hs_model_set_kc(HsModel* model, const HsKcParams* kc);
 
 /* Bytes of workspace render_score_batch needs for P particles (32 bytes per
- * particle: a work-queue ticket, an exit count and fixed-point sums).  The
+ * particle: an exit count and fixed-point sums; then a 64-byte control block
+ * holding the persistent launch's particle counter), rounded up to 256.  The
  * workspace must be zeroed once (hs_workspace_reset) before first use; every
  * call leaves it zeroed again.  Calls sharing one workspace must not overlap
  * on the GPU.
@@ -319,7 +331,7 @@ int pso_step(const HsModel* model, const HsSwarm* swarm, int P, const HsPsoParam
  * bytes per GPU), so the call itself allocates nothing (no cudaMalloc, no
  * allocating library routine).
  *  - P is limited to what the array holds: calls with hs_workspace_size(P) >
- *    HS_NOALLOC_SCRATCH_BYTES (P > 8192 with the current 32-byte per-particle
+ *    HS_NOALLOC_SCRATCH_BYTES (P > 8190 with the current 32-byte per-particle
  *    layout) return HS_ERR_SIZE and launch nothing.
  *  - The first call on a device looks up the array's device address (with
  *    cudaGetSymbolAddress) and caches it.  Under lazy module loading (the
@@ -446,7 +458,13 @@ int render_score_multi(const HsModel* model, const HsBatch* batch, const HsPrim*
 int pso_init_multi(const HsModel* model, const HsBatch* batch, const HsSwarm* swarm, const float* seed_poses,
                    const float* scale, uint32_t frame, hs_stream_t stream);
 /* pso_step_fk for every swarm in one launch (n_mutate from each swarm's
- * descriptor; c1, c2 and mutate_every from params). */
+ * descriptor; c1, c2 and mutate_every from params).  Device-side stop flags
+ * (params->e_stop > 0): a swarm whose global best E, after this generation's
+ * personal- and global-best update, is below e_stop stops -- this
+ * generation's positions are kept (x_next = x, velocity unchanged, no FK),
+ * and in the later generations of the frame render_score_multi does not
+ * score its particles and pso_step_fk_multi only carries its positions over.
+ * pso_init_multi starts every swarm running again. */
 int pso_step_fk_multi(const HsModel* model, const HsBatch* batch, const HsSwarm* swarm, float* x_next,
                       const HsPsoParams* params, uint32_t frame, uint32_t gen, HsPrim* prims, float* kc,
                       hs_stream_t stream);

@@ -134,7 +134,7 @@ static cudaError_t launch_render(const HsScoreParams& prm, const CUtensorMap& tm
     a.lambda = prm.lambda;
     a.lambda_k = prm.lambda_k;
     if (variant == HS_RENDER_UNITS) return launch_render_score(tm_depth, tm_skin, a, s);
-    if (variant == HS_RENDER_STRIPS_8x16 || variant == HS_RENDER_STRIPS_8x32)
+    if (variant >= HS_RENDER_STRIPS_8x16 && variant <= HS_RENDER_PERSISTENT_8x32)
         return launch_render_strips(variant, tm_depth, tm_skin, a, s);
     return launch_render_tiles(variant, tm_depth, tm_skin, a, s);
 }
@@ -368,7 +368,8 @@ int hs_workspace_size(int P, size_t* bytes)
 {
     if (!bytes) return HS_ERR_ARG;
     if (P < 0 || P > HS_MAX_PARTICLES) return HS_ERR_SIZE;
-    *bytes = ((size_t)P * sizeof(HsParticleWork) + 255) / 256 * 256;
+    // per particle a 32-byte slot, then the persistent launch's control block
+    *bytes = ((size_t)P * sizeof(HsParticleWork) + sizeof(RenderCtl) + 255) / 256 * 256;
     return HS_OK;
 }
 
@@ -460,6 +461,7 @@ int render_score_batch(const HsModel* model, const HsObs* obs, const HsCamera* c
     a.depth_f32 = f32;
     a.stats = obs->stats;
     a.work = static_cast<HsParticleWork*>(workspace);
+    a.ctl = reinterpret_cast<RenderCtl*>(a.work + P);
     a.E = E;
     a.parts = parts;
     a.dbg_depth = dbg_depth;
@@ -501,6 +503,7 @@ int pso_step(const HsModel* model, const HsSwarm* sw, int P, const HsPsoParams* 
     if (P < 1 || P > 4096) return HS_ERR_SIZE;
     const double psi = (double)prm->c1 + (double)prm->c2;
     if (!std::isfinite(psi) || prm->c1 < 0.f || prm->c2 < 0.f || psi <= 4.0) return HS_ERR_ARG;
+    if (prm->e_stop != 0.f) return HS_ERR_ARG;  // the stopping rule is the batch step's
     if (prm->mutate_every > 0 && (prm->n_mutate < 0 || prm->n_mutate > P)) return HS_ERR_ARG;
     PsoStepArgs a = {};
     a.x = sw->x;
@@ -537,6 +540,7 @@ int pso_step_fk(const HsModel* model, const HsSwarm* sw, float* x_next, int P, c
     if (!aligned16(prims)) return HS_ERR_ALIGN;
     const double psi = (double)prm->c1 + (double)prm->c2;
     if (!std::isfinite(psi) || prm->c1 < 0.f || prm->c2 < 0.f || psi <= 4.0) return HS_ERR_ARG;
+    if (prm->e_stop != 0.f) return HS_ERR_ARG;  // the stopping rule is the batch step's
     if (prm->mutate_every > 0 && (prm->n_mutate < 0 || prm->n_mutate > P)) return HS_ERR_ARG;
     PsoFkArgs a = {};
     a.x = sw->x;
@@ -596,6 +600,7 @@ int track_frame(const HsModel* model, const HsObs* obs, const HsCamera* cam, con
     if (ctas < 0) return HS_ERR_ARG;
     const double psi = (double)prm->c1 + (double)prm->c2;
     if (!std::isfinite(psi) || prm->c1 < 0.f || prm->c2 < 0.f || psi <= 4.0) return HS_ERR_ARG;
+    if (prm->e_stop != 0.f) return HS_ERR_ARG;  // the stopping rule is the batch step's
     if (prm->mutate_every > 0 && (prm->n_mutate < 0 || prm->n_mutate > P)) return HS_ERR_ARG;
     if (!workspace || (prims && !aligned16(prims)) || !aligned16(workspace)) return workspace ? HS_ERR_ALIGN : HS_ERR_ARG;
     size_t need = 0;
@@ -977,6 +982,7 @@ int render_score_multi(const HsModel* model, const HsBatch* b, const HsPrim* pri
     a.P = b->P_total;
     a.n_prims = model->dev.n_prims;
     a.work = static_cast<HsParticleWork*>(workspace);
+    a.ctl = reinterpret_cast<RenderCtl*>(a.work + b->P_total);
     a.E = E;
     a.parts = parts;
     a.batch = b->dev;
@@ -1019,6 +1025,7 @@ int pso_step_fk_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw,
     if (!aligned16(prims)) return HS_ERR_ALIGN;
     const double psi = (double)prm->c1 + (double)prm->c2;
     if (!std::isfinite(psi) || prm->c1 < 0.f || prm->c2 < 0.f || psi <= 4.0) return HS_ERR_ARG;
+    if (!(prm->e_stop >= 0.f) || !std::isfinite(prm->e_stop)) return HS_ERR_ARG;
     PsoFkArgs a = {};
     a.x = sw->x;
     a.x_next = x_next;
@@ -1035,6 +1042,7 @@ int pso_step_fk_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw,
     a.mutate = prm->mutate_every > 0 && gen % (uint32_t)prm->mutate_every == 0;
     a.frame = frame;
     a.gen = gen;
+    a.e_stop = prm->e_stop;
     a.prims = reinterpret_cast<float4*>(prims);
     a.kc = kc;
     a.batch = b->dev;
@@ -1074,6 +1082,8 @@ int autotune(HsScoreParams* params, int P, int reps, float* times_us, cudaStream
         for (int c = 0; c < HS_TUNE_CTAS && rc == HS_OK; ++c) {
             // more CTAs per particle only while the launch stays within a few waves
             if (kTuneCtas[c] > 1 && (long long)kTuneCtas[c] * P > 4LL * kTargetCtas) break;
+            // the persistent launches deal whole particles: no CTAs-per-particle choice
+            if (c > 0 && (v == HS_RENDER_PERSISTENT_8x16 || v == HS_RENDER_PERSISTENT_8x32)) break;
             HsScoreParams cand = *params;
             cand.variant = v;
             cand.ctas_per_particle = kTuneCtas[c];

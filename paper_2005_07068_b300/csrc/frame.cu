@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
                                   make_float4(rec[4], rec[5], rec[6], rec[7]),
                                   make_float4(rec[8], rec[9], rec[10], rec[11]),
                                   make_float4(rec[12], rec[13], rec[14], rec[15])};
-            make_raster(r4, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y, sh.rast + kRastVec * j);
+            store_raster(make_raster(r4, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y), sh.rast + kRastVec * j);
             sh.pbox[j] = make_int2(__float_as_int(rec[14]), __float_as_int(rec[15]));
             // the union of the pixel boxes, per warp of record threads
             const int w = j >> 5;

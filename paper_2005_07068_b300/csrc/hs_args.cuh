@@ -22,6 +22,9 @@ struct SwarmView {  // 128-byte aligned (CUtensorMap)
     const uint8_t* skin;
     uint32_t* stats;
     uint32_t key0, key1;
+    uint32_t stop_gen;  // device state: 0 while the swarm runs, else the generation at which it stopped
+                        // (e_stop); cleared by the batch init, set by the batch step
+    uint32_t pad;
 };
 
 // header of a batch buffer: S views, then the swarm index of every particle
@@ -30,6 +33,18 @@ struct BatchDev {
     const SwarmView* views;  // [S]
     const int32_t* sid;      // [P_total]
 };
+
+// swarm s's stop word (SwarmView::stop_gen), read and written through
+// volatile accesses: kernels of the same stream write it, so it must not be
+// served from a read-only cache
+__device__ __forceinline__ uint32_t swarm_stop_gen(const BatchDev& b, int s)
+{
+    return *reinterpret_cast<const volatile uint32_t*>(&b.views[s].stop_gen);
+}
+__device__ __forceinline__ void set_swarm_stop_gen(const BatchDev& b, int s, uint32_t gen)
+{
+    *reinterpret_cast<volatile uint32_t*>(const_cast<uint32_t*>(&b.views[s].stop_gen)) = gen;
+}
 
 
 struct FkArgs {
@@ -54,6 +69,15 @@ struct HsParticleWork {
                                   // only read it, and the last contributor clears the slot as usual
 };
 
+// control block of the persistent render launch, at the end of the render
+// workspace (64 bytes, zero between calls)
+struct RenderCtl {
+    uint32_t next;    // the next particle (index into the call's order) to be taken
+    uint32_t exited;  // CTAs that have left
+    uint32_t pad[14];
+};
+static_assert(sizeof(RenderCtl) == 64, "64-byte control block");
+
 struct RenderArgs {
     const float4* prims;  // [P][n_prims][4]
     const float* kc;      // [P]
@@ -71,6 +95,7 @@ struct RenderArgs {
     uint32_t* status;
     BatchDev batch;  // batch.views == nullptr: one swarm described by the fields above
     const int32_t* order;  // CTA row y scores particle order[y] (nullptr: particle y)
+    RenderCtl* ctl;        // the persistent launch's counters (after work[P] in the workspace)
 };
 
 struct PsoInitArgs {
@@ -101,6 +126,7 @@ struct PsoFkArgs {
     float c1, c2, w;
     int mutate, n_mutate;
     uint32_t key0, key1, frame, gen;
+    float e_stop;          // batch only: a swarm stops once its global best E is below this (0: never)
     float4 cam;            // fx, fy, cx, cy
     float4* prims;         // [P][n_prims][4]
     float* kc;             // [P]

@@ -92,46 +92,40 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // at depth t0 + s where the quadratic A s^2 + 2 B s + C = 0 holds (t0 = C_z, the
 // primitive's centre depth).  Written relative to the ray through the projected
 // centre, d = d_c + (alpha, beta, 0) with t0 d_c = C, the local ray is g + s h
-// with k = M (alpha, beta, 0) = du k_u + dv k_v, g = t0 k, h = h_c + k,
-// h_c = M d_c, (du, dv) = (u - u_c, v - v_c) the pixel's offsets from the
-// projected centre.
+// with k = M (alpha, beta, 0), g = t0 k, h = h_c + k, h_c = M d_c.
 //
-// Since g and h are linear in (du, dv), A, B and C are quadratic polynomials
-// in them, and so is the discriminant B^2 - A C (its quartic and cubic terms
-// cancel exactly, because shifting s does not change it).  The discriminant's
-// coefficients are written with the identity
-// (x.Dy)^2 - (x.Dx)(y.Dy) = -sum_{i<j} d_i d_j (x_i y_j - x_j y_i)^2 for
-// diagonal D, as sums of squares of small terms, with no cancellation of the
-// ~t0^2 |h_c|^2 parts:
+// Its discriminant B^2 - A C is a quadratic polynomial in the pixel offsets
+// (du, dv) = (u - u_c, v - v_c) from the projected centre (the quartic and
+// cubic terms cancel exactly, because shifting s does not change it).  Written
+// with the identity (x.Dy)^2 - (x.Dx)(y.Dy) = -sum_{i<j} d_i d_j (x_i y_j - x_j y_i)^2
+// for diagonal D, its coefficients are sums of squares of small terms, with no
+// cancellation of the ~t0^2 |h_c|^2 parts:
 //   ellipsoid: disc = |h_c|^2 + 2 h_c.k + |k|^2 - t0^2 |h_c x k|^2
 //   cone:      disc = h_X^2 + h_Z^2 + 2 (h_X k_X + h_Z k_Z) + 2 kappa t0 (h_X n_XY - h_Z n_YZ)
 //                     + k_X^2 + k_Z^2 + 2 t0 kappa (k_X n_XY - k_Z n_YZ)
 //                     + t0^2 (kappa^2 (n_XY^2 + n_YZ^2) - n_XZ^2)
 //              (h = h_c, n_ij = h_i k_j - h_j k_i)
-// With the bilinear form Q(x, y) = x.y (ellipsoid) or x_X y_X + x_Z y_Z -
-// kappa^2 x_Y y_Y (cone):
-//   A = Q(h, h)
-//   B = Q(g, h)              (cone: - kappa h_Y)
-//   C = Q(g, g) - 1          (cone: - 2 kappa g_Y; only cones need C)
-// So a pixel is tested for coverage with one polynomial, and the roots take
-// two or three more (and, for cones, the axial coordinates g_Y, h_Y, which
-// are linear).  Every quadratic is evaluated by poly2, the same association
-// everywhere, so a kernel that forms the du terms once per pixel column gives
-// the same bits as one that evaluates the polynomial whole.
+// So a pixel is tested for coverage with one polynomial; the roots, which need
+// A, B, C, are formed only where the discriminant is not negative.  The
+// polynomial is evaluated by poly2, one association everywhere (the dv terms
+// outermost), so a kernel that forms a pixel column's du terms once (Poly2Col)
+// gets the same bits as one that evaluates it whole.
 //
-// Raster record: kRastVec float4, formed once per CTA from the 64-byte FK record:
-//   r[0] = (u_c, v_c, D_0, D_u)      r[1] = (D_v, D_uu, D_uv, D_vv)      discriminant
-//   r[2] = (A_0, A_u, A_v, A_uu)     r[3] = (A_uv, A_vv, t0, kappa or the ellipsoid marker)
-//   r[4] = (B_0, B_u, B_v, B_uu)     r[5] = (B_uv, B_vv, caps, 0)
-//   cones:          r[6] = (C_0, C_u, C_v, C_uu)   r[7] = (C_uv, C_vv, gY_u, gY_v)   r[8] = (hY_0, hY_u, hY_v, 0)
-//   visible caps:   r[9] = (h_cX, k_uX, k_vX, h_cZ)   r[10] = (k_uZ, k_vZ, 0, 0)
-constexpr int kRastVec = 11;
+// Raster record (5 float4, built once per CTA from the 64-byte FK record):
+//   q0 = (u_c, v_c, c0, c_u)   q1 = (c_v, c_uu, c_uv, c_vv)   disc polynomial
+//   q2 = (k_u, t0)             q3 = (k_v, kappa or ellipsoid marker)
+//   q4 = (h_c, caps)           k = du k_u + dv k_v
+constexpr int kRastVec = 5;
+
+struct RasterPrim {
+    float4 q0, q1, q2, q3, q4;
+};
 
 __device__ __forceinline__ float poly2(float c0, float cu, float cv, float cuu, float cuv, float cvv, float du, float dv)
 {
     return fmaf(dv, fmaf(dv, cvv, fmaf(du, cuv, cv)), fmaf(du, fmaf(du, cuu, cu), c0));
 }
-// a quadratic with its du terms formed once for a pixel column: col(du) then at(dv)
+// a quadratic with its du terms formed once for a pixel column: poly2_col(du) then at(dv)
 struct Poly2Col {
     float u0, u1, vv;
     __device__ __forceinline__ float at(float dv) const { return fmaf(dv, fmaf(dv, vv, u1), u0); }
@@ -140,48 +134,25 @@ __device__ __forceinline__ Poly2Col poly2_col(float c0, float cu, float cv, floa
 {
     return Poly2Col{fmaf(du, fmaf(du, cuu, cu), c0), fmaf(du, cuv, cv), cvv};
 }
-// a linear form c0 + du cu + dv cv, with the same association
-__device__ __forceinline__ float lin2(float c0, float cu, float cv, float du, float dv)
-{
-    return fmaf(dv, cv, fmaf(du, cu, c0));
-}
 
-// What every part of a raster record is formed from: the projected centre,
-// h_c, k_u, k_v (scaled local coordinates), t0 and kappa.
-struct RasterBase {
-    float uc, vc, t0, kap, caps;
-    float hc[3], ku[3], kv[3];
-};
-
-__device__ __forceinline__ RasterBase raster_base(const float4* rec, float inv_fx, float off_x, float inv_fy,
+__device__ __forceinline__ RasterPrim make_raster(const float4* rec, float inv_fx, float off_x, float inv_fy,
                                                   float off_y)
 {
     const float4 r0 = rec[0], r1 = rec[1], r2 = rec[2], r3 = rec[3];
     const float m0[3] = {r0.x, r0.y, r0.z}, m1[3] = {r0.w, r1.x, r1.y}, m2[3] = {r1.z, r1.w, r2.x};
-    RasterBase b;
-    b.t0 = r2.w;
-    b.kap = r3.y;
-    b.caps = r3.x;
+    const float t0 = r2.w, kap = r3.y;
     // projected centre direction and pixel (correctly rounded reciprocals: a
     // few ulps in u_c, v_c shift the silhouette by ~1e-4 px at most)
-    const float it0 = __frcp_rn(b.t0);
+    const float it0 = __frcp_rn(t0);
     const float ac = r2.y * it0, bc = r2.z * it0;
-    b.uc = (ac - off_x) * __frcp_rn(inv_fx);
-    b.vc = (bc - off_y) * __frcp_rn(inv_fy);
+    const float uc = (ac - off_x) * __frcp_rn(inv_fx), vc = (bc - off_y) * __frcp_rn(inv_fy);
+    float hc[3], ku[3], kv[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        b.hc[i] = fmaf(ac, m0[i], fmaf(bc, m1[i], m2[i]));
-        b.ku[i] = m0[i] * inv_fx;
-        b.kv[i] = m1[i] * inv_fy;
+        hc[i] = fmaf(ac, m0[i], fmaf(bc, m1[i], m2[i]));
+        ku[i] = m0[i] * inv_fx;
+        kv[i] = m1[i] * inv_fy;
     }
-    return b;
-}
-
-// part 0 of the record: r[0], r[1] (discriminant) and r[9], r[10] (the caps' linear forms)
-__device__ __forceinline__ void raster_part_disc(const RasterBase& b, float4* out)
-{
-    const float *hc = b.hc, *ku = b.ku, *kv = b.kv;
-    const float t0 = b.t0, kap = b.kap;
     // (u, v) coefficients of the linear forms, and of products of two of them
     struct L { float u, v; };
     auto cr = [&](int i, int j) { return L{hc[i] * ku[j] - hc[j] * ku[i], hc[i] * kv[j] - hc[j] * kv[i]}; };
@@ -210,160 +181,94 @@ __device__ __forceinline__ void raster_part_disc(const RasterBase& b, float4* ou
         cvv = kX.v * kX.v + kZ.v * kZ.v + 2.f * tk * (kX.v * nXY.v - kZ.v * nYZ.v) +
               tk2 * (nXY.v * nXY.v + nYZ.v * nYZ.v) - t2 * nXZ.v * nXZ.v;
     }
-    out[0] = make_float4(b.uc, b.vc, c0, cu);
-    out[1] = make_float4(cv, cuu, cuv, cvv);
-    out[9] = make_float4(hc[0], ku[0], kv[0], hc[2]);
-    out[10] = make_float4(ku[2], kv[2], 0.f, 0.f);
+    RasterPrim R;
+    R.q0 = make_float4(uc, vc, c0, cu);
+    R.q1 = make_float4(cv, cuu, cuv, cvv);
+    R.q2 = make_float4(ku[0], ku[1], ku[2], t0);
+    R.q3 = make_float4(kv[0], kv[1], kv[2], kap);
+    R.q4 = make_float4(hc[0], hc[1], hc[2], r3.x);
+    return R;
 }
 
-// the bilinear form Q of the quadric: x.y (ellipsoid), x_X y_X + x_Z y_Z - kappa^2 x_Y y_Y (cone)
-__device__ __forceinline__ float raster_q(const RasterBase& b, const float* x, const float* y)
+// the record into shared memory (5 float4 at d)
+__device__ __forceinline__ void store_raster(const RasterPrim& R, float4* d)
 {
-    const float wy = b.kap > 1.5f ? 1.f : -b.kap * b.kap;
-    return (x[0] * y[0] + x[2] * y[2]) + wy * x[1] * y[1];
+    d[0] = R.q0;
+    d[1] = R.q1;
+    d[2] = R.q2;
+    d[3] = R.q3;
+    d[4] = R.q4;
 }
-
-// part 1: r[2] .. r[5] (A and B of the roots, t0, kappa, caps)
-__device__ __forceinline__ void raster_part_ab(const RasterBase& b, float4* out)
-{
-    const float *hc = b.hc, *ku = b.ku, *kv = b.kv;
-    const float t0 = b.t0;
-    const float Qhh = raster_q(b, hc, hc), Qhu = raster_q(b, hc, ku), Qhv = raster_q(b, hc, kv),
-                Quu = raster_q(b, ku, ku), Quv = raster_q(b, ku, kv), Qvv = raster_q(b, kv, kv);
-    const float lk = b.kap > 1.5f ? 0.f : b.kap;  // the cone's linear term of B: - kappa h_Y
-    out[2] = make_float4(Qhh, 2.f * Qhu, 2.f * Qhv, Quu);
-    out[3] = make_float4(2.f * Quv, Qvv, t0, b.kap);
-    out[4] = make_float4(-lk * hc[1], t0 * Qhu - lk * ku[1], t0 * Qhv - lk * kv[1], t0 * Quu);
-    out[5] = make_float4(2.f * t0 * Quv, t0 * Qvv, b.caps, 0.f);
-}
-
-// part 2: r[6] .. r[8] (C of the cone's roots and the axial coordinate)
-__device__ __forceinline__ void raster_part_c(const RasterBase& b, float4* out)
-{
-    const float *hc = b.hc, *ku = b.ku, *kv = b.kv;
-    const float t0 = b.t0, t2 = t0 * t0;
-    const float Quu = raster_q(b, ku, ku), Quv = raster_q(b, ku, kv), Qvv = raster_q(b, kv, kv);
-    const float lk = b.kap > 1.5f ? 0.f : b.kap;  // the cone's linear term of C: - 2 kappa g_Y
-    out[6] = make_float4(-1.f, -2.f * lk * t0 * ku[1], -2.f * lk * t0 * kv[1], t2 * Quu);
-    out[7] = make_float4(2.f * t2 * Quv, t2 * Qvv, t0 * ku[1], t0 * kv[1]);
-    out[8] = make_float4(hc[1], ku[1], kv[1], 0.f);
-}
-
-// part `part` (0, 1, 2) of the raster record of the 64-byte FK record rec
-__device__ __forceinline__ void make_raster_part(const float4* rec, float inv_fx, float off_x, float inv_fy,
-                                                 float off_y, int part, float4* out)
-{
-    const RasterBase b = raster_base(rec, inv_fx, off_x, inv_fy, off_y);
-    if (part == 0) raster_part_disc(b, out);
-    else if (part == 1) raster_part_ab(b, out);
-    else raster_part_c(b, out);
-}
-
-// the whole raster record (the three parts in one thread)
-__device__ __forceinline__ void make_raster(const float4* rec, float inv_fx, float off_x, float inv_fy, float off_y,
-                                            float4* out)
-{
-    const RasterBase b = raster_base(rec, inv_fx, off_x, inv_fy, off_y);
-    raster_part_disc(b, out);
-    raster_part_ab(b, out);
-    raster_part_c(b, out);
-}
-
-__device__ __forceinline__ bool raster_is_ellipsoid(const float4* r) { return r[3].w > 1.5f; }
-__device__ __forceinline__ uint32_t raster_caps(const float4* r) { return __float_as_uint(r[5].z); }
 
 // the discriminant at pixel offsets (du, dv): >= 0 where the quadric's surface
 // can be hit (for a cone with visible caps the caps are tested regardless)
-__device__ __forceinline__ float raster_disc(const float4* r, float du, float dv)
+__device__ __forceinline__ float raster_disc(const float4& q0, const float4& q1, float du, float dv)
 {
-    const float4 r0 = r[0], r1 = r[1];
-    return poly2(r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, du, dv);
+    return poly2(q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, du, dv);
 }
-
-// the nearer root of an ellipsoid in front of the camera (the far one when
-// the camera is inside it), as the depth offset s from t0, or +inf
-__device__ __forceinline__ float ellipsoid_root(float t0, float A, float B, float disc)
+// the discriminant's du terms for a pixel column
+__device__ __forceinline__ Poly2Col raster_disc_col(const float4& q0, const float4& q1, float du)
 {
-    const float sq = sqrt_approx(disc);
-    const float ia = rcp_approx(A);
-    // (__fmul_rn: never fused with a later add, so every kernel rounds the root alike)
-    const float sn = __fmul_rn(-B - sq, ia);
-    const float sf = __fmul_rn(-B + sq, ia);  // the camera is inside the ellipsoid: the far root, if in front
-    return t0 + sn > 0.f ? sn : (t0 + sf > 0.f ? sf : INFINITY);
-}
-
-// the nearer root of a cone's side surface within |Y| <= 1 and in front of
-// the camera, or +inf (gy, hy: the axial coordinate of the ray point at t0
-// and its rate)
-__device__ __forceinline__ float cone_root(float t0, float A, float B, float C, float gy, float hy, float disc)
-{
-    const float sq = sqrt_approx(disc);
-    const float qq = -(B + copysignf(sq, B));
-    const float s1 = __fmul_rn(qq, rcp_approx(A));
-    const float s2 = __fmul_rn(C, rcp_approx(qq));
-    const float y1 = fmaf(s1, hy, gy), y2 = fmaf(s2, hy, gy);
-    float best = INFINITY;
-    if (fabsf(y1) <= 1.f && t0 + s1 > 0.f) best = s1;
-    if (fabsf(y2) <= 1.f && t0 + s2 > 0.f) best = fminf(best, s2);
-    return best;
-}
-
-// the visible planar caps of a cone at Y = -1 (radius 1 - kappa) and Y = +1
-// (radius 1 + kappa): the nearer of best and their hits
-__device__ __forceinline__ float cone_caps(const float4* r, uint32_t caps, float du, float dv, float best)
-{
-    const float4 r3 = r[3], r7 = r[7], r8 = r[8], r9 = r[9], r10 = r[10];
-    const float t0 = r3.z, kap = r3.w;
-    const float gy = lin2(0.f, r7.z, r7.w, du, dv), hy = lin2(r8.x, r8.y, r8.z, du, dv);
-    const float kx = lin2(0.f, r9.y, r9.z, du, dv), kz = lin2(0.f, r10.x, r10.y, du, dv);
-    const float hx = r9.x + kx, hz = r9.w + kz, gx = t0 * kx, gz = t0 * kz;
-    const float ihy = rcp_approx(hy);
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        if (!(caps & (1u << c))) continue;
-        const float yc = c ? 1.f : -1.f;
-        const float s = __fmul_rn(yc - gy, ihy);
-        const float X = fmaf(s, hx, gx), Z = fmaf(s, hz, gz);
-        const float w = 1.f + yc * kap;
-        if (fmaf(X, X, Z * Z) <= w * w && t0 + s > 0.f) best = fminf(best, s);
-    }
-    return best;
-}
-
-// The nearest hit of a primitive's quadric surface (no caps) at pixel offsets
-// (du, dv), given the discriminant there, as the depth offset s from t0, or
-// +inf; ELL: the primitive is an ellipsoid (reads r[0..5]), else a cone
-// (r[0..8]).
-template <bool ELL>
-__device__ __forceinline__ float raster_surface_hit(const float4* r, float du, float dv, float disc)
-{
-    if (!(disc >= 0.f)) return INFINITY;
-    const float4 r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
-    const float A = poly2(r2.x, r2.y, r2.z, r2.w, r3.x, r3.y, du, dv);
-    const float B = poly2(r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, du, dv);
-    if (ELL) return ellipsoid_root(r3.z, A, B, disc);
-    const float4 r6 = r[6], r7 = r[7], r8 = r[8];
-    const float C = poly2(r6.x, r6.y, r6.z, r6.w, r7.x, r7.y, du, dv);
-    const float gy = lin2(0.f, r7.z, r7.w, du, dv), hy = lin2(r8.x, r8.y, r8.z, du, dv);
-    return cone_root(r3.z, A, B, C, gy, hy, disc);
+    return poly2_col(q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, du);
 }
 
 // Nearest hit of the pixel at offsets (du, dv) with one primitive, given its
 // discriminant there, as the depth offset s from the primitive's centre depth
-// t0 (depth = t0 + s), or +inf.
-__device__ __forceinline__ float raster_hit(const float4* r, float du, float dv, float disc)
+// t0 (depth = t0 + s), or +inf.  (__fmul_rn: the roots' last products are
+// never fused with a later add, so every kernel rounds them alike.)
+__device__ __forceinline__ float raster_hit(const float4& q2, const float4& q3, const float4& q4, float du, float dv,
+                                            float disc)
 {
-    float best = raster_is_ellipsoid(r) ? raster_surface_hit<true>(r, du, dv, disc)
-                                        : raster_surface_hit<false>(r, du, dv, disc);
-    const uint32_t caps = raster_caps(r);
-    if (caps) best = cone_caps(r, caps, du, dv, best);
+    const float t0 = q2.w, kap = q3.w;
+    const float kx = fmaf(du, q2.x, dv * q3.x), ky = fmaf(du, q2.y, dv * q3.y), kz = fmaf(du, q2.z, dv * q3.z);
+    const float hx = q4.x + kx, hy = q4.y + ky, hz = q4.z + kz;
+    const float gx = t0 * kx, gy = t0 * ky, gz = t0 * kz;
+    float best = INFINITY;
+    if (kap > 1.5f) {
+        if (disc >= 0.f) {
+            const float A = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+            const float B = fmaf(gx, hx, fmaf(gy, hy, gz * hz));
+            const float sq = sqrt_approx(disc);
+            const float ia = rcp_approx(A);
+            const float sn = __fmul_rn(-B - sq, ia);
+            const float sf = __fmul_rn(-B + sq, ia);  // the camera is inside the ellipsoid: the far root, if in front
+            best = t0 + sn > 0.f ? sn : (t0 + sf > 0.f ? sf : INFINITY);
+        }
+    } else {
+        if (disc >= 0.f) {
+            const float w0 = fmaf(kap, gy, 1.f), w1 = kap * hy;
+            const float A = fmaf(hx, hx, fmaf(hz, hz, -w1 * w1));
+            const float B = fmaf(gx, hx, fmaf(gz, hz, -w0 * w1));
+            const float C = fmaf(gx, gx, fmaf(gz, gz, -w0 * w0));
+            const float sq = sqrt_approx(disc);
+            const float qq = -(B + copysignf(sq, B));
+            const float s1 = __fmul_rn(qq, rcp_approx(A));
+            const float s2 = __fmul_rn(C, rcp_approx(qq));
+            const float y1 = fmaf(s1, hy, gy), y2 = fmaf(s2, hy, gy);
+            if (fabsf(y1) <= 1.f && t0 + s1 > 0.f) best = s1;
+            if (fabsf(y2) <= 1.f && t0 + s2 > 0.f) best = fminf(best, s2);
+        }
+        const uint32_t caps = __float_as_uint(q4.w);
+        if (caps) {  // planar caps at Y = -1 (radius 1 - kappa) and Y = +1 (radius 1 + kappa)
+            const float ihy = rcp_approx(hy);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (!(caps & (1u << c))) continue;
+                const float yc = c ? 1.f : -1.f;
+                const float s = __fmul_rn(yc - gy, ihy);
+                const float X = fmaf(s, hx, gx), Z = fmaf(s, hz, gz);
+                const float w = 1.f + yc * kap;
+                if (fmaf(X, X, Z * Z) <= w * w && t0 + s > 0.f) best = fminf(best, s);
+            }
+        }
+    }
     return best;
 }
 
 // true when the primitive must be tested at a pixel whose discriminant is disc
-__device__ __forceinline__ bool raster_maybe(const float4* r, float disc)
+__device__ __forceinline__ bool raster_maybe(const float4& q4, float disc)
 {
-    return disc >= 0.f || raster_caps(r) != 0u;
+    return disc >= 0.f || __float_as_uint(q4.w) != 0u;
 }
 
 // per-pixel terms of Eq. 4 (reading R1) as differences to the no-hit baseline,
@@ -406,6 +311,14 @@ __device__ __forceinline__ ParticleView particle_view(const RenderArgs& a, int p
                          &s.tm_skin};
     }
     return v;
+}
+
+// true when particle p belongs to a swarm of a batch that has stopped (the
+// batch step's stop flag): its E is not scored again this frame.  Read after
+// the programmatic-launch wait (the previous step kernel writes the flag).
+__device__ __forceinline__ bool particle_stopped(const RenderArgs& a, int p)
+{
+    return a.batch.views && swarm_stop_gen(a.batch, a.batch.sid[p]) != 0u;
 }
 
 // E of a particle none of whose primitives reaches the ROI: every pixel keeps

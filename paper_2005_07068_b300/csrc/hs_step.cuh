@@ -87,6 +87,7 @@ struct StepOut {
     float xn, vn, pb;  // new position, velocity and personal best of dimension t
     bool imp;          // the personal best improved (pbest_E becomes E_i)
     int g;             // the swarm's global best (index within the swarm)
+    float gE;          // and its E
 };
 
 // a caller's early read of one particle's x and pbest (dimension t), taken
@@ -237,7 +238,7 @@ __device__ __forceinline__ StepOut swarm_update(const SwarmRefs& R, int q, int i
     const SwarmBest b = kWarpBest ? swarm_best_warp(P, i, R.mutate, s_e, s_pe)
                                   : swarm_best<NT>(P, i, R.mutate, s_e, s_pe, red_v, red_i, red_r);
     const float ei = s_e[i];
-    StepOut out{0.f, 0.f, 0.f, ei < own_pe, b.g};  // strict improvement of this particle's personal best
+    StepOut out{0.f, 0.f, 0.f, ei < own_pe, b.g, b.gE};  // strict improvement of this particle's personal best
     const bool mutated = R.mutate && b.rank >= P - n_mutate;
     if (t < kNdof) {
         const bool x_is_best = s_e[b.g] <= s_pe[b.g];
@@ -247,6 +248,7 @@ __device__ __forceinline__ StepOut swarm_update(const SwarmRefs& R, int q, int i
         if (store && out.imp) R.pbest[(size_t)q * kNdof + t] = xi;
         out = swarm_move(R.c1, R.c2, R.w, out.imp, mutated, t, xi, pbi, vi, gv, s_r, s_m, lo, hi);
         out.g = b.g;
+        out.gE = b.gE;
         if (store) {
             R.v[(size_t)q * kNdof + t] = out.vn;
             R.x_next[(size_t)q * kNdof + t] = out.xn;

@@ -28,20 +28,15 @@ constexpr int kUW = 16, kUH = 4, kSub = 2;
 constexpr int kSlot = 384;    // one stage: depth [4][16] (<= float32, 256 B) at 0, skin [4][16] at 256
 constexpr int kStages = 4;    // observation stages per warp: loads run kStages - 1 units ahead
 
-// raster records + pixel boxes of the primitives from the 64-byte FK records
-// rec (global or shared memory), by nthreads threads: each record's three
-// parts (make_raster_part) are formed by three threads, so the prologue's
-// critical path is a third of a whole record
+// raster record + pixel box of primitives j = tid, tid + nthreads, ... from the
+// 64-byte FK records rec (global or shared memory)
 __device__ __forceinline__ void stage_prims(const float4* rec, int n_prims, const ParticleView& pv, float4* rast,
                                             int2* pbox, int tid, int nthreads)
 {
-    for (int t = tid; t < 3 * n_prims; t += nthreads) {
-        const int j = t % n_prims, part = t / n_prims;
-        make_raster_part(rec + 4 * j, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y, part, rast + kRastVec * j);
-        if (part == 0) {
-            const float4 r3 = rec[4 * j + 3];
-            pbox[j] = make_int2(__float_as_int(r3.z), __float_as_int(r3.w));
-        }
+    for (int j = tid; j < n_prims; j += nthreads) {
+        store_raster(make_raster(rec + 4 * j, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y), rast + kRastVec * j);
+        const float4 r3 = rec[4 * j + 3];
+        pbox[j] = make_int2(__float_as_int(r3.z), __float_as_int(r3.w));
     }
 }
 
@@ -183,16 +178,17 @@ __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2
                     mask &= mask - 1;
                     const float4* R = rast + kRastVec * (b + 32 * w);
                     const bool in0 = (a0 >> b) & 1u, in1 = (a1 >> b) & 1u;  // warp-uniform
-                    const float4 q0 = R[0];
+                    const float4 q0 = R[0], q1 = R[1];
                     const float dv = fpy - q0.y, du0 = fpx0 - q0.x, du1 = fpx1 - q0.x;
-                    const float d0 = raster_disc(R, du0, dv), d1 = raster_disc(R, du1, dv);
-                    const bool caps = raster_caps(R) != 0u;
+                    const float d0 = raster_disc(q0, q1, du0, dv), d1 = raster_disc(q0, q1, du1, dv);
+                    const bool caps = __float_as_uint(R[4].w) != 0u;
                     const uint32_t v0 = __ballot_sync(0xffffffffu, in0 && (d0 >= 0.f || caps));
                     const uint32_t v1 = __ballot_sync(0xffffffffu, in1 && (d1 >= 0.f || caps));
                     if (v0 | v1) {
-                        const float t0 = R[3].z;
+                        const float4 q2 = R[2], q3 = R[3], q4 = R[4];
+                        const float t0 = q2.w;
                         if (v0) {
-                            const float sh0 = raster_hit(R, du0, dv, d0);
+                            const float sh0 = raster_hit(q2, q3, q4, du0, dv, d0);
                             const float zz0 = t0 + sh0;
                             if (zz0 < z[0]) {
                                 z[0] = zz0;
@@ -201,7 +197,7 @@ __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2
                             }
                         }
                         if (v1) {
-                            const float sh1 = raster_hit(R, du1, dv, d1);
+                            const float sh1 = raster_hit(q2, q3, q4, du1, dv, d1);
                             const float zz1 = t0 + sh1;
                             if (zz1 < z[1]) {
                                 z[1] = zz1;

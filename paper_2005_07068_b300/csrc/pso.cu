@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(256) pso_init_kernel(const __grid_constant__ L
         k1 = v.key1;
     }
     const float* seed_pose = a.seed_pose + (size_t)s * kNdof;
+    if (a.batch.views && li == 0 && j == 0) set_swarm_stop_gen(a.batch, s, 0u);  // the swarm runs this frame
     const U4 r = philox4x32_10(U4{(uint32_t)li, (kStreamInit << 16) | (uint32_t)j, 0u, a.frame}, k0, k1);
     const uint32_t u[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
@@ -210,6 +211,14 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
         // the first are drawn while the previous kernel finishes
         draw_step_randoms(i, a.gen, a.frame, k0, k1, s_r, s_m, t);
         if (q == (int)blockIdx.x) pdl_wait();  // E comes from the previous kernel
+        if (a.batch.views) {
+            const uint32_t stopped = swarm_stop_gen(a.batch, s);
+            if (stopped != 0u && stopped < a.gen) {  // stopped earlier in the frame: positions carried over
+                if (t < kNdof) a.x_next[(size_t)q * kNdof + t] = a.x[(size_t)q * kNdof + t];
+                __syncthreads();  // the shared random numbers are drawn anew for the next particle
+                continue;
+            }
+        }
         float xi = 0.f, pbi = 0.f, vi = 0.f;
         if (t < kNdof) {  // this particle's own state, loaded before the global best is known
             xi = a.x[(size_t)q * kNdof + t];
@@ -224,6 +233,19 @@ __global__ void __launch_bounds__(64) pso_step_fk_kernel(const __grid_constant__
         const SwarmRefs R{a.x, a.x_next, a.v, a.pbest, a.pbest_E, a.gbest, a.gbest_E, a.c1, a.c2, a.w, a.mutate};
         const StepOut o = swarm_update<64>(R, q, i, off, P, s, n_mutate, s_e, s_pe, s_r, s_m, sh.model.lo,
                                            sh.model.hi, xi, pbi, vi, s_pe[i], true, red_v, red_i, red_r);
+        if (a.batch.views && a.e_stop > 0.f && o.gE < a.e_stop) {
+            // Section III.B's stopping rule: the swarm's best is good enough.  This
+            // generation's bests stand (stored above); the swarm stays where it was
+            // (x_next = x, v as it was, the records of x kept), and the later
+            // generations of the frame skip it
+            if (t < kNdof) {
+                a.x_next[(size_t)q * kNdof + t] = xi;
+                a.v[(size_t)q * kNdof + t] = vi;
+            }
+            if (i == 0 && t == 0) set_swarm_stop_gen(a.batch, s, a.gen);
+            __syncthreads();
+            continue;
+        }
         if (t < kNdof) s_xn[t] = o.xn;
         // FK of the new pose (fk_particle starts with a barrier that publishes s_xn)
         fk_particle(sh, col, s_xn, cam, a.prims + (size_t)q * sh.model.n_prims * 4, a.kc + q,

@@ -66,6 +66,10 @@ __global__ void __launch_bounds__(kWarps * 32, 6)
     if (lane < kStages) mbar_init(&sm.bar[warp][lane], 1);
     if (tid == 0) mbar_fence_init();
     pdl_wait();  // the primitive records and kc come from the previous kernel
+    if (particle_stopped(a, p)) {
+        pdl_launch_dependents();
+        return;
+    }
     const float4* src = a.prims + (size_t)p * a.n_prims * 4;
     stage_prims(src, a.n_prims, pv, sm.rast, sm.pbox, tid, kWarps * 32);
     if (warp == 0) unit_box(src, a.n_prims, pv.W, pv.H, lane, sm.box);

@@ -11,12 +11,12 @@
 //    (8 x 4 pixels per step, SH / 4 steps), and keeps the nearest hit of its
 //    SH / 4 pixels in registers;
 //  * per strip, the primitives whose box meets it are culled with two
-//    ballots; for each of them every lane forms the du terms of its column
-//    once (discriminant, A, B and, for cones, C and the axial coordinate:
-//    Poly2Col), then each step of the primitive's rows costs one polynomial
-//    (two FMAs) and a vote, and the roots run only in steps where some lane
-//    can be hit -- the same arithmetic as raster_hit, so the nearest hit is
-//    bit-identical to the unit kernel's (lower primitive index on equal depth);
+//    ballots; for each of them every lane forms the du terms of its column's
+//    discriminant polynomial once (Poly2Col), the coverage of all the steps of
+//    the primitive's rows is one straight-line block (two FMAs per step, one
+//    bit each), and raster_hit solves for the roots only in steps where some
+//    lane can be hit -- the same arithmetic as the unit kernel, so the nearest
+//    hit is bit-identical to its (lower primitive index on equal depth);
 //  * the strip's observation (16-pixel-wide 2-D TMA boxes, one per 4-row
 //    band, the skin needs 16-byte rows) is loaded into one of the warp's two
 //    shared-memory buffers while the previous strip renders;
@@ -66,26 +66,17 @@ __device__ __forceinline__ uint64_t cull_strip(const int2* pbox, int n_prims, in
 template <int SH>
 constexpr int strip_min_ctas() { return SH > 16 ? 5 : 6; }
 
+// The CTA's copy of particle p's raster records and pixel boxes, and p's
+// screen box clipped to the ROI (sm.box: xa, v0, u1, v1; u1 < 0 when nothing
+// is in the ROI).  Ends with a CTA barrier.
 template <int SH>
-__global__ void __launch_bounds__(kStripWarps * 32, strip_min_ctas<SH>())
-    render_strips_kernel(const __grid_constant__ CUtensorMap tm_depth, const __grid_constant__ CUtensorMap tm_skin,
-                         const RenderArgs a)
+__device__ __forceinline__ void strip_stage(StripShared<SH>& sm, const RenderArgs& a, int p, const ParticleView& pv,
+                                            int tid, int lane, int warp)
 {
-    constexpr int kSteps = SH / 4;
-    using Sh = StripShared<SH>;
-    __shared__ Sh sm;
-    const int p = a.order ? a.order[blockIdx.y] : (int)blockIdx.y;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    HsParticleWork* wk = a.work + p;
-    const ParticleView pv = particle_view(a, p, &tm_depth, &tm_skin);
-
-    if (lane < 2) mbar_init(&sm.bar[warp][lane], 1);
-    if (tid == 0) mbar_fence_init();
-    pdl_wait();  // the primitive records and kc come from the previous kernel
     const int n_prims = a.n_prims;
     const float4* src = a.prims + (size_t)p * n_prims * 4;
     stage_prims(src, n_prims, pv, sm.rast, sm.pbox, tid, kStripWarps * 32);
-    if (warp == 0) {  // the particle's screen box, clipped to the ROI
+    if (warp == 0) {
         int u0 = INT_MAX, v0 = INT_MAX, u1 = INT_MIN, v1 = INT_MIN;
         for (int i = lane; i < n_prims; i += 32) {
             const float4 r3 = src[4 * i + 3];
@@ -111,23 +102,30 @@ __global__ void __launch_bounds__(kStripWarps * 32, strip_min_ctas<SH>())
         }
     }
     __syncthreads();
+}
+
+// One warp's strips q = first, first + stride, ... of particle p (staged by
+// strip_stage): their render and Eq. 4 terms, added to the lane's sums.
+// phases (bit b = parity of buffer b's next completion) and buf (the buffer
+// the next load goes to) carry over from one call to the next.  extra_tx:
+// zero, except in the test of the observation wait's time limit.  Returns
+// false if an observation load did not arrive in time (status flagged; the
+// warp's remaining strips are skipped and no copy is left in flight).
+template <int SH>
+__device__ __forceinline__ bool render_strips_warp(StripShared<SH>& sm, const RenderArgs& a, int p,
+                                                   const ParticleView& pv, int lane, int warp, int first, int stride,
+                                                   uint32_t extra_tx, uint32_t& phases, int& buf, long long& acc_t,
+                                                   uint32_t& acc_a, uint32_t& acc_o, uint32_t& acc_h)
+{
+    constexpr int kSteps = SH / 4;
+    const int n_prims = a.n_prims;
     const int xa = sm.box[0], by0 = sm.box[1], bx1 = sm.box[2], by1 = sm.box[3];
-    const float kcp = a.kc[p];
-    if (bx1 < 0) {  // nothing of the hand inside the ROI: E is the baseline
-        pdl_launch_dependents();
-        if (blockIdx.x == 0 && tid == 0) write_baseline(a, p, pv.stats, kcp);
-        return;
-    }
     const int nsx = (bx1 + 1 - xa + kStripW - 1) / kStripW;
     const int n_strips = nsx * ((by1 + 1 - by0 + SH - 1) / SH);
-    const int first = blockIdx.x * kStripWarps + warp, stride = gridDim.x * kStripWarps;
     const int W = pv.W, H = pv.H, depth_f32 = pv.depth_f32;
     const int lx = lane & 7, ly = lane >> 3;
     uint64_t* bar = sm.bar[warp];
 
-    // zero but in the test of the observation wait's time limit (bytes the
-    // particle's first load is armed for beyond those copied)
-    uint32_t extra_tx = blockIdx.x == 0 && warp == 0 ? wk->tx_test : 0u;
     // the observation of strip q into buffer b: one 16 x 4 box of depth and of
     // skin per band of rows inside the box, issued by one lane each
     auto issue = [&](int q, int b) {
@@ -146,14 +144,10 @@ __global__ void __launch_bounds__(kStripWarps * 32, strip_min_ctas<SH>())
         }
     };
 
-    long long acc_t = 0;
-    uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
-    uint32_t phases = 0u;
     bool ok = true;
-    int buf = 0;
     int q = first;
     bool next_issued = false;  // the load of strip q + stride is in flight in buffer buf ^ 1
-    if (first < n_strips) issue(first, 0);
+    if (first < n_strips) issue(first, buf);
     for (; q < n_strips; q += stride, buf ^= 1) {
         next_issued = q + stride < n_strips;
         if (next_issued) issue(q + stride, buf ^ 1);  // the next strip's observation meanwhile
@@ -180,52 +174,28 @@ __global__ void __launch_bounds__(kStripWarps * 32, strip_min_ctas<SH>())
             const int s1 = (min(hi_i16(__int_as_float(pb.y)), y1) - y0) >> 2;
             const float4 q0 = R[0], q1 = R[1];
             const float du = fx - q0.x;
-            const uint32_t caps = raster_caps(R);
-            const Poly2Col PD = poly2_col(q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, du);
+            const bool caps = __float_as_uint(R[4].w) != 0u;
+            const Poly2Col PD = raster_disc_col(q0, q1, du);
             // coverage of every step of the primitive's rows at once
             // (independent polynomials, one bit each, no branch per step)
             uint32_t m = 0u;
 #pragma unroll
             for (int s = 0; s < kSteps; ++s) {
                 const float dv = (fy0 + (float)(4 * s)) - q0.y;
-                m |= (uint32_t)(PD.at(dv) >= 0.f || caps != 0u) << s;
+                m |= (uint32_t)(PD.at(dv) >= 0.f || caps) << s;
             }
             m &= (2u << s1) - (1u << s0);  // the steps of the primitive's rows
             const uint32_t wm = __reduce_or_sync(0xffffffffu, m);  // steps some lane can hit
             if (!wm) continue;
             // the roots, where some lane of the step can be hit; the nearest hit
             // per pixel (strict <: the lower primitive index wins equal depths)
-            const float4 q2 = R[2], q3 = R[3], q4 = R[4], q5 = R[5];
-            const float t0 = q3.z;
-            const bool ell = q3.w > 1.5f;
-            const Poly2Col PA = poly2_col(q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, du);
-            const Poly2Col PB = poly2_col(q4.x, q4.y, q4.z, q4.w, q5.x, q5.y, du);
-            Poly2Col PC{0.f, 0.f, 0.f};
-            float gy_u = 0.f, gy_v = 0.f, hy_u = 0.f, hy_v = 0.f;
-            if (!ell) {
-                const float4 q6 = R[6], q7 = R[7], q8 = R[8];
-                PC = poly2_col(q6.x, q6.y, q6.z, q6.w, q7.x, q7.y, du);
-                gy_u = fmaf(du, q7.z, 0.f);  // lin2(0, gY_u, gY_v) with its du term formed once
-                gy_v = q7.w;
-                hy_u = fmaf(du, q8.y, q8.x);
-                hy_v = q8.z;
-            }
+            const float4 q2 = R[2], q3 = R[3], q4 = R[4];
+            const float t0 = q2.w;
 #pragma unroll
             for (int s = 0; s < kSteps; ++s) {
                 if (!((wm >> s) & 1u)) continue;  // no lane can be hit in this step (warp-uniform)
                 const float dv = (fy0 + (float)(4 * s)) - q0.y;
-                const float disc = PD.at(dv);
-                float sh = INFINITY;
-                if (disc >= 0.f) {
-                    const float A = PA.at(dv), B = PB.at(dv);
-                    if (ell) {
-                        sh = ellipsoid_root(t0, A, B, disc);
-                    } else {
-                        const float C = PC.at(dv);
-                        sh = cone_root(t0, A, B, C, fmaf(dv, gy_v, gy_u), fmaf(dv, hy_v, hy_u), disc);
-                    }
-                }
-                if (caps) sh = cone_caps(R, caps, du, dv, sh);
+                const float sh = raster_hit(q2, q3, q4, du, dv, PD.at(dv));
                 const float zz = t0 + sh;
                 if (((m >> s) & 1u) && zz < z[s]) {
                     z[s] = zz;
@@ -261,24 +231,122 @@ __global__ void __launch_bounds__(kStripWarps * 32, strip_min_ctas<SH>())
         __syncwarp();  // every lane is done with this buffer before it is refilled
     }
     if (!ok) {
-        // a load that did not arrive in time (status flagged): the warp's
-        // remaining strips are skipped, and the copies still expected -- the
-        // late one and the next strip's, if issued -- are awaited (bounded)
-        // so that none is in flight when the CTA leaves
+        // the copies still expected -- the late one and the next strip's, if
+        // issued -- are awaited (bounded) so that none is in flight when the
+        // CTA leaves
         mbar_wait_bounded(&bar[buf], ((phases >> buf) & 1u) ^ 1u, a.status);
         if (next_issued) mbar_wait_bounded(&bar[buf ^ 1], (phases >> (buf ^ 1)) & 1u, a.status);
     }
+    return ok;
+}
+
+// Grid (K, P): CTA k of particle p takes p's strips k, k + K, ... (per warp:
+// 4k + w, 4k + w + 4K, ...); the last warp of the particle forms E.
+template <int SH>
+__global__ void __launch_bounds__(kStripWarps * 32, strip_min_ctas<SH>())
+    render_strips_kernel(const __grid_constant__ CUtensorMap tm_depth, const __grid_constant__ CUtensorMap tm_skin,
+                         const RenderArgs a)
+{
+    __shared__ StripShared<SH> sm;
+    const int p = a.order ? a.order[blockIdx.y] : (int)blockIdx.y;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    HsParticleWork* wk = a.work + p;
+    const ParticleView pv = particle_view(a, p, &tm_depth, &tm_skin);
+
+    if (lane < 2) mbar_init(&sm.bar[warp][lane], 1);
+    if (tid == 0) mbar_fence_init();
+    pdl_wait();  // the primitive records and kc come from the previous kernel
+    if (particle_stopped(a, p)) {
+        pdl_launch_dependents();
+        return;
+    }
+    strip_stage(sm, a, p, pv, tid, lane, warp);
+    const float kcp = a.kc[p];
+    if (sm.box[2] < 0) {  // nothing of the hand inside the ROI: E is the baseline
+        pdl_launch_dependents();
+        if (blockIdx.x == 0 && tid == 0) write_baseline(a, p, pv.stats, kcp);
+        return;
+    }
+    long long acc_t = 0;
+    uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
+    uint32_t phases = 0u;
+    int buf = 0;
+    // zero but in the test of the observation wait's time limit (bytes the
+    // particle's first load is armed for beyond those copied)
+    const uint32_t extra_tx = blockIdx.x == 0 && warp == 0 ? wk->tx_test : 0u;
+    render_strips_warp(sm, a, p, pv, lane, warp, blockIdx.x * kStripWarps + warp, gridDim.x * kStripWarps, extra_tx,
+                       phases, buf, acc_t, acc_a, acc_o, acc_h);
     pdl_launch_dependents();
     warp_sum(acc_t, acc_a, acc_o, acc_h);
     if (lane == 0) flush_and_finish(a, p, wk, pv.stats, kcp, acc_t, acc_a, acc_o, acc_h, gridDim.x * kStripWarps);
 }
 
+// The persistent form (Section IV's parallelism between particles, dealt at
+// run time): as many CTAs as the GPU keeps resident, each taking the next
+// particle (of any swarm of a batch, in the call's order: largest ROI first)
+// from a counter in the workspace's control block, rendering all of its
+// strips with its four warps, forming its E, and taking the next, until
+// every particle is done.  The last CTA to leave returns the counters to
+// zero for the next call.
+template <int SH>
+__global__ void __launch_bounds__(kStripWarps * 32, strip_min_ctas<SH>())
+    render_strips_persistent_kernel(const __grid_constant__ CUtensorMap tm_depth,
+                                    const __grid_constant__ CUtensorMap tm_skin, const RenderArgs a)
+{
+    __shared__ StripShared<SH> sm;
+    __shared__ int s_item;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    RenderCtl* ctl = a.ctl;
+
+    if (lane < 2) mbar_init(&sm.bar[warp][lane], 1);
+    if (tid == 0) mbar_fence_init();
+    pdl_wait();  // the primitive records and kc come from the previous kernel
+    uint32_t phases = 0u;
+    int buf = 0;
+    bool alive = true;  // false once one of this warp's observation waits ran out (status flagged): the warp
+                        // renders nothing more in this launch, and the call's results are void
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(&ctl->next, 1u);
+        __syncthreads();  // also: every warp is done with the previous particle's records
+        const int item = s_item;
+        if (item >= a.P) break;
+        const int p = a.order ? a.order[item] : item;
+        if (particle_stopped(a, p)) continue;
+        HsParticleWork* wk = a.work + p;
+        const ParticleView pv = particle_view(a, p, &tm_depth, &tm_skin);
+        strip_stage(sm, a, p, pv, tid, lane, warp);
+        const float kcp = a.kc[p];
+        if (sm.box[2] < 0) {  // nothing of the hand inside the ROI: E is the baseline
+            if (tid == 0) write_baseline(a, p, pv.stats, kcp);
+            continue;
+        }
+        long long acc_t = 0;
+        uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
+        const uint32_t extra_tx = warp == 0 ? wk->tx_test : 0u;
+        if (alive)
+            alive = render_strips_warp(sm, a, p, pv, lane, warp, warp, kStripWarps, extra_tx, phases, buf, acc_t,
+                                       acc_a, acc_o, acc_h);
+        warp_sum(acc_t, acc_a, acc_o, acc_h);
+        if (lane == 0) flush_and_finish(a, p, wk, pv.stats, kcp, acc_t, acc_a, acc_o, acc_h, kStripWarps);
+    }
+    pdl_launch_dependents();
+    if (tid == 0) {
+        // the last CTA to leave: every CTA has taken its last ticket, so the
+        // counters can return to zero for the next call
+        uint32_t done;
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(done) : "l"(&ctl->exited) : "memory");
+        if (done == gridDim.x - 1) {
+            ctl->next = 0u;
+            ctl->exited = 0u;
+        }
+    }
+}
+
 template <int SH>
 static cudaError_t launch_strips(const CUtensorMap& tm_depth, const CUtensorMap& tm_skin, const RenderArgs& args,
-                                 cudaStream_t stream)
+                                 bool persistent, cudaStream_t stream)
 {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(args.K, args.P);
     cfg.blockDim = dim3(kStripWarps * 32);
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
@@ -286,15 +354,31 @@ static cudaError_t launch_strips(const CUtensorMap& tm_depth, const CUtensorMap&
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, render_strips_kernel<SH>, tm_depth, tm_skin, args);
+    if (!persistent) {
+        cfg.gridDim = dim3(args.K, args.P);
+        return cudaLaunchKernelEx(&cfg, render_strips_kernel<SH>, tm_depth, tm_skin, args);
+    }
+    // one CTA per resident slot of the device, at most one per particle
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_strips_persistent_kernel<SH>,
+                                                          kStripWarps * 32, 0);
+    if (e != cudaSuccess) return e;
+    const long long slots = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    cfg.gridDim = dim3((unsigned)(slots < args.P ? slots : args.P));
+    return cudaLaunchKernelEx(&cfg, render_strips_persistent_kernel<SH>, tm_depth, tm_skin, args);
 }
 
 cudaError_t launch_render_strips(int variant, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,
                                  const RenderArgs& args, cudaStream_t stream)
 {
     switch (variant) {
-    case HS_RENDER_STRIPS_8x16: return launch_strips<16>(tm_depth, tm_skin, args, stream);
-    case HS_RENDER_STRIPS_8x32: return launch_strips<32>(tm_depth, tm_skin, args, stream);
+    case HS_RENDER_STRIPS_8x16: return launch_strips<16>(tm_depth, tm_skin, args, false, stream);
+    case HS_RENDER_STRIPS_8x32: return launch_strips<32>(tm_depth, tm_skin, args, false, stream);
+    case HS_RENDER_PERSISTENT_8x16: return launch_strips<16>(tm_depth, tm_skin, args, true, stream);
+    case HS_RENDER_PERSISTENT_8x32: return launch_strips<32>(tm_depth, tm_skin, args, true, stream);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -83,6 +83,10 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
         mbar_fence_init();
     }
     pdl_wait();  // the primitive records and kc come from the previous kernel
+    if (particle_stopped(a, p)) {
+        pdl_launch_dependents();
+        return;
+    }
     const int n_prims = a.n_prims;
     const float4* src = a.prims + (size_t)p * n_prims * 4;
     stage_prims(src, n_prims, pv, s_rast, s_pbox, tid, NW * 32);  // raster form of each primitive, once per CTA
@@ -208,42 +212,23 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
             const uint32_t mg = s_magic[k];
             const int c0 = s_pre[k], c1 = s_pre[k + 1];
             const float4* R = s_rast + kRastVec * j;
-            const float4 q0 = R[0];
-            const float t0 = R[3].z;
-            // the primitive's chunks; hit(du, dv, disc) gives the depth offset
-            auto chunks = [&](const float4* Rd, auto hit) {
-                for (; c < c1; c += NW) {
-                    const int idx = ((c - c0) << 5) + lane;
-                    if (idx < rc.w) {
-                        const int y = (int)(((unsigned long long)(uint32_t)idx * mg) >> 31);
-                        const int px = rc.x + idx - y * rc.z, py = rc.y + y;
-                        const float du = (float)px - q0.x, dv = (float)py - q0.y;
-                        const float sh = hit(du, dv, raster_disc(Rd, du, dv));
-                        const float zz = t0 + sh;
-                        if (zz < INFINITY) {
-                            const float dz = sh - (zz - t0);  // z - t0 is exact (Sterbenz): dz is the residual
-                            atomicMin(&s_z[(py - ty0) * TW + (px - tx0)],
-                                      ((unsigned long long)__float_as_uint(zz) << 32) | __float_as_uint(dz));
-                        }
+            const float4 q0 = R[0], q1 = R[1], q2 = R[2], q3 = R[3], q4 = R[4];  // in registers for the chunks
+            const float t0 = q2.w;
+            for (; c < c1; c += NW) {
+                const int idx = ((c - c0) << 5) + lane;
+                if (idx < rc.w) {
+                    const int y = (int)(((unsigned long long)(uint32_t)idx * mg) >> 31);
+                    const int px = rc.x + idx - y * rc.z, py = rc.y + y;
+                    const float du = (float)px - q0.x, dv = (float)py - q0.y;
+                    const float disc = raster_disc(q0, q1, du, dv);
+                    const float sh = raster_maybe(q4, disc) ? raster_hit(q2, q3, q4, du, dv, disc) : INFINITY;
+                    const float zz = t0 + sh;
+                    if (zz < INFINITY) {
+                        const float dz = sh - (zz - t0);  // z - t0 is exact (Sterbenz): dz is the residual
+                        atomicMin(&s_z[(py - ty0) * TW + (px - tx0)],
+                                  ((unsigned long long)__float_as_uint(zz) << 32) | __float_as_uint(dz));
                     }
                 }
-            };
-            // the record in registers for the primitive's chunks (the z-buffer
-            // atomics would otherwise make every pixel reload it), split by kind
-            if (raster_caps(R) != 0u) {  // visible cone caps: the general path, from shared memory
-                chunks(R, [&](float du, float dv, float disc) {
-                    return raster_maybe(R, disc) ? raster_hit(R, du, dv, disc) : INFINITY;
-                });
-            } else if (raster_is_ellipsoid(R)) {
-                float4 Rl[6];
-#pragma unroll
-                for (int k = 0; k < 6; ++k) Rl[k] = R[k];
-                chunks(Rl, [&](float du, float dv, float disc) { return raster_surface_hit<true>(Rl, du, dv, disc); });
-            } else {
-                float4 Rl[9];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) Rl[k] = R[k];
-                chunks(Rl, [&](float du, float dv, float disc) { return raster_surface_hit<false>(Rl, du, dv, disc); });
             }
         }
         extra_tx = 0u;

@@ -63,11 +63,12 @@ class HsScoreParams(ctypes.Structure):
 
 # render kernels (same results, different work layout); AUTO picks by particles per call
 (RENDER_AUTO, RENDER_UNITS, RENDER_TILES_32x16, RENDER_TILES_32x32, RENDER_TILES_64x32, RENDER_TILES_64x64,
- RENDER_STRIPS_8x16, RENDER_STRIPS_8x32) = range(8)
+ RENDER_STRIPS_8x16, RENDER_STRIPS_8x32, RENDER_PERSISTENT_8x16, RENDER_PERSISTENT_8x32) = range(10)
 RENDER_VARIANTS = {"auto": RENDER_AUTO, "units": RENDER_UNITS, "tiles32x16": RENDER_TILES_32x16,
                    "tiles32x32": RENDER_TILES_32x32, "tiles64x32": RENDER_TILES_64x32,
                    "tiles64x64": RENDER_TILES_64x64, "strips8x16": RENDER_STRIPS_8x16,
-                   "strips8x32": RENDER_STRIPS_8x32}
+                   "strips8x32": RENDER_STRIPS_8x32, "persistent8x16": RENDER_PERSISTENT_8x16,
+                   "persistent8x32": RENDER_PERSISTENT_8x32}
 
 
 class HsSwarm(ctypes.Structure):
@@ -76,7 +77,7 @@ class HsSwarm(ctypes.Structure):
 
 class HsPsoParams(ctypes.Structure):
     _fields_ = [("c1", ctypes.c_float), ("c2", ctypes.c_float), ("mutate_every", ctypes.c_int32),
-                ("n_mutate", ctypes.c_int32)]
+                ("n_mutate", ctypes.c_int32), ("e_stop", ctypes.c_float)]
 
 
 class HsSoftParams(ctypes.Structure):
@@ -273,11 +274,12 @@ def score_params(d_m=10.0, d_M=40.0, lam=20.0, lam_k=10.0, variant=RENDER_AUTO, 
     return HsScoreParams(d_m, d_M, lam, lam_k, int(variant), int(ctas_per_particle))
 
 
-def pso_params(c1=2.8, c2=1.3, mutate_every=3, n_mutate=None, P=None) -> HsPsoParams:
-    """Section III.B constants; n_mutate defaults to half the swarm."""
+def pso_params(c1=2.8, c2=1.3, mutate_every=3, n_mutate=None, P=None, e_stop=0.0) -> HsPsoParams:
+    """Section III.B constants; n_mutate defaults to half the swarm; e_stop > 0
+    (batch steps only) stops a swarm once its best E falls below it."""
     if n_mutate is None:
         n_mutate = (P or 0) // 2
-    return HsPsoParams(c1, c2, mutate_every, n_mutate)
+    return HsPsoParams(c1, c2, mutate_every, n_mutate, e_stop)
 
 
 # ---- observation ----------------------------------------------------------------------

@@ -237,7 +237,7 @@ def test_other_host_checks():
     assert L.pose_grad(m.handle, FAKE, 4, ctypes.byref(cam), ctypes.byref(prm), FAKE + 8, FAKE, FAKE, FAKE,
                        None) == hs.HS_ERR_ALIGN
     # render launch shape: variant and CTAs per particle are validated; autotuning needs params and reps >= 1
-    bad_v = hs.score_params(variant=9)
+    bad_v = hs.score_params(variant=len(hs.RENDER_VARIANTS))  # one past the last kernel
     assert L.render_score_batch(m.handle, ctypes.byref(o), ctypes.byref(cam), FAKE, FAKE, 64, ctypes.byref(bad_v),
                                 FAKE, 1 << 20, FAKE, None, None, None, None) == hs.HS_ERR_ARG
     bad_k = hs.score_params(ctas_per_particle=65)

@@ -208,7 +208,7 @@ def test_autotune_picks_a_valid_shape_and_keeps_results(scenes):
     E = torch.zeros(P, device=dev)
     prm, table = hs.render_score_batch_autotune(sc.model_g, obs, cam, prims, kc, hs.score_params(),
                                                 hs.new_workspace(P), E, reps=2)
-    assert prm.variant in range(1, 6) and prm.ctas_per_particle in hs.TUNE_CTAS
+    assert prm.variant in range(1, len(hs.RENDER_VARIANTS)) and prm.ctas_per_particle in hs.TUNE_CTAS
     assert len(table) >= 5 and all(t > 0 for t in table.values())
     assert min(table.values()) == table[f"{hs.render_variant(prm, P)}/k{prm.ctas_per_particle}"]
     assert np.float32(prm.d_M) == 40.0
@@ -222,5 +222,116 @@ def test_autotune_picks_a_valid_shape_and_keeps_results(scenes):
     before = [t.clone() for t in bt._state()]
     starts = torch.from_numpy(np.stack([s.poses[0] for s in scenes])).cuda()
     table = bt.autotune(starts, reps=1)
-    assert bt.score.variant in range(1, 6) and len(table) >= 5
+    assert bt.score.variant in range(1, len(hs.RENDER_VARIANTS)) and len(table) >= 5
     assert all(torch.equal(a, c) for a, c in zip(before, bt._state()))
+
+
+@pytest.mark.parametrize("variant", [hs.RENDER_PERSISTENT_8x16, hs.RENDER_PERSISTENT_8x32])
+def test_persistent_render_equals_grid_kernels(scenes, variant):
+    """The persistent launch (resident CTAs taking particles from a counter)
+    gives the grid kernels' E and sums bit for bit: on the uneven batch, on
+    2400 particles (several per CTA), twice in a row (its counters return to
+    zero), and on a single swarm."""
+    obs, cams, b = _batch(scenes)
+    m = scenes[0].model_g
+    poses = torch.from_numpy(np.concatenate([sc.poses for sc in scenes])).cuda()
+    prims = torch.zeros(b.P_total, m.n_prims, 16, device="cuda")
+    kc = torch.zeros(b.P_total, device="cuda")
+    hs.hs_obs_prepare_multi(b)
+    hs.pose_fk_multi(m, b, poses, prims, kc)
+
+    def score(v, bb, pr, k):
+        E = torch.zeros(bb.P_total, device="cuda")
+        parts = torch.zeros(bb.P_total, 4, dtype=torch.int32, device="cuda")
+        ws = hs.new_workspace(bb.P_total)
+        hs.render_score_multi(m, bb, pr, k, hs.score_params(variant=v), ws, E, parts)
+        hs.render_score_multi(m, bb, pr, k, hs.score_params(variant=v), ws, E, parts)
+        torch.cuda.synchronize()
+        assert int(ws.count_nonzero()) == 0
+        return E.cpu().numpy(), parts.cpu().numpy()
+
+    ref = score(hs.RENDER_STRIPS_8x16, b, prims, kc)
+    got = score(variant, b, prims, kc)
+    assert np.array_equal(got[0].view(np.uint32), ref[0].view(np.uint32)) and np.array_equal(got[1], ref[1])
+    # many particles: the CTAs take several each
+    sc = C.make_scene(96, 72, 60, 511, noisy=True, f32=False)
+    _, _, b2 = _batch([sc] * 40)
+    tp = torch.from_numpy(np.concatenate([sc.poses] * 40)).cuda()
+    pr2 = torch.zeros(b2.P_total, m.n_prims, 16, device="cuda")
+    kc2 = torch.zeros(b2.P_total, device="cuda")
+    hs.hs_obs_prepare_multi(b2)
+    hs.pose_fk_multi(m, b2, tp, pr2, kc2)
+    ref = score(hs.RENDER_UNITS, b2, pr2, kc2)
+    got = score(variant, b2, pr2, kc2)
+    assert np.array_equal(got[0].view(np.uint32), ref[0].view(np.uint32)) and np.array_equal(got[1], ref[1])
+    # a single swarm
+    gr = C.run_gpu(scenes[2], debug=True, variant=variant)
+    gu = C.run_gpu(scenes[2], debug=True, variant=hs.RENDER_UNITS)
+    assert np.array_equal(gr.E.view(np.uint32), gu.E.view(np.uint32)) and np.array_equal(gr.mask, gu.mask)
+    assert hs.hs_get_device_status(clear=True) == 0
+
+
+def _run_batch_frame(m, b, starts, gens, e_stop, seeds_key=0):
+    """One frame of every swarm through the batch calls, step by step; the
+    global best E of every swarm after each generation."""
+    sw = hs.batch_swarm(b, torch.device("cuda"))
+    x_buf = (sw.x, torch.zeros_like(sw.x))
+    prims = torch.zeros(b.P_total, m.n_prims, 16, device="cuda")
+    kc = torch.zeros(b.P_total, device="cuda")
+    ws = hs.new_workspace(b.P_total)
+    scale = np.full(26, np.radians(10.0), np.float32)
+    scale[:3] = 10.0
+    pso = hs.pso_params(e_stop=e_stop)
+    hs.hs_obs_prepare_multi(b)
+    cur, nxt = x_buf
+    sw.x = cur
+    hs.pso_init_multi(m, b, sw, torch.from_numpy(starts).cuda(), scale, 0)
+    hs.pose_fk_multi(m, b, cur, prims, kc)
+    traj = []
+    for g in range(1, gens + 1):
+        hs.render_score_multi(m, b, prims, kc, hs.score_params(), ws, sw.E)
+        sw.x = cur
+        hs.pso_step_fk_multi(m, b, sw, nxt, pso, 0, g, prims, kc)
+        cur, nxt = nxt, cur
+        torch.cuda.synchronize()
+        traj.append((sw.gbest_E.cpu().numpy().copy(), sw.gbest.cpu().numpy().copy(), cur.cpu().numpy().copy(),
+                     sw.E.cpu().numpy().copy()))
+    return traj
+
+
+def test_device_stop_flags(scenes):
+    """Section III.B's stopping rule on the device (e_stop): a swarm whose best
+    E falls below e_stop after generation g keeps generation g's bests, stays
+    where it was, and is neither scored nor moved again in the frame, while
+    the other swarms go on exactly as without the rule; the next frame's init
+    starts every swarm again."""
+    sub = scenes[:4]
+    obs, cams, b = _batch(sub)
+    m = sub[0].model_g
+    starts = np.stack([sc.poses[-1] for sc in sub]).astype(np.float32)
+    gens = 7
+    free = _run_batch_frame(m, b, starts, gens, 0.0)
+    gE = np.stack([t[0] for t in free])  # [gens, S]
+    # a threshold that swarm 0 crosses at generation 3 at the latest
+    e_stop = float(np.nextafter(np.float32(gE[2, 0]), np.float32(np.inf)))
+    stop_gen = [next((g + 1 for g in range(gens) if gE[g, s] < e_stop), None) for s in range(len(sub))]
+    assert stop_gen[0] is not None and stop_gen[0] <= 3
+    got = _run_batch_frame(m, b, starts, gens, e_stop)
+    last = got[-1]
+    for s in range(len(sub)):
+        lo, hi = b.offsets[s], b.offsets[s + 1]
+        g = stop_gen[s]
+        if g is None:  # never stopped: exactly the run without the rule
+            assert last[0][s] == free[-1][0][s] and np.array_equal(last[1][s], free[-1][1][s]), s
+            assert np.array_equal(last[2][lo:hi], free[-1][2][lo:hi]), s
+        else:
+            # generation g's bests, and the positions scored at generation g
+            assert last[0][s] == gE[g - 1, s] and np.array_equal(last[1][s], free[g - 1][1][s]), s
+            scored = free[g - 2][2][lo:hi] if g >= 2 else None
+            if scored is not None:
+                assert np.array_equal(last[2][lo:hi], scored), s
+            assert np.array_equal(last[3][lo:hi], free[g - 1][3][lo:hi]), s  # E not scored again
+    # the next frame's init starts every swarm again: with the rule off it
+    # equals the free run
+    again = _run_batch_frame(m, b, starts, gens, 0.0)
+    assert np.array_equal(again[-1][0], free[-1][0]) and np.array_equal(again[-1][2], free[-1][2])

@@ -92,9 +92,11 @@ def parse():
     ap.add_argument("--render", default="tune", help="render kernel: tune (timed on the workload first), auto, "
                     "units, tiles32x16, tiles32x32, tiles64x32, tiles64x64")
     ap.add_argument("--ctas", type=int, default=0, help="render CTAs per particle (0 = automatic)")
-    ap.add_argument("--workload", choices=["kinect", "batch", "fullframe"], default="kinect",
+    ap.add_argument("--workload", choices=["kinect", "batch", "fullframe", "render"], default="kinect",
                     help="kinect: one 320x240 sequence (the headline); batch: 64 sequences with uneven ROIs and P; "
-                         "fullframe: 640x480 sequence, s/frame to <= 5 deg at several swarm sizes")
+                         "fullframe: 640x480 sequence, s/frame to <= 5 deg at several swarm sizes; render: "
+                         "render_score_batch alone on one frame (--roi, the first of --particles, --render; for "
+                         "profiling one kernel)")
     ap.add_argument("--particles", default="256,1024,4096", help="fullframe: swarm sizes")
     ap.add_argument("--frames", type=int, default=100, help="fullframe: frames of the sequence")
     ap.add_argument("--gens", default="5,10,20,50", help="fullframe: generation budgets per frame")
@@ -127,7 +129,8 @@ KERNEL_SOURCES = {
 }
 PROFILE_FILES = {("kinect", "units"): "render_units_kinect_320x240.txt",
                  ("batch", "tiles"): "render_tiles32x32_batch_64seq.txt",
-                 ("kinect", "frame"): "track_frame_kinect_320x240.txt"}
+                 ("kinect", "frame"): "track_frame_kinect_320x240.txt",
+                 ("fullframe640x480P4096", "strips"): "render_strips8x32_fullframe_640x480.txt"}
 
 
 def source_sha256(kind: str) -> str:
@@ -482,6 +485,39 @@ def batch_render_roofline(hs, model, sizes, Ps, store, staging, batch, trk, gt0,
     return rec
 
 
+def batch_throughput(hs, bset, frames, steps, warmup, dev):
+    """Tracking throughput of the batched workload: frames of every sequence
+    replayed from their captured graphs (frame f's data copied into the bound
+    buffers first), L2 flushed between steps, CUDA events around each step.
+    Returns evals/s and the per-frame latency of every sequence (p50 / p99)."""
+    import torch
+    sizes, Ps, store, staging, batch, trk, gt0, _ = bset
+    graphs = [trk.graph(f, gt0 if f == 0 else None) for f in range(frames)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        staging.dev.copy_(store[i % frames].dev)
+        graphs[i % frames].replay()
+
+    for i in range(warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step(warmup + i)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = [a.elapsed_time(b) for a, b in evs]
+    return {"value": steps * trk.evals_per_frame() / (sum(ms) * 1e-3), "unit": "evals/s",
+            "ms_per_frame": sum(ms) / steps, "latency_ms": {"p50": percentile(ms, 50), "p99": percentile(ms, 99)},
+            "steps": steps, "warmup": warmup, "gpu_launches_per_step": trk.launches_per_frame(),
+            "sequences": batch.S, "particles_total": batch.P_total,
+            "step": "one frame of every sequence: one frame copy + one CUDA graph; L2 flushed between steps"}
+
+
 def run_batch(args, rank, world, local):
     import torch
     from paper_2005_07068_b300 import build as B
@@ -808,6 +844,60 @@ def run_fullframe(args, rank, world, local):
     return 0
 
 
+def run_render(args, rank, world, local):
+    """render_score_batch alone: one seeded Kinect-style frame at --roi, the
+    first swarm size of --particles spread around the ground truth (half the
+    tracking perturbation), kernel --render (not tuned), --warmup untimed and
+    --steps timed launches (CUDA events).  Few launches, small device
+    footprint: the command profiling summaries capture one kernel with."""
+    import torch
+    from paper_2005_07068_b300 import build as B
+    from paper_2005_07068_b300 import handscore as hs
+    from paper_2005_07068_b300 import inputs as I
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    Wr, Hr = (int(v) for v in args.roi.split(","))
+    P = int(args.particles.split(",")[0])
+    g = I.hand_geometry()
+    lo, hi = (a.astype(np.float32) for a in I.search_limits())
+    model = hs.Model.from_geometry(g, lo, hi)
+    camt = I.kinect_camera(Wr, Hr)
+    cam = hs.camera(camt.fx, camt.fy, camt.cx, camt.cy)
+    seed = I.CONFIG_SEED_BASE + 5
+    traj, obs, _ = make_frames(seed, 1, hs, I, model, cam, dev, W=Wr, H=Hr)
+    rng = np.random.default_rng(seed)
+    poses = np.clip(traj[0][None] + 0.5 * rng.uniform(-1, 1, (P, 26)) * I.perturbation_scale(), lo, hi)
+    prims = torch.zeros(P, model.n_prims, 16, device=dev)
+    kc = torch.zeros(P, device=dev)
+    hs.pose_fk(model, torch.from_numpy(poses.astype(np.float32)).to(dev), cam, prims, kc)
+    hs.hs_obs_prepare(obs[0])
+    ws = hs.new_workspace(P, dev)
+    E = torch.zeros(P, device=dev)
+    variant = "auto" if args.render == "tune" else args.render
+    prm = hs.score_params(variant=hs.RENDER_VARIANTS[variant], ctas_per_particle=args.ctas)
+    for _ in range(args.warmup):
+        hs.render_score_batch(model, obs[0], cam, prims, kc, prm, ws, E)
+    torch.cuda.synchronize(dev)
+    a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a_ev.record()
+    for _ in range(args.steps):
+        hs.render_score_batch(model, obs[0], cam, prims, kc, prm, ws, E)
+    b_ev.record()
+    torch.cuda.synchronize(dev)
+    tests = algorithmic_tests(prims[:, :, 14:16].cpu().numpy(), g.prims_i[:, 1], Wr, Hr)
+    us = a_ev.elapsed_time(b_ev) * 1e3 / max(args.steps, 1)
+    rec = roofline_record(tests, us, fp32_xu_peaks(dev, measured_peaks()), f"render_score_batch ({variant})",
+                          "CUDA events around back-to-back eager launches", args.steps)
+    if rank == 0:
+        print(json.dumps({"workload": f"render only: {Wr}x{Hr}, {P} particles", "launch_us": us,
+                          "roofline": rec, "gpu_launches": args.warmup + args.steps}), flush=True)
+    return 0
+
+
 # ---- the native arm ------------------------------------------------------------------------
 
 def main():
@@ -821,6 +911,8 @@ def main():
         return run_batch(args, rank, world, local)
     if args.workload == "fullframe":
         return run_fullframe(args, rank, world, local)
+    if args.workload == "render":
+        return run_render(args, rank, world, local)
 
     import torch
     from paper_2005_07068_b300 import build as B
@@ -968,9 +1060,11 @@ def main():
         # 640x480 frames with 4096 particles (render_score_batch)
         if not args.no_sub_rooflines:
             bseed = R.replica_seed(I.CONFIG_SEED_BASE + 4, rank)
-            bset = batch_setup(hs, I, model, bseed, 1, dev, args.render, args.ctas)
+            bset = batch_setup(hs, I, model, bseed, 2, dev, args.render, args.ctas)
+            thr = batch_throughput(hs, bset, 2, 8, 3, dev)
             sub["batch_64seq"] = batch_render_roofline(hs, model, *bset[:7], kinds, pk, dev)
             sub["batch_64seq"]["autotune_us"] = bset[7]
+            sub["batch_64seq"]["tracking"] = thr
             del bset
             torch.cuda.empty_cache()
             fseed = R.replica_seed(I.CONFIG_SEED_BASE + 5, rank)

@@ -26,8 +26,8 @@
 //    (width tau_mm) on valid pixels, r_m's test sigma((d_m - diff) / tau_mm),
 //    t = c t_hit + (1 - c) t_miss, r_m = c m; then D_s and E_s as Eq. 4-5.
 //
-// soft_kernel<false> forms E_s (fixed-point integer sums, like the hard
-// path); soft_kernel<true> recomputes each pixel and pushes dE_s/d(pixel
+// soft_forward_kernel forms E_s (fixed-point integer sums, like the hard
+// path); soft_backward_kernel recomputes each pixel and pushes dE_s/d(pixel
 // terms) back through the compositing and each primitive's coverage and depth
 // to its record (M, C: 12 numbers) and, for cones, to L; pose_grad_kernel maps
 // those adjoints to the 26 pose parameters with forward-mode tangents of the
@@ -311,9 +311,26 @@ __device__ __forceinline__ float cone_pixel_length(const float4& r0, const float
     return fmaxf(half, r_px);
 }
 
-// byte offsets of soft_kernel's dynamic shared memory (each 16-byte aligned)
+// Work layout of soft_backward_kernel.  A CTA of kSoftWarps warps works on one strip
+// of 32 pixels of the particle's union box (row-major order) at a time; lane
+// l of every warp stands for pixel l of the strip.
+//  A. the warps split the primitives (j = w, w + kSoftWarps, ...): each lane
+//     evaluates primitive j at its pixel (soft_eval) and, where alpha >
+//     kAlphaMin, appends (alpha, z, j) to the pixel's list;
+//  B. warp 0 sorts each pixel's list front to back (depth, then primitive
+//     index: the forward kernel's order), composites it, forms the pixel's
+//     terms of Eq. 4 and pushes dE_s back through the compositing to every
+//     entry's (d alpha, d z);
+//  C. the warps split the primitives again: the lanes whose pixel
+//     lists primitive j push its (d alpha, d z) back to its record (soft_eval
+//     again, then soft_backprop), and the warp sums the 13 adjoints.
+// So a strip's chain of evaluations is split kSoftWarps ways, and the lists
+// are sized for one strip (32 pixels), not for every thread of the CTA.
+constexpr int kSoftWarps = kSoftThreads / 32;
+
+// byte offsets of soft_backward_kernel's dynamic shared memory (each 16-byte aligned)
 struct SoftLayout {
-    size_t rec, box, L, R, uni, adj, al, zl, Tl, jl, mp, bytes;
+    size_t rec, box, L, R, uni, adj, al, zl, Tl, jl, mp, cnt, pres, bytes;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) / 16 * 16; }
@@ -327,40 +344,27 @@ __host__ __device__ inline SoftLayout soft_layout(int n, bool bwd)
     l.R = align16(l.L + (size_t)n * 4);                // float [n]: bounding radius (depth clamp)
     l.uni = align16(l.R + (size_t)n * 4);              // int [4]: union box
     l.adj = align16(l.uni + 16);                       // int64 [n][kAdj] (backward, fixed point 2^-40)
-    l.al = align16(l.adj + (bwd ? (size_t)n * kAdj * 8 : 0));  // float [n][threads]: alpha
-    l.zl = align16(l.al + (size_t)n * kSoftThreads * 4);       // float [n][threads]: depth
-    l.Tl = align16(l.zl + (size_t)n * kSoftThreads * 4);       // float [n][threads]: transmittance (backward)
-    l.jl = align16(l.Tl + (bwd ? (size_t)n * kSoftThreads * 4 : 0));  // uint8 [n][threads]: primitive (backward)
-    l.mp = align16(l.jl + (bwd ? (size_t)n * kSoftThreads : 0));      // uint8 [n][threads]: entry of a primitive + 1
-    l.bytes = align16(l.mp + (bwd ? (size_t)n * kSoftThreads : 0));
+    l.al = align16(l.adj + (bwd ? (size_t)n * kAdj * 8 : 0));  // float [n][32]: alpha, then d E / d z
+    l.zl = align16(l.al + (size_t)n * 32 * 4);                 // float [n][32]: depth
+    l.Tl = align16(l.zl + (size_t)n * 32 * 4);                 // float [n][32]: transmittance, then d E / d alpha
+    l.jl = align16(l.Tl + (bwd ? (size_t)n * 32 * 4 : 0));     // uint8 [n][32]: primitive of each entry
+    l.mp = align16(l.jl + (size_t)n * 32);                     // uint8 [n][32]: entry of a primitive + 1 (backward)
+    l.cnt = align16(l.mp + (bwd ? (size_t)n * 32 : 0));        // int [32]: entries of each pixel's list
+    l.pres = align16(l.cnt + 32 * 4);                          // uint64: primitives listed by some pixel
+    l.bytes = align16(l.pres + 8);
     return l;
 }
 
-template <bool BWD>
-__global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
+// Set-up shared by the forward and backward kernels: particle p's records
+// into shared memory, each primitive's cone length in pixels, bounding radius
+// (for the depth clamp) and pixel box plus margin, and the union box
+// (s_uni: u0, v0, width, height).  Ends with a CTA barrier.
+__device__ __forceinline__ void soft_setup(const SoftArgs& a, int p, int tid, float4* s_rec, int4* s_box, float* s_L,
+                                           float* s_R, int* s_uni)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n_prims;
-    const int p = blockIdx.y, tid = threadIdx.x;
-    const SoftLayout lay = soft_layout(n, BWD);
-    float4* s_rec = reinterpret_cast<float4*>(smem + lay.rec);
-    int4* s_box = reinterpret_cast<int4*>(smem + lay.box);
-    float* s_L = reinterpret_cast<float*>(smem + lay.L);
-    float* s_R = reinterpret_cast<float*>(smem + lay.R);
-    int* s_uni = reinterpret_cast<int*>(smem + lay.uni);
-    unsigned long long* s_adj = reinterpret_cast<unsigned long long*>(smem + lay.adj);
-    float* s_al = reinterpret_cast<float*>(smem + lay.al);
-    float* s_zl = reinterpret_cast<float*>(smem + lay.zl);
-    float* s_Tl = reinterpret_cast<float*>(smem + lay.Tl);
-    uint8_t* s_jl = smem + lay.jl;
-    uint8_t* s_mp = smem + lay.mp;
-
     const float4* src = a.prims + (size_t)p * n * 4;
     for (int i = tid; i < n * 4; i += kSoftThreads) s_rec[i] = src[i];
-    if (BWD) {
-        for (int i = tid; i < n * kAdj; i += kSoftThreads) s_adj[i] = 0ull;
-        for (int i = tid; i < n * kSoftThreads; i += kSoftThreads) s_mp[i] = 0;
-    }
     __syncthreads();
     if (tid < n) {
         const float4 r0 = s_rec[4 * tid], r1 = s_rec[4 * tid + 1], r2 = s_rec[4 * tid + 2], r3 = s_rec[4 * tid + 3];
@@ -400,11 +404,65 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
         s_uni[3] = v1 >= v0 ? v1 - v0 + 1 : 0;
     }
     __syncthreads();
+}
+
+// A covered pixel's smoothed terms of Eq. 4 (reading R1) from its composited
+// depth zt: t_hit and t_miss (the depth term where the hand is / is not
+// rendered), m (the smoothed r_m test), and the derivatives the backward pass
+// needs: dsmin = d smin / d diff, dm = d m / d diff.
+__device__ __forceinline__ void soft_pixel_terms(float od, bool S, float zt, float d_m, float d_M, float tm,
+                                                 float& t_hit, float& m, float& t_miss, float& dd, float& diff,
+                                                 float& dsmin, float& dm)
+{
+    const bool valid = S && od > 0.f;
+    dd = od - zt;
+    diff = sqrtf(fmaf(dd, dd, tm * tm));
+    dsmin = 0.f;
+    dm = 0.f;
+    if (valid) {
+        const float m0 = fminf(diff, d_M);
+        t_hit = m0 - tm * logf(expf(-(diff - m0) / tm) + expf(-(d_M - m0) / tm));
+        dsmin = sigm((d_M - diff) / tm);
+        m = sigm((d_m - diff) / tm);
+        dm = -m * (1.f - m) / tm;
+        t_miss = d_M;
+    } else {
+        t_hit = S ? 0.f : d_M;
+        m = 1.f;
+        t_miss = 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(kSoftThreads) soft_backward_kernel(const SoftArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = a.n_prims;
+    const int p = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const SoftLayout lay = soft_layout(n, true);
+    float4* s_rec = reinterpret_cast<float4*>(smem + lay.rec);
+    int4* s_box = reinterpret_cast<int4*>(smem + lay.box);
+    float* s_L = reinterpret_cast<float*>(smem + lay.L);
+    float* s_R = reinterpret_cast<float*>(smem + lay.R);
+    int* s_uni = reinterpret_cast<int*>(smem + lay.uni);
+    unsigned long long* s_adj = reinterpret_cast<unsigned long long*>(smem + lay.adj);
+    float* s_al = reinterpret_cast<float*>(smem + lay.al);
+    float* s_zl = reinterpret_cast<float*>(smem + lay.zl);
+    float* s_Tl = reinterpret_cast<float*>(smem + lay.Tl);
+    uint8_t* s_jl = smem + lay.jl;
+    uint8_t* s_mp = smem + lay.mp;
+    int* s_cnt = reinterpret_cast<int*>(smem + lay.cnt);
+    unsigned long long* s_pres = reinterpret_cast<unsigned long long*>(smem + lay.pres);
+
+    for (int i = tid; i < n * kAdj; i += kSoftThreads) s_adj[i] = 0ull;
+    for (int i = tid; i < n * 32; i += kSoftThreads) s_mp[i] = 0;
+    if (tid < 32) s_cnt[tid] = 0;
+    soft_setup(a, p, tid, s_rec, s_box, s_L, s_R, s_uni);
     const int bu0 = s_uni[0], bv0 = s_uni[1], bw = s_uni[2], bh = s_uni[3];
     const int npix = bw * bh;
 
+    // d E_s / d (sum t, sum and, sum or) from the forward pass's sums
     float G_t = 0.f, G_and = 0.f, G_or = 0.f;
-    if (BWD) {
+    {
         const float St = a.sums[3 * p], Sa = a.sums[3 * p + 1], So = a.sums[3 * p + 2];
         if (So > 0.f) {
             const float den = Sa + So;
@@ -413,113 +471,112 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
             G_or = -St / (So * So) + 2.f * a.lambda * Sa / (den * den);
         }
     }
-    long long acc_t = 0, acc_a = 0, acc_o = 0;
     const float tm = a.tau_mm;
-    // The trip count is the same for every thread, so that the backward pass can
-    // reduce each primitive's adjoint across the warp (lanes without a pixel idle).
-    for (int base = blockIdx.x * kSoftThreads; base < npix; base += gridDim.x * kSoftThreads) {
-        const int i = base + tid;
-        uint64_t present = 0ull;  // backward: primitives in this lane's list
-        float ra = 0.f, rb = 0.f;
-        do {
-        if (i >= npix) break;
-        const int v = bv0 + i / bw, u = bu0 + i % bw;
-        ra = fmaf((float)u, a.inv_fx, a.off_x);
-        rb = fmaf((float)v, a.inv_fy, a.off_y);
-        int cnt = 0;
-        for (int j = 0; j < n; ++j) {
+    for (int base = blockIdx.x * 32; base < npix; base += gridDim.x * 32) {
+        // lane l of every warp stands for pixel base + l of the union box
+        const int i = base + lane;
+        const bool pix = i < npix;
+        const int v = pix ? bv0 + i / bw : 0, u = pix ? bu0 + i % bw : 0;
+        const float ra = fmaf((float)u, a.inv_fx, a.off_x);
+        const float rb = fmaf((float)v, a.inv_fy, a.off_y);
+        // A: this warp's primitives at the lane's pixel, appended to its list
+        for (int j = warp; j < n; j += kSoftWarps) {
             const int4 bx = s_box[j];
-            if (u < bx.x || u > bx.z || v < bx.y || v > bx.w) continue;
+            if (!pix || u < bx.x || u > bx.z || v < bx.y || v > bx.w) continue;
             SoftPrimEval e;
-            soft_eval(s_rec[4 * j], s_rec[4 * j + 1], s_rec[4 * j + 2], s_rec[4 * j + 3], s_L[j], s_R[j], ra, rb, a.inv_fx,
-                      a.inv_fy, a.tau, e);
+            soft_eval(s_rec[4 * j], s_rec[4 * j + 1], s_rec[4 * j + 2], s_rec[4 * j + 3], s_L[j], s_R[j], ra, rb,
+                      a.inv_fx, a.inv_fy, a.tau, e);
             if (!(e.alpha > kAlphaMin)) continue;
-            // insert, keeping the list sorted front to back (depth, then primitive index)
-            int k = cnt++;
-            while (k > 0 && s_zl[(k - 1) * kSoftThreads + tid] > e.z) {
-                s_al[k * kSoftThreads + tid] = s_al[(k - 1) * kSoftThreads + tid];
-                s_zl[k * kSoftThreads + tid] = s_zl[(k - 1) * kSoftThreads + tid];
-                if (BWD) s_jl[k * kSoftThreads + tid] = s_jl[(k - 1) * kSoftThreads + tid];
-                --k;
+            const int k = atomicAdd(&s_cnt[lane], 1);
+            s_al[k * 32 + lane] = e.alpha;
+            s_zl[k * 32 + lane] = e.z;
+            s_jl[k * 32 + lane] = (uint8_t)j;
+        }
+        __syncthreads();
+        // B: warp 0 sorts, composites, forms the pixel's terms and pushes dE_s back
+        // through the compositing (lane = pixel)
+        if (warp == 0) {
+            const int cnt = s_cnt[lane];
+            // front to back: depth, then primitive index (insertion sort of a short list)
+            for (int k = 1; k < cnt; ++k) {
+                const float ak = s_al[k * 32 + lane], zk = s_zl[k * 32 + lane];
+                const uint8_t jk = s_jl[k * 32 + lane];
+                int m = k;
+                while (m > 0) {
+                    const float zm = s_zl[(m - 1) * 32 + lane];
+                    const uint8_t jm = s_jl[(m - 1) * 32 + lane];
+                    if (!(zm > zk || (zm == zk && jm > jk))) break;
+                    s_al[m * 32 + lane] = s_al[(m - 1) * 32 + lane];
+                    s_zl[m * 32 + lane] = zm;
+                    s_jl[m * 32 + lane] = jm;
+                    --m;
+                }
+                s_al[m * 32 + lane] = ak;
+                s_zl[m * 32 + lane] = zk;
+                s_jl[m * 32 + lane] = jk;
             }
-            s_al[k * kSoftThreads + tid] = e.alpha;
-            s_zl[k * kSoftThreads + tid] = e.z;
-            if (BWD) s_jl[k * kSoftThreads + tid] = (uint8_t)j;
-        }
-        if (cnt == 0) break;
-        float T = 1.f, Nz = 0.f;
-        for (int k = 0; k < cnt; ++k) {
-            const float al = s_al[k * kSoftThreads + tid];
-            if (BWD) s_Tl[k * kSoftThreads + tid] = T;
-            Nz = fmaf(T * al, s_zl[k * kSoftThreads + tid], Nz);
-            T *= 1.f - al;
-        }
-        const float c = 1.f - T;
-        if (!(c > 0.f)) break;
-        const float zt = Nz / c;
-        const float od = a.depth_f32 ? reinterpret_cast<const float*>(a.depth + (size_t)v * a.depth_pitch)[u]
+            uint64_t present = 0ull;  // primitives in this pixel's list
+            float T = 1.f, Nz = 0.f;
+            for (int k = 0; k < cnt; ++k) {
+                const float al = s_al[k * 32 + lane];
+                s_Tl[k * 32 + lane] = T;
+                Nz = fmaf(T * al, s_zl[k * 32 + lane], Nz);
+                T *= 1.f - al;
+            }
+            const float c = 1.f - T;
+            if (cnt > 0 && c > 0.f) {
+                const float zt = Nz / c;
+                const float od = a.depth_f32
+                                     ? reinterpret_cast<const float*>(a.depth + (size_t)v * a.depth_pitch)[u]
                                      : (float)reinterpret_cast<const uint16_t*>(a.depth + (size_t)v * a.depth_pitch)[u];
-        const bool S = a.skin[(size_t)v * a.skin_pitch + u] != 0;
-        const bool valid = S && od > 0.f;
-        const float dd = od - zt;
-        const float diff = sqrtf(fmaf(dd, dd, tm * tm));
-        float t_hit, m, t_miss, dsmin = 0.f, dm = 0.f;
-        if (valid) {
-            const float m0 = fminf(diff, a.d_M);
-            t_hit = m0 - tm * logf(expf(-(diff - m0) / tm) + expf(-(a.d_M - m0) / tm));
-            dsmin = sigm((a.d_M - diff) / tm);
-            m = sigm((a.d_m - diff) / tm);
-            dm = -m * (1.f - m) / tm;
-            t_miss = a.d_M;
-        } else {
-            t_hit = S ? 0.f : a.d_M;
-            m = 1.f;
-            t_miss = 0.f;
-        }
-        if (!BWD) {
-            // |c (t_hit - t_miss)| <= d_M < 127 and c m <= 1: 32-bit fixed point per pixel
-            acc_t += (long long)__float2int_rn(c * (t_hit - t_miss) * kFix);
-            if (S)
-                acc_a += (long long)__float2int_rn(c * m * kFix);
-            else
-                acc_o += (long long)__float2int_rn(c * m * kFix);
-        } else {
-            // per-entry adjoints of alpha and z through the compositing (back to front);
-            // each entry's (d alpha, d z) replaces its (T, alpha) in place
-            const float gr_ = S ? G_and : G_or;
-            const float gc = G_t * (t_hit - t_miss) + gr_ * m;
-            const float gzt = valid ? (G_t * c * dsmin + gr_ * c * dm) * (-dd / diff) : 0.f;
-            const float gN = gzt / c;
-            const float gct = gc - gzt * zt / c;
-            float Rsuf = 0.f, Psuf = 1.f;
-            for (int k = cnt - 1; k >= 0; --k) {
-                const float al = s_al[k * kSoftThreads + tid], zk = s_zl[k * kSoftThreads + tid];
-                const float Tk = s_Tl[k * kSoftThreads + tid];
-                s_Tl[k * kSoftThreads + tid] = gN * Tk * (zk - Rsuf) + gct * Tk * Psuf;  // d E / d alpha
-                s_al[k * kSoftThreads + tid] = gN * Tk * al;                            // d E / d z
-                const int j = s_jl[k * kSoftThreads + tid];
-                s_mp[j * kSoftThreads + tid] = (uint8_t)(k + 1);
-                present |= 1ull << j;
-                Rsuf = fmaf(al, zk, (1.f - al) * Rsuf);
-                Psuf *= 1.f - al;
+                const bool S = a.skin[(size_t)v * a.skin_pitch + u] != 0;
+                const bool valid = S && od > 0.f;
+                float t_hit, m, t_miss, dd, diff, dsmin, dm;
+                soft_pixel_terms(od, S, zt, a.d_m, a.d_M, tm, t_hit, m, t_miss, dd, diff, dsmin, dm);
+                {
+                    // per-entry adjoints of alpha and z through the compositing (back to front);
+                    // each entry's (d alpha, d z) replaces its (T, alpha) in place
+                    const float gr_ = S ? G_and : G_or;
+                    const float gc = G_t * (t_hit - t_miss) + gr_ * m;
+                    const float gzt = valid ? (G_t * c * dsmin + gr_ * c * dm) * (-dd / diff) : 0.f;
+                    const float gN = gzt / c;
+                    const float gct = gc - gzt * zt / c;
+                    float Rsuf = 0.f, Psuf = 1.f;
+                    for (int k = cnt - 1; k >= 0; --k) {
+                        const float al = s_al[k * 32 + lane], zk = s_zl[k * 32 + lane];
+                        const float Tk = s_Tl[k * 32 + lane];
+                        s_Tl[k * 32 + lane] = gN * Tk * (zk - Rsuf) + gct * Tk * Psuf;  // d E / d alpha
+                        s_al[k * 32 + lane] = gN * Tk * al;                            // d E / d z
+                        const int j = s_jl[k * 32 + lane];
+                        s_mp[j * 32 + lane] = (uint8_t)(k + 1);
+                        present |= 1ull << j;
+                        Rsuf = fmaf(al, zk, (1.f - al) * Rsuf);
+                        Psuf *= 1.f - al;
+                    }
+                }
             }
+            {
+                const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)present);
+                const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(present >> 32));
+                if (lane == 0) *s_pres = ((unsigned long long)hi << 32) | lo;
+            }
+            s_cnt[lane] = 0;  // the list is consumed (the reverse pass finds entries through s_mp)
         }
-        } while (0);
-        if constexpr (BWD) {
-            // one primitive at a time across the warp: lanes that touch it push their
-            // (d alpha, d z) back to its record; the warp sums the 13 adjoints in fixed
-            // point and 13 lanes add them to the CTA's accumulators
-            const int lane = tid & 31;
-            for (int j = 0; j < n; ++j) {
-                const bool mine = (present >> j) & 1ull;
-                if (!__any_sync(0xffffffffu, mine)) continue;
+        __syncthreads();
+        {
+            // C: the warps split the primitives again; the lanes whose pixel lists
+            // primitive j push its (d alpha, d z) back to its record; the warp sums
+            // the 13 adjoints in fixed point and 13 lanes add them to the CTA's
+            const uint64_t pres = *s_pres;
+            for (int j = warp; j < n; j += kSoftWarps) {
+                if (!((pres >> j) & 1ull)) continue;
+                const int k = (int)s_mp[j * 32 + lane] - 1;
                 long long f[kAdj];
 #pragma unroll
                 for (int q = 0; q < kAdj; ++q) f[q] = 0;
-                if (mine) {
-                    const int k = (int)s_mp[j * kSoftThreads + tid] - 1;
-                    s_mp[j * kSoftThreads + tid] = 0;
-                    const float ga = s_Tl[k * kSoftThreads + tid], gz = s_al[k * kSoftThreads + tid];
+                if (k >= 0) {
+                    s_mp[j * 32 + lane] = 0;
+                    const float ga = s_Tl[k * 32 + lane], gz = s_al[k * 32 + lane];
                     const float4 r0 = s_rec[4 * j], r1 = s_rec[4 * j + 1], r2 = s_rec[4 * j + 2], r3 = s_rec[4 * j + 3];
                     SoftPrimEval e;
                     soft_eval(r0, r1, r2, r3, s_L[j], s_R[j], ra, rb, a.inv_fx, a.inv_fy, a.tau, e);
@@ -539,16 +596,106 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
                 for (int q = 0; q < kAdj; ++q)
                     if (lane == q && f[q] != 0) atomicAdd(&s_adj[j * kAdj + q], (unsigned long long)f[q]);
             }
+            __syncthreads();  // the lists are free for the next strip
         }
     }
 
-    if constexpr (BWD) {
-        __syncthreads();
-        unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.adj) + (size_t)p * n * kAdj;
-        for (int i = tid; i < n * kAdj; i += kSoftThreads)
-            if (s_adj[i] != 0ull) atomicAdd(&dst[i], s_adj[i]);
-    } else {
-    // forward: CTA sums, then the particle's last CTA forms E_s
+    __syncthreads();
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.adj) + (size_t)p * n * kAdj;
+    for (int i = tid; i < n * kAdj; i += kSoftThreads)
+        if (s_adj[i] != 0ull) atomicAdd(&dst[i], s_adj[i]);
+}
+
+// The forward pass (E_s and its sums) with every warp on its own: a CTA takes
+// 128-pixel pieces of the particle's union box (k, k + K, ... over the
+// particle's K CTAs), each lane walks its pixel's primitives, keeps its list
+// front to back in shared memory (sorted on insertion: depth, then primitive
+// index, the order soft_backward_kernel sorts in) and composites it.  No CTA
+// barrier per piece: where the box holds many pixels per CTA this is faster
+// than the backward kernel's split of each strip over the warps.
+struct SoftFwdLayout {
+    size_t rec, box, L, R, uni, al, zl, bytes;
+};
+
+__host__ __device__ inline SoftFwdLayout soft_fwd_layout(int n)
+{
+    SoftFwdLayout l;
+    l.rec = 0;                                          // float4 [n][4]
+    l.box = align16(l.rec + (size_t)n * 64);            // int4 [n]: box + margin, clipped
+    l.L = align16(l.box + (size_t)n * 16);              // float [n]: cone length in pixels
+    l.R = align16(l.L + (size_t)n * 4);                 // float [n]: bounding radius (depth clamp)
+    l.uni = align16(l.R + (size_t)n * 4);               // int [4]: union box
+    l.al = align16(l.uni + 16);                         // float [n][threads]: alpha
+    l.zl = align16(l.al + (size_t)n * kSoftThreads * 4);  // float [n][threads]: depth
+    l.bytes = align16(l.zl + (size_t)n * kSoftThreads * 4);
+    return l;
+}
+
+__global__ void __launch_bounds__(kSoftThreads) soft_forward_kernel(const SoftArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = a.n_prims;
+    const int p = blockIdx.y, tid = threadIdx.x;
+    const SoftFwdLayout lay = soft_fwd_layout(n);
+    float4* s_rec = reinterpret_cast<float4*>(smem + lay.rec);
+    int4* s_box = reinterpret_cast<int4*>(smem + lay.box);
+    float* s_L = reinterpret_cast<float*>(smem + lay.L);
+    float* s_R = reinterpret_cast<float*>(smem + lay.R);
+    int* s_uni = reinterpret_cast<int*>(smem + lay.uni);
+    float* s_al = reinterpret_cast<float*>(smem + lay.al);
+    float* s_zl = reinterpret_cast<float*>(smem + lay.zl);
+    soft_setup(a, p, tid, s_rec, s_box, s_L, s_R, s_uni);
+    const int bu0 = s_uni[0], bv0 = s_uni[1], bw = s_uni[2], bh = s_uni[3];
+    const int npix = bw * bh;
+
+    long long acc_t = 0, acc_a = 0, acc_o = 0;
+    const float tm = a.tau_mm;
+    for (int i = blockIdx.x * kSoftThreads + tid; i < npix; i += gridDim.x * kSoftThreads) {
+        const int v = bv0 + i / bw, u = bu0 + i % bw;
+        const float ra = fmaf((float)u, a.inv_fx, a.off_x);
+        const float rb = fmaf((float)v, a.inv_fy, a.off_y);
+        int cnt = 0;
+        for (int j = 0; j < n; ++j) {
+            const int4 bx = s_box[j];
+            if (u < bx.x || u > bx.z || v < bx.y || v > bx.w) continue;
+            SoftPrimEval e;
+            soft_eval(s_rec[4 * j], s_rec[4 * j + 1], s_rec[4 * j + 2], s_rec[4 * j + 3], s_L[j], s_R[j], ra, rb,
+                      a.inv_fx, a.inv_fy, a.tau, e);
+            if (!(e.alpha > kAlphaMin)) continue;
+            // insert, keeping the list sorted front to back (depth, then primitive index)
+            int k = cnt++;
+            while (k > 0 && s_zl[(k - 1) * kSoftThreads + tid] > e.z) {
+                s_al[k * kSoftThreads + tid] = s_al[(k - 1) * kSoftThreads + tid];
+                s_zl[k * kSoftThreads + tid] = s_zl[(k - 1) * kSoftThreads + tid];
+                --k;
+            }
+            s_al[k * kSoftThreads + tid] = e.alpha;
+            s_zl[k * kSoftThreads + tid] = e.z;
+        }
+        if (cnt == 0) continue;
+        float T = 1.f, Nz = 0.f;
+        for (int k = 0; k < cnt; ++k) {
+            const float al = s_al[k * kSoftThreads + tid];
+            Nz = fmaf(T * al, s_zl[k * kSoftThreads + tid], Nz);
+            T *= 1.f - al;
+        }
+        const float c = 1.f - T;
+        if (!(c > 0.f)) continue;
+        const float zt = Nz / c;
+        const float od = a.depth_f32 ? reinterpret_cast<const float*>(a.depth + (size_t)v * a.depth_pitch)[u]
+                                     : (float)reinterpret_cast<const uint16_t*>(a.depth + (size_t)v * a.depth_pitch)[u];
+        const bool S = a.skin[(size_t)v * a.skin_pitch + u] != 0;
+        float t_hit, m, t_miss, dd, diff, dsmin, dm;
+        soft_pixel_terms(od, S, zt, a.d_m, a.d_M, tm, t_hit, m, t_miss, dd, diff, dsmin, dm);
+        // |c (t_hit - t_miss)| <= d_M < 127 and c m <= 1: 32-bit fixed point per pixel
+        acc_t += (long long)__float2int_rn(c * (t_hit - t_miss) * kFix);
+        if (S)
+            acc_a += (long long)__float2int_rn(c * m * kFix);
+        else
+            acc_o += (long long)__float2int_rn(c * m * kFix);
+    }
+
+    // CTA sums, then the particle's last CTA forms E_s
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         acc_t += __shfl_xor_sync(0xffffffffu, acc_t, o);
@@ -591,7 +738,6 @@ __global__ void __launch_bounds__(kSoftThreads) soft_kernel(const SoftArgs a)
         a.sums[3 * p + 2] = So;
     }
     *wk = SoftWork{};
-    }
 }
 
 // ---- pose gradient: record adjoints -> d E_s / d pose ------------------------------
@@ -839,41 +985,46 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ M
 static constexpr int kMaxDevicesSoft = 64;
 static constexpr int kMaxSoftCtas = 64;  // CTAs per particle at most (HsSoftParams.ctas_per_particle's range)
 
-template <bool BWD>
-static cudaError_t launch_soft_impl(const SoftArgs& args, cudaStream_t stream)
+// kern: the forward or the backward kernel; smem(n): its dynamic shared memory
+// for n primitives; opted: its per-device flag of the shared-memory opt-in
+template <class Kernel, class Smem>
+static cudaError_t launch_soft_impl(Kernel kern, Smem smem_of, std::atomic<uint32_t>* opted, const SoftArgs& args,
+                                   cudaStream_t stream)
 {
-    const size_t smem = soft_layout(args.n_prims, BWD).bytes;
-    static std::atomic<uint32_t> opted[kMaxDevicesSoft];
+    const size_t smem = smem_of(args.n_prims);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevicesSoft) return cudaErrorInvalidDevice;
     if (!opted[dev].load(std::memory_order_acquire)) {
-        e = cudaFuncSetAttribute(soft_kernel<BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)soft_layout(kMaxPrims, BWD).bytes);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of(kMaxPrims));
         if (e != cudaSuccess) return e;
         opted[dev].store(1u, std::memory_order_release);
     }
     int K = args.K;
     if (K == 0) {
-        // CTAs per particle: one resident wave of this kernel in all (the backward
-        // pass keeps per-pixel lists in shared memory and fits fewer CTAs per SM;
-        // a grid a little over one wave would take about two waves' time)
+        // CTAs per particle: one resident wave of this kernel in all (a grid a
+        // little over one wave would take about two waves' time); each CTA takes
+        // the particle's 32-pixel strips in a grid-stride loop
         int sms = 0, per_sm = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, soft_kernel<BWD>, kSoftThreads, smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSoftThreads, smem);
         if (e != cudaSuccess) return e;
         K = args.P > 0 ? sms * per_sm / args.P : 1;
         K = K < 1 ? 1 : (K > kMaxSoftCtas ? kMaxSoftCtas : K);
     }
-    soft_kernel<BWD><<<dim3(K, args.P), kSoftThreads, smem, stream>>>(args);
+    kern<<<dim3(K, args.P), kSoftThreads, smem, stream>>>(args);
     return cudaGetLastError();
 }
 
 cudaError_t launch_soft(bool backward, const SoftArgs& args, cudaStream_t stream)
 {
-    return backward ? launch_soft_impl<true>(args, stream) : launch_soft_impl<false>(args, stream);
+    static std::atomic<uint32_t> opted[2][kMaxDevicesSoft];
+    if (backward)
+        return launch_soft_impl(soft_backward_kernel, [](int n) { return soft_layout(n, true).bytes; }, opted[1], args,
+                                stream);
+    return launch_soft_impl(soft_forward_kernel, [](int n) { return soft_fwd_layout(n).bytes; }, opted[0], args,
+                            stream);
 }
 
 cudaError_t launch_pose_grad(const DevModel& model, const GradArgs& args, cudaStream_t stream)

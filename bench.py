@@ -92,11 +92,12 @@ def parse():
     ap.add_argument("--render", default="tune", help="render kernel: tune (timed on the workload first), auto, "
                     "units, tiles32x16, tiles32x32, tiles64x32, tiles64x64")
     ap.add_argument("--ctas", type=int, default=0, help="render CTAs per particle (0 = automatic)")
-    ap.add_argument("--workload", choices=["kinect", "batch", "fullframe", "render"], default="kinect",
+    ap.add_argument("--workload", choices=["kinect", "batch", "fullframe", "render", "equaltime"], default="kinect",
                     help="kinect: one 320x240 sequence (the headline); batch: 64 sequences with uneven ROIs and P; "
                          "fullframe: 640x480 sequence, s/frame to <= 5 deg at several swarm sizes; render: "
                          "render_score_batch alone on one frame (--roi, the first of --particles, --render; for "
-                         "profiling one kernel)")
+                         "profiling one kernel); equaltime: hybrid 64 x 20 + polish against plain PSO given the "
+                         "same time per frame, on the 320x240 sequence")
     ap.add_argument("--particles", default="256,1024,4096", help="fullframe: swarm sizes")
     ap.add_argument("--frames", type=int, default=100, help="fullframe: frames of the sequence")
     ap.add_argument("--gens", default="5,10,20,50", help="fullframe: generation budgets per frame")
@@ -898,6 +899,80 @@ def run_render(args, rank, world, local):
     return 0
 
 
+EQ_METRIC = "share of frames within 5 deg mean joint error at equal time per frame (320x240)"
+
+
+def run_equal_time(args, rank, world, local):
+    """Hybrid PSO (64 particles x 20 generations, every generation 5 descent
+    steps of E_s on the 8 best) against plain PSO given the same wall time per
+    frame, on the Kinect-scale sequence: plain with 64 particles and as many
+    generations as fit, and plain with the swarm size (x 40 generations) whose
+    frame time is nearest.  Every frame is one CUDA graph timed with events."""
+    import torch
+    from paper_2005_07068_b300 import build as B
+    from paper_2005_07068_b300 import handscore as hs
+    from paper_2005_07068_b300 import inputs as I
+    from paper_2005_07068_b300 import replicas as R
+    from paper_2005_07068_b300 import sweep as SW
+    from paper_2005_07068_b300.tracker import HybridTracker, Tracker
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks = measured_peaks()
+    seed = R.replica_seed(I.CONFIG_SEED_BASE + 2, rank)
+    g = I.hand_geometry()
+    lo, hi = (a.astype(np.float32) for a in I.search_limits())
+    model = hs.Model.from_geometry(g, lo, hi)
+    camt = I.kinect_camera(W, H)
+    cam = hs.camera(camt.fx, camt.fy, camt.cx, camt.cy)
+    frames = min(args.frames, FRAMES)
+    traj, obs, _ = make_frames(seed, frames, hs, I, model, cam, dev)
+    rng = np.random.default_rng(seed)
+    start = torch.from_numpy(np.clip(traj[0] + rng.uniform(-1, 1, 26) * I.perturbation_scale(), lo, hi)
+                             .astype(np.float32)).to(dev)
+
+    def run(trk, n=frames):
+        summ = SW.summarize(SW.track_sequence(trk, obs, traj, start, frames=n))
+        summ.update({"particles": trk.P, "generations": trk.gens, "launches_per_frame": trk.launches_per_frame()})
+        return summ
+
+    k_pol, steps_pol = (int(v) for v in args.polish.split(","))
+    with ClockSampler(local) as clk:
+        hyb = run(HybridTracker(model, cam, 64, 20, seed=seed, device=dev, k=k_pol, steps=steps_pol))
+        hyb["method"] = "hybrid"
+        t_h = hyb["frame_ms_mean"]
+        # plain, 64 particles: generations that fill the hybrid's frame time
+        cal = run(Tracker(model, cam, 64, 40, seed=seed, device=dev), n=min(4, frames))
+        g_eq = max(40, int(round(40 * t_h / cal["frame_ms_mean"])))
+        plain_g = run(Tracker(model, cam, 64, g_eq, seed=seed, device=dev))
+        plain_g["method"] = "plain, more generations"
+        # plain, 40 generations: the swarm size whose frame time is nearest
+        best = None
+        for P in (256, 512, 1024, 2048, 4096):
+            c = run(Tracker(model, cam, P, 40, seed=seed, device=dev), n=min(4, frames))
+            if best is None or abs(c["frame_ms_mean"] - t_h) < abs(best[1] - t_h):
+                best = (P, c["frame_ms_mean"])
+        plain_p = run(Tracker(model, cam, best[0], 40, seed=seed, device=dev))
+        plain_p["method"] = "plain, larger swarm"
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2032.0))
+    if rank == 0:
+        rows = [hyb, plain_g, plain_p]
+        print(json.dumps({"metric": EQ_METRIC, "value": hyb["within_fraction"], "unit": "fraction of frames",
+                          "n_gpus": world, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                          "vs_baseline": None,
+                          "config": {"workload": WORKLOAD, "frames": frames, "threshold_deg": 5.0,
+                                     "hybrid": f"64 particles x 20 generations, every generation {steps_pol} descent "
+                                               f"steps of E_s on the {k_pol} best",
+                                     "value_from": "the hybrid's share; the plain rows get the same time per frame",
+                                     "timing": "CUDA events around each frame's graph"},
+                          "settings": rows, "clocks": clocks,
+                          "gpu_launches": sum(r["frames"] * r["launches_per_frame"] for r in rows)}), flush=True)
+    return 0
+
+
 # ---- the native arm ------------------------------------------------------------------------
 
 def main():
@@ -913,6 +988,8 @@ def main():
         return run_fullframe(args, rank, world, local)
     if args.workload == "render":
         return run_render(args, rank, world, local)
+    if args.workload == "equaltime":
+        return run_equal_time(args, rank, world, local)
 
     import torch
     from paper_2005_07068_b300 import build as B

@@ -212,57 +212,82 @@ __device__ __forceinline__ Poly2Col raster_disc_col(const float4& q0, const floa
     return poly2_col(q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, du);
 }
 
-// Nearest hit of the pixel at offsets (du, dv) with one primitive, given its
-// discriminant there, as the depth offset s from the primitive's centre depth
-// t0 (depth = t0 + s), or +inf.  (__fmul_rn: the roots' last products are
-// never fused with a later add, so every kernel rounds them alike.)
-__device__ __forceinline__ float raster_hit(const float4& q2, const float4& q3, const float4& q4, float du, float dv,
-                                            float disc)
+// The ray of the pixel at offsets (du, dv) in the primitive's scaled frame:
+// h = h_c + k and g = t0 k with k = du k_u + dv k_v (the point of the ray at
+// depth t0 + s is g + s h).
+struct RasterRay {
+    float hx, hy, hz, gx, gy, gz;
+};
+__device__ __forceinline__ RasterRay raster_ray(const float4& q2, const float4& q3, const float4& q4, float du,
+                                                float dv)
 {
-    const float t0 = q2.w, kap = q3.w;
+    const float t0 = q2.w;
     const float kx = fmaf(du, q2.x, dv * q3.x), ky = fmaf(du, q2.y, dv * q3.y), kz = fmaf(du, q2.z, dv * q3.z);
-    const float hx = q4.x + kx, hy = q4.y + ky, hz = q4.z + kz;
-    const float gx = t0 * kx, gy = t0 * ky, gz = t0 * kz;
+    return RasterRay{q4.x + kx, q4.y + ky, q4.z + kz, t0 * kx, t0 * ky, t0 * kz};
+}
+
+// Nearest hit with an ellipsoid (|g + s h| = 1) given the discriminant, as the
+// depth offset s from its centre depth t0, or +inf.  (__fmul_rn: the roots'
+// last products are never fused with a later add, so every kernel rounds them
+// alike.)
+__device__ __forceinline__ float raster_root_ellipsoid(float t0, const RasterRay& r, float disc)
+{
     float best = INFINITY;
-    if (kap > 1.5f) {
-        if (disc >= 0.f) {
-            const float A = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-            const float B = fmaf(gx, hx, fmaf(gy, hy, gz * hz));
-            const float sq = sqrt_approx(disc);
-            const float ia = rcp_approx(A);
-            const float sn = __fmul_rn(-B - sq, ia);
-            const float sf = __fmul_rn(-B + sq, ia);  // the camera is inside the ellipsoid: the far root, if in front
-            best = t0 + sn > 0.f ? sn : (t0 + sf > 0.f ? sf : INFINITY);
-        }
-    } else {
-        if (disc >= 0.f) {
-            const float w0 = fmaf(kap, gy, 1.f), w1 = kap * hy;
-            const float A = fmaf(hx, hx, fmaf(hz, hz, -w1 * w1));
-            const float B = fmaf(gx, hx, fmaf(gz, hz, -w0 * w1));
-            const float C = fmaf(gx, gx, fmaf(gz, gz, -w0 * w0));
-            const float sq = sqrt_approx(disc);
-            const float qq = -(B + copysignf(sq, B));
-            const float s1 = __fmul_rn(qq, rcp_approx(A));
-            const float s2 = __fmul_rn(C, rcp_approx(qq));
-            const float y1 = fmaf(s1, hy, gy), y2 = fmaf(s2, hy, gy);
-            if (fabsf(y1) <= 1.f && t0 + s1 > 0.f) best = s1;
-            if (fabsf(y2) <= 1.f && t0 + s2 > 0.f) best = fminf(best, s2);
-        }
-        const uint32_t caps = __float_as_uint(q4.w);
-        if (caps) {  // planar caps at Y = -1 (radius 1 - kappa) and Y = +1 (radius 1 + kappa)
-            const float ihy = rcp_approx(hy);
+    if (disc >= 0.f) {
+        const float A = fmaf(r.hx, r.hx, fmaf(r.hy, r.hy, r.hz * r.hz));
+        const float B = fmaf(r.gx, r.hx, fmaf(r.gy, r.hy, r.gz * r.hz));
+        const float sq = sqrt_approx(disc);
+        const float ia = rcp_approx(A);
+        const float sn = __fmul_rn(-B - sq, ia);
+        const float sf = __fmul_rn(-B + sq, ia);  // the camera is inside the ellipsoid: the far root, if in front
+        best = t0 + sn > 0.f ? sn : (t0 + sf > 0.f ? sf : INFINITY);
+    }
+    return best;
+}
+
+// Nearest hit with a truncated cone (X^2 + Z^2 = (1 + kappa Y)^2, |Y| <= 1, and
+// its planar caps where the bits of caps say they are visible) given the
+// discriminant, as the depth offset s from t0, or +inf.
+__device__ __forceinline__ float raster_root_cone(float t0, float kap, uint32_t caps, const RasterRay& r, float disc)
+{
+    float best = INFINITY;
+    if (disc >= 0.f) {
+        const float w0 = fmaf(kap, r.gy, 1.f), w1 = kap * r.hy;
+        const float A = fmaf(r.hx, r.hx, fmaf(r.hz, r.hz, -w1 * w1));
+        const float B = fmaf(r.gx, r.hx, fmaf(r.gz, r.hz, -w0 * w1));
+        const float C = fmaf(r.gx, r.gx, fmaf(r.gz, r.gz, -w0 * w0));
+        const float sq = sqrt_approx(disc);
+        const float qq = -(B + copysignf(sq, B));
+        const float s1 = __fmul_rn(qq, rcp_approx(A));
+        const float s2 = __fmul_rn(C, rcp_approx(qq));
+        const float y1 = fmaf(s1, r.hy, r.gy), y2 = fmaf(s2, r.hy, r.gy);
+        if (fabsf(y1) <= 1.f && t0 + s1 > 0.f) best = s1;
+        if (fabsf(y2) <= 1.f && t0 + s2 > 0.f) best = fminf(best, s2);
+    }
+    if (caps) {  // planar caps at Y = -1 (radius 1 - kappa) and Y = +1 (radius 1 + kappa)
+        const float ihy = rcp_approx(r.hy);
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                if (!(caps & (1u << c))) continue;
-                const float yc = c ? 1.f : -1.f;
-                const float s = __fmul_rn(yc - gy, ihy);
-                const float X = fmaf(s, hx, gx), Z = fmaf(s, hz, gz);
-                const float w = 1.f + yc * kap;
-                if (fmaf(X, X, Z * Z) <= w * w && t0 + s > 0.f) best = fminf(best, s);
-            }
+        for (int c = 0; c < 2; ++c) {
+            if (!(caps & (1u << c))) continue;
+            const float yc = c ? 1.f : -1.f;
+            const float s = __fmul_rn(yc - r.gy, ihy);
+            const float X = fmaf(s, r.hx, r.gx), Z = fmaf(s, r.hz, r.gz);
+            const float w = 1.f + yc * kap;
+            if (fmaf(X, X, Z * Z) <= w * w && t0 + s > 0.f) best = fminf(best, s);
         }
     }
     return best;
+}
+
+// Nearest hit of the pixel at offsets (du, dv) with one primitive, given its
+// discriminant there, as the depth offset s from the primitive's centre depth
+// t0 (depth = t0 + s), or +inf.
+__device__ __forceinline__ float raster_hit(const float4& q2, const float4& q3, const float4& q4, float du, float dv,
+                                            float disc)
+{
+    const RasterRay r = raster_ray(q2, q3, q4, du, dv);
+    return q3.w > 1.5f ? raster_root_ellipsoid(q2.w, r, disc)
+                       : raster_root_cone(q2.w, q3.w, __float_as_uint(q4.w), r, disc);
 }
 
 // true when the primitive must be tested at a pixel whose discriminant is disc
@@ -272,14 +297,15 @@ __device__ __forceinline__ bool raster_maybe(const float4& q4, float disc)
 }
 
 // per-pixel terms of Eq. 4 (reading R1) as differences to the no-hit baseline,
-// added to the lane's fixed-point / integer sums; returns r_m.  The rendered
-// depth is zt0 + zs, split so that O_d - zt0 is exact (both ~500 mm) and the
-// small part zs is subtracted after.
-__device__ __forceinline__ bool add_pixel(float od, bool S, float zt0, float zs, const RenderArgs& a, long long& at,
-                                          uint32_t& aa, uint32_t& ao, uint32_t& ah)
+// added to the lane's fixed-point / integer sums; returns r_m.  z: the rendered
+// depth, t0 + s rounded once to FP32 (within 2^-24 of it, 3e-5 mm at 500 mm);
+// O_d - z is exact wherever it can fall below d_M (the two are then within a
+// factor of two of each other).
+__device__ __forceinline__ bool add_pixel(float od, bool S, float z, const RenderArgs& a, long long& at, uint32_t& aa,
+                                          uint32_t& ao, uint32_t& ah)
 {
     const bool valid = S && od > 0.f;
-    const float diff = fabsf((od - zt0) - zs);  // O_d - z without rounding at the ~500 mm scale
+    const float diff = fabsf(od - z);
     const bool rm = !valid || diff < a.d_m;
     const float t = valid ? fminf(diff, a.d_M) : (S ? 0.f : a.d_M);
     // |t - d_M| <= d_M < 128 mm, so the 2^-24 mm fixed-point term fits in 32 bits;

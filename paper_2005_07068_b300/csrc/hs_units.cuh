@@ -163,8 +163,8 @@ __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2
         cull_unit(pbox, n_prims, lane, x0, y0, mk);
         const uint64_t any = mk[0] | mk[1];
         const int px0 = x0 + lx, py = y0 + ly;
-        // nearest hit per pixel as (t0, s): depth z = t0 + s
-        float z[kSub] = {INFINITY, INFINITY}, zt[kSub] = {0.f, 0.f}, zs[kSub] = {0.f, 0.f};
+        // nearest depth per pixel
+        float z[kSub] = {INFINITY, INFINITY};
         if (any) {
             const float fpx0 = (float)px0, fpx1 = (float)(px0 + 8), fpy = (float)py;
             // the primitive mask as two 32-bit words; the roots of each half only
@@ -187,24 +187,8 @@ __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2
                     if (v0 | v1) {
                         const float4 q2 = R[2], q3 = R[3], q4 = R[4];
                         const float t0 = q2.w;
-                        if (v0) {
-                            const float sh0 = raster_hit(q2, q3, q4, du0, dv, d0);
-                            const float zz0 = t0 + sh0;
-                            if (zz0 < z[0]) {
-                                z[0] = zz0;
-                                zt[0] = t0;
-                                zs[0] = sh0;
-                            }
-                        }
-                        if (v1) {
-                            const float sh1 = raster_hit(q2, q3, q4, du1, dv, d1);
-                            const float zz1 = t0 + sh1;
-                            if (zz1 < z[1]) {
-                                z[1] = zz1;
-                                zt[1] = t0;
-                                zs[1] = sh1;
-                            }
-                        }
+                        if (v0) z[0] = fminf(z[0], t0 + raster_hit(q2, q3, q4, du0, dv, d0));
+                        if (v1) z[1] = fminf(z[1], t0 + raster_hit(q2, q3, q4, du1, dv, d1));
                     }
                 }
             }
@@ -222,7 +206,7 @@ __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2
                 const int oi = ly * kUW + xr;
                 const float od = depth_f32 ? reinterpret_cast<const float*>(t)[oi]
                                            : (float)reinterpret_cast<const uint16_t*>(t)[oi];
-                const bool rm = add_pixel(od, t[256 + oi] != 0, zt[q], zs[q], a, acc_t, acc_a, acc_o, acc_h);
+                const bool rm = add_pixel(od, t[256 + oi] != 0, z[q], a, acc_t, acc_a, acc_o, acc_h);
                 if (a.dbg_depth) {
                     const size_t o = ((size_t)p * H + py) * W + px;
                     a.dbg_depth[o] = z[q];

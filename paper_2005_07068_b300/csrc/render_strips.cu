@@ -14,9 +14,9 @@
 //    ballots; for each of them every lane forms the du terms of its column's
 //    discriminant polynomial once (Poly2Col), the coverage of all the steps of
 //    the primitive's rows is one straight-line block (two FMAs per step, one
-//    bit each), and raster_hit solves for the roots only in steps where some
-//    lane can be hit -- the same arithmetic as the unit kernel, so the nearest
-//    hit is bit-identical to its (lower primitive index on equal depth);
+//    sign bit each), and raster_hit solves for the roots only in steps where
+//    some lane can be hit -- the same arithmetic as the unit kernel, so the
+//    nearest depth is bit-identical to its;
 //  * the strip's observation (16-pixel-wide 2-D TMA boxes, one per 4-row
 //    band, the skin needs 16-byte rows) is loaded into one of the warp's two
 //    shared-memory buffers while the previous strip renders;
@@ -61,10 +61,9 @@ __device__ __forceinline__ uint64_t cull_strip(const int2* pbox, int n_prims, in
     return m;
 }
 
-// resident CTAs per SM the register budget is set for: the 32-row strips keep
-// twice the per-pixel state of the 16-row ones in registers
+// resident CTAs per SM the register budget is set for (80 registers a thread)
 template <int SH>
-constexpr int strip_min_ctas() { return SH > 16 ? 5 : 6; }
+constexpr int strip_min_ctas() { return 6; }
 
 // The CTA's copy of particle p's raster records and pixel boxes, and p's
 // screen box clipped to the ROI (sm.box: xa, v0, u1, v1; u1 < 0 when nothing
@@ -154,15 +153,10 @@ __device__ __forceinline__ bool render_strips_warp(StripShared<SH>& sm, const Re
         const int sy = q / nsx, sx = q - sy * nsx;
         const int x0 = xa + kStripW * sx, y0 = by0 + SH * sy;
         const int y1 = min(y0 + SH - 1, by1);
-        // per pixel of the lane: nearest depth z = t0 + zs, the offset zs from
-        // the primitive's centre depth t0, and that t0
-        float z[kSteps], zt[kSteps], zs[kSteps];
+        // per pixel of the lane: the nearest depth so far
+        float z[kSteps];
 #pragma unroll
-        for (int s = 0; s < kSteps; ++s) {
-            z[s] = INFINITY;
-            zt[s] = 0.f;
-            zs[s] = 0.f;
-        }
+        for (int s = 0; s < kSteps; ++s) z[s] = INFINITY;
         const float fx = (float)(x0 + lx), fy0 = (float)(y0 + ly);
         uint64_t mask = cull_strip(sm.pbox, n_prims, lane, x0, y0, y1);
         while (mask) {  // warp-uniform walk over the strip's primitives, in index order
@@ -177,18 +171,19 @@ __device__ __forceinline__ bool render_strips_warp(StripShared<SH>& sm, const Re
             const bool caps = __float_as_uint(R[4].w) != 0u;
             const Poly2Col PD = raster_disc_col(q0, q1, du);
             // coverage of every step of the primitive's rows at once
-            // (independent polynomials, one bit each, no branch per step)
-            uint32_t m = 0u;
+            // (independent polynomials, one sign bit each, no branch per step;
+            // the polynomial is never -0, so a clear sign bit is disc >= 0, and
+            // a NaN only costs roots that return +inf)
+            uint32_t neg = 0u;
 #pragma unroll
             for (int s = 0; s < kSteps; ++s) {
                 const float dv = (fy0 + (float)(4 * s)) - q0.y;
-                m |= (uint32_t)(PD.at(dv) >= 0.f || caps) << s;
+                neg |= (__float_as_uint(PD.at(dv)) >> 31) << s;
             }
-            m &= (2u << s1) - (1u << s0);  // the steps of the primitive's rows
+            const uint32_t m = (caps ? ~0u : ~neg) & ((2u << s1) - (1u << s0));  // within the primitive's rows
             const uint32_t wm = __reduce_or_sync(0xffffffffu, m);  // steps some lane can hit
             if (!wm) continue;
-            // the roots, where some lane of the step can be hit; the nearest hit
-            // per pixel (strict <: the lower primitive index wins equal depths)
+            // the roots, where some lane of the step can be hit; the nearest hit per pixel
             const float4 q2 = R[2], q3 = R[3], q4 = R[4];
             const float t0 = q2.w;
 #pragma unroll
@@ -196,12 +191,7 @@ __device__ __forceinline__ bool render_strips_warp(StripShared<SH>& sm, const Re
                 if (!((wm >> s) & 1u)) continue;  // no lane can be hit in this step (warp-uniform)
                 const float dv = (fy0 + (float)(4 * s)) - q0.y;
                 const float sh = raster_hit(q2, q3, q4, du, dv, PD.at(dv));
-                const float zz = t0 + sh;
-                if (((m >> s) & 1u) && zz < z[s]) {
-                    z[s] = zz;
-                    zt[s] = t0;
-                    zs[s] = sh;
-                }
+                z[s] = fminf(z[s], ((m >> s) & 1u) ? t0 + sh : INFINITY);
             }
         }
         ok = mbar_wait_bounded(&bar[buf], (phases >> buf) & 1u, a.status);
@@ -219,7 +209,7 @@ __device__ __forceinline__ bool render_strips_warp(StripShared<SH>& sm, const Re
                     const int oi = ly * 16 + c;
                     const float od = depth_f32 ? reinterpret_cast<const float*>(t)[oi]
                                                : (float)reinterpret_cast<const uint16_t*>(t)[oi];
-                    const bool rm = add_pixel(od, t[256 + oi] != 0, zt[s], zs[s], a, acc_t, acc_a, acc_o, acc_h);
+                    const bool rm = add_pixel(od, t[256 + oi] != 0, z[s], a, acc_t, acc_a, acc_o, acc_h);
                     if (a.dbg_depth) {
                         const size_t o = ((size_t)p * H + py) * W + px;
                         a.dbg_depth[o] = z[s];

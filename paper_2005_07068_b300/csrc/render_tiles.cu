@@ -13,11 +13,9 @@
 //    pixel of one primitive per step (pixel-exact culling, the primitive's
 //    raster record held in registers while its chunks last): the discriminant
 //    polynomial decides coverage, the roots are solved only on a hit;
-//  * hits go to a z-buffer in shared memory as 64-bit keys with atomicMin: the
-//    depth z = t0 + s rounded to float in the high word (nearest surface wins),
-//    and in the low word the exact rounding residual dz = s - (z - t0), so
-//    that O_d - (t0 + s) = (O_d - z) - dz keeps the precision of the
-//    centre-relative form at ~500 mm without knowing which primitive won;
+//  * hits go to a z-buffer in shared memory with atomicMin on the bits of the
+//    depth z = t0 + s (positive floats order as their bit patterns, so the
+//    nearest surface wins whatever the order of the updates);
 //  * meanwhile the tile's observation (depth + skin) arrives by TMA; a second
 //    pass visits the tile's rendered pixels and adds their Eq. 4 terms to
 //    integer sums;
@@ -28,7 +26,7 @@
 
 namespace hs {
 
-constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr uint32_t kEmptyKey = 0x7f800000u;  // +inf: no hit
 constexpr int kMaxDevices = 64;
 
 // byte offsets of the dynamic shared memory of a TW x TH tile
@@ -37,8 +35,8 @@ struct TileLayout {
     static constexpr int kBoxes = (TW / 16) * (TH / 4);  // 16 x 4 TMA boxes per tile
     static constexpr int kRast = 0;                       // float4 [kMaxPrims][kRastVec]: raster records
     static constexpr int kPBox = kRast + kMaxPrims * 16 * kRastVec;  // int2 [kMaxPrims]: packed pixel boxes
-    static constexpr int kZ = kPBox + kMaxPrims * 8;      // u64 [TH][TW]
-    static constexpr int kDepth = kZ + TW * TH * 8;       // box b at b * 256 (16 x 4 x <= 4 bytes)
+    static constexpr int kZ = kPBox + kMaxPrims * 8;      // u32 [TH][TW]: depth bits
+    static constexpr int kDepth = kZ + TW * TH * 4;       // box b at b * 256 (16 x 4 x <= 4 bytes)
     static constexpr int kSkin = kDepth + kBoxes * 256;   // box b at b * 128 (16 x 4 bytes)
     static constexpr int kRect = kSkin + kBoxes * 128;    // int4 [kMaxPrims]: x0, y0, w, pixels
     static constexpr int kMagic = kRect + kMaxPrims * 16; // u32 [kMaxPrims]: ~2^31 / w, rounded up
@@ -62,7 +60,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
     extern __shared__ __align__(128) unsigned char smem[];
     float4* s_rast = reinterpret_cast<float4*>(smem + Lay::kRast);
     int2* s_pbox = reinterpret_cast<int2*>(smem + Lay::kPBox);
-    unsigned long long* s_z = reinterpret_cast<unsigned long long*>(smem + Lay::kZ);
+    uint32_t* s_z = reinterpret_cast<uint32_t*>(smem + Lay::kZ);
     unsigned char* s_depth = smem + Lay::kDepth;
     unsigned char* s_skin = smem + Lay::kSkin;
     int4* s_rect = reinterpret_cast<int4*>(smem + Lay::kRect);
@@ -198,8 +196,8 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
             }
         }
         const int rows = cy1 - ty0 + 1;  // rows of the tile inside the particle's box
-        for (int i = tid; i < TW * rows / 2; i += NW * 32)
-            reinterpret_cast<ulonglong2*>(s_z)[i] = make_ulonglong2(kEmptyKey, kEmptyKey);
+        for (int i = tid; i < TW * rows / 4; i += NW * 32)
+            reinterpret_cast<uint4*>(s_z)[i] = make_uint4(kEmptyKey, kEmptyKey, kEmptyKey, kEmptyKey);
         __syncthreads();
 
         // raster: chunk c of the tile's list goes to warp c mod NW
@@ -223,11 +221,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
                     const float disc = raster_disc(q0, q1, du, dv);
                     const float sh = raster_maybe(q4, disc) ? raster_hit(q2, q3, q4, du, dv, disc) : INFINITY;
                     const float zz = t0 + sh;
-                    if (zz < INFINITY) {
-                        const float dz = sh - (zz - t0);  // z - t0 is exact (Sterbenz): dz is the residual
-                        atomicMin(&s_z[(py - ty0) * TW + (px - tx0)],
-                                  ((unsigned long long)__float_as_uint(zz) << 32) | __float_as_uint(dz));
-                    }
+                    if (zz < INFINITY) atomicMin(&s_z[(py - ty0) * TW + (px - tx0)], __float_as_uint(zz));
                 }
             }
         }
@@ -238,14 +232,14 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
 
         // cost: every rendered pixel of the tile against the observation
         for (int i = tid; i < TW * rows; i += NW * 32) {
-            const unsigned long long key = s_z[i];
+            const uint32_t key = s_z[i];
             if (key == kEmptyKey) continue;
-            const float z = __uint_as_float((uint32_t)(key >> 32)), dz = __uint_as_float((uint32_t)key);
+            const float z = __uint_as_float(key);
             const int ly = i / TW, lx = i % TW;
             const int b = (ly >> 2) * (TW / 16) + (lx >> 4), oi = ((ly & 3) << 4) | (lx & 15);
             const float od = pv.depth_f32 ? reinterpret_cast<const float*>(s_depth + b * 256)[oi]
                                           : (float)reinterpret_cast<const uint16_t*>(s_depth + b * 256)[oi];
-            const bool rm = add_pixel(od, s_skin[b * 128 + oi] != 0, z, dz, a, acc_t, acc_a, acc_o, acc_h);
+            const bool rm = add_pixel(od, s_skin[b * 128 + oi] != 0, z, a, acc_t, acc_a, acc_o, acc_h);
             if (a.dbg_depth) {
                 const size_t o = ((size_t)p * pv.H + ty0 + ly) * pv.W + tx0 + lx;
                 a.dbg_depth[o] = z;

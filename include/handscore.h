@@ -48,7 +48,7 @@ typedef struct CUstream_st* hs_stream_t;
 /* ---- device status bits (hs_get_device_status) ------------------------- */
 #define HS_DEV_NONFINITE_POSE 0x1u /* pose_fk met a NaN/inf pose; that particle's E is NaN */
 #define HS_DEV_TMA_TIMEOUT    0x2u /* an observation tile load did not arrive in time */
-#define HS_DEV_BARRIER_TIMEOUT 0x4u /* track_frame: a grid barrier wait ran out (the frame's results are void) */
+#define HS_DEV_BARRIER_TIMEOUT 0x4u /* track_frame(_multi): a wait for other CTAs ran out (the frame's results are void) */
 
 /* ---- limits -------------------------------------------------------------- */
 #define HS_NDOF            26
@@ -468,6 +468,51 @@ int pso_init_multi(const HsModel* model, const HsBatch* batch, const HsSwarm* sw
 int pso_step_fk_multi(const HsModel* model, const HsBatch* batch, const HsSwarm* swarm, float* x_next,
                       const HsPsoParams* params, uint32_t frame, uint32_t gen, HsPrim* prims, float* kc,
                       hs_stream_t stream);
+
+/* A whole frame of every swarm of the batch (Section III.B's per-frame loop,
+ * Section IV's parallelism between particles, across sequences) as one
+ * cooperative launch, after the observation totals (hs_obs_prepare_multi's
+ * two launches, issued here first).  The resident CTAs take tasks from a
+ * counter, generation by generation, each generation's particles largest ROI
+ * first: a task is one particle's initialisation (generation 1) or step of the
+ * previous generation, then its FK, render and E.  A particle's step waits
+ * only until every particle of its own swarm has been scored at the previous
+ * generation (a per-swarm count, awaited with a time limit), so the swarms
+ * run generations apart and no CTA waits at a grid barrier.
+ *
+ * Results are exactly those of the step-by-step batch calls
+ *     hs_obs_prepare_multi; pso_init_multi(seed_poses, scale, frame);
+ *     pose_fk_multi(x); for g = 1..gens: render_score_multi (any variant);
+ *     pso_step_fk_multi(gen = g) with swarm->x and x_next alternating
+ * bit for bit, whatever `ctas`: E (written through the const pointer: it must
+ * be a writable device array), pbest, pbest_E, gbest, gbest_E, v, the
+ * positions (step g writes buffer g & 1 of {swarm->x, x_next}), and prims /
+ * kc [P_total] (the records and kc of the final positions).  seed_poses:
+ * device [S][26]; scale: host [26].
+ *
+ * ctas: CTAs of the grid, 1..hs_frame_multi_capacity(); 0 picks the capacity.
+ * workspace: hs_frame_multi_workspace_size(batch) bytes (a 128-byte control
+ * block, a count per swarm from byte 128 on, then two generations of E), zeroed
+ * once before first use (every call leaves the control block and the counts
+ * zeroed; the E part needs no initial value).  Calls that share a workspace must not
+ * overlap on the GPU.  If a wait runs out (about a second) or an observation
+ * load does not arrive, every CTA stops taking tasks, HS_DEV_BARRIER_TIMEOUT
+ * (or HS_DEV_TMA_TIMEOUT) is set and the swarms' contents are void; the next
+ * call runs normally.  The workspace's fourth 32-bit word is read as a number
+ * of renders every wait expects beyond its swarm's own: leave it zero (a test
+ * sets it to make the wait run out).  The stopping rule (params->e_stop) is
+ * the step-by-step calls' only: e_stop must be 0 here.
+ * Errors: HS_ERR_ARG (NULL, x_next == swarm->x, bad constants, e_stop != 0,
+ * gens < 0, ctas < 0), HS_ERR_ALIGN, HS_ERR_SIZE (a swarm over
+ * HS_FRAME_MAX_PARTICLES particles, ctas over capacity, workspace too small),
+ * HS_ERR_CUDA. */
+int hs_frame_multi_workspace_size(const HsBatch* batch, size_t* bytes);
+/* CTAs of track_frame_multi that the current device keeps resident at once */
+int hs_frame_multi_capacity(int* ctas);
+int track_frame_multi(const HsModel* model, const HsBatch* batch, const HsSwarm* swarm, float* x_next, int gens,
+                      const HsScoreParams* score, const HsPsoParams* pso, const float* seed_poses,
+                      const float* scale, uint32_t frame, int ctas, void* workspace, size_t workspace_bytes,
+                      HsPrim* prims, float* kc, hs_stream_t stream);
 
 /* ---- the smoothed objective E_s and its gradient (gradient polish) ---------------
  * E (Eq. 4-5) is piecewise constant in the pose at every silhouette and depth

@@ -1051,6 +1051,86 @@ int pso_step_fk_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw,
     return launch_pso_step_fk(model->dev, a, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 
+// ---- a whole frame of every swarm of a batch in one cooperative launch ----------------
+
+static size_t frame_multi_done_bytes(int S) { return ((size_t)S * 4 + 127) / 128 * 128; }
+
+int hs_frame_multi_workspace_size(const HsBatch* b, size_t* bytes)
+{
+    if (!b || !bytes) return HS_ERR_ARG;
+    *bytes = sizeof(FrameMultiCtl) + frame_multi_done_bytes(b->S) + 2 * (size_t)b->P_total * sizeof(float);
+    return HS_OK;
+}
+
+int hs_frame_multi_capacity(int* ctas)
+{
+    if (!ctas) return HS_ERR_ARG;
+    return track_frame_multi_capacity(ctas) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+int track_frame_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw, float* x_next, int gens,
+                      const HsScoreParams* score, const HsPsoParams* prm, const float* seed_poses,
+                      const float* scale, uint32_t frame, int ctas, void* workspace, size_t workspace_bytes,
+                      HsPrim* prims, float* kc, hs_stream_t stream)
+{
+    if (!model || !b || !sw || !x_next || !score || !prm || !seed_poses || !scale || !prims || !kc)
+        return HS_ERR_ARG;
+    if (!sw->x || !sw->v || !sw->pbest || !sw->pbest_E || !sw->gbest || !sw->gbest_E || !sw->E) return HS_ERR_ARG;
+    if (x_next == sw->x || gens < 0 || ctas < 0) return HS_ERR_ARG;
+    int rc = validate_score_params(score);
+    if (rc) return rc;
+    const double psi = (double)prm->c1 + (double)prm->c2;
+    if (!std::isfinite(psi) || prm->c1 < 0.f || prm->c2 < 0.f || psi <= 4.0) return HS_ERR_ARG;
+    if (prm->e_stop != 0.f) return HS_ERR_ARG;  // the stopping rule is the step-by-step batch calls'
+    if (b->P_max > HS_FRAME_MAX_PARTICLES) return HS_ERR_SIZE;
+    if (!workspace) return HS_ERR_ARG;
+    if (!aligned16(prims) || !aligned16(workspace)) return HS_ERR_ALIGN;
+    size_t need = 0;
+    hs_frame_multi_workspace_size(b, &need);
+    if (workspace_bytes < need) return HS_ERR_SIZE;
+    FrameMultiArgs a = {};
+    for (int d = 0; d < HS_NDOF; ++d) {
+        if (!std::isfinite(scale[d]) || scale[d] < 0.f) return HS_ERR_ARG;
+        a.scale[d] = scale[d];
+    }
+    int cap = 0;
+    if (track_frame_multi_capacity(&cap) != cudaSuccess) return HS_ERR_CUDA;
+    const int nb = ctas ? ctas : cap;
+    if (nb < 1 || nb > cap) return HS_ERR_SIZE;
+    a.batch = b->dev;
+    a.order = b->order;
+    a.d_m = score->d_m;
+    a.d_M = score->d_M;
+    a.lambda = score->lambda;
+    a.lambda_k = score->lambda_k;
+    a.xbuf[0] = sw->x;
+    a.xbuf[1] = x_next;
+    a.v = sw->v;
+    a.pbest = sw->pbest;
+    a.pbest_E = sw->pbest_E;
+    a.gbest = sw->gbest;
+    a.gbest_E = sw->gbest_E;
+    a.E = const_cast<float*>(sw->E);
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    a.ctl = reinterpret_cast<FrameMultiCtl*>(ws);
+    a.done = reinterpret_cast<uint32_t*>(ws + sizeof(FrameMultiCtl));
+    a.Ebuf = reinterpret_cast<float*>(ws + sizeof(FrameMultiCtl) + frame_multi_done_bytes(b->S));
+    a.prims_out = reinterpret_cast<float4*>(prims);
+    a.kc = kc;
+    a.seed_poses = seed_poses;
+    a.c1 = prm->c1;
+    a.c2 = prm->c2;
+    a.w = (float)(2.0 / std::fabs(2.0 - psi - std::sqrt(psi * psi - 4.0 * psi)));
+    a.mutate_every = prm->mutate_every;
+    a.frame = frame;
+    a.gens = gens;
+    a.P_max = b->P_max;
+    if ((rc = status_ptr(&a.status))) return rc;
+    // the frame's observation totals (as hs_obs_prepare_multi), then the frame
+    if ((rc = hs_obs_prepare_multi(b, stream))) return rc;
+    return launch_track_frame_multi(model->dev, a, nb, (cudaStream_t)stream) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
 // ---- render autotuning -------------------------------------------------------------
 
 }  // extern "C"

@@ -40,26 +40,28 @@ constexpr unsigned long long kBarrierWaitNs = 1000000000ull;  // a grid barrier 
 constexpr uint32_t kBarrierPolls = 1u << 26;  // and at most this many polls, should the clock not advance
 
 
-struct FrameShared {
+template <int NW>  // warps of the CTA
+struct FrameSharedT {
     FkShared fk;                      // model, pose, bone frames
     CollideShared col;                // the kc variants' collision data
     float4 rec[kMaxPrims * 4];        // this particle's FK records
     float4 rast[kMaxPrims * kRastVec];  // their raster records
     int2 pbox[kMaxPrims];
-    alignas(128) unsigned char tile[kFrameWarps][kStages][kSlot];
-    uint64_t bar[kFrameWarps][kStages];
+    alignas(128) unsigned char tile[NW][kStages][kSlot];
+    uint64_t bar[NW][kStages];
     float x[kNdof], v[kNdof], pb[kNdof];  // the particle's state (identical in all its CTAs)
     float pe;                             // its personal-best E
     float kc;
     float r[4 * kPairBlocks], m[4 * kMutBlocks];
-    long long red_t[kFrameWarps];
-    uint32_t red_c[kFrameWarps][3];
-    float red_v[kFrameWarps];
-    int red_i[kFrameWarps], red_r[kFrameWarps];
+    long long red_t[NW];
+    uint32_t red_c[NW][3];
+    float red_v[NW];
+    int red_i[NW], red_r[NW];
     int gprev;  // the swarm's global best after the previous generation
     uint32_t st[2];
     int4 wbox[2];  // union of the pixel boxes of primitives 0..31 and 32..63
 };
+using FrameShared = FrameSharedT<kFrameWarps>;
 
 // all threads of every CTA: returns false if the wait ran out.  work() runs
 // on every thread after this CTA has arrived, while the others are awaited
@@ -331,6 +333,240 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
     }
 }
 
+// ---- every swarm of a batch: a whole frame in one cooperative launch ----
+//
+// The frame of S sequences at once (uneven ROIs and swarm sizes, Section IV's
+// parallelism between particles): the work is a list of tasks, generation by
+// generation, each generation's particles in the batch's order (largest ROI
+// first).  A resident CTA takes the next task from a counter and does, for
+// particle q (number i of swarm s) at generation g:
+//
+//  * g == 1: the tracking initialisation of q (as pso_init_multi);
+//    g >= 2: once every particle of s has been rendered at generation g - 1
+//    (a per-swarm count of finished renders, awaited with a time limit),
+//    q's step of generation g - 1 (swarm_update: the global best and the
+//    mutation rank from the swarm's E and pbest_E, then Eq. 6-7), as
+//    pso_step_fk_multi does;
+//  * g <= gens: FK of q's new pose, its raster records, the render of all its
+//    16x4 units by the CTA's warps (the unit renderer, hs_units.cuh), and E
+//    (form_E from the CTA's integer sums) into the generation's E buffer;
+//    then the swarm's count goes up (release);
+//  * g == gens + 1: q's final E, and the records and kc of its final pose.
+//
+// A task waits only for tasks of an earlier generation, and those were taken
+// earlier by CTAs that are resident (the launch is cooperative), so the
+// earliest unfinished task never waits: the frame always ends.  Swarms run
+// generations apart from one another, so no CTA idles at a grid barrier.
+// Every piece of arithmetic is the code of the step-by-step batch calls, so
+// the results equal theirs bit for bit.  If a wait runs out (about a second),
+// HS_DEV_BARRIER_TIMEOUT is set and every CTA stops taking tasks; the last CTA
+// to leave returns the workspace's counters to zero.
+// warps of a task's CTA: four, so that six CTAs share an SM and the latency of
+// one task's serial phases (FK, the swarm scan) hides behind the others'
+constexpr int kMultiWarps = 4;
+constexpr int kMultiThreads = kMultiWarps * 32;
+
+__global__ void __launch_bounds__(kMultiThreads, 24 / kMultiWarps)
+    track_frame_multi_kernel(const __grid_constant__ DevModel model, const FrameMultiArgs a)
+{
+    __shared__ FrameSharedT<kMultiWarps> sh;
+    __shared__ int s_task, s_go;
+    extern __shared__ float s_dyn[];  // E [P_max], then pbest_E [P_max] of the task's swarm
+    float* s_e = s_dyn;
+    float* s_pe = s_dyn + a.P_max;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int n_prims = model.n_prims;
+    const int P_total = a.batch.P_total, G = a.gens;
+    const uint32_t total = (uint32_t)(G + 1) * (uint32_t)P_total;
+    FrameMultiCtl* ctl = a.ctl;
+    const uint32_t missing = ctl->missing;  // zero but in the test of the wait's time limit
+
+    fk_load_model(sh.fk, model);
+    const CollideShared* col = collide_load(sh.col, model);
+    if (lane < kStages) mbar_init(&sh.bar[warp][lane], 1);
+    if (t == 0) mbar_fence_init();
+    __syncthreads();
+
+    RenderArgs ra = {};
+    ra.d_m = a.d_m;
+    ra.d_M = a.d_M;
+    ra.status = a.status;
+    uint32_t phases = 0u;
+    for (;;) {
+        if (t == 0) {
+            const uint32_t k = atomicAdd(&ctl->next, 1u);
+            s_task = k < total && *reinterpret_cast<volatile uint32_t*>(&ctl->abort) == 0u ? (int)k : -1;
+        }
+        __syncthreads();  // also: the previous task's shared state is no longer read
+        const int k = s_task;
+        if (k < 0) break;
+        const int g = k / P_total + 1;
+        const int q = a.order[k - (g - 1) * P_total];
+        const int s = a.batch.sid[q];
+        const SwarmView& view = a.batch.views[s];
+        const int off = view.offset, P = view.P, i = q - off;
+        const uint32_t k0 = view.key0, k1 = view.key1;
+        const float4 cam = make_float4(view.fx, view.fy, view.cx, view.cy);
+
+        if (g == 1) {
+            // the tracking initialisation of q (as pso_init_multi)
+            if (t < kNdof) {
+                const float xv = init_position(i, t, a.seed_poses[(size_t)s * kNdof + t], a.scale[t],
+                                               sh.fk.model.lo[t], sh.fk.model.hi[t], a.frame, k0, k1);
+                sh.x[t] = xv;
+                const size_t o = (size_t)q * kNdof + t;
+                a.xbuf[0][o] = xv;
+                a.v[o] = 0.f;
+                a.pbest[o] = xv;
+                if (i == 0) a.gbest[(size_t)s * kNdof + t] = xv;
+            }
+            if (t == 0) {
+                a.pbest_E[q] = INFINITY;
+                if (i == 0) {
+                    a.gbest_E[s] = INFINITY;
+                    set_swarm_stop_gen(a.batch, s, 0u);  // the swarm runs this frame
+                }
+            }
+        } else {
+            // every particle of s rendered at generation g - 1 (acquire: their
+            // E, positions and bests are visible)
+            if (t == 0) {
+                const uint32_t target = (uint32_t)(g - 1) * (uint32_t)P + missing;
+                int go = 1;
+                uint32_t polls = 0;
+                const unsigned long long t0 = global_ns();
+                for (;;) {
+                    uint32_t v;
+                    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(a.done + s) : "memory");
+                    if (v >= target) break;
+                    if (*reinterpret_cast<volatile uint32_t*>(&ctl->abort) != 0u) {
+                        go = 0;
+                        break;
+                    }
+                    if (global_ns() - t0 > kBarrierWaitNs || ++polls >= kBarrierPolls) {
+                        set_status(a.status, HS_DEV_BARRIER_TIMEOUT);
+                        atomicExch(&ctl->abort, 1u);
+                        go = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                s_go = go;
+            }
+            draw_step_randoms(i, (uint32_t)(g - 1), a.frame, k0, k1, sh.r, sh.m, t);
+            __syncthreads();
+            if (!s_go) break;
+            // q's step of generation g - 1 (as pso_step_fk_multi); loads through
+            // L2: other CTAs wrote these during this launch
+            const float* Eg = a.Ebuf + (size_t)((g - 1) & 1) * P_total;
+            float xi = 0.f, pbi = 0.f, vi = 0.f;
+            const float* x_cur = a.xbuf[(g - 2) & 1];
+            if (t < kNdof) {
+                xi = __ldcg(x_cur + (size_t)q * kNdof + t);
+                pbi = __ldcg(a.pbest + (size_t)q * kNdof + t);
+                vi = __ldcg(a.v + (size_t)q * kNdof + t);
+            }
+            for (int j = t; j < P; j += kMultiThreads) {
+                s_e[j] = __ldcg(Eg + off + j);
+                s_pe[j] = __ldcg(a.pbest_E + off + j);
+            }
+            __syncthreads();
+            SwarmRefs R{x_cur, a.xbuf[(g - 1) & 1], a.v, a.pbest, a.pbest_E, a.gbest, a.gbest_E, a.c1, a.c2, a.w,
+                        a.mutate_every > 0 && (g - 1) % a.mutate_every == 0};
+            const StepOut o = swarm_update<kMultiThreads>(R, q, i, off, P, s, view.n_mutate, s_e, s_pe, sh.r, sh.m,
+                                                          sh.fk.model.lo, sh.fk.model.hi, xi, pbi, vi, s_pe[i],
+                                                          true, sh.red_v, sh.red_i, sh.red_r);
+            if (t < kNdof) sh.x[t] = o.xn;
+            if (g > G) {  // after the last generation: q's E, and the records and kc of its final pose
+                if (t == 0) a.E[q] = s_e[i];
+                fk_particle(sh.fk, col, sh.x, cam, a.prims_out + (size_t)q * n_prims * 4, a.kc + q, a.status);
+                continue;
+            }
+        }
+        if (g > G) {  // no generation at all: the records and kc of the initial pose
+            fk_particle(sh.fk, col, sh.x, cam, a.prims_out + (size_t)q * n_prims * 4, a.kc + q, a.status);
+            continue;
+        }
+
+        // generation g: FK of q's pose (fk_particle starts with a barrier that
+        // publishes sh.x), raster records, the render of all q's units
+        const ParticleView pv{view.W, view.H, view.depth_f32, view.inv_fx, view.off_x, view.inv_fy, view.off_y,
+                              view.stats, &view.tm_depth, &view.tm_skin};
+        fk_particle(sh.fk, col, sh.x, cam, sh.rec, &sh.kc, a.status, [&](int j, const float* rec) {
+            const float4 r4[4] = {make_float4(rec[0], rec[1], rec[2], rec[3]),
+                                  make_float4(rec[4], rec[5], rec[6], rec[7]),
+                                  make_float4(rec[8], rec[9], rec[10], rec[11]),
+                                  make_float4(rec[12], rec[13], rec[14], rec[15])};
+            store_raster(make_raster(r4, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y), sh.rast + kRastVec * j);
+            sh.pbox[j] = make_int2(__float_as_int(rec[14]), __float_as_int(rec[15]));
+            const int w = j >> 5;
+            const uint32_t mask = n_prims >= 32 * (w + 1) ? 0xffffffffu : (1u << (n_prims - 32 * w)) - 1u;
+            const int u0 = __reduce_min_sync(mask, lo_i16(rec[14])), v0 = __reduce_min_sync(mask, hi_i16(rec[14]));
+            const int u1 = __reduce_max_sync(mask, lo_i16(rec[15])), v1 = __reduce_max_sync(mask, hi_i16(rec[15]));
+            if ((j & 31) == 0) sh.wbox[w] = make_int4(u0, v0, u1, v1);
+        });
+        __syncthreads();
+        int box[4];
+        {
+            int4 b = sh.wbox[0];
+            if (n_prims > 32) {
+                const int4 b1 = sh.wbox[1];
+                b = make_int4(min(b.x, b1.x), min(b.y, b1.y), max(b.z, b1.z), max(b.w, b1.w));
+            }
+            unit_box_clip(b.x, b.y, b.z, b.w, view.W, view.H, box);
+        }
+        long long acc_t = 0;
+        uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
+        bool ok = true;
+        if (box[3] > 0)
+            ok = render_units_warp(sh.rast, sh.pbox, n_prims, box, sh.tile[warp], sh.bar[warp], phases, warp,
+                                   kMultiWarps, pv, ra, q, lane, acc_t, acc_a, acc_o, acc_h);
+        warp_sum(acc_t, acc_a, acc_o, acc_h);
+        if (lane == 0) {
+            sh.red_t[warp] = acc_t;
+            sh.red_c[warp][0] = acc_a;
+            sh.red_c[warp][1] = acc_o;
+            sh.red_c[warp][2] = acc_h;
+        }
+        // a warp whose observation wait ran out (status flagged) voids the frame
+        if (!__syncthreads_and(ok)) {
+            if (t == 0) atomicExch(&ctl->abort, 1u);
+            break;
+        }
+        if (t == 0) {
+            for (int w = 1; w < kMultiWarps; ++w) {
+                acc_t += sh.red_t[w];
+                acc_a += sh.red_c[w][0];
+                acc_o += sh.red_c[w][1];
+            }
+            float t_sum;
+            uint32_t so;
+            a.Ebuf[(size_t)(g & 1) * P_total + q] =
+                form_E(acc_t, acc_a, acc_o, view.stats, a.d_M, a.lambda, a.lambda_k, sh.kc, t_sum, so);
+            // release: this task's E and q's step (stored by the CTA's threads
+            // before the barriers above) are visible to whoever sees the count
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.done + s) : "memory");
+        }
+    }
+    // leave; the last CTA returns the workspace to zero
+    __syncthreads();
+    __shared__ uint32_t s_last;
+    if (t == 0) {
+        uint32_t d;
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(d) : "l"(&ctl->exited) : "memory");
+        s_last = d == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        for (int j = t; j < a.batch.S; j += kMultiThreads) a.done[j] = 0u;
+        if (t == 0) {
+            ctl->next = 0u;
+            ctl->exited = 0u;
+            ctl->abort = 0u;
+        }
+    }
+}
+
 // the dynamic shared memory of the largest swarm (2 P floats) on top of the
 // static part passes the default 48 KB: opt in once per device
 static std::atomic<uint32_t> g_frame_opted[64];
@@ -369,6 +605,46 @@ cudaError_t launch_track_frame(const DevModel& model, const CUtensorMap& tm_dept
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, track_frame_kernel, model, tm_depth, tm_skin, args);
+}
+
+
+// the batch frame: the same static part, dynamic shared memory for the
+// largest swarm of the batch (2 P_max floats)
+static std::atomic<uint32_t> g_frame_multi_opted[64];
+static cudaError_t frame_multi_smem_opt_in()
+{
+    return opt_in_dynamic_smem(track_frame_multi_kernel, 2 * HS_FRAME_MAX_PARTICLES * (int)sizeof(float),
+                               g_frame_multi_opted);
+}
+
+cudaError_t track_frame_multi_capacity(int* ctas)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = frame_multi_smem_opt_in();
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_frame_multi_kernel, kMultiThreads,
+                                                          2 * HS_FRAME_MAX_PARTICLES * sizeof(float));
+    *ctas = e == cudaSuccess ? sms * per_sm : 0;
+    return e;
+}
+
+cudaError_t launch_track_frame_multi(const DevModel& model, const FrameMultiArgs& args, int ctas, cudaStream_t stream)
+{
+    const cudaError_t e = frame_multi_smem_opt_in();
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(kMultiThreads);
+    cfg.dynamicSmemBytes = 2 * (size_t)args.P_max * sizeof(float);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident at once (tasks wait on other CTAs' tasks)
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, track_frame_multi_kernel, model, args);
 }
 
 }  // namespace hs

@@ -176,6 +176,38 @@ struct FrameArgs {
     uint32_t* status;
 };
 
+// ---- every swarm of a batch, a whole frame in one cooperative launch (frame.cu) ----
+// control block at the start of the batch-frame workspace (128 bytes, zero between calls)
+struct FrameMultiCtl {
+    uint32_t next;     // the next task to be taken
+    uint32_t exited;   // CTAs that have finished
+    uint32_t abort;    // set when a wait ran out: no CTA takes another task
+    uint32_t missing;  // renders every wait expects beyond its swarm's own: zero, except to test the wait's time
+                       // limit (the wait then runs out); the kernel only reads it
+    uint32_t pad[28];
+};
+static_assert(sizeof(FrameMultiCtl) == 128, "128-byte control block");
+
+struct FrameMultiArgs {
+    BatchDev batch;
+    const int32_t* order;                // [P_total] the particles of a generation in task order
+    float d_m, d_M, lambda, lambda_k;
+    float* xbuf[2];                      // positions: step g reads xbuf[(g - 1) & 1], writes xbuf[g & 1]
+    float *v, *pbest, *pbest_E, *gbest, *gbest_E, *E;
+    float* Ebuf;                         // [2][P_total]: E of generation g at Ebuf[(g & 1) P_total + q]
+    uint32_t* done;                      // [S] renders finished per swarm in this launch
+    float4* prims_out;                   // [P_total][n_prims][4] records of the final positions
+    float* kc;                           // [P_total] kc of the final positions
+    const float* seed_poses;             // [S][26]
+    float scale[kNdof];                  // initial spread per dimension
+    float c1, c2, w;
+    int mutate_every;
+    uint32_t frame;
+    int gens, P_max;
+    FrameMultiCtl* ctl;
+    uint32_t* status;
+};
+
 // ---- the smoothed objective and its gradient (soft.cu) ----
 constexpr int kAdj = HS_SOFT_ADJ;  // per-primitive adjoint: record M (9), C (3), cone length L (1)
 
@@ -235,6 +267,8 @@ cudaError_t launch_pso_step_fk(const DevModel& model, const PsoFkArgs& args, cud
 cudaError_t launch_track_frame(const DevModel& model, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,
                                const FrameArgs& args, int ctas, cudaStream_t stream);
 cudaError_t track_frame_capacity(int* ctas);  // co-resident CTAs of track_frame_kernel on the current device
+cudaError_t launch_track_frame_multi(const DevModel& model, const FrameMultiArgs& args, int ctas, cudaStream_t stream);
+cudaError_t track_frame_multi_capacity(int* ctas);  // co-resident CTAs of track_frame_multi_kernel
 cudaError_t launch_render_score(const CUtensorMap& tm_depth, const CUtensorMap& tm_skin, const RenderArgs& args,
                                 cudaStream_t stream);
 cudaError_t launch_render_tiles(int variant, const CUtensorMap& tm_depth, const CUtensorMap& tm_skin,

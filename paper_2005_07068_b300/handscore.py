@@ -155,6 +155,11 @@ _SIGS = {
                      ctypes.c_int, ctypes.POINTER(HsScoreParams), ctypes.POINTER(HsPsoParams), _vp,
                      ctypes.POINTER(ctypes.c_float), ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, _vp,
                      ctypes.c_size_t, _vp, _vp, _vp], ctypes.c_int),
+    "hs_frame_multi_workspace_size": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "hs_frame_multi_capacity": ([ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "track_frame_multi": ([_vp, _vp, ctypes.POINTER(HsSwarm), _vp, ctypes.c_int, ctypes.POINTER(HsScoreParams),
+                           ctypes.POINTER(HsPsoParams), _vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32,
+                           ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp, _vp], ctypes.c_int),
 }
 NOALLOC_SCRATCH_BYTES = 256 * 1024
 MAX_PARTICLES = 65535
@@ -595,6 +600,37 @@ def batch_swarm(batch: Batch, device="cuda") -> Swarm:
     Pt, S = batch.P_total, batch.S
     return Swarm(torch.zeros(Pt, NDOF, **f), torch.zeros(Pt, NDOF, **f), torch.zeros(Pt, NDOF, **f),
                  torch.zeros(Pt, **f), torch.zeros(S, NDOF, **f), torch.zeros(S, **f), torch.zeros(Pt, **f))
+
+
+def new_frame_multi_workspace(batch: Batch, device="cuda") -> torch.Tensor:
+    """Zeroed workspace of track_frame_multi for a batch: a control block and a
+    count per swarm, which every call leaves zeroed, then two generations of E."""
+    n = ctypes.c_size_t()
+    _check("hs_frame_multi_workspace_size", lib().hs_frame_multi_workspace_size(batch.handle, ctypes.byref(n)))
+    return torch.zeros((n.value + 15) // 16 * 4, dtype=torch.int32, device=device)
+
+
+def frame_multi_capacity() -> int:
+    """CTAs of track_frame_multi the current device keeps resident at once."""
+    n = ctypes.c_int()
+    _check("hs_frame_multi_capacity", lib().hs_frame_multi_capacity(ctypes.byref(n)))
+    return n.value
+
+
+def track_frame_multi(model: Model, batch: Batch, sw: Swarm, x_next: torch.Tensor, gens: int, score: HsScoreParams,
+                      pso: HsPsoParams, seed_poses: torch.Tensor, scale, frame: int, ctas: int, ws: torch.Tensor,
+                      prims: torch.Tensor, kc: torch.Tensor, stream=None) -> None:
+    """A whole frame of every swarm of the batch (obs totals, init around
+    seed_poses [S, 26], gens x (score, step)) in one cooperative launch of
+    `ctas` CTAs (0: the capacity) taking per-particle tasks; identical to the
+    step-by-step batch calls.  Step g writes positions to (sw.x, x_next)[g & 1]."""
+    st = sw.struct()
+    sc = (ctypes.c_float * NDOF)(*[float(v) for v in np.asarray(scale, np.float32)])
+    _check("track_frame_multi",
+           lib().track_frame_multi(model.handle, batch.handle, ctypes.byref(st), _ptr(x_next), gens,
+                                   ctypes.byref(score), ctypes.byref(pso), _ptr(seed_poses), sc, frame, ctas,
+                                   _ptr(ws), ws.numel() * ws.element_size(), _ptr(prims), _ptr(kc),
+                                   _stream(stream)))
 
 
 TUNE_CTAS = (0, 1, 2, 4, 8, 16, 32)  # 0: the automatic choice

@@ -387,3 +387,35 @@ class BatchTracker:
 
     def evals_per_frame(self) -> int:
         return self.batch.P_total * self.gens
+
+
+class BatchFrameTracker(BatchTracker):
+    """BatchTracker with each frame of every sequence in ONE cooperative launch
+    (track_frame_multi, after the two observation passes): the resident CTAs
+    take per-particle tasks (a particle's step, FK, render and E) generation by
+    generation, each swarm advancing as soon as all its particles are scored,
+    with no grid barrier.  Bit for bit the same swarms as BatchTracker.  ctas =
+    0 uses every CTA the device keeps resident."""
+
+    def __init__(self, model: hs.Model, batch: hs.Batch, gens: int = 40, *, ctas: int = 0, **kw):
+        super().__init__(model, batch, gens, **kw)
+        if max(batch.P) > hs.FRAME_MAX_PARTICLES:
+            raise ValueError(f"track_frame_multi takes at most {hs.FRAME_MAX_PARTICLES} particles per swarm")
+        self.ctas = ctas
+        self.fws = hs.new_frame_multi_workspace(batch, self.device)
+
+    def enqueue_frame(self, frame: int, seed_poses: torch.Tensor | None = None) -> None:
+        src = self.swarm.gbest if seed_poses is None else seed_poses
+        self.seed_poses.copy_(src)
+        x0, x1 = self.x_buf
+        self.swarm.x = x0
+        hs.track_frame_multi(self.model, self.batch, self.swarm, x1, self.gens, self.score, self.pso,
+                             self.seed_poses, self.scale, frame, self.ctas, self.fws, self.prims, self.kc)
+        self.swarm.x = self.x_buf[self.gens & 1]
+
+    def run_frame(self, frame: int, seed_poses: torch.Tensor | None = None, graph: bool = True) -> None:
+        self.enqueue_frame(frame, seed_poses)
+
+    def launches_per_frame(self) -> int:
+        """The two observation passes and the frame."""
+        return 3

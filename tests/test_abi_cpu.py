@@ -295,6 +295,13 @@ def test_batch_host_checks():
     assert L.pose_fk_multi(m.handle, None, FAKE, FAKE, FAKE, None) == hs.HS_ERR_ARG
     assert L.hs_obs_prepare_multi(None, None) == hs.HS_ERR_ARG
     assert L.hs_batch_destroy(None) == hs.HS_ERR_ARG
+    # the batch frame: no batch, no workspace size, no frame
+    assert L.hs_frame_multi_workspace_size(None, ctypes.byref(n)) == hs.HS_ERR_ARG
+    sw = hs.HsSwarm(FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
+    scale = (ctypes.c_float * 26)(*([1.0] * 26))
+    pp = hs.pso_params()
+    assert L.track_frame_multi(m.handle, None, ctypes.byref(sw), FAKE + 4096, 40, ctypes.byref(prm), ctypes.byref(pp),
+                               FAKE, scale, 0, 0, FAKE, 1 << 20, FAKE, FAKE, None) == hs.HS_ERR_ARG
 
 
 @pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU behaviour")

@@ -519,6 +519,44 @@ def batch_throughput(hs, bset, frames, steps, warmup, dev):
             "step": "one frame of every sequence: one frame copy + one CUDA graph; L2 flushed between steps"}
 
 
+def batch_frame_throughput(hs, bset, frames, steps, warmup, dev):
+    """The same tracking with each frame of every sequence in one cooperative
+    launch (track_frame_multi, after the two observation passes), bit for bit
+    the graph path's swarms; timed like batch_throughput."""
+    import torch
+    from paper_2005_07068_b300.tracker import BatchFrameTracker
+    sizes, Ps, store, staging, batch, trk, gt0, _ = bset
+    ft = BatchFrameTracker(trk.model, batch, trk.gens, score=trk.score)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        f = i % frames
+        staging.dev.copy_(store[f].dev)
+        ft.run_frame(f, gt0 if f == 0 else None)
+
+    for i in range(warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step(warmup + i)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = [a.elapsed_time(b) for a, b in evs]
+    out = {"value": steps * ft.evals_per_frame() / (sum(ms) * 1e-3), "unit": "evals/s",
+           "ms_per_frame": sum(ms) / steps, "latency_ms": {"p50": percentile(ms, 50), "p99": percentile(ms, 99)},
+           "steps": steps, "warmup": warmup, "gpu_launches_per_step": ft.launches_per_frame(),
+           "ctas": hs.frame_multi_capacity(),
+           "kernel": "track_frame_multi: one cooperative launch per frame of every sequence (per-particle tasks)",
+           "step": "one frame of every sequence: one frame copy + the observation passes + one launch; "
+                   "L2 flushed between steps"}
+    del ft
+    return out
+
+
 def run_batch(args, rank, world, local):
     import torch
     from paper_2005_07068_b300 import build as B
@@ -584,6 +622,10 @@ def run_batch(args, rank, world, local):
                               "clocks": clocks, "gpu_launches": K * trk.launches_per_frame()}), flush=True)
         return 0
 
+    # the same frames with each frame in one cooperative launch
+    frame_path = batch_frame_throughput(hs, (sizes, Ps, store, staging, batch, trk, gt0, tune), frames, K,
+                                        args.warmup, dev)
+
     # roofline: the render launches of one frame replayed back to back
     Pt = batch.P_total
     roofline = batch_render_roofline(hs, model, sizes, Ps, store, staging, batch, trk, gt0, g.prims_i[:, 1],
@@ -637,7 +679,7 @@ def run_batch(args, rank, world, local):
                 "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99),
                                "what": "per-frame latency of every sequence (one step advances all of them)"},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
-                "gpu_launches": K * trk.launches_per_frame()}
+                "gpu_launches": K * trk.launches_per_frame(), "frame_path": frame_path}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -1139,9 +1181,11 @@ def main():
             bseed = R.replica_seed(I.CONFIG_SEED_BASE + 4, rank)
             bset = batch_setup(hs, I, model, bseed, 2, dev, args.render, args.ctas)
             thr = batch_throughput(hs, bset, 2, 8, 3, dev)
+            thr_f = batch_frame_throughput(hs, bset, 2, 8, 3, dev)
             sub["batch_64seq"] = batch_render_roofline(hs, model, *bset[:7], kinds, pk, dev)
             sub["batch_64seq"]["autotune_us"] = bset[7]
             sub["batch_64seq"]["tracking"] = thr
+            sub["batch_64seq"]["tracking_frame_kernel"] = thr_f
             del bset
             torch.cuda.empty_cache()
             fseed = R.replica_seed(I.CONFIG_SEED_BASE + 5, rank)

@@ -615,11 +615,14 @@ def run_batch(args, rank, world, local):
 
     clocks = clk.summary(peaks.get("sm_max_mhz", 2032.0))
     if args.profile or args.no_roofline:
+        # the short form also runs two frames through the batch frame kernel
+        fp = batch_frame_throughput(hs, (sizes, Ps, store, staging, batch, trk, gt0, tune), frames, 1, 1, dev)
         if rank == 0:
             print(json.dumps({"metric": BATCH_METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
                               "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / K,
                               "higher_is_better": True, "note": "short run (--profile / --no-roofline)",
-                              "clocks": clocks, "gpu_launches": K * trk.launches_per_frame()}), flush=True)
+                              "clocks": clocks, "gpu_launches": K * trk.launches_per_frame(),
+                              "frame_path": fp}), flush=True)
         return 0
 
     # the same frames with each frame in one cooperative launch

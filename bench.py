@@ -129,7 +129,7 @@ KERNEL_SOURCES = {
     "strips": ["render_strips.cu", "hs_units.cuh", "hs_render.cuh", "hs_args.cuh", "hs_device.cuh"],
 }
 PROFILE_FILES = {("kinect", "units"): "render_units_kinect_320x240.txt",
-                 ("batch", "tiles"): "render_tiles32x32_batch_64seq.txt",
+                 ("batch", "tiles"): "render_tiles64x32_batch_64seq.txt",
                  ("kinect", "frame"): "track_frame_kinect_320x240.txt",
                  ("fullframe640x480P4096", "strips"): "render_strips8x32_fullframe_640x480.txt"}
 

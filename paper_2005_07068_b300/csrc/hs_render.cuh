@@ -290,6 +290,86 @@ __device__ __forceinline__ float raster_hit(const float4& q2, const float4& q3, 
                        : raster_root_cone(q2.w, q3.w, __float_as_uint(q4.w), r, disc);
 }
 
+// ---- two pixels at once with packed FP32 (fma / add / mul .f32x2) ----
+// Each function below is its single-pixel namesake's operations applied to
+// two pixels at once, lane by lane (the packed operations round every
+// component exactly as the scalar ones), so both give the same bits.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+struct Ray2 {
+    float2 hx, hy, hz, gx, gy, gz;
+};
+// raster_ray for the pixels (du.x, dv.x) and (du.y, dv.y)
+__device__ __forceinline__ Ray2 raster_ray2(const float4& q2, const float4& q3, const float4& q4, float2 du2,
+                                            float2 dv)
+{
+    const float2 t02 = f2(q2.w);
+    const float2 kx = __ffma2_rn(du2, f2(q2.x), __fmul2_rn(dv, f2(q3.x)));
+    const float2 ky = __ffma2_rn(du2, f2(q2.y), __fmul2_rn(dv, f2(q3.y)));
+    const float2 kz = __ffma2_rn(du2, f2(q2.z), __fmul2_rn(dv, f2(q3.z)));
+    return Ray2{__fadd2_rn(f2(q4.x), kx), __fadd2_rn(f2(q4.y), ky), __fadd2_rn(f2(q4.z), kz),
+                __fmul2_rn(t02, kx), __fmul2_rn(t02, ky), __fmul2_rn(t02, kz)};
+}
+// raster_root_ellipsoid for both pixels
+__device__ __forceinline__ float2 raster_root_ellipsoid2(float t0, const Ray2& r, float2 disc)
+{
+    const float2 A = __ffma2_rn(r.hx, r.hx, __ffma2_rn(r.hy, r.hy, __fmul2_rn(r.hz, r.hz)));
+    const float2 B = __ffma2_rn(r.gx, r.hx, __ffma2_rn(r.gy, r.hy, __fmul2_rn(r.gz, r.hz)));
+    const float2 sq = make_float2(sqrt_approx(disc.x), sqrt_approx(disc.y));
+    const float2 ia = make_float2(rcp_approx(A.x), rcp_approx(A.y));
+    const float2 nB = neg2(B);
+    const float2 sn = __fmul2_rn(__fadd2_rn(nB, neg2(sq)), ia);
+    const float2 sf = __fmul2_rn(__fadd2_rn(nB, sq), ia);
+    const float2 tn = __fadd2_rn(f2(t0), sn), tf = __fadd2_rn(f2(t0), sf);
+    float2 best;
+    best.x = disc.x >= 0.f ? (tn.x > 0.f ? sn.x : (tf.x > 0.f ? sf.x : INFINITY)) : INFINITY;
+    best.y = disc.y >= 0.f ? (tn.y > 0.f ? sn.y : (tf.y > 0.f ? sf.y : INFINITY)) : INFINITY;
+    return best;
+}
+// raster_root_cone for both pixels
+__device__ __forceinline__ float2 raster_root_cone2(float t0, float kap, uint32_t caps, const Ray2& r, float2 disc)
+{
+    const float2 t02 = f2(t0), kap2 = f2(kap);
+    const float2 w0 = __ffma2_rn(kap2, r.gy, f2(1.f)), w1 = __fmul2_rn(kap2, r.hy);
+    const float2 nw0 = neg2(w0), nw1 = neg2(w1);
+    const float2 A = __ffma2_rn(r.hx, r.hx, __ffma2_rn(r.hz, r.hz, __fmul2_rn(nw1, w1)));
+    const float2 B = __ffma2_rn(r.gx, r.hx, __ffma2_rn(r.gz, r.hz, __fmul2_rn(nw0, w1)));
+    const float2 C = __ffma2_rn(r.gx, r.gx, __ffma2_rn(r.gz, r.gz, __fmul2_rn(nw0, w0)));
+    const float2 sq = make_float2(sqrt_approx(disc.x), sqrt_approx(disc.y));
+    const float2 qq = neg2(__fadd2_rn(B, make_float2(copysignf(sq.x, B.x), copysignf(sq.y, B.y))));
+    const float2 s1 = __fmul2_rn(qq, make_float2(rcp_approx(A.x), rcp_approx(A.y)));
+    const float2 s2 = __fmul2_rn(C, make_float2(rcp_approx(qq.x), rcp_approx(qq.y)));
+    const float2 y1 = __ffma2_rn(s1, r.hy, r.gy), y2 = __ffma2_rn(s2, r.hy, r.gy);
+    const float2 u1 = __fadd2_rn(t02, s1), u2 = __fadd2_rn(t02, s2);
+    float2 best = make_float2(INFINITY, INFINITY);
+    if (disc.x >= 0.f) {
+        if (fabsf(y1.x) <= 1.f && u1.x > 0.f) best.x = s1.x;
+        if (fabsf(y2.x) <= 1.f && u2.x > 0.f) best.x = fminf(best.x, s2.x);
+    }
+    if (disc.y >= 0.f) {
+        if (fabsf(y1.y) <= 1.f && u1.y > 0.f) best.y = s1.y;
+        if (fabsf(y2.y) <= 1.f && u2.y > 0.f) best.y = fminf(best.y, s2.y);
+    }
+    if (caps) {
+        const float2 ihy = make_float2(rcp_approx(r.hy.x), rcp_approx(r.hy.y));
+        const float2 ngy = neg2(r.gy);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (!(caps & (1u << c))) continue;
+            const float yc = c ? 1.f : -1.f;
+            const float2 s = __fmul2_rn(__fadd2_rn(f2(yc), ngy), ihy);
+            const float2 X = __ffma2_rn(s, r.hx, r.gx), Z = __ffma2_rn(s, r.hz, r.gz);
+            const float2 rr = __ffma2_rn(X, X, __fmul2_rn(Z, Z));
+            const float w = 1.f + yc * kap;
+            const float ww = w * w;
+            const float2 u = __fadd2_rn(t02, s);
+            if (rr.x <= ww && u.x > 0.f) best.x = fminf(best.x, s.x);
+            if (rr.y <= ww && u.y > 0.f) best.y = fminf(best.y, s.y);
+        }
+    }
+    return best;
+}
+
 // true when the primitive must be tested at a pixel whose discriminant is disc
 __device__ __forceinline__ bool raster_maybe(const float4& q4, float disc)
 {

@@ -185,10 +185,17 @@ __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2
                     const uint32_t v0 = __ballot_sync(0xffffffffu, in0 && (d0 >= 0.f || caps));
                     const uint32_t v1 = __ballot_sync(0xffffffffu, in1 && (d1 >= 0.f || caps));
                     if (v0 | v1) {
+                        // the roots of both halves' pixels at once (packed FP32), kept
+                        // where some lane of the half can be hit
                         const float4 q2 = R[2], q3 = R[3], q4 = R[4];
                         const float t0 = q2.w;
-                        if (v0) z[0] = fminf(z[0], t0 + raster_hit(q2, q3, q4, du0, dv, d0));
-                        if (v1) z[1] = fminf(z[1], t0 + raster_hit(q2, q3, q4, du1, dv, d1));
+                        const Ray2 r = raster_ray2(q2, q3, q4, make_float2(du0, du1), f2(dv));
+                        const float2 disc = make_float2(d0, d1);
+                        const float2 sh = q3.w > 1.5f ? raster_root_ellipsoid2(t0, r, disc)
+                                                      : raster_root_cone2(t0, q3.w, __float_as_uint(q4.w), r, disc);
+                        const float2 zz = __fadd2_rn(f2(t0), sh);
+                        if (v0) z[0] = fminf(z[0], zz.x);
+                        if (v1) z[1] = fminf(z[1], zz.y);
                     }
                 }
             }

@@ -14,8 +14,9 @@
 //    ballots; for each of them every lane forms the du terms of its column's
 //    discriminant polynomial once (Poly2Col), the coverage of all the steps of
 //    the primitive's rows is one straight-line block (two FMAs per step, one
-//    sign bit each), and raster_hit solves for the roots only in steps where
-//    some lane can be hit -- the same arithmetic as the unit kernel, so the
+//    sign bit each; two steps per packed FP32 instruction), and the roots are
+//    solved two steps at a time (raster_root_*2) where some lane of either
+//    step can be hit -- the unit kernel's arithmetic lane by lane, so the
 //    nearest depth is bit-identical to its;
 //  * the strip's observation (16-pixel-wide 2-D TMA boxes, one per 4-row
 //    band, the skin needs 16-byte rows) is loaded into one of the warp's two
@@ -174,24 +175,45 @@ __device__ __forceinline__ bool render_strips_warp(StripShared<SH>& sm, const Re
             // (independent polynomials, one sign bit each, no branch per step;
             // the polynomial is never -0, so a clear sign bit is disc >= 0, and
             // a NaN only costs roots that return +inf)
+            // (two steps per packed FP32 instruction)
+            const float2 nqy = f2(-q0.y), vv2 = f2(PD.vv), u12 = f2(PD.u1), u02 = f2(PD.u0);
             uint32_t neg = 0u;
 #pragma unroll
-            for (int s = 0; s < kSteps; ++s) {
-                const float dv = (fy0 + (float)(4 * s)) - q0.y;
-                neg |= (__float_as_uint(PD.at(dv)) >> 31) << s;
+            for (int s = 0; s < kSteps; s += 2) {
+                const float2 dv = __fadd2_rn(make_float2(fy0 + (float)(4 * s), fy0 + (float)(4 * s + 4)), nqy);
+                const float2 d = __ffma2_rn(dv, __ffma2_rn(dv, vv2, u12), u02);  // PD.at of both steps
+                neg |= ((__float_as_uint(d.x) >> 31) << s) | ((__float_as_uint(d.y) >> 31) << (s + 1));
             }
             const uint32_t m = (caps ? ~0u : ~neg) & ((2u << s1) - (1u << s0));  // within the primitive's rows
             const uint32_t wm = __reduce_or_sync(0xffffffffu, m);  // steps some lane can hit
             if (!wm) continue;
-            // the roots, where some lane of the step can be hit; the nearest hit per pixel
+            // the roots, two steps at a time (packed FP32) where some lane of either
+            // step can be hit; the nearest depth per pixel
             const float4 q2 = R[2], q3 = R[3], q4 = R[4];
             const float t0 = q2.w;
+            auto take2 = [&](int s, float2 sh) {
+                const float2 zz = __fadd2_rn(f2(t0), sh);
+                z[s] = fminf(z[s], ((m >> s) & 1u) ? zz.x : INFINITY);
+                z[s + 1] = fminf(z[s + 1], ((m >> (s + 1)) & 1u) ? zz.y : INFINITY);
+            };
+            if (q3.w > 1.5f) {  // ellipsoid (warp-uniform)
 #pragma unroll
-            for (int s = 0; s < kSteps; ++s) {
-                if (!((wm >> s) & 1u)) continue;  // no lane can be hit in this step (warp-uniform)
-                const float dv = (fy0 + (float)(4 * s)) - q0.y;
-                const float sh = raster_hit(q2, q3, q4, du, dv, PD.at(dv));
-                z[s] = fminf(z[s], ((m >> s) & 1u) ? t0 + sh : INFINITY);
+                for (int s = 0; s < kSteps; s += 2) {
+                    if (!((wm >> s) & 3u)) continue;  // no lane can be hit in either step (warp-uniform)
+                    const float2 dv = __fadd2_rn(make_float2(fy0 + (float)(4 * s), fy0 + (float)(4 * s + 4)), nqy);
+                    const float2 disc = __ffma2_rn(dv, __ffma2_rn(dv, vv2, u12), u02);
+                    take2(s, raster_root_ellipsoid2(t0, raster_ray2(q2, q3, q4, f2(du), dv), disc));
+                }
+            } else {
+                const float kap = q3.w;
+                const uint32_t capw = __float_as_uint(q4.w);
+#pragma unroll
+                for (int s = 0; s < kSteps; s += 2) {
+                    if (!((wm >> s) & 3u)) continue;
+                    const float2 dv = __fadd2_rn(make_float2(fy0 + (float)(4 * s), fy0 + (float)(4 * s + 4)), nqy);
+                    const float2 disc = __ffma2_rn(dv, __ffma2_rn(dv, vv2, u12), u02);
+                    take2(s, raster_root_cone2(t0, kap, capw, raster_ray2(q2, q3, q4, f2(du), dv), disc));
+                }
             }
         }
         ok = mbar_wait_bounded(&bar[buf], (phases >> buf) & 1u, a.status);

@@ -299,6 +299,12 @@ __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y
 struct Ray2 {
     float2 hx, hy, hz, gx, gy, gz;
 };
+// raster_disc for the pixels (du.x, dv.x) and (du.y, dv.y)
+__device__ __forceinline__ float2 raster_disc2(const float4& q0, const float4& q1, float2 du, float2 dv)
+{
+    return __ffma2_rn(dv, __ffma2_rn(dv, f2(q1.w), __ffma2_rn(du, f2(q1.z), f2(q1.x))),
+                      __ffma2_rn(du, __ffma2_rn(du, f2(q1.y), f2(q0.w)), f2(q0.z)));
+}
 // raster_ray for the pixels (du.x, dv.x) and (du.y, dv.y)
 __device__ __forceinline__ Ray2 raster_ray2(const float4& q2, const float4& q3, const float4& q4, float2 du2,
                                             float2 dv)

@@ -179,8 +179,10 @@ __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2
                     const float4* R = rast + kRastVec * (b + 32 * w);
                     const bool in0 = (a0 >> b) & 1u, in1 = (a1 >> b) & 1u;  // warp-uniform
                     const float4 q0 = R[0], q1 = R[1];
-                    const float dv = fpy - q0.y, du0 = fpx0 - q0.x, du1 = fpx1 - q0.x;
-                    const float d0 = raster_disc(q0, q1, du0, dv), d1 = raster_disc(q0, q1, du1, dv);
+                    const float dv = fpy - q0.y;
+                    const float2 du = __fadd2_rn(make_float2(fpx0, fpx1), f2(-q0.x));
+                    const float2 d = raster_disc2(q0, q1, du, f2(dv));  // both halves' pixels
+                    const float du0 = du.x, du1 = du.y, d0 = d.x, d1 = d.y;
                     const bool caps = __float_as_uint(R[4].w) != 0u;
                     const uint32_t v0 = __ballot_sync(0xffffffffu, in0 && (d0 >= 0.f || caps));
                     const uint32_t v1 = __ballot_sync(0xffffffffu, in1 && (d1 >= 0.f || caps));

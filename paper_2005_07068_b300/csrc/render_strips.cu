@@ -126,10 +126,9 @@ __device__ __forceinline__ bool render_strips_warp(StripShared<SH>& sm, const Re
     const int lx = lane & 7, ly = lane >> 3;
     uint64_t* bar = sm.bar[warp];
 
-    // the observation of strip q into buffer b: one 16 x 4 box of depth and of
-    // skin per band of rows inside the box, issued by one lane each
-    auto issue = [&](int q, int b) {
-        const int sy = q / nsx, sx = q - sy * nsx;
+    // the observation of strip (sx, sy) into buffer b: one 16 x 4 box of depth
+    // and of skin per band of rows inside the box, issued by one lane each
+    auto issue = [&](int sx, int sy, int b) {
         const int x16 = (xa + kStripW * sx) & ~15, y0 = by0 + SH * sy;
         const int nb = (min(y0 + SH - 1, by1) - y0) / 4 + 1;
         if (lane == 0) {
@@ -144,14 +143,28 @@ __device__ __forceinline__ bool render_strips_warp(StripShared<SH>& sm, const Re
         }
     };
 
+    // strip q is (q mod nsx, q div nsx); the warp's strips advance by `stride`
+    // without a division per strip: one cursor for the strip rendered, one for
+    // the strip whose observation is loaded next
+    const int ssy = stride / nsx, ssx = stride - ssy * nsx;
+    auto advance = [&](int& cx, int& cy) {
+        cx += ssx;
+        cy += ssy;
+        if (cx >= nsx) {
+            cx -= nsx;
+            ++cy;
+        }
+    };
+    int sx = first % nsx, sy = first / nsx;  // the strip being rendered
+    int nx = sx, ny = sy;                    // the strip after it
+    advance(nx, ny);
     bool ok = true;
     int q = first;
     bool next_issued = false;  // the load of strip q + stride is in flight in buffer buf ^ 1
-    if (first < n_strips) issue(first, buf);
+    if (first < n_strips) issue(sx, sy, buf);
     for (; q < n_strips; q += stride, buf ^= 1) {
         next_issued = q + stride < n_strips;
-        if (next_issued) issue(q + stride, buf ^ 1);  // the next strip's observation meanwhile
-        const int sy = q / nsx, sx = q - sy * nsx;
+        if (next_issued) issue(nx, ny, buf ^ 1);  // the next strip's observation meanwhile
         const int x0 = xa + kStripW * sx, y0 = by0 + SH * sy;
         const int y1 = min(y0 + SH - 1, by1);
         // per pixel of the lane: the nearest depth so far
@@ -241,6 +254,9 @@ __device__ __forceinline__ bool render_strips_warp(StripShared<SH>& sm, const Re
             }
         }
         __syncwarp();  // every lane is done with this buffer before it is refilled
+        sx = nx;
+        sy = ny;
+        advance(nx, ny);
     }
     if (!ok) {
         // the copies still expected -- the late one and the next strip's, if

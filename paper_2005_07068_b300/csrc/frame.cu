@@ -617,7 +617,7 @@ static cudaError_t frame_multi_smem_opt_in()
                                g_frame_multi_opted);
 }
 
-cudaError_t track_frame_multi_capacity(int* ctas)
+cudaError_t track_frame_multi_capacity(int* ctas, int P_max)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -625,7 +625,7 @@ cudaError_t track_frame_multi_capacity(int* ctas)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_frame_multi_kernel, kMultiThreads,
-                                                          2 * HS_FRAME_MAX_PARTICLES * sizeof(float));
+                                                          2 * (size_t)P_max * sizeof(float));
     *ctas = e == cudaSuccess ? sms * per_sm : 0;
     return e;
 }

@@ -180,7 +180,9 @@ def test_batch_frame_rejects_bad_arguments(scenes):
                              ft.pso if pso is None else pso, starts, ft.scale, 0, ctas,
                              ft.fws if ws is None else ws, ft.prims, ft.kc)
 
-    for kw, status in ((dict(ctas=hs.frame_multi_capacity() + 1), hs.HS_ERR_SIZE),
+    cap = hs.frame_multi_capacity(b)
+    assert cap >= hs.frame_multi_capacity() >= torch.cuda.get_device_properties(0).multi_processor_count
+    for kw, status in ((dict(ctas=cap + 1), hs.HS_ERR_SIZE),
                        (dict(ctas=-1), hs.HS_ERR_ARG),
                        (dict(ws=ft.fws[:8]), hs.HS_ERR_SIZE),
                        (dict(x_next=ft.swarm.x), hs.HS_ERR_ARG),

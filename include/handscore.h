@@ -504,8 +504,8 @@ int pso_step_fk_multi(const HsModel* model, const HsBatch* batch, const HsSwarm*
  * the step-by-step calls' only: e_stop must be 0 here.
  * Errors: HS_ERR_ARG (NULL, x_next == swarm->x, bad constants, e_stop != 0,
  * gens < 0, ctas < 0), HS_ERR_ALIGN, HS_ERR_SIZE (a swarm over
- * HS_FRAME_MAX_PARTICLES particles, ctas over capacity, workspace too small),
- * HS_ERR_CUDA. */
+ * HS_FRAME_MAX_PARTICLES particles, (gens + 1) x P_total over 2^31 - 1 tasks,
+ * ctas over capacity, workspace too small), HS_ERR_CUDA. */
 int hs_frame_multi_workspace_size(const HsBatch* batch, size_t* bytes);
 /* CTAs of track_frame_multi that the current device keeps resident at once for this batch (its shared memory
  * holds two values per particle of the batch's largest swarm); batch NULL: for any batch (swarms of up to

@@ -1085,6 +1085,7 @@ int track_frame_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw,
     if (!std::isfinite(psi) || prm->c1 < 0.f || prm->c2 < 0.f || psi <= 4.0) return HS_ERR_ARG;
     if (prm->e_stop != 0.f) return HS_ERR_ARG;  // the stopping rule is the step-by-step batch calls'
     if (b->P_max > HS_FRAME_MAX_PARTICLES) return HS_ERR_SIZE;
+    if ((long long)(gens + 1) * b->P_total > INT_MAX) return HS_ERR_SIZE;  // the task counter's range
     if (!workspace) return HS_ERR_ARG;
     if (!aligned16(prims) || !aligned16(workspace)) return HS_ERR_ALIGN;
     size_t need = 0;

@@ -175,8 +175,8 @@ def test_batch_frame_rejects_bad_arguments(scenes):
     ft = T.BatchFrameTracker(m, b, gens=3)
     starts = torch.from_numpy(np.stack([sc.gt for sc in sub]).astype(np.float32)).cuda()
 
-    def call(ctas=0, x_next=None, ws=None, pso=None):
-        hs.track_frame_multi(m, b, ft.swarm, ft.x_buf[1] if x_next is None else x_next, 3, ft.score,
+    def call(ctas=0, x_next=None, ws=None, pso=None, gens=3):
+        hs.track_frame_multi(m, b, ft.swarm, ft.x_buf[1] if x_next is None else x_next, gens, ft.score,
                              ft.pso if pso is None else pso, starts, ft.scale, 0, ctas,
                              ft.fws if ws is None else ws, ft.prims, ft.kc)
 
@@ -186,7 +186,9 @@ def test_batch_frame_rejects_bad_arguments(scenes):
                        (dict(ctas=-1), hs.HS_ERR_ARG),
                        (dict(ws=ft.fws[:8]), hs.HS_ERR_SIZE),
                        (dict(x_next=ft.swarm.x), hs.HS_ERR_ARG),
-                       (dict(pso=hs.pso_params(e_stop=1.0)), hs.HS_ERR_ARG)):
+                       (dict(pso=hs.pso_params(e_stop=1.0)), hs.HS_ERR_ARG),
+                       (dict(gens=-1), hs.HS_ERR_ARG),
+                       (dict(gens=(1 << 31) // b.P_total), hs.HS_ERR_SIZE)):  # beyond the task counter
         with pytest.raises(hs.HandscoreError) as e:
             call(**kw)
         assert e.value.status == status, kw

@@ -92,9 +92,11 @@ def parse():
     ap.add_argument("--render", default="tune", help="render kernel: tune (timed on the workload first), auto, "
                     "units, tiles32x16, tiles32x32, tiles64x32, tiles64x64")
     ap.add_argument("--ctas", type=int, default=0, help="render CTAs per particle (0 = automatic)")
-    ap.add_argument("--workload", choices=["kinect", "batch", "fullframe", "render", "equaltime"], default="kinect",
+    ap.add_argument("--workload", choices=["kinect", "batch", "fullframe", "render", "equaltime", "polish"],
+                    default="kinect",
                     help="kinect: one 320x240 sequence (the headline); batch: 64 sequences with uneven ROIs and P; "
-                         "fullframe: 640x480 sequence, s/frame to <= 5 deg at several swarm sizes; render: "
+                         "fullframe: 640x480 sequence, s/frame to <= 5 deg at several swarm sizes; polish: the "
+                         "gradient polish's kernels for 8 particles; render: "
                          "render_score_batch alone on one frame (--roi, the first of --particles, --render; for "
                          "profiling one kernel); equaltime: hybrid 64 x 20 + polish against plain PSO given the "
                          "same time per frame, on the 320x240 sequence")
@@ -940,6 +942,85 @@ def run_fullframe(args, rank, world, local):
     return 0
 
 
+POLISH_METRIC = "gradient polish: one descent step of 8 particles (us)"
+
+
+def run_polish(args, rank, world, local):
+    """The gradient polish's kernels alone (Section III.B's hybrid, the
+    smoothed objective E_s and its adjoint): 8 particles around the ground
+    truth of a seeded Kinect-style frame at 320x240 and 640x480, each kernel
+    and one whole descent step (FK, soft_score, soft_score_backward,
+    pose_grad, polish_step) replayed from a captured graph, CUDA events."""
+    import torch
+    from paper_2005_07068_b300 import build as B
+    from paper_2005_07068_b300 import grad as GR
+    from paper_2005_07068_b300 import handscore as hs
+    from paper_2005_07068_b300 import inputs as I
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g = I.hand_geometry()
+    lo, hi = (a.astype(np.float32) for a in I.search_limits())
+    model = hs.Model.from_geometry(g, lo, hi)
+    P = 8
+    scale = np.full(26, np.radians(10.0), np.float32)
+    scale[:3] = 10.0
+    out = {}
+    with ClockSampler(local) as clk:
+        for Wp, Hp in ((320, 240), (640, 480)):
+            ct = I.kinect_camera(Wp, Hp)
+            cam = hs.camera(ct.fx, ct.fy, ct.cx, ct.cy)
+            traj, obs, _ = make_frames(I.CONFIG_SEED_BASE + 3, 1, hs, I, model, cam, dev, W=Wp, H=Hp)
+            hs.hs_obs_prepare(obs[0])
+            rng = np.random.default_rng(3)
+            poses = torch.from_numpy(np.clip(traj[0][None] + 0.3 * rng.uniform(-1, 1, (P, 26)) *
+                                             I.perturbation_scale(), lo, hi).astype(np.float32)).to(dev)
+            sc = GR.SoftScorer(model, obs[0], cam, max_particles=P, device=dev)
+            E = torch.empty(P, device=dev)
+            x = poses.clone()
+            sc.forward(x)
+            sc.gradient(x)
+            calls = {
+                "soft_score": lambda: hs.soft_score(model, obs[0], cam, sc.prims, sc.kc, sc.params, sc.soft, sc.ws,
+                                                    E, sc.sums),
+                "soft_score_backward": lambda: hs.soft_score_backward(model, obs[0], cam, sc.prims, sc.params,
+                                                                      sc.soft, sc.sums, sc.adj),
+                "pose_grad": lambda: hs.pose_grad(model, x, cam, sc.params, sc.prims, sc.kc, sc.adj, sc.grad),
+            }
+
+            def step():
+                hs.pose_fk(model, x, cam, sc.prims, sc.kc)
+                for fn in calls.values():
+                    fn()
+                hs.polish_step(model, x, sc.grad, 0.5, scale)
+
+            calls["descent_step"] = step
+            rec = {}
+            reps = max(1, args.steps)
+
+            def repeat(fn):
+                for _ in range(reps):
+                    fn()
+                return reps
+
+            for name, fn in calls.items():
+                rec[name + "_us"] = replay_render_us(dev, lambda: repeat(fn))
+            out[f"{Wp}x{Hp}"] = rec
+    clocks = clk.summary(measured_peaks().get("sm_max_mhz", 2032.0))
+    if rank == 0:
+        print(json.dumps({"metric": POLISH_METRIC, "value": out["320x240"]["descent_step_us"], "unit": "us",
+                          "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": "8 particles around the ground truth (0.3 of the tracking "
+                                                 "perturbation) of a seeded Kinect-style frame; tau 0.5 px, "
+                                                 "tau_mm 0.5 mm", "step": "pose_fk, soft_score, "
+                                     "soft_score_backward, pose_grad, polish_step"},
+                          "per_roi": out, "clocks": clocks}), flush=True)
+    return 0
+
+
 def run_render(args, rank, world, local):
     """render_score_batch alone: one seeded Kinect-style frame at --roi, the
     first swarm size of --particles spread around the ground truth (half the
@@ -1085,6 +1166,8 @@ def main():
         return run_render(args, rank, world, local)
     if args.workload == "equaltime":
         return run_equal_time(args, rank, world, local)
+    if args.workload == "polish":
+        return run_polish(args, rank, world, local)
 
     import torch
     from paper_2005_07068_b300 import build as B

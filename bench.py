@@ -991,9 +991,11 @@ def run_polish(args, rank, world, local):
                 "pose_grad": lambda: hs.pose_grad(model, x, cam, sc.params, sc.prims, sc.kc, sc.adj, sc.grad),
             }
 
+            kernels = tuple(calls.values())
+
             def step():
                 hs.pose_fk(model, x, cam, sc.prims, sc.kc)
-                for fn in calls.values():
+                for fn in kernels:
                     fn()
                 hs.polish_step(model, x, sc.grad, 0.5, scale)
 

@@ -983,7 +983,7 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ M
 // ---- launchers ----------------------------------------------------------------------
 
 static constexpr int kMaxDevicesSoft = 64;
-static constexpr int kMaxSoftCtas = 64;  // CTAs per particle at most (HsSoftParams.ctas_per_particle's range)
+static constexpr int kMaxSoftCtas = 256;  // CTAs per particle at most in the automatic choice
 
 // kern: the forward or the backward kernel; smem(n): its dynamic shared memory
 // for n primitives; opted: its per-device flag of the shared-memory opt-in

@@ -747,14 +747,17 @@ constexpr float kPenGradFix = 4294967296.0f;  // 2^32
 
 // Model: DevModelCore for the paper's kc, DevModel when the kc variant needs
 // the collision data (then the adjoint of the interpenetration term is added)
+constexpr int kGradThreads = 256;  // threads of pose_grad_kernel (one CTA per particle)
+
 template <class Model>
-__global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ Model model_param, const GradArgs a)
+__global__ void __launch_bounds__(kGradThreads) pose_grad_kernel(const __grid_constant__ Model model_param, const GradArgs a)
 {
     __shared__ FkShared sh;
     __shared__ long long s_gc[kMaxProxies * 3];  // d pen / d (proxy centre), fixed point
     __shared__ CollideSmem<Model> s_col;
     extern __shared__ float s_tan[];  // [26][n_bones][12]: dR (9), dP (3) of every bone for every DOF,
-                                      // then [n_prims][26]: each primitive's contribution
+                                      // then [n_prims][26]: each primitive's contribution,
+                                      // then [n_prims][13]: its adjoints
     fk_load_model(sh, model_param);
     const int p = blockIdx.x, t = threadIdx.x;
     const float* pose = a.poses + (size_t)p * kNdof;
@@ -768,9 +771,9 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ M
         // d pen / d c_i = sum over the penetrating pairs (i, j) of -(c_i - c_j) / |c_i - c_j|
         // (and + for c_j), the same pairs and the same test as the sum in FK;
         // accumulated in fixed point so that the order of the pairs does not matter
-        for (int i = t; i < 3 * sh.model.n_proxies; i += 64) s_gc[i] = 0ll;
+        for (int i = t; i < 3 * sh.model.n_proxies; i += kGradThreads) s_gc[i] = 0ll;
         __syncthreads();
-        for (int k = t; k < sh.model.n_pairs; k += 64) {
+        for (int k = t; k < sh.model.n_pairs; k += kGradThreads) {
             const uint32_t ij = mp->pairs[k];
             const int i = ij & 0xffu, j = ij >> 8;
             const float4 ci = sh.pc[i], cj = sh.pc[j];
@@ -872,13 +875,20 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ M
                 dP[i] = pdP[i] + pdR[3 * i] * B.off[0] + pdR[3 * i + 1] * B.off[1] + pdR[3 * i + 2] * B.off[2];
         }
     }
-    __syncthreads();
+    // meanwhile the other threads: the primitives' adjoints from fixed point
+    // (and their slots cleared for the next backward pass)
     long long* adjp = a.adj + (size_t)p * np * kAdj;
-    for (int j = t; j < np; j += 64) {
+    float* s_ad = s_contrib + (size_t)np * kNdof;  // [n_prims][13]
+    for (int i = t; i < np * kAdj; i += kGradThreads) s_ad[i] = adj_from_fix(adjp[i]);
+    __syncthreads();
+    for (int i = t; i < np * kAdj; i += kGradThreads) adjp[i] = 0ll;  // ready for the next backward pass
+    // every (primitive, parameter) contribution on its own thread
+    for (int jk = t; jk < np * kNdof; jk += kGradThreads) {
+        const int j = jk / kNdof, k = jk - j * kNdof;
         const DevPrimDesc& D = sh.model.prims[j];
         float ad[kAdj];
 #pragma unroll
-        for (int q = 0; q < kAdj; ++q) ad[q] = adj_from_fix(adjp[j * kAdj + q]);
+        for (int q = 0; q < kAdj; ++q) ad[q] = s_ad[j * kAdj + q];
         const float* R = sh.bR[D.bone];
         const float* O = sh.bP[D.bone];
         const bool cone = D.kind == HS_PRIM_ECONE;
@@ -900,7 +910,7 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ M
             half = 0.5f * sqrtf(du * du + dv * dv);
             r_px = fmaxf(D.dims[0], D.dims[1]) * (1.f + fabsf(D.dims[3])) * a.fx / C[2];
         }
-        for (int k = 0; k < kNdof; ++k) {
+        {
             const float* dR = s_tan + ((size_t)k * nb + D.bone) * 12;
             const float* dP = dR + 9;
             float acc = 0.f;
@@ -937,8 +947,6 @@ __global__ void __launch_bounds__(64) pose_grad_kernel(const __grid_constant__ M
             }
             s_contrib[j * kNdof + k] = acc;
         }
-#pragma unroll
-        for (int q = 0; q < kAdj; ++q) adjp[j * kAdj + q] = 0ll;  // ready for the next backward pass
     }
     __syncthreads();
     if (t < kNdof) {
@@ -1029,17 +1037,18 @@ cudaError_t launch_soft(bool backward, const SoftArgs& args, cudaStream_t stream
 
 cudaError_t launch_pose_grad(const DevModel& model, const GradArgs& args, cudaStream_t stream)
 {
-    const size_t smem = ((size_t)kNdof * model.n_bones * 12 + (size_t)model.n_prims * kNdof) * sizeof(float);
+    const size_t smem =
+        ((size_t)kNdof * model.n_bones * 12 + (size_t)model.n_prims * (kNdof + kAdj)) * sizeof(float);
     static std::atomic<uint32_t> opted[2][64];
-    const int smem_max = (kNdof * kMaxBones * 12 + kMaxPrims * kNdof) * 4;
+    const int smem_max = (kNdof * kMaxBones * 12 + kMaxPrims * (kNdof + kAdj)) * 4;
     if (model.kc_variant == HS_KC_ABDUCTION) {
         const cudaError_t e = opt_in_dynamic_smem(pose_grad_kernel<DevModelCore>, smem_max, opted[0]);
         if (e != cudaSuccess) return e;
-        pose_grad_kernel<DevModelCore><<<args.P, 64, smem, stream>>>(static_cast<const DevModelCore&>(model), args);
+        pose_grad_kernel<DevModelCore><<<args.P, kGradThreads, smem, stream>>>(static_cast<const DevModelCore&>(model), args);
     } else {
         const cudaError_t e = opt_in_dynamic_smem(pose_grad_kernel<DevModel>, smem_max, opted[1]);
         if (e != cudaSuccess) return e;
-        pose_grad_kernel<DevModel><<<args.P, 64, smem, stream>>>(model, args);
+        pose_grad_kernel<DevModel><<<args.P, kGradThreads, smem, stream>>>(model, args);
     }
     return cudaGetLastError();
 }

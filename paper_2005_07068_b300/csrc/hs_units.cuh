@@ -15,7 +15,7 @@
 //    every remaining primitive with the discriminant polynomial, solves for
 //    the root only when some lane can be hit, and adds the Eq. 4 terms of the
 //    rendered pixels (reading R1) to the lane's fixed-point / integer sums.
-//    Nearest hit: the smallest float depth, the lower primitive index on ties.
+//    Nearest hit: the smallest float depth.
 #pragma once
 
 #include "hs_render.cuh"

@@ -416,6 +416,36 @@ class BatchFrameTracker(BatchTracker):
     def run_frame(self, frame: int, seed_poses: torch.Tensor | None = None, graph: bool = True) -> None:
         self.enqueue_frame(frame, seed_poses)
 
+    def candidates(self) -> list[int]:
+        """Grid sizes to try: whole waves of the device's SMs up to the batch's resident capacity."""
+        cap = hs.frame_multi_capacity(self.batch)
+        sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+        return sorted({sms * k for k in range(1, 8)} & set(range(1, cap + 1)) | {cap})
+
+    def autotune(self, seed_poses: torch.Tensor, reps: int = 3) -> dict:
+        """Pick the fastest grid size (the kernel renders with its own unit
+        renderer, so there is no render kernel to choose): whole frames from
+        seed_poses [S, 26], timed with CUDA events; returns the table (us per
+        frame) and leaves the tracker's state as it was."""
+        saved = [t.clone() for t in self._state()]
+        keep, cur = self.ctas, self.swarm.x
+        table = {}
+        for n in self.candidates():
+            self.ctas = n
+            self.enqueue_frame(0, seed_poses)  # warm
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record()
+            for _ in range(reps):
+                self.enqueue_frame(0, seed_poses)
+            t1.record()
+            t1.synchronize()
+            table[f"frame_multi/n{n}"] = 1e3 * t0.elapsed_time(t1) / reps
+        self.ctas = min(self.candidates(), key=lambda n: table[f"frame_multi/n{n}"]) if table else keep
+        for t, v in zip(self._state(), saved):
+            t.copy_(v)
+        self.swarm.x = cur
+        return table
+
     def launches_per_frame(self) -> int:
         """The two observation passes and the frame."""
         return 3

@@ -194,3 +194,25 @@ def test_batch_frame_rejects_bad_arguments(scenes):
         assert e.value.status == status, kw
     torch.cuda.synchronize()
     assert hs.hs_get_device_status(clear=True) == 0
+
+
+def test_batch_frame_autotune_keeps_state(scenes):
+    """The grid-size tuner times real grids, picks one of them, and leaves the
+    swarms as they were; a frame at the chosen grid still equals the
+    step-by-step calls."""
+    sub = scenes[:3]
+    m = sub[0].model_g
+    obs, b = _batch(sub)
+    starts = torch.from_numpy(np.stack([sc.gt for sc in sub]).astype(np.float32)).cuda()
+    ft = T.BatchFrameTracker(m, b, gens=2)
+    before = [t.clone() for t in ft._state()]
+    table = ft.autotune(starts, reps=1)
+    assert ft.ctas in ft.candidates() and len(table) == len(ft.candidates())
+    assert all(v > 0 for v in table.values())
+    assert all(torch.equal(x, y) for x, y in zip(before, ft._state()))
+    got = _run(ft, 1, starts)
+    ref = _run(T.BatchTracker(m, b, gens=2), 1, starts)
+    for k, (x, y) in enumerate(zip(got[0], ref[0])):
+        assert _equal(x, y), k
+    assert hs.hs_get_device_status(clear=True) == 0
+

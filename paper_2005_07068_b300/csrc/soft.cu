@@ -30,8 +30,8 @@
 // path); soft_backward_kernel recomputes each pixel and pushes dE_s/d(pixel
 // terms) back through the compositing and each primitive's coverage and depth
 // to its record (M, C: 12 numbers) and, for cones, to L; pose_grad_kernel maps
-// those adjoints to the 26 pose parameters with forward-mode tangents of the
-// FK (one thread per pose parameter).
+// those adjoints to the 26 pose parameters with the FK's tangents (each bone
+// frame's derivative for each parameter from the world axes of its joints).
 #include <atomic>
 
 #include "hs_fk.cuh"
@@ -43,7 +43,11 @@ constexpr int kSoftThreads = 128;
 constexpr int kSoftMargin = 8;      // pixels around each box where alpha may still exceed kAlphaMin
 constexpr float kAlphaMin = 1e-7f;  // touches below this are dropped
 
-__device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + expf(-x)); }
+// The smoothed objective is itself an approximation (its tolerance against the
+// FP64 oracle is far above a few ulps), so its arithmetic takes the hardware's
+// approximate forms: reciprocal and square root (rcp_approx, sqrt_approx),
+// __fdividef and __expf / __logf.
+__device__ __forceinline__ float sigm(float x) { return __fdividef(1.f, 1.f + __expf(-x)); }
 
 // Adjoints are summed as 64-bit fixed point with 2^-40 resolution (|value| <
 // 2^23), so that the totals do not depend on the order of the atomic adds.
@@ -56,6 +60,23 @@ __device__ __forceinline__ long long adj_to_fix(float v)
     const float hi = floorf(w * 2.3283064365386963e-10f);  // w / 2^32
     const float lo = fmaf(-hi, 4294967296.0f, w);          // exact: w - hi 2^32, in [0, 2^32)
     return ((long long)__float2int_rn(hi) << 32) + (long long)__float2uint_rn(lo);
+}
+// A warp's exact sum of 64-bit fixed-point values (mod 2^64, as the 64-bit
+// adds they replace): f = l0 + l1 2^21 + l2 2^42 with l0, l1 in [0, 2^21) and
+// l2 in [-2^21, 2^21), so each limb's sum over 32 lanes fits in 32 bits and
+// takes one integer warp reduction.  Returns the three limb sums (the same
+// on every lane); fix_from_limbs recombines them.
+__device__ __forceinline__ int3 warp_sum_limbs(long long f)
+{
+    const unsigned long long u = (unsigned long long)f;
+    const int l0 = (int)(u & 0x1fffffull), l1 = (int)((u >> 21) & 0x1fffffull), l2 = (int)(f >> 42);
+    return make_int3(__reduce_add_sync(0xffffffffu, l0), __reduce_add_sync(0xffffffffu, l1),
+                     __reduce_add_sync(0xffffffffu, l2));
+}
+__device__ __forceinline__ long long fix_from_limbs(int3 s)
+{
+    return (long long)((unsigned long long)(long long)s.x + ((unsigned long long)(long long)s.y << 21) +
+                       ((unsigned long long)(long long)s.z << 42));
 }
 __device__ __forceinline__ float adj_from_fix(long long f)
 {
@@ -84,7 +105,7 @@ __device__ __forceinline__ float clamp_offset(float s, float R, float& ds)
         ds = 1.f;
         return s;
     }
-    const float ex = expf(1.f - as / R);
+    const float ex = __expf(1.f - __fdividef(as, R));
     ds = ex;
     return copysignf(R * (2.f - ex), s);
 }
@@ -136,35 +157,36 @@ __device__ __forceinline__ void soft_eval(const float4& r0, const float4& r1, co
     e.D = fmaf(B, B, -A * C);
     e.Du = fmaf(2.f * B, Bu, -fmaf(Au, C, A * Cu));
     e.Dv = fmaf(2.f * B, Bv, -fmaf(Av, C, A * Cv));
-    e.N = fmaxf(sqrtf(fmaf(e.Du, e.Du, e.Dv * e.Dv)), 1e-30f);
-    e.delta = e.D / e.N;
+    e.N = fmaxf(sqrt_approx(fmaf(e.Du, e.Du, e.Dv * e.Dv)), 1e-30f);
+    e.delta = __fdividef(e.D, e.N);
     const float tn = tau * e.N;
-    e.q = sqrtf(fmaf(e.D, e.D, tn * tn));
+    e.q = sqrt_approx(fmaf(e.D, e.D, tn * tn));
     e.Dp = 0.5f * (e.D + e.q);
-    e.r = sqrtf(e.Dp);
+    e.r = sqrt_approx(e.Dp);
     // near root in the camera-ray parameter t = t0 + s: t = C_cam / (-B_cam + r) with
     // B_cam = B - t0 A and C_cam = C - 2 t0 B + t0^2 A, i.e. s = num / den below
     e.num = C - t0 * (B + e.r);
     e.den = fmaf(t0, A, -B) + e.r;
     e.ok = A > 0.f && fmaf(-t0, A, B) < 0.f && e.den > 0.f;
     float ds;
-    e.s_raw = e.ok ? e.num / e.den : 0.f;
+    e.s_raw = e.ok ? __fdividef(e.num, e.den) : 0.f;
     e.s = clamp_offset(e.s_raw, Rb, ds);
     e.z = t0 + e.s;
     e.ok = e.ok && e.z > 0.f;
-    e.sig_d = sigm(e.delta / tau);
+    const float itau = rcp_approx(tau);
+    e.sig_d = sigm(e.delta * itau);
     float alpha = e.sig_d;
     if (cone && e.ok) {
-        e.w = sigm(e.delta / tau - 2.f);
-        e.sstar = -B / A;
+        e.w = sigm(fmaf(e.delta, itau, -2.f));
+        e.sstar = __fdividef(-B, A);
         float dss;
         e.sstar_c = clamp_offset(e.sstar, Rb, dss);
         e.Ye = fmaf(fmaf(e.w, e.s - e.sstar_c, e.sstar_c), e.h[1], e.g[1]);  // g_y + (w s + (1 - w) s*) h_y
-        e.sig_y = sigm((1.f - fabsf(e.Ye)) * L / tau);
+        e.sig_y = sigm((1.f - fabsf(e.Ye)) * L * itau);
         e.hh = fmaf(e.h[0], e.h[0], fmaf(e.h[1], e.h[1], e.h[2] * e.h[2]));
-        e.a_rel = A / e.hh;
+        e.a_rel = __fdividef(A, e.hh);
         const float a4 = e.a_rel * e.a_rel * e.a_rel * e.a_rel, f0 = 0.06f * tau, f4 = f0 * f0 * f0 * f0;
-        e.fade = a4 / (a4 + f4);
+        e.fade = __fdividef(a4, a4 + f4);
         alpha *= e.sig_y * e.fade;
     }
     e.alpha = e.ok ? alpha : 0.f;
@@ -187,17 +209,19 @@ __device__ __forceinline__ void soft_backprop(const float4& r0, const float4& r1
     // alpha = sig_d (x sig_y x fade for a cone); z = t0 + s, s = clamp(s_raw)
     float gsd = ga, gs = gz;
     gt0 += gz;
+    const float itau = rcp_approx(tau);
     if (cone) {
         gsd = ga * e.sig_y * e.fade;
         // fade = a^4 / (a^4 + f^4), a = A / |h|^2
         const float f0 = 0.06f * tau, f4 = f0 * f0 * f0 * f0;
         const float a4 = e.a_rel * e.a_rel * e.a_rel * e.a_rel;
-        const float dfade = 4.f * e.a_rel * e.a_rel * e.a_rel * f4 / ((a4 + f4) * (a4 + f4));
+        const float dfade = __fdividef(4.f * e.a_rel * e.a_rel * e.a_rel * f4, (a4 + f4) * (a4 + f4));
         const float gar = ga * e.sig_d * e.sig_y * dfade;
-        gA += gar / e.hh;
+        const float ihh = rcp_approx(e.hh);
+        gA += gar * ihh;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) gh[i] += -gar * 2.f * e.a_rel * e.h[i] / e.hh;
-        const float gdy = ga * e.sig_d * e.fade * e.sig_y * (1.f - e.sig_y) / tau;  // d alpha / d delta_Y
+        for (int i = 0; i < 3; ++i) gh[i] += -gar * 2.f * e.a_rel * e.h[i] * ihh;
+        const float gdy = ga * e.sig_d * e.fade * e.sig_y * (1.f - e.sig_y) * itau;  // d alpha / d delta_Y
         if (gdy != 0.f) {
             adj[12] += gdy * (1.f - fabsf(e.Ye));
             const float gY = -gdy * L * (e.Ye >= 0.f ? 1.f : -1.f);
@@ -208,36 +232,40 @@ __device__ __forceinline__ void soft_backprop(const float4& r0, const float4& r1
             const float gu_ = gY * e.h[1];
             gs += gu_ * e.w;
             const float gw = gu_ * (e.s - e.sstar_c);
-            gdelta += gw * e.w * (1.f - e.w) / tau;
+            gdelta += gw * e.w * (1.f - e.w) * itau;
             float dss;
             clamp_offset(e.sstar, Rb, dss);
             const float gss = gu_ * (1.f - e.w) * dss;  // d / d s* (s* = -B / A)
-            gB += -gss / e.A;
-            gA += -gss * e.sstar / e.A;
+            const float iA = rcp_approx(e.A);
+            gB += -gss * iA;
+            gA += -gss * e.sstar * iA;
         }
     }
-    gdelta += gsd * e.sig_d * (1.f - e.sig_d) / tau;
+    gdelta += gsd * e.sig_d * (1.f - e.sig_d) * itau;
     // s = clamp(s_raw), s_raw = num / den, num = C - t0 (B + r), den = t0 A - B + r
     float dcl;
     clamp_offset(e.s_raw, Rb, dcl);
     const float gsr = gs * dcl;
-    const float gnum = gsr / e.den, gden = -gsr * e.s_raw / e.den;
+    const float iden = rcp_approx(e.den);
+    const float gnum = gsr * iden, gden = -gsr * e.s_raw * iden;
     gC += gnum;
     gt0 += -gnum * (e.B + e.r) + gden * e.A;
     gB += -t0 * gnum - gden;
     gr += -t0 * gnum + gden;
     gA += gden * t0;
     // r = sqrt(Dp), Dp = (D + q) / 2, q = sqrt(D^2 + (tau N)^2)
-    const float gDp = gr / (2.f * e.r);
-    gD += 0.5f * gDp * (1.f + e.D / e.q);
-    gN += 0.5f * gDp * (tau * tau * e.N / e.q);
+    const float gDp = 0.5f * gr * rcp_approx(e.r);
+    const float iq = rcp_approx(e.q);
+    gD += 0.5f * gDp * fmaf(e.D, iq, 1.f);
+    gN += 0.5f * gDp * (tau * tau * e.N * iq);
     // delta = D / N (skipped when sigma saturated: then delta / N may overflow)
     if (gdelta != 0.f) {
-        gD += gdelta / e.N;
-        gN += -gdelta * e.delta / e.N;
+        gD += __fdividef(gdelta, e.N);
+        gN += -__fdividef(gdelta * e.delta, e.N);
     }
     // N = |(Du, Dv)|
-    const float gDu = gN * e.Du / e.N, gDv = gN * e.Dv / e.N;
+    const float gNN = __fdividef(gN, e.N);
+    const float gDu = gNN * e.Du, gDv = gNN * e.Dv;
     // D = B^2 - A C
     gB += 2.f * e.B * gD;
     gA += -e.C * gD;
@@ -416,15 +444,16 @@ __device__ __forceinline__ void soft_pixel_terms(float od, bool S, float zt, flo
 {
     const bool valid = S && od > 0.f;
     dd = od - zt;
-    diff = sqrtf(fmaf(dd, dd, tm * tm));
+    diff = sqrt_approx(fmaf(dd, dd, tm * tm));
+    const float itm = rcp_approx(tm);
     dsmin = 0.f;
     dm = 0.f;
     if (valid) {
         const float m0 = fminf(diff, d_M);
-        t_hit = m0 - tm * logf(expf(-(diff - m0) / tm) + expf(-(d_M - m0) / tm));
-        dsmin = sigm((d_M - diff) / tm);
-        m = sigm((d_m - diff) / tm);
-        dm = -m * (1.f - m) / tm;
+        t_hit = m0 - tm * __logf(__expf(-(diff - m0) * itm) + __expf(-(d_M - m0) * itm));
+        dsmin = sigm((d_M - diff) * itm);
+        m = sigm((d_m - diff) * itm);
+        dm = -m * (1.f - m) * itm;
         t_miss = d_M;
     } else {
         t_hit = S ? 0.f : d_M;
@@ -433,7 +462,7 @@ __device__ __forceinline__ void soft_pixel_terms(float od, bool S, float zt, flo
     }
 }
 
-__global__ void __launch_bounds__(kSoftThreads) soft_backward_kernel(const SoftArgs a)
+__global__ void __launch_bounds__(kSoftThreads, 5) soft_backward_kernel(const SoftArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n_prims;
@@ -525,7 +554,7 @@ __global__ void __launch_bounds__(kSoftThreads) soft_backward_kernel(const SoftA
             }
             const float c = 1.f - T;
             if (cnt > 0 && c > 0.f) {
-                const float zt = Nz / c;
+                const float zt = __fdividef(Nz, c);
                 const float od = a.depth_f32
                                      ? reinterpret_cast<const float*>(a.depth + (size_t)v * a.depth_pitch)[u]
                                      : (float)reinterpret_cast<const uint16_t*>(a.depth + (size_t)v * a.depth_pitch)[u];
@@ -538,9 +567,10 @@ __global__ void __launch_bounds__(kSoftThreads) soft_backward_kernel(const SoftA
                     // each entry's (d alpha, d z) replaces its (T, alpha) in place
                     const float gr_ = S ? G_and : G_or;
                     const float gc = G_t * (t_hit - t_miss) + gr_ * m;
-                    const float gzt = valid ? (G_t * c * dsmin + gr_ * c * dm) * (-dd / diff) : 0.f;
-                    const float gN = gzt / c;
-                    const float gct = gc - gzt * zt / c;
+                    const float gzt = valid ? (G_t * c * dsmin + gr_ * c * dm) * __fdividef(-dd, diff) : 0.f;
+                    const float ic = rcp_approx(c);
+                    const float gN = gzt * ic;
+                    const float gct = gc - gzt * zt * ic;
                     float Rsuf = 0.f, Psuf = 1.f;
                     for (int k = cnt - 1; k >= 0; --k) {
                         const float al = s_al[k * 32 + lane], zk = s_zl[k * 32 + lane];
@@ -587,14 +617,14 @@ __global__ void __launch_bounds__(kSoftThreads) soft_backward_kernel(const SoftA
 #pragma unroll
                     for (int q = 0; q < kAdj; ++q) f[q] = adj_to_fix(adj[q]);
                 }
+                int3 mine = make_int3(0, 0, 0);  // lane q keeps adjoint q's limb sums
 #pragma unroll
                 for (int q = 0; q < kAdj; ++q) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
+                    const int3 sq = warp_sum_limbs(f[q]);
+                    if (lane == q) mine = sq;
                 }
-#pragma unroll
-                for (int q = 0; q < kAdj; ++q)
-                    if (lane == q && f[q] != 0) atomicAdd(&s_adj[j * kAdj + q], (unsigned long long)f[q]);
+                const long long tot = fix_from_limbs(mine);
+                if (lane < kAdj && tot != 0) atomicAdd(&s_adj[j * kAdj + lane], (unsigned long long)tot);
             }
             __syncthreads();  // the lists are free for the next strip
         }
@@ -681,7 +711,7 @@ __global__ void __launch_bounds__(kSoftThreads) soft_forward_kernel(const SoftAr
         }
         const float c = 1.f - T;
         if (!(c > 0.f)) continue;
-        const float zt = Nz / c;
+        const float zt = __fdividef(Nz, c);
         const float od = a.depth_f32 ? reinterpret_cast<const float*>(a.depth + (size_t)v * a.depth_pitch)[u]
                                      : (float)reinterpret_cast<const uint16_t*>(a.depth + (size_t)v * a.depth_pitch)[u];
         const bool S = a.skin[(size_t)v * a.skin_pitch + u] != 0;
@@ -797,86 +827,75 @@ __global__ void __launch_bounds__(kGradThreads) pose_grad_kernel(const __grid_co
         }
     }
     float* s_contrib = s_tan + (size_t)kNdof * nb * 12;
-    if (t < kNdof) {
-        // tangents of every bone frame with respect to pose parameter t (parents first)
-        for (int k = 0; k < nb; ++k) {
-            float* dR = s_tan + ((size_t)t * nb + k) * 12;
-            float* dP = dR + 9;
-            float dl[9];
-            bool own = false;
-            if (k == 0) {
-                if (t >= 3 && t <= 5) {
-                    // palm: Mount Rz(q5) Ry(q4) Rx(q3), Mount = diag(1, -1, -1)
-                    float sx, cx, sy, cy, sz, cz;
-                    sincosf(sh.q[3], &sx, &cx);
-                    sincosf(sh.q[4], &sy, &cy);
-                    sincosf(sh.q[5], &sz, &cz);
-                    float Rx[9] = {1.f, 0.f, 0.f, 0.f, cx, -sx, 0.f, sx, cx};
-                    float Ry[9] = {cy, 0.f, sy, 0.f, 1.f, 0.f, -sy, 0.f, cy};
-                    float Rz[9] = {cz, -sz, 0.f, sz, cz, 0.f, 0.f, 0.f, 1.f};
-                    if (t == 3) {
-                        const float d[9] = {0.f, 0.f, 0.f, 0.f, -sx, -cx, 0.f, cx, -sx};
+    // Tangents of every bone frame for every pose parameter, each (parameter d,
+    // bone k) on its own thread.  An angle turns everything below its joint
+    // about a world axis w through the joint's position J, so
+    //   dR_k / dq_d = [w]x R_k,  dP_k / dq_d = w x (P_k - J),
+    // summed over the joints of bone k's path that q_d drives (the palm's
+    // three angles drive every bone; the translation q_0..2 drives no frame).
+    // The axes, from the global frames FK formed (G = U Rz Rx for a finger
+    // joint with U = R_parent rest; G = Mount Rz Ry Rx for the palm,
+    // Mount = diag(1, -1, -1)):
+    //   finger z angle: U e_z;  finger x angle: U Rz e_x = G e_x;
+    //   palm q5: Mount e_z;  q4: Mount Rz(q5) e_y;  q3: Mount Rz Ry e_x = G_palm e_x.
+    for (int i = t; i < kNdof * nb; i += kGradThreads) {
+        const int d = i / nb, k = i - d * nb;
+        const DevBone& Bk = sh.model.bones[k];
+        float W[3] = {0.f, 0.f, 0.f}, V[3] = {0.f, 0.f, 0.f};  // sum of axes w, sum of w x J
+        if (d >= 3 && d <= 5) {
+            // the palm's angles; its joint is the wrist (J = 0)
+            if (d == 5) {
+                W[2] = -1.f;
+            } else if (d == 4) {
+                W[0] = -sh.sn[5];
+                W[1] = -sh.cs[5];
+            } else {
+                W[0] = sh.bR[0][0];
+                W[1] = sh.bR[0][3];
+                W[2] = sh.bR[0][6];
+            }
+        } else if (d >= 6) {
+            for (int lv = 1; lv <= Bk.depth; ++lv) {
+                const int b = Bk.anc[lv];
+                const DevBone& B = sh.model.bones[b];
+                if (B.dof_z != d && B.dof_x != d) continue;
+                float w[3];
+                if (B.dof_z == d) {
+                    const float* Rp = sh.bR[B.parent];
 #pragma unroll
-                        for (int q = 0; q < 9; ++q) Rx[q] = d[q];
-                    } else if (t == 4) {
-                        const float d[9] = {-sy, 0.f, cy, 0.f, 0.f, 0.f, -cy, 0.f, -sy};
-#pragma unroll
-                        for (int q = 0; q < 9; ++q) Ry[q] = d[q];
-                    } else {
-                        const float d[9] = {-sz, -cz, 0.f, cz, -sz, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                        for (int q = 0; q < 9; ++q) Rz[q] = d[q];
-                    }
-                    float tmp[9], M[9];
-                    mat3_mul(Rz, Ry, tmp);
-                    mat3_mul(tmp, Rx, M);
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) dR[q] = q < 3 ? M[q] : -M[q];
+                    for (int r = 0; r < 3; ++r)
+                        w[r] = fmaf(Rp[3 * r], B.rest[2], fmaf(Rp[3 * r + 1], B.rest[5], Rp[3 * r + 2] * B.rest[8]));
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) dR[q] = 0.f;
+                    for (int r = 0; r < 3; ++r) w[r] = sh.bR[b][3 * r];
                 }
-                dP[0] = dP[1] = dP[2] = 0.f;  // positions are wrist-relative
-                continue;
+                const float* J = sh.bP[b];
+                W[0] += w[0];
+                W[1] += w[1];
+                W[2] += w[2];
+                V[0] += w[1] * J[2] - w[2] * J[1];
+                V[1] += w[2] * J[0] - w[0] * J[2];
+                V[2] += w[0] * J[1] - w[1] * J[0];
             }
-            const DevBone& B = sh.model.bones[k];
-            const float* pdR = s_tan + ((size_t)t * nb + B.parent) * 12;
-            const float* pdP = pdR + 9;
-            if (B.dof_z == t || B.dof_x == t) {
-                own = true;
-                float sz = 0.f, cz = 1.f, sx = 0.f, cx = 1.f;
-                if (B.dof_z >= 0) sincosf(sh.q[B.dof_z], &sz, &cz);
-                if (B.dof_x >= 0) sincosf(sh.q[B.dof_x], &sx, &cx);
-                float ZX[9];
-                if (B.dof_z == t) {
-                    const float d[9] = {-sz, -cz * cx, cz * sx, cz, -sz * cx, sz * sx, 0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) ZX[q] = d[q];
-                } else {
-                    const float d[9] = {0.f, sz * sx, sz * cx, 0.f, -cz * sx, -cz * cx, 0.f, cx, -sx};
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) ZX[q] = d[q];
-                }
-                mat3_mul(B.rest, ZX, dl);
-            }
-            // dR_k = dR_parent lR_k + R_parent dlR_k ; dP_k = dP_parent + dR_parent off_k
-            float t1[9];
-            mat3_mul(pdR, sh.lR[k], t1);
-            if (own) {
-                float t2[9];
-                mat3_mul(sh.bR[B.parent], dl, t2);
-#pragma unroll
-                for (int q = 0; q < 9; ++q) t1[q] += t2[q];
-            }
-#pragma unroll
-            for (int q = 0; q < 9; ++q) dR[q] = t1[q];
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-                dP[i] = pdP[i] + pdR[3 * i] * B.off[0] + pdR[3 * i + 1] * B.off[1] + pdR[3 * i + 2] * B.off[2];
         }
+        float* dR = s_tan + ((size_t)d * nb + k) * 12;
+        float* dP = dR + 9;
+        const float* R = sh.bR[k];
+        const float* P = sh.bP[k];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            // column c of dR = W x (column c of R)
+            const float x = R[c], y = R[3 + c], z = R[6 + c];
+            dR[c] = W[1] * z - W[2] * y;
+            dR[3 + c] = W[2] * x - W[0] * z;
+            dR[6 + c] = W[0] * y - W[1] * x;
+        }
+        dP[0] = W[1] * P[2] - W[2] * P[1] - V[0];
+        dP[1] = W[2] * P[0] - W[0] * P[2] - V[1];
+        dP[2] = W[0] * P[1] - W[1] * P[0] - V[2];
     }
-    // meanwhile the other threads: the primitives' adjoints from fixed point
-    // (and their slots cleared for the next backward pass)
+    // the primitives' adjoints from fixed point (and their slots cleared for
+    // the next backward pass)
     long long* adjp = a.adj + (size_t)p * np * kAdj;
     float* s_ad = s_contrib + (size_t)np * kNdof;  // [n_prims][13]
     for (int i = t; i < np * kAdj; i += kGradThreads) s_ad[i] = adj_from_fix(adjp[i]);

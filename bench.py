@@ -551,7 +551,7 @@ def batch_frame_throughput(hs, bset, frames, steps, warmup, dev):
     out = {"value": steps * ft.evals_per_frame() / (sum(ms) * 1e-3), "unit": "evals/s",
            "ms_per_frame": sum(ms) / steps, "latency_ms": {"p50": percentile(ms, 50), "p99": percentile(ms, 99)},
            "steps": steps, "warmup": warmup, "gpu_launches_per_step": ft.launches_per_frame(),
-           "ctas": hs.frame_multi_capacity(batch),
+           "ctas": hs.frame_multi_capacity(batch, trk.model),
            "kernel": "track_frame_multi: one cooperative launch per frame of every sequence (per-particle tasks)",
            "step": "one frame of every sequence: one frame copy + the observation passes + one launch; "
                    "L2 flushed between steps"}

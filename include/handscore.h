@@ -490,7 +490,7 @@ int pso_step_fk_multi(const HsModel* model, const HsBatch* batch, const HsSwarm*
  * kc [P_total] (the records and kc of the final positions).  seed_poses:
  * device [S][26]; scale: host [26].
  *
- * ctas: CTAs of the grid, 1..hs_frame_multi_capacity(batch); 0 picks the capacity.
+ * ctas: CTAs of the grid, 1..hs_frame_multi_capacity(model, batch); 0 picks the capacity.
  * workspace: hs_frame_multi_workspace_size(batch) bytes (a 128-byte control
  * block, a count per swarm from byte 128 on, then two generations of E), zeroed
  * once before first use (every call leaves the control block and the counts
@@ -507,11 +507,12 @@ int pso_step_fk_multi(const HsModel* model, const HsBatch* batch, const HsSwarm*
  * HS_FRAME_MAX_PARTICLES particles, (gens + 1) x P_total over 2^31 - 1 tasks,
  * ctas over capacity, workspace too small), HS_ERR_CUDA. */
 int hs_frame_multi_workspace_size(const HsBatch* batch, size_t* bytes);
-/* CTAs of track_frame_multi that the current device keeps resident at once for this batch (its shared memory
- * holds two values per particle of the batch's largest swarm); batch NULL: for any batch (swarms of up to
- * HS_FRAME_MAX_PARTICLES particles).  Errors: HS_ERR_ARG, HS_ERR_SIZE (a swarm over HS_FRAME_MAX_PARTICLES),
- * HS_ERR_CUDA. */
-int hs_frame_multi_capacity(const HsBatch* batch, int* ctas);
+/* CTAs of track_frame_multi that the current device keeps resident at once for this model and batch (its
+ * shared memory holds two values per particle of the batch's largest swarm, and, for a model whose kc variant
+ * uses the interpenetration test, the model's collision data, which leaves room for fewer CTAs); model NULL: a
+ * model with the paper's kc; batch NULL: for any batch (swarms of up to HS_FRAME_MAX_PARTICLES particles).
+ * Errors: HS_ERR_ARG, HS_ERR_SIZE (a swarm over HS_FRAME_MAX_PARTICLES), HS_ERR_CUDA. */
+int hs_frame_multi_capacity(const HsModel* model, const HsBatch* batch, int* ctas);
 int track_frame_multi(const HsModel* model, const HsBatch* batch, const HsSwarm* swarm, float* x_next, int gens,
                       const HsScoreParams* score, const HsPsoParams* pso, const float* seed_poses,
                       const float* scale, uint32_t frame, int ctas, void* workspace, size_t workspace_bytes,

@@ -1062,12 +1062,13 @@ int hs_frame_multi_workspace_size(const HsBatch* b, size_t* bytes)
     return HS_OK;
 }
 
-int hs_frame_multi_capacity(const HsBatch* b, int* ctas)
+int hs_frame_multi_capacity(const HsModel* model, const HsBatch* b, int* ctas)
 {
     if (!ctas) return HS_ERR_ARG;
     const int P_max = b ? b->P_max : HS_FRAME_MAX_PARTICLES;
     if (P_max > HS_FRAME_MAX_PARTICLES) return HS_ERR_SIZE;
-    return track_frame_multi_capacity(ctas, P_max) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+    const bool collide = model && frame_multi_needs_collide(model->dev);
+    return track_frame_multi_capacity(ctas, P_max, collide) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 
 int track_frame_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw, float* x_next, int gens,
@@ -1097,7 +1098,8 @@ int track_frame_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw,
         a.scale[d] = scale[d];
     }
     int cap = 0;
-    if (track_frame_multi_capacity(&cap, b->P_max) != cudaSuccess) return HS_ERR_CUDA;  // for this batch's swarms
+    if (track_frame_multi_capacity(&cap, b->P_max, frame_multi_needs_collide(model->dev)) != cudaSuccess)
+        return HS_ERR_CUDA;  // for this batch's swarms and this model's kernel
     const int nb = ctas ? ctas : cap;
     if (nb < 1 || nb > cap) return HS_ERR_SIZE;
     a.batch = b->dev;

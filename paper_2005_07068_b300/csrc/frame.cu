@@ -40,10 +40,12 @@ constexpr unsigned long long kBarrierWaitNs = 1000000000ull;  // a grid barrier 
 constexpr uint32_t kBarrierPolls = 1u << 26;  // and at most this many polls, should the clock not advance
 
 
-template <int NW>  // warps of the CTA
+// NW: warps of the CTA; Col: the kc variants' collision data (CollideShared),
+// or a placeholder byte for kernels launched only for the paper's kc
+template <int NW, class Col = CollideShared>
 struct FrameSharedT {
     FkShared fk;                      // model, pose, bone frames
-    CollideShared col;                // the kc variants' collision data
+    Col col;                          // the kc variants' collision data
     float4 rec[kMaxPrims * 4];        // this particle's FK records
     float4 rast[kMaxPrims * kRastVec];  // their raster records
     int2 pbox[kMaxPrims];
@@ -366,10 +368,13 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
 constexpr int kMultiWarps = 4;
 constexpr int kMultiThreads = kMultiWarps * 32;
 
+// Model: DevModelCore for the paper's kc (no collision data in shared memory,
+// so more CTAs stay resident), DevModel for the kc variants
+template <class Model>
 __global__ void __launch_bounds__(kMultiThreads, 24 / kMultiWarps)
-    track_frame_multi_kernel(const __grid_constant__ DevModel model, const FrameMultiArgs a)
+    track_frame_multi_kernel(const __grid_constant__ Model model, const FrameMultiArgs a)
 {
-    __shared__ FrameSharedT<kMultiWarps> sh;
+    __shared__ FrameSharedT<kMultiWarps, CollideSmem<Model>> sh;
     __shared__ int s_task, s_go;
     extern __shared__ float s_dyn[];  // E [P_max], then pbest_E [P_max] of the task's swarm
     float* s_e = s_dyn;
@@ -609,30 +614,38 @@ cudaError_t launch_track_frame(const DevModel& model, const CUtensorMap& tm_dept
 
 
 // the batch frame: the same static part, dynamic shared memory for the
-// largest swarm of the batch (2 P_max floats)
-static std::atomic<uint32_t> g_frame_multi_opted[64];
+// largest swarm of the batch (2 P_max floats); one kernel per model type
+static std::atomic<uint32_t> g_frame_multi_opted[2][64];
+template <class Model>
 static cudaError_t frame_multi_smem_opt_in()
 {
-    return opt_in_dynamic_smem(track_frame_multi_kernel, 2 * HS_FRAME_MAX_PARTICLES * (int)sizeof(float),
-                               g_frame_multi_opted);
+    return opt_in_dynamic_smem(track_frame_multi_kernel<Model>, 2 * HS_FRAME_MAX_PARTICLES * (int)sizeof(float),
+                               g_frame_multi_opted[std::is_same<Model, DevModel>::value ? 1 : 0]);
 }
 
-cudaError_t track_frame_multi_capacity(int* ctas, int P_max)
+template <class Model>
+static cudaError_t frame_multi_capacity_of(int* ctas, int P_max)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = frame_multi_smem_opt_in();
+    if (e == cudaSuccess) e = frame_multi_smem_opt_in<Model>();
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_frame_multi_kernel, kMultiThreads,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_frame_multi_kernel<Model>, kMultiThreads,
                                                           2 * (size_t)P_max * sizeof(float));
     *ctas = e == cudaSuccess ? sms * per_sm : 0;
     return e;
 }
 
-cudaError_t launch_track_frame_multi(const DevModel& model, const FrameMultiArgs& args, int ctas, cudaStream_t stream)
+cudaError_t track_frame_multi_capacity(int* ctas, int P_max, bool collide)
 {
-    const cudaError_t e = frame_multi_smem_opt_in();
+    return collide ? frame_multi_capacity_of<DevModel>(ctas, P_max) : frame_multi_capacity_of<DevModelCore>(ctas, P_max);
+}
+
+template <class Model>
+static cudaError_t launch_frame_multi_as(const Model& model, const FrameMultiArgs& args, int ctas, cudaStream_t stream)
+{
+    const cudaError_t e = frame_multi_smem_opt_in<Model>();
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ctas);
@@ -644,7 +657,14 @@ cudaError_t launch_track_frame_multi(const DevModel& model, const FrameMultiArgs
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, track_frame_multi_kernel, model, args);
+    return cudaLaunchKernelEx(&cfg, track_frame_multi_kernel<Model>, model, args);
+}
+
+cudaError_t launch_track_frame_multi(const DevModel& model, const FrameMultiArgs& args, int ctas, cudaStream_t stream)
+{
+    if (frame_multi_needs_collide(model))
+        return launch_frame_multi_as(model, args, ctas, stream);
+    return launch_frame_multi_as(static_cast<const DevModelCore&>(model), args, ctas, stream);
 }
 
 }  // namespace hs

@@ -156,7 +156,7 @@ _SIGS = {
                      ctypes.POINTER(ctypes.c_float), ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, _vp,
                      ctypes.c_size_t, _vp, _vp, _vp], ctypes.c_int),
     "hs_frame_multi_workspace_size": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
-    "hs_frame_multi_capacity": ([_vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "hs_frame_multi_capacity": ([_vp, _vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "track_frame_multi": ([_vp, _vp, ctypes.POINTER(HsSwarm), _vp, ctypes.c_int, ctypes.POINTER(HsScoreParams),
                            ctypes.POINTER(HsPsoParams), _vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32,
                            ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp, _vp], ctypes.c_int),
@@ -610,12 +610,14 @@ def new_frame_multi_workspace(batch: Batch, device="cuda") -> torch.Tensor:
     return torch.zeros((n.value + 15) // 16 * 4, dtype=torch.int32, device=device)
 
 
-def frame_multi_capacity(batch: Batch | None = None) -> int:
+def frame_multi_capacity(batch: Batch | None = None, model: Model | None = None) -> int:
     """CTAs of track_frame_multi the current device keeps resident at once for
-    this batch (None: for any batch)."""
+    this batch (None: for any batch) and model (None: one with the paper's kc;
+    a kc variant with the interpenetration test leaves room for fewer)."""
     n = ctypes.c_int()
     _check("hs_frame_multi_capacity",
-           lib().hs_frame_multi_capacity(batch.handle if batch is not None else None, ctypes.byref(n)))
+           lib().hs_frame_multi_capacity(model.handle if model is not None else None,
+                                         batch.handle if batch is not None else None, ctypes.byref(n)))
     return n.value
 
 

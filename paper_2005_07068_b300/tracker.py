@@ -418,7 +418,7 @@ class BatchFrameTracker(BatchTracker):
 
     def candidates(self) -> list[int]:
         """Grid sizes to try: whole waves of the device's SMs up to the batch's resident capacity."""
-        cap = hs.frame_multi_capacity(self.batch)
+        cap = hs.frame_multi_capacity(self.batch, self.model)
         sms = torch.cuda.get_device_properties(self.device).multi_processor_count
         return sorted({sms * k for k in range(1, 8)} & set(range(1, cap + 1)) | {cap})
 

@@ -297,7 +297,7 @@ def test_batch_host_checks():
     assert L.hs_batch_destroy(None) == hs.HS_ERR_ARG
     # the batch frame: no batch, no workspace size, no frame
     assert L.hs_frame_multi_workspace_size(None, ctypes.byref(n)) == hs.HS_ERR_ARG
-    assert L.hs_frame_multi_capacity(None, None) == hs.HS_ERR_ARG
+    assert L.hs_frame_multi_capacity(None, None, None) == hs.HS_ERR_ARG
     sw = hs.HsSwarm(FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE)
     scale = (ctypes.c_float * 26)(*([1.0] * 26))
     pp = hs.pso_params()

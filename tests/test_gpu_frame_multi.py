@@ -180,7 +180,8 @@ def test_batch_frame_rejects_bad_arguments(scenes):
                              ft.pso if pso is None else pso, starts, ft.scale, 0, ctas,
                              ft.fws if ws is None else ws, ft.prims, ft.kc)
 
-    cap = hs.frame_multi_capacity(b)
+    cap = hs.frame_multi_capacity(b, m)
+    assert cap == hs.frame_multi_capacity(b)  # the paper's kc: the model's default
     assert cap >= hs.frame_multi_capacity() >= torch.cuda.get_device_properties(0).multi_processor_count
     for kw, status in ((dict(ctas=cap + 1), hs.HS_ERR_SIZE),
                        (dict(ctas=-1), hs.HS_ERR_ARG),
@@ -192,6 +193,16 @@ def test_batch_frame_rejects_bad_arguments(scenes):
         with pytest.raises(hs.HandscoreError) as e:
             call(**kw)
         assert e.value.status == status, kw
+    # a kc variant keeps the collision data in shared memory: fewer CTAs fit, and the frame takes no more
+    m.set_kc(hs.HS_KC_ABD_PEN, 0.05)
+    try:
+        cap_pen = hs.frame_multi_capacity(b, m)
+        assert torch.cuda.get_device_properties(0).multi_processor_count <= cap_pen <= cap
+        with pytest.raises(hs.HandscoreError) as e:
+            call(ctas=cap_pen + 1)
+        assert e.value.status == hs.HS_ERR_SIZE
+    finally:
+        m.set_kc(hs.HS_KC_ABDUCTION, 0.0)
     torch.cuda.synchronize()
     assert hs.hs_get_device_status(clear=True) == 0
 

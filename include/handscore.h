@@ -508,9 +508,10 @@ int pso_step_fk_multi(const HsModel* model, const HsBatch* batch, const HsSwarm*
  * ctas over capacity, workspace too small), HS_ERR_CUDA. */
 int hs_frame_multi_workspace_size(const HsBatch* batch, size_t* bytes);
 /* CTAs of track_frame_multi that the current device keeps resident at once for this model and batch (its
- * shared memory holds two values per particle of the batch's largest swarm, and, for a model whose kc variant
- * uses the interpenetration test, the model's collision data, which leaves room for fewer CTAs); model NULL: a
- * model with the paper's kc; batch NULL: for any batch (swarms of up to HS_FRAME_MAX_PARTICLES particles).
+ * shared memory holds two values per particle of the batch's largest swarm, the records of the model's
+ * primitives, and, for a model whose kc variant uses the interpenetration test, the model's collision data,
+ * which leaves room for fewer CTAs); model NULL: for any model with the paper's kc (HS_MAX_PRIMS primitives);
+ * batch NULL: for any batch (swarms of up to HS_FRAME_MAX_PARTICLES particles).
  * Errors: HS_ERR_ARG, HS_ERR_SIZE (a swarm over HS_FRAME_MAX_PARTICLES), HS_ERR_CUDA. */
 int hs_frame_multi_capacity(const HsModel* model, const HsBatch* batch, int* ctas);
 int track_frame_multi(const HsModel* model, const HsBatch* batch, const HsSwarm* swarm, float* x_next, int gens,

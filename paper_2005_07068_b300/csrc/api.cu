@@ -1068,7 +1068,8 @@ int hs_frame_multi_capacity(const HsModel* model, const HsBatch* b, int* ctas)
     const int P_max = b ? b->P_max : HS_FRAME_MAX_PARTICLES;
     if (P_max > HS_FRAME_MAX_PARTICLES) return HS_ERR_SIZE;
     const bool collide = model && frame_multi_needs_collide(model->dev);
-    return track_frame_multi_capacity(ctas, P_max, collide) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+    const int n_prims = model ? model->dev.n_prims : HS_MAX_PRIMS;
+    return track_frame_multi_capacity(ctas, P_max, n_prims, collide) == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 
 int track_frame_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw, float* x_next, int gens,
@@ -1098,7 +1099,8 @@ int track_frame_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw,
         a.scale[d] = scale[d];
     }
     int cap = 0;
-    if (track_frame_multi_capacity(&cap, b->P_max, frame_multi_needs_collide(model->dev)) != cudaSuccess)
+    if (track_frame_multi_capacity(&cap, b->P_max, model->dev.n_prims, frame_multi_needs_collide(model->dev)) !=
+        cudaSuccess)
         return HS_ERR_CUDA;  // for this batch's swarms and this model's kernel
     const int nb = ctas ? ctas : cap;
     if (nb < 1 || nb > cap) return HS_ERR_SIZE;

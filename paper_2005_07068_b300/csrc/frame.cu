@@ -40,15 +40,23 @@ constexpr unsigned long long kBarrierWaitNs = 1000000000ull;  // a grid barrier 
 constexpr uint32_t kBarrierPolls = 1u << 26;  // and at most this many polls, should the clock not advance
 
 
+// a particle's FK records, raster records and pixel boxes for up to MP primitives
+template <int MP>
+struct FramePrims {
+    float4 rec[MP * 4];
+    float4 rast[MP * kRastVec];
+    int2 pbox[MP];
+};
+template <>
+struct FramePrims<0> {};  // kept in dynamic shared memory, sized for the model
+
 // NW: warps of the CTA; Col: the kc variants' collision data (CollideShared),
-// or a placeholder byte for kernels launched only for the paper's kc
-template <int NW, class Col = CollideShared>
+// or a placeholder byte for kernels launched only for the paper's kc; MP: see FramePrims
+template <int NW, class Col = CollideShared, int MP = kMaxPrims>
 struct FrameSharedT {
     FkShared fk;                      // model, pose, bone frames
     Col col;                          // the kc variants' collision data
-    float4 rec[kMaxPrims * 4];        // this particle's FK records
-    float4 rast[kMaxPrims * kRastVec];  // their raster records
-    int2 pbox[kMaxPrims];
+    FramePrims<MP> pr;                // this particle's records
     alignas(128) unsigned char tile[NW][kStages][kSlot];
     uint64_t bar[NW][kStages];
     float x[kNdof], v[kNdof], pb[kNdof];  // the particle's state (identical in all its CTAs)
@@ -195,13 +203,13 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
     for (int g = 1; g <= a.gens; ++g) {
         // FK of the current pose (fk_particle starts with a barrier that publishes
         // sh.x); each record's raster form is made by the thread that formed it
-        fk_particle(sh.fk, col, sh.x, a.cam, sh.rec, &sh.kc, a.status, [&](int j, const float* rec) {
+        fk_particle(sh.fk, col, sh.x, a.cam, sh.pr.rec, &sh.kc, a.status, [&](int j, const float* rec) {
             const float4 r4[4] = {make_float4(rec[0], rec[1], rec[2], rec[3]),
                                   make_float4(rec[4], rec[5], rec[6], rec[7]),
                                   make_float4(rec[8], rec[9], rec[10], rec[11]),
                                   make_float4(rec[12], rec[13], rec[14], rec[15])};
-            store_raster(make_raster(r4, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y), sh.rast + kRastVec * j);
-            sh.pbox[j] = make_int2(__float_as_int(rec[14]), __float_as_int(rec[15]));
+            store_raster(make_raster(r4, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y), sh.pr.rast + kRastVec * j);
+            sh.pr.pbox[j] = make_int2(__float_as_int(rec[14]), __float_as_int(rec[15]));
             // the union of the pixel boxes, per warp of record threads
             const int w = j >> 5;
             const uint32_t mask = n_prims >= 32 * (w + 1) ? 0xffffffffu : (1u << (n_prims - 32 * w)) - 1u;
@@ -223,7 +231,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
         long long acc_t = 0;
         uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
         if (box[3] > 0)
-            render_units_warp(sh.rast, sh.pbox, n_prims, box, sh.tile[warp], sh.bar[warp], phases,
+            render_units_warp(sh.pr.rast, sh.pr.pbox, n_prims, box, sh.tile[warp], sh.bar[warp], phases,
                               c * kFrameWarps + warp, C * kFrameWarps, pv, ra, p, lane, acc_t, acc_a, acc_o, acc_h);
         warp_sum(acc_t, acc_a, acc_o, acc_h);
         if (lane == 0) {
@@ -308,12 +316,12 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
     }
     if (alive) {
         // the records and kc of the final positions
-        fk_particle(sh.fk, col, sh.x, a.cam, sh.rec, &sh.kc, a.status);
+        fk_particle(sh.fk, col, sh.x, a.cam, sh.pr.rec, &sh.kc, a.status);
         __syncthreads();
         if (primary) {
             if (a.prims_out)
                 for (int i = t; i < n_prims * 4; i += kFrameThreads)
-                    a.prims_out[(size_t)p * n_prims * 4 + i] = sh.rec[i];
+                    a.prims_out[(size_t)p * n_prims * 4 + i] = sh.pr.rec[i];
             if (t == 0) a.kc[p] = sh.kc;
         }
     }
@@ -363,22 +371,37 @@ __global__ void __launch_bounds__(kFrameThreads, 3)
 // the results equal theirs bit for bit.  If a wait runs out (about a second),
 // HS_DEV_BARRIER_TIMEOUT is set and every CTA stops taking tasks; the last CTA
 // to leave returns the workspace's counters to zero.
-// warps of a task's CTA: four, so that six CTAs share an SM and the latency of
-// one task's serial phases (FK, the swarm scan) hides behind the others'
+// warps of a task's CTA: four, and registers (64) and shared memory (the
+// particle's records sized for the model) for eight CTAs per SM, so that the
+// latency of one task's serial phases (FK, the swarm scan) hides behind the
+// others' (more CTAs of four warps measured faster than fewer of eight, and
+// than CTAs of two warps)
 constexpr int kMultiWarps = 4;
 constexpr int kMultiThreads = kMultiWarps * 32;
+
+// dynamic shared memory of track_frame_multi_kernel: E and pbest_E of the
+// task's swarm [P_max] each, then the particle's FK records, raster records
+// and pixel boxes [n_prims] (16-byte aligned)
+__host__ __device__ inline size_t frame_multi_prims_offset(int P_max) { return ((size_t)P_max * 8 + 15) / 16 * 16; }
+__host__ __device__ inline size_t frame_multi_dyn_bytes(int P_max, int n_prims)
+{
+    return frame_multi_prims_offset(P_max) + (size_t)n_prims * (sizeof(float4) * (4 + kRastVec) + sizeof(int2));
+}
 
 // Model: DevModelCore for the paper's kc (no collision data in shared memory,
 // so more CTAs stay resident), DevModel for the kc variants
 template <class Model>
-__global__ void __launch_bounds__(kMultiThreads, 24 / kMultiWarps)
+__global__ void __launch_bounds__(kMultiThreads, 8)
     track_frame_multi_kernel(const __grid_constant__ Model model, const FrameMultiArgs a)
 {
-    __shared__ FrameSharedT<kMultiWarps, CollideSmem<Model>> sh;
+    __shared__ FrameSharedT<kMultiWarps, CollideSmem<Model>, 0> sh;
     __shared__ int s_task, s_go;
-    extern __shared__ float s_dyn[];  // E [P_max], then pbest_E [P_max] of the task's swarm
+    extern __shared__ __align__(16) float s_dyn[];
     float* s_e = s_dyn;
     float* s_pe = s_dyn + a.P_max;
+    float4* s_rec = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_dyn) + frame_multi_prims_offset(a.P_max));
+    float4* s_rast = s_rec + model.n_prims * 4;
+    int2* s_pbox = reinterpret_cast<int2*>(s_rast + model.n_prims * kRastVec);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int n_prims = model.n_prims;
     const int P_total = a.batch.P_total, G = a.gens;
@@ -497,13 +520,13 @@ __global__ void __launch_bounds__(kMultiThreads, 24 / kMultiWarps)
         // publishes sh.x), raster records, the render of all q's units
         const ParticleView pv{view.W, view.H, view.depth_f32, view.inv_fx, view.off_x, view.inv_fy, view.off_y,
                               view.stats, &view.tm_depth, &view.tm_skin};
-        fk_particle(sh.fk, col, sh.x, cam, sh.rec, &sh.kc, a.status, [&](int j, const float* rec) {
+        fk_particle(sh.fk, col, sh.x, cam, s_rec, &sh.kc, a.status, [&](int j, const float* rec) {
             const float4 r4[4] = {make_float4(rec[0], rec[1], rec[2], rec[3]),
                                   make_float4(rec[4], rec[5], rec[6], rec[7]),
                                   make_float4(rec[8], rec[9], rec[10], rec[11]),
                                   make_float4(rec[12], rec[13], rec[14], rec[15])};
-            store_raster(make_raster(r4, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y), sh.rast + kRastVec * j);
-            sh.pbox[j] = make_int2(__float_as_int(rec[14]), __float_as_int(rec[15]));
+            store_raster(make_raster(r4, pv.inv_fx, pv.off_x, pv.inv_fy, pv.off_y), s_rast + kRastVec * j);
+            s_pbox[j] = make_int2(__float_as_int(rec[14]), __float_as_int(rec[15]));
             const int w = j >> 5;
             const uint32_t mask = n_prims >= 32 * (w + 1) ? 0xffffffffu : (1u << (n_prims - 32 * w)) - 1u;
             const int u0 = __reduce_min_sync(mask, lo_i16(rec[14])), v0 = __reduce_min_sync(mask, hi_i16(rec[14]));
@@ -524,7 +547,7 @@ __global__ void __launch_bounds__(kMultiThreads, 24 / kMultiWarps)
         uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
         bool ok = true;
         if (box[3] > 0)
-            ok = render_units_warp(sh.rast, sh.pbox, n_prims, box, sh.tile[warp], sh.bar[warp], phases, warp,
+            ok = render_units_warp(s_rast, s_pbox, n_prims, box, sh.tile[warp], sh.bar[warp], phases, warp,
                                    kMultiWarps, pv, ra, q, lane, acc_t, acc_a, acc_o, acc_h);
         warp_sum(acc_t, acc_a, acc_o, acc_h);
         if (lane == 0) {
@@ -613,18 +636,19 @@ cudaError_t launch_track_frame(const DevModel& model, const CUtensorMap& tm_dept
 }
 
 
-// the batch frame: the same static part, dynamic shared memory for the
-// largest swarm of the batch (2 P_max floats); one kernel per model type
+// the batch frame: its static part, then dynamic shared memory for the
+// largest swarm of the batch and the model's primitives; one kernel per model type
 static std::atomic<uint32_t> g_frame_multi_opted[2][64];
 template <class Model>
 static cudaError_t frame_multi_smem_opt_in()
 {
-    return opt_in_dynamic_smem(track_frame_multi_kernel<Model>, 2 * HS_FRAME_MAX_PARTICLES * (int)sizeof(float),
+    return opt_in_dynamic_smem(track_frame_multi_kernel<Model>,
+                               (int)frame_multi_dyn_bytes(HS_FRAME_MAX_PARTICLES, kMaxPrims),
                                g_frame_multi_opted[std::is_same<Model, DevModel>::value ? 1 : 0]);
 }
 
 template <class Model>
-static cudaError_t frame_multi_capacity_of(int* ctas, int P_max)
+static cudaError_t frame_multi_capacity_of(int* ctas, int P_max, int n_prims)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -632,14 +656,15 @@ static cudaError_t frame_multi_capacity_of(int* ctas, int P_max)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_frame_multi_kernel<Model>, kMultiThreads,
-                                                          2 * (size_t)P_max * sizeof(float));
+                                                          frame_multi_dyn_bytes(P_max, n_prims));
     *ctas = e == cudaSuccess ? sms * per_sm : 0;
     return e;
 }
 
-cudaError_t track_frame_multi_capacity(int* ctas, int P_max, bool collide)
+cudaError_t track_frame_multi_capacity(int* ctas, int P_max, int n_prims, bool collide)
 {
-    return collide ? frame_multi_capacity_of<DevModel>(ctas, P_max) : frame_multi_capacity_of<DevModelCore>(ctas, P_max);
+    return collide ? frame_multi_capacity_of<DevModel>(ctas, P_max, n_prims)
+                   : frame_multi_capacity_of<DevModelCore>(ctas, P_max, n_prims);
 }
 
 template <class Model>
@@ -650,7 +675,7 @@ static cudaError_t launch_frame_multi_as(const Model& model, const FrameMultiArg
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ctas);
     cfg.blockDim = dim3(kMultiThreads);
-    cfg.dynamicSmemBytes = 2 * (size_t)args.P_max * sizeof(float);
+    cfg.dynamicSmemBytes = frame_multi_dyn_bytes(args.P_max, model.n_prims);
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident at once (tasks wait on other CTAs' tasks)

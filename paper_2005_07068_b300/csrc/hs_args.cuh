@@ -268,9 +268,10 @@ cudaError_t launch_track_frame(const DevModel& model, const CUtensorMap& tm_dept
                                const FrameArgs& args, int ctas, cudaStream_t stream);
 cudaError_t track_frame_capacity(int* ctas);  // co-resident CTAs of track_frame_kernel on the current device
 cudaError_t launch_track_frame_multi(const DevModel& model, const FrameMultiArgs& args, int ctas, cudaStream_t stream);
-// co-resident CTAs of track_frame_multi_kernel with shared memory for swarms of up to P_max particles; collide:
-// the kernel of a kc variant, which keeps the model's collision data in shared memory (fewer CTAs)
-cudaError_t track_frame_multi_capacity(int* ctas, int P_max, bool collide);
+// co-resident CTAs of track_frame_multi_kernel with shared memory for swarms of up to P_max particles and a model
+// of n_prims primitives; collide: the kernel of a kc variant, which keeps the model's collision data in shared
+// memory (fewer CTAs)
+cudaError_t track_frame_multi_capacity(int* ctas, int P_max, int n_prims, bool collide);
 // whether a model's kc variant needs its collision data in the kernels
 inline bool frame_multi_needs_collide(const DevModelCore& m) { return m.kc_variant != HS_KC_ABDUCTION; }
 cudaError_t launch_render_score(const CUtensorMap& tm_depth, const CUtensorMap& tm_skin, const RenderArgs& args,

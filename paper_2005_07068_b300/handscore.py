@@ -612,8 +612,9 @@ def new_frame_multi_workspace(batch: Batch, device="cuda") -> torch.Tensor:
 
 def frame_multi_capacity(batch: Batch | None = None, model: Model | None = None) -> int:
     """CTAs of track_frame_multi the current device keeps resident at once for
-    this batch (None: for any batch) and model (None: one with the paper's kc;
-    a kc variant with the interpenetration test leaves room for fewer)."""
+    this batch (None: for any batch) and model (None: any model with the
+    paper's kc; a kc variant with the interpenetration test leaves room for
+    fewer)."""
     n = ctypes.c_int()
     _check("hs_frame_multi_capacity",
            lib().hs_frame_multi_capacity(model.handle if model is not None else None,

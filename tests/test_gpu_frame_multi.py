@@ -181,7 +181,7 @@ def test_batch_frame_rejects_bad_arguments(scenes):
                              ft.fws if ws is None else ws, ft.prims, ft.kc)
 
     cap = hs.frame_multi_capacity(b, m)
-    assert cap == hs.frame_multi_capacity(b)  # the paper's kc: the model's default
+    assert cap >= hs.frame_multi_capacity(b)  # (None: any model, up to HS_MAX_PRIMS primitives)
     assert cap >= hs.frame_multi_capacity() >= torch.cuda.get_device_properties(0).multi_processor_count
     for kw, status in ((dict(ctas=cap + 1), hs.HS_ERR_SIZE),
                        (dict(ctas=-1), hs.HS_ERR_ARG),

@@ -29,46 +29,56 @@ namespace hs {
 constexpr uint32_t kEmptyKey = 0x7f800000u;  // +inf: no hit
 constexpr int kMaxDevices = 64;
 
-// byte offsets of the dynamic shared memory of a TW x TH tile
-template <int TW, int TH>
+__host__ __device__ constexpr int tile_align16(int x) { return (x + 15) / 16 * 16; }
+
+// byte offsets of the dynamic shared memory of a TW x TH tile of a CTA of NW
+// warps: the tile's buffers, then arrays sized for the model's n primitives
+template <int TW, int TH, int NW>
 struct TileLayout {
     static constexpr int kBoxes = (TW / 16) * (TH / 4);  // 16 x 4 TMA boxes per tile
-    static constexpr int kRast = 0;                       // float4 [kMaxPrims][kRastVec]: raster records
-    static constexpr int kPBox = kRast + kMaxPrims * 16 * kRastVec;  // int2 [kMaxPrims]: packed pixel boxes
-    static constexpr int kZ = kPBox + kMaxPrims * 8;      // u32 [TH][TW]: depth bits
-    static constexpr int kDepth = kZ + TW * TH * 4;       // box b at b * 256 (16 x 4 x <= 4 bytes)
+    static constexpr int kDepth = 0;                      // box b at b * 256 (16 x 4 x <= 4 bytes)
     static constexpr int kSkin = kDepth + kBoxes * 256;   // box b at b * 128 (16 x 4 bytes)
-    static constexpr int kRect = kSkin + kBoxes * 128;    // int4 [kMaxPrims]: x0, y0, w, pixels
-    static constexpr int kMagic = kRect + kMaxPrims * 16; // u32 [kMaxPrims]: ~2^31 / w, rounded up
-    static constexpr int kPre = kMagic + kMaxPrims * 4;   // int [kMaxPrims + 1]: first chunk of each entry
-    static constexpr int kList = kPre + (kMaxPrims + 4) * 4;  // int [kMaxPrims]: primitive of each entry
-    static constexpr int kRed = kList + kMaxPrims * 4;    // per-warp sums: i64 + 3 u32
-    static constexpr int kBar = kRed + 16 * 16;           // mbarrier
-    static constexpr int kBox = kBar + 16;                // int [8]
-    static constexpr int kBytes = kBox + 32;
+    static constexpr int kZ = kSkin + kBoxes * 128;       // u32 [TH][TW]: depth bits
+    static constexpr int kRast = kZ + TW * TH * 4;        // float4 [n][kRastVec]: raster records
+    int pbox, rect, magic, pre, list, red, bar, box, bytes;
+    __host__ __device__ explicit TileLayout(int n)
+    {
+        pbox = kRast + n * 16 * kRastVec;   // int2 [n]: packed pixel boxes
+        rect = tile_align16(pbox + n * 8);  // int4 [n]: x0, y0, w, pixels
+        magic = rect + n * 16;              // u32 [n]: ~2^31 / w, rounded up
+        pre = tile_align16(magic + n * 4);  // int [n + 1]: first chunk of each entry
+        list = tile_align16(pre + (n + 1) * 4);  // int [n]: primitive of each entry
+        red = tile_align16(list + n * 4);   // per-warp sums: i64 [NW], then u32 [NW][3]
+        bar = tile_align16(red + 20 * NW);  // mbarrier
+        box = bar + 16;                     // int [8]
+        bytes = box + 32;
+    }
     static_assert(TW % 16 == 0 && TH % 4 == 0, "tiles are made of 16 x 4 TMA boxes");
     static_assert((TW & (TW - 1)) == 0, "TW is a power of two");
     static_assert(kDepth % 128 == 0 && kSkin % 128 == 0, "TMA destinations are 128-byte aligned");
 };
 
+// 64 registers: eight CTAs of four warps per SM (the arrays sized for the
+// model, not for kMaxPrims, leave the shared memory for them)
 template <int TW, int TH, int NW>
-__global__ void __launch_bounds__(NW * 32, 24 / NW)
+__global__ void __launch_bounds__(NW * 32, 32 / NW)
     render_tiles_kernel(const __grid_constant__ CUtensorMap tm_depth, const __grid_constant__ CUtensorMap tm_skin,
                         const RenderArgs a)
 {
-    using Lay = TileLayout<TW, TH>;
+    using Lay = TileLayout<TW, TH, NW>;
+    const Lay L(a.n_prims);
     extern __shared__ __align__(128) unsigned char smem[];
     float4* s_rast = reinterpret_cast<float4*>(smem + Lay::kRast);
-    int2* s_pbox = reinterpret_cast<int2*>(smem + Lay::kPBox);
+    int2* s_pbox = reinterpret_cast<int2*>(smem + L.pbox);
     uint32_t* s_z = reinterpret_cast<uint32_t*>(smem + Lay::kZ);
     unsigned char* s_depth = smem + Lay::kDepth;
     unsigned char* s_skin = smem + Lay::kSkin;
-    int4* s_rect = reinterpret_cast<int4*>(smem + Lay::kRect);
-    uint32_t* s_magic = reinterpret_cast<uint32_t*>(smem + Lay::kMagic);
-    int* s_pre = reinterpret_cast<int*>(smem + Lay::kPre);
-    int* s_list = reinterpret_cast<int*>(smem + Lay::kList);
-    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + Lay::kBar);
-    int* s_box = reinterpret_cast<int*>(smem + Lay::kBox);
+    int4* s_rect = reinterpret_cast<int4*>(smem + L.rect);
+    uint32_t* s_magic = reinterpret_cast<uint32_t*>(smem + L.magic);
+    int* s_pre = reinterpret_cast<int*>(smem + L.pre);
+    int* s_list = reinterpret_cast<int*>(smem + L.list);
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+    int* s_box = reinterpret_cast<int*>(smem + L.box);
 
     const int p = a.order ? a.order[blockIdx.y] : (int)blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -259,8 +269,8 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
         acc_o += __shfl_xor_sync(0xffffffffu, acc_o, o);
         acc_h += __shfl_xor_sync(0xffffffffu, acc_h, o);
     }
-    long long* red_t = reinterpret_cast<long long*>(smem + Lay::kRed);
-    uint32_t* red_c = reinterpret_cast<uint32_t*>(smem + Lay::kRed + 8 * NW);
+    long long* red_t = reinterpret_cast<long long*>(smem + L.red);
+    uint32_t* red_c = reinterpret_cast<uint32_t*>(smem + L.red + 8 * NW);
     if (lane == 0) {
         red_t[warp] = acc_t;
         red_c[3 * warp] = acc_a;
@@ -283,8 +293,7 @@ template <int TW, int TH, int NW>
 static cudaError_t launch_tiles(const CUtensorMap& tm_depth, const CUtensorMap& tm_skin, const RenderArgs& args,
                                 cudaStream_t stream)
 {
-    using Lay = TileLayout<TW, TH>;
-    static_assert(Lay::kRed + 8 * NW + 12 * NW <= Lay::kBar, "reduction scratch");
+    using Lay = TileLayout<TW, TH, NW>;
     auto kern = render_tiles_kernel<TW, TH, NW>;
     // the shared-memory opt-in, once per device
     static std::atomic<uint32_t> opted[kMaxDevices];
@@ -293,14 +302,14 @@ static cudaError_t launch_tiles(const CUtensorMap& tm_depth, const CUtensorMap& 
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     if (!opted[dev].load(std::memory_order_acquire)) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::kBytes);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay(kMaxPrims).bytes);
         if (e != cudaSuccess) return e;
         opted[dev].store(1u, std::memory_order_release);
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(args.K, args.P);
     cfg.blockDim = dim3(NW * 32);
-    cfg.dynamicSmemBytes = Lay::kBytes;
+    cfg.dynamicSmemBytes = Lay(args.n_prims).bytes;
     cfg.stream = stream;
     cudaLaunchAttribute attr_pdl[1];
     attr_pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

@@ -586,9 +586,10 @@ int polish_keep_better(float* x, float* E, const int32_t* sel, int k, const floa
                        const float* E_new, hs_stream_t stream);
 
 /* ---- render autotuning -----------------------------------------------------------
- * Time every render kernel (HS_RENDER_UNITS .. HS_RENDER_TILES_64x64) with CTAs
+ * Time every render kernel (HS_RENDER_UNITS .. HS_RENDER_VARIANTS - 1) with CTAs
  * per particle from {automatic, 1, 2, 4, 8, 16, 32} (more than 1 only while
- * K * P stays within about four resident waves) on the caller's own inputs, and
+ * K * P stays within about four resident waves; the persistent kernels take
+ * none) on the caller's own inputs, and
  * write the fastest into params->variant and params->ctas_per_particle (the
  * Eq. 4-5 constants are kept).  The choice never changes results, only time.
  * Each candidate's `reps` calls are captured into a CUDA graph on a private

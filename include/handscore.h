@@ -559,8 +559,10 @@ int soft_score(const HsModel* model, const HsObs* obs, const HsCamera* cam, cons
 int soft_score_backward(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsPrim* prims, int P,
                         const HsScoreParams* params, const HsSoftParams* soft, const float* sums, int64_t* adj,
                         hs_stream_t stream);
-/* dE_s / d pose [P][26] from the record adjoints (forward-mode tangents of the
- * FK, Eq. 1-3) plus lambda_k dkc/dpose; zero for a parameter outside its
+/* dE_s / d pose [P][26] from the record adjoints (the FK's tangents, Eq. 1-3:
+ * each joint angle turns the bones below it about its world axis) plus
+ * lambda_k dkc/dpose (and, with a kc variant, the interpenetration term's
+ * derivative); zero for a parameter outside its
  * limits (the FK clamps it).  Rewrites prims/kc with pose_fk's values and
  * clears adj. */
 int pose_grad(const HsModel* model, const float* poses, int P, const HsCamera* cam, const HsScoreParams* params,

@@ -162,6 +162,7 @@ _SIGS = {
                            ctypes.c_int, _vp, ctypes.c_size_t, _vp, _vp, _vp], ctypes.c_int),
 }
 NOALLOC_SCRATCH_BYTES = 256 * 1024
+MAX_PRIMS = 64
 MAX_PARTICLES = 65535
 FUSED_MAX_PARTICLES = 4096
 FRAME_MAX_PARTICLES = 1024

@@ -33,6 +33,32 @@ def geometry_f32():
     return g
 
 
+def geometry_max_prims():
+    """The seeded hand with extra ellipsoids up to the library's limit of
+    primitives (HS_MAX_PRIMS): small ones on each finger bone beside the
+    phalanx (some stand out of the hand, some are hidden) and flat ones on the
+    back of the palm, so that every kernel's per-primitive arrays are full."""
+    g = geometry_f32()
+    n0 = g.prims_i.shape[0]
+    extra = hs.MAX_PRIMS - n0
+    pi = np.zeros((extra, 2), np.int32)
+    pf = np.zeros((extra, 7))
+    for e in range(extra):
+        b = 1 + e % (g.bones_i.shape[0] - 1) if e < extra - 3 else 0
+        if b:
+            side = 1.0 if e % 2 else -1.0
+            pi[e] = (b, I.PRIM_ELLIPSOID)
+            pf[e, :3] = (side * (5.0 + 0.5 * (e % 5)), 8.0 + e % 7, 2.0 * side)
+            pf[e, 3:6] = (3.0 + 0.25 * (e % 4), 4.0, 3.0)
+        else:
+            pi[e] = (0, I.PRIM_ELLIPSOID)
+            pf[e, :3] = (-20.0 + 20.0 * (e - (extra - 3)), 40.0, -9.0)
+            pf[e, 3:6] = (9.0, 12.0, 3.0)
+    g.prims_i = np.concatenate([g.prims_i, pi])
+    g.prims_f = np.concatenate([g.prims_f, pf.astype(np.float32).astype(np.float64)])
+    return g
+
+
 @dataclass
 class Scene:
     W: int
@@ -47,8 +73,8 @@ class Scene:
 
 
 def make_scene(W, H, P, seed, *, zoom=1.0, noisy=False, f32=True, spread=1.0, shift=(0.0, 0.0),
-               cam=None) -> Scene:
-    g = geometry_f32()
+               cam=None, geometry=None) -> Scene:
+    g = geometry_f32() if geometry is None else geometry
     lo, hi = I.search_limits()
     if cam is None:
         cam = oracle.camera_tuple(I.kinect_camera(W, H))

@@ -227,3 +227,21 @@ def test_batch_frame_autotune_keeps_state(scenes):
         assert _equal(x, y), k
     assert hs.hs_get_device_status(clear=True) == 0
 
+
+def test_batch_frame_max_primitive_model():
+    """A model with HS_MAX_PRIMS primitives: the frame kernel's shared memory is
+    sized for the model's primitives, so this is its largest layout; the frame
+    still equals the step-by-step calls bit for bit."""
+    g = C.geometry_max_prims()
+    sub = [C.make_scene(W, H, P, seed, geometry=g, **kw) for W, H, P, seed, kw in SWARMS[:3]]
+    m = sub[0].model_g
+    assert m.n_prims == hs.MAX_PRIMS
+    obs, b = _batch(sub)
+    starts = torch.from_numpy(np.stack([sc.gt for sc in sub]).astype(np.float32)).cuda()
+    assert torch.cuda.get_device_properties(0).multi_processor_count <= hs.frame_multi_capacity(b, m)
+    ref = _run(T.BatchTracker(m, b, gens=3), 1, starts)
+    got = _run(T.BatchFrameTracker(m, b, gens=3), 1, starts)
+    for k, (x, y) in enumerate(zip(got[0], ref[0])):
+        assert _equal(x, y), k
+    assert hs.hs_get_device_status(clear=True) == 0
+

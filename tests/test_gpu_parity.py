@@ -152,24 +152,40 @@ def test_render_score_parity(name, W, H, P, seed, kw, variant):
     REPORT[f"{name}/variant{variant}"] = rep
 
 
+def _assert_same_bits(gr, ref, v):
+    assert np.array_equal(gr.parts, ref.parts), v
+    assert np.array_equal(gr.E.view(np.uint32), ref.E.view(np.uint32)), v
+    if ref.depth is not None and gr.depth is not None:
+        assert np.array_equal(gr.mask, ref.mask), v
+        assert np.array_equal(gr.depth.view(np.uint32), ref.depth.view(np.uint32)), v
+
+
 @pytest.mark.parametrize("ctas", [1, 3, 16])
 def test_render_variants_agree(ctas):
-    """Every render kernel and launch shape gives the same counts and E (they
-    share the nearest-hit rule and integer sums; only the work layout differs)."""
+    """Every render kernel and launch shape gives the same depth, masks,
+    counts and E bit for bit: they share the nearest-hit rule (the smallest
+    float depth of one arithmetic), the per-pixel terms and the integer sums;
+    only the work layout differs."""
     sc = C.make_scene(200, 150, 40, 2005070683, noisy=True, f32=False, spread=1.5)
     ref = C.run_gpu(sc, debug=True, variant=hs.RENDER_UNITS)
     for v in sorted(set(hs.RENDER_VARIANTS.values()) - {hs.RENDER_AUTO}):
-        gr = C.run_gpu(sc, debug=True, variant=v, ctas=ctas)
-        assert np.array_equal(gr.parts[:, 1:], ref.parts[:, 1:]), v
-        assert np.array_equal(gr.mask, ref.mask), v
-        assert np.abs(gr.depth - ref.depth).max() <= 1e-4, v
-        assert np.all(np.abs(gr.E - ref.E) <= 1e-6 * np.abs(ref.E) + 1e-5), v
-        if v in (hs.RENDER_STRIPS_8x16, hs.RENDER_STRIPS_8x32):
-            # the strip kernels run the unit kernel's arithmetic with the column
-            # terms formed once: the same nearest hit and sums, bit for bit
-            assert np.array_equal(gr.depth.view(np.uint32), ref.depth.view(np.uint32)), v
-            assert np.array_equal(gr.E.view(np.uint32), ref.E.view(np.uint32)), v
-            assert np.array_equal(gr.parts, ref.parts), v
+        _assert_same_bits(C.run_gpu(sc, debug=True, variant=v, ctas=ctas), ref, v)
+
+
+def test_max_primitive_model_every_kernel():
+    """A model with the library's limit of HS_MAX_PRIMS primitives (the hand
+    plus 27 small ellipsoids) fills every kernel's per-primitive arrays, which
+    the tile kernels size for the model: the unit kernel against the FP64
+    oracle with the full protocol, every other kernel bit-identical to it."""
+    sc = C.make_scene(160, 120, 24, 812, noisy=True, f32=False, geometry=C.geometry_max_prims())
+    assert sc.model_g.n_prims == hs.MAX_PRIMS
+    ref = C.run_gpu(sc, debug=True, variant=hs.RENDER_UNITS)
+    rep = {}
+    C.check_parity(sc, ref, C.run_oracle(sc), rep)
+    REPORT["max_prims_160x120"] = rep
+    for v in sorted(set(hs.RENDER_VARIANTS.values()) - {hs.RENDER_AUTO, hs.RENDER_UNITS}):
+        _assert_same_bits(C.run_gpu(sc, debug=True, variant=v), ref, v)
+    assert hs.hs_get_device_status(clear=True) == 0
 
 
 def test_ground_truth_scores_zero_depth_term():

@@ -107,6 +107,9 @@ def parse():
     ap.add_argument("--methods", default="plain,hybrid",
                     help="fullframe: plain (PSO) and/or hybrid (PSO + gradient polish of the k best particles)")
     ap.add_argument("--polish", default="8,5", help="fullframe: hybrid polish: particles k, descent steps")
+    ap.add_argument("--log", default="", help="fullframe: append JSON lines (every generation's best and mean E "
+                    "and the best pose's joint error, one line per setting) to this file; the per-generation "
+                    "copies add a little time to every frame")
     ap.add_argument("--kc", default="0,0", help="fullframe: kc variant and penetration weight (rad/mm): 0 = the "
                     "paper's, 1 = plus the interpenetration of different fingers, 2 = interpenetration only")
     return ap.parse_args()
@@ -891,6 +894,10 @@ def run_fullframe(args, rank, world, local):
     pk = fp32_xu_peaks(dev, peaks)
     settings, per_p = [], []
     gen_budgets = [int(v) for v in args.gens.split(",") if v]
+    log = None
+    if args.log and rank == 0:
+        from paper_2005_07068_b300.runlog import RunLog
+        log = RunLog(args.log)
     with ClockSampler(local) as clk:
         for P in [int(v) for v in args.particles.split(",") if v]:
             score = hs.score_params(variant=hs.RENDER_VARIANTS.get(args.render, 0), ctas_per_particle=args.ctas)
@@ -902,17 +909,21 @@ def run_fullframe(args, rank, world, local):
                 del tuner
             for method in methods:
                 for G in gen_budgets:
+                    hist = log is not None
                     if method == "plain":
-                        trk = Tracker(model, cam, P, G, seed=seed, device=dev, score=score)
+                        trk = Tracker(model, cam, P, G, seed=seed, device=dev, score=score, record_history=hist)
                     else:
                         trk = HybridTracker(model, cam, P, G, seed=seed, device=dev, score=score,
-                                            k=min(k_pol, P), steps=steps_pol)
-                    results = SW.track_sequence(trk, obs, traj, start, frames=frames)
+                                            k=min(k_pol, P), steps=steps_pol, record_history=hist)
+                    results = SW.track_sequence(trk, obs, traj, start, frames=frames, log=log, method=method,
+                                                particles=P, generations=G)
                     summ = SW.summarize(results)
                     summ.update({"method": method, "particles": P, "generations": G,
                                  "evals_per_s": P * G * frames / (sum(r.frame_ms for r in results) * 1e-3),
                                  "launches_per_frame": trk.launches_per_frame()})
                     settings.append(summ)
+                    if log is not None:
+                        log.run(**summ)
                     del trk
             # render roofline at this P: generations of frame 0 replayed back to back
             rec = fullframe_render_roofline(hs, I, model, kinds, pk, dev, P, seed, FULL_W, FULL_H, obs=obs[0],
@@ -921,6 +932,10 @@ def run_fullframe(args, rank, world, local):
             per_p.append(rec)
     clocks = clk.summary(peaks.get("sm_max_mhz", 2032.0))
     best = SW.fastest_within(settings, 0.9)
+    if log is not None:
+        for rec in per_p:
+            log.run(record="render roofline", **{k: v for k, v in rec.items() if k != "autotune_us"})
+        log.close()
     if rank == 0:
         work = FULL_WORKLOAD.format(W=FULL_W, H=FULL_H, F=frames, M=" / ".join(methods), P=args.particles,
                                     G=args.gens)

@@ -32,9 +32,11 @@ class FrameResult:
     final_E: float
 
 
-def track_sequence(trk, obs: list, gt: np.ndarray, start: torch.Tensor, frames: int | None = None
-                   ) -> list[FrameResult]:
-    """Track obs[0..frames) with `trk` (a Tracker), frame 0 from `start`."""
+def track_sequence(trk, obs: list, gt: np.ndarray, start: torch.Tensor, frames: int | None = None,
+                   log=None, **log_fields) -> list[FrameResult]:
+    """Track obs[0..frames) with `trk` (a Tracker), frame 0 from `start`.  With
+    `log` (a runlog.RunLog; the tracker built with record_history=True), every
+    frame's generations are written to it, tagged with log_fields."""
     n = len(obs) if frames is None else min(frames, len(obs))
     stream = torch.cuda.current_stream()
     graphs = [trk.graph(obs[f], f, start if f == 0 else None) for f in range(n)]
@@ -48,6 +50,8 @@ def track_sequence(trk, obs: list, gt: np.ndarray, start: torch.Tensor, frames: 
         gbest = trk.swarm.gbest.cpu().numpy()
         out.append(FrameResult(f, e0.elapsed_time(e1), float(mean_joint_error_deg(gbest, gt[f])),
                                float(trk.swarm.gbest_E.cpu()[0])))
+        if log is not None:
+            log.frame_from(trk, f, gt[f], frame_ms=out[-1].frame_ms, **log_fields)
     return out
 
 

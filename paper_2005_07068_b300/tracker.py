@@ -54,8 +54,11 @@ class Tracker:
         self.kc = torch.zeros(P, **f)
         self.ws = hs.new_workspace(P, self.device)
         self.seed_pose = torch.zeros(26, **f)
+        # record_history: each generation's global best and E kept on the device
+        # by the frame's graph (runlog.RunLog reads them after the frame)
         self.record_history = record_history
         self.history = torch.zeros(gens, 27, **f) if record_history else None
+        self.history_E = torch.zeros(gens, P, **f) if record_history else None
         self._graphs: dict = {}
 
     # ---- one frame, enqueued on the current stream ---------------------------------
@@ -71,6 +74,8 @@ class Tracker:
         for g in range(1, self.gens + 1):
             hs.render_score_batch(self.model, obs, self.cam, self.prims, self.kc, self.score, self.ws, self.swarm.E)
             self._after_render(obs, cur)
+            if self.record_history:
+                self.history_E[g - 1].copy_(self.swarm.E)
             self.swarm.x = cur
             hs.pso_step_fk(self.model, self.swarm, nxt, self.pso, self.seed, frame, g, self.cam, self.prims, self.kc)
             cur, nxt = nxt, cur
@@ -147,6 +152,8 @@ class FrameTracker(Tracker):
         super().__init__(model, cam, P, gens, **kw)
         if P > hs.FRAME_MAX_PARTICLES:
             raise ValueError(f"track_frame takes at most {hs.FRAME_MAX_PARTICLES} particles")
+        if self.record_history:
+            raise ValueError("the per-generation history is recorded by the step-by-step path (Tracker) only")
         self.ctas = ctas
         self.fws = hs.new_frame_workspace(P, self.device)
 

@@ -199,8 +199,8 @@ class _Nvml:
 
 
 class ClockSampler:
-    """SM clock and throttle reasons sampled every 2 ms through NVML
-    (read-only), so that even a short timed region gets several samples (the
+    """SM clock and throttle reasons sampled every 0.5 ms through NVML
+    (read-only), so that even a short timed region gets dozens of samples (the
     host enqueues the timed steps ahead of the GPU, so the sampler's brief
     turns on the interpreter do not open gaps on the device)."""
     HW, HW_THERMAL, SW_THERMAL, SW_POWER = 0x8, 0x40, 0x20, 0x4
@@ -228,7 +228,7 @@ class ClockSampler:
                     self.samples.append((self._nv.clock(), self._nv.reasons()))
                 except Exception:
                     pass
-                self._stop.wait(0.002)
+                self._stop.wait(0.0005)
 
         self._t = threading.Thread(target=run, daemon=True)
         self._t.start()
@@ -247,7 +247,7 @@ class ClockSampler:
                  self.SW_THERMAL: "sw_thermal_slowdown", self.SW_POWER: "sw_power_cap"}
         reasons = sorted({n for _, r in self.samples for bit, n in names.items() if r & bit})
         return {"sm_mhz": statistics.median(sm for sm, _ in self.samples), "sm_max_mhz": self.max_mhz,
-                "reasons": reasons, "samples": len(self.samples), "source": "NVML every 2 ms"}
+                "reasons": reasons, "samples": len(self.samples), "source": "NVML every 0.5 ms"}
 
 
 # ---- synthetic frames ----------------------------------------------------------------------

@@ -231,8 +231,7 @@ def test_many_particles_sampled():
     sc = C.make_scene(64, 64, 1500, 105, spread=2.0)
     gr = C.run_gpu(sc, debug=False)
     gt = C.run_gpu(sc, debug=False, variant=hs.RENDER_TILES_64x32)
-    assert np.all(np.abs(gt.E - gr.E) <= 1e-6 * np.abs(gr.E) + 1e-5)
-    assert np.array_equal(gt.parts[:, 1:], gr.parts[:, 1:])
+    _assert_same_bits(gt, gr, hs.RENDER_TILES_64x32)
     o = C.run_oracle(sc, per_pixel=False)
     err = np.abs(gr.E - o["E"])
     ok = err <= C.E_REL_TOL * np.abs(o["E"]) + C.E_ABS_TOL
@@ -247,6 +246,34 @@ def test_many_particles_sampled():
         # a particle outside the direct tolerance is explained by a boundary flip
         # (check_parity has then passed its conditional E check)
         assert np.all(flipped[np.isin(chunk, out)])
+
+
+def test_maximum_particle_count():
+    """P = HS_MAX_PARTICLES (65535) in one call at a small ROI: every particle's E
+    and counts equal those of the same particles scored in two separate calls
+    (a particle's result depends on it alone), with the automatic kernel and the
+    64x32 tiles; 64 sampled particles against the FP64 oracle with the full
+    per-pixel protocol."""
+    sc = C.make_scene(40, 30, 64, 813, noisy=True, f32=False, spread=2.0)
+    P = hs.MAX_PARTICLES
+    rng = np.random.default_rng(813)
+    lo, hi = (a.astype(np.float32) for a in I.search_limits())
+    poses = np.resize(sc.poses, (P, 26)).astype(np.float64)
+    poses[64:] += 0.3 * rng.uniform(-1, 1, (P - 64, 26)) * I.perturbation_scale()
+    poses = np.clip(poses, lo, hi).astype(np.float32)
+    half = P // 2
+    for v in (hs.RENDER_AUTO, hs.RENDER_TILES_64x32):
+        full = C.run_gpu(sc, debug=False, poses=poses, variant=v)
+        a = C.run_gpu(sc, debug=False, poses=poses[:half], variant=v)
+        b = C.run_gpu(sc, debug=False, poses=poses[half:], variant=v)
+        assert np.array_equal(full.E.view(np.uint32), np.concatenate([a.E, b.E]).view(np.uint32)), v
+        assert np.array_equal(full.parts, np.concatenate([a.parts, b.parts])), v
+    idx = np.sort(rng.choice(P, 64, replace=False))
+    sub = C.Scene(sc.W, sc.H, sc.cam, sc.gt, sc.Od, sc.S, poses[idx], sc.model_o, sc.model_g)
+    gs = C.run_gpu(sub)
+    assert np.array_equal(gs.E.view(np.uint32), full.E[idx].view(np.uint32))
+    C.check_parity(sub, gs, C.run_oracle(sub))
+    assert hs.hs_get_device_status(clear=True) == 0
 
 
 def test_deterministic_repeat():

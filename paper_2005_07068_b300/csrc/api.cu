@@ -89,7 +89,7 @@ static int validate_cam(const HsCamera* c)
 
 constexpr int kMaxK = 16;             // default cap of CTAs per particle in the render
 constexpr int kMaxCtasPerParticle = 64;
-constexpr int kTargetCtas = 148 * 6;  // one resident wave (6 CTAs of 4 warps per SM)
+constexpr int kTargetCtas = 148 * 6;  // one resident wave of the unit and strip kernels (6 CTAs of 4 warps per SM)
 
 }  // namespace hs
 

@@ -101,7 +101,8 @@ def parse():
                          "profiling one kernel); equaltime: hybrid 64 x 20 + polish against plain PSO given the "
                          "same time per frame, on the 320x240 sequence")
     ap.add_argument("--particles", default="256,1024,4096", help="fullframe: swarm sizes")
-    ap.add_argument("--frames", type=int, default=100, help="fullframe: frames of the sequence")
+    ap.add_argument("--frames", type=int, default=None, help="fullframe: frames of the sequence (default 100); "
+                    "equaltime: frames of the Kinect-scale sequence (default 30)")
     ap.add_argument("--gens", default="5,10,20,50", help="fullframe: generation budgets per frame")
     ap.add_argument("--roi", default="640,480", help="fullframe: ROI W,H (the Kinect camera scaled to it)")
     ap.add_argument("--methods", default="plain,hybrid",
@@ -112,7 +113,11 @@ def parse():
                     "copies add a little time to every frame")
     ap.add_argument("--kc", default="0,0", help="fullframe: kc variant and penetration weight (rad/mm): 0 = the "
                     "paper's, 1 = plus the interpenetration of different fingers, 2 = interpenetration only")
-    return ap.parse_args()
+    args = ap.parse_args()
+    args.frames_given = args.frames is not None
+    if args.frames is None:
+        args.frames = 100
+    return args
 
 
 # ---- host-side helpers ---------------------------------------------------------------
@@ -1121,7 +1126,8 @@ def run_equal_time(args, rank, world, local):
     model = hs.Model.from_geometry(g, lo, hi)
     camt = I.kinect_camera(W, H)
     cam = hs.camera(camt.fx, camt.fy, camt.cx, camt.cy)
-    frames = min(args.frames, FRAMES)
+    # the Kinect-scale sequence: its first 30 frames unless --frames asks for more (up to 300)
+    frames = max(2, min(args.frames, 300)) if args.frames_given else FRAMES
     traj, obs, _ = make_frames(seed, frames, hs, I, model, cam, dev)
     rng = np.random.default_rng(seed)
     start = torch.from_numpy(np.clip(traj[0] + rng.uniform(-1, 1, 26) * I.perturbation_scale(), lo, hi)

@@ -248,6 +248,29 @@ def test_many_particles_sampled():
         assert np.all(flipped[np.isin(chunk, out)])
 
 
+@pytest.mark.parametrize("variant", [hs.RENDER_UNITS, hs.RENDER_TILES_64x32, hs.RENDER_STRIPS_8x32])
+def test_degenerate_observations(variant):
+    """The method's degenerate inputs against the oracle: no skin pixel and
+    nothing rendered (a camera whose principal point lies 400 px off the ROI, so
+    every hand projects outside it: an empty union, where Eq. 4's ratio is 0/0
+    and D = lambda by reading R-S7), no skin pixel with the hands rendered (the
+    union is the rendered mask alone), and a depth map that is all holes
+    (O_d = 0: no valid pixel)."""
+    sc = C.make_scene(64, 48, 8, 815, zoom=2.0, noisy=True, f32=False)
+    off = C.make_scene(64, 48, 8, 815, noisy=True, f32=False, cam=(105.0, 105.0, 432.0, 24.0))
+    no_skin = np.zeros_like(sc.S)
+    cases = ((off, off.Od, no_skin), (sc, sc.Od, no_skin), (sc, np.zeros_like(sc.Od), sc.S))
+    for k, (base, Od, S) in enumerate(cases):
+        sub = C.Scene(base.W, base.H, base.cam, base.gt, Od, S, base.poses, base.model_o, base.model_g)
+        gr = C.run_gpu(sub, variant=variant)
+        C.check_parity(sub, gr, C.run_oracle(sub))
+        if k == 0:
+            assert np.all(gr.parts[:, 2] == 0) and np.all(gr.parts[:, 3] == 0)  # nothing rendered, empty union
+            lam, lam_k = C.PARAMS[2], C.PARAMS[3]
+            assert np.allclose(gr.E, lam + lam_k * gr.kc, rtol=1e-6, atol=0)
+    assert hs.hs_get_device_status(clear=True) == 0
+
+
 def test_maximum_particle_count():
     """P = HS_MAX_PARTICLES (65535) in one call at a small ROI: every particle's E
     and counts equal those of the same particles scored in two separate calls

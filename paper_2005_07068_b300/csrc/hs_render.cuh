@@ -376,6 +376,126 @@ __device__ __forceinline__ float2 raster_root_cone2(float t0, float kap, uint32_
     return best;
 }
 
+// ---- primitives in front of the camera ----
+// FK gives a primitive whose solid lies beyond the plane z = 1 mm its screen
+// box, and one that reaches the plane the sentinel box from -32767 (a box
+// clamped there is treated alike).  Every point of a primitive in front has
+// depth >= 1 mm, so a covered pixel's near root lies in front of the camera:
+// the roots' FP32 error (~1e-3 mm at 500 mm) cannot make t0 + s <= 0.  Its
+// renderer may then skip the far root and the tests of positive depth, and
+// the depths are bit for bit those of the general functions above.
+__device__ __forceinline__ bool raster_in_front(int box_u0) { return box_u0 != -32767; }
+
+// raster_root_ellipsoid for a primitive in front, as the depth t0 + s of the
+// near root (the same operations, so the same bits); call where disc >= 0
+__device__ __forceinline__ float raster_z_ellipsoid_front(float t0, const RasterRay& r, float disc)
+{
+    const float A = fmaf(r.hx, r.hx, fmaf(r.hy, r.hy, r.hz * r.hz));
+    const float B = fmaf(r.gx, r.hx, fmaf(r.gy, r.hy, r.gz * r.hz));
+    const float sq = sqrt_approx(disc);
+    const float ia = rcp_approx(A);
+    return t0 + __fmul_rn(-B - sq, ia);
+}
+// raster_root_cone for a primitive in front (no test of positive depth)
+__device__ __forceinline__ float raster_root_cone_front(float kap, uint32_t caps, const RasterRay& r, float disc)
+{
+    float best = INFINITY;
+    if (disc >= 0.f) {
+        const float w0 = fmaf(kap, r.gy, 1.f), w1 = kap * r.hy;
+        const float A = fmaf(r.hx, r.hx, fmaf(r.hz, r.hz, -w1 * w1));
+        const float B = fmaf(r.gx, r.hx, fmaf(r.gz, r.hz, -w0 * w1));
+        const float C = fmaf(r.gx, r.gx, fmaf(r.gz, r.gz, -w0 * w0));
+        const float sq = sqrt_approx(disc);
+        const float qq = -(B + copysignf(sq, B));
+        const float s1 = __fmul_rn(qq, rcp_approx(A));
+        const float s2 = __fmul_rn(C, rcp_approx(qq));
+        const float y1 = fmaf(s1, r.hy, r.gy), y2 = fmaf(s2, r.hy, r.gy);
+        if (fabsf(y1) <= 1.f) best = s1;
+        if (fabsf(y2) <= 1.f) best = fminf(best, s2);
+    }
+    if (caps) {
+        const float ihy = rcp_approx(r.hy);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (!(caps & (1u << c))) continue;
+            const float yc = c ? 1.f : -1.f;
+            const float s = __fmul_rn(yc - r.gy, ihy);
+            const float X = fmaf(s, r.hx, r.gx), Z = fmaf(s, r.hz, r.gz);
+            const float w = 1.f + yc * kap;
+            if (fmaf(X, X, Z * Z) <= w * w) best = fminf(best, s);
+        }
+    }
+    return best;
+}
+// The depth t0 + s of the nearest hit (raster_hit), or +inf; where raster_maybe
+// holds.  front: the primitive is in front of the camera (raster_in_front).
+__device__ __forceinline__ float raster_hit_z(const float4& q2, const float4& q3, const float4& q4, float du, float dv,
+                                              float disc, bool front)
+{
+    const RasterRay r = raster_ray(q2, q3, q4, du, dv);
+    const float t0 = q2.w;
+    if (!front)
+        return t0 + (q3.w > 1.5f ? raster_root_ellipsoid(t0, r, disc)
+                                 : raster_root_cone(t0, q3.w, __float_as_uint(q4.w), r, disc));
+    return q3.w > 1.5f ? raster_z_ellipsoid_front(t0, r, disc)
+                       : t0 + raster_root_cone_front(q3.w, __float_as_uint(q4.w), r, disc);
+}
+
+// raster_root_ellipsoid2 for a primitive in front: the near root s (the same
+// operations, so the same bits), NaN where disc < 0.  The caller selects it
+// by its coverage bits before adding t0, as after the general functions'
+// selects: a packed add that directly follows the root's packed product was
+// measured to round differently (contracted), one ulp on some pixels.
+__device__ __forceinline__ float2 raster_near_ellipsoid2_front(const Ray2& r, float2 disc)
+{
+    const float2 A = __ffma2_rn(r.hx, r.hx, __ffma2_rn(r.hy, r.hy, __fmul2_rn(r.hz, r.hz)));
+    const float2 B = __ffma2_rn(r.gx, r.hx, __ffma2_rn(r.gy, r.hy, __fmul2_rn(r.gz, r.hz)));
+    const float2 sq = make_float2(sqrt_approx(disc.x), sqrt_approx(disc.y));
+    const float2 ia = make_float2(rcp_approx(A.x), rcp_approx(A.y));
+    return __fmul2_rn(__fadd2_rn(neg2(B), neg2(sq)), ia);
+}
+// raster_root_cone2 for a primitive in front (no test of positive depth)
+__device__ __forceinline__ float2 raster_root_cone2_front(float kap, uint32_t caps, const Ray2& r, float2 disc)
+{
+    const float2 kap2 = f2(kap);
+    const float2 w0 = __ffma2_rn(kap2, r.gy, f2(1.f)), w1 = __fmul2_rn(kap2, r.hy);
+    const float2 nw0 = neg2(w0), nw1 = neg2(w1);
+    const float2 A = __ffma2_rn(r.hx, r.hx, __ffma2_rn(r.hz, r.hz, __fmul2_rn(nw1, w1)));
+    const float2 B = __ffma2_rn(r.gx, r.hx, __ffma2_rn(r.gz, r.hz, __fmul2_rn(nw0, w1)));
+    const float2 C = __ffma2_rn(r.gx, r.gx, __ffma2_rn(r.gz, r.gz, __fmul2_rn(nw0, w0)));
+    const float2 sq = make_float2(sqrt_approx(disc.x), sqrt_approx(disc.y));
+    const float2 qq = neg2(__fadd2_rn(B, make_float2(copysignf(sq.x, B.x), copysignf(sq.y, B.y))));
+    const float2 s1 = __fmul2_rn(qq, make_float2(rcp_approx(A.x), rcp_approx(A.y)));
+    const float2 s2 = __fmul2_rn(C, make_float2(rcp_approx(qq.x), rcp_approx(qq.y)));
+    const float2 y1 = __ffma2_rn(s1, r.hy, r.gy), y2 = __ffma2_rn(s2, r.hy, r.gy);
+    float2 best = make_float2(INFINITY, INFINITY);
+    if (disc.x >= 0.f) {
+        if (fabsf(y1.x) <= 1.f) best.x = s1.x;
+        if (fabsf(y2.x) <= 1.f) best.x = fminf(best.x, s2.x);
+    }
+    if (disc.y >= 0.f) {
+        if (fabsf(y1.y) <= 1.f) best.y = s1.y;
+        if (fabsf(y2.y) <= 1.f) best.y = fminf(best.y, s2.y);
+    }
+    if (caps) {
+        const float2 ihy = make_float2(rcp_approx(r.hy.x), rcp_approx(r.hy.y));
+        const float2 ngy = neg2(r.gy);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (!(caps & (1u << c))) continue;
+            const float yc = c ? 1.f : -1.f;
+            const float2 s = __fmul2_rn(__fadd2_rn(f2(yc), ngy), ihy);
+            const float2 X = __ffma2_rn(s, r.hx, r.gx), Z = __ffma2_rn(s, r.hz, r.gz);
+            const float2 rr = __ffma2_rn(X, X, __fmul2_rn(Z, Z));
+            const float w = 1.f + yc * kap;
+            const float ww = w * w;
+            if (rr.x <= ww) best.x = fminf(best.x, s.x);
+            if (rr.y <= ww) best.y = fminf(best.y, s.y);
+        }
+    }
+    return best;
+}
+
 // true when the primitive must be tested at a pixel whose discriminant is disc
 __device__ __forceinline__ bool raster_maybe(const float4& q4, float disc)
 {

@@ -193,8 +193,18 @@ __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2
                         const float t0 = q2.w;
                         const Ray2 r = raster_ray2(q2, q3, q4, make_float2(du0, du1), f2(dv));
                         const float2 disc = make_float2(d0, d1);
-                        const float2 sh = q3.w > 1.5f ? raster_root_ellipsoid2(t0, r, disc)
-                                                      : raster_root_cone2(t0, q3.w, __float_as_uint(q4.w), r, disc);
+                        // in front of the camera (warp-uniform): no far root, no depth tests
+                        const bool front = raster_in_front(lo_i16(__int_as_float(pbox[b + 32 * w].x)));
+                        float2 sh;
+                        if (q3.w > 1.5f && front) {
+                            const float2 sn = raster_near_ellipsoid2_front(r, disc);
+                            sh = make_float2(d0 >= 0.f ? sn.x : INFINITY, d1 >= 0.f ? sn.y : INFINITY);
+                        } else {
+                            const uint32_t capw = __float_as_uint(q4.w);
+                            sh = q3.w > 1.5f ? raster_root_ellipsoid2(t0, r, disc)
+                                 : front     ? raster_root_cone2_front(q3.w, capw, r, disc)
+                                             : raster_root_cone2(t0, q3.w, capw, r, disc);
+                        }
                         const float2 zz = __fadd2_rn(f2(t0), sh);
                         if (v0) z[0] = fminf(z[0], zz.x);
                         if (v1) z[1] = fminf(z[1], zz.y);

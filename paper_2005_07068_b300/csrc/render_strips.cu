@@ -209,23 +209,55 @@ __device__ __forceinline__ bool render_strips_warp(StripShared<SH>& sm, const Re
                 z[s] = fminf(z[s], ((m >> s) & 1u) ? zz.x : INFINITY);
                 z[s + 1] = fminf(z[s + 1], ((m >> (s + 1)) & 1u) ? zz.y : INFINITY);
             };
+            // a primitive in front of the camera (warp-uniform; all of them unless
+            // one reaches the plane z = 1 mm) skips the far root and the depth tests
+            const bool front = raster_in_front(lo_i16(__int_as_float(pb.x)));
             if (q3.w > 1.5f) {  // ellipsoid (warp-uniform)
+                if (front) {
 #pragma unroll
-                for (int s = 0; s < kSteps; s += 2) {
-                    if (!((wm >> s) & 3u)) continue;  // no lane can be hit in either step (warp-uniform)
-                    const float2 dv = __fadd2_rn(make_float2(fy0 + (float)(4 * s), fy0 + (float)(4 * s + 4)), nqy);
-                    const float2 disc = __ffma2_rn(dv, __ffma2_rn(dv, vv2, u12), u02);
-                    take2(s, raster_root_ellipsoid2(t0, raster_ray2(q2, q3, q4, f2(du), dv), disc));
+                    for (int s = 0; s < kSteps; s += 2) {
+                        if (!((wm >> s) & 3u)) continue;  // no lane can be hit in either step (warp-uniform)
+                        const float2 dv =
+                            __fadd2_rn(make_float2(fy0 + (float)(4 * s), fy0 + (float)(4 * s + 4)), nqy);
+                        const float2 disc = __ffma2_rn(dv, __ffma2_rn(dv, vv2, u12), u02);
+                        const float2 sn = raster_near_ellipsoid2_front(raster_ray2(q2, q3, q4, f2(du), dv), disc);
+                        const float2 sh = make_float2(((m >> s) & 1u) ? sn.x : INFINITY,
+                                                      ((m >> (s + 1)) & 1u) ? sn.y : INFINITY);
+                        const float2 zz = __fadd2_rn(f2(t0), sh);
+                        z[s] = fminf(z[s], zz.x);
+                        z[s + 1] = fminf(z[s + 1], zz.y);
+                    }
+                } else {
+#pragma unroll
+                    for (int s = 0; s < kSteps; s += 2) {
+                        if (!((wm >> s) & 3u)) continue;
+                        const float2 dv =
+                            __fadd2_rn(make_float2(fy0 + (float)(4 * s), fy0 + (float)(4 * s + 4)), nqy);
+                        const float2 disc = __ffma2_rn(dv, __ffma2_rn(dv, vv2, u12), u02);
+                        take2(s, raster_root_ellipsoid2(t0, raster_ray2(q2, q3, q4, f2(du), dv), disc));
+                    }
                 }
             } else {
                 const float kap = q3.w;
                 const uint32_t capw = __float_as_uint(q4.w);
+                if (front) {
 #pragma unroll
-                for (int s = 0; s < kSteps; s += 2) {
-                    if (!((wm >> s) & 3u)) continue;
-                    const float2 dv = __fadd2_rn(make_float2(fy0 + (float)(4 * s), fy0 + (float)(4 * s + 4)), nqy);
-                    const float2 disc = __ffma2_rn(dv, __ffma2_rn(dv, vv2, u12), u02);
-                    take2(s, raster_root_cone2(t0, kap, capw, raster_ray2(q2, q3, q4, f2(du), dv), disc));
+                    for (int s = 0; s < kSteps; s += 2) {
+                        if (!((wm >> s) & 3u)) continue;
+                        const float2 dv =
+                            __fadd2_rn(make_float2(fy0 + (float)(4 * s), fy0 + (float)(4 * s + 4)), nqy);
+                        const float2 disc = __ffma2_rn(dv, __ffma2_rn(dv, vv2, u12), u02);
+                        take2(s, raster_root_cone2_front(kap, capw, raster_ray2(q2, q3, q4, f2(du), dv), disc));
+                    }
+                } else {
+#pragma unroll
+                    for (int s = 0; s < kSteps; s += 2) {
+                        if (!((wm >> s) & 3u)) continue;
+                        const float2 dv =
+                            __fadd2_rn(make_float2(fy0 + (float)(4 * s), fy0 + (float)(4 * s + 4)), nqy);
+                        const float2 disc = __ffma2_rn(dv, __ffma2_rn(dv, vv2, u12), u02);
+                        take2(s, raster_root_cone2(t0, kap, capw, raster_ray2(q2, q3, q4, f2(du), dv), disc));
+                    }
                 }
             }
         }

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW)
             const int c0 = s_pre[k], c1 = s_pre[k + 1];
             const float4* R = s_rast + kRastVec * j;
             const float4 q0 = R[0], q1 = R[1], q2 = R[2], q3 = R[3], q4 = R[4];  // in registers for the chunks
-            const float t0 = q2.w;
+            const bool front = raster_in_front(lo_i16(__int_as_float(s_pbox[j].x)));
             for (; c < c1; c += NW) {
                 const int idx = ((c - c0) << 5) + lane;
                 if (idx < rc.w) {
@@ -229,8 +229,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW)
                     const int px = rc.x + idx - y * rc.z, py = rc.y + y;
                     const float du = (float)px - q0.x, dv = (float)py - q0.y;
                     const float disc = raster_disc(q0, q1, du, dv);
-                    const float sh = raster_maybe(q4, disc) ? raster_hit(q2, q3, q4, du, dv, disc) : INFINITY;
-                    const float zz = t0 + sh;
+                    const float zz = raster_maybe(q4, disc) ? raster_hit_z(q2, q3, q4, du, dv, disc, front) : INFINITY;
                     if (zz < INFINITY) atomicMin(&s_z[(py - ty0) * TW + (px - tx0)], __float_as_uint(zz));
                 }
             }

@@ -73,9 +73,15 @@ class Scene:
 
 
 def make_scene(W, H, P, seed, *, zoom=1.0, noisy=False, f32=True, spread=1.0, shift=(0.0, 0.0),
-               cam=None, geometry=None) -> Scene:
+               cam=None, geometry=None, place=None) -> Scene:
+    """place: (x, y, z) of the hand's root in mm in place of the seeded pose's,
+    with the model's translation limits widened to hold it."""
     g = geometry_f32() if geometry is None else geometry
     lo, hi = I.search_limits()
+    if place is not None:
+        lo, hi = lo.copy(), hi.copy()
+        lo[:3] = np.minimum(lo[:3], np.asarray(place) - 50.0)
+        hi[:3] = np.maximum(hi[:3], np.asarray(place) + 50.0)
     if cam is None:
         cam = oracle.camera_tuple(I.kinect_camera(W, H))
         cam[:2] *= zoom
@@ -83,6 +89,8 @@ def make_scene(W, H, P, seed, *, zoom=1.0, noisy=False, f32=True, spread=1.0, sh
     gt = I.ground_truth_pose(seed).astype(np.float32)
     gt[0] += shift[0]
     gt[1] += shift[1]
+    if place is not None:
+        gt[:3] = place
     mo = oracle.Model.from_geometry(g, lo.astype(np.float32), hi.astype(np.float32))
     depth, hit, _, _ = oracle.render_pose(mo, gt.astype(np.float64), cam.astype(np.float64), W, H, boundary=False)
     if noisy:

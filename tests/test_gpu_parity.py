@@ -152,6 +152,28 @@ def test_render_score_parity(name, W, H, P, seed, kw, variant):
     REPORT[f"{name}/variant{variant}"] = rep
 
 
+@pytest.mark.parametrize("name,place", [
+    ("camera_inside_palm", (-18.4, 41.1, 12.0)),
+    ("hand_across_near_plane", (0.0, 60.0, 50.0)),
+])
+@pytest.mark.parametrize("variant", sorted(set(hs.RENDER_VARIANTS.values()) - {hs.RENDER_AUTO}))
+def test_hand_at_the_camera(name, place, variant):
+    """The hand placed at the camera (particles within 5 mm of it, some behind
+    the camera): primitives that reach the plane z = 1 mm get the whole ROI from
+    FK and the renderers' general roots (the far root where the camera is inside
+    a primitive, depth tests for what lies behind it); those beyond the plane
+    take the roots for primitives in front of the camera.  Every kernel against
+    the FP64 oracle with the full protocol, and bit-identical to the unit kernel."""
+    sc = C.make_scene(64, 48, 12, 816, spread=0.5, place=place)
+    gr = C.run_gpu(sc, variant=variant)
+    rep = {}
+    C.check_parity(sc, gr, C.run_oracle(sc), rep)
+    REPORT[f"{name}/variant{variant}"] = rep
+    if variant != hs.RENDER_UNITS:
+        _assert_same_bits(gr, C.run_gpu(sc, variant=hs.RENDER_UNITS), variant)
+    assert hs.hs_get_device_status(clear=True) == 0
+
+
 def _assert_same_bits(gr, ref, v):
     assert np.array_equal(gr.parts, ref.parts), v
     assert np.array_equal(gr.E.view(np.uint32), ref.E.view(np.uint32)), v

@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(kMultiThreads, 8)
         uint32_t acc_a = 0, acc_o = 0, acc_h = 0;
         bool ok = true;
         if (box[3] > 0)
-            ok = render_units_warp(s_rast, s_pbox, n_prims, box, sh.tile[warp], sh.bar[warp], phases, warp,
+            ok = render_units_warp<false>(s_rast, s_pbox, n_prims, box, sh.tile[warp], sh.bar[warp], phases, warp,
                                    kMultiWarps, pv, ra, q, lane, acc_t, acc_a, acc_o, acc_h);
         warp_sum(acc_t, acc_a, acc_o, acc_h);
         if (lane == 0) {

@@ -113,7 +113,10 @@ __device__ __forceinline__ void cull_unit(const int2* pbox, int n_prims, int lan
 // an observation load did not arrive in time (status flagged; the warp's
 // remaining units are skipped and no copy is left in flight).  extra_tx: zero,
 // except in the test of that time limit (bytes the first load is armed for
-// beyond those copied).
+// beyond those copied).  kFrontRoots: primitives in front of the camera take
+// the shorter roots (same bits; the batch frame kernel, at 64 registers, keeps
+// the general roots only, which spill less there).
+template <bool kFrontRoots = true>
 __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2* pbox, int n_prims, const int* box,
                                                   unsigned char (*tile)[kSlot], uint64_t* bar, uint32_t& phases,
                                                   int first, int stride, const ParticleView& pv, const RenderArgs& a,
@@ -194,7 +197,8 @@ __device__ __forceinline__ bool render_units_warp(const float4* rast, const int2
                         const Ray2 r = raster_ray2(q2, q3, q4, make_float2(du0, du1), f2(dv));
                         const float2 disc = make_float2(d0, d1);
                         // in front of the camera (warp-uniform): no far root, no depth tests
-                        const bool front = raster_in_front(lo_i16(__int_as_float(pbox[b + 32 * w].x)));
+                        const bool front =
+                            kFrontRoots && raster_in_front(lo_i16(__int_as_float(pbox[b + 32 * w].x)));
                         float2 sh;
                         if (q3.w > 1.5f && front) {
                             const float2 sn = raster_near_ellipsoid2_front(r, disc);

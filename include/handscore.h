@@ -589,7 +589,7 @@ int polish_keep_better(float* x, float* E, const int32_t* sel, int k, const floa
 
 /* ---- render autotuning -----------------------------------------------------------
  * Time every render kernel (HS_RENDER_UNITS .. HS_RENDER_VARIANTS - 1) with CTAs
- * per particle from {automatic, 1, 2, 4, 8, 16, 32} (more than 1 only while
+ * per particle from {automatic, 1, 2, 3, 4, 6, 8, 16, 32} (more than 1 only while
  * K * P stays within about four resident waves; the persistent kernels take
  * none) on the caller's own inputs, and
  * write the fastest into params->variant and params->ctas_per_particle (the
@@ -603,7 +603,7 @@ int polish_keep_better(float* x, float* E, const int32_t* sel, int k, const floa
  * objectives.  Errors: as render_score_batch / render_score_multi, and
  * HS_ERR_ARG for reps outside 1..1000.  The paper has no counterpart: its
  * render is a fixed OpenGL pipeline. */
-#define HS_TUNE_CTAS 7
+#define HS_TUNE_CTAS 9
 int render_score_batch_autotune(const HsModel* model, const HsObs* obs, const HsCamera* cam, const HsPrim* prims,
                                 const float* kc, int P, HsScoreParams* params, void* workspace,
                                 size_t workspace_bytes, float* E, int reps, float* times_us, hs_stream_t stream);

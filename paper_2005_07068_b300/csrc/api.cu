@@ -1143,7 +1143,7 @@ int track_frame_multi(const HsModel* model, const HsBatch* b, const HsSwarm* sw,
 }  // extern "C"
 
 namespace {
-constexpr int kTuneCtas[HS_TUNE_CTAS] = {0, 1, 2, 4, 8, 16, 32};  // 0: the automatic choice
+constexpr int kTuneCtas[HS_TUNE_CTAS] = {0, 1, 2, 3, 4, 6, 8, 16, 32};  // 0: the automatic choice
 
 // Times every (kernel, CTAs per particle) candidate of one render call and keeps
 // the fastest.  Each candidate's `reps` calls are captured into a CUDA graph on

@@ -639,7 +639,7 @@ def track_frame_multi(model: Model, batch: Batch, sw: Swarm, x_next: torch.Tenso
                                    _stream(stream)))
 
 
-TUNE_CTAS = (0, 1, 2, 4, 8, 16, 32)  # 0: the automatic choice
+TUNE_CTAS = (0, 1, 2, 3, 4, 6, 8, 16, 32)  # 0: the automatic choice
 
 
 def _tune_table(times) -> dict:

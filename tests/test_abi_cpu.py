@@ -60,6 +60,7 @@ int main(void) {
   printf("HS_MAX_PARTICLES %d\\n", (int)HS_MAX_PARTICLES);
   printf("HS_MAX_PRIMS %d\\n", (int)HS_MAX_PRIMS);
   printf("HS_FRAME_MAX_PARTICLES %d\\n", (int)HS_FRAME_MAX_PARTICLES);
+  printf("HS_TUNE_CTAS %d\\n", (int)HS_TUNE_CTAS);
   return 0;
 }
 """)
@@ -82,7 +83,7 @@ int main(void) {
         # constants the binding repeats
         "HS_NOALLOC_SCRATCH_BYTES": hs.NOALLOC_SCRATCH_BYTES, "HS_FUSED_MAX_PARTICLES": hs.FUSED_MAX_PARTICLES,
         "HS_MAX_PARTICLES": hs.MAX_PARTICLES, "HS_FRAME_MAX_PARTICLES": hs.FRAME_MAX_PARTICLES,
-        "HS_MAX_PRIMS": hs.MAX_PRIMS,
+        "HS_MAX_PRIMS": hs.MAX_PRIMS, "HS_TUNE_CTAS": len(hs.TUNE_CTAS),
     }
     for k, v in py.items():
         assert int(got[k]) == v, k

@@ -117,7 +117,8 @@ class GpuResult:
     kc: np.ndarray
 
 
-def run_gpu(sc: Scene, debug=True, poses=None, variant=hs.RENDER_AUTO, ctas=0) -> GpuResult:
+def run_gpu(sc: Scene, debug=True, poses=None, variant=hs.RENDER_AUTO, ctas=0, edit_prims=None) -> GpuResult:
+    """edit_prims: called with the FK records (device tensor) before the render, to change them in place."""
     poses = sc.poses if poses is None else poses
     P = poses.shape[0]
     dev = torch.device("cuda")
@@ -128,6 +129,8 @@ def run_gpu(sc: Scene, debug=True, poses=None, variant=hs.RENDER_AUTO, ctas=0) -
     prims = torch.zeros(P, sc.model_g.n_prims, 16, dtype=torch.float32, device=dev)
     kc = torch.zeros(P, dtype=torch.float32, device=dev)
     hs.pose_fk(sc.model_g, tp, cam, prims, kc)
+    if edit_prims is not None:
+        edit_prims(prims)
     ws = hs.new_workspace(P, dev)
     E = torch.zeros(P, dtype=torch.float32, device=dev)
     parts = torch.zeros(P, 4, dtype=torch.int32, device=dev)

@@ -174,6 +174,32 @@ def test_hand_at_the_camera(name, place, variant):
     assert hs.hs_get_device_status(clear=True) == 0
 
 
+def _sentinel_boxes(prims):
+    """Every record's screen box set to the one FK gives a primitive that
+    reaches the plane z = 1 mm: (-32767, -32767) to (32767, 32767)."""
+    w = prims.cpu().numpy().view(np.uint32)
+    w[..., 14] = 0x80018001  # u0, v0 = -32767 (int16 pairs)
+    w[..., 15] = 0x7FFF7FFF  # u1, v1 = 32767
+    prims.copy_(torch.from_numpy(w.view(np.float32)))
+
+
+@pytest.mark.parametrize("variant", sorted(set(hs.RENDER_VARIANTS.values()) - {hs.RENDER_AUTO}))
+def test_front_roots_equal_general_roots(variant):
+    """The shorter roots of primitives in front of the camera give the general
+    roots' bits.  The same particles are rendered once with FK's boxes and once
+    with every box set to the sentinel of a primitive that reaches the plane
+    z = 1 mm, which sends every primitive through the general roots (far root,
+    depth tests) over the whole ROI: every pixel's depth and mask, the counts
+    and E agree bit for bit."""
+    sc = C.make_scene(96, 72, 12, 817, zoom=1.5, noisy=True, f32=False, spread=1.5)
+    front = C.run_gpu(sc, variant=variant)
+    general = C.run_gpu(sc, variant=variant, edit_prims=_sentinel_boxes)
+    assert (general.prims[..., 14:16].view(np.int16)[..., 0] == -32767).all()
+    assert (front.prims[..., 14:16].view(np.int16)[..., 0] > -32767).all()  # every primitive in front
+    assert front.mask.any()
+    _assert_same_bits(general, front, variant)
+
+
 def _assert_same_bits(gr, ref, v):
     assert np.array_equal(gr.parts, ref.parts), v
     assert np.array_equal(gr.E.view(np.uint32), ref.E.view(np.uint32)), v

@@ -173,7 +173,12 @@ typedef struct {
  *            ellipsoid are left out, which does not change any depth
  *   m[13]    kappa for HS_PRIM_ECONE; 2.0 marks an ellipsoid
  *   m[14]    (int16 u0, int16 v0), m[15] (int16 u1, int16 v1): conservative
- *            inclusive pixel box of the primitive's projection              */
+ *            inclusive pixel box of the primitive's projection; a primitive
+ *            that reaches the plane z = 1 mm gets (-32767, -32767, 32767,
+ *            32767).  The renderers take u0 != -32767 to mean that the whole
+ *            solid lies beyond that plane (they then skip the far root and
+ *            the tests of positive depth), so records made elsewhere than by
+ *            pose_fk must keep that rule                                    */
 typedef struct {
     float m[16];
 } HsPrim;
